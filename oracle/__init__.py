@@ -1,0 +1,172 @@
+"""CPU oracle for the fit-objective gradients -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package.  The CUDA
+product path (``paper_2203_06139_gb300``) never imports it and shares no code
+with it.
+
+The arithmetic lives in ``cg_oracle.c``: a scalar tape-based reverse-mode AD
+(Sec. 1-2 of the paper: reverse accumulation recorded on a tape, the
+"tracing" approach) over the fit objectives of the histogram-fitting use case
+(Sec. 4, Fig. 3).  This module compiles it with gcc (``-ffp-contract=off``)
+and calls it through ctypes.  ctypes releases the GIL during the call, so
+``many()`` evaluates independent parameter points on several host threads.
+"""
+import ctypes
+import os
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cg_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "libcg_oracle.so")
+
+# objective codes of the oracle (its own numbering)
+CHI2, POISSON, POISSON_BC = 0, 1, 2
+OK, INVALID, DOMAIN = 0, 1, 2
+
+_lib = None
+
+
+def build(force=False):
+    """Compile cg_oracle.c into libcg_oracle.so next to it (plain gcc, no FMA contraction)."""
+    stale = (not os.path.exists(_LIB_PATH)
+             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+    if force or stale:
+        tmp = "%s.%d.tmp" % (_LIB_PATH, os.getpid())
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    dp = ctypes.POINTER(ctypes.c_double)
+    i64, c_int, c_d = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    lib.orc_binned1d.argtypes = [c_int, c_int, c_int, c_int, i64, c_d, c_d, dp, dp, dp, dp, dp, dp]
+    lib.orc_binned1d_gn.argtypes = [c_int, c_int, c_int, c_int, i64, c_d, c_d, dp, dp, dp, dp]
+    lib.orc_gauss_poly_eval.argtypes = [c_int, c_int, c_int, c_d, c_d, i64, dp, dp, dp]
+    lib.orc_unbinned_mix.argtypes = [i64, dp, dp, c_d, c_d, dp, dp, dp, dp]
+    lib.orc_binned2d.argtypes = [c_int, i64, i64, c_d, c_d, c_d, c_d, dp, dp, dp, dp, dp]
+    lib.orc_listing1_gauss.argtypes = [c_d, c_d, c_d, dp, dp, dp]
+    for f in (lib.orc_binned1d, lib.orc_binned1d_gn, lib.orc_gauss_poly_eval,
+              lib.orc_unbinned_mix, lib.orc_binned2d, lib.orc_listing1_gauss):
+        f.restype = c_int
+    _lib = lib
+    return lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Result:
+    """Objective value, gradient, per-component scale S_k = sum_i |dT_i/dtheta_k|, status."""
+
+    def __init__(self, value, grad, scale, rc):
+        self.value, self.grad, self.scale, self.rc = value, grad, scale, rc
+
+    def __repr__(self):
+        return "Result(value=%r, grad=%r, rc=%d)" % (self.value, self.grad, self.rc)
+
+
+def num_params_gauss_poly(K, D):
+    return 3 * K + D + 1
+
+
+def binned1d(K, D, poly_mode, obj, y, lo, hi, theta, centres=None):
+    """1-D binned objective of K Gaussian peaks + degree-D polynomial (see cg_oracle.c)."""
+    lib = _load()
+    y = _f64(y)
+    theta = _f64(theta)
+    centres = _f64(centres)
+    P = 3 * K + D + 1
+    assert theta.shape == (P,)
+    g = np.zeros(P)
+    s = np.zeros(P)
+    v = ctypes.c_double(0.0)
+    rc = lib.orc_binned1d(K, D, poly_mode, obj, y.size, lo, hi, _p(centres), _p(y), _p(theta),
+                          ctypes.byref(v), _p(g), _p(s))
+    return Result(v.value, g, s, rc)
+
+
+def binned1d_gn(K, D, poly_mode, obj, y, lo, hi, theta, centres=None):
+    """Gauss-Newton diagonal sum_i h_i (df_i/dtheta_k)^2 of a 1-D binned objective."""
+    lib = _load()
+    y = _f64(y)
+    theta = _f64(theta)
+    centres = _f64(centres)
+    gn = np.zeros(3 * K + D + 1)
+    rc = lib.orc_binned1d_gn(K, D, poly_mode, obj, y.size, lo, hi, _p(centres), _p(y), _p(theta),
+                             _p(gn))
+    assert rc == OK
+    return gn
+
+
+def gauss_poly_eval(K, D, poly_mode, lo, hi, x, theta):
+    """Model value f(x) of the 1-D family at points x."""
+    lib = _load()
+    x = _f64(x)
+    theta = _f64(theta)
+    out = np.zeros(x.size)
+    rc = lib.orc_gauss_poly_eval(K, D, poly_mode, lo, hi, x.size, _p(x), _p(theta), _p(out))
+    assert rc == OK
+    return out
+
+
+def unbinned_mix(x, lo, hi, theta, weights=None):
+    """Unbinned NLL of the Gaussian + exponential mixture, theta = (frac, mu, s, lambda)."""
+    lib = _load()
+    x = _f64(x)
+    theta = _f64(theta)
+    weights = _f64(weights)
+    g = np.zeros(4)
+    s = np.zeros(4)
+    v = ctypes.c_double(0.0)
+    rc = lib.orc_unbinned_mix(x.size, _p(x), _p(weights), lo, hi, _p(theta), ctypes.byref(v),
+                              _p(g), _p(s))
+    return Result(v.value, g, s, rc)
+
+
+def binned2d(K, counts, lx, hx, ly, hy, theta):
+    """2-D binned Poisson NLL of K rotated Gaussians + constant; counts has shape (ny, nx)."""
+    lib = _load()
+    counts = _f64(counts)
+    ny, nx = counts.shape
+    theta = _f64(theta)
+    P = 6 * K + 1
+    g = np.zeros(P)
+    s = np.zeros(P)
+    v = ctypes.c_double(0.0)
+    rc = lib.orc_binned2d(K, nx, ny, lx, hx, ly, hy, _p(counts), _p(theta), ctypes.byref(v),
+                          _p(g), _p(s))
+    return Result(v.value, g, s, rc)
+
+
+def listing1_gauss(x, p, sigma):
+    """The Gaussian of Listing 1 and its derivatives with respect to x and p."""
+    lib = _load()
+    v, dx, dp = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    rc = lib.orc_listing1_gauss(x, p, sigma, ctypes.byref(v), ctypes.byref(dx), ctypes.byref(dp))
+    assert rc == OK
+    return v.value, dx.value, dp.value
+
+
+def many(fn, thetas, threads=None, **kw):
+    """Evaluate fn(theta=t, **kw) for every row of thetas on a pool of host threads."""
+    thetas = np.asarray(thetas, dtype=np.float64)
+    threads = threads or os.cpu_count() or 1
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        return list(ex.map(lambda t: fn(theta=t, **kw), list(thetas)))

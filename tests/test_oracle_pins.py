@@ -1,0 +1,350 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+Each test checks the tape-AD oracle (oracle/cg_oracle.c) against one of:
+closed-form derivatives derived by hand (written independently below),
+central finite differences of its own value, invariants that hold exactly
+(vanishing gradient at noise-free data, the normalisation of a pdf, the
+linear-least-squares sub-problem), library routines (numpy.linalg.lstsq,
+scipy.integrate.quad, Gauss-Legendre nodes) and brute-force expansion of
+tiny cases.  The objective definitions follow the histogram-fitting use of
+AD gradients in Sec. 4 (Fig. 3) of the paper and the Gaussian of Listing 1.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle
+from oracle.fit import CONVERGED, bfgs_fit
+from paper_2203_06139_gb300 import synth
+from tests._metrics import max_rel_err
+
+OBJS = [oracle.CHI2, oracle.POISSON, oracle.POISSON_BC]
+
+
+# --------------------------------------------------------------------------
+# hand-derived closed forms (independent of the tape)
+# --------------------------------------------------------------------------
+def closed_form_binned1d(K, D, poly_mode, obj, y, lo, hi, theta):
+    """Value and gradient of a 1-D binned objective from derivatives taken by
+    hand: dG/dA = e, dG/dmu = A e (x-mu)/s^2, dG/ds = A e (x-mu)^2/s^3,
+    df/dc_j = u^j; dT/df = -2 w (y-f) (chi2), 1 - y/f (Poisson),
+    2 (1 - y/f) (Baker-Cousins)."""
+    n = y.size
+    x = lo + (np.arange(n) + 0.5) * ((hi - lo) / n)
+    u = x if poly_mode == 0 else (2 * x - lo - hi) / (hi - lo)
+    P = 3 * K + D + 1
+    J = np.zeros((n, P))
+    f = np.zeros(n)
+    for k in range(K):
+        A, mu, s = theta[3 * k:3 * k + 3]
+        e = np.exp(-(x - mu) ** 2 / (2 * s * s))
+        f += A * e
+        J[:, 3 * k] = e
+        J[:, 3 * k + 1] = A * e * (x - mu) / s ** 2
+        J[:, 3 * k + 2] = A * e * (x - mu) ** 2 / s ** 3
+    for j in range(D + 1):
+        f += theta[3 * K + j] * u ** j
+        J[:, 3 * K + j] = u ** j
+    if obj == oracle.CHI2:
+        w = 1.0 / np.maximum(y, 1.0)
+        T = w * (y - f) ** 2
+        dT = -2 * w * (y - f)
+    elif obj == oracle.POISSON:
+        T = f - np.where(y > 0, y * np.log(np.where(y > 0, f, 1.0)), 0.0)
+        dT = 1 - y / f
+    else:
+        ylog = np.where(y > 0, y * np.log(np.where(y > 0, y / f, 1.0)), 0.0)
+        T = 2 * (f - y + ylog)
+        dT = 2 * (1 - y / f)
+    return math.fsum(T), np.array([math.fsum(dT * J[:, k]) for k in range(P)])
+
+
+@pytest.mark.parametrize("obj", OBJS)
+@pytest.mark.parametrize("K,D,poly_mode", [(1, 1, 0), (2, 2, 1), (3, 1, 0), (1, -1, 0), (0, 3, 1)])
+def test_binned1d_matches_hand_derivatives(obj, K, D, poly_mode):
+    p = synth.random_gauss_poly(max(K, 1) if K else 1, D, 301, lo=-1.0, hi=2.0,
+                                poly_mode=poly_mode, seed=7 * K + D + 3)
+    if K == 0:
+        theta = p["theta"][3:]
+        y = np.maximum(p["y"], 0.0)
+        mean = synth.expected_counts_1d(0, D, poly_mode, -1.0, 2.0, 301, theta)
+        y = np.random.default_rng(1).poisson(np.maximum(mean, 1.0)).astype(float)
+        theta = theta.copy()
+        theta[0] = abs(theta[0]) + 50.0
+    else:
+        theta, y = p["theta"], p["y"]
+    r = oracle.binned1d(K, D, poly_mode, obj, y, -1.0, 2.0, theta)
+    assert r.rc == oracle.OK
+    v, g = closed_form_binned1d(K, D, poly_mode, obj, y, -1.0, 2.0, theta)
+    assert abs(r.value - v) <= 1e-13 * abs(v)
+    assert max_rel_err(r.grad, g, r.scale, floor=1e-9) <= 1e-12
+
+
+def test_brute_force_four_bins():
+    """Four bins of one Gaussian on a constant, expanded term by term."""
+    y = np.array([3.0, 0.0, 7.0, 2.0])
+    th = np.array([5.0, 0.45, 0.2, 1.5])   # A, mu, s, c0
+    xs = [0.125, 0.375, 0.625, 0.875]
+    val = 0.0
+    grad = np.zeros(4)
+    for xi, yi in zip(xs, y):
+        e = math.exp(-((xi - 0.45) ** 2) / (2 * 0.04))
+        f = 5.0 * e + 1.5
+        w = 1.0 / max(yi, 1.0)
+        val += w * (yi - f) ** 2
+        c = -2.0 * w * (yi - f)
+        grad += c * np.array([e, 5.0 * e * (xi - 0.45) / 0.04, 5.0 * e * (xi - 0.45) ** 2 / 0.008, 1.0])
+    r = oracle.binned1d(1, 0, 0, oracle.CHI2, y, 0.0, 1.0, th)
+    assert abs(r.value - val) <= 1e-14 * val
+    np.testing.assert_allclose(r.grad, grad, rtol=1e-13, atol=0)
+
+
+def test_peak_height_convention():
+    """Amplitude is the peak height ("gaus" of Fig. 3a): f(mu) = A + background."""
+    th = np.array([123.0, 0.3, 0.05, 7.0, 2.0])
+    f = oracle.gauss_poly_eval(1, 1, 0, 0.0, 1.0, np.array([0.3, 0.35]), th)
+    assert abs(f[0] - (123.0 + 7.0 + 0.6)) < 1e-12
+    assert abs(f[1] - (123.0 * math.exp(-0.5) + 7.0 + 0.7)) < 1e-12
+
+
+@pytest.mark.parametrize("obj", OBJS)
+def test_binned1d_central_fd(obj):
+    p = synth.random_gauss_poly(2, 1, 500, seed=11)
+    th = p["theta"]
+    r = oracle.binned1d(2, 1, 0, obj, p["y"], 0.0, 1.0, th)
+    fd = np.zeros_like(th)
+    for k in range(th.size):
+        h = 1e-6 * max(abs(th[k]), 1e-3)
+        tp, tm = th.copy(), th.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd[k] = (oracle.binned1d(2, 1, 0, obj, p["y"], 0.0, 1.0, tp).value
+                 - oracle.binned1d(2, 1, 0, obj, p["y"], 0.0, 1.0, tm).value) / (2 * h)
+    assert max_rel_err(r.grad, fd, r.scale) <= 1e-5
+
+
+@pytest.mark.parametrize("obj", OBJS)
+def test_noise_free_gradient_vanishes(obj):
+    """Counts equal to the truth density (from the generator, not the oracle)
+    make every residual zero, so the gradient vanishes at the truth."""
+    h = synth.c1_histogram(n_bins=2000, noise=False)
+    r = oracle.binned1d(1, 1, 0, obj, h["y"], 0.0, 10.0, h["truth"])
+    assert r.rc == oracle.OK
+    # at the truth every per-bin term is rounding noise; measure it against
+    # the per-component scale 1% away from the truth
+    ref = oracle.binned1d(1, 1, 0, obj, h["y"], 0.0, 10.0, h["truth"] * 1.01)
+    assert np.all(np.abs(r.grad) <= 1e-12 * ref.scale)
+    assert np.all(np.abs(ref.grad) > 1e-3 * ref.scale)
+    if obj == oracle.CHI2 or obj == oracle.POISSON_BC:
+        assert abs(r.value) <= 1e-9 * h["y"].sum()
+
+
+def test_linear_least_squares_subproblem():
+    """At fixed (mu, s), chi2 is linear least squares in (A, c0, c1); at the
+    numpy.linalg.lstsq solution the oracle's gradient in those is zero."""
+    h = synth.c1_histogram(n_bins=3000)
+    x = synth.uniform_centres(3000, 0.0, 10.0)
+    mu, s = 5.02, 0.49
+    e = np.exp(-(x - mu) ** 2 / (2 * s * s))
+    sw = np.sqrt(1.0 / np.maximum(h["y"], 1.0))
+    X = np.stack([e, np.ones_like(x), x], 1) * sw[:, None]
+    coef = np.linalg.lstsq(X, h["y"] * sw, rcond=None)[0]
+    th = np.array([coef[0], mu, s, coef[1], coef[2]])
+    r = oracle.binned1d(1, 1, 0, oracle.CHI2, h["y"], 0.0, 10.0, th)
+    for k in (0, 3, 4):
+        assert abs(r.grad[k]) <= 1e-9 * r.scale[k]
+    assert abs(r.grad[1]) > 1e-6 * r.scale[1]
+
+
+def test_gauss_newton_diagonal():
+    p = synth.random_gauss_poly(2, 2, 400, poly_mode=1, seed=3)
+    th = p["theta"]
+    for obj in OBJS:
+        gn = oracle.binned1d_gn(2, 2, 1, obj, p["y"], 0.0, 1.0, th)
+        x = synth.uniform_centres(400, 0.0, 1.0)
+        t = 2 * x - 1
+        J = []
+        f = np.zeros(400)
+        for k in range(2):
+            A, mu, s = th[3 * k:3 * k + 3]
+            e = np.exp(-(x - mu) ** 2 / (2 * s * s))
+            f += A * e
+            J += [e, A * e * (x - mu) / s ** 2, A * e * (x - mu) ** 2 / s ** 3]
+        for j in range(3):
+            f += th[6 + j] * t ** j
+            J.append(t ** j)
+        J = np.array(J)
+        y = p["y"]
+        hh = {oracle.CHI2: 2 / np.maximum(y, 1), oracle.POISSON: y / f ** 2,
+              oracle.POISSON_BC: 2 * y / f ** 2}[obj]
+        np.testing.assert_allclose(gn, (hh[None, :] * J ** 2).sum(1), rtol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# unbinned mixture
+# --------------------------------------------------------------------------
+def test_unbinned_pdf_normalised():
+    """exp(-NLL) of one event is p(x); its integral over [lo, hi] is 1 for any
+    parameters (scipy quad), and separately for each component."""
+    for th in ([0.3, 2.0, 0.3, 0.5], [0.7, 9.5, 1.7, 2.2], [1.0, 4.0, 0.8, 0.1], [0.0, 4.0, 0.8, 0.9]):
+        def p(x):
+            return math.exp(-oracle.unbinned_mix(np.array([x]), 0.0, 10.0, np.array(th)).value)
+        val, _ = integrate.quad(p, 0.0, 10.0, points=[th[1]], limit=200, epsabs=1e-13, epsrel=1e-12)
+        assert abs(val - 1.0) < 1e-9
+
+
+def test_unbinned_hand_derivatives():
+    x = synth.c2_events(2000)
+    th = np.array([0.35, 2.1, 0.27, 0.55])
+    f, mu, s, lam = th
+    lo, hi = 0.0, 10.0
+    Phi = lambda z: 0.5 * math.erfc(-z / math.sqrt(2))
+    phi = lambda z: math.exp(-0.5 * z * z) / math.sqrt(2 * math.pi)
+    a, b = (lo - mu) / s, (hi - mu) / s
+    ZG = Phi(b) - Phi(a)
+    ZE = math.exp(-lam * lo) - math.exp(-lam * hi)
+    g = np.exp(-0.5 * ((x - mu) / s) ** 2) / (s * math.sqrt(2 * math.pi)) / ZG
+    e = lam * np.exp(-lam * x) / ZE
+    p = f * g + (1 - f) * e
+    # dZG/dmu = (phi(a) - phi(b))/s ; dZG/ds = (a phi(a) - b phi(b))/s
+    dZG_mu = (phi(a) - phi(b)) / s
+    dZG_s = (a * phi(a) - b * phi(b)) / s
+    dg_mu = g * ((x - mu) / s ** 2 - dZG_mu / ZG)
+    dg_s = g * ((x - mu) ** 2 / s ** 3 - 1 / s - dZG_s / ZG)
+    dZE_lam = -lo * math.exp(-lam * lo) + hi * math.exp(-lam * hi)
+    de_lam = e * (1 / lam - x - dZE_lam / ZE)
+    grad = -np.array([math.fsum((g - e) / p), math.fsum(f * dg_mu / p), math.fsum(f * dg_s / p),
+                      math.fsum((1 - f) * de_lam / p)])
+    r = oracle.unbinned_mix(x, lo, hi, th)
+    assert abs(r.value + math.fsum(np.log(p))) <= 1e-13 * abs(r.value)
+    assert max_rel_err(r.grad, grad, r.scale, floor=1e-9) <= 1e-11
+
+
+def test_unbinned_asimov_gradient_vanishes():
+    """Weighted events at Gauss-Legendre nodes with weights w_j p(x_j; theta*)
+    integrate the NLL against the true pdf; its gradient at theta* is
+    -grad of the integral of p, which is zero because p stays normalised."""
+    th = np.array([0.3, 2.0, 0.3, 0.5])
+    nodes, wts = np.polynomial.legendre.leggauss(64)
+    xs, ws = [], []
+    edges = np.concatenate([np.linspace(0.0, 4.0, 81), np.linspace(4.0, 10.0, 13)[1:]])
+    for a, b in zip(edges[:-1], edges[1:]):
+        xs.append(0.5 * (b - a) * nodes + 0.5 * (a + b))
+        ws.append(0.5 * (b - a) * wts)
+    xs = np.concatenate(xs)
+    ws = np.concatenate(ws)
+    px = np.array([math.exp(-oracle.unbinned_mix(np.array([xx]), 0.0, 10.0, th).value) for xx in xs])
+    assert abs(np.dot(ws, px) - 1.0) < 1e-12
+    r = oracle.unbinned_mix(xs, 0.0, 10.0, th, weights=ws * px)
+    assert np.all(np.abs(r.grad) <= 1e-11 * r.scale), (r.grad, r.scale)
+    # and it does not vanish away from the truth
+    r2 = oracle.unbinned_mix(xs, 0.0, 10.0, th * 1.05, weights=ws * px)
+    assert np.all(np.abs(r2.grad) > 1e-5 * r2.scale)
+
+
+def test_unbinned_central_fd():
+    x = synth.c2_events(5000)
+    th = np.array([0.28, 1.9, 0.33, 0.47])
+    r = oracle.unbinned_mix(x, 0.0, 10.0, th)
+    for k in range(4):
+        h = 1e-6 * abs(th[k])
+        tp, tm = th.copy(), th.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd = (oracle.unbinned_mix(x, 0.0, 10.0, tp).value - oracle.unbinned_mix(x, 0.0, 10.0, tm).value) / (2 * h)
+        assert abs(fd - r.grad[k]) <= 1e-5 * max(abs(r.grad[k]), 1e-6 * r.scale[k])
+
+
+# --------------------------------------------------------------------------
+# 2-D rotated Gaussians
+# --------------------------------------------------------------------------
+def closed_form_2d(K, counts, theta):
+    ny, nx = counts.shape
+    X = synth.uniform_centres(nx, 0.0, 1.0)[None, :]
+    Y = synth.uniform_centres(ny, 0.0, 1.0)[:, None]
+    mu = np.full(counts.shape, theta[6 * K])
+    parts = []
+    for k in range(K):
+        A, mx, my, sx, sy, ph = theta[6 * k:6 * k + 6]
+        c, s = math.cos(ph), math.sin(ph)
+        dx, dy = X - mx, Y - my
+        u = c * dx + s * dy
+        v = -s * dx + c * dy
+        e = np.exp(-0.5 * (u * u / sx ** 2 + v * v / sy ** 2))
+        mu = mu + A * e
+        # d/d(mu_x): A e (u c/sx^2 - v s/sy^2); d/d(mu_y): A e (u s/sx^2 + v c/sy^2)
+        # d/d(sx): A e u^2/sx^3; d/d(sy): A e v^2/sy^3; d/d(phi): -A e u v (1/sx^2 - 1/sy^2)
+        parts += [e, A * e * (u * c / sx ** 2 - v * s / sy ** 2), A * e * (u * s / sx ** 2 + v * c / sy ** 2),
+                  A * e * u * u / sx ** 3, A * e * v * v / sy ** 3, -A * e * u * v * (1 / sx ** 2 - 1 / sy ** 2)]
+    parts.append(np.ones(counts.shape))
+    dT = 1 - counts / mu
+    T = mu - np.where(counts > 0, counts * np.log(mu), 0.0)
+    return math.fsum(T.ravel()), np.array([math.fsum((dT * p).ravel()) for p in parts])
+
+
+def test_binned2d_hand_derivatives():
+    K = 3
+    truth = synth.c3_truth(K)
+    th = truth * (1 + np.random.default_rng(5).uniform(-0.05, 0.05, truth.size))
+    counts = np.random.default_rng(6).poisson(synth.expected_counts_2d(truth, K, 37, 29)).astype(float)
+    r = oracle.binned2d(K, counts, 0.0, 1.0, 0.0, 1.0, th)
+    v, g = closed_form_2d(K, counts, th)
+    assert abs(r.value - v) <= 1e-13 * abs(v)
+    assert max_rel_err(r.grad, g, r.scale, floor=1e-9) <= 1e-11
+
+
+def test_binned2d_noise_free_vanishes_and_fd():
+    K = 2
+    truth = synth.c3_truth(K)
+    mean = synth.expected_counts_2d(truth, K, 40, 33)
+    r0 = oracle.binned2d(K, mean, 0.0, 1.0, 0.0, 1.0, truth)
+    th = truth * 1.02
+    r = oracle.binned2d(K, mean, 0.0, 1.0, 0.0, 1.0, th)
+    assert np.all(np.abs(r0.grad) <= 1e-12 * r.scale)
+    for k in range(th.size):
+        h = 1e-6 * max(abs(th[k]), 1e-3)
+        tp, tm = th.copy(), th.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd = (oracle.binned2d(K, mean, 0.0, 1.0, 0.0, 1.0, tp).value
+              - oracle.binned2d(K, mean, 0.0, 1.0, 0.0, 1.0, tm).value) / (2 * h)
+        assert abs(fd - r.grad[k]) <= 1e-5 * max(abs(r.grad[k]), 1e-6 * r.scale[k])
+
+
+# --------------------------------------------------------------------------
+# Listing 1
+# --------------------------------------------------------------------------
+def test_listing1_gauss():
+    for x, p, s in [(0.3, 0.1, 2.0), (-1.0, 0.5, 0.7), (4.0, 4.0, 1.3)]:
+        v, dx, dp = oracle.listing1_gauss(x, p, s)
+        ref = (2 * math.pi) ** -0.5 * s ** -0.5 * math.exp(-(x - p) ** 2 / (2 * s * s))
+        assert abs(v - ref) <= 1e-15 * ref
+        assert abs(dx - (-(x - p) / s ** 2 * ref)) <= 1e-14 * max(abs(ref), 1e-300)
+        assert abs(dp - ((x - p) / s ** 2 * ref)) <= 1e-14 * max(abs(ref), 1e-300)
+
+
+# --------------------------------------------------------------------------
+# oracle fit
+# --------------------------------------------------------------------------
+def test_oracle_fit_reaches_lstsq_consistent_minimum():
+    """The BFGS fit of one histogram ends at a point where the linear
+    parameters are the weighted least-squares solution for its (mu, s), and
+    chi2/ndf is statistically sane."""
+    n = 2000
+    h = synth.c1_histogram(n_bins=n)
+    y = h["y"]
+    fg = lambda t: (lambda r: (r.value, r.grad))(oracle.binned1d(1, 1, 0, oracle.CHI2, y, 0.0, 10.0, t))
+    gn = lambda t: oracle.binned1d_gn(1, 1, 0, oracle.CHI2, y, 0.0, 10.0, t)
+    res = bfgs_fit(fg, gn, h["truth"] * np.array([1.15, 0.97, 1.2, 0.85, 1.1]), max_iter=200, tol=1e-12)
+    assert res["status"] == CONVERGED
+    th = res["theta"]
+    x = synth.uniform_centres(n, 0.0, 10.0)
+    e = np.exp(-(x - th[1]) ** 2 / (2 * th[2] ** 2))
+    sw = np.sqrt(1 / np.maximum(y, 1))
+    coef = np.linalg.lstsq(np.stack([e, np.ones(n), x], 1) * sw[:, None], y * sw, rcond=None)[0]
+    np.testing.assert_allclose([th[0], th[3], th[4]], coef, rtol=1e-6)
+    ndf = n - 5
+    assert abs(res["F"] / ndf - 1) < 5 * math.sqrt(2 / ndf)
+    assert abs(th[1] - 5.0) < 0.01
