@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Throughput of exact fit-objective gradients on GB300.
+
+One step = one cg_batch_gradient call: the unbinned Gaussian + exponential
+mixture NLL and its exact gradient over 10^7 events at 50 parameter points
+(the fused forward + adjoint kernel and the fixed-order finalize).  The
+events (80 MB) are below L2 size, so L2 is flushed (a 256 MB write) before
+every timed step; only the step itself is inside the CUDA events.
+
+Reported: bin-grads/s (events x parameter points per second, the headline
+value), gradient evaluations/s, the end-to-end figure through the public
+API with host buffers, the roofline of the dominant kernel, and the CPU
+oracle timed on the host's cores.  `--impl reference` times the CPU oracle
+alone (the reference arm).  Under torchrun each rank evaluates its own 50
+parameter points on its own copy of the events (weak scaling; no
+collective on the data path).
+"""
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gradient evals/s and bin-grads/s (frac of roofline); time-to-fit vs plain path"
+UNIT = "bin-grads/s"
+N_EVENTS = 10 ** 7
+N_POINTS = 50
+
+
+def workload_name(n_events, n_points):
+    return ("unbinned NLL, 0.3 N(2,0.3) + 0.7 Exp(0.5) on [0,10], %g events x %d parameter points"
+            % (n_events, n_points))
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = open(os.devnull if False else "/tmp/cg_clocks_%d.csv" % os.getpid(), "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.out.close()
+        rows = [l.split(",") for l in open(self.out.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.out.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def unit_rates():
+    """FP64 FMA, exp, log, reciprocal and FP32 FMA rates measured on this GPU."""
+    import torch
+    from paper_2203_06139_gb300 import _build
+    L = ctypes.CDLL(_build.build_probe())
+    L.cgp_unit_rates.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    scratch = torch.empty(nsm * 4 * 256, dtype=torch.float64, device="cuda")
+    out = (ctypes.c_double * 6)()
+    rc = L.cgp_unit_rates(out, ctypes.c_void_p(scratch.data_ptr()))
+    torch.cuda.synchronize()
+    if rc != 0:
+        return None
+    return dict(dfma_per_s=out[0], exp_per_s=out[1], log_per_s=out[2], rcp_per_s=out[3], ffma_per_s=out[4],
+                n_sm=int(out[5]))
+
+
+# Algorithmic FP64 work of one event at one parameter point in the fused
+# unbinned kernel: basic add/mul/fma operations and library calls.
+MIX_OPS = dict(basic=17, exp=2, log=1, rcp=1)
+
+
+def fp64_roofline(dur_s, n_units, rates, sm_max_mhz):
+    """ALU roofline of the FP64 kernel: DFMA-slot-equivalent work / time vs the
+    FP64 unit rate at the maximum SM clock (152 SMs x 2 DFMA/clk x 2 flop)."""
+    nsm = rates["n_sm"] if rates else 152
+    peak_dfma = nsm * 2 * (sm_max_mhz or 2070.0) * 1e6
+    if rates:
+        c_exp = rates["dfma_per_s"] / rates["exp_per_s"]
+        c_log = rates["dfma_per_s"] / rates["log_per_s"]
+        c_rcp = rates["dfma_per_s"] / rates["rcp_per_s"]
+    else:
+        c_exp, c_log, c_rcp = 23.7, 36.6, 7.8
+    slots = MIX_OPS["basic"] + MIX_OPS["exp"] * c_exp + MIX_OPS["log"] * c_log + MIX_OPS["rcp"] * c_rcp
+    achieved = slots * n_units * 2 / dur_s / 1e12
+    peak = peak_dfma * 2 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_mix_fp64",
+            "work_per_unit": "%.1f DFMA-slot equivalents per event-point (17 add/mul/fma + 2 exp x %.1f + "
+                             "1 log x %.1f + 1 rcp x %.1f)" % (slots, c_exp, c_log, c_rcp),
+            "peak_basis": "FP64 unit: %d SMs x 2 DFMA/clk x 2 flop x %.0f MHz (unit counts and max clock)"
+                          % (nsm, sm_max_mhz or 2070.0)}
+
+
+def cpu_oracle_rate(n_events, thetas, threads=None):
+    """The CPU tape oracle over a bounded sample, parallel over parameter points."""
+    import oracle
+    from paper_2203_06139_gb300 import synth
+    oracle.build()
+    x = synth.c2_events(n_events)
+    threads = threads or os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.many(oracle.unbinned_mix, thetas, threads=threads, x=x, lo=0.0, hi=10.0)
+    dt = time.perf_counter() - t0
+    return n_events * len(thetas) / dt, threads, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2203_06139_gb300 import synth
+    thetas = synth.c2_theta_points(args.points)
+    n_sample = 400000
+    cores = os.cpu_count() or 1
+    times = []
+    for _ in range(args.warmup):
+        cpu_oracle_rate(n_sample, thetas, cores)
+    for _ in range(args.steps):
+        r, cores, dt = cpu_oracle_rate(n_sample, thetas, cores)
+        times.append(dt)
+    dt = sum(times) / len(times)
+    value = n_sample * args.points / dt
+    sample = "first %d of the %g events x all %d parameter points per step" % (n_sample, args.events, args.points)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.events, args.points), "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2203_06139_gb300 import cg, synth
+
+    N_EV, N_PT = args.events, args.points
+    x_host = synth.c2_events(N_EV)
+    th_host = synth.c2_theta_points(N_PT * world)[rank * N_PT:(rank + 1) * N_PT].copy()
+    x = torch.tensor(x_host, device=dev)
+    th = torch.tensor(th_host, device=dev)
+    prec = cg.PREC_DF64 if args.prec == "df64" else cg.PREC_FP64
+    pb = cg.Problem.mixture(x, 0.0, 10.0, precision=prec)
+    values = torch.empty(N_PT, dtype=torch.float64, device=dev)
+    grads = torch.empty((N_PT, 4), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        cg.batch_gradient(pb, th, values, grads)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if pb.status(N_PT) != cg.OK:
+        raise SystemExit("device status not OK after warm-up")
+
+    rates = unit_rates() if rank == 0 else None
+
+    # ---- timed region: K steps, L2 flushed before each, CUDA events per step ----
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    k0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    k1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for e in k0 + k1:
+        e.record(stream)  # torch creates the CUDA event lazily, on first record
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        cg.set_profile_events(k0[i], k1[i])
+        step()
+        cg.set_profile_events(None, None)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    kern_ms = [s.elapsed_time(e) for s, e in zip(k0, k1)]
+    total_s = sum(step_ms) / 1e3
+    kern_s = sum(kern_ms) / 1e3 / args.steps
+    if world > 1:
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    units = N_EV * N_PT * args.steps * world
+    value = units / total_s
+
+    # ---- end to end through the public API from pinned host memory ----
+    x_pin = torch.tensor(x_host).pin_memory()
+    th_pin = torch.tensor(th_host).pin_memory()
+    v_pin = torch.empty(N_PT, dtype=torch.float64).pin_memory()
+    g_pin = torch.empty((N_PT, 4), dtype=torch.float64).pin_memory()
+    x_dev = torch.empty_like(x)
+    th_dev = torch.empty_like(th)
+    pe = cg.Problem.mixture(x_dev, 0.0, 10.0, precision=prec)
+    for _ in range(2):
+        x_dev.copy_(x_pin, non_blocking=True)
+        th_dev.copy_(th_pin, non_blocking=True)
+        cg.batch_gradient(pe, th_dev, values, grads)
+        v_pin.copy_(values, non_blocking=True)
+        g_pin.copy_(grads, non_blocking=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        x_dev.copy_(x_pin, non_blocking=True)
+        th_dev.copy_(th_pin, non_blocking=True)
+        cg.batch_gradient(pe, th_dev, values, grads)
+        v_pin.copy_(values, non_blocking=True)
+        g_pin.copy_(grads, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    assert np.allclose(v_pin.numpy(), values.cpu().numpy())
+
+    if rank == 0:
+        roof = fp64_roofline(kern_s, N_EV * N_PT, rates, clk.get("sm_max_mhz")) if prec == cg.PREC_FP64 \
+            else df64_roofline(kern_s, N_EV * N_PT, rates, clk.get("sm_max_mhz"))
+        cpu_v, cores, cpu_dt = cpu_oracle_rate(1000000, synth.c2_theta_points(N_PT))
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == cg.PREC_FP64 else "df64 (f32 pairs) with f64 accumulation",
+            "data": "synthetic (seeded numpy PCG64; see synth.py)",
+            "config": {"workload": workload_name(N_EV, N_PT), "events": N_EV, "points_per_gpu": N_PT,
+                       "l2": "flushed before every timed step (256 MB write)", "parallelism":
+                       "replicas over %d GPU(s), independent parameter points" % world},
+            "grad_evals_per_s": N_PT * args.steps * world / total_s,
+            "e2e": {"value": units / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": x_pin.numel() * 8 + th_pin.numel() * 8,
+                    "d2h_bytes_per_step": v_pin.numel() * 8 + g_pin.numel() * 8},
+            "gpu_launches": 2 * args.steps,
+            "kernel_ms": kern_s * 1e3,
+            "roofline": roof,
+            "clocks": clk,
+            "unit_rates": rates,
+            "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "first 1e6 events x %d parameter points (%.1f s wall)" % (N_PT, cpu_dt)},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def df64_roofline(dur_s, n_units, rates, sm_max_mhz):
+    return {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cg", choices=["cg", "reference"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "df64"])
+    ap.add_argument("--events", type=int, default=N_EVENTS)
+    ap.add_argument("--points", type=int, default=N_POINTS)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,262 @@
+/*
+ * cg.h -- C ABI of libcg: objective values and exact reverse-mode gradients
+ * of histogram and event fit objectives, computed by hand-written sm_103a
+ * CUDA kernels.
+ *
+ * The problem is the one of the paper's histogram-fitting use of AD
+ * (Sec. 4, Fig. 3): a parameter vector and data go in, the objective value
+ * and its exact gradient with respect to the parameters come out.  The
+ * gradient is the reverse-mode (adjoint) derivative of Sec. 1-2: one fused
+ * pass evaluates each bin's or event's term and sweeps its adjoint back to
+ * the parameters, and the per-element parameter adjoints are summed -- the
+ * "parallel reads become parallel writes" situation of Sec. 3, handled here
+ * by a deterministic reduction (warp shuffle, then block, then a fixed-order
+ * sum over blocks) with no floating-point atomics.
+ *
+ * Conventions for every call:
+ *  - Pointers documented "device" are caller-owned device memory; the
+ *    library never allocates or frees device memory.  Scratch comes from a
+ *    caller-provided workspace `ws` of at least the size the matching
+ *    *_workspace_size() call returns (256-byte aligned).
+ *  - Structs (cg_problem, cg_batch, cg_tile_map) are host memory read during
+ *    the call only.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on it and may be captured in a CUDA
+ *    graph; argument errors are returned synchronously before any launch.
+ *  - Device-detected problems (log of a non-positive model value, a
+ *    non-finite parameter, a wait that ran out) do not stop the kernels;
+ *    they are recorded in a status word inside `ws`, read by cg_get_status().
+ *  - All results are deterministic for a given launch configuration: the
+ *    summation tree depends on the problem size and the tile mapping only.
+ *  - No call throws, traps or asserts on the device.
+ */
+#ifndef CG_H
+#define CG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CG_OK = 0,
+    CG_ERR_INVALID_ARG = 1,  /* bad sizes, null pointers, unknown enums */
+    CG_ERR_DOMAIN = 2,       /* device: log of a non-positive model value or non-finite term */
+    CG_ERR_CUDA = 3,         /* a CUDA runtime call or launch failed */
+    CG_ERR_TIMEOUT = 4,      /* device: a bounded wait gave up */
+    CG_ERR_NOT_CONVERGED = 5,
+    CG_ERR_UNSUPPORTED = 6,  /* combination not implemented */
+    CG_ERR_WORKSPACE = 7     /* workspace missing, misaligned or too small */
+} cg_status;
+
+/* Model families (parameter order is fixed and part of the ABI):
+ *  CG_MODEL_GAUSS_POLY   1-D binned: K Gaussian peaks (amplitude = peak
+ *                        height, the "gaus" of Fig. 3a) plus a polynomial of
+ *                        degree D: theta = (A_1, mu_1, s_1, ..., A_K, mu_K,
+ *                        s_K, c_0, ..., c_D), P = 3K + D + 1.
+ *                        f(x) = sum_k A_k exp(-(x-mu_k)^2/(2 s_k^2)) + sum_j c_j u^j
+ *                        with u = x (poly_mode 0) or u = (2x-lo-hi)/(hi-lo) (1).
+ *  CG_MODEL_MIX_GAUSS_EXP unbinned on [lo, hi]: theta = (frac, mu, s, lambda),
+ *                        p(x) = frac N(x;mu,s)/Z_G + (1-frac) lambda e^{-lambda x}/Z_E,
+ *                        each component normalised over [lo, hi].
+ *  CG_MODEL_ROTGAUSS2D   2-D binned: K rotated Gaussians + constant:
+ *                        theta = (A, mu_x, mu_y, s_x, s_y, phi) x K, then C.
+ */
+typedef enum {
+    CG_MODEL_GAUSS_POLY = 0,
+    CG_MODEL_MIX_GAUSS_EXP = 1,
+    CG_MODEL_ROTGAUSS2D = 2
+} cg_model;
+
+/* Objectives (the per-element term T_i; the objective is sum_i T_i):
+ *  CG_OBJ_CHI2        w_i (y_i - f_i)^2, w_i = 1/max(y_i, 1)
+ *  CG_OBJ_POISSON     f_i - y_i log f_i              (log y_i! dropped)
+ *  CG_OBJ_POISSON_BC  2 (f_i - y_i + y_i log(y_i/f_i)), 2 f_i when y_i = 0
+ *  CG_OBJ_UNBINNED_NLL -w_i log p(x_i)               (w_i = 1 without weights)
+ */
+typedef enum {
+    CG_OBJ_CHI2 = 0,
+    CG_OBJ_POISSON = 1,
+    CG_OBJ_POISSON_BC = 2,
+    CG_OBJ_UNBINNED_NLL = 3
+} cg_objective_kind;
+
+/* Arithmetic of the per-element work.  Accumulation is FP64 in every mode.
+ *  CG_PREC_FP64  FP64 throughout (the FP64 pipe).
+ *  CG_PREC_DF64  per-element arithmetic in double-float (pairs of FP32
+ *                values with error-free transformations) on the FP32 pipe;
+ *                per-term relative error about 1e-14, stated per workload
+ *                by the test suite against FP64. */
+typedef enum {
+    CG_PREC_FP64 = 0,
+    CG_PREC_DF64 = 1
+} cg_precision;
+
+#define CG_MAX_PEAKS_1D 4
+#define CG_MAX_POLY_DEGREE 3
+#define CG_MAX_PEAKS_2D 8
+#define CG_MAX_PARAMS 49
+
+/* One fit problem: model, objective and data (host struct). */
+typedef struct {
+    int32_t model;          /* cg_model */
+    int32_t objective;      /* cg_objective_kind */
+    int32_t precision;      /* cg_precision */
+    int32_t n_peaks;        /* K: 0..CG_MAX_PEAKS_1D (1-D), 1..CG_MAX_PEAKS_2D (2-D) */
+    int32_t poly_degree;    /* D: -1..CG_MAX_POLY_DEGREE (1-D only) */
+    int32_t poly_mode;      /* 0: powers of x, 1: powers of t = (2x-lo-hi)/(hi-lo) */
+    int64_t n_bins[2];      /* binned: bins along x and y (1-D uses n_bins[0]) */
+    double lo[2], hi[2];    /* range along x and y; bin centres are lo+(i+0.5)(hi-lo)/n */
+    const double *centres;  /* device, optional explicit 1-D bin centres [n_bins[0]] (NULL: uniform) */
+    const double *data;     /* device: counts, 1-D [n_bins[0]] or 2-D [n_bins[1]][n_bins[0]]
+                               (x index fastest); unbinned: events [n_events] */
+    const double *weights;  /* device, optional per-event weights [n_events] (unbinned only) */
+    int64_t n_events;       /* unbinned: number of events */
+} cg_problem;
+
+/* Many histograms of one model/objective, concatenated (host struct).
+ * Histogram h owns bins offsets[h] .. offsets[h+1]-1 of tmpl.data and has
+ * range [lo[h], hi[h]] with uniform bins.  When offsets == NULL the batch is
+ * n_hist parameter points on the single problem `tmpl`. */
+typedef struct {
+    cg_problem tmpl;
+    int64_t n_hist;
+    const int64_t *offsets; /* device [n_hist + 1], or NULL */
+    const double *lo;       /* device [n_hist], used when offsets != NULL */
+    const double *hi;       /* device [n_hist], used when offsets != NULL */
+} cg_batch;
+
+/* Number of parameters P of the problem's model, or -1 if it is invalid. */
+int cg_num_params(const cg_problem *pb);
+
+/* Workspace bytes for cg_objective / cg_gradient (n_theta = 1) and
+ * cg_batch_gradient with offsets == NULL (n_theta = n_hist).  0 when the
+ * problem is invalid. */
+size_t cg_workspace_size(const cg_problem *pb, int64_t n_theta);
+
+/* Objective value at one parameter point (Sec. 4: the fit objective).
+ * theta: device [P]; value: device [1].  Runs the same fused kernel as
+ * cg_gradient and discards the gradient. */
+cg_status cg_objective(const cg_problem *pb, const double *theta, double *value,
+                       void *ws, size_t ws_bytes, void *stream);
+
+/* Objective value and its exact gradient at one parameter point: the fused
+ * per-element forward evaluation + adjoint sweep (reverse mode, Sec. 1-2;
+ * the generated-gradient-in-a-kernel pattern of Listing 1, here with the
+ * per-parameter adjoints reduced over all elements as Sec. 3 requires).
+ * theta: device [P]; value: device [1]; grad: device [P]. */
+cg_status cg_gradient(const cg_problem *pb, const double *theta, double *value, double *grad,
+                      void *ws, size_t ws_bytes, void *stream);
+
+/* Values and gradients for many parameter points or many histograms in one
+ * launch sequence.  theta: device [n_hist][P] (row-major); value: device
+ * [n_hist]; grad: device [n_hist][P].
+ *  - offsets == NULL: n_hist parameter points on the single problem tmpl
+ *    (one thread per evaluation in Listing 1; here each point's gradient is
+ *    itself a reduction over all bins or events).
+ *  - offsets != NULL: histogram h is evaluated at theta[h]; binned 1-D
+ *    models only.  Workspace: cg_batch_workspace_size(). */
+size_t cg_batch_workspace_size(const cg_batch *b);
+cg_status cg_batch_gradient(const cg_batch *b, const double *theta, double *value, double *grad,
+                            void *ws, size_t ws_bytes, void *stream);
+
+/* Device status recorded by the last call that used `ws`: synchronises
+ * `stream`, returns CG_OK, CG_ERR_DOMAIN or CG_ERR_TIMEOUT (or CG_ERR_CUDA
+ * if the copy fails). */
+cg_status cg_get_status(const void *ws, void *stream);
+
+/* Profiling hook: when start/stop are non-NULL cudaEvent_t handles (passed as
+ * void*), every later launch of a fused accumulation kernel (the dominant
+ * kernel of cg_objective / cg_gradient / cg_batch_gradient / cg_fit_*)
+ * records `start` immediately before and `stop` immediately after it, on the
+ * call's stream.  NULL, NULL switches it off.  Process-wide; not meant to be
+ * changed while other threads are calling the library. */
+void cg_set_profile_events(void *start, void *stop);
+
+/* Static description of a status code. */
+const char *cg_status_string(cg_status s);
+
+/* ------------------------------------------------------------------------
+ * Fitting (Sec. 4: AD gradients replacing numerical ones inside the
+ * histogram fitter; the minimiser is gradient-only since second
+ * derivatives are not taken from AD).  The minimiser is BFGS with a
+ * backtracking Armijo line search; see cg_fit_step.
+ * ------------------------------------------------------------------------ */
+
+#define CG_FIT_MAX_PARAMS 12
+
+enum {
+    CG_FIT_RUNNING = 0,
+    CG_FIT_CONVERGED = 1,
+    CG_FIT_MAX_ITER = 2,
+    CG_FIT_LINESEARCH_FAILED = 3,
+    CG_FIT_DOMAIN = 4
+};
+
+/* Per-histogram fit state (device memory, one per histogram). */
+typedef struct {
+    double theta[CG_FIT_MAX_PARAMS];
+    double grad[CG_FIT_MAX_PARAMS];
+    double hinv[CG_FIT_MAX_PARAMS * CG_FIT_MAX_PARAMS]; /* inverse-Hessian approximation, row-major P x P */
+    double h0[CG_FIT_MAX_PARAMS];   /* initial diagonal: 1 / Gauss-Newton diagonal */
+    double f;                       /* objective at theta */
+    double edm;                     /* g^T H g / 2 */
+    int32_t iter;                   /* accepted iterations */
+    int32_t n_eval;                 /* objective+gradient evaluations */
+    int32_t status;                 /* CG_FIT_* */
+    int32_t n_params;
+} cg_fit_state;
+
+/* How histograms are mapped onto the GPU by the batched fitter.  Histograms
+ * with n <= warp_max_bins are fitted by one warp each, those with
+ * n <= cta_max_bins by one CTA each, larger ones by a cluster of
+ * cluster_size CTAs.  Chosen by the autotuner in the Python layer. */
+typedef struct {
+    int32_t warp_max_bins;
+    int32_t cta_max_bins;
+    int32_t cta_threads;     /* 64..512, multiple of 32 */
+    int32_t cluster_size;    /* 1, 2, 4 or 8 */
+} cg_tile_map;
+
+/* Workspace for the fit calls on batch b (offsets != NULL). */
+size_t cg_fit_workspace_size(const cg_batch *b);
+
+/* Work queues of the batched fitter, built on the host from the host copy of
+ * the bin offsets (host_offsets[n_hist + 1]) and uploaded into ws.  Must be
+ * called once before cg_fit_init/cg_fit_step with the same ws and map. */
+cg_status cg_fit_plan(const cg_batch *b, const int64_t *host_offsets, const cg_tile_map *map,
+                      void *ws, size_t ws_bytes, void *stream);
+
+/* Initialise fit states at theta0 (device [n_hist][P]): evaluates F, g and
+ * the Gauss-Newton diagonal, sets H = diag(1/GN). */
+cg_status cg_fit_init(const cg_batch *b, const double *theta0, cg_fit_state *state,
+                      void *ws, size_t ws_bytes, void *stream);
+
+/* Run up to n_steps BFGS iterations on every histogram whose status is
+ * CG_FIT_RUNNING, in ONE persistent launch (histograms of different sizes
+ * handled by warps, CTAs or CTA clusters as the plan says).  One iteration:
+ * d = -H g (reset to the initial diagonal when g.d >= 0); trial points
+ * theta + alpha d from alpha = 1, accepted when F(trial) <= F + 1e-4 alpha
+ * g.d, otherwise alpha shrinks to the clamped quadratic-interpolation
+ * minimiser in [0.1, 0.5] alpha (0.1 alpha for a non-finite F), at most 20
+ * trials; BFGS update when s.y > 1e-12 |s||y|; converged when
+ * EDM = g.H.g/2 < tol * max(1, |F|). */
+cg_status cg_fit_step(const cg_batch *b, cg_fit_state *state, int n_steps, double tol,
+                      void *ws, size_t ws_bytes, void *stream);
+
+/* The same iteration for ONE histogram (the plain per-histogram path): each
+ * trial point is one fused gradient launch on the full GPU followed by a
+ * one-thread update kernel; no host synchronisation. state: device [1]. */
+size_t cg_fit_single_workspace_size(const cg_problem *pb);
+cg_status cg_fit_single_init(const cg_problem *pb, const double *theta0, cg_fit_state *state,
+                             void *ws, size_t ws_bytes, void *stream);
+cg_status cg_fit_single_step(const cg_problem *pb, cg_fit_state *state, int n_evals, double tol,
+                             void *ws, size_t ws_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CG_H */

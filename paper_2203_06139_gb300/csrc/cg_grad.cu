@@ -1,0 +1,514 @@
+// cg_grad.cu -- fused forward + adjoint kernels (FP64) and the C-ABI entry
+// points cg_objective / cg_gradient / cg_batch_gradient (parameter-point
+// batches) of libcg.
+//
+// The method (Sec. 1-2 of the paper): reverse-mode AD of F(theta) =
+// sum_i T_i(theta).  Per element i one thread evaluates the model and the
+// term T_i (forward), seeds the term's adjoint dT_i/df_i and propagates it to
+// per-thread FP64 adjoint accumulators (reverse); no tape is kept, every
+// intermediate lives in registers.  Quantities that depend on theta alone
+// (1/(2 s^2), normalisation integrals, cos/sin of angles) are computed once
+// per tile in a prologue, and their adjoints are chained back to theta once
+// per parameter point in the epilogue, so the per-element adjoint is a small
+// set of sums (the model's "accumulators").  Summing the per-element
+// adjoints is the "parallel reads become parallel writes" step of Sec. 3:
+// here a deterministic warp-butterfly -> block -> fixed-order tile sum, with
+// no floating-point atomics.
+//
+// Work decomposition: a tile is (parameter point, contiguous chunk of
+// elements).  A persistent grid of (#SMs x resident CTAs) blocks walks the
+// tiles round-robin; each tile writes one partial vector; a finalize kernel
+// (one block per parameter point) sums the partials of a point in chunk
+// order and applies the epilogue.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+#include <unordered_map>
+
+#include "cg_internal.cuh"
+#include "cg_models.cuh"
+
+namespace cg {
+
+cudaEvent_t g_prof_start = nullptr, g_prof_stop = nullptr;
+
+int device_sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return kNumSMsFallback;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+        return kNumSMsFallback;
+    return n;
+}
+
+// Resident blocks per SM of a kernel, cached per (kernel, threads).
+static int resident_blocks(const void* fn, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(fn);
+    if (it != cache.end()) return it->second;
+    int r = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, fn, threads, smem) != cudaSuccess || r < 1) r = 1;
+    cache[fn] = r;
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Tile accumulation kernels
+// ---------------------------------------------------------------------------
+
+// Write one tile's partial sums: part[(th * (NACC + 1) + a) * nbx + c].
+template <int NACC>
+__device__ __forceinline__ void write_partial(double* __restrict__ part, const TileGrid& tg, int th,
+                                              int c, const double* tot, int bad) {
+    if (threadIdx.x == 0) {
+        double* p = part + (size_t)th * (NACC + 1) * tg.nbx + c;
+        for (int a = 0; a < NACC; ++a) p[(size_t)a * tg.nbx] = tot[a];
+        p[(size_t)NACC * tg.nbx] = bad ? 1.0 : 0.0;
+    }
+}
+
+template <int K, int OBJ, int NT>
+__global__ void __launch_bounds__(NT) k_gp1_fp64(GP1Data d, const double* __restrict__ theta,
+                                                 TileGrid tg, double* __restrict__ part,
+                                                 WsHeader* __restrict__ hdr) {
+    constexpr int NACC = GP1Acc<K>::N;
+    __shared__ GP1Consts cs;
+    __shared__ int cs_bad;
+    __shared__ double red[NACC * (NT / 32)];
+    __shared__ double tot[NACC];
+    if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
+    const int P = 3 * K + d.D + 1;
+    for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
+        const int th = t / tg.nbx, c = t - th * tg.nbx;
+        if (threadIdx.x == 0) cs_bad = gp1_prologue<K>(theta + (size_t)th * P, d.D, cs) ? 0 : 1;
+        __syncthreads();
+        double acc[NACC];
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) acc[a] = 0.0;
+        bool bad = false;
+        const int64_t e0 = (int64_t)c * tg.chunk;
+        const int64_t e1 = min(tg.n_elem, e0 + tg.chunk);
+        if (d.vec_ok) {
+            // two consecutive bins per thread with one 16-byte load of the counts
+            for (int64_t i = e0 + 2 * threadIdx.x; i < e1; i += 2 * NT) {
+                if (i + 1 < e1) {
+                    const double2 y2 = __ldg(reinterpret_cast<const double2*>(d.y + i));
+                    double2 x2;
+                    if (d.centres) x2 = __ldg(reinterpret_cast<const double2*>(d.centres + i));
+                    else { x2.x = fma((double)i + 0.5, d.h, d.lo); x2.y = fma((double)i + 1.5, d.h, d.lo); }
+                    gp1_elem_fp64<K, OBJ>(x2.x, y2.x, cs, d, acc, bad);
+                    gp1_elem_fp64<K, OBJ>(x2.y, y2.y, cs, d, acc, bad);
+                } else {
+                    const double x = d.centres ? d.centres[i] : fma((double)i + 0.5, d.h, d.lo);
+                    gp1_elem_fp64<K, OBJ>(x, d.y[i], cs, d, acc, bad);
+                }
+            }
+        } else {
+            for (int64_t i = e0 + threadIdx.x; i < e1; i += NT) {
+                const double x = d.centres ? d.centres[i] : fma((double)i + 0.5, d.h, d.lo);
+                gp1_elem_fp64<K, OBJ>(x, d.y[i], cs, d, acc, bad);
+            }
+        }
+        const int any_bad = __syncthreads_or(bad ? 1 : 0) | cs_bad;
+        block_sum<NACC, NT>(acc, red, tot);
+        write_partial<NACC>(part, tg, th, c, tot, any_bad);
+    }
+}
+
+template <bool W, int NT>
+__global__ void __launch_bounds__(NT) k_mix_fp64(MixData d, const double* __restrict__ theta,
+                                                 TileGrid tg, double* __restrict__ part,
+                                                 WsHeader* __restrict__ hdr) {
+    constexpr int NACC = MixAcc::N;
+    __shared__ MixConsts cs;
+    __shared__ int cs_bad;
+    __shared__ double red[NACC * (NT / 32)];
+    __shared__ double tot[NACC];
+    if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
+    for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
+        const int th = t / tg.nbx, c = t - th * tg.nbx;
+        if (threadIdx.x == 0) cs_bad = mix_prologue(theta + (size_t)th * 4, d.lo, d.hi, cs) ? 0 : 1;
+        __syncthreads();
+        double acc[NACC];
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) acc[a] = 0.0;
+        bool bad = false;
+        const int64_t e0 = (int64_t)c * tg.chunk;
+        const int64_t e1 = min(tg.n_elem, e0 + tg.chunk);
+        if (d.vec_ok) {
+            for (int64_t i = e0 + 2 * threadIdx.x; i < e1; i += 2 * NT) {
+                if (i + 1 < e1) {
+                    const double2 x2 = __ldg(reinterpret_cast<const double2*>(d.x + i));
+                    double2 w2 = make_double2(1.0, 1.0);
+                    if (W) w2 = __ldg(reinterpret_cast<const double2*>(d.w + i));
+                    mix_elem_fp64<W>(x2.x, w2.x, cs, acc, bad);
+                    mix_elem_fp64<W>(x2.y, w2.y, cs, acc, bad);
+                } else {
+                    mix_elem_fp64<W>(d.x[i], W ? d.w[i] : 1.0, cs, acc, bad);
+                }
+            }
+        } else {
+            for (int64_t i = e0 + threadIdx.x; i < e1; i += NT)
+                mix_elem_fp64<W>(d.x[i], W ? d.w[i] : 1.0, cs, acc, bad);
+        }
+        const int any_bad = __syncthreads_or(bad ? 1 : 0) | cs_bad;
+        block_sum<NACC, NT>(acc, red, tot);
+        write_partial<NACC>(part, tg, th, c, tot, any_bad);
+    }
+}
+
+template <int K, int NT>
+__global__ void __launch_bounds__(NT) k_rg2_fp64(RG2Data d, const double* __restrict__ theta,
+                                                 TileGrid tg, double* __restrict__ part,
+                                                 WsHeader* __restrict__ hdr) {
+    constexpr int NACC = RG2Acc<K>::N;
+    __shared__ RG2Consts cs;
+    __shared__ int cs_bad;
+    __shared__ double red[NACC * (NT / 32)];
+    __shared__ double tot[NACC];
+    if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
+    const int P = 6 * K + 1;
+    for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
+        const int th = t / tg.nbx, c = t - th * tg.nbx;
+        if (threadIdx.x == 0) cs_bad = rg2_prologue<K>(theta + (size_t)th * P, cs) ? 0 : 1;
+        __syncthreads();
+        double acc[NACC];
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) acc[a] = 0.0;
+        bool bad = false;
+        const int64_t e0 = (int64_t)c * tg.chunk;
+        const int64_t e1 = min(tg.n_elem, e0 + tg.chunk);
+        int64_t i = e0 + threadIdx.x;
+        int64_t iy = i / d.nx, ix = i - iy * d.nx;
+        double yc = fma((double)iy + 0.5, d.hy, d.ly);
+        for (; i < e1; i += NT) {
+            const double xc = fma((double)ix + 0.5, d.hx, d.lx);
+            rg2_elem_fp64<K>(xc, yc, __ldg(d.n + i), cs, acc, bad);
+            ix += NT;
+            if (ix >= d.nx) {
+                while (ix >= d.nx) { ix -= d.nx; ++iy; }
+                yc = fma((double)iy + 0.5, d.hy, d.ly);
+            }
+        }
+        const int any_bad = __syncthreads_or(bad ? 1 : 0) | cs_bad;
+        block_sum<NACC, NT>(acc, red, tot);
+        write_partial<NACC>(part, tg, th, c, tot, any_bad);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Finalize: fixed-order sum of the tile partials of one parameter point and
+// the epilogue (adjoints of the prologue constants chained back to theta).
+// ---------------------------------------------------------------------------
+template <int NT>
+__global__ void __launch_bounds__(NT) k_finalize(const double* __restrict__ part, int nacc, TileGrid tg,
+                                                 EpiParams ep, const double* __restrict__ theta,
+                                                 double* __restrict__ value, double* __restrict__ grad,
+                                                 WsHeader* __restrict__ hdr) {
+    __shared__ double tot[kMaxAcc + 1];
+    __shared__ double red[NT / 32];
+    const int th = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int a = 0; a <= nacc; ++a) {
+        const double* p = part + ((size_t)th * (nacc + 1) + a) * tg.nbx;
+        double s = 0.0;
+        for (int c = threadIdx.x; c < tg.nbx; c += NT) s += p[c];
+        s = warp_sum(s);
+        if (lane == 0) red[wid] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < NT / 32; ++w) t += red[w];
+            tot[a] = t;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double* tht = theta + (size_t)th * ep.P;
+        double g[kMaxParams];
+        double v = epilogue(ep, tht, tot, g);
+        if (value) value[th] = v;
+        if (grad)
+            for (int k = 0; k < ep.P; ++k) grad[(size_t)th * ep.P + k] = g[k];
+        if (tot[nacc] != 0.0) atomicOr(&hdr->status, (int)DEV_DOMAIN);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static constexpr int kMaxTiles = 16384;
+
+static int acc_count(const cg_problem* pb) {
+    switch (pb->model) {
+        case CG_MODEL_GAUSS_POLY: return 1 + 3 * pb->n_peaks + 4;
+        case CG_MODEL_MIX_GAUSS_EXP: return MixAcc::N;
+        case CG_MODEL_ROTGAUSS2D: return 2 + 6 * pb->n_peaks;
+        default: return -1;
+    }
+}
+
+static int64_t n_elements(const cg_problem* pb) {
+    switch (pb->model) {
+        case CG_MODEL_GAUSS_POLY: return pb->n_bins[0];
+        case CG_MODEL_MIX_GAUSS_EXP: return pb->n_events;
+        case CG_MODEL_ROTGAUSS2D: return pb->n_bins[0] * pb->n_bins[1];
+        default: return -1;
+    }
+}
+
+static cg_status validate(const cg_problem* pb) {
+    if (!pb) return CG_ERR_INVALID_ARG;
+    if (pb->precision != CG_PREC_FP64 && pb->precision != CG_PREC_DF64) return CG_ERR_INVALID_ARG;
+    switch (pb->model) {
+        case CG_MODEL_GAUSS_POLY:
+            if (pb->n_peaks < 0 || pb->n_peaks > CG_MAX_PEAKS_1D) return CG_ERR_INVALID_ARG;
+            if (pb->poly_degree < -1 || pb->poly_degree > CG_MAX_POLY_DEGREE) return CG_ERR_INVALID_ARG;
+            if (pb->n_peaks == 0 && pb->poly_degree < 0) return CG_ERR_INVALID_ARG;
+            if (pb->poly_mode != 0 && pb->poly_mode != 1) return CG_ERR_INVALID_ARG;
+            if (pb->objective != CG_OBJ_CHI2 && pb->objective != CG_OBJ_POISSON &&
+                pb->objective != CG_OBJ_POISSON_BC)
+                return CG_ERR_INVALID_ARG;
+            if (pb->n_bins[0] < 0) return CG_ERR_INVALID_ARG;
+            if (pb->n_bins[0] > 0 && !pb->data) return CG_ERR_INVALID_ARG;
+            if (!pb->centres && !(pb->hi[0] > pb->lo[0])) return CG_ERR_INVALID_ARG;
+            return CG_OK;
+        case CG_MODEL_MIX_GAUSS_EXP:
+            if (pb->objective != CG_OBJ_UNBINNED_NLL) return CG_ERR_INVALID_ARG;
+            if (pb->n_events < 0 || (pb->n_events > 0 && !pb->data)) return CG_ERR_INVALID_ARG;
+            if (!(pb->hi[0] > pb->lo[0])) return CG_ERR_INVALID_ARG;
+            return CG_OK;
+        case CG_MODEL_ROTGAUSS2D:
+            if (pb->n_peaks < 1 || pb->n_peaks > CG_MAX_PEAKS_2D) return CG_ERR_INVALID_ARG;
+            if (pb->objective != CG_OBJ_POISSON) return CG_ERR_INVALID_ARG;
+            if (pb->n_bins[0] < 0 || pb->n_bins[1] < 0) return CG_ERR_INVALID_ARG;
+            if (pb->n_bins[0] * pb->n_bins[1] > 0 && !pb->data) return CG_ERR_INVALID_ARG;
+            if (!(pb->hi[0] > pb->lo[0]) || !(pb->hi[1] > pb->lo[1])) return CG_ERR_INVALID_ARG;
+            return CG_OK;
+        default:
+            return CG_ERR_INVALID_ARG;
+    }
+}
+
+static int num_params(const cg_problem* pb) {
+    switch (pb->model) {
+        case CG_MODEL_GAUSS_POLY: return 3 * pb->n_peaks + pb->poly_degree + 1;
+        case CG_MODEL_MIX_GAUSS_EXP: return 4;
+        case CG_MODEL_ROTGAUSS2D: return 6 * pb->n_peaks + 1;
+        default: return -1;
+    }
+}
+
+static int max_nbx(int64_t n_theta) {
+    int64_t m = (kMaxTiles + n_theta - 1) / n_theta;
+    return (int)(m < 1 ? 1 : m);
+}
+
+size_t grad_workspace_bytes(const cg_problem* pb, int64_t n_theta) {
+    if (validate(pb) != CG_OK || n_theta < 1) return 0;
+    const int nacc = acc_count(pb);
+    return sizeof(WsHeader) + align_up((size_t)n_theta * (nacc + 1) * max_nbx(n_theta) * sizeof(double), 256);
+}
+
+// Choose the tile grid: ~4 tiles per resident block, at least 8 elements per
+// thread per tile, chunk a multiple of 2*NT (keeps 16-byte alignment).
+static TileGrid make_tiles(int64_t n_elem, int64_t n_theta, int NT, int grid_blocks) {
+    TileGrid tg;
+    tg.n_elem = n_elem;
+    int64_t want = ((int64_t)grid_blocks * 4 + n_theta - 1) / n_theta;
+    int64_t per_tile_min = (int64_t)NT * 8;
+    int64_t most = (n_elem + per_tile_min - 1) / per_tile_min;
+    int64_t nbx = want < most ? want : most;
+    if (nbx < 1) nbx = 1;
+    if (nbx > max_nbx(n_theta)) nbx = max_nbx(n_theta);
+    int64_t chunk = (n_elem + nbx - 1) / nbx;
+    chunk = (chunk + 2 * NT - 1) / (2 * NT) * (2 * NT);
+    if (chunk < 2 * NT) chunk = 2 * NT;
+    nbx = (n_elem + chunk - 1) / chunk;
+    if (nbx < 1) nbx = 1;
+    tg.chunk = chunk;
+    tg.nbx = (int)nbx;
+    tg.n_theta = (int)n_theta;
+    tg.n_tiles = (int)(n_theta * nbx);
+    return tg;
+}
+
+template <typename KernelT, typename DataT>
+static cg_status launch_tiles(KernelT kern, int NT, const DataT& d, const double* theta, int64_t n_elem,
+                              int64_t n_theta, double* part, WsHeader* hdr, TileGrid* tg_out,
+                              cudaStream_t st) {
+    const int R = resident_blocks((const void*)kern, NT, 0);
+    const int G = device_sm_count() * R;
+    TileGrid tg = make_tiles(n_elem, n_theta, NT, G);
+    int grid = tg.n_tiles < G ? tg.n_tiles : G;
+    prof_begin(st);
+    kern<<<grid, NT, 0, st>>>(d, theta, tg, part, hdr);
+    prof_end(st);
+    *tg_out = tg;
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
+
+template <int K>
+static cg_status launch_gp1_k(const cg_problem* pb, const GP1Data& d, const double* theta, int64_t n_theta,
+                              double* part, WsHeader* hdr, TileGrid* tg, cudaStream_t st) {
+    constexpr int NT = 256;
+    const int64_t n = pb->n_bins[0];
+    switch (pb->objective) {
+        case CG_OBJ_CHI2: return launch_tiles(k_gp1_fp64<K, CG_OBJ_CHI2, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st);
+        case CG_OBJ_POISSON: return launch_tiles(k_gp1_fp64<K, CG_OBJ_POISSON, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st);
+        case CG_OBJ_POISSON_BC: return launch_tiles(k_gp1_fp64<K, CG_OBJ_POISSON_BC, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st);
+        default: return CG_ERR_UNSUPPORTED;
+    }
+}
+
+template <int K>
+static cg_status launch_rg2_k(const RG2Data& d, const double* theta, int64_t n, int64_t n_theta, double* part,
+                              WsHeader* hdr, TileGrid* tg, cudaStream_t st) {
+    constexpr int NT = 128;
+    return launch_tiles(k_rg2_fp64<K, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st);
+}
+
+cg_status grad_points(const cg_problem* pb, const double* theta, int64_t n_theta, double* value, double* grad,
+                      void* ws, size_t ws_bytes, cudaStream_t st) {
+    cg_status s = validate(pb);
+    if (s != CG_OK) return s;
+    if (n_theta < 1 || !theta || (!value && !grad)) return CG_ERR_INVALID_ARG;
+    if (n_theta > (int64_t)kMaxTiles * 64) return CG_ERR_INVALID_ARG;
+    const size_t need = grad_workspace_bytes(pb, n_theta);
+    if (!ws || ((uintptr_t)ws & 255) || ws_bytes < need) return CG_ERR_WORKSPACE;
+    if (pb->precision != CG_PREC_FP64 && !df64_supported(pb)) return CG_ERR_UNSUPPORTED;
+    WsHeader* hdr = (WsHeader*)ws;
+    double* part = (double*)((char*)ws + sizeof(WsHeader));
+    const int64_t n = n_elements(pb);
+    const int nacc = acc_count(pb);
+    TileGrid tg;
+    EpiParams ep;
+    memset(&ep, 0, sizeof(ep));
+    ep.model = pb->model;
+    ep.P = num_params(pb);
+    ep.K = pb->n_peaks;
+    ep.D = pb->poly_degree;
+    ep.lo = pb->lo[0];
+    ep.hi = pb->hi[0];
+    if (n == 0) {
+        // empty data: every sum is zero; still produce value/grad and a clean status
+        cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st);
+        tg.n_elem = 0; tg.chunk = 1; tg.nbx = 1; tg.n_theta = (int)n_theta; tg.n_tiles = (int)n_theta;
+        cudaMemsetAsync(part, 0, (size_t)n_theta * (nacc + 1) * sizeof(double), st);
+        s = CG_OK;
+    } else if (pb->precision == CG_PREC_DF64) {
+        s = launch_df64(pb, theta, n_theta, part, hdr, &tg, st);
+    } else if (pb->model == CG_MODEL_GAUSS_POLY) {
+        GP1Data d;
+        d.y = pb->data;
+        d.centres = pb->centres;
+        d.lo = pb->lo[0];
+        d.h = (pb->hi[0] - pb->lo[0]) / (double)pb->n_bins[0];
+        d.au = 2.0 / (pb->hi[0] - pb->lo[0]);
+        d.bu = -(pb->lo[0] + pb->hi[0]) / (pb->hi[0] - pb->lo[0]);
+        d.D = pb->poly_degree;
+        d.pm = pb->poly_mode;
+        d.vec_ok = (((uintptr_t)pb->data & 15) == 0) && (!pb->centres || (((uintptr_t)pb->centres & 15) == 0));
+        switch (pb->n_peaks) {
+            case 0: s = launch_gp1_k<0>(pb, d, theta, n_theta, part, hdr, &tg, st); break;
+            case 1: s = launch_gp1_k<1>(pb, d, theta, n_theta, part, hdr, &tg, st); break;
+            case 2: s = launch_gp1_k<2>(pb, d, theta, n_theta, part, hdr, &tg, st); break;
+            case 3: s = launch_gp1_k<3>(pb, d, theta, n_theta, part, hdr, &tg, st); break;
+            case 4: s = launch_gp1_k<4>(pb, d, theta, n_theta, part, hdr, &tg, st); break;
+            default: return CG_ERR_INVALID_ARG;
+        }
+    } else if (pb->model == CG_MODEL_MIX_GAUSS_EXP) {
+        MixData d;
+        d.x = pb->data;
+        d.w = pb->weights;
+        d.lo = pb->lo[0];
+        d.hi = pb->hi[0];
+        d.vec_ok = (((uintptr_t)pb->data & 15) == 0) && (!pb->weights || (((uintptr_t)pb->weights & 15) == 0));
+        constexpr int NT = 256;
+        if (pb->weights) s = launch_tiles(k_mix_fp64<true, NT>, NT, d, theta, n, n_theta, part, hdr, &tg, st);
+        else s = launch_tiles(k_mix_fp64<false, NT>, NT, d, theta, n, n_theta, part, hdr, &tg, st);
+    } else {
+        RG2Data d;
+        d.n = pb->data;
+        d.nx = pb->n_bins[0];
+        d.lx = pb->lo[0];
+        d.ly = pb->lo[1];
+        d.hx = (pb->hi[0] - pb->lo[0]) / (double)pb->n_bins[0];
+        d.hy = (pb->hi[1] - pb->lo[1]) / (double)pb->n_bins[1];
+        switch (pb->n_peaks) {
+            case 1: s = launch_rg2_k<1>(d, theta, n, n_theta, part, hdr, &tg, st); break;
+            case 2: s = launch_rg2_k<2>(d, theta, n, n_theta, part, hdr, &tg, st); break;
+            case 3: s = launch_rg2_k<3>(d, theta, n, n_theta, part, hdr, &tg, st); break;
+            case 4: s = launch_rg2_k<4>(d, theta, n, n_theta, part, hdr, &tg, st); break;
+            case 5: s = launch_rg2_k<5>(d, theta, n, n_theta, part, hdr, &tg, st); break;
+            case 6: s = launch_rg2_k<6>(d, theta, n, n_theta, part, hdr, &tg, st); break;
+            case 7: s = launch_rg2_k<7>(d, theta, n, n_theta, part, hdr, &tg, st); break;
+            case 8: s = launch_rg2_k<8>(d, theta, n, n_theta, part, hdr, &tg, st); break;
+            default: return CG_ERR_INVALID_ARG;
+        }
+    }
+    if (s != CG_OK) return s;
+    k_finalize<128><<<(unsigned)n_theta, 128, 0, st>>>(part, nacc, tg, ep, theta, value, grad, hdr);
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
+
+}  // namespace cg
+
+using namespace cg;
+
+extern "C" {
+
+int cg_num_params(const cg_problem* pb) {
+    if (validate(pb) != CG_OK) return -1;
+    return num_params(pb);
+}
+
+size_t cg_workspace_size(const cg_problem* pb, int64_t n_theta) { return grad_workspace_bytes(pb, n_theta); }
+
+cg_status cg_objective(const cg_problem* pb, const double* theta, double* value, void* ws, size_t ws_bytes,
+                       void* stream) {
+    if (!value) return CG_ERR_INVALID_ARG;
+    return grad_points(pb, theta, 1, value, nullptr, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+cg_status cg_gradient(const cg_problem* pb, const double* theta, double* value, double* grad, void* ws,
+                      size_t ws_bytes, void* stream) {
+    if (!value || !grad) return CG_ERR_INVALID_ARG;
+    return grad_points(pb, theta, 1, value, grad, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+void cg_set_profile_events(void* start, void* stop) {
+    g_prof_start = (cudaEvent_t)start;
+    g_prof_stop = (cudaEvent_t)stop;
+}
+
+cg_status cg_get_status(const void* ws, void* stream) {
+    if (!ws) return CG_ERR_INVALID_ARG;
+    int32_t st = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&st, ws, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CG_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CG_ERR_CUDA;
+    if (st & DEV_TIMEOUT) return CG_ERR_TIMEOUT;
+    if (st & DEV_DOMAIN) return CG_ERR_DOMAIN;
+    return CG_OK;
+}
+
+const char* cg_status_string(cg_status s) {
+    switch (s) {
+        case CG_OK: return "ok";
+        case CG_ERR_INVALID_ARG: return "invalid argument";
+        case CG_ERR_DOMAIN: return "domain error (non-positive model value under a log, or non-finite term)";
+        case CG_ERR_CUDA: return "CUDA error";
+        case CG_ERR_TIMEOUT: return "device wait timed out";
+        case CG_ERR_NOT_CONVERGED: return "not converged";
+        case CG_ERR_UNSUPPORTED: return "unsupported combination";
+        case CG_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+"""The C ABI library loads on the host and exports every entry point that
+include/*.h declares; host-side argument checks run without a GPU."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import __graft_entry__
+from tests.conftest import ROOT
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(cg_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    __graft_entry__.build()
+    from paper_2203_06139_gb300 import cg
+    return cg.lib()
+
+
+def test_header_declares_the_four_calls():
+    names = declared_functions()
+    for n in ("cg_objective", "cg_gradient", "cg_batch_gradient", "cg_fit_step"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_side_validation_without_gpu(lib):
+    from paper_2203_06139_gb300 import cg
+    p = cg._Problem()
+    p.model, p.objective, p.precision = cg.MODEL_GAUSS_POLY, cg.OBJ_CHI2, cg.PREC_FP64
+    p.n_peaks, p.poly_degree, p.poly_mode = 1, 1, 0
+    p.n_bins[0] = 10000
+    p.lo[0], p.hi[0] = 0.0, 10.0
+    p.data = 256  # never dereferenced by the host checks
+    assert lib.cg_num_params(ctypes.byref(p)) == 5
+    assert lib.cg_workspace_size(ctypes.byref(p), 100) > 0
+    bad = cg._Problem()
+    bad.model = 7
+    assert lib.cg_num_params(ctypes.byref(bad)) == -1
+    assert lib.cg_workspace_size(ctypes.byref(bad), 1) == 0
+    assert lib.cg_gradient(None, None, None, None, None, 0, None) == cg.ERR_INVALID_ARG
+    p2 = cg._Problem.from_buffer_copy(p)
+    p2.n_peaks = 5
+    assert lib.cg_num_params(ctypes.byref(p2)) == -1
+    # workspace too small / misaligned is refused before any launch
+    assert lib.cg_gradient(ctypes.byref(p), ctypes.c_void_p(256), ctypes.c_void_p(512), ctypes.c_void_p(768),
+                           ctypes.c_void_p(1024), 16, None) == cg.ERR_WORKSPACE
+    assert lib.cg_gradient(ctypes.byref(p), ctypes.c_void_p(256), ctypes.c_void_p(512), ctypes.c_void_p(768),
+                           ctypes.c_void_p(1025), 1 << 30, None) == cg.ERR_WORKSPACE
+    assert lib.cg_status_string(cg.ERR_DOMAIN).startswith(b"domain")
