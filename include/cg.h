@@ -167,6 +167,36 @@ cg_status cg_batch_gradient(const cg_batch *b, const double *theta, double *valu
  * if the copy fails). */
 cg_status cg_get_status(const void *ws, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Gradient without any caller-provided or library-allocated device memory.
+ * The paper has no counterpart; this exists for callers that cannot
+ * allocate device memory or pass a workspace (code running under another
+ * framework's allocator or memory pool, plug-ins whose host owns every
+ * device buffer, real-time loops where an allocation may block or fail).
+ *
+ * Same result as cg_batch_gradient with offsets == NULL for the unbinned
+ * mixture model (CG_MODEL_MIX_GAUSS_EXP, CG_OBJ_UNBINNED_NLL, CG_PREC_FP64),
+ * for n_theta parameter points: theta device [n_theta][4], value device
+ * [n_theta], grad device [n_theta][4]; events (and optional weights) as in
+ * cg_problem.  The per-tile partial sums live in one static device array of
+ * CG_NOALLOC_SCRATCH_BYTES bytes inside libcg, created on every GPU that
+ * loads the library and kept until the process exits.
+ *  - n_theta > CG_NOALLOC_MAX_POINTS returns CG_ERR_INVALID_ARG (the array
+ *    would not hold the partials); so do other models or precisions.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before capturing any stream.
+ *  - It calls no cudaMalloc, cudaFree or allocating library routine.
+ *  - All calls share the array and it keeps the last call's contents; every
+ *    call overwrites the slots it reads, so nothing is cleared.  Calls that
+ *    overlap on the GPU (other streams, other host threads) race on it.
+ *  - A parameter point whose terms hit a domain error gets a NaN value
+ *    (there is no workspace status word to read). */
+#define CG_NOALLOC_SCRATCH_BYTES (1u << 20)
+#define CG_NOALLOC_MAX_POINTS 4096
+cg_status cg_mixture_gradient_noalloc(const cg_problem *pb, const double *theta, int64_t n_theta,
+                                      double *value, double *grad, void *stream);
+
 /* Profiling hook: when start/stop are non-NULL cudaEvent_t handles (passed as
  * void*), every later launch of a fused accumulation kernel (the dominant
  * kernel of cg_objective / cg_gradient / cg_batch_gradient / cg_fit_*)
