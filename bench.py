@@ -308,8 +308,26 @@ def run(args):
         torch.distributed.destroy_process_group()
 
 
+# FP32-pipe operations of one event at one parameter point in the double-float
+# kernel, counted from its arithmetic (csrc/cg_df64.cuh, cg_df64.cu): two
+# df64 subtractions (11 each), a square and 6 products/ratios at 7 (df_mul),
+# two exp (60 each), one df64 sum of products (25), reciprocal (8), log (65),
+# 6 compensated accumulations (8 each).
+DF64_MIX_OPS = 346
+
+
 def df64_roofline(dur_s, n_units, rates, sm_max_mhz):
-    return {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None}
+    """ALU roofline of the double-float kernel: FP32-pipe operations / time vs the
+    FP32 unit rate at the maximum SM clock (152 SMs x 128 lanes x 2 flop)."""
+    nsm = rates["n_sm"] if rates else 152
+    peak = nsm * 128 * 2 * (sm_max_mhz or 2070.0) * 1e6 / 1e12
+    achieved = DF64_MIX_OPS * n_units * 2 / dur_s / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_mix_df64",
+            "work_per_unit": "%d FP32-pipe operations per event-point (FMA-equivalent flops = 2 per op)"
+                             % DF64_MIX_OPS,
+            "peak_basis": "FP32 unit: %d SMs x 128 lanes x 2 flop x %.0f MHz (unit counts and max clock)"
+                          % (nsm, sm_max_mhz or 2070.0)}
 
 
 def main():

@@ -1,12 +1,138 @@
 // cg_df64.cu -- double-float (FP32-pipe) variants of the fused kernels.
+//
+// Same models, same accumulators and same epilogue as the FP64 kernels
+// (cg_models.cuh); only the per-element forward + adjoint arithmetic is
+// carried out in df64 (cg_df64.cuh).  Per-thread accumulators are
+// compensated float pairs flushed into FP64 sums every kFlush elements, so
+// every sum that leaves a thread is FP64.  Elements whose df64 evaluation
+// could lose accuracy (an exponential flushed to zero while the model value
+// is itself tiny) are recomputed in FP64 in place.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "cg_df64.cuh"
 #include "cg_internal.cuh"
 #include "cg_models.cuh"
+#include "cg_tiles.cuh"
 
 namespace cg {
 
-bool df64_supported(const cg_problem*) { return false; }
+constexpr int kFlush = 32;
 
-cg_status launch_df64(const cg_problem*, const double*, int64_t, double*, WsHeader*, TileGrid*, cudaStream_t) {
+// ===========================================================================
+// Unbinned mixture
+// ===========================================================================
+struct MixDf {
+    df mu, c, a, b, mlam, lo;
+};
+
+__device__ __forceinline__ void mix_split(const MixConsts& c64, MixDf& c) {
+    c.mu = df_from_double(c64.mu);
+    c.c = df_from_double(c64.c);
+    c.a = df_from_double(c64.a);
+    c.b = df_from_double(c64.b);
+    c.mlam = df_from_double(-c64.lam);
+    c.lo = df_from_double(c64.lo);
+}
+
+template <bool W>
+__device__ __forceinline__ void mix_elem_df64(double x, double w, const MixDf& c, const MixConsts& c64,
+                                              const DfTables& tab, DfAcc (&acc)[MixAcc::N],
+                                              double (&sum)[MixAcc::N], bool& bad) {
+    const df X = df_from_double(x);
+    const df d = df_sub(X, c.mu);
+    const df q = df_mul(c.c, df_sqr(d));
+    const df xl = df_sub(X, c.lo);
+    const df t = df_mul(c.mlam, xl);
+    bool flG = false, flE = false;
+    const df eG = df_exp(q, tab, flG);
+    const df eE = df_exp(t, tab, flE);
+    const df p = df_add(df_mul(c.a, eG), df_mul(c.b, eE));
+    // a flushed component (< 1e-30 of its coefficient) is negligible unless p is tiny too
+    if ((flG && p.h < 1e-13f * fabsf(c.a.h)) || (flE && p.h < 1e-13f * fabsf(c.b.h)) || !(p.h > 1e-30f)) {
+        mix_elem_fp64<W>(x, w, c64, sum, bad);
+        return;
+    }
+    df r = df_rcp(p);
+    df L = df_log(p, tab);
+    if (W) {
+        const df wd = df_from_double(w);
+        r = df_mul(r, wd);
+        L = df_mul(L, wd);
+    }
+    const df U = df_mul(eG, r);
+    const df V = df_mul(eE, r);
+    const df Ud = df_mul(U, d);
+    dfacc_add(acc[0], L);
+    dfacc_add(acc[1], U);
+    dfacc_add(acc[2], Ud);
+    dfacc_add(acc[3], df_mul(Ud, d));
+    dfacc_add(acc[4], V);
+    dfacc_add(acc[5], df_mul(V, xl));
+}
+
+template <bool W, int NT>
+__global__ void __launch_bounds__(NT, 2) k_mix_df64(MixData d, const double* __restrict__ theta, TileGrid tg,
+                                                 double* __restrict__ part, WsHeader* __restrict__ hdr) {
+    constexpr int NACC = MixAcc::N;
+    __shared__ DfTables tab;
+    __shared__ MixConsts cs64;
+    __shared__ MixDf cs;
+    __shared__ int cs_bad;
+    __shared__ double red[NACC * (NT / 32)];
+    __shared__ double tot[NACC];
+    if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
+    df_tables_init(tab);
+    for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
+        const int th = t / tg.nbx, c = t - th * tg.nbx;
+        if (threadIdx.x == 0) {
+            cs_bad = mix_prologue(theta + (size_t)th * 4, d.lo, d.hi, cs64) ? 0 : 1;
+            mix_split(cs64, cs);
+        }
+        __syncthreads();
+        DfAcc acc[NACC];
+        double sum[NACC];
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) {
+            acc[a].s = acc[a].c = 0.0f;
+            sum[a] = 0.0;
+        }
+        bool bad = false;
+        int cnt = 0;
+        const int64_t e0 = (int64_t)c * tg.chunk;
+        const int64_t e1 = min(tg.n_elem, e0 + tg.chunk);
+        for (int64_t i = e0 + threadIdx.x; i < e1; i += NT) {
+            mix_elem_df64<W>(__ldg(d.x + i), W ? __ldg(d.w + i) : 1.0, cs, cs64, tab, acc, sum, bad);
+            if (++cnt == kFlush) {
+#pragma unroll
+                for (int a = 0; a < NACC; ++a) dfacc_flush(acc[a], sum[a]);
+                cnt = 0;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) dfacc_flush(acc[a], sum[a]);
+        const int any_bad = __syncthreads_or(bad ? 1 : 0) | cs_bad;
+        block_sum<NACC, NT>(sum, red, tot);
+        write_partial<NACC>(part, tg, th, c, tot, any_bad);
+    }
+}
+
+bool df64_supported(const cg_problem* pb) { return pb->model == CG_MODEL_MIX_GAUSS_EXP; }
+
+cg_status launch_df64(const cg_problem* pb, const double* theta, int64_t n_theta, double* part, WsHeader* hdr,
+                      TileGrid* tg, cudaStream_t st) {
+    if (pb->model == CG_MODEL_MIX_GAUSS_EXP) {
+        MixData d;
+        d.x = pb->data;
+        d.w = pb->weights;
+        d.lo = pb->lo[0];
+        d.hi = pb->hi[0];
+        d.vec_ok = 0;
+        constexpr int NT = 256;
+        if (pb->weights) return launch_tiles(k_mix_df64<true, NT>, NT, d, theta, pb->n_events, n_theta, part, hdr, tg, st);
+        return launch_tiles(k_mix_df64<false, NT>, NT, d, theta, pb->n_events, n_theta, part, hdr, tg, st);
+    }
     return CG_ERR_UNSUPPORTED;
 }
 

@@ -30,6 +30,7 @@
 
 #include "cg_internal.cuh"
 #include "cg_models.cuh"
+#include "cg_tiles.cuh"
 
 namespace cg {
 
@@ -43,33 +44,9 @@ int device_sm_count() {
     return n;
 }
 
-// Resident blocks per SM of a kernel, cached per (kernel, threads).
-static int resident_blocks(const void* fn, int threads, size_t smem) {
-    static std::mutex mu;
-    static std::unordered_map<const void*, int> cache;
-    std::lock_guard<std::mutex> lk(mu);
-    auto it = cache.find(fn);
-    if (it != cache.end()) return it->second;
-    int r = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, fn, threads, smem) != cudaSuccess || r < 1) r = 1;
-    cache[fn] = r;
-    return r;
-}
-
 // ---------------------------------------------------------------------------
 // Tile accumulation kernels
 // ---------------------------------------------------------------------------
-
-// Write one tile's partial sums: part[(th * (NACC + 1) + a) * nbx + c].
-template <int NACC>
-__device__ __forceinline__ void write_partial(double* __restrict__ part, const TileGrid& tg, int th,
-                                              int c, const double* tot, int bad) {
-    if (threadIdx.x == 0) {
-        double* p = part + (size_t)th * (NACC + 1) * tg.nbx + c;
-        for (int a = 0; a < NACC; ++a) p[(size_t)a * tg.nbx] = tot[a];
-        p[(size_t)NACC * tg.nbx] = bad ? 1.0 : 0.0;
-    }
-}
 
 template <int K, int OBJ, int NT>
 __global__ void __launch_bounds__(NT) k_gp1_fp64(GP1Data d, const double* __restrict__ theta,
@@ -241,8 +218,6 @@ __global__ void __launch_bounds__(NT) k_finalize(const double* __restrict__ part
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-static constexpr int kMaxTiles = 16384;
-
 static int acc_count(const cg_problem* pb) {
     switch (pb->model) {
         case CG_MODEL_GAUSS_POLY: return 1 + 3 * pb->n_peaks + 4;
@@ -303,53 +278,10 @@ static int num_params(const cg_problem* pb) {
     }
 }
 
-static int max_nbx(int64_t n_theta) {
-    int64_t m = (kMaxTiles + n_theta - 1) / n_theta;
-    return (int)(m < 1 ? 1 : m);
-}
-
 size_t grad_workspace_bytes(const cg_problem* pb, int64_t n_theta) {
     if (validate(pb) != CG_OK || n_theta < 1) return 0;
     const int nacc = acc_count(pb);
     return sizeof(WsHeader) + align_up((size_t)n_theta * (nacc + 1) * max_nbx(n_theta) * sizeof(double), 256);
-}
-
-// Choose the tile grid: ~4 tiles per resident block, at least 8 elements per
-// thread per tile, chunk a multiple of 2*NT (keeps 16-byte alignment).
-static TileGrid make_tiles(int64_t n_elem, int64_t n_theta, int NT, int grid_blocks) {
-    TileGrid tg;
-    tg.n_elem = n_elem;
-    int64_t want = ((int64_t)grid_blocks * 4 + n_theta - 1) / n_theta;
-    int64_t per_tile_min = (int64_t)NT * 8;
-    int64_t most = (n_elem + per_tile_min - 1) / per_tile_min;
-    int64_t nbx = want < most ? want : most;
-    if (nbx < 1) nbx = 1;
-    if (nbx > max_nbx(n_theta)) nbx = max_nbx(n_theta);
-    int64_t chunk = (n_elem + nbx - 1) / nbx;
-    chunk = (chunk + 2 * NT - 1) / (2 * NT) * (2 * NT);
-    if (chunk < 2 * NT) chunk = 2 * NT;
-    nbx = (n_elem + chunk - 1) / chunk;
-    if (nbx < 1) nbx = 1;
-    tg.chunk = chunk;
-    tg.nbx = (int)nbx;
-    tg.n_theta = (int)n_theta;
-    tg.n_tiles = (int)(n_theta * nbx);
-    return tg;
-}
-
-template <typename KernelT, typename DataT>
-static cg_status launch_tiles(KernelT kern, int NT, const DataT& d, const double* theta, int64_t n_elem,
-                              int64_t n_theta, double* part, WsHeader* hdr, TileGrid* tg_out,
-                              cudaStream_t st) {
-    const int R = resident_blocks((const void*)kern, NT, 0);
-    const int G = device_sm_count() * R;
-    TileGrid tg = make_tiles(n_elem, n_theta, NT, G);
-    int grid = tg.n_tiles < G ? tg.n_tiles : G;
-    prof_begin(st);
-    kern<<<grid, NT, 0, st>>>(d, theta, tg, part, hdr);
-    prof_end(st);
-    *tg_out = tg;
-    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
 }
 
 template <int K>

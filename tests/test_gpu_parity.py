@@ -215,3 +215,61 @@ def test_c3_full_size(dev):
     p2 = cg.Problem.rotgauss2d(torch.tensor(h["counts"], device=dev), 8)
     v, g = cg.gradient(p2, torch.tensor(th, device=dev))
     check(v, g, oracle.binned2d(8, h["counts"], 0.0, 1.0, 0.0, 1.0, th))
+
+
+# --------------------------------------------------------------------------
+# double-float (FP32-pipe) path: same bar against the oracle, and its error
+# against the FP64 path is recorded
+# --------------------------------------------------------------------------
+def test_mixture_df64_small(dev):
+    x = synth.c2_events(100003)
+    th = synth.c2_theta_points(5)
+    pm = cg.Problem.mixture(torch.tensor(x, device=dev), 0.0, 10.0, precision=cg.PREC_DF64)
+    v, g = cg.batch_gradient(pm, torch.tensor(th, device=dev))
+    assert pm.status(5) == cg.OK
+    for i in range(5):
+        check(v[i], g[i], oracle.unbinned_mix(x, 0.0, 10.0, th[i]))
+
+
+def test_mixture_df64_weighted_other_range(dev):
+    x = synth.c2_events(50001, truth=np.array([0.6, 3.0, 0.8, 0.3]), lo=1.0, hi=7.5)
+    w = np.random.default_rng(9).uniform(0.2, 2.0, x.size)
+    th = np.array([0.55, 3.1, 0.75, 0.33])
+    pm = cg.Problem.mixture(torch.tensor(x, device=dev), 1.0, 7.5, weights=torch.tensor(w, device=dev),
+                            precision=cg.PREC_DF64)
+    v, g = cg.gradient(pm, torch.tensor(th, device=dev))
+    check(v, g, oracle.unbinned_mix(x, 1.0, 7.5, th, weights=w))
+
+
+def test_mixture_df64_tails_fall_back(dev):
+    """Events deep in both tails (both exponentials below 1e-30 of their
+    coefficients) take the FP64 fallback; results still match the oracle."""
+    x = np.concatenate([synth.c2_events(4001), np.array([9.99, 9.999, 0.0, 1e-12])])
+    th = np.array([0.999, 0.5, 0.05, 9.0])   # narrow Gaussian, steep exponential
+    pm = cg.Problem.mixture(torch.tensor(x, device=dev), 0.0, 10.0, precision=cg.PREC_DF64)
+    v, g = cg.gradient(pm, torch.tensor(th, device=dev))
+    check(v, g, oracle.unbinned_mix(x, 0.0, 10.0, th))
+
+
+@pytest.mark.slow
+def test_c2_df64_full_size_and_error_vs_fp64(dev, record_property):
+    x = synth.c2_events()
+    th = synth.c2_theta_points()
+    xt, tt = torch.tensor(x, device=dev), torch.tensor(th, device=dev)
+    p64 = cg.Problem.mixture(xt, 0.0, 10.0)
+    pdf = cg.Problem.mixture(xt, 0.0, 10.0, precision=cg.PREC_DF64)
+    v64, g64 = cg.batch_gradient(p64, tt)
+    vdf, gdf = cg.batch_gradient(pdf, tt)
+    assert pdf.status(50) == cg.OK
+    idx = [0, 17, 33, 49]
+    refs = oracle.many(oracle.unbinned_mix, th[idx], x=x, lo=0.0, hi=10.0)
+    for i, ref in zip(idx, refs):
+        check(vdf[i], gdf[i], ref)
+    # stated error of the double-float path against the FP64 path, all 50 points
+    gv = (gdf - g64).abs() / g64.abs()
+    vv = (vdf - v64).abs() / v64.abs()
+    err_g, err_v = float(gv.max()), float(vv.max())
+    record_property("df64_vs_fp64_max_rel_grad", err_g)
+    record_property("df64_vs_fp64_max_rel_value", err_v)
+    print("df64 vs fp64: max rel grad %.3e, value %.3e" % (err_g, err_v))
+    assert err_g < 1e-11 and err_v < 1e-12
