@@ -279,6 +279,31 @@ def run(args):
         e2e_s = float(t.item())
     assert np.allclose(v_pin.numpy(), values.cpu().numpy())
 
+    # ---- the same step on the FP64 path (comparison leg) ----
+    fp64_leg = None
+    if prec != cg.PREC_FP64 and not args.no_fp64_leg:
+        p64 = cg.Problem.mixture(x, 0.0, 10.0, precision=cg.PREC_FP64)
+        v64 = torch.empty_like(values)
+        g64 = torch.empty_like(grads)
+        for _ in range(3):
+            cg.batch_gradient(p64, th, v64, g64)
+        torch.cuda.synchronize()
+        f0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        f1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            f0[i].record(stream)
+            cg.batch_gradient(p64, th, v64, g64)
+            f1[i].record(stream)
+        torch.cuda.synchronize()
+        ms64 = sum(a.elapsed_time(b) for a, b in zip(f0, f1)) / args.steps
+        cg.batch_gradient(pb, th, values, grads)
+        rel_g = float(((grads - g64).abs() / g64.abs()).max())
+        rel_v = float(((values - v64).abs() / v64.abs()).max())
+        fp64_leg = {"ms_per_step": ms64, "value": N_EV * N_PT / (ms64 / 1e3), "unit": UNIT,
+                    "speedup_of_headline": ms64 / (total_s / args.steps * 1e3),
+                    "headline_vs_fp64_max_rel_err": {"grad": rel_g, "value": rel_v}}
+
     if rank == 0:
         roof = fp64_roofline(kern_s, N_EV * N_PT, rates, clk.get("sm_max_mhz")) if prec == cg.PREC_FP64 \
             else df64_roofline(kern_s, N_EV * N_PT, rates, clk.get("sm_max_mhz"))
@@ -286,7 +311,8 @@ def run(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == cg.PREC_FP64 else "df64 (f32 pairs) with f64 accumulation",
+            "dtype": "f64" if prec == cg.PREC_FP64 else
+            "f64-accurate double-float (f32 pairs, FP32 pipe) with f64 accumulation",
             "data": "synthetic (seeded numpy PCG64; see synth.py)",
             "config": {"workload": workload_name(N_EV, N_PT), "events": N_EV, "points_per_gpu": N_PT,
                        "l2": "flushed before every timed step (256 MB write)", "parallelism":
@@ -300,6 +326,7 @@ def run(args):
             "roofline": roof,
             "clocks": clk,
             "unit_rates": rates,
+            "fp64_path": fp64_leg,
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "first 1e6 events x %d parameter points (%.1f s wall)" % (N_PT, cpu_dt)},
         }
@@ -336,7 +363,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cg", choices=["cg", "reference"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "df64"])
+    ap.add_argument("--prec", default="df64", choices=["fp64", "df64"])
+    ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64-path comparison leg")
     ap.add_argument("--events", type=int, default=N_EVENTS)
     ap.add_argument("--points", type=int, default=N_POINTS)
     args = ap.parse_args()

@@ -18,7 +18,7 @@
 
 namespace cg {
 
-constexpr int kFlush = 32;
+constexpr int kFlush = 32;   // elements per compensated run before the FP64 flush
 
 // ===========================================================================
 // Unbinned mixture
@@ -36,11 +36,24 @@ __device__ __forceinline__ void mix_split(const MixConsts& c64, MixDf& c) {
     c.lo = df_from_double(c64.lo);
 }
 
+// FP64 evaluation of one event, added to this thread's FP64 sums (rare path).
+template <bool W>
+__device__ __noinline__ void mix_elem_fallback(double x, double w, const MixConsts& c64, double* sum, int* bad) {
+    double a[MixAcc::N] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    bool b = false;
+    mix_elem_fp64<W>(x, w, c64, a, b);
+    for (int k = 0; k < MixAcc::N; ++k) sum[k * 256] += a[k];
+    if (b) *bad = 1;
+}
+
+// One event: forward p(x), adjoint accumulators.  Without weights the log
+// terms are gathered as a running product P (one df_log per flush); with
+// weights each log is taken and weighted.
 template <bool W>
 __device__ __forceinline__ void mix_elem_df64(double x, double w, const MixDf& c, const MixConsts& c64,
-                                              const DfTables& tab, DfAcc (&acc)[MixAcc::N],
-                                              double (&sum)[MixAcc::N], bool& bad) {
-    const df X = df_from_double(x);
+                                              const DfTables& tab, DfAcc (&acc)[MixAcc::N], DfProd& P,
+                                              double* sum, int* bad) {
+    const df X = df_split(x);
     const df d = df_sub(X, c.mu);
     const df q = df_mul(c.c, df_sqr(d));
     const df xl = df_sub(X, c.lo);
@@ -48,32 +61,32 @@ __device__ __forceinline__ void mix_elem_df64(double x, double w, const MixDf& c
     bool flG = false, flE = false;
     const df eG = df_exp(q, tab, flG);
     const df eE = df_exp(t, tab, flE);
-    const df p = df_add(df_mul(c.a, eG), df_mul(c.b, eE));
+    const df p = df_add(df_mul_nn(c.a, eG), df_mul_nn(c.b, eE));
     // a flushed component (< 1e-30 of its coefficient) is negligible unless p is tiny too
     if ((flG && p.h < 1e-13f * fabsf(c.a.h)) || (flE && p.h < 1e-13f * fabsf(c.b.h)) || !(p.h > 1e-30f)) {
-        mix_elem_fp64<W>(x, w, c64, sum, bad);
+        mix_elem_fallback<W>(x, w, c64, sum, bad);
         return;
     }
     df r = df_rcp(p);
-    df L = df_log(p, tab);
     if (W) {
-        const df wd = df_from_double(w);
+        const df wd = df_split(w);
         r = df_mul(r, wd);
-        L = df_mul(L, wd);
+        dfacc_add(acc[0], df_mul(df_log(p, tab), wd));
+    } else {
+        dfprod_mul(P, p);
     }
-    const df U = df_mul(eG, r);
-    const df V = df_mul(eE, r);
-    const df Ud = df_mul(U, d);
-    dfacc_add(acc[0], L);
+    const df U = df_mul_nn(eG, r);
+    const df V = df_mul_nn(eE, r);
+    const df Ud = df_mul_nn(U, d);
     dfacc_add(acc[1], U);
     dfacc_add(acc[2], Ud);
-    dfacc_add(acc[3], df_mul(Ud, d));
+    dfacc_add(acc[3], df_mul_nn(Ud, d));
     dfacc_add(acc[4], V);
-    dfacc_add(acc[5], df_mul(V, xl));
+    dfacc_add(acc[5], df_mul_nn(V, xl));
 }
 
 template <bool W, int NT>
-__global__ void __launch_bounds__(NT, 2) k_mix_df64(MixData d, const double* __restrict__ theta, TileGrid tg,
+__global__ void __launch_bounds__(NT, 3) k_mix_df64(MixData d, const double* __restrict__ theta, TileGrid tg,
                                                  double* __restrict__ part, WsHeader* __restrict__ hdr) {
     constexpr int NACC = MixAcc::N;
     __shared__ DfTables tab;
@@ -82,6 +95,8 @@ __global__ void __launch_bounds__(NT, 2) k_mix_df64(MixData d, const double* __r
     __shared__ int cs_bad;
     __shared__ double red[NACC * (NT / 32)];
     __shared__ double tot[NACC];
+    __shared__ double ssum[NACC * NT];
+    static_assert(NT == 256, "fallback sums use a stride of 256");
     if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
     df_tables_init(tab);
     for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
@@ -91,29 +106,42 @@ __global__ void __launch_bounds__(NT, 2) k_mix_df64(MixData d, const double* __r
             mix_split(cs64, cs);
         }
         __syncthreads();
+        const MixDf cr = cs;   // per-tile constants in registers
+        double* sum = ssum + threadIdx.x;   // this thread's FP64 sums, stride NT
         DfAcc acc[NACC];
-        double sum[NACC];
 #pragma unroll
         for (int a = 0; a < NACC; ++a) {
             acc[a].s = acc[a].c = 0.0f;
-            sum[a] = 0.0;
+            sum[a * NT] = 0.0;
         }
-        bool bad = false;
+        DfProd P;
+        P.m = df_make(1.0f, 0.0f);
+        P.E = 0;
+        int bad = 0;
         int cnt = 0;
         const int64_t e0 = (int64_t)c * tg.chunk;
         const int64_t e1 = min(tg.n_elem, e0 + tg.chunk);
         for (int64_t i = e0 + threadIdx.x; i < e1; i += NT) {
-            mix_elem_df64<W>(__ldg(d.x + i), W ? __ldg(d.w + i) : 1.0, cs, cs64, tab, acc, sum, bad);
+            mix_elem_df64<W>(__ldg(d.x + i), W ? __ldg(d.w + i) : 1.0, cr, cs64, tab, acc, P, sum, &bad);
             if (++cnt == kFlush) {
+                if (!W) {
+                    dfacc_add(acc[0], dfprod_log(P, tab));
+                    P.m = df_make(1.0f, 0.0f);
+                    P.E = 0;
+                }
 #pragma unroll
-                for (int a = 0; a < NACC; ++a) dfacc_flush(acc[a], sum[a]);
+                for (int a = 0; a < NACC; ++a) dfacc_flush(acc[a], sum[a * NT]);
                 cnt = 0;
             }
         }
+        if (!W) dfacc_add(acc[0], dfprod_log(P, tab));
 #pragma unroll
-        for (int a = 0; a < NACC; ++a) dfacc_flush(acc[a], sum[a]);
-        const int any_bad = __syncthreads_or(bad ? 1 : 0) | cs_bad;
-        block_sum<NACC, NT>(sum, red, tot);
+        for (int a = 0; a < NACC; ++a) dfacc_flush(acc[a], sum[a * NT]);
+        double fin[NACC];
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) fin[a] = sum[a * NT];
+        const int any_bad = __syncthreads_or(bad) | cs_bad;
+        block_sum<NACC, NT>(fin, red, tot);
         write_partial<NACC>(part, tg, th, c, tot, any_bad);
     }
 }

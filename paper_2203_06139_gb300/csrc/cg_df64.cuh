@@ -44,6 +44,29 @@ __device__ __forceinline__ df df_from_double(double x) {
 
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.h + (double)a.l; }
 
+// Split a double into a float pair with integer operations only (no FP64
+// instruction): hi = the leading 24 significand bits, lo = the next 29 bits
+// rounded to 23; |x - (hi + lo)| <= 2^-47 |x|.  Doubles with exponents
+// outside [-80, 127] go through the conversion instructions instead.
+__device__ __forceinline__ df df_split(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+    const int e = (int)((hw >> 20) & 0x7ffu) - 1023;
+    if (e < -80 || e > 127) return df_from_double(x);
+    const unsigned sign = hw & 0x80000000u;
+    const float h = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
+    // remaining 29 bits r of the significand; value r 2^(e-52)
+    const unsigned rt = ((lw & 0x1fffffffu) + 32u) >> 6;                  // 23 bits, rounded (may reach 2^23)
+    float l = __fsub_rn(__uint_as_float(0x4b000000u | rt), 8388608.0f);   // exact float(rt)
+    if (rt == 0x800000u) l = 8388608.0f;
+    l = __fmul_rn(l, __uint_as_float((unsigned)(e + 81) << 23));          // * 2^(e - 46)
+    return df_make(h, __uint_as_float(__float_as_uint(l) | sign));
+}
+
+// Products whose result only feeds an accumulator or another product do not
+// need the final renormalisation: hi + lo is still the rounded product.
+__device__ __forceinline__ df df_mul_nn(df a, df b);
+
 // s + e = a + b exactly
 __device__ __forceinline__ df two_sum(float a, float b) {
     const float s = __fadd_rn(a, b);
@@ -84,6 +107,12 @@ __device__ __forceinline__ df df_mul(df a, df b) {
     float e = fmaf(a.h, b.l, p.l);
     e = fmaf(a.l, b.h, e);
     return fast_two_sum(p.h, e);
+}
+
+__device__ __forceinline__ df df_mul_nn(df a, df b) {
+    df p = two_prod(a.h, b.h);
+    float e = fmaf(a.h, b.l, p.l);
+    return df_make(p.h, fmaf(a.l, b.h, e));
 }
 
 __device__ __forceinline__ df df_mul_f(df a, float b) {
@@ -218,6 +247,32 @@ __device__ __forceinline__ df df_log(df p, const DfTables& tab) {
     float l2 = __fadd_rn(__fadd_rn(a.l, c.l),
                          __fadd_rn(__fadd_rn(b.h, fmaf(Ef, CG_LN2_L, b.l)), __fadd_rn(lf.y, lo)));
     return fast_two_sum(c.h, l2);
+}
+
+// Running product of positive df64 factors with its binary exponent kept
+// apart (so a long product neither underflows nor overflows): value =
+// (m.h + m.l) 2^E.  log of it = df_log(m) + E ln2.
+struct DfProd {
+    df m;
+    int E;
+};
+
+__device__ __forceinline__ void dfprod_mul(DfProd& P, df x) {
+    df r = df_mul(P.m, x);
+    // move the binary exponent eb of r.h (r.h > 0, normal) into E: scale by 2^-eb exactly
+    const int eb = (int)((__float_as_uint(r.h) >> 23) & 0xffu) - 127;
+    const float sc = __uint_as_float((unsigned)(127 - eb) << 23);
+    P.m.h = __fmul_rn(r.h, sc);
+    P.m.l = __fmul_rn(r.l, sc);
+    P.E += eb;
+}
+
+__device__ __forceinline__ df dfprod_log(const DfProd& P, const DfTables& tab) {
+    df l = df_log(P.m, tab);
+    const float Ef = (float)P.E;
+    df a = two_sum(l.h, __fmul_rn(Ef, CG_LN2_H));
+    df b = two_prod(Ef, CG_LN2_M);
+    return fast_two_sum(a.h, __fadd_rn(__fadd_rn(a.l, l.l), __fadd_rn(b.h, fmaf(Ef, CG_LN2_L, b.l))));
 }
 
 // Compensated per-thread accumulator of df64 terms, flushed into an FP64 sum.
