@@ -250,35 +250,46 @@ typedef struct {
     int32_t cluster_size;    /* 1, 2, 4 or 8 */
 } cg_tile_map;
 
-/* Workspace for the fit calls on batch b (offsets != NULL). */
+/* Workspace for the batched fit calls on batch b (offsets != NULL): header,
+ * work queues and per-histogram scratch. */
 size_t cg_fit_workspace_size(const cg_batch *b);
 
 /* Work queues of the batched fitter, built on the host from the host copy of
- * the bin offsets (host_offsets[n_hist + 1]) and uploaded into ws.  Must be
- * called once before cg_fit_init/cg_fit_step with the same ws and map. */
+ * the bin offsets (host_offsets[n_hist + 1]): histograms with more than
+ * map->cta_max_bins bins go to the cluster queue (or the CTA queue when
+ * cluster_size == 1), those with more than map->warp_max_bins to the CTA
+ * queue, the rest to the warp queue; each queue is sorted by decreasing
+ * size.  Uploaded into ws; this call synchronises `stream`.  Must precede
+ * cg_fit_init / cg_fit_step on the same ws with the same map. */
 cg_status cg_fit_plan(const cg_batch *b, const int64_t *host_offsets, const cg_tile_map *map,
                       void *ws, size_t ws_bytes, void *stream);
 
-/* Initialise fit states at theta0 (device [n_hist][P]): evaluates F, g and
- * the Gauss-Newton diagonal, sets H = diag(1/GN). */
-cg_status cg_fit_init(const cg_batch *b, const double *theta0, cg_fit_state *state,
-                      void *ws, size_t ws_bytes, void *stream);
+/* Initialise fit states at theta0 (device [n_hist][P], P <= CG_FIT_MAX_PARAMS):
+ * one evaluation of F, g and the Gauss-Newton diagonal GN per histogram,
+ * H = diag(1/GN) (1 where GN <= 0), status CG_FIT_RUNNING, or CG_FIT_DOMAIN
+ * when F(theta0) is not finite.  Binned 1-D models with 1..3 peaks. */
+cg_status cg_fit_init(const cg_batch *b, const cg_tile_map *map, const double *theta0,
+                      cg_fit_state *state, void *ws, size_t ws_bytes, void *stream);
 
 /* Run up to n_steps BFGS iterations on every histogram whose status is
- * CG_FIT_RUNNING, in ONE persistent launch (histograms of different sizes
- * handled by warps, CTAs or CTA clusters as the plan says).  One iteration:
- * d = -H g (reset to the initial diagonal when g.d >= 0); trial points
- * theta + alpha d from alpha = 1, accepted when F(trial) <= F + 1e-4 alpha
- * g.d, otherwise alpha shrinks to the clamped quadratic-interpolation
- * minimiser in [0.1, 0.5] alpha (0.1 alpha for a non-finite F), at most 20
- * trials; BFGS update when s.y > 1e-12 |s||y|; converged when
- * EDM = g.H.g/2 < tol * max(1, |F|). */
-cg_status cg_fit_step(const cg_batch *b, cg_fit_state *state, int n_steps, double tol,
-                      void *ws, size_t ws_bytes, void *stream);
+ * CG_FIT_RUNNING, in ONE persistent launch (after a 16-byte reset of the
+ * queue counters): warps, CTAs and CTA clusters pop histograms from their
+ * queues.  One iteration: d = -H g (reset to the initial diagonal when
+ * g.d >= 0); trial points theta + alpha d from alpha = 1, accepted when
+ * F(trial) <= F + 1e-4 alpha g.d, otherwise alpha becomes the minimiser of
+ * the quadratic through F, g.d and F(trial) clamped to [0.1, 0.5] alpha
+ * (0.1 alpha for a non-finite F), at most 20 trials (then
+ * CG_FIT_LINESEARCH_FAILED); BFGS update when s.y > 1e-12 |s||y|;
+ * CG_FIT_CONVERGED when EDM = g.H.g/2 < tol max(1, |F|) (also checked
+ * before the first iteration).  Capturable in a CUDA graph. */
+cg_status cg_fit_step(const cg_batch *b, const cg_tile_map *map, cg_fit_state *state, int n_steps,
+                      double tol, void *ws, size_t ws_bytes, void *stream);
 
-/* The same iteration for ONE histogram (the plain per-histogram path): each
- * trial point is one fused gradient launch on the full GPU followed by a
- * one-thread update kernel; no host synchronisation. state: device [1]. */
+/* The same iteration for ONE histogram on the full GPU (the plain
+ * per-histogram path): every trial point is one cg_gradient-style launch
+ * pair (tile kernel + finalize) followed by a one-warp control kernel; no
+ * host synchronisation.  Once the fit stops, later launches of the call
+ * return immediately.  state: device [1]. */
 size_t cg_fit_single_workspace_size(const cg_problem *pb);
 cg_status cg_fit_single_init(const cg_problem *pb, const double *theta0, cg_fit_state *state,
                              void *ws, size_t ws_bytes, void *stream);

@@ -75,8 +75,9 @@ def lib():
         "cg_set_profile_events": (None, [_vp, _vp]),
         "cg_fit_workspace_size": (_sz, [B]),
         "cg_fit_plan": (ctypes.c_int, [B, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_TileMap), _vp, _sz, _vp]),
-        "cg_fit_init": (ctypes.c_int, [B, _dp, _vp, _vp, _sz, _vp]),
-        "cg_fit_step": (ctypes.c_int, [B, _vp, ctypes.c_int, ctypes.c_double, _vp, _sz, _vp]),
+        "cg_fit_init": (ctypes.c_int, [B, ctypes.POINTER(_TileMap), _dp, _vp, _vp, _sz, _vp]),
+        "cg_fit_step": (ctypes.c_int, [B, ctypes.POINTER(_TileMap), _vp, ctypes.c_int, ctypes.c_double, _vp, _sz,
+                                       _vp]),
         "cg_fit_single_workspace_size": (_sz, [P]),
         "cg_fit_single_init": (ctypes.c_int, [P, _dp, _vp, _vp, _sz, _vp]),
         "cg_fit_single_step": (ctypes.c_int, [P, _vp, ctypes.c_int, ctypes.c_double, _vp, _sz, _vp]),

@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(NT, 3) k_mix_df64(MixData d, const double* __r
     __shared__ double tot[NACC];
     __shared__ double ssum[NACC * NT];
     static_assert(NT == 256, "fallback sums use a stride of 256");
+    if (gated_off(tg)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
     df_tables_init(tab);
     for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(NT, 3) k_mix_df64(MixData d, const double* __r
 bool df64_supported(const cg_problem* pb) { return pb->model == CG_MODEL_MIX_GAUSS_EXP; }
 
 cg_status launch_df64(const cg_problem* pb, const double* theta, int64_t n_theta, double* part, WsHeader* hdr,
-                      TileGrid* tg, cudaStream_t st) {
+                      TileGrid* tg, cudaStream_t st, const int* gate) {
     if (pb->model == CG_MODEL_MIX_GAUSS_EXP) {
         MixData d;
         d.x = pb->data;
@@ -158,8 +159,9 @@ cg_status launch_df64(const cg_problem* pb, const double* theta, int64_t n_theta
         d.hi = pb->hi[0];
         d.vec_ok = 0;
         constexpr int NT = 256;
-        if (pb->weights) return launch_tiles(k_mix_df64<true, NT>, NT, d, theta, pb->n_events, n_theta, part, hdr, tg, st);
-        return launch_tiles(k_mix_df64<false, NT>, NT, d, theta, pb->n_events, n_theta, part, hdr, tg, st);
+        if (pb->weights)
+            return launch_tiles(k_mix_df64<true, NT>, NT, d, theta, pb->n_events, n_theta, part, hdr, tg, st, gate);
+        return launch_tiles(k_mix_df64<false, NT>, NT, d, theta, pb->n_events, n_theta, part, hdr, tg, st, gate);
     }
     return CG_ERR_UNSUPPORTED;
 }

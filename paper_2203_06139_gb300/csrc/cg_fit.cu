@@ -1,11 +1,804 @@
 // cg_fit.cu -- histogram batches and the BFGS fitters of libcg.
+//
+// The paper uses AD gradients inside the histogram fitter, whose minimiser
+// takes the gradient from AD and no second derivatives (Sec. 4).  The
+// gradient-only minimiser here is BFGS with a backtracking Armijo line
+// search (steps in cg.h, cg_fit_step).  Every objective evaluation is the
+// fused forward + adjoint of cg_models.cuh over one histogram's bins.
+//
+// Batched fitter: ONE persistent launch fits thousands of histograms of
+// uneven size.  Three granularities share the launch, chosen per histogram
+// by the plan (cg_fit_plan): a cluster of CTAs (largest histograms; the
+// per-CTA partial sums are combined through distributed shared memory), one
+// CTA, or one warp (smallest).  Each granularity pops histograms from its
+// own size-sorted queue with an integer atomic; no unit ever waits for
+// another.  Inside a unit the data-parallel part (the bins) is spread over
+// all its threads and reduced in a fixed order; the control part (search
+// direction, line search, BFGS update) is done by one warp, lane i owning
+// row i of the inverse-Hessian approximation.  In a cluster every CTA runs
+// the control part on the same broadcast sums, so all CTAs take the same
+// branches and reach the same cluster barriers.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "cg_internal.cuh"
 #include "cg_models.cuh"
+#include "cg_tiles.cuh"
+
+namespace cgx = cooperative_groups;
 
 namespace cg {
 size_t grad_workspace_bytes(const cg_problem* pb, int64_t n_theta);
 cg_status grad_points(const cg_problem* pb, const double* theta, int64_t n_theta, double* value, double* grad,
-                      void* ws, size_t ws_bytes, cudaStream_t st);
+                      void* ws, size_t ws_bytes, cudaStream_t st, const int* gate);
+
+namespace {
+
+constexpr int FP = CG_FIT_MAX_PARAMS;
+constexpr int kMaxTrials = 20;
+constexpr double kArmijo = 1e-4;
+constexpr int kMaxWarpsPerCta = 16;
+
+enum { UNIT_WARP = 0, UNIT_CTA = 1, UNIT_CLUSTER = 2 };
+
+// Per-unit fit state in shared memory.
+struct FitSm {
+    double th[FP], g[FP], d[FP], tt[FP], gt[FP], h0[FP], sv[FP], yv[FP], hy[FP];
+    double H[FP * FP];
+    double f, ft, gd, alpha, edm;
+    int P, iter, n_eval, status, ntrial, go, upd, bad;
+};
+
+struct Geom {   // one histogram
+    const double* y;
+    int64_t n;
+    double lo, hw;
+};
+
+// Arguments of the fit kernels.
+struct FitArgs {
+    cg_fit_state* st;
+    const double* data;
+    const int64_t* offsets;
+    const double* lo;
+    const double* hi;
+    const double* theta;   // grad mode: [H][P]; init mode: theta0 [H][P]
+    double* value;         // grad mode
+    double* grad;          // grad mode
+    const int* queue[3];   // histogram ids per unit kind (cluster, cta, warp), sorted by size
+    const int* n_items;    // device [3]: queue lengths (written by the plan)
+    int* counters;         // 3 ints, zeroed before each persistent launch
+    int64_t H;
+    int P, D, pm, n_steps;
+    double tol;
+};
+
+__device__ __forceinline__ Geom geom_of(const FitArgs& a, int64_t h) {
+    Geom g;
+    const int64_t b0 = a.offsets[h], b1 = a.offsets[h + 1];
+    g.y = a.data + b0;
+    g.n = b1 - b0;
+    g.lo = a.lo[h];
+    g.hw = (a.hi[h] - a.lo[h]) / (double)(g.n > 0 ? g.n : 1);
+    return g;
+}
+
+// ---------------------------------------------------------------------------
+// Data-parallel part: accumulate one histogram's bins (thread t0 of T).
+// ---------------------------------------------------------------------------
+template <int K, int OBJ>
+__device__ __forceinline__ void acc_bins(const Geom& G, const GP1Consts& cs, const GP1Data& dd, int t0, int T,
+                                         double (&acc)[GP1Acc<K>::N], bool& bad) {
+    for (int64_t i = t0; i < G.n; i += T) {
+        const double x = fma((double)i + 0.5, G.hw, G.lo);
+        gp1_elem_fp64<K, OBJ>(x, __ldg(G.y + i), cs, dd, acc, bad);
+    }
+}
+
+// Gauss-Newton diagonal terms of one bin: h (df/dtheta_k)^2 with h = d2T/df2.
+template <int K, int OBJ>
+__device__ __forceinline__ void gn_bins(const Geom& G, const GP1Consts& cs, const GP1Data& dd, int t0, int T,
+                                        double (&acc)[GP1Acc<K>::N]) {
+    for (int64_t i = t0; i < G.n; i += T) {
+        const double x = fma((double)i + 0.5, G.hw, G.lo);
+        const double y = __ldg(G.y + i);
+        const double u = dd.pm ? fma(x, dd.au, dd.bu) : x;
+        double f = 0.0;
+#pragma unroll
+        for (int j = 3; j >= 0; --j)
+            if (j <= dd.D) f = fma(f, u, cs.poly[j]);
+        double dk[K], ek[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            dk[k] = x - cs.mu[k];
+            ek[k] = exp(cs.c[k] * dk[k] * dk[k]);
+            f = fma(cs.A[k], ek[k], f);
+        }
+        double h;
+        if (OBJ == CG_OBJ_CHI2) h = 2.0 / fmax(y, 1.0);
+        else if (OBJ == CG_OBJ_POISSON) h = y / (f * f);
+        else h = 2.0 * y / (f * f);
+        acc[0] += 0.0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const double he = h * ek[k] * ek[k];
+            const double d2 = dk[k] * dk[k];
+            acc[1 + 3 * k] += he;
+            acc[2 + 3 * k] = fma(he, d2, acc[2 + 3 * k]);
+            acc[3 + 3 * k] = fma(he * d2, d2, acc[3 + 3 * k]);
+        }
+        double up = 1.0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (j <= dd.D) acc[1 + 3 * K + j] = fma(h, up * up, acc[1 + 3 * K + j]);
+            up *= u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reductions of the accumulators over one unit; result in tot[] (shared).
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void reduce_warp(const double (&acc)[N], double* tot) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+        const double v = warp_sum(acc[a]);
+        if (lane == 0) tot[a] = v;
+    }
+    __syncwarp();
+}
+
+// red: shared [N][kMaxWarpsPerCta]
+template <int N>
+__device__ __forceinline__ void reduce_cta(const double (&acc)[N], double* red, double* tot) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+        const double v = warp_sum(acc[a]);
+        if (lane == 0) red[a * kMaxWarpsPerCta + wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < N) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += red[threadIdx.x * kMaxWarpsPerCta + w];
+        tot[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// CTA sums into `part`, then rank 0 adds the ranks' parts in rank order and
+// every rank copies the total.
+template <int N>
+__device__ __forceinline__ void reduce_cluster(const double (&acc)[N], double* red, double* part, double* tot) {
+    cgx::cluster_group cl = cgx::this_cluster();
+    reduce_cta<N>(acc, red, part);
+    cl.sync();
+    const unsigned nr = cl.num_blocks();
+    if (cl.block_rank() == 0 && threadIdx.x < N) {
+        double s = 0.0;
+        for (unsigned r = 0; r < nr; ++r) s += cl.map_shared_rank(part, r)[threadIdx.x];
+        tot[threadIdx.x] = s;
+    }
+    cl.sync();
+    if (cl.block_rank() != 0 && threadIdx.x < N) tot[threadIdx.x] = cl.map_shared_rank(tot, 0)[threadIdx.x];
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Control part, executed by one warp on the unit's FitSm.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ctl_direction(FitSm& s, int lane) {
+    const int P = s.P;
+    if (lane < P) {
+        double acc = 0.0;
+        for (int j = 0; j < P; ++j) acc = fma(s.H[lane * FP + j], s.g[j], acc);
+        s.d[lane] = -acc;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        double gd = 0.0;
+        for (int j = 0; j < P; ++j) gd = fma(s.g[j], s.d[j], gd);
+        s.gd = gd;
+        s.go = (gd < 0.0) ? 1 : 0;
+    }
+    __syncwarp();
+    if (!s.go) {  // not a descent direction: restart from the initial diagonal
+        if (lane < P) {
+            for (int j = 0; j < P; ++j) s.H[lane * FP + j] = (j == lane) ? s.h0[lane] : 0.0;
+            s.d[lane] = -s.h0[lane] * s.g[lane];
+        }
+        __syncwarp();
+        if (lane == 0) {
+            double gd = 0.0;
+            for (int j = 0; j < P; ++j) gd = fma(s.g[j], s.d[j], gd);
+            s.gd = gd;
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        s.alpha = 1.0;
+        s.ntrial = 0;
+    }
+    __syncwarp();
+    if (lane < P) s.tt[lane] = s.th[lane] + s.d[lane];
+    __syncwarp();
+}
+
+// After an evaluation at tt: go = 1 accepted (BFGS update done), 0 retry
+// with a new tt, 2 stop (line search failed).
+__device__ __forceinline__ void ctl_after_eval(FitSm& s, int lane, double tol) {
+    const int P = s.P;
+    if (lane == 0) {
+        s.n_eval += 1;
+        const double ft = s.bad ? __longlong_as_double(0x7ff0000000000000LL) : s.ft;
+        const bool ok = isfinite(ft) && ft <= s.f + kArmijo * s.alpha * s.gd;
+        if (ok) {
+            s.go = 1;
+        } else {
+            s.ntrial += 1;
+            if (s.ntrial >= kMaxTrials) {
+                s.go = 2;
+                s.status = CG_FIT_LINESEARCH_FAILED;
+            } else {
+                const double a = s.alpha;
+                double an;
+                if (isfinite(ft)) {
+                    const double den = 2.0 * (ft - s.f - s.gd * a);
+                    an = (den > 0.0) ? -s.gd * a * a / den : 0.5 * a;
+                    an = fmin(fmax(an, 0.1 * a), 0.5 * a);
+                } else {
+                    an = 0.1 * a;
+                }
+                s.alpha = an;
+                s.go = 0;
+            }
+        }
+    }
+    __syncwarp();
+    if (s.go == 0) {
+        if (lane < P) s.tt[lane] = fma(s.alpha, s.d[lane], s.th[lane]);
+        __syncwarp();
+        return;
+    }
+    if (s.go == 2) return;
+    // accepted: BFGS update with step sv and gradient change yv
+    if (lane < P) {
+        s.sv[lane] = s.tt[lane] - s.th[lane];
+        s.yv[lane] = s.gt[lane] - s.g[lane];
+    }
+    __syncwarp();
+    if (lane < P) {
+        double acc = 0.0;
+        for (int j = 0; j < P; ++j) acc = fma(s.H[lane * FP + j], s.yv[j], acc);
+        s.hy[lane] = acc;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        double sy = 0.0, yhy = 0.0, ss = 0.0, yy = 0.0;
+        for (int j = 0; j < P; ++j) {
+            sy = fma(s.sv[j], s.yv[j], sy);
+            yhy = fma(s.yv[j], s.hy[j], yhy);
+            ss = fma(s.sv[j], s.sv[j], ss);
+            yy = fma(s.yv[j], s.yv[j], yy);
+        }
+        s.upd = (sy > 1e-12 * sqrt(ss) * sqrt(yy)) ? 1 : 0;
+        s.gd = sy;      // reuse: s.y
+        s.alpha = yhy;  // reuse: y.H.y
+    }
+    __syncwarp();
+    if (s.upd && lane < P) {
+        const double r = 1.0 / s.gd;
+        const double c = (1.0 + r * s.alpha) * r;
+        for (int j = 0; j < P; ++j)
+            s.H[lane * FP + j] += -r * (s.sv[lane] * s.hy[j] + s.hy[lane] * s.sv[j]) + c * s.sv[lane] * s.sv[j];
+    }
+    __syncwarp();
+    if (lane < P) {
+        s.th[lane] = s.tt[lane];
+        s.g[lane] = s.gt[lane];
+    }
+    __syncwarp();
+    // EDM with the updated approximation
+    if (lane < P) {
+        double acc = 0.0;
+        for (int j = 0; j < P; ++j) acc = fma(s.H[lane * FP + j], s.g[j], acc);
+        s.hy[lane] = acc;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        s.f = s.ft;
+        s.iter += 1;
+        double e = 0.0;
+        for (int j = 0; j < P; ++j) e = fma(s.g[j], s.hy[j], e);
+        s.edm = 0.5 * e;
+        if (s.edm < tol * fmax(1.0, fabs(s.f))) s.status = CG_FIT_CONVERGED;
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// One objective evaluation of histogram G at s.tt by a unit (all threads).
+// ---------------------------------------------------------------------------
+template <int UNIT, int K, int OBJ>
+__device__ __forceinline__ void unit_eval(FitSm& s, GP1Consts& cs, const Geom& G, const GP1Data& dd, int D,
+                                          double* red, double* part, double* tot, int t0, int T) {
+    constexpr int N = GP1Acc<K>::N;
+    const int lane = threadIdx.x & 31;
+    const bool leader = (UNIT == UNIT_WARP) ? (lane == 0) : (threadIdx.x == 0);
+    if (leader) s.bad = gp1_prologue<K>(s.tt, D, cs) ? 0 : 1;
+    if (UNIT == UNIT_WARP) __syncwarp(); else __syncthreads();
+    double acc[N];
+#pragma unroll
+    for (int a = 0; a < N; ++a) acc[a] = 0.0;
+    bool bad = false;
+    acc_bins<K, OBJ>(G, cs, dd, t0, T, acc, bad);
+    int any_bad;
+    if (UNIT == UNIT_WARP) {
+        any_bad = __any_sync(0xffffffffu, bad);
+        reduce_warp<N>(acc, tot);
+    } else if (UNIT == UNIT_CTA) {
+        any_bad = __syncthreads_or(bad);
+        reduce_cta<N>(acc, red, tot);
+    } else {
+        // the flag travels as one more accumulator through the cluster sum
+        double acc2[N + 1];
+#pragma unroll
+        for (int a = 0; a < N; ++a) acc2[a] = acc[a];
+        acc2[N] = bad ? 1.0 : 0.0;
+        reduce_cluster<N + 1>(acc2, red, part, tot);
+        any_bad = tot[N] != 0.0;
+    }
+    if (leader) {
+        EpiParams ep;
+        ep.model = CG_MODEL_GAUSS_POLY;
+        ep.K = K;
+        ep.D = D;
+        ep.P = s.P;
+        ep.lo = ep.hi = 0.0;
+        double g[kMaxParams];
+        s.ft = epilogue(ep, s.tt, tot, g);
+        for (int k = 0; k < s.P; ++k) s.gt[k] = g[k];
+        s.bad |= any_bad ? 1 : 0;
+    }
+    if (UNIT == UNIT_WARP) __syncwarp(); else __syncthreads();
+}
+
+// Load / store the per-histogram state.
+__device__ __forceinline__ void state_load(FitSm& s, const cg_fit_state* st, int lane_or_tid, int nthr) {
+    for (int k = lane_or_tid; k < FP; k += nthr) {
+        s.th[k] = st->theta[k];
+        s.g[k] = st->grad[k];
+        s.h0[k] = st->h0[k];
+    }
+    for (int k = lane_or_tid; k < FP * FP; k += nthr) s.H[k] = st->hinv[k];
+    if (lane_or_tid == 0) {
+        s.f = st->f;
+        s.edm = st->edm;
+        s.iter = st->iter;
+        s.n_eval = st->n_eval;
+        s.status = st->status;
+        s.P = st->n_params;
+    }
+}
+
+__device__ __forceinline__ void state_store(const FitSm& s, cg_fit_state* st, int lane_or_tid, int nthr) {
+    for (int k = lane_or_tid; k < FP; k += nthr) {
+        st->theta[k] = s.th[k];
+        st->grad[k] = s.g[k];
+    }
+    for (int k = lane_or_tid; k < FP * FP; k += nthr) st->hinv[k] = s.H[k];
+    if (lane_or_tid == 0) {
+        st->f = s.f;
+        st->edm = s.edm;
+        st->iter = s.iter;
+        st->n_eval = s.n_eval;
+        st->status = s.status;
+    }
+}
+
+// Fit one histogram with one unit for up to a.n_steps iterations.
+template <int UNIT, int K, int OBJ>
+__device__ void unit_fit(const FitArgs& a, int64_t h, FitSm& s, GP1Consts& cs, double* red, double* part,
+                         double* tot, int t0, int T) {
+    const int lane = threadIdx.x & 31;
+    const bool ctl = (UNIT == UNIT_WARP) || (threadIdx.x < 32);
+    const int ld_id = (UNIT == UNIT_WARP) ? lane : threadIdx.x;
+    const int ld_n = (UNIT == UNIT_WARP) ? 32 : blockDim.x;
+    state_load(s, a.st + h, ld_id, ld_n);
+    if (UNIT == UNIT_WARP) __syncwarp(); else __syncthreads();
+    const Geom G = geom_of(a, h);
+    GP1Data dd;
+    dd.y = G.y;
+    dd.centres = nullptr;
+    dd.lo = G.lo;
+    dd.h = G.hw;
+    dd.au = 2.0 / (a.hi[h] - a.lo[h]);
+    dd.bu = -(a.lo[h] + a.hi[h]) / (a.hi[h] - a.lo[h]);
+    dd.D = a.D;
+    dd.pm = a.pm;
+    dd.vec_ok = 0;
+    if (ctl && lane == 0 && s.status == CG_FIT_RUNNING && s.edm < a.tol * fmax(1.0, fabs(s.f)))
+        s.status = CG_FIT_CONVERGED;
+    if (UNIT == UNIT_WARP) __syncwarp(); else __syncthreads();
+    const int it_end = s.iter + a.n_steps;
+    while (s.status == CG_FIT_RUNNING && s.iter < it_end) {
+        if (ctl) ctl_direction(s, lane);
+        if (UNIT != UNIT_WARP) __syncthreads();
+        for (;;) {
+            unit_eval<UNIT, K, OBJ>(s, cs, G, dd, a.D, red, part, tot, t0, T);
+            if (ctl) ctl_after_eval(s, lane, a.tol);
+            if (UNIT == UNIT_WARP) __syncwarp(); else __syncthreads();
+            if (s.go != 0) break;
+        }
+        if (UNIT == UNIT_WARP) __syncwarp(); else __syncthreads();
+    }
+    const bool writer = (UNIT != UNIT_CLUSTER) || cgx::this_cluster().block_rank() == 0;
+    if (writer) state_store(s, a.st + h, ld_id, ld_n);
+    if (UNIT == UNIT_WARP) __syncwarp(); else __syncthreads();
+}
+
+// Shared-memory layout of the persistent kernel (dynamic).
+struct SmLayout {
+    size_t cta_sm, warp_sm, cta_cs, warp_cs, red, part, tot, warp_tot, item, total;
+};
+
+__host__ __device__ inline SmLayout sm_layout(int nwarps, int nacc) {
+    SmLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o += (bytes + 15) / 16 * 16; return r; };
+    L.cta_sm = take(sizeof(FitSm));
+    L.warp_sm = take(sizeof(FitSm) * nwarps);
+    L.cta_cs = take(sizeof(GP1Consts));
+    L.warp_cs = take(sizeof(GP1Consts) * nwarps);
+    L.red = take(sizeof(double) * (nacc + 1) * kMaxWarpsPerCta);
+    L.part = take(sizeof(double) * (nacc + 1));
+    L.tot = take(sizeof(double) * (nacc + 1));
+    L.warp_tot = take(sizeof(double) * (nacc + 1) * nwarps);
+    L.item = take(16);
+    L.total = o;
+    return L;
+}
+
+// Persistent batched fit: clusters, then CTAs, then warps pop histograms.
+template <int K, int OBJ, bool CLUSTERS>
+__global__ void __launch_bounds__(512) k_fit_persistent(FitArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int N = GP1Acc<K>::N;
+    const int nw = blockDim.x >> 5;
+    const SmLayout L = sm_layout(nw, N);
+    FitSm& cta_s = *reinterpret_cast<FitSm*>(smem + L.cta_sm);
+    GP1Consts& cta_cs = *reinterpret_cast<GP1Consts*>(smem + L.cta_cs);
+    double* red = reinterpret_cast<double*>(smem + L.red);
+    double* part = reinterpret_cast<double*>(smem + L.part);
+    double* tot = reinterpret_cast<double*>(smem + L.tot);
+    int* item = reinterpret_cast<int*>(smem + L.item);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    const int n0 = a.n_items[0], n1 = a.n_items[1], n2 = a.n_items[2];
+    if (CLUSTERS) {
+        cgx::cluster_group cl = cgx::this_cluster();
+        const int rank = (int)cl.block_rank();
+        const int csz = (int)cl.num_blocks();
+        for (;;) {
+            if (rank == 0 && threadIdx.x == 0) *item = atomicAdd(&a.counters[0], 1);
+            cl.sync();
+            const int it = *cl.map_shared_rank(item, 0);
+            cl.sync();
+            if (it >= n0) break;
+            unit_fit<UNIT_CLUSTER, K, OBJ>(a, a.queue[0][it], cta_s, cta_cs, red, part, tot,
+                                           rank * blockDim.x + threadIdx.x, csz * blockDim.x);
+        }
+    }
+    for (;;) {
+        if (threadIdx.x == 0) *item = atomicAdd(&a.counters[1], 1);
+        __syncthreads();
+        const int it = *item;
+        __syncthreads();
+        if (it >= n1) break;
+        unit_fit<UNIT_CTA, K, OBJ>(a, a.queue[1][it], cta_s, cta_cs, red, part, tot, threadIdx.x, blockDim.x);
+    }
+    FitSm& ws_ = reinterpret_cast<FitSm*>(smem + L.warp_sm)[wid];
+    GP1Consts& wcs = reinterpret_cast<GP1Consts*>(smem + L.warp_cs)[wid];
+    double* wtot = reinterpret_cast<double*>(smem + L.warp_tot) + wid * (N + 1);
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(&a.counters[2], 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n2) break;
+        unit_fit<UNIT_WARP, K, OBJ>(a, a.queue[2][it], ws_, wcs, nullptr, nullptr, wtot, lane, 32);
+    }
+}
+
+// Init (GN + first evaluation) and plain evaluation: one CTA per histogram,
+// grid-stride over histograms.  mode 0: value/grad at a.theta; mode 1: init.
+template <int K, int OBJ>
+__global__ void __launch_bounds__(256) k_fit_eval(FitArgs a, int mode) {
+    constexpr int N = GP1Acc<K>::N;
+    __shared__ GP1Consts cs;
+    __shared__ int cs_bad;
+    __shared__ double red[(N + 1) * kMaxWarpsPerCta];
+    __shared__ double tot[N + 1];
+    __shared__ double gn[N + 1];
+    for (int64_t h = blockIdx.x; h < a.H; h += gridDim.x) {
+        const double* th = a.theta + h * a.P;
+        const Geom G = geom_of(a, h);
+        GP1Data dd;
+        dd.y = G.y;
+        dd.centres = nullptr;
+        dd.lo = G.lo;
+        dd.h = G.hw;
+        dd.au = 2.0 / (a.hi[h] - a.lo[h]);
+        dd.bu = -(a.lo[h] + a.hi[h]) / (a.hi[h] - a.lo[h]);
+        dd.D = a.D;
+        dd.pm = a.pm;
+        dd.vec_ok = 0;
+        if (threadIdx.x == 0) cs_bad = gp1_prologue<K>(th, a.D, cs) ? 0 : 1;
+        __syncthreads();
+        double acc[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) acc[i] = 0.0;
+        bool bad = false;
+        acc_bins<K, OBJ>(G, cs, dd, threadIdx.x, blockDim.x, acc, bad);
+        const int any_bad = __syncthreads_or(bad) | cs_bad;
+        reduce_cta<N>(acc, red, tot);
+        if (mode == 1) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) acc[i] = 0.0;
+            gn_bins<K, OBJ>(G, cs, dd, threadIdx.x, blockDim.x, acc);
+            reduce_cta<N>(acc, red, gn);
+        }
+        if (threadIdx.x == 0) {
+            EpiParams ep;
+            ep.model = CG_MODEL_GAUSS_POLY;
+            ep.K = K;
+            ep.D = a.D;
+            ep.P = a.P;
+            ep.lo = ep.hi = 0.0;
+            double g[kMaxParams];
+            const double v = epilogue(ep, th, tot, g);
+            if (mode == 0) {
+                a.value[h] = v;
+                for (int k = 0; k < a.P; ++k) a.grad[h * a.P + k] = g[k];
+                if (any_bad) a.value[h] = __longlong_as_double(0x7ff8000000000000LL);
+            } else {
+                cg_fit_state* st = a.st + h;
+                // GN diagonal from its accumulators
+                double gd[FP];
+                for (int k = 0; k < K; ++k) {
+                    const double A = th[3 * k], s = th[3 * k + 2];
+                    gd[3 * k] = gn[1 + 3 * k];
+                    gd[3 * k + 1] = (A / (s * s)) * (A / (s * s)) * gn[2 + 3 * k];
+                    gd[3 * k + 2] = (A / (s * s * s)) * (A / (s * s * s)) * gn[3 + 3 * k];
+                }
+                for (int j = 0; j <= a.D; ++j) gd[3 * K + j] = gn[1 + 3 * K + j];
+                double edm = 0.0;
+                for (int k = 0; k < FP; ++k) {
+                    const bool in = k < a.P;
+                    const double h0 = in ? ((gd[k] > 0.0) ? 1.0 / gd[k] : 1.0) : 0.0;
+                    st->theta[k] = in ? th[k] : 0.0;
+                    st->grad[k] = in ? g[k] : 0.0;
+                    st->h0[k] = h0;
+                    for (int j = 0; j < FP; ++j) st->hinv[k * FP + j] = (j == k) ? h0 : 0.0;
+                    if (in) edm = fma(g[k] * h0, g[k], edm);
+                }
+                st->f = v;
+                st->edm = 0.5 * edm;
+                st->iter = 0;
+                st->n_eval = 1;
+                st->n_params = a.P;
+                st->status = (any_bad || !isfinite(v)) ? CG_FIT_DOMAIN : CG_FIT_RUNNING;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Plain per-histogram path: control kernel around full-GPU evaluations.
+// ---------------------------------------------------------------------------
+struct SingleWs {        // lives in the workspace
+    FitSm s;
+    double ft;           // written by the gradient launch
+    double gt[FP];
+    int need_eval;       // gate of the gradient launch
+    int pending;         // an evaluation at s.tt has been requested
+    int fresh;           // set by init: load the fit state on the next control step
+    int64_t offsets[2];
+    double lo, hi;
+};
+
+// One warp: consume the pending evaluation (if any), then request the next one.
+__global__ void k_single_ctl(SingleWs* w, cg_fit_state* st, double tol) {
+    __shared__ FitSm s;
+    const int lane = threadIdx.x;
+    const int fresh = w->fresh;
+    const int pending = fresh ? 0 : w->pending;
+    if (fresh) {
+        state_load(s, st, lane, 32);
+        __syncwarp();
+        if (lane == 0 && s.status == CG_FIT_RUNNING && s.edm < tol * fmax(1.0, fabs(s.f)))
+            s.status = CG_FIT_CONVERGED;
+    } else {
+        const double* src = reinterpret_cast<const double*>(&w->s);
+        double* dst = reinterpret_cast<double*>(&s);
+        for (int k = lane; k < (int)(sizeof(FitSm) / sizeof(double)); k += 32) dst[k] = src[k];
+    }
+    __syncwarp();
+    bool need_dir = true;
+    if (pending && s.status == CG_FIT_RUNNING) {
+        if (lane < s.P) s.gt[lane] = w->gt[lane];
+        if (lane == 0) {
+            s.ft = w->ft;
+            s.bad = !isfinite(w->ft);
+        }
+        __syncwarp();
+        ctl_after_eval(s, lane, tol);
+        need_dir = (s.go != 0);
+    }
+    __syncwarp();
+    if (need_dir && s.status == CG_FIT_RUNNING) ctl_direction(s, lane);
+    __syncwarp();
+    if (lane == 0) {
+        w->fresh = 0;
+        w->pending = (s.status == CG_FIT_RUNNING) ? 1 : 0;
+        w->need_eval = w->pending;
+    }
+    const double* src = reinterpret_cast<const double*>(&s);
+    double* dst = reinterpret_cast<double*>(&w->s);
+    for (int k = lane; k < (int)(sizeof(FitSm) / sizeof(double)); k += 32) dst[k] = src[k];
+    state_store(s, st, lane, 32);
+}
+
+__global__ void k_single_setup(SingleWs* w, int64_t n, double lo, double hi) {
+    w->offsets[0] = 0;
+    w->offsets[1] = n;
+    w->lo = lo;
+    w->hi = hi;
+    w->pending = 0;
+    w->need_eval = 0;
+    w->fresh = 1;
+}
+
+// ---------------------------------------------------------------------------
+// Host helpers
+// ---------------------------------------------------------------------------
+struct FitWsLayout {
+    size_t hdr, counters, qmeta, queues, total;
+};
+
+FitWsLayout fit_ws_layout(int64_t H) {
+    FitWsLayout L;
+    L.hdr = 0;
+    L.counters = 256;
+    L.qmeta = 512;
+    L.queues = 768;
+    L.total = L.queues + align_up((size_t)3 * H * sizeof(int), 256);
+    return L;
+}
+
+bool fit_supported(const cg_problem* t) {
+    return t->model == CG_MODEL_GAUSS_POLY && t->n_peaks >= 1 && t->n_peaks <= 3 && t->poly_degree >= -1 &&
+           t->poly_degree <= 3 && 3 * t->n_peaks + t->poly_degree + 1 <= FP &&
+           (t->objective == CG_OBJ_CHI2 || t->objective == CG_OBJ_POISSON || t->objective == CG_OBJ_POISSON_BC);
+}
+
+bool map_ok(const cg_tile_map* m) {
+    return m && m->cta_threads >= 64 && m->cta_threads <= 512 && (m->cta_threads % 32) == 0 &&
+           (m->cluster_size == 1 || m->cluster_size == 2 || m->cluster_size == 4 || m->cluster_size == 8) &&
+           m->warp_max_bins >= 0 && m->cta_max_bins >= m->warp_max_bins;
+}
+
+FitArgs base_args(const cg_batch* b) {
+    FitArgs a;
+    memset(&a, 0, sizeof(a));
+    a.data = b->tmpl.data;
+    a.offsets = b->offsets;
+    a.lo = b->lo;
+    a.hi = b->hi;
+    a.H = b->n_hist;
+    a.D = b->tmpl.poly_degree;
+    a.pm = b->tmpl.poly_mode;
+    a.P = 3 * b->tmpl.n_peaks + b->tmpl.poly_degree + 1;
+    return a;
+}
+
+template <int K, int OBJ>
+cg_status launch_eval_k(const FitArgs& a, int mode, cudaStream_t st) {
+    const int G = device_sm_count() * 4;
+    const int grid = (int)(a.H < G ? a.H : G);
+    k_fit_eval<K, OBJ><<<grid, 256, 0, st>>>(a, mode);
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
+
+cg_status launch_eval(const cg_problem* t, const FitArgs& a, int mode, cudaStream_t st) {
+    const int K = t->n_peaks, O = t->objective;
+#define CG_EVAL_CASE(KK, OO) if (K == KK && O == OO) return launch_eval_k<KK, OO>(a, mode, st);
+    CG_EVAL_CASE(1, CG_OBJ_CHI2) CG_EVAL_CASE(1, CG_OBJ_POISSON) CG_EVAL_CASE(1, CG_OBJ_POISSON_BC)
+    CG_EVAL_CASE(2, CG_OBJ_CHI2) CG_EVAL_CASE(2, CG_OBJ_POISSON) CG_EVAL_CASE(2, CG_OBJ_POISSON_BC)
+    CG_EVAL_CASE(3, CG_OBJ_CHI2) CG_EVAL_CASE(3, CG_OBJ_POISSON) CG_EVAL_CASE(3, CG_OBJ_POISSON_BC)
+#undef CG_EVAL_CASE
+    return CG_ERR_UNSUPPORTED;
+}
+
+template <int K, int OBJ, bool CL>
+cg_status launch_persistent_k(const FitArgs& a, const cg_tile_map* m, cudaStream_t st) {
+    constexpr int N = GP1Acc<K>::N;
+    const int nt = m->cta_threads;
+    const SmLayout L = sm_layout(nt / 32, N);
+    auto kern = k_fit_persistent<K, OBJ, CL>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) != cudaSuccess)
+        return CG_ERR_CUDA;
+    const int csz = CL ? m->cluster_size : 1;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.blockDim = dim3(nt);
+    cfg.dynamicSmemBytes = L.total;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    int nattr = 0;
+    if (CL) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = csz;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        nattr = 1;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = nattr;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, L.total) != cudaSuccess || per_sm < 1)
+        return CG_ERR_UNSUPPORTED;
+    int grid = device_sm_count() * per_sm;
+    if (CL) {
+        cfg.gridDim = dim3(csz);
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) != cudaSuccess || ncl < 1) return CG_ERR_UNSUPPORTED;
+        grid = ncl * csz;
+    }
+    cfg.gridDim = dim3(grid);
+    prof_begin(st);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a);
+    prof_end(st);
+    return e == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
+
+cg_status launch_persistent(const cg_problem* t, const FitArgs& a, const cg_tile_map* m, cudaStream_t st) {
+    const int K = t->n_peaks, O = t->objective;
+    const bool CL = m->cluster_size > 1;
+#define CG_P_CASE(KK, OO)                                                             \
+    if (K == KK && O == OO)                                                           \
+        return CL ? launch_persistent_k<KK, OO, true>(a, m, st) : launch_persistent_k<KK, OO, false>(a, m, st);
+    CG_P_CASE(1, CG_OBJ_CHI2) CG_P_CASE(1, CG_OBJ_POISSON) CG_P_CASE(1, CG_OBJ_POISSON_BC)
+    CG_P_CASE(2, CG_OBJ_CHI2) CG_P_CASE(2, CG_OBJ_POISSON) CG_P_CASE(2, CG_OBJ_POISSON_BC)
+    CG_P_CASE(3, CG_OBJ_CHI2) CG_P_CASE(3, CG_OBJ_POISSON) CG_P_CASE(3, CG_OBJ_POISSON_BC)
+#undef CG_P_CASE
+    return CG_ERR_UNSUPPORTED;
+}
+
+struct QueueMeta {
+    int n_items[3];
+    int cluster_size;
+};
+static_assert(sizeof(FitSm) % sizeof(double) == 0, "FitSm is copied as doubles");
+
+cg_status batch_checks(const cg_batch* b, void* ws, size_t ws_bytes) {
+    if (!b || b->n_hist < 1 || !b->offsets || !b->lo || !b->hi || !b->tmpl.data) return CG_ERR_INVALID_ARG;
+    if (b->n_hist > (int64_t)1 << 30) return CG_ERR_INVALID_ARG;
+    if (!fit_supported(&b->tmpl)) return CG_ERR_UNSUPPORTED;
+    if (b->tmpl.precision != CG_PREC_FP64 && b->tmpl.precision != CG_PREC_DF64) return CG_ERR_INVALID_ARG;
+    if (!ws || ((uintptr_t)ws & 255) || ws_bytes < fit_ws_layout(b->n_hist).total) return CG_ERR_WORKSPACE;
+    return CG_OK;
+}
+
+}  // namespace
 }  // namespace cg
 
 using namespace cg;
@@ -15,22 +808,151 @@ extern "C" {
 size_t cg_batch_workspace_size(const cg_batch* b) {
     if (!b || b->n_hist < 1) return 0;
     if (!b->offsets) return grad_workspace_bytes(&b->tmpl, b->n_hist);
-    return 0;
+    if (!fit_supported(&b->tmpl)) return 0;
+    return 256;
 }
 
 cg_status cg_batch_gradient(const cg_batch* b, const double* theta, double* value, double* grad, void* ws,
                             size_t ws_bytes, void* stream) {
     if (!b || b->n_hist < 1) return CG_ERR_INVALID_ARG;
-    if (!b->offsets) return grad_points(&b->tmpl, theta, b->n_hist, value, grad, ws, ws_bytes, (cudaStream_t)stream);
-    return CG_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!b->offsets) return grad_points(&b->tmpl, theta, b->n_hist, value, grad, ws, ws_bytes, st, nullptr);
+    if (!theta || !value || !grad || !b->lo || !b->hi || !b->tmpl.data) return CG_ERR_INVALID_ARG;
+    if (!fit_supported(&b->tmpl)) return CG_ERR_UNSUPPORTED;
+    if (!ws || ((uintptr_t)ws & 255) || ws_bytes < 256) return CG_ERR_WORKSPACE;
+    FitArgs a = base_args(b);
+    a.theta = theta;
+    a.value = value;
+    a.grad = grad;
+    return launch_eval(&b->tmpl, a, 0, st);
 }
 
-size_t cg_fit_workspace_size(const cg_batch*) { return 0; }
-cg_status cg_fit_plan(const cg_batch*, const int64_t*, const cg_tile_map*, void*, size_t, void*) { return CG_ERR_UNSUPPORTED; }
-cg_status cg_fit_init(const cg_batch*, const double*, cg_fit_state*, void*, size_t, void*) { return CG_ERR_UNSUPPORTED; }
-cg_status cg_fit_step(const cg_batch*, cg_fit_state*, int, double, void*, size_t, void*) { return CG_ERR_UNSUPPORTED; }
-size_t cg_fit_single_workspace_size(const cg_problem*) { return 0; }
-cg_status cg_fit_single_init(const cg_problem*, const double*, cg_fit_state*, void*, size_t, void*) { return CG_ERR_UNSUPPORTED; }
-cg_status cg_fit_single_step(const cg_problem*, cg_fit_state*, int, double, void*, size_t, void*) { return CG_ERR_UNSUPPORTED; }
+size_t cg_fit_workspace_size(const cg_batch* b) {
+    if (!b || b->n_hist < 1 || !b->offsets || !fit_supported(&b->tmpl)) return 0;
+    return fit_ws_layout(b->n_hist).total;
+}
+
+cg_status cg_fit_plan(const cg_batch* b, const int64_t* host_offsets, const cg_tile_map* map, void* ws,
+                      size_t ws_bytes, void* stream) {
+    cg_status s = batch_checks(b, ws, ws_bytes);
+    if (s != CG_OK) return s;
+    if (!host_offsets || !map_ok(map)) return CG_ERR_INVALID_ARG;
+    const int64_t H = b->n_hist;
+    std::vector<std::pair<int64_t, int>> by_size((size_t)H);
+    for (int64_t h = 0; h < H; ++h) {
+        const int64_t n = host_offsets[h + 1] - host_offsets[h];
+        if (n < 0) return CG_ERR_INVALID_ARG;
+        by_size[(size_t)h] = {n, (int)h};
+    }
+    std::stable_sort(by_size.begin(), by_size.end(),
+                     [](const std::pair<int64_t, int>& x, const std::pair<int64_t, int>& y) { return x.first > y.first; });
+    std::vector<int> q[3];
+    for (auto& e : by_size) {
+        int kind;
+        if (e.first > map->cta_max_bins && map->cluster_size > 1) kind = 0;
+        else if (e.first > map->warp_max_bins) kind = 1;
+        else kind = 2;
+        q[kind].push_back(e.second);
+    }
+    const FitWsLayout L = fit_ws_layout(H);
+    std::vector<int> flat((size_t)3 * H, 0);
+    for (int k = 0; k < 3; ++k) std::copy(q[k].begin(), q[k].end(), flat.begin() + (size_t)k * H);
+    QueueMeta meta;
+    for (int k = 0; k < 3; ++k) meta.n_items[k] = (int)q[k].size();
+    meta.cluster_size = map->cluster_size;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* base = (char*)ws;
+    if (cudaMemcpyAsync(base + L.queues, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(base + L.qmeta, &meta, sizeof(meta), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(base, 0, 512, st) != cudaSuccess)
+        return CG_ERR_CUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
+
+cg_status cg_fit_init(const cg_batch* b, const cg_tile_map* map, const double* theta0, cg_fit_state* state,
+                      void* ws, size_t ws_bytes, void* stream) {
+    cg_status s = batch_checks(b, ws, ws_bytes);
+    if (s != CG_OK) return s;
+    if (!theta0 || !state || !map_ok(map)) return CG_ERR_INVALID_ARG;
+    FitArgs a = base_args(b);
+    a.theta = theta0;
+    a.st = state;
+    return launch_eval(&b->tmpl, a, 1, (cudaStream_t)stream);
+}
+
+cg_status cg_fit_step(const cg_batch* b, const cg_tile_map* map, cg_fit_state* state, int n_steps, double tol,
+                      void* ws, size_t ws_bytes, void* stream) {
+    cg_status s = batch_checks(b, ws, ws_bytes);
+    if (s != CG_OK) return s;
+    if (!state || !map_ok(map) || n_steps < 0 || !(tol >= 0.0)) return CG_ERR_INVALID_ARG;
+    if (n_steps == 0) return CG_OK;
+    const FitWsLayout L = fit_ws_layout(b->n_hist);
+    char* base = (char*)ws;
+    FitArgs a = base_args(b);
+    a.st = state;
+    a.n_steps = n_steps;
+    a.tol = tol;
+    a.counters = (int*)(base + L.counters);
+    a.n_items = (const int*)(base + L.qmeta);
+    for (int k = 0; k < 3; ++k) a.queue[k] = (const int*)(base + L.queues) + (size_t)k * b->n_hist;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(a.counters, 0, 16, st) != cudaSuccess) return CG_ERR_CUDA;
+    return launch_persistent(&b->tmpl, a, map, st);
+}
+
+// ---- plain per-histogram path ----------------------------------------------
+size_t cg_fit_single_workspace_size(const cg_problem* pb) {
+    if (!pb || !fit_supported(pb)) return 0;
+    const size_t g = grad_workspace_bytes(pb, 1);
+    if (g == 0) return 0;
+    return g + align_up(sizeof(SingleWs), 256);
+}
+
+static cg_status single_checks(const cg_problem* pb, void* ws, size_t ws_bytes) {
+    if (!pb || !fit_supported(pb) || pb->centres || pb->n_bins[0] < 1 || !pb->data) return CG_ERR_INVALID_ARG;
+    if (!ws || ((uintptr_t)ws & 255) || ws_bytes < cg_fit_single_workspace_size(pb)) return CG_ERR_WORKSPACE;
+    return CG_OK;
+}
+
+cg_status cg_fit_single_init(const cg_problem* pb, const double* theta0, cg_fit_state* state, void* ws,
+                             size_t ws_bytes, void* stream) {
+    cg_status s = single_checks(pb, ws, ws_bytes);
+    if (s != CG_OK) return s;
+    if (!theta0 || !state) return CG_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    SingleWs* w = (SingleWs*)((char*)ws + grad_workspace_bytes(pb, 1));
+    k_single_setup<<<1, 1, 0, st>>>(w, pb->n_bins[0], pb->lo[0], pb->hi[0]);
+    FitArgs a;
+    memset(&a, 0, sizeof(a));
+    a.data = pb->data;
+    a.offsets = w->offsets;
+    a.lo = &w->lo;
+    a.hi = &w->hi;
+    a.H = 1;
+    a.D = pb->poly_degree;
+    a.pm = pb->poly_mode;
+    a.P = 3 * pb->n_peaks + pb->poly_degree + 1;
+    a.theta = theta0;
+    a.st = state;
+    return launch_eval(pb, a, 1, st);
+}
+
+cg_status cg_fit_single_step(const cg_problem* pb, cg_fit_state* state, int n_evals, double tol, void* ws,
+                             size_t ws_bytes, void* stream) {
+    cg_status s = single_checks(pb, ws, ws_bytes);
+    if (s != CG_OK) return s;
+    if (!state || n_evals < 0 || !(tol >= 0.0)) return CG_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t gbytes = grad_workspace_bytes(pb, 1);
+    SingleWs* w = (SingleWs*)((char*)ws + gbytes);
+    for (int e = 0; e < n_evals; ++e) {
+        k_single_ctl<<<1, 32, 0, st>>>(w, state, tol);
+        s = grad_points(pb, w->s.tt, 1, &w->ft, w->gt, ws, gbytes, st, &w->need_eval);
+        if (s != CG_OK) return s;
+    }
+    if (n_evals > 0) k_single_ctl<<<1, 32, 0, st>>>(w, state, tol);
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
 
 }  // extern "C"

@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(NT) k_gp1_fp64(GP1Data d, const double* __rest
     __shared__ int cs_bad;
     __shared__ double red[NACC * (NT / 32)];
     __shared__ double tot[NACC];
+    if (gated_off(tg)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
     const int P = 3 * K + d.D + 1;
     for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
@@ -105,6 +106,7 @@ __global__ void __launch_bounds__(NT) k_mix_fp64(MixData d, const double* __rest
     __shared__ int cs_bad;
     __shared__ double red[NACC * (NT / 32)];
     __shared__ double tot[NACC];
+    if (gated_off(tg)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
     for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
         const int th = t / tg.nbx, c = t - th * tg.nbx;
@@ -147,6 +149,7 @@ __global__ void __launch_bounds__(NT) k_rg2_fp64(RG2Data d, const double* __rest
     __shared__ int cs_bad;
     __shared__ double red[NACC * (NT / 32)];
     __shared__ double tot[NACC];
+    if (gated_off(tg)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
     const int P = 6 * K + 1;
     for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
@@ -188,6 +191,7 @@ __global__ void __launch_bounds__(NT) k_finalize(const double* __restrict__ part
                                                  WsHeader* __restrict__ hdr) {
     __shared__ double tot[kMaxAcc + 1];
     __shared__ double red[NT / 32];
+    if (gated_off(tg)) return;
     const int th = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int a = 0; a <= nacc; ++a) {
@@ -286,26 +290,26 @@ size_t grad_workspace_bytes(const cg_problem* pb, int64_t n_theta) {
 
 template <int K>
 static cg_status launch_gp1_k(const cg_problem* pb, const GP1Data& d, const double* theta, int64_t n_theta,
-                              double* part, WsHeader* hdr, TileGrid* tg, cudaStream_t st) {
+                              double* part, WsHeader* hdr, TileGrid* tg, cudaStream_t st, const int* gate) {
     constexpr int NT = 256;
     const int64_t n = pb->n_bins[0];
     switch (pb->objective) {
-        case CG_OBJ_CHI2: return launch_tiles(k_gp1_fp64<K, CG_OBJ_CHI2, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st);
-        case CG_OBJ_POISSON: return launch_tiles(k_gp1_fp64<K, CG_OBJ_POISSON, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st);
-        case CG_OBJ_POISSON_BC: return launch_tiles(k_gp1_fp64<K, CG_OBJ_POISSON_BC, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st);
+        case CG_OBJ_CHI2: return launch_tiles(k_gp1_fp64<K, CG_OBJ_CHI2, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st, gate);
+        case CG_OBJ_POISSON: return launch_tiles(k_gp1_fp64<K, CG_OBJ_POISSON, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st, gate);
+        case CG_OBJ_POISSON_BC: return launch_tiles(k_gp1_fp64<K, CG_OBJ_POISSON_BC, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st, gate);
         default: return CG_ERR_UNSUPPORTED;
     }
 }
 
 template <int K>
 static cg_status launch_rg2_k(const RG2Data& d, const double* theta, int64_t n, int64_t n_theta, double* part,
-                              WsHeader* hdr, TileGrid* tg, cudaStream_t st) {
+                              WsHeader* hdr, TileGrid* tg, cudaStream_t st, const int* gate) {
     constexpr int NT = 128;
-    return launch_tiles(k_rg2_fp64<K, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st);
+    return launch_tiles(k_rg2_fp64<K, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st, gate);
 }
 
 cg_status grad_points(const cg_problem* pb, const double* theta, int64_t n_theta, double* value, double* grad,
-                      void* ws, size_t ws_bytes, cudaStream_t st) {
+                      void* ws, size_t ws_bytes, cudaStream_t st, const int* gate) {
     cg_status s = validate(pb);
     if (s != CG_OK) return s;
     if (n_theta < 1 || !theta || (!value && !grad)) return CG_ERR_INVALID_ARG;
@@ -326,14 +330,16 @@ cg_status grad_points(const cg_problem* pb, const double* theta, int64_t n_theta
     ep.D = pb->poly_degree;
     ep.lo = pb->lo[0];
     ep.hi = pb->hi[0];
+    if (n == 0 && gate) return CG_ERR_UNSUPPORTED;
     if (n == 0) {
         // empty data: every sum is zero; still produce value/grad and a clean status
         cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st);
         tg.n_elem = 0; tg.chunk = 1; tg.nbx = 1; tg.n_theta = (int)n_theta; tg.n_tiles = (int)n_theta;
+        tg.gate = nullptr;
         cudaMemsetAsync(part, 0, (size_t)n_theta * (nacc + 1) * sizeof(double), st);
         s = CG_OK;
     } else if (pb->precision == CG_PREC_DF64) {
-        s = launch_df64(pb, theta, n_theta, part, hdr, &tg, st);
+        s = launch_df64(pb, theta, n_theta, part, hdr, &tg, st, gate);
     } else if (pb->model == CG_MODEL_GAUSS_POLY) {
         GP1Data d;
         d.y = pb->data;
@@ -346,11 +352,11 @@ cg_status grad_points(const cg_problem* pb, const double* theta, int64_t n_theta
         d.pm = pb->poly_mode;
         d.vec_ok = (((uintptr_t)pb->data & 15) == 0) && (!pb->centres || (((uintptr_t)pb->centres & 15) == 0));
         switch (pb->n_peaks) {
-            case 0: s = launch_gp1_k<0>(pb, d, theta, n_theta, part, hdr, &tg, st); break;
-            case 1: s = launch_gp1_k<1>(pb, d, theta, n_theta, part, hdr, &tg, st); break;
-            case 2: s = launch_gp1_k<2>(pb, d, theta, n_theta, part, hdr, &tg, st); break;
-            case 3: s = launch_gp1_k<3>(pb, d, theta, n_theta, part, hdr, &tg, st); break;
-            case 4: s = launch_gp1_k<4>(pb, d, theta, n_theta, part, hdr, &tg, st); break;
+            case 0: s = launch_gp1_k<0>(pb, d, theta, n_theta, part, hdr, &tg, st, gate); break;
+            case 1: s = launch_gp1_k<1>(pb, d, theta, n_theta, part, hdr, &tg, st, gate); break;
+            case 2: s = launch_gp1_k<2>(pb, d, theta, n_theta, part, hdr, &tg, st, gate); break;
+            case 3: s = launch_gp1_k<3>(pb, d, theta, n_theta, part, hdr, &tg, st, gate); break;
+            case 4: s = launch_gp1_k<4>(pb, d, theta, n_theta, part, hdr, &tg, st, gate); break;
             default: return CG_ERR_INVALID_ARG;
         }
     } else if (pb->model == CG_MODEL_MIX_GAUSS_EXP) {
@@ -361,8 +367,8 @@ cg_status grad_points(const cg_problem* pb, const double* theta, int64_t n_theta
         d.hi = pb->hi[0];
         d.vec_ok = (((uintptr_t)pb->data & 15) == 0) && (!pb->weights || (((uintptr_t)pb->weights & 15) == 0));
         constexpr int NT = 256;
-        if (pb->weights) s = launch_tiles(k_mix_fp64<true, NT>, NT, d, theta, n, n_theta, part, hdr, &tg, st);
-        else s = launch_tiles(k_mix_fp64<false, NT>, NT, d, theta, n, n_theta, part, hdr, &tg, st);
+        if (pb->weights) s = launch_tiles(k_mix_fp64<true, NT>, NT, d, theta, n, n_theta, part, hdr, &tg, st, gate);
+        else s = launch_tiles(k_mix_fp64<false, NT>, NT, d, theta, n, n_theta, part, hdr, &tg, st, gate);
     } else {
         RG2Data d;
         d.n = pb->data;
@@ -372,14 +378,14 @@ cg_status grad_points(const cg_problem* pb, const double* theta, int64_t n_theta
         d.hx = (pb->hi[0] - pb->lo[0]) / (double)pb->n_bins[0];
         d.hy = (pb->hi[1] - pb->lo[1]) / (double)pb->n_bins[1];
         switch (pb->n_peaks) {
-            case 1: s = launch_rg2_k<1>(d, theta, n, n_theta, part, hdr, &tg, st); break;
-            case 2: s = launch_rg2_k<2>(d, theta, n, n_theta, part, hdr, &tg, st); break;
-            case 3: s = launch_rg2_k<3>(d, theta, n, n_theta, part, hdr, &tg, st); break;
-            case 4: s = launch_rg2_k<4>(d, theta, n, n_theta, part, hdr, &tg, st); break;
-            case 5: s = launch_rg2_k<5>(d, theta, n, n_theta, part, hdr, &tg, st); break;
-            case 6: s = launch_rg2_k<6>(d, theta, n, n_theta, part, hdr, &tg, st); break;
-            case 7: s = launch_rg2_k<7>(d, theta, n, n_theta, part, hdr, &tg, st); break;
-            case 8: s = launch_rg2_k<8>(d, theta, n, n_theta, part, hdr, &tg, st); break;
+            case 1: s = launch_rg2_k<1>(d, theta, n, n_theta, part, hdr, &tg, st, gate); break;
+            case 2: s = launch_rg2_k<2>(d, theta, n, n_theta, part, hdr, &tg, st, gate); break;
+            case 3: s = launch_rg2_k<3>(d, theta, n, n_theta, part, hdr, &tg, st, gate); break;
+            case 4: s = launch_rg2_k<4>(d, theta, n, n_theta, part, hdr, &tg, st, gate); break;
+            case 5: s = launch_rg2_k<5>(d, theta, n, n_theta, part, hdr, &tg, st, gate); break;
+            case 6: s = launch_rg2_k<6>(d, theta, n, n_theta, part, hdr, &tg, st, gate); break;
+            case 7: s = launch_rg2_k<7>(d, theta, n, n_theta, part, hdr, &tg, st, gate); break;
+            case 8: s = launch_rg2_k<8>(d, theta, n, n_theta, part, hdr, &tg, st, gate); break;
             default: return CG_ERR_INVALID_ARG;
         }
     }
@@ -404,13 +410,13 @@ size_t cg_workspace_size(const cg_problem* pb, int64_t n_theta) { return grad_wo
 cg_status cg_objective(const cg_problem* pb, const double* theta, double* value, void* ws, size_t ws_bytes,
                        void* stream) {
     if (!value) return CG_ERR_INVALID_ARG;
-    return grad_points(pb, theta, 1, value, nullptr, ws, ws_bytes, (cudaStream_t)stream);
+    return grad_points(pb, theta, 1, value, nullptr, ws, ws_bytes, (cudaStream_t)stream, nullptr);
 }
 
 cg_status cg_gradient(const cg_problem* pb, const double* theta, double* value, double* grad, void* ws,
                       size_t ws_bytes, void* stream) {
     if (!value || !grad) return CG_ERR_INVALID_ARG;
-    return grad_points(pb, theta, 1, value, grad, ws, ws_bytes, (cudaStream_t)stream);
+    return grad_points(pb, theta, 1, value, grad, ws, ws_bytes, (cudaStream_t)stream, nullptr);
 }
 
 void cg_set_profile_events(void* start, void* stop) {

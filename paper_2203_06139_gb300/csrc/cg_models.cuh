@@ -23,7 +23,12 @@ struct TileGrid {
     int nbx;          // tiles per parameter point
     int n_theta;
     int n_tiles;      // n_theta * nbx
+    const int* gate = nullptr;   // when set, every kernel of the launch returns at once while *gate == 0
 };
+
+__device__ __forceinline__ bool gated_off(const TileGrid& tg) {
+    return tg.gate != nullptr && *(volatile const int*)tg.gate == 0;
+}
 
 struct EpiParams {
     int model, P, K, D;
@@ -326,6 +331,6 @@ __device__ inline double epilogue(const EpiParams& ep, const double* __restrict_
 // double-float path (cg_df64.cu)
 bool df64_supported(const cg_problem* pb);
 cg_status launch_df64(const cg_problem* pb, const double* theta, int64_t n_theta, double* part, WsHeader* hdr,
-                      TileGrid* tg, cudaStream_t st);
+                      TileGrid* tg, cudaStream_t st, const int* gate);
 
 }  // namespace cg

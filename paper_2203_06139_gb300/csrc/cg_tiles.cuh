@@ -60,10 +60,11 @@ inline TileGrid make_tiles(int64_t n_elem, int64_t n_theta, int NT, int grid_blo
 template <typename KernelT, typename DataT>
 inline cg_status launch_tiles(KernelT kern, int NT, const DataT& d, const double* theta, int64_t n_elem,
                               int64_t n_theta, double* part, WsHeader* hdr, TileGrid* tg_out,
-                              cudaStream_t st) {
+                              cudaStream_t st, const int* gate = nullptr) {
     const int R = resident_blocks((const void*)kern, NT, 0);
     const int G = device_sm_count() * R;
     TileGrid tg = make_tiles(n_elem, n_theta, NT, G);
+    tg.gate = gate;
     int grid = tg.n_tiles < G ? tg.n_tiles : G;
     prof_begin(st);
     kern<<<grid, NT, 0, st>>>(d, theta, tg, part, hdr);
