@@ -357,6 +357,155 @@ def df64_roofline(dur_s, n_units, rates, sm_max_mhz):
                           % (nsm, sm_max_mhz or 2070.0)}
 
 
+def _timed(fn, steps, warmup, flush=None):
+    """Device time per call of fn (CUDA events on the current stream), L2 flushed before each."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return sum(ms) / len(ms)
+
+
+def run_c1(args):
+    """10,000-bin histogram: gradients at 100 points, and one full fit."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2203_06139_gb300 import cg, synth
+    from paper_2203_06139_gb300.fit import BatchFitter, HistBatch, SingleFitter, TileMap
+    h = synth.c1_histogram()
+    y = torch.tensor(h["y"], device="cuda")
+    pb = cg.Problem.gauss_poly(y, 0.0, 10.0, 1, 1, cg.OBJ_CHI2)
+    th = torch.tensor(synth.c1_theta_points(), device="cuda")
+    v = torch.empty(100, dtype=torch.float64, device="cuda")
+    g = torch.empty((100, 5), dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    ms = _timed(lambda: cg.batch_gradient(pb, th, v, g), args.steps, max(3, args.warmup), flush)
+    th0 = torch.tensor(synth.c1_theta_points(1)[0], device="cuda")
+    sf = SingleFitter(pb)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = sf.fit(th0, max_iter=50, tol=1e-9)
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t0
+    b = HistBatch(y, [0, 10000], [0.0], [10.0], 1, 1, cg.OBJ_CHI2)
+    bf = BatchFitter(b, TileMap(0, 0, 512, 8))
+    def batched():
+        bf.init(th0.view(1, 5))
+        bf.step(50, 1e-9)
+    ms_fit = _timed(batched, 3, 2)
+    line = {"metric": METRIC, "workload": "c1", "value": 100 * 10000 / (ms / 1e3), "unit": UNIT,
+            "higher_is_better": True, "ms_per_step": ms, "grad_evals_per_s": 100 / (ms / 1e3),
+            "config": {"workload": "chi2, Gaussian + linear, 10,000 bins x 100 parameter points, FP64",
+                       "l2": "flushed before every timed step"},
+            "full_fit": {"plain_path_s": t_single, "plain_iters": int(st.iters[0]), "plain_evals": int(st.n_eval[0]),
+                         "plain_F": float(st.f[0]), "one_cluster_fit_ms": ms_fit,
+                         "one_cluster_F": float(bf.states.f[0]), "status": int(bf.states.status[0])},
+            "gpu_launches": 2 * args.steps}
+    print(json.dumps(line), flush=True)
+
+
+def run_c3(args):
+    """4096 x 4096 bins, 8 rotated Gaussians: autograd forward + backward."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2203_06139_gb300 import cg, synth
+    from paper_2203_06139_gb300.autograd import fit_objective
+    hh = synth.c3_histogram()
+    prec = cg.PREC_DF64 if args.prec == "df64" else cg.PREC_FP64
+    try:
+        pb = cg.Problem.rotgauss2d(torch.tensor(hh["counts"], device="cuda"), 8, precision=prec)
+        pb.workspace(1)
+    except cg.CgError:
+        prec = cg.PREC_FP64
+        pb = cg.Problem.rotgauss2d(torch.tensor(hh["counts"], device="cuda"), 8, precision=prec)
+    th = torch.tensor(synth.c3_theta_point(hh["truth"])[0], device="cuda", requires_grad=True)
+    def fwd_bwd():
+        th.grad = None
+        fit_objective(th, pb).backward()
+    ms = _timed(fwd_bwd, args.steps, max(3, args.warmup))
+    n = 4096 * 4096
+    line = {"metric": METRIC, "workload": "c3", "value": n / (ms / 1e3), "unit": UNIT, "higher_is_better": True,
+            "ms_per_step": ms, "grad_evals_per_s": 1e3 / ms, "dtype": "f64" if prec == cg.PREC_FP64 else "df64",
+            "config": {"workload": "Poisson NLL, 8 rotated 2-D Gaussians + constant, 4096 x 4096 bins, 49 params, "
+                                   "autograd forward+backward", "l2": "inputs (134 MB) larger than L2"},
+            "gpu_launches": 2 * args.steps}
+    print(json.dumps(line), flush=True)
+
+
+def run_c4(args):
+    """4096 uneven histograms: time-to-fit, batched persistent launch vs the plain per-histogram path."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2203_06139_gb300 import cg, synth
+    from paper_2203_06139_gb300.fit import BatchFitter, HistBatch, SingleFitter, autotune
+    d = synth.c4_batch()
+    prec = cg.PREC_FP64   # the fit kernels evaluate in FP64
+    b = HistBatch(d["y"], d["offsets"], d["lo"], d["hi"], 1, 2, cg.OBJ_CHI2, poly_mode=1, precision=prec)
+    th0 = torch.tensor(d["start"], device="cuda")
+    best, timings = autotune(b, th0, n_steps=3)
+    f = BatchFitter(b, best)
+    f.capture(50, 1e-9, theta0=th0)   # init + 50 iterations in one graph
+    def batched():
+        f.replay()
+    ms = _timed(batched, max(1, min(args.steps, 5)), 2)
+    Fb = f.states.f.cpu().numpy()
+    stb = f.states.status.cpu().numpy()
+    itb = f.states.iters.cpu().numpy()
+    # plain path: every histogram on its own, full-GPU launches per trial point
+    n_plain = args.plain_hists or d["H"]
+    idx = np.arange(d["H"]) if n_plain >= d["H"] else np.random.default_rng(0).choice(d["H"], n_plain, replace=False)
+    yt = b.y
+    Fp = np.zeros(len(idx))
+    sp = np.zeros(len(idx), dtype=np.int64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j, h in enumerate(idx):
+        o0, o1 = int(d["offsets"][h]), int(d["offsets"][h + 1])
+        pb = cg.Problem.gauss_poly(yt[o0:o1], 0.0, 1.0, 1, 2, cg.OBJ_CHI2, poly_mode=1)
+        st = SingleFitter(pb).fit(th0[h], max_iter=50, tol=1e-9)
+        Fp[j] = float(st.f[0])
+        sp[j] = int(st.status[0])
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    t_plain_full = t_plain * d["H"] / len(idx)
+    same = np.abs(Fb[idx] - Fp) <= 1e-6 * np.abs(Fp)
+    both = (stb[idx] == cg.FIT_CONVERGED) & (sp == cg.FIT_CONVERGED)
+    line = {"metric": METRIC, "workload": "c4", "value": ms / 1e3, "unit": "s time-to-fit (4096 histograms)",
+            "higher_is_better": False, "ms_per_step": ms,
+            "config": {"workload": "4096 histograms, 64-65536 bins (log-uniform), Gaussian + quadratic, chi2, "
+                                   "50 BFGS iterations in one graph-captured persistent launch",
+                       "tile_map": best.as_dict(), "bins": int(d["offsets"][-1])},
+            "dtype": "f64" if prec == cg.PREC_FP64 else "df64",
+            "batched": {"converged": int((stb == cg.FIT_CONVERGED).sum()), "mean_iters": float(itb.mean()),
+                        "ms": ms},
+            "plain_path": {"seconds_measured": t_plain, "histograms_measured": int(len(idx)),
+                           "seconds_for_all": t_plain_full},
+            "speedup_vs_plain": t_plain_full / (ms / 1e3),
+            "status_counts": {"batched": np.bincount(stb, minlength=5).tolist(),
+                              "plain": np.bincount(sp, minlength=5).tolist()},
+            "same_minimum_frac": float(same.mean()),
+            "same_minimum_frac_both_converged": float(same[both].mean()) if both.any() else None,
+            "lower_F_when_different": {"batched": int(((Fb[idx] < Fp) & ~same).sum()),
+                                       "plain": int(((Fp < Fb[idx]) & ~same).sum())},
+            "autotune": timings[:4]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -367,9 +516,20 @@ def main():
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64-path comparison leg")
     ap.add_argument("--events", type=int, default=N_EVENTS)
     ap.add_argument("--points", type=int, default=N_POINTS)
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--plain-hists", type=int, default=0, help="c4: histograms timed on the plain path (0 = all)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c1":
+        run_c1(args)
+    elif args.workload == "c3":
+        run_c3(args)
+    elif args.workload == "c4":
+        run_c4(args)
+    elif args.workload == "c5":
+        from paper_2203_06139_gb300 import learned_start
+        learned_start.bench(args)
     else:
         run(args)
 

@@ -143,32 +143,45 @@ class BatchFitter:
         self.states = None
         self.graph = None
 
-    def init(self, theta0):
-        theta0 = cg._dev_f64(theta0, "theta0")
-        raw = torch.zeros((self.b.H, STATE_BYTES), dtype=torch.uint8, device=self.b.y.device)
+    def _init_into(self, theta0, stream=None):
         cg._check(cg.lib().cg_fit_init(ctypes.byref(self.b.c), ctypes.byref(self.mc), cg._ptr(theta0),
-                                       cg._ptr(raw), cg._ptr(self.ws), self.ws.numel(), cg._stream()),
-                  "cg_fit_init")
-        self.states = States(raw, self.b.P)
-        self.graph = None
+                                       cg._ptr(self.states.raw), cg._ptr(self.ws), self.ws.numel(),
+                                       cg._stream(stream)), "cg_fit_init")
+
+    def init(self, theta0):
+        """(Re)initialise every fit state at theta0 [H, P]; the state buffer is reused."""
+        theta0 = cg._dev_f64(theta0, "theta0")
+        if self.states is None:
+            raw = torch.zeros((self.b.H, STATE_BYTES), dtype=torch.uint8, device=self.b.y.device)
+            self.states = States(raw, self.b.P)
+        self._init_into(theta0)
         return self.states
+
+    def _step_into(self, st, n_steps, tol, stream=None):
+        cg._check(cg.lib().cg_fit_step(ctypes.byref(self.b.c), ctypes.byref(self.mc), cg._ptr(st.raw), int(n_steps),
+                                       float(tol), cg._ptr(self.ws), self.ws.numel(), cg._stream(stream)),
+                  "cg_fit_step")
 
     def step(self, n_steps=50, tol=1e-9, states=None):
         st = states or self.states
-        cg._check(cg.lib().cg_fit_step(ctypes.byref(self.b.c), ctypes.byref(self.mc), cg._ptr(st.raw), int(n_steps),
-                                       float(tol), cg._ptr(self.ws), self.ws.numel(), cg._stream()), "cg_fit_step")
+        self._step_into(st, n_steps, tol)
         return st
 
-    def capture(self, n_steps=50, tol=1e-9):
-        """Capture one cg_fit_step (counter reset + persistent kernel) into a CUDA graph."""
+    def capture(self, n_steps=50, tol=1e-9, theta0=None):
+        """Capture the fit into a CUDA graph: cg_fit_step (counter reset + persistent
+        kernel), preceded by cg_fit_init from theta0 when given (theta0 is kept)."""
+        if theta0 is not None:
+            self._theta0 = cg._dev_f64(theta0, "theta0")
+            if self.states is None:
+                self.init(self._theta0)
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         g = torch.cuda.CUDAGraph()
         with torch.cuda.stream(s):
             g.capture_begin()
-            cg._check(cg.lib().cg_fit_step(ctypes.byref(self.b.c), ctypes.byref(self.mc), cg._ptr(self.states.raw),
-                                           int(n_steps), float(tol), cg._ptr(self.ws), self.ws.numel(),
-                                           cg._stream(s)), "cg_fit_step (capture)")
+            if theta0 is not None:
+                self._init_into(self._theta0, s)
+            self._step_into(self.states, n_steps, tol, s)
             g.capture_end()
         torch.cuda.current_stream().wait_stream(s)
         self.graph = g
