@@ -197,6 +197,25 @@ cg_status cg_get_status(const void *ws, void *stream);
 cg_status cg_mixture_gradient_noalloc(const cg_problem *pb, const double *theta, int64_t n_theta,
                                       double *value, double *grad, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Learned start (a network that proposes fit starting parameters).  The
+ * paper has no network; these calls serve the BF16 multilayer perceptron
+ * that maps a coarse rebinned histogram to starting parameters, trained and
+ * run by the kernels below.
+ * ------------------------------------------------------------------------ */
+
+/* C[M][N] = sum_k A(m, k) B(n, k) on the tensor cores: BF16 operands
+ * (uint16 storage), FP32 accumulation in tensor memory.  A is [M][lda]
+ * (transA = 0) or [K][lda] read transposed (transA = 1); B is [N][ldb]
+ * (transB = 0) or [K][ldb] (transB = 1); C row stride ldc.  Epilogues:
+ * 0 Cf = acc; 1 Cf = acc + bias[n]; 2 z = acc + bias[n], aux_out = z,
+ * Cb = bf16(gelu(z)) (and Cf = gelu(z) if given); 3 dz = acc * gelu'(aux_in),
+ * Cb = bf16(dz) (and/or Cf = dz).  gelu(z) = z Phi(z).  err (device int, may
+ * be NULL) gets bit 0 when a bounded wait on the tensor core gave up. */
+cg_status cg_gemm_bf16(const void *A, const void *B, int M, int N, int K, int lda, int ldb, int transA,
+                       int transB, float *Cf, void *Cb, int ldc, const float *bias, const float *aux_in,
+                       float *aux_out, int epilogue, int *err, void *stream);
+
 /* Profiling hook: when start/stop are non-NULL cudaEvent_t handles (passed as
  * void*), every later launch of a fused accumulation kernel (the dominant
  * kernel of cg_objective / cg_gradient / cg_batch_gradient / cg_fit_*)

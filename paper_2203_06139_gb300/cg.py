@@ -73,6 +73,9 @@ def lib():
         "cg_get_status": (ctypes.c_int, [_vp, _vp]),
         "cg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "cg_set_profile_events": (None, [_vp, _vp]),
+        "cg_gemm_bf16": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp,
+                                        _vp, ctypes.c_int, _vp, _vp]),
         "cg_fit_workspace_size": (_sz, [B]),
         "cg_fit_plan": (ctypes.c_int, [B, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_TileMap), _vp, _sz, _vp]),
         "cg_fit_init": (ctypes.c_int, [B, ctypes.POINTER(_TileMap), _dp, _vp, _vp, _sz, _vp]),
@@ -232,3 +235,21 @@ def set_profile_events(start=None, stop=None):
         lib().cg_set_profile_events(None, None)
     else:
         lib().cg_set_profile_events(ctypes.c_void_p(start.cuda_event), ctypes.c_void_p(stop.cuda_event))
+
+
+EPI_F32, EPI_BIAS_F32, EPI_BIAS_GELU, EPI_GELU_GRAD = 0, 1, 2, 3
+
+
+def gemm_bf16(A, B, M, N, K, transA=0, transB=0, Cf=None, Cb=None, bias=None, aux_in=None, aux_out=None,
+              epilogue=EPI_F32, err=None, stream=None):
+    """C[M, N] = sum_k A[m, k] B[n, k] on the tensor cores (BF16 in, FP32 accumulate).
+    A is [M, K] (transA = 0) or [K, M] (transA = 1); B is [N, K] (transB = 0) or [K, N]."""
+    for t in (A, B):
+        if t.dtype != torch.bfloat16 or not t.is_cuda or not t.is_contiguous():
+            raise CgError(ERR_INVALID_ARG, "gemm operands must be contiguous bf16 CUDA tensors")
+    lda = A.shape[1]
+    ldb = B.shape[1]
+    ldc = N
+    _check(lib().cg_gemm_bf16(_ptr(A), _ptr(B), M, N, K, lda, ldb, transA, transB, _ptr(Cf), _ptr(Cb), ldc,
+                              _ptr(bias), _ptr(aux_in), _ptr(aux_out), epilogue, _ptr(err), _stream(stream)),
+           "cg_gemm_bf16")
