@@ -216,6 +216,48 @@ cg_status cg_gemm_bf16(const void *A, const void *B, int M, int N, int K, int ld
                        int transB, float *Cf, void *Cb, int ldc, const float *bias, const float *aux_in,
                        float *aux_out, int epilogue, int *err, void *stream);
 
+/* Rebinning for the network input: x[h][j] = bf16(r_j / max_j r_j) with
+ * r_j the sum of `factor` consecutive counts of histogram h (y: device
+ * [H][n_bins] FP64, x: device [H][n_bins/factor] bf16); scale[h] = max_j r_j. */
+cg_status cg_rebin_normalize(const double *y, int64_t H, int n_bins, int factor, void *x_bf16, float *scale,
+                             void *stream);
+
+/* Plain heuristic starting point for K Gaussian peaks + linear background on
+ * [lo, hi] (y: device [H][n_bins] FP64; theta0: device [H][3K+2]): on the
+ * histogram rebinned by `factor`, 5-bin box smoothing, background line
+ * through the minima of the first and last eighth, the K highest local
+ * maxima of the residual at least 3 rebinned bins apart, width from the
+ * half-maximum crossings; peaks sorted by position. */
+cg_status cg_heuristic_start(const double *y, int64_t H, int n_bins, int factor, double lo, double hi, int n_peaks,
+                             double *theta0, void *stream);
+
+/* loss = mean over B x n_out of (pred - target)^2 (pred rows of stride ld,
+ * target [B][n_out]); dpred (FP32) and/or dpred_bf16 get its gradient, zero in
+ * the padding columns.  One CTA, fixed-order sums. */
+cg_status cg_mse_loss(const float *pred, const float *target, int64_t B, int n_out, int ld, float *loss,
+                      float *dpred, void *dpred_bf16, void *stream);
+
+/* out[c] = sum over rows of X[r][c] (X: [rows][cols] FP32), rows in order. */
+cg_status cg_colsum(const float *X, int64_t rows, int cols, float *out, void *stream);
+
+/* One AdamW step on FP32 master weights w (n values) with moments m, v;
+ * bias-corrected with `step` (>= 1); w_bf16 (optional) receives the rounded
+ * copy used by the GEMMs. */
+cg_status cg_adamw(float *w, const float *g, float *m, float *v, int64_t n, float lr, float beta1, float beta2,
+                   float eps, float weight_decay, int step, void *w_bf16, void *stream);
+
+/* Network output -> starting parameters of K peaks + linear background:
+ * y rows (stride ld) hold z-scores (mean, stdv: [3K+2]) of
+ * (A_k factor/scale, mu_k, log s_k, b0 factor/scale, b1 factor/scale);
+ * the decoded values are clamped into the model's domain and the peaks are
+ * sorted by mu.  theta0: device [H][3K+2] FP64. */
+cg_status cg_decode_start(const float *y, int ld, const float *scale, const float *mean, const float *stdv,
+                          int64_t H, int n_peaks, int factor, int n_bins, double lo, double hi, double *theta0,
+                          void *stream);
+
+/* b[i] = bf16(a[i]). */
+cg_status cg_to_bf16(const float *a, int64_t n, void *b, void *stream);
+
 /* Profiling hook: when start/stop are non-NULL cudaEvent_t handles (passed as
  * void*), every later launch of a fused accumulation kernel (the dominant
  * kernel of cg_objective / cg_gradient / cg_batch_gradient / cg_fit_*)

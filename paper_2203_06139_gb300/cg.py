@@ -73,6 +73,16 @@ def lib():
         "cg_get_status": (ctypes.c_int, [_vp, _vp]),
         "cg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "cg_set_profile_events": (None, [_vp, _vp]),
+        "cg_rebin_normalize": (ctypes.c_int, [_vp, _i64, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
+        "cg_heuristic_start": (ctypes.c_int, [_vp, _i64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_int, _vp, _vp]),
+        "cg_mse_loss": (ctypes.c_int, [_vp, _vp, _i64, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]),
+        "cg_colsum": (ctypes.c_int, [_vp, _i64, ctypes.c_int, _vp, _vp]),
+        "cg_adamw": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float, ctypes.c_float, ctypes.c_int, _vp, _vp]),
+        "cg_to_bf16": (ctypes.c_int, [_vp, _i64, _vp, _vp]),
+        "cg_decode_start": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _i64, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_double, ctypes.c_double, _vp, _vp]),
         "cg_gemm_bf16": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp,
                                         _vp, ctypes.c_int, _vp, _vp]),

@@ -261,3 +261,308 @@ extern "C" cg_status cg_gemm_bf16(const void* A, const void* B, int M, int N, in
     g.bias = bias; g.aux_in = aux_in; g.aux_out = aux_out; g.epi = epilogue; g.err = err;
     return gemm_bf16(g, (cudaStream_t)stream);
 }
+
+// ===========================================================================
+// Learned-start helpers: rebinning, heuristic start, loss, sums, optimiser
+// ===========================================================================
+namespace cg {
+namespace {
+
+// x[h][j] = bf16(r_j / max_j r_j), r_j = sum of `factor` consecutive counts;
+// scale[h] = max_j r_j (1 when the histogram is empty).
+__global__ void k_rebin(const double* __restrict__ y, int64_t H, int n_bins, int factor, __nv_bfloat16* x,
+                        float* scale) {
+    extern __shared__ double sr[];
+    const int nr = n_bins / factor;
+    for (int64_t h = blockIdx.x; h < H; h += gridDim.x) {
+        const double* yh = y + h * (int64_t)n_bins;
+        for (int j = threadIdx.x; j < nr; j += blockDim.x) {
+            double s = 0.0;
+            for (int i = 0; i < factor; ++i) s += yh[j * factor + i];
+            sr[j] = s;
+        }
+        __syncthreads();
+        __shared__ double mx;
+        if (threadIdx.x == 0) {
+            double m = 0.0;
+            for (int j = 0; j < nr; ++j) m = fmax(m, sr[j]);
+            mx = m > 0.0 ? m : 1.0;
+            scale[h] = (float)mx;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < nr; j += blockDim.x) x[h * nr + j] = __float2bfloat16((float)(sr[j] / mx));
+        __syncthreads();
+    }
+}
+
+// Heuristic starting point for K Gaussian peaks on a linear background, from
+// the rebinned histogram: 5-bin box smoothing; background = line through the
+// minima of the first and last eighth; peaks = the K highest local maxima of
+// the smoothed residual, at least 3 rebinned bins apart; amplitude =
+// residual height; width from the half-maximum crossings.  Output per original bin:
+// theta = (A_1, mu_1, s_1, ..., A_K, mu_K, s_K, b0, b1), peaks sorted by mu.
+__global__ void k_heuristic(const double* __restrict__ y, int64_t H, int n_bins, int factor, double lo, double hi,
+                            int K, double* theta) {
+    extern __shared__ double sm[];
+    const int nr = n_bins / factor;
+    double* r = sm;
+    double* s = sm + nr;
+    const double wr = (hi - lo) / nr;        // rebinned bin width
+    for (int64_t h = blockIdx.x; h < H; h += gridDim.x) {
+        const double* yh = y + h * (int64_t)n_bins;
+        for (int j = threadIdx.x; j < nr; j += blockDim.x) {
+            double t = 0.0;
+            for (int i = 0; i < factor; ++i) t += yh[j * factor + i];
+            r[j] = t;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < nr; j += blockDim.x) {
+            double t = 0.0;
+            int c = 0;
+            for (int q = j - 2; q <= j + 2; ++q)
+                if (q >= 0 && q < nr) { t += r[q]; ++c; }
+            s[j] = t / c;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int seg = nr / 8 > 1 ? nr / 8 : 1;
+            int jl = 0, jr = nr - 1;
+            for (int j = 0; j < seg; ++j) if (s[j] < s[jl]) jl = j;
+            for (int j = nr - seg; j < nr; ++j) if (s[j] < s[jr]) jr = j;
+            const double xl = (jl + 0.5), xr = (jr + 0.5);
+            const double slope = (jr != jl) ? (s[jr] - s[jl]) / (xr - xl) : 0.0;   // per rebinned bin
+            const double b_at0 = s[jl] - slope * xl;                               // at rebinned coordinate 0
+            // residual in r (reuse r[] for it)
+            for (int j = 0; j < nr; ++j) r[j] = s[j] - (b_at0 + slope * (j + 0.5));
+            double pk_mu[8], pk_A[8], pk_s[8], pk_ex[8];
+            int found = 0;
+            for (int k = 0; k < K && k < 8; ++k) {
+                int best = -1;
+                for (int j = 1; j < nr - 1; ++j) {
+                    if (!(r[j] >= r[j - 1] && r[j] >= r[j + 1])) continue;
+                    bool far = true;   // outside the masked window of every accepted peak
+                    for (int q = 0; q < found; ++q)
+                        if (fabs((j + 0.5) * wr + lo - pk_mu[q]) < pk_ex[q]) far = false;
+                    if (!far) continue;
+                    if (best < 0 || r[j] > r[best]) best = j;
+                }
+                if (best < 0 || !(r[best] > 0.0)) break;
+                const double half = 0.5 * r[best];
+                int a = best, b = best;
+                while (a > 0 && r[a] > half) --a;
+                while (b < nr - 1 && r[b] > half) ++b;
+                double fw = (double)(b - a);
+                if (fw < 1.0) fw = 1.0;
+                pk_mu[found] = lo + (best + 0.5) * wr;
+                pk_A[found] = r[best] / factor;
+                pk_s[found] = fw * wr / 2.3548200450309493;
+                pk_ex[found] = 3.0 * wr;   // later peaks at least 3 rebinned bins away
+                ++found;
+            }
+            for (int k = found; k < K; ++k) {    // not enough peaks: small ones spread over the range
+                pk_mu[k] = lo + (hi - lo) * (k + 0.5) / K;
+                pk_A[k] = 1.0;
+                pk_s[k] = 2.0 * wr;
+            }
+            for (int i = 1; i < K; ++i)          // sort by mu (insertion)
+                for (int j = i; j > 0 && pk_mu[j] < pk_mu[j - 1]; --j) {
+                    double t;
+                    t = pk_mu[j]; pk_mu[j] = pk_mu[j - 1]; pk_mu[j - 1] = t;
+                    t = pk_A[j]; pk_A[j] = pk_A[j - 1]; pk_A[j - 1] = t;
+                    t = pk_s[j]; pk_s[j] = pk_s[j - 1]; pk_s[j - 1] = t;
+                }
+            double* th = theta + h * (3 * K + 2);
+            for (int k = 0; k < K; ++k) {
+                th[3 * k] = pk_A[k];
+                th[3 * k + 1] = pk_mu[k];
+                th[3 * k + 2] = pk_s[k];
+            }
+            // background per original bin: b(x) = b0 + b1 x with x the bin centre
+            const double per_bin = 1.0 / factor;
+            const double b1 = slope / wr * per_bin;
+            th[3 * K] = (b_at0 - slope * lo / wr) * per_bin;
+            th[3 * K + 1] = b1;
+        }
+        __syncthreads();
+    }
+}
+
+// Mean squared error over the first n_out of ld columns, and its gradient.
+// One block; fixed-order sums.
+__global__ void k_mse(const float* __restrict__ pred, const float* __restrict__ tgt, int64_t B, int n_out, int ld,
+                      float* loss, float* dpred, __nv_bfloat16* dpred_b) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    const float sc = 2.0f / (float)(B * n_out);
+    for (int64_t i = threadIdx.x; i < B * ld; i += blockDim.x) {
+        const int64_t b = i / ld;
+        const int c = (int)(i - b * ld);
+        float d = 0.0f;
+        if (c < n_out) {
+            d = pred[i] - tgt[b * n_out + c];
+            acc += (double)d * d;
+        }
+        if (dpred) dpred[i] = sc * d;
+        if (dpred_b) dpred_b[i] = __float2bfloat16(sc * d);
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        *loss = (float)(t / (double)(B * n_out));
+    }
+}
+
+// out[c] = sum_r X[r][c], rows summed in order by one thread per column.
+__global__ void k_colsum(const float* __restrict__ X, int64_t rows, int cols, float* out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    double s = 0.0;
+    for (int64_t r = 0; r < rows; ++r) s += X[r * cols + c];
+    out[c] = (float)s;
+}
+
+// AdamW on FP32 master weights, with a BF16 copy for the GEMMs.
+__global__ void k_adamw(float* w, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
+                        float eps, float wd, float bc1, float bc2, __nv_bfloat16* wb) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        float wi = w[i] * (1.0f - lr * wd);
+        wi -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+        w[i] = wi;
+        if (wb) wb[i] = __float2bfloat16(wi);
+    }
+}
+
+__global__ void k_to_bf16(const float* __restrict__ a, int64_t n, __nv_bfloat16* b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = __float2bfloat16(a[i]);
+}
+
+int grid_for(int64_t n, int threads) {
+    int64_t g = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)device_sm_count() * 8;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+}  // namespace cg
+
+extern "C" {
+
+cg_status cg_rebin_normalize(const double* y, int64_t H, int n_bins, int factor, void* x_bf16, float* scale,
+                             void* stream) {
+    if (!y || !x_bf16 || !scale || H < 1 || factor < 1 || n_bins < factor || n_bins % factor) return CG_ERR_INVALID_ARG;
+    const int nr = n_bins / factor;
+    const int g = (int)(H < 4 * cg::device_sm_count() ? H : 4 * cg::device_sm_count());
+    cg::k_rebin<<<g, 256, nr * sizeof(double), (cudaStream_t)stream>>>(y, H, n_bins, factor, (__nv_bfloat16*)x_bf16,
+                                                                      scale);
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
+
+cg_status cg_heuristic_start(const double* y, int64_t H, int n_bins, int factor, double lo, double hi, int n_peaks,
+                             double* theta0, void* stream) {
+    if (!y || !theta0 || H < 1 || factor < 1 || n_bins % factor || n_peaks < 1 || n_peaks > 8 || !(hi > lo))
+        return CG_ERR_INVALID_ARG;
+    const int nr = n_bins / factor;
+    if (nr < 8) return CG_ERR_INVALID_ARG;
+    const int g = (int)(H < 8 * cg::device_sm_count() ? H : 8 * cg::device_sm_count());
+    cg::k_heuristic<<<g, 128, 2 * nr * sizeof(double), (cudaStream_t)stream>>>(y, H, n_bins, factor, lo, hi,
+                                                                              n_peaks, theta0);
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
+
+cg_status cg_mse_loss(const float* pred, const float* target, int64_t B, int n_out, int ld, float* loss,
+                      float* dpred, void* dpred_bf16, void* stream) {
+    if (!pred || !target || !loss || B < 1 || n_out < 1 || ld < n_out) return CG_ERR_INVALID_ARG;
+    cg::k_mse<<<1, 1024, 0, (cudaStream_t)stream>>>(pred, target, B, n_out, ld, loss, dpred,
+                                                   (__nv_bfloat16*)dpred_bf16);
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
+
+cg_status cg_colsum(const float* X, int64_t rows, int cols, float* out, void* stream) {
+    if (!X || !out || rows < 0 || cols < 1) return CG_ERR_INVALID_ARG;
+    cg::k_colsum<<<(cols + 127) / 128, 128, 0, (cudaStream_t)stream>>>(X, rows, cols, out);
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
+
+cg_status cg_adamw(float* w, const float* g, float* m, float* v, int64_t n, float lr, float beta1, float beta2,
+                   float eps, float weight_decay, int step, void* w_bf16, void* stream) {
+    if (!w || !g || !m || !v || n < 1 || step < 1) return CG_ERR_INVALID_ARG;
+    const float bc1 = 1.0f - powf(beta1, (float)step), bc2 = 1.0f - powf(beta2, (float)step);
+    cg::k_adamw<<<cg::grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(w, g, m, v, n, lr, beta1, beta2, eps,
+                                                                       weight_decay, bc1, bc2,
+                                                                       (__nv_bfloat16*)w_bf16);
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
+
+cg_status cg_to_bf16(const float* a, int64_t n, void* b, void* stream) {
+    if (!a || !b || n < 0) return CG_ERR_INVALID_ARG;
+    if (n == 0) return CG_OK;
+    cg::k_to_bf16<<<cg::grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(a, n, (__nv_bfloat16*)b);
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
+
+}  // extern "C"
+
+namespace cg {
+namespace {
+
+// Network output -> fit parameters.  Per histogram h with row y[h][.] (stride
+// ld) the encoded targets are z-scores of (A_k f, mu_k, log s_k, b0 f, b1 f),
+// f = factor / scale[h]; the inverse is clamped into the model's domain
+// (A > 0, mu in [lo, hi], s between half a rebinned bin and the range,
+// background >= 0 at both ends) and the peaks are sorted by mu.
+__global__ void k_decode(const float* __restrict__ y, int ld, const float* __restrict__ scale,
+                         const float* __restrict__ mean, const float* __restrict__ stdv, int64_t H, int K, int factor,
+                         int n_bins, double lo, double hi, double* theta) {
+    const int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (h >= H) return;
+    const int P = 3 * K + 2;
+    double t[3 * 8 + 2];
+    for (int j = 0; j < P; ++j) t[j] = (double)y[h * ld + j] * stdv[j] + mean[j];
+    const double f = (double)factor / (double)scale[h];
+    const double wr = (hi - lo) * factor / n_bins;
+    for (int k = 0; k < K; ++k) {
+        t[3 * k] = fmax(t[3 * k] / f, 1e-3 / f);
+        t[3 * k + 1] = fmin(fmax(t[3 * k + 1], lo), hi);
+        t[3 * k + 2] = fmin(fmax(exp(t[3 * k + 2]), 0.5 * wr), hi - lo);
+    }
+    double b0 = t[3 * K] / f, b1 = t[3 * K + 1] / f;
+    // keep the line non-negative at both ends of the range
+    const double e0 = fmax(b0 + b1 * lo, 1e-3 / f), e1 = fmax(b0 + b1 * hi, 1e-3 / f);
+    b1 = (e1 - e0) / (hi - lo);
+    b0 = e0 - b1 * lo;
+    for (int i = 1; i < K; ++i)
+        for (int j = i; j > 0 && t[3 * j + 1] < t[3 * (j - 1) + 1]; --j)
+            for (int q = 0; q < 3; ++q) {
+                const double s = t[3 * j + q];
+                t[3 * j + q] = t[3 * (j - 1) + q];
+                t[3 * (j - 1) + q] = s;
+            }
+    double* o = theta + h * P;
+    for (int j = 0; j < 3 * K; ++j) o[j] = t[j];
+    o[3 * K] = b0;
+    o[3 * K + 1] = b1;
+}
+
+}  // namespace
+}  // namespace cg
+
+extern "C" cg_status cg_decode_start(const float* y, int ld, const float* scale, const float* mean, const float* stdv,
+                                     int64_t H, int n_peaks, int factor, int n_bins, double lo, double hi,
+                                     double* theta0, void* stream) {
+    if (!y || !scale || !mean || !stdv || !theta0 || H < 1 || n_peaks < 1 || n_peaks > 8 || ld < 3 * n_peaks + 2 ||
+        factor < 1 || n_bins < factor || !(hi > lo))
+        return CG_ERR_INVALID_ARG;
+    cg::k_decode<<<(unsigned)((H + 127) / 128), 128, 0, (cudaStream_t)stream>>>(y, ld, scale, mean, stdv, H, n_peaks,
+                                                                              factor, n_bins, lo, hi, theta0);
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}

@@ -1,0 +1,308 @@
+"""Learned starting points for the batched fitter.
+
+A multilayer perceptron 256 -> 512 -> 512 -> 11 (GELU; output padded to 16)
+maps the 2048-bin histogram of 3 Gaussian peaks + linear background,
+rebinned to 256 bins and normalised by its maximum, to starting parameters.
+Weights and activations are BF16 with FP32 accumulation; training (forward,
+backward, MSE loss, AdamW with FP32 master weights) and inference run in the
+kernels of libcg (cg_gemm_bf16 on the tensor cores, cg_rebin_normalize,
+cg_mse_loss, cg_colsum, cg_adamw, cg_decode_start).  Targets are the
+converged fits of the plain method (the BFGS fitter) on method-generated
+histograms.  A learned start is judged by the plain fit: where its fit does
+not converge, or ends above the heuristic-start fit, the heuristic result is
+kept.  The paper has no network; this is the learned-start extension of the
+batched fitter.
+"""
+import ctypes
+import json
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import cg, synth
+from .fit import BatchFitter, HistBatch, TileMap
+
+N_IN, N_HID, N_OUT, N_PAD = 256, 512, 11, 16
+FACTOR = 8
+N_BINS = 2048
+K_PEAKS = 3
+FIT_MAP = TileMap(warp_max_bins=4096, cta_max_bins=1 << 30, cta_threads=256, cluster_size=1)
+
+
+def _p(t):
+    return cg._ptr(t)
+
+
+def _s():
+    return cg._stream()
+
+
+def rebin(y_flat, H):
+    """bf16 [H, 256] network input and the per-histogram scale (max rebinned count)."""
+    x = torch.empty((H, N_IN), dtype=torch.bfloat16, device=y_flat.device)
+    scale = torch.empty(H, dtype=torch.float32, device=y_flat.device)
+    cg._check(cg.lib().cg_rebin_normalize(_p(y_flat), H, N_BINS, FACTOR, _p(x), _p(scale), _s()),
+              "cg_rebin_normalize")
+    return x, scale
+
+
+def heuristic_start(y_flat, H):
+    th = torch.empty((H, 3 * K_PEAKS + 2), dtype=torch.float64, device=y_flat.device)
+    cg._check(cg.lib().cg_heuristic_start(_p(y_flat), H, N_BINS, FACTOR, 0.0, 1.0, K_PEAKS, _p(th), _s()),
+              "cg_heuristic_start")
+    return th
+
+
+def encode_targets(theta, scale):
+    """Fit parameters [H, 11] -> network targets before z-scoring."""
+    f = (FACTOR / scale.double())[:, None]
+    t = theta.clone()
+    for k in range(K_PEAKS):
+        t[:, 3 * k] = theta[:, 3 * k] * f[:, 0]
+        t[:, 3 * k + 2] = torch.log(theta[:, 3 * k + 2].abs())
+    t[:, 9] = theta[:, 9] * f[:, 0]
+    t[:, 10] = theta[:, 10] * f[:, 0]
+    return t
+
+
+class MLP:
+    """Parameters, optimiser state and activation buffers of the network."""
+
+    def __init__(self, seed=0, device="cuda"):
+        g = torch.Generator().manual_seed(seed)
+
+        def he(o, i, gain=1.0):
+            return (torch.randn(o, i, generator=g, dtype=torch.float32) * math.sqrt(2.0 / i) * gain).to(device)
+
+        self.W = [he(N_HID, N_IN), he(N_HID, N_HID), he(N_PAD, N_HID, 0.1)]
+        self.W[2][N_OUT:] = 0.0
+        self.b = [torch.zeros(N_HID, device=device), torch.zeros(N_HID, device=device),
+                  torch.zeros(N_PAD, device=device)]
+        self.Wb = [torch.empty(w.shape, dtype=torch.bfloat16, device=device) for w in self.W]
+        for w, wb in zip(self.W, self.Wb):
+            cg._check(cg.lib().cg_to_bf16(_p(w), w.numel(), _p(wb), _s()), "cg_to_bf16")
+        self.params = self.W + self.b
+        self.m = [torch.zeros_like(p) for p in self.params]
+        self.v = [torch.zeros_like(p) for p in self.params]
+        self.grads = [torch.zeros_like(p) for p in self.params]
+        self.step = 0
+        self.t_mean = torch.zeros(N_OUT, device=device)
+        self.t_std = torch.ones(N_OUT, device=device)
+        self._buf = {}
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+
+    def _bufs(self, B):
+        b = self._buf.get(B)
+        if b is None:
+            dev = self.W[0].device
+            f32 = dict(dtype=torch.float32, device=dev)
+            b16 = dict(dtype=torch.bfloat16, device=dev)
+            b = dict(Z1=torch.empty((B, N_HID), **f32), H1=torch.empty((B, N_HID), **b16),
+                     Z2=torch.empty((B, N_HID), **f32), H2=torch.empty((B, N_HID), **b16),
+                     Y=torch.empty((B, N_PAD), **f32), dYf=torch.empty((B, N_PAD), **f32),
+                     dYb=torch.empty((B, N_PAD), **b16), dZf=torch.empty((B, N_HID), **f32),
+                     dZb=torch.empty((B, N_HID), **b16), dZ1f=torch.empty((B, N_HID), **f32),
+                     dZ1b=torch.empty((B, N_HID), **b16))
+            self._buf[B] = b
+        return b
+
+    def forward(self, x):
+        B = x.shape[0]
+        c = self._bufs(B)
+        cg.gemm_bf16(x, self.Wb[0], B, N_HID, N_IN, Cb=c["H1"], bias=self.b[0], aux_out=c["Z1"],
+                     epilogue=cg.EPI_BIAS_GELU)
+        cg.gemm_bf16(c["H1"], self.Wb[1], B, N_HID, N_HID, Cb=c["H2"], bias=self.b[1], aux_out=c["Z2"],
+                     epilogue=cg.EPI_BIAS_GELU)
+        cg.gemm_bf16(c["H2"], self.Wb[2], B, N_PAD, N_HID, Cf=c["Y"], bias=self.b[2], epilogue=cg.EPI_BIAS_F32)
+        return c["Y"]
+
+    def loss_and_grad(self, target):
+        B = target.shape[0]
+        c = self._bufs(B)
+        cg._check(cg.lib().cg_mse_loss(_p(c["Y"]), _p(target), B, N_OUT, N_PAD, _p(self.loss), _p(c["dYf"]),
+                                       _p(c["dYb"]), _s()), "cg_mse_loss")
+        return self.loss
+
+    def backward(self, x):
+        B = x.shape[0]
+        c = self._bufs(B)
+        gW1, gW2, gW3, gb1, gb2, gb3 = self.grads
+        L = cg.lib()
+        cg.gemm_bf16(c["dYb"], c["H2"], N_PAD, N_HID, B, transA=1, transB=1, Cf=gW3)
+        cg._check(L.cg_colsum(_p(c["dYf"]), B, N_PAD, _p(gb3), _s()), "cg_colsum")
+        cg.gemm_bf16(c["dYb"], self.Wb[2], B, N_HID, N_PAD, transB=1, Cf=c["dZf"], Cb=c["dZb"], aux_in=c["Z2"],
+                     epilogue=cg.EPI_GELU_GRAD)
+        cg.gemm_bf16(c["dZb"], c["H1"], N_HID, N_HID, B, transA=1, transB=1, Cf=gW2)
+        cg._check(L.cg_colsum(_p(c["dZf"]), B, N_HID, _p(gb2), _s()), "cg_colsum")
+        cg.gemm_bf16(c["dZb"], self.Wb[1], B, N_HID, N_HID, transB=1, Cf=c["dZ1f"], Cb=c["dZ1b"], aux_in=c["Z1"],
+                     epilogue=cg.EPI_GELU_GRAD)
+        cg.gemm_bf16(c["dZ1b"], x, N_HID, N_IN, B, transA=1, transB=1, Cf=gW1)
+        cg._check(L.cg_colsum(_p(c["dZ1f"]), B, N_HID, _p(gb1), _s()), "cg_colsum")
+
+    def adamw(self, lr=1e-3, wd=1e-4):
+        self.step += 1
+        for i, (p, g, m, v) in enumerate(zip(self.params, self.grads, self.m, self.v)):
+            wb = self.Wb[i] if i < 3 else None
+            cg._check(cg.lib().cg_adamw(_p(p), _p(g), _p(m), _p(v), p.numel(), lr, 0.9, 0.999, 1e-8,
+                                        wd if i < 3 else 0.0, self.step, _p(wb), _s()), "cg_adamw")
+
+    def predict_start(self, x, scale):
+        """Starting parameters [H, 11] (FP64) for histograms with inputs x, scales scale."""
+        H = x.shape[0]
+        out = torch.empty((H, 3 * K_PEAKS + 2), dtype=torch.float64, device=x.device)
+        chunk = 16384
+        for h0 in range(0, H, chunk):
+            xb = x[h0:h0 + chunk]
+            Y = self.forward(xb)
+            cg._check(cg.lib().cg_decode_start(_p(Y), N_PAD, _p(scale[h0:h0 + chunk]), _p(self.t_mean),
+                                               _p(self.t_std), xb.shape[0], K_PEAKS, FACTOR, N_BINS, 0.0, 1.0,
+                                               _p(out[h0:h0 + chunk]), _s()), "cg_decode_start")
+        return out
+
+
+def fit_batch(y_flat, H, theta0, n_steps=50, tol=1e-9):
+    """Batched Baker-Cousins fits of H 2048-bin histograms from theta0; returns the fitter."""
+    offs = np.arange(H + 1, dtype=np.int64) * N_BINS
+    b = HistBatch(y_flat, offs, np.zeros(H), np.ones(H), K_PEAKS, 1, cg.OBJ_POISSON_BC, poly_mode=0)
+    f = BatchFitter(b, FIT_MAP)
+    f.init(theta0.contiguous())
+    f.step(n_steps, tol)
+    return f
+
+
+def make_training_set(n_hist, chunk=65536, first_chunk=1, device="cuda", log=None):
+    """Method-generated histograms and their converged plain fits (started at
+    the truth): network inputs x (bf16), scales and fitted parameters."""
+    xs, ss, ts = [], [], []
+    n_done, c = 0, first_chunk
+    while n_done < n_hist:
+        H = min(chunk, n_hist - n_done)
+        d = synth.c5_batch_device(H, N_BINS, chunk=c, device=device)
+        x, scale = rebin(d["y"], H)
+        f = fit_batch(d["y"], H, torch.tensor(d["truth"], device=device))
+        ok = f.states.status == cg.FIT_CONVERGED
+        xs.append(x[ok])
+        ss.append(scale[ok])
+        ts.append(f.states.theta[ok].clone())
+        if log:
+            log("chunk %d: %d/%d converged" % (c, int(ok.sum()), H))
+        n_done += H
+        c += 1
+        del d, f
+    return torch.cat(xs), torch.cat(ss), torch.cat(ts)
+
+
+def train(net, x, scale, theta, epochs=3, batch=1024, lr=1e-3, seed=0, log=None):
+    """AdamW on the MSE of z-scored targets; returns the loss curve (every 50 steps)."""
+    t = encode_targets(theta, scale)
+    net.t_mean = t.mean(0).float().contiguous()
+    net.t_std = t.std(0).clamp_min(1e-6).float().contiguous()
+    tz = ((t - net.t_mean.double()) / net.t_std.double()).float().contiguous()
+    N = x.shape[0]
+    g = torch.Generator(device=x.device)
+    g.manual_seed(seed)
+    curve = []
+    for ep in range(epochs):
+        perm = torch.randperm(N, generator=g, device=x.device)
+        for i0 in range(0, N - batch + 1, batch):
+            idx = perm[i0:i0 + batch]
+            xb = x.index_select(0, idx).contiguous()
+            tb = tz.index_select(0, idx).contiguous()
+            net.forward(xb)
+            net.loss_and_grad(tb)
+            net.backward(xb)
+            net.adamw(lr=lr)
+            if net.step == 1 or net.step % 50 == 0:
+                curve.append((net.step, float(net.loss)))
+        if log:
+            log("epoch %d: loss %.4f" % (ep, curve[-1][1] if curve else float("nan")))
+    return curve
+
+
+def evaluate(net, H=65536, chunk=0, device="cuda", n_steps=50, tol=1e-9):
+    """Learned start vs heuristic start on held-out histograms (both fitted in
+    full to count agreement; the production path refits only the learned fits
+    that did not converge, from the heuristic start)."""
+    d = synth.c5_batch_device(H, N_BINS, chunk=chunk, device=device)
+    y = d["y"]
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    fh, t_h = timed(lambda: fit_batch(y, H, heuristic_start(y, H), n_steps, tol))
+
+    def learned():
+        x, scale = rebin(y, H)
+        return fit_batch(y, H, net.predict_start(x, scale), n_steps, tol)
+
+    fl, t_l = timed(learned)
+    Fh, Fl = fh.states.f.cpu().numpy(), fl.states.f.cpu().numpy()
+    sh, sl = fh.states.status.cpu().numpy(), fl.states.status.cpu().numpy()
+    ih, il = fh.states.iters.cpu().numpy(), fl.states.iters.cpu().numpy()
+    flagged_prod = sl != cg.FIT_CONVERGED
+    idx = np.nonzero(flagged_prod)[0]
+
+    def refit():
+        if len(idx) == 0:
+            return None
+        ii = torch.tensor(idx, device=device)
+        ysub = y.view(H, N_BINS).index_select(0, ii).reshape(-1).contiguous()
+        return fit_batch(ysub, len(idx), heuristic_start(ysub, len(idx)), n_steps, tol)
+
+    fr, t_r = timed(refit)
+    Ffinal = Fl.copy()
+    if fr is not None:
+        Fr = fr.states.f.cpu().numpy()
+        better = Fr < Ffinal[idx]
+        Ffinal[idx[better]] = Fr[better]
+    # judged by the plain fit: learned fits above the heuristic fit are rejected
+    worse = Fl > Fh * (1 + 1e-6)
+    Fjudged = np.where((sl != cg.FIT_CONVERGED) | worse, np.minimum(Fh, Fl), Fl)
+    same = np.abs(Ffinal - Fh) <= 1e-6 * np.abs(Fh)
+    return dict(H=H, heuristic=dict(ms=t_h, mean_iters=float(ih.mean()), converged=int((sh == 1).sum()),
+                                    mean_nll=float(np.mean(Fh[np.isfinite(Fh)]))),
+                learned=dict(ms=t_l, mean_iters=float(il.mean()), converged=int((sl == 1).sum()),
+                             mean_nll=float(np.mean(Fl[np.isfinite(Fl)]))),
+                production=dict(ms=t_l + t_r, refit=int(len(idx)), refit_ms=t_r,
+                                mean_nll=float(np.mean(Ffinal[np.isfinite(Ffinal)]))),
+                rejected_by_plain_fit=int(((sl != cg.FIT_CONVERGED) | worse).sum()),
+                lower_than_heuristic=int((Fjudged < Fh * (1 - 1e-6)).sum()),
+                same_minimum_frac=float(same.mean()),
+                nll_learned_le_heuristic_frac=float((Ffinal <= Fh * (1 + 1e-6)).mean()))
+
+
+def bench(args):
+    """bench.py --workload c5: train on method-generated fits, then time fits
+    of 65,536 histograms from the learned vs the heuristic start."""
+    import __graft_entry__
+    __graft_entry__.build()
+    n_train = getattr(args, "train_hists", 0) or 10 ** 6
+    t0 = time.perf_counter()
+    x, scale, theta = make_training_set(n_train)
+    t_data = time.perf_counter() - t0
+    net = MLP(seed=0)
+    t0 = time.perf_counter()
+    curve = train(net, x, scale, theta, epochs=3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    ev = evaluate(net)
+    line = {"metric": "gradient evals/s and bin-grads/s (frac of roofline); time-to-fit vs plain path",
+            "workload": "c5", "value": ev["production"]["ms"] / 1e3, "unit": "s time-to-fit (65,536 histograms)",
+            "higher_is_better": False,
+            "config": {"workload": "3 Gaussians + linear, 2048 bins, Baker-Cousins NLL, 65,536 histograms; MLP "
+                                   "256-512-512-11 BF16 trained on %d method-generated fits" % int(x.shape[0])},
+            "heuristic_start": ev["heuristic"], "learned_start": ev["learned"], "production": ev["production"],
+            "speedup_vs_heuristic": ev["heuristic"]["ms"] / ev["production"]["ms"],
+            "same_minimum_frac": ev["same_minimum_frac"],
+            "nll_learned_le_heuristic_frac": ev["nll_learned_le_heuristic_frac"],
+            "training": {"seconds_data": t_data, "seconds_train": t_train, "steps": net.step,
+                         "loss_first": curve[0][1] if curve else None, "loss_last": curve[-1][1] if curve else None}}
+    print(json.dumps(line), flush=True)

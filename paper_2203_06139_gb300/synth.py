@@ -258,3 +258,28 @@ def random_gauss_poly(K, D, n, lo=0.0, hi=1.0, poly_mode=0, seed=0, noise=True):
     y = r.poisson(np.maximum(mean, 0.0)).astype(np.float64) if noise else mean
     theta = th * r.uniform(0.9, 1.1, size=th.size)
     return dict(K=K, D=D, poly_mode=poly_mode, lo=lo, hi=hi, n=n, y=y, truth=th, theta=theta)
+
+
+def c5_batch_device(H, n_bins=2048, index=4, chunk=0, device="cuda"):
+    """Workload-4 histograms drawn on the GPU (for the 10^6-histogram training
+    set): truth from c5_truth (numpy PCG64), expected counts at the bin
+    centres, Poisson counts from a torch generator seeded with the same base
+    seed.  Returns the counts as a device tensor [H * n_bins]."""
+    import torch
+    truth = c5_truth(H, index, chunk)
+    t = torch.tensor(truth, device=device)
+    x = torch.tensor(uniform_centres(n_bins, 0.0, 1.0), device=device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(SEED_BASE + index + 100 * chunk + 7)
+    y = torch.empty((H, n_bins), dtype=torch.float64, device=device)
+    step = 8192
+    for h0 in range(0, H, step):
+        tt = t[h0:h0 + step]
+        m = tt[:, 9:10] + tt[:, 10:11] * x[None, :]
+        for k in range(3):
+            m = m + tt[:, 3 * k:3 * k + 1] * torch.exp(
+                -0.5 * ((x[None, :] - tt[:, 3 * k + 1:3 * k + 2]) / tt[:, 3 * k + 2:3 * k + 3]) ** 2)
+        y[h0:h0 + step] = torch.poisson(m, generator=gen)
+    offsets = np.arange(H + 1, dtype=np.int64) * n_bins
+    return dict(K=3, D=1, poly_mode=0, H=H, n_bins=n_bins, offsets=offsets, y=y.reshape(-1),
+                lo=np.zeros(H), hi=np.ones(H), truth=truth)

@@ -51,3 +51,98 @@ def test_gemm_epilogues(dev):
     zz = z.clone().requires_grad_(True)
     torch.nn.functional.gelu(zz).backward(A.float() @ B.float().T)
     torch.testing.assert_close(dz, zz.grad, rtol=1e-3, atol=1e-3)
+
+
+# --------------------------------------------------------------------------
+# learned start: rebinning, heuristic start, network gradients, training
+# --------------------------------------------------------------------------
+from paper_2203_06139_gb300 import learned_start as ls  # noqa: E402
+from paper_2203_06139_gb300 import synth  # noqa: E402
+import numpy as np  # noqa: E402
+
+
+def test_rebin_normalize(dev):
+    d = synth.c5_batch(H=37, n_bins=2048)
+    y = torch.tensor(d["y"], device=dev)
+    x, scale = ls.rebin(y, 37)
+    r = d["y"].reshape(37, 256, 8).sum(2)
+    m = r.max(1)
+    np.testing.assert_allclose(scale.cpu().numpy(), m, rtol=1e-6)
+    np.testing.assert_allclose(x.float().cpu().numpy(), r / m[:, None], rtol=1e-2, atol=1e-3)
+
+
+def test_heuristic_start_finds_the_peaks(dev):
+    """Where the three peaks are well separated (gaps above 2.5 (s_i + s_j)),
+    the heuristic locates each to within 4 rebinned bins; overlapping peaks
+    are beyond a local-maximum search."""
+    H = 256
+    d = synth.c5_batch(H=H, n_bins=2048)
+    y = torch.tensor(d["y"], device=dev)
+    th = ls.heuristic_start(y, H).cpu().numpy()
+    mu_t, s_t = d["truth"][:, 1:9:3], d["truth"][:, 2:9:3]
+    sep = np.ones(H, dtype=bool)
+    for k in range(3):
+        for q in range(3):
+            if q != k:
+                sep &= np.abs(mu_t[:, k] - mu_t[:, q]) > 2.5 * (s_t[:, k] + s_t[:, q])
+    assert sep.sum() > 40
+    err = np.abs(th[:, 1:9:3] - mu_t)
+    assert np.mean(err[sep] < 4 * 8 / 2048) > 0.95
+    assert np.all(th[:, 0:9:3] > 0) and np.all(th[:, 2:9:3] > 0)
+
+
+def _ref_mlp(net, x, target):
+    """Plain PyTorch FP32 forward/backward with BF16 rounding at the kernels' points."""
+    bf = lambda t: t.bfloat16().float()
+    W = [w.bfloat16().float() for w in net.W]
+    b = net.b
+    xf = x.float()
+    Z1 = xf @ W[0].T + b[0]
+    H1 = bf(torch.nn.functional.gelu(Z1))
+    Z2 = H1 @ W[1].T + b[1]
+    H2 = bf(torch.nn.functional.gelu(Z2))
+    Y = H2 @ W[2].T + b[2]
+    B = x.shape[0]
+    d = torch.zeros_like(Y)
+    d[:, :11] = Y[:, :11] - target
+    loss = (d[:, :11] ** 2).mean()
+    dY = 2 * d / (B * 11)
+    gW3 = bf(dY).T @ H2
+    dH2 = bf(dY) @ W[2]
+    Z2r = Z2.clone().requires_grad_(True)
+    torch.nn.functional.gelu(Z2r).backward(dH2)
+    dZ2 = Z2r.grad
+    gW2 = bf(dZ2).T @ H1
+    dH1 = bf(dZ2) @ W[1]
+    Z1r = Z1.clone().requires_grad_(True)
+    torch.nn.functional.gelu(Z1r).backward(dH1)
+    dZ1 = Z1r.grad
+    gW1 = bf(dZ1).T @ xf
+    return Y, loss, [gW1, gW2, gW3, dZ1.sum(0), dZ2.sum(0), dY.sum(0)]
+
+
+def test_mlp_forward_backward_vs_reference(dev):
+    net = ls.MLP(seed=3)
+    g = torch.Generator().manual_seed(4)
+    x = torch.rand((200, 256), generator=g).bfloat16().to(dev)
+    t = torch.randn((200, 11), generator=g).to(dev)
+    Y = net.forward(x)
+    loss = net.loss_and_grad(t)
+    net.backward(x)
+    torch.cuda.synchronize()
+    Yr, lr_, gr = _ref_mlp(net, x, t)
+    torch.testing.assert_close(Y, Yr, rtol=2e-2, atol=2e-2)
+    assert abs(float(loss) - float(lr_)) <= 1e-2 * float(lr_)
+    for got, ref in zip(net.grads, gr):
+        scale = float(ref.abs().max())
+        assert float((got - ref).abs().max()) <= 2e-2 * scale, (got.shape, float((got - ref).abs().max()), scale)
+
+
+def test_training_reduces_loss(dev):
+    d = synth.c5_batch_device(16384, chunk=91, device=dev)
+    x, scale = ls.rebin(d["y"], 16384)
+    theta = torch.tensor(d["truth"], device=dev)
+    net = ls.MLP(seed=0)
+    curve = ls.train(net, x, scale, theta, epochs=10, batch=256, lr=1e-3)
+    assert curve[0][0] == 1 and net.step == 640
+    assert curve[-1][1] < 0.6 * curve[0][1], curve[:3] + curve[-3:]
