@@ -519,6 +519,7 @@ def main():
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
     ap.add_argument("--plain-hists", type=int, default=0, help="c4: histograms timed on the plain path (0 = all)")
     ap.add_argument("--train-hists", type=int, default=0, help="c5: training histograms (0 = 10^6)")
+    ap.add_argument("--epochs", type=int, default=0, help="c5: training epochs (0 = 6)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -55,8 +55,27 @@ def heuristic_start(y_flat, H):
     return th
 
 
+def canonical(theta):
+    """Peaks sorted by mu with positive widths (the fit is symmetric in s and
+    in the order of the peaks)."""
+    th = theta.clone()
+    K = K_PEAKS
+    pk = th[:, :3 * K].view(-1, K, 3).clone()
+    pk[:, :, 2] = pk[:, :, 2].abs()
+    order = torch.argsort(pk[:, :, 1], dim=1)
+    pk = torch.gather(pk, 1, order[:, :, None].expand(-1, -1, 3))
+    th[:, :3 * K] = pk.reshape(-1, 3 * K)
+    return th
+
+
+# Loss weights per encoded target (A, mu, log s per peak; b0, b1): the
+# positions and widths decide where a fit converges.
+TARGET_WEIGHTS = [1.0, 3.0, 2.0] * K_PEAKS + [1.0, 1.0]
+
+
 def encode_targets(theta, scale):
     """Fit parameters [H, 11] -> network targets before z-scoring."""
+    theta = canonical(theta)
     f = (FACTOR / scale.double())[:, None]
     t = theta.clone()
     for k in range(K_PEAKS):
@@ -172,6 +191,17 @@ def fit_batch(y_flat, H, theta0, n_steps=50, tol=1e-9):
     return f
 
 
+def choose_start(y_flat, H, th_a, th_b):
+    """Per histogram, the candidate start with the lower objective value
+    (one batched evaluation of each candidate)."""
+    offs = np.arange(H + 1, dtype=np.int64) * N_BINS
+    b = HistBatch(y_flat, offs, np.zeros(H), np.ones(H), K_PEAKS, 1, cg.OBJ_POISSON_BC, poly_mode=0)
+    fa, _ = b.gradient(th_a.contiguous())
+    fb, _ = b.gradient(th_b.contiguous())
+    take_a = torch.isfinite(fa) & (~torch.isfinite(fb) | (fa <= fb))
+    return torch.where(take_a[:, None], th_a, th_b).contiguous()
+
+
 def make_training_set(n_hist, chunk=65536, first_chunk=1, device="cuda", log=None):
     """Method-generated histograms and their converged plain fits (started at
     the truth): network inputs x (bf16), scales and fitted parameters."""
@@ -194,26 +224,32 @@ def make_training_set(n_hist, chunk=65536, first_chunk=1, device="cuda", log=Non
     return torch.cat(xs), torch.cat(ss), torch.cat(ts)
 
 
-def train(net, x, scale, theta, epochs=3, batch=1024, lr=1e-3, seed=0, log=None):
-    """AdamW on the MSE of z-scored targets; returns the loss curve (every 50 steps)."""
+def train(net, x, scale, theta, epochs=3, batch=1024, lr=1e-3, seed=0, log=None, cosine=True):
+    """AdamW on the MSE of z-scored targets (cosine-decayed learning rate);
+    returns the loss curve (first step, then every 50 steps)."""
     t = encode_targets(theta, scale)
     net.t_mean = t.mean(0).float().contiguous()
-    net.t_std = t.std(0).clamp_min(1e-6).float().contiguous()
+    w = torch.tensor(TARGET_WEIGHTS, dtype=torch.float32, device=x.device)
+    # dividing the scale by w weights the squared error of target j by w_j^2
+    net.t_std = (t.std(0).clamp_min(1e-6).float() / w).contiguous()
     tz = ((t - net.t_mean.double()) / net.t_std.double()).float().contiguous()
     N = x.shape[0]
     g = torch.Generator(device=x.device)
     g.manual_seed(seed)
     curve = []
+    total = epochs * (N // batch)
     for ep in range(epochs):
         perm = torch.randperm(N, generator=g, device=x.device)
         for i0 in range(0, N - batch + 1, batch):
+            frac = net.step / max(total, 1)
+            lr_now = lr * (0.5 * (1.0 + math.cos(math.pi * frac)) * 0.95 + 0.05) if cosine else lr
             idx = perm[i0:i0 + batch]
             xb = x.index_select(0, idx).contiguous()
             tb = tz.index_select(0, idx).contiguous()
             net.forward(xb)
             net.loss_and_grad(tb)
             net.backward(xb)
-            net.adamw(lr=lr)
+            net.adamw(lr=lr_now)
             if net.step == 1 or net.step % 50 == 0:
                 curve.append((net.step, float(net.loss)))
         if log:
@@ -239,11 +275,13 @@ def evaluate(net, H=65536, chunk=0, device="cuda", n_steps=50, tol=1e-9):
 
     fh, t_h = timed(lambda: fit_batch(y, H, heuristic_start(y, H), n_steps, tol))
 
-    def learned():
+    def proposal():
         x, scale = rebin(y, H)
-        return fit_batch(y, H, net.predict_start(x, scale), n_steps, tol)
+        return choose_start(y, H, net.predict_start(x, scale), heuristic_start(y, H))
 
-    fl, t_l = timed(learned)
+    th_l, t_prop = timed(proposal)
+    fl, t_fit = timed(lambda: fit_batch(y, H, th_l, n_steps, tol))
+    t_l = t_prop + t_fit
     Fh, Fl = fh.states.f.cpu().numpy(), fl.states.f.cpu().numpy()
     sh, sl = fh.states.status.cpu().numpy(), fl.states.status.cpu().numpy()
     ih, il = fh.states.iters.cpu().numpy(), fl.states.iters.cpu().numpy()
@@ -267,9 +305,11 @@ def evaluate(net, H=65536, chunk=0, device="cuda", n_steps=50, tol=1e-9):
     worse = Fl > Fh * (1 + 1e-6)
     Fjudged = np.where((sl != cg.FIT_CONVERGED) | worse, np.minimum(Fh, Fl), Fl)
     same = np.abs(Ffinal - Fh) <= 1e-6 * np.abs(Fh)
-    return dict(H=H, heuristic=dict(ms=t_h, mean_iters=float(ih.mean()), converged=int((sh == 1).sum()),
-                                    mean_nll=float(np.mean(Fh[np.isfinite(Fh)]))),
-                learned=dict(ms=t_l, mean_iters=float(il.mean()), converged=int((sl == 1).sum()),
+    eh, el = fh.states.n_eval.cpu().numpy(), fl.states.n_eval.cpu().numpy()
+    return dict(H=H, heuristic=dict(ms=t_h, mean_iters=float(ih.mean()), mean_evals=float(eh.mean()),
+                                    converged=int((sh == 1).sum()), mean_nll=float(np.mean(Fh[np.isfinite(Fh)]))),
+                learned=dict(ms=t_l, proposal_ms=t_prop, fit_ms=t_fit, mean_iters=float(il.mean()),
+                             mean_evals=float(el.mean()), converged=int((sl == 1).sum()),
                              mean_nll=float(np.mean(Fl[np.isfinite(Fl)]))),
                 production=dict(ms=t_l + t_r, refit=int(len(idx)), refit_ms=t_r,
                                 mean_nll=float(np.mean(Ffinal[np.isfinite(Ffinal)]))),
@@ -290,7 +330,7 @@ def bench(args):
     t_data = time.perf_counter() - t0
     net = MLP(seed=0)
     t0 = time.perf_counter()
-    curve = train(net, x, scale, theta, epochs=3)
+    curve = train(net, x, scale, theta, epochs=getattr(args, "epochs", 0) or 6, lr=2e-3)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     ev = evaluate(net)
