@@ -386,14 +386,16 @@ def run_c1(args):
     from paper_2203_06139_gb300.fit import BatchFitter, HistBatch, SingleFitter, TileMap
     h = synth.c1_histogram()
     y = torch.tensor(h["y"], device="cuda")
-    pb = cg.Problem.gauss_poly(y, 0.0, 10.0, 1, 1, cg.OBJ_CHI2)
+    prec = cg.PREC_DF64 if args.prec == "df64" else cg.PREC_FP64
+    pb = cg.Problem.gauss_poly(y, 0.0, 10.0, 1, 1, cg.OBJ_CHI2, precision=prec)
+    pb64 = cg.Problem.gauss_poly(y, 0.0, 10.0, 1, 1, cg.OBJ_CHI2)
     th = torch.tensor(synth.c1_theta_points(), device="cuda")
     v = torch.empty(100, dtype=torch.float64, device="cuda")
     g = torch.empty((100, 5), dtype=torch.float64, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     ms = _timed(lambda: cg.batch_gradient(pb, th, v, g), args.steps, max(3, args.warmup), flush)
     th0 = torch.tensor(synth.c1_theta_points(1)[0], device="cuda")
-    sf = SingleFitter(pb)
+    sf = SingleFitter(pb64)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     st = sf.fit(th0, max_iter=50, tol=1e-9)
@@ -407,7 +409,8 @@ def run_c1(args):
     ms_fit = _timed(batched, 3, 2)
     line = {"metric": METRIC, "workload": "c1", "value": 100 * 10000 / (ms / 1e3), "unit": UNIT,
             "higher_is_better": True, "ms_per_step": ms, "grad_evals_per_s": 100 / (ms / 1e3),
-            "config": {"workload": "chi2, Gaussian + linear, 10,000 bins x 100 parameter points, FP64",
+            "dtype": "f64" if prec == cg.PREC_FP64 else "df64",
+            "config": {"workload": "chi2, Gaussian + linear, 10,000 bins x 100 parameter points",
                        "l2": "flushed before every timed step"},
             "full_fit": {"plain_path_s": t_single, "plain_iters": int(st.iters[0]), "plain_evals": int(st.n_eval[0]),
                          "plain_F": float(st.f[0]), "one_cluster_fit_ms": ms_fit,

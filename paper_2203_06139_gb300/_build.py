@@ -18,7 +18,7 @@ LIB = os.path.join(PKG, "libcg.so")
 PROBE_SRC = os.path.join(PKG, "probe", "unit_rates.cu")
 PROBE_LIB = os.path.join(PKG, "libcg_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-split-compile=0"]
 
 
 def _nvcc():

@@ -14,6 +14,7 @@
 #include "cg_df64.cuh"
 #include "cg_internal.cuh"
 #include "cg_models.cuh"
+#include "cg_models_df64.cuh"
 #include "cg_tiles.cuh"
 
 namespace cg {
@@ -147,7 +148,82 @@ __global__ void __launch_bounds__(NT, 3) k_mix_df64(MixData d, const double* __r
     }
 }
 
-bool df64_supported(const cg_problem* pb) { return pb->model == CG_MODEL_MIX_GAUSS_EXP; }
+// ===========================================================================
+// 1-D Gaussian peaks + polynomial
+// ===========================================================================
+template <int K, int OBJ, int NT>
+__global__ void __launch_bounds__(NT, 2) k_gp1_df64(GP1Data d, const double* __restrict__ theta, TileGrid tg,
+                                                    double* __restrict__ part, WsHeader* __restrict__ hdr) {
+    constexpr int NACC = GP1Acc<K>::N;
+    __shared__ DfTables tab;
+    __shared__ GP1Consts cs64;
+    __shared__ GP1Df cs;
+    __shared__ int cs_bad;
+    __shared__ double red[NACC * (NT / 32)];
+    __shared__ double tot[NACC];
+    if (gated_off(tg)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
+    df_tables_init(tab);
+    const int P = 3 * K + d.D + 1;
+    for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
+        const int th = t / tg.nbx, c = t - th * tg.nbx;
+        if (threadIdx.x == 0) {
+            cs_bad = gp1_prologue<K>(theta + (size_t)th * P, d.D, cs64) ? 0 : 1;
+            gp1_split(cs64, d.lo, d.h, d.au, d.bu, K, cs);
+        }
+        __syncthreads();
+        DfAcc acc[NACC];
+        double sum[NACC];
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) {
+            acc[a].s = acc[a].c = 0.0f;
+            sum[a] = 0.0;
+        }
+        bool bad = false;
+        int cnt = 0;
+        const int64_t e0 = (int64_t)c * tg.chunk;
+        const int64_t e1 = min(tg.n_elem, e0 + tg.chunk);
+        for (int64_t i = e0 + threadIdx.x; i < e1; i += NT) {
+            const double yv = __ldg(d.y + i);
+            const df X = d.centres ? df_split(__ldg(d.centres + i)) : gp1_centre_df(cs, i);
+            if (!gp1_elem_df64<K, OBJ>(X, yv, cs, d.D, d.pm, acc, tab)) {
+                const double x = d.centres ? d.centres[i] : fma((double)i + 0.5, d.h, d.lo);
+                gp1_elem_fp64<K, OBJ>(x, yv, cs64, d, sum, bad);
+            }
+            if (++cnt == kFlush) {
+#pragma unroll
+                for (int a = 0; a < NACC; ++a) dfacc_flush(acc[a], sum[a]);
+                cnt = 0;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) dfacc_flush(acc[a], sum[a]);
+        const int any_bad = __syncthreads_or(bad ? 1 : 0) | cs_bad;
+        block_sum<NACC, NT>(sum, red, tot);
+        write_partial<NACC>(part, tg, th, c, tot, any_bad);
+    }
+}
+
+template <int K>
+static cg_status launch_gp1_df64_k(const cg_problem* pb, const GP1Data& d, const double* theta, int64_t n_theta,
+                                   double* part, WsHeader* hdr, TileGrid* tg, cudaStream_t st, const int* gate) {
+    constexpr int NT = 256;
+    const int64_t n = pb->n_bins[0];
+    switch (pb->objective) {
+        case CG_OBJ_CHI2:
+            return launch_tiles(k_gp1_df64<K, CG_OBJ_CHI2, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st, gate);
+        case CG_OBJ_POISSON:
+            return launch_tiles(k_gp1_df64<K, CG_OBJ_POISSON, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st, gate);
+        case CG_OBJ_POISSON_BC:
+            return launch_tiles(k_gp1_df64<K, CG_OBJ_POISSON_BC, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st,
+                                gate);
+        default: return CG_ERR_UNSUPPORTED;
+    }
+}
+
+bool df64_supported(const cg_problem* pb) {
+    return pb->model == CG_MODEL_MIX_GAUSS_EXP || (pb->model == CG_MODEL_GAUSS_POLY && pb->n_bins[0] < (1 << 24));
+}
 
 cg_status launch_df64(const cg_problem* pb, const double* theta, int64_t n_theta, double* part, WsHeader* hdr,
                       TileGrid* tg, cudaStream_t st, const int* gate) {
@@ -162,6 +238,26 @@ cg_status launch_df64(const cg_problem* pb, const double* theta, int64_t n_theta
         if (pb->weights)
             return launch_tiles(k_mix_df64<true, NT>, NT, d, theta, pb->n_events, n_theta, part, hdr, tg, st, gate);
         return launch_tiles(k_mix_df64<false, NT>, NT, d, theta, pb->n_events, n_theta, part, hdr, tg, st, gate);
+    }
+    if (pb->model == CG_MODEL_GAUSS_POLY) {
+        GP1Data d;
+        d.y = pb->data;
+        d.centres = pb->centres;
+        d.lo = pb->lo[0];
+        d.h = (pb->hi[0] - pb->lo[0]) / (double)pb->n_bins[0];
+        d.au = 2.0 / (pb->hi[0] - pb->lo[0]);
+        d.bu = -(pb->lo[0] + pb->hi[0]) / (pb->hi[0] - pb->lo[0]);
+        d.D = pb->poly_degree;
+        d.pm = pb->poly_mode;
+        d.vec_ok = 0;
+        switch (pb->n_peaks) {
+            case 0: return launch_gp1_df64_k<0>(pb, d, theta, n_theta, part, hdr, tg, st, gate);
+            case 1: return launch_gp1_df64_k<1>(pb, d, theta, n_theta, part, hdr, tg, st, gate);
+            case 2: return launch_gp1_df64_k<2>(pb, d, theta, n_theta, part, hdr, tg, st, gate);
+            case 3: return launch_gp1_df64_k<3>(pb, d, theta, n_theta, part, hdr, tg, st, gate);
+            case 4: return launch_gp1_df64_k<4>(pb, d, theta, n_theta, part, hdr, tg, st, gate);
+            default: return CG_ERR_INVALID_ARG;
+        }
     }
     return CG_ERR_UNSUPPORTED;
 }

@@ -29,6 +29,7 @@
 
 #include "cg_internal.cuh"
 #include "cg_models.cuh"
+#include "cg_models_df64.cuh"
 #include "cg_tiles.cuh"
 
 namespace cgx = cooperative_groups;
@@ -99,6 +100,31 @@ __device__ __forceinline__ void acc_bins(const Geom& G, const GP1Consts& cs, con
         const double x = fma((double)i + 0.5, G.hw, G.lo);
         gp1_elem_fp64<K, OBJ>(x, __ldg(G.y + i), cs, dd, acc, bad);
     }
+}
+
+// The same in double-float arithmetic (FP32 pipe), flushed into the FP64
+// accumulators every 32 bins; elements that need it fall back to FP64.
+template <int K, int OBJ>
+__device__ __forceinline__ void acc_bins_df64(const Geom& G, const GP1Consts& cs, const GP1Df& cd,
+                                              const GP1Data& dd, const DfTables& tab, int t0, int T,
+                                              double (&acc)[GP1Acc<K>::N], bool& bad) {
+    constexpr int N = GP1Acc<K>::N;
+    DfAcc da[N];
+#pragma unroll
+    for (int a = 0; a < N; ++a) da[a].s = da[a].c = 0.0f;
+    int cnt = 0;
+    for (int64_t i = t0; i < G.n; i += T) {
+        const double y = __ldg(G.y + i);
+        if (!gp1_elem_df64<K, OBJ>(gp1_centre_df(cd, i), y, cd, dd.D, dd.pm, da, tab))
+            gp1_elem_fp64<K, OBJ>(fma((double)i + 0.5, G.hw, G.lo), y, cs, dd, acc, bad);
+        if (++cnt == 32) {
+#pragma unroll
+            for (int a = 0; a < N; ++a) dfacc_flush(da[a], acc[a]);
+            cnt = 0;
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < N; ++a) dfacc_flush(da[a], acc[a]);
 }
 
 // Gauss-Newton diagonal terms of one bin: h (df/dtheta_k)^2 with h = d2T/df2.
@@ -327,19 +353,24 @@ __device__ __forceinline__ void ctl_after_eval(FitSm& s, int lane, double tol) {
 // ---------------------------------------------------------------------------
 // One objective evaluation of histogram G at s.tt by a unit (all threads).
 // ---------------------------------------------------------------------------
-template <int UNIT, int K, int OBJ>
-__device__ __forceinline__ void unit_eval(FitSm& s, GP1Consts& cs, const Geom& G, const GP1Data& dd, int D,
-                                          double* red, double* part, double* tot, int t0, int T) {
+template <int UNIT, int K, int OBJ, int PREC>
+__device__ __forceinline__ void unit_eval(FitSm& s, GP1Consts& cs, GP1Df& cd, const DfTables& tab, const Geom& G,
+                                          const GP1Data& dd, int D, double* red, double* part, double* tot, int t0,
+                                          int T) {
     constexpr int N = GP1Acc<K>::N;
     const int lane = threadIdx.x & 31;
     const bool leader = (UNIT == UNIT_WARP) ? (lane == 0) : (threadIdx.x == 0);
-    if (leader) s.bad = gp1_prologue<K>(s.tt, D, cs) ? 0 : 1;
+    if (leader) {
+        s.bad = gp1_prologue<K>(s.tt, D, cs) ? 0 : 1;
+        if (PREC == CG_PREC_DF64) gp1_split(cs, G.lo, G.hw, dd.au, dd.bu, K, cd);
+    }
     if (UNIT == UNIT_WARP) __syncwarp(); else __syncthreads();
     double acc[N];
 #pragma unroll
     for (int a = 0; a < N; ++a) acc[a] = 0.0;
     bool bad = false;
-    acc_bins<K, OBJ>(G, cs, dd, t0, T, acc, bad);
+    if (PREC == CG_PREC_DF64) acc_bins_df64<K, OBJ>(G, cs, cd, dd, tab, t0, T, acc, bad);
+    else acc_bins<K, OBJ>(G, cs, dd, t0, T, acc, bad);
     int any_bad;
     if (UNIT == UNIT_WARP) {
         any_bad = __any_sync(0xffffffffu, bad);
@@ -405,9 +436,9 @@ __device__ __forceinline__ void state_store(const FitSm& s, cg_fit_state* st, in
 }
 
 // Fit one histogram with one unit for up to a.n_steps iterations.
-template <int UNIT, int K, int OBJ>
-__device__ void unit_fit(const FitArgs& a, int64_t h, FitSm& s, GP1Consts& cs, double* red, double* part,
-                         double* tot, int t0, int T) {
+template <int UNIT, int K, int OBJ, int PREC>
+__device__ void unit_fit(const FitArgs& a, int64_t h, FitSm& s, GP1Consts& cs, GP1Df& cd, const DfTables& tab,
+                         double* red, double* part, double* tot, int t0, int T) {
     const int lane = threadIdx.x & 31;
     const bool ctl = (UNIT == UNIT_WARP) || (threadIdx.x < 32);
     const int ld_id = (UNIT == UNIT_WARP) ? lane : threadIdx.x;
@@ -433,7 +464,7 @@ __device__ void unit_fit(const FitArgs& a, int64_t h, FitSm& s, GP1Consts& cs, d
         if (ctl) ctl_direction(s, lane);
         if (UNIT != UNIT_WARP) __syncthreads();
         for (;;) {
-            unit_eval<UNIT, K, OBJ>(s, cs, G, dd, a.D, red, part, tot, t0, T);
+            unit_eval<UNIT, K, OBJ, PREC>(s, cs, cd, tab, G, dd, a.D, red, part, tot, t0, T);
             if (ctl) ctl_after_eval(s, lane, a.tol);
             if (UNIT == UNIT_WARP) __syncwarp(); else __syncthreads();
             if (s.go != 0) break;
@@ -447,7 +478,7 @@ __device__ void unit_fit(const FitArgs& a, int64_t h, FitSm& s, GP1Consts& cs, d
 
 // Shared-memory layout of the persistent kernel (dynamic).
 struct SmLayout {
-    size_t cta_sm, warp_sm, cta_cs, warp_cs, red, part, tot, warp_tot, item, total;
+    size_t cta_sm, warp_sm, cta_cs, warp_cs, cta_cd, warp_cd, tab, red, part, tot, warp_tot, item, total;
 };
 
 __host__ __device__ inline SmLayout sm_layout(int nwarps, int nacc) {
@@ -458,6 +489,9 @@ __host__ __device__ inline SmLayout sm_layout(int nwarps, int nacc) {
     L.warp_sm = take(sizeof(FitSm) * nwarps);
     L.cta_cs = take(sizeof(GP1Consts));
     L.warp_cs = take(sizeof(GP1Consts) * nwarps);
+    L.cta_cd = take(sizeof(GP1Df));
+    L.warp_cd = take(sizeof(GP1Df) * nwarps);
+    L.tab = take(sizeof(DfTables));
     L.red = take(sizeof(double) * (nacc + 1) * kMaxWarpsPerCta);
     L.part = take(sizeof(double) * (nacc + 1));
     L.tot = take(sizeof(double) * (nacc + 1));
@@ -468,7 +502,7 @@ __host__ __device__ inline SmLayout sm_layout(int nwarps, int nacc) {
 }
 
 // Persistent batched fit: clusters, then CTAs, then warps pop histograms.
-template <int K, int OBJ, bool CLUSTERS>
+template <int K, int OBJ, bool CLUSTERS, int PREC>
 __global__ void __launch_bounds__(512) k_fit_persistent(FitArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int N = GP1Acc<K>::N;
@@ -480,7 +514,13 @@ __global__ void __launch_bounds__(512) k_fit_persistent(FitArgs a) {
     double* part = reinterpret_cast<double*>(smem + L.part);
     double* tot = reinterpret_cast<double*>(smem + L.tot);
     int* item = reinterpret_cast<int*>(smem + L.item);
+    GP1Df& cta_cd = *reinterpret_cast<GP1Df*>(smem + L.cta_cd);
+    DfTables& tab = *reinterpret_cast<DfTables*>(smem + L.tab);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (PREC == CG_PREC_DF64) {
+        df_tables_init(tab);
+        __syncthreads();
+    }
 
     const int n0 = a.n_items[0], n1 = a.n_items[1], n2 = a.n_items[2];
     if (CLUSTERS) {
@@ -493,8 +533,8 @@ __global__ void __launch_bounds__(512) k_fit_persistent(FitArgs a) {
             const int it = *cl.map_shared_rank(item, 0);
             cl.sync();
             if (it >= n0) break;
-            unit_fit<UNIT_CLUSTER, K, OBJ>(a, a.queue[0][it], cta_s, cta_cs, red, part, tot,
-                                           rank * blockDim.x + threadIdx.x, csz * blockDim.x);
+            unit_fit<UNIT_CLUSTER, K, OBJ, PREC>(a, a.queue[0][it], cta_s, cta_cs, cta_cd, tab, red, part, tot,
+                                                 rank * blockDim.x + threadIdx.x, csz * blockDim.x);
         }
     }
     for (;;) {
@@ -503,17 +543,19 @@ __global__ void __launch_bounds__(512) k_fit_persistent(FitArgs a) {
         const int it = *item;
         __syncthreads();
         if (it >= n1) break;
-        unit_fit<UNIT_CTA, K, OBJ>(a, a.queue[1][it], cta_s, cta_cs, red, part, tot, threadIdx.x, blockDim.x);
+        unit_fit<UNIT_CTA, K, OBJ, PREC>(a, a.queue[1][it], cta_s, cta_cs, cta_cd, tab, red, part, tot, threadIdx.x,
+                                         blockDim.x);
     }
     FitSm& ws_ = reinterpret_cast<FitSm*>(smem + L.warp_sm)[wid];
     GP1Consts& wcs = reinterpret_cast<GP1Consts*>(smem + L.warp_cs)[wid];
+    GP1Df& wcd = reinterpret_cast<GP1Df*>(smem + L.warp_cd)[wid];
     double* wtot = reinterpret_cast<double*>(smem + L.warp_tot) + wid * (N + 1);
     for (;;) {
         int it = 0;
         if (lane == 0) it = atomicAdd(&a.counters[2], 1);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= n2) break;
-        unit_fit<UNIT_WARP, K, OBJ>(a, a.queue[2][it], ws_, wcs, nullptr, nullptr, wtot, lane, 32);
+        unit_fit<UNIT_WARP, K, OBJ, PREC>(a, a.queue[2][it], ws_, wcs, wcd, tab, nullptr, nullptr, wtot, lane, 32);
     }
 }
 
@@ -728,12 +770,12 @@ cg_status launch_eval(const cg_problem* t, const FitArgs& a, int mode, cudaStrea
     return CG_ERR_UNSUPPORTED;
 }
 
-template <int K, int OBJ, bool CL>
+template <int K, int OBJ, bool CL, int PREC>
 cg_status launch_persistent_k(const FitArgs& a, const cg_tile_map* m, cudaStream_t st) {
     constexpr int N = GP1Acc<K>::N;
     const int nt = m->cta_threads;
     const SmLayout L = sm_layout(nt / 32, N);
-    auto kern = k_fit_persistent<K, OBJ, CL>;
+    auto kern = k_fit_persistent<K, OBJ, CL, PREC>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) != cudaSuccess)
         return CG_ERR_CUDA;
     const int csz = CL ? m->cluster_size : 1;
@@ -773,9 +815,14 @@ cg_status launch_persistent_k(const FitArgs& a, const cg_tile_map* m, cudaStream
 cg_status launch_persistent(const cg_problem* t, const FitArgs& a, const cg_tile_map* m, cudaStream_t st) {
     const int K = t->n_peaks, O = t->objective;
     const bool CL = m->cluster_size > 1;
-#define CG_P_CASE(KK, OO)                                                             \
-    if (K == KK && O == OO)                                                           \
-        return CL ? launch_persistent_k<KK, OO, true>(a, m, st) : launch_persistent_k<KK, OO, false>(a, m, st);
+    const bool DF = t->precision == CG_PREC_DF64;
+#define CG_P_CASE(KK, OO)                                                                                  \
+    if (K == KK && O == OO) {                                                                              \
+        if (DF) return CL ? launch_persistent_k<KK, OO, true, CG_PREC_DF64>(a, m, st)                      \
+                          : launch_persistent_k<KK, OO, false, CG_PREC_DF64>(a, m, st);                     \
+        return CL ? launch_persistent_k<KK, OO, true, CG_PREC_FP64>(a, m, st)                              \
+                  : launch_persistent_k<KK, OO, false, CG_PREC_FP64>(a, m, st);                             \
+    }
     CG_P_CASE(1, CG_OBJ_CHI2) CG_P_CASE(1, CG_OBJ_POISSON) CG_P_CASE(1, CG_OBJ_POISSON_BC)
     CG_P_CASE(2, CG_OBJ_CHI2) CG_P_CASE(2, CG_OBJ_POISSON) CG_P_CASE(2, CG_OBJ_POISSON_BC)
     CG_P_CASE(3, CG_OBJ_CHI2) CG_P_CASE(3, CG_OBJ_POISSON) CG_P_CASE(3, CG_OBJ_POISSON_BC)

@@ -20,6 +20,15 @@ def dev():
     return torch.device("cuda:0")
 
 
+def _fd_ok(g, fd, F, th, scale):
+    """Central differences at h_k = 1e-6 |theta_k| agree with g to 1e-5 (relative,
+    floored at 1e-6 S_k) plus their own rounding error: F is known to an ulp or
+    so at each point, so the difference quotient carries ~8 eps |F| / h_k."""
+    h = 1e-6 * np.maximum(np.abs(th), 1e-3)
+    allowed = 1e-5 * np.maximum(np.abs(g), 1e-6 * scale) + 8 * np.finfo(float).eps * abs(F) / h
+    return np.all(np.abs(g - fd) <= allowed), np.max(np.abs(g - fd) / allowed)
+
+
 def _fd(pb, th):
     g = np.zeros(th.numel())
     base = th.detach().cpu().numpy()
@@ -47,9 +56,8 @@ def test_autograd_matches_fd_and_oracle(dev, K, nx, ny):
     ref = oracle.binned2d(K, counts, 0.0, 1.0, 0.0, 1.0, th0)
     assert max_rel_err(g, ref.grad, ref.scale) <= 1e-10
     assert abs(float(F) - ref.value) <= 1e-10 * abs(ref.value)
-    # central differences at h = 1e-6 relative carry their own cancellation
-    # error eps |F| / h (about 1e-11 / 1e-8 for the width parameters here)
-    assert max_rel_err(g, _fd(pb, theta), ref.scale) <= 1e-4
+    ok, worst = _fd_ok(g, _fd(pb, theta), ref.value, th0, ref.scale)
+    assert ok, worst
 
 
 def test_autograd_chain_rule_and_batch(dev):
@@ -72,8 +80,9 @@ def test_autograd_c3_full_size(dev):
     th0 = synth.c3_theta_point(hh["truth"])[0]
     pb = cg.Problem.rotgauss2d(torch.tensor(hh["counts"], device=dev), 8)
     theta = torch.tensor(th0, device=dev, requires_grad=True)
-    fit_objective(theta, pb).backward()
+    F = fit_objective(theta, pb)
+    F.backward()
     g = theta.grad.detach().cpu().numpy()
     fd = _fd(pb, theta)
-    scale = np.abs(g) + 1e-3 * np.abs(g).max()
-    assert np.max(np.abs(g - fd) / scale) <= 1e-4
+    ok, worst = _fd_ok(g, fd, float(F.detach()), th0, np.abs(g))
+    assert ok, worst

@@ -141,3 +141,21 @@ def test_autotuner_returns_a_valid_map(dev, tmp_path, monkeypatch):
     assert len(timings) >= 4 and isinstance(best, TileMap)
     best2, _ = autotune(b, torch.tensor(d["start"], device=dev), n_steps=2)
     assert best2.as_dict() == best.as_dict()
+
+
+@pytest.mark.parametrize("obj,K,D,pm", [(cg.OBJ_CHI2, 1, 2, 1), (cg.OBJ_POISSON_BC, 3, 1, 0)])
+def test_batched_fit_df64_reaches_oracle_minimum(dev, obj, K, D, pm):
+    if K == 1:
+        d = small_c4(H=24)
+        start = d["start"]
+    else:
+        d = synth.c5_batch(H=12, n_bins=2048)
+        start = d["truth"] * np.random.default_rng(1).uniform(0.97, 1.03, d["truth"].shape)
+    b = HistBatch(d["y"], d["offsets"], d["lo"], d["hi"], K, D, obj, poly_mode=pm, precision=cg.PREC_DF64)
+    f = BatchFitter(b, TileMap(1024, 8192, 256, 4))
+    f.init(torch.tensor(start, device=dev))
+    F = f.step(200, 1e-12).f.cpu().numpy()
+    for h in range(0, d["H"], 3):
+        y = d["y"][d["offsets"][h]:d["offsets"][h + 1]]
+        ref = oracle_fit(y, K, D, pm, OBJ_MAP[obj], 0.0, 1.0, start[h], max_iter=400)
+        assert abs(F[h] - ref["F"]) <= 1e-6 * abs(ref["F"]), (h, F[h], ref["F"])

@@ -273,3 +273,36 @@ def test_c2_df64_full_size_and_error_vs_fp64(dev, record_property):
     record_property("df64_vs_fp64_max_rel_value", err_v)
     print("df64 vs fp64: max rel grad %.3e, value %.3e" % (err_g, err_v))
     assert err_g < 1e-11 and err_v < 1e-12
+
+
+@pytest.mark.parametrize("obj", [cg.OBJ_CHI2, cg.OBJ_POISSON, cg.OBJ_POISSON_BC])
+@pytest.mark.parametrize("K,D,pm", [(1, 1, 0), (2, 2, 1), (3, 1, 0), (4, 3, 1), (0, 2, 1), (1, -1, 0)])
+def test_gauss_poly_df64_small(dev, obj, K, D, pm):
+    n = 3001
+    p = synth.random_gauss_poly(max(K, 1), D, n, lo=-2.0, hi=3.0, poly_mode=pm, seed=10 * K + D + pm)
+    if K == 0:
+        th0 = p["theta"][3:].copy()
+        th0[0] = abs(th0[0]) + 50.0
+        y = np.random.default_rng(4).poisson(np.maximum(
+            synth.expected_counts_1d(0, D, pm, -2.0, 3.0, n, th0), 1.0)).astype(float)
+        thetas = np.stack([th0, th0 * 1.03])
+    else:
+        y = p["y"]
+        thetas = np.stack([p["theta"], p["truth"] * 1.02])
+    pb = cg.Problem.gauss_poly(torch.tensor(y, device=dev), -2.0, 3.0, K, D, obj, poly_mode=pm,
+                               precision=cg.PREC_DF64)
+    v, g = cg.batch_gradient(pb, torch.tensor(thetas, device=dev))
+    assert pb.status(len(thetas)) == cg.OK
+    for i in range(len(thetas)):
+        check(v[i], g[i], oracle.binned1d(K, D, pm, OBJ_MAP[obj], y, -2.0, 3.0, thetas[i]))
+
+
+def test_c1_df64_full_size_all_points(dev):
+    h = synth.c1_histogram()
+    th = synth.c1_theta_points()
+    pb = cg.Problem.gauss_poly(torch.tensor(h["y"], device=dev), 0.0, 10.0, 1, 1, cg.OBJ_CHI2, precision=cg.PREC_DF64)
+    v, g = cg.batch_gradient(pb, torch.tensor(th, device=dev))
+    refs = oracle.many(oracle.binned1d, th, K=1, D=1, poly_mode=0, obj=oracle.CHI2, y=h["y"], lo=0.0, hi=10.0)
+    g = g.cpu().numpy()
+    for i, ref in enumerate(refs):
+        check(v[i], g[i], ref)
