@@ -457,7 +457,7 @@ def run_c4(args):
     from paper_2203_06139_gb300 import cg, synth
     from paper_2203_06139_gb300.fit import BatchFitter, HistBatch, SingleFitter, autotune
     d = synth.c4_batch()
-    prec = cg.PREC_FP64   # the fit kernels evaluate in FP64
+    prec = cg.PREC_DF64 if args.prec == "df64" else cg.PREC_FP64
     b = HistBatch(d["y"], d["offsets"], d["lo"], d["hi"], 1, 2, cg.OBJ_CHI2, poly_mode=1, precision=prec)
     th0 = torch.tensor(d["start"], device="cuda")
     best, timings = autotune(b, th0, n_steps=3)

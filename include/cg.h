@@ -255,6 +255,12 @@ cg_status cg_decode_start(const float *y, int ld, const float *scale, const floa
                           int64_t H, int n_peaks, int factor, int n_bins, double lo, double hi, double *theta0,
                           void *stream);
 
+/* Per histogram h, theta_out[h] = theta_a[h] if fa[h] <= fb[h] (a non-finite
+ * value loses), else theta_b[h]: the objective judges two candidate starts.
+ * took_a (optional, device [H]) records the choice. */
+cg_status cg_select_start(const double *fa, const double *fb, const double *theta_a, const double *theta_b,
+                          int64_t H, int P, double *theta_out, int *took_a, void *stream);
+
 /* b[i] = bf16(a[i]). */
 cg_status cg_to_bf16(const float *a, int64_t n, void *b, void *stream);
 

@@ -81,6 +81,7 @@ def lib():
         "cg_adamw": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                     ctypes.c_float, ctypes.c_float, ctypes.c_int, _vp, _vp]),
         "cg_to_bf16": (ctypes.c_int, [_vp, _i64, _vp, _vp]),
+        "cg_select_start": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, ctypes.c_int, _vp, _vp, _vp]),
         "cg_decode_start": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp, _i64, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int, ctypes.c_double, ctypes.c_double, _vp, _vp]),
         "cg_gemm_bf16": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,

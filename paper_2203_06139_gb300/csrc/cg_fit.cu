@@ -561,11 +561,17 @@ __global__ void __launch_bounds__(512) k_fit_persistent(FitArgs a) {
 
 // Init (GN + first evaluation) and plain evaluation: one CTA per histogram,
 // grid-stride over histograms.  mode 0: value/grad at a.theta; mode 1: init.
-template <int K, int OBJ>
+template <int K, int OBJ, int PREC>
 __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a, int mode) {
     constexpr int N = GP1Acc<K>::N;
     __shared__ GP1Consts cs;
+    __shared__ GP1Df cd;
+    __shared__ DfTables tab;
     __shared__ int cs_bad;
+    if (PREC == CG_PREC_DF64) {
+        df_tables_init(tab);
+        __syncthreads();
+    }
     __shared__ double red[(N + 1) * kMaxWarpsPerCta];
     __shared__ double tot[N + 1];
     __shared__ double gn[N + 1];
@@ -582,13 +588,17 @@ __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a, int mode) {
         dd.D = a.D;
         dd.pm = a.pm;
         dd.vec_ok = 0;
-        if (threadIdx.x == 0) cs_bad = gp1_prologue<K>(th, a.D, cs) ? 0 : 1;
+        if (threadIdx.x == 0) {
+            cs_bad = gp1_prologue<K>(th, a.D, cs) ? 0 : 1;
+            if (PREC == CG_PREC_DF64) gp1_split(cs, G.lo, G.hw, dd.au, dd.bu, K, cd);
+        }
         __syncthreads();
         double acc[N];
 #pragma unroll
         for (int i = 0; i < N; ++i) acc[i] = 0.0;
         bool bad = false;
-        acc_bins<K, OBJ>(G, cs, dd, threadIdx.x, blockDim.x, acc, bad);
+        if (PREC == CG_PREC_DF64 && mode == 0) acc_bins_df64<K, OBJ>(G, cs, cd, dd, tab, threadIdx.x, blockDim.x, acc, bad);
+        else acc_bins<K, OBJ>(G, cs, dd, threadIdx.x, blockDim.x, acc, bad);
         const int any_bad = __syncthreads_or(bad) | cs_bad;
         reduce_cta<N>(acc, red, tot);
         if (mode == 1) {
@@ -753,16 +763,17 @@ FitArgs base_args(const cg_batch* b) {
 }
 
 template <int K, int OBJ>
-cg_status launch_eval_k(const FitArgs& a, int mode, cudaStream_t st) {
+cg_status launch_eval_k(const FitArgs& a, int mode, int prec, cudaStream_t st) {
     const int G = device_sm_count() * 4;
     const int grid = (int)(a.H < G ? a.H : G);
-    k_fit_eval<K, OBJ><<<grid, 256, 0, st>>>(a, mode);
+    if (prec == CG_PREC_DF64 && mode == 0) k_fit_eval<K, OBJ, CG_PREC_DF64><<<grid, 256, 0, st>>>(a, mode);
+    else k_fit_eval<K, OBJ, CG_PREC_FP64><<<grid, 256, 0, st>>>(a, mode);
     return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
 }
 
 cg_status launch_eval(const cg_problem* t, const FitArgs& a, int mode, cudaStream_t st) {
     const int K = t->n_peaks, O = t->objective;
-#define CG_EVAL_CASE(KK, OO) if (K == KK && O == OO) return launch_eval_k<KK, OO>(a, mode, st);
+#define CG_EVAL_CASE(KK, OO) if (K == KK && O == OO) return launch_eval_k<KK, OO>(a, mode, t->precision, st);
     CG_EVAL_CASE(1, CG_OBJ_CHI2) CG_EVAL_CASE(1, CG_OBJ_POISSON) CG_EVAL_CASE(1, CG_OBJ_POISSON_BC)
     CG_EVAL_CASE(2, CG_OBJ_CHI2) CG_EVAL_CASE(2, CG_OBJ_POISSON) CG_EVAL_CASE(2, CG_OBJ_POISSON_BC)
     CG_EVAL_CASE(3, CG_OBJ_CHI2) CG_EVAL_CASE(3, CG_OBJ_POISSON) CG_EVAL_CASE(3, CG_OBJ_POISSON_BC)

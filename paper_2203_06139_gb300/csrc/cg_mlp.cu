@@ -566,3 +566,28 @@ extern "C" cg_status cg_decode_start(const float* y, int ld, const float* scale,
                                                                               factor, n_bins, lo, hi, theta0);
     return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
 }
+
+namespace cg {
+namespace {
+// Per histogram, the candidate whose objective value is lower (a non-finite
+// value loses); ties keep candidate a.
+__global__ void k_select(const double* fa, const double* fb, const double* ta, const double* tb, int64_t H, int P,
+                         double* out, int* took_a) {
+    const int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (h >= H) return;
+    const double a = fa[h], b = fb[h];
+    const bool pick_a = isfinite(a) && (!isfinite(b) || a <= b);
+    const double* src = pick_a ? ta + h * P : tb + h * P;
+    for (int k = 0; k < P; ++k) out[h * P + k] = src[k];
+    if (took_a) took_a[h] = pick_a ? 1 : 0;
+}
+}  // namespace
+}  // namespace cg
+
+extern "C" cg_status cg_select_start(const double* fa, const double* fb, const double* theta_a, const double* theta_b,
+                                     int64_t H, int P, double* theta_out, int* took_a, void* stream) {
+    if (!fa || !fb || !theta_a || !theta_b || !theta_out || H < 1 || P < 1) return CG_ERR_INVALID_ARG;
+    cg::k_select<<<(unsigned)((H + 255) / 256), 256, 0, (cudaStream_t)stream>>>(fa, fb, theta_a, theta_b, H, P,
+                                                                              theta_out, took_a);
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
