@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(NT, 3) k_mix_df64(MixData d, const double* __r
     if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
     df_tables_init(tab);
     for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
-        const int th = t / tg.nbx, c = t - th * tg.nbx;
+        const int c = t / tg.n_theta, th = t - c * tg.n_theta;   // chunk-major: a chunk stays in L2 across points
         if (threadIdx.x == 0) {
             cs_bad = mix_prologue(theta + (size_t)th * 4, d.lo, d.hi, cs64) ? 0 : 1;
             mix_split(cs64, cs);
@@ -123,8 +123,11 @@ __global__ void __launch_bounds__(NT, 3) k_mix_df64(MixData d, const double* __r
         int cnt = 0;
         const int64_t e0 = (int64_t)c * tg.chunk;
         const int64_t e1 = min(tg.n_elem, e0 + tg.chunk);
+        double xn = (e0 + threadIdx.x < e1) ? __ldg(d.x + e0 + threadIdx.x) : 0.0;
         for (int64_t i = e0 + threadIdx.x; i < e1; i += NT) {
-            mix_elem_df64<W>(__ldg(d.x + i), W ? __ldg(d.w + i) : 1.0, cr, cs64, tab, acc, P, sum, &bad);
+            const double xi = xn;
+            if (i + NT < e1) xn = __ldg(d.x + i + NT);   // next event in flight during this one
+            mix_elem_df64<W>(xi, W ? __ldg(d.w + i) : 1.0, cr, cs64, tab, acc, P, sum, &bad);
             if (++cnt == kFlush) {
                 if (!W) {
                     dfacc_add(acc[0], dfprod_log(P, tab));
@@ -166,7 +169,7 @@ __global__ void __launch_bounds__(NT, 2) k_gp1_df64(GP1Data d, const double* __r
     df_tables_init(tab);
     const int P = 3 * K + d.D + 1;
     for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
-        const int th = t / tg.nbx, c = t - th * tg.nbx;
+        const int c = t / tg.n_theta, th = t - c * tg.n_theta;   // chunk-major: a chunk stays in L2 across points
         if (threadIdx.x == 0) {
             cs_bad = gp1_prologue<K>(theta + (size_t)th * P, d.D, cs64) ? 0 : 1;
             gp1_split(cs64, d.lo, d.h, d.au, d.bu, K, cs);

@@ -48,11 +48,14 @@ __device__ __forceinline__ double df_to_double(df a) { return (double)a.h + (dou
 // instruction): hi = the leading 24 significand bits, lo = the next 29 bits
 // rounded to 23; |x - (hi + lo)| <= 2^-47 |x|.  Doubles with exponents
 // outside [-80, 127] go through the conversion instructions instead.
+static __device__ __noinline__ df df_from_double_slow(double x) { return df_from_double(x); }
+
 __device__ __forceinline__ df df_split(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
     const int e = (int)((hw >> 20) & 0x7ffu) - 1023;
-    if (e < -80 || e > 127) return df_from_double(x);
+    // rare: a call is never if-converted, so its conversions stay off the common path
+    if (e < -80 || e > 127) return df_from_double_slow(x);
     const unsigned sign = hw & 0x80000000u;
     const float h = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29));
     // remaining 29 bits r of the significand; value r 2^(e-52)

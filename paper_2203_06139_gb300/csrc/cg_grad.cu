@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(NT) k_gp1_fp64(GP1Data d, const double* __rest
     if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
     const int P = 3 * K + d.D + 1;
     for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
-        const int th = t / tg.nbx, c = t - th * tg.nbx;
+        const int c = t / tg.n_theta, th = t - c * tg.n_theta;   // chunk-major: a chunk stays in L2 across points
         if (threadIdx.x == 0) cs_bad = gp1_prologue<K>(theta + (size_t)th * P, d.D, cs) ? 0 : 1;
         __syncthreads();
         double acc[NACC];
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(NT) k_mix_fp64(MixData d, const double* __rest
     if (gated_off(tg)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
     for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
-        const int th = t / tg.nbx, c = t - th * tg.nbx;
+        const int c = t / tg.n_theta, th = t - c * tg.n_theta;   // chunk-major: a chunk stays in L2 across points
         if (threadIdx.x == 0) cs_bad = mix_prologue(theta + (size_t)th * 4, d.lo, d.hi, cs) ? 0 : 1;
         __syncthreads();
         double acc[NACC];
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(NT) k_rg2_fp64(RG2Data d, const double* __rest
     if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
     const int P = 6 * K + 1;
     for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
-        const int th = t / tg.nbx, c = t - th * tg.nbx;
+        const int c = t / tg.n_theta, th = t - c * tg.n_theta;   // chunk-major: a chunk stays in L2 across points
         if (threadIdx.x == 0) cs_bad = rg2_prologue<K>(theta + (size_t)th * P, cs) ? 0 : 1;
         __syncthreads();
         double acc[NACC];
