@@ -57,7 +57,7 @@ __device__ __forceinline__ void mix_elem_df64(double x, double w, const MixDf& c
     const df X = df_split(x);
     const df d = df_sub(X, c.mu);
     const df q = df_mul(c.c, df_sqr(d));
-    const df xl = df_sub(X, c.lo);
+    const df xl = (c.lo.h == 0.0f && c.lo.l == 0.0f) ? X : df_sub(X, c.lo);   // uniform per tile
     const df t = df_mul(c.mlam, xl);
     bool flG = false, flE = false;
     const df eG = df_exp(q, tab, flG);

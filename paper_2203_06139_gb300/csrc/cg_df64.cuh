@@ -203,7 +203,7 @@ __device__ __forceinline__ df df_exp(df q, const DfTables& tab, bool& flushed) {
     tail = fmaf(rh, tail, 1.0f / 6.0f);
     tail = __fmul_rn(__fmul_rn(__fmul_rn(rh, rh), rh), tail);
     df sq = two_prod(rh, rh);
-    df u = two_sum(rh, __fmul_rn(0.5f, sq.h));
+    df u = fast_two_sum(rh, __fmul_rn(0.5f, sq.h));   // exact: |r| > r^2/2 for |r| < ln2/128
     lo = __fadd_rn(__fadd_rn(u.l, r.l), __fadd_rn(fmaf(0.5f, sq.l, __fmul_rn(rh, r.l)), tail));
     const df em1 = fast_two_sum(u.h, lo);
     // 2^(j/64) (1 + em1)

@@ -34,21 +34,40 @@ inline int max_nbx(int64_t n_theta) {
     return (int)(m < 1 ? 1 : m);
 }
 
-// Choose the tile grid: ~4 tiles per resident block, at least 8 elements per
-// thread per tile, chunk a multiple of 2*NT (keeps 16-byte alignment).
+// Choose the tile grid: among chunk counts per point that keep at least 8
+// elements per thread per tile (and the workspace bound), the one whose tile
+// count best fills whole waves of the persistent grid (every CTA gets the
+// same number of tiles), preferring about 4 waves; chunk a multiple of
+// 2*NT (keeps 16-byte alignment).
 inline TileGrid make_tiles(int64_t n_elem, int64_t n_theta, int NT, int grid_blocks) {
     TileGrid tg;
     tg.n_elem = n_elem;
-    int64_t want = ((int64_t)grid_blocks * 4 + n_theta - 1) / n_theta;
-    int64_t per_tile_min = (int64_t)NT * 8;
+    const int64_t per_tile_min = (int64_t)NT * 8;
     int64_t most = (n_elem + per_tile_min - 1) / per_tile_min;
-    int64_t nbx = want < most ? want : most;
-    if (nbx < 1) nbx = 1;
-    if (nbx > max_nbx(n_theta)) nbx = max_nbx(n_theta);
-    int64_t chunk = (n_elem + nbx - 1) / nbx;
+    if (most > max_nbx(n_theta)) most = max_nbx(n_theta);
+    if (most < 1) most = 1;
+    const int64_t G = grid_blocks > 0 ? grid_blocks : 1;
+    int64_t best = 1;
+    double best_score = -1.0;
+    for (int64_t nbx = 1; nbx <= most; ++nbx) {
+        // the chunk that nbx implies (rounded to 2*NT) and the tile count it really gives
+        int64_t chunk = (n_elem + nbx - 1) / nbx;
+        chunk = (chunk + 2 * NT - 1) / (2 * NT) * (2 * NT);
+        const int64_t real = (n_elem + chunk - 1) / chunk;
+        if (real != nbx) continue;
+        const int64_t nt = n_theta * nbx;
+        const int64_t waves = (nt + G - 1) / G;
+        const double eff = (double)nt / (double)(waves * G);
+        const double score = eff - 0.002 * (double)(waves > 4 ? waves - 4 : 4 - waves);
+        if (score > best_score + 1e-12) {
+            best_score = score;
+            best = nbx;
+        }
+    }
+    int64_t chunk = (n_elem + best - 1) / best;
     chunk = (chunk + 2 * NT - 1) / (2 * NT) * (2 * NT);
     if (chunk < 2 * NT) chunk = 2 * NT;
-    nbx = (n_elem + chunk - 1) / chunk;
+    int64_t nbx = (n_elem + chunk - 1) / chunk;
     if (nbx < 1) nbx = 1;
     tg.chunk = chunk;
     tg.nbx = (int)nbx;
