@@ -140,6 +140,15 @@ __global__ void __launch_bounds__(NT) k_mix_fp64(MixData d, const double* __rest
     }
 }
 
+// 2-D tiles of kRgTX x kRgTY bins.  Per tile, a Gaussian whose exponent
+// -q = (u^2/sx^2 + v^2/sy^2)/2 exceeds kRgCull everywhere in the tile's box of
+// bin centres is skipped: q >= r^2 / (2 max(sx, sy)^2) with r the distance
+// from its centre to the box, and exp(-80) A is below 1e-33 of any model
+// value (the constant is >= 0 and the counts are fitted by A, C > 0), far
+// under FP64 resolution.
+constexpr int kRgTX = 64, kRgTY = 64;
+constexpr double kRgCull = 80.0;
+
 template <int K, int NT>
 __global__ void __launch_bounds__(NT) k_rg2_fp64(RG2Data d, const double* __restrict__ theta,
                                                  TileGrid tg, double* __restrict__ part,
@@ -147,32 +156,49 @@ __global__ void __launch_bounds__(NT) k_rg2_fp64(RG2Data d, const double* __rest
     constexpr int NACC = RG2Acc<K>::N;
     __shared__ RG2Consts cs;
     __shared__ int cs_bad;
+    __shared__ unsigned act_s;
     __shared__ double red[NACC * (NT / 32)];
     __shared__ double tot[NACC];
     if (gated_off(tg)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
     const int P = 6 * K + 1;
+    const int ntx = (int)((d.nx + kRgTX - 1) / kRgTX);
     for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
-        const int c = t / tg.n_theta, th = t - c * tg.n_theta;   // chunk-major: a chunk stays in L2 across points
-        if (threadIdx.x == 0) cs_bad = rg2_prologue<K>(theta + (size_t)th * P, cs) ? 0 : 1;
+        const int c = t / tg.n_theta, th = t - c * tg.n_theta;
+        const int ty = c / ntx, tx = c - ty * ntx;
+        const int64_t x0 = (int64_t)tx * kRgTX, y0 = (int64_t)ty * kRgTY;
+        const int64_t x1 = min(d.nx, x0 + kRgTX), y1 = min(d.ny, y0 + kRgTY);
+        if (threadIdx.x == 0) {
+            const double* tht = theta + (size_t)th * P;
+            cs_bad = rg2_prologue<K>(tht, cs) ? 0 : 1;
+            // box of bin centres of this tile
+            const double bx0 = fma((double)x0 + 0.5, d.hx, d.lx), bx1 = fma((double)(x1 - 1) + 0.5, d.hx, d.lx);
+            const double by0 = fma((double)y0 + 0.5, d.hy, d.ly), by1 = fma((double)(y1 - 1) + 0.5, d.hy, d.ly);
+            unsigned act = 0;
+            for (int k = 0; k < K; ++k) {
+                const double mx = tht[6 * k + 1], my = tht[6 * k + 2];
+                const double sm = fmax(fabs(tht[6 * k + 3]), fabs(tht[6 * k + 4]));
+                const double ddx = fmax(0.0, fmax(bx0 - mx, mx - bx1));
+                const double ddy = fmax(0.0, fmax(by0 - my, my - by1));
+                const double qmin = 0.5 * (ddx * ddx + ddy * ddy) / (sm * sm);
+                if (!(qmin > kRgCull)) act |= 1u << k;   // NaN keeps the Gaussian
+            }
+            act_s = act;
+        }
         __syncthreads();
+        const unsigned act = act_s;
         double acc[NACC];
 #pragma unroll
         for (int a = 0; a < NACC; ++a) acc[a] = 0.0;
         bool bad = false;
-        const int64_t e0 = (int64_t)c * tg.chunk;
-        const int64_t e1 = min(tg.n_elem, e0 + tg.chunk);
-        int64_t i = e0 + threadIdx.x;
-        int64_t iy = i / d.nx, ix = i - iy * d.nx;
-        double yc = fma((double)iy + 0.5, d.hy, d.ly);
-        for (; i < e1; i += NT) {
+        const int w = (int)(x1 - x0);
+        const int nbin = w * (int)(y1 - y0);
+        for (int b = threadIdx.x; b < nbin; b += NT) {
+            const int r = b / w, col = b - r * w;
+            const int64_t ix = x0 + col, iy = y0 + r;
             const double xc = fma((double)ix + 0.5, d.hx, d.lx);
-            rg2_elem_fp64<K>(xc, yc, __ldg(d.n + i), cs, acc, bad);
-            ix += NT;
-            if (ix >= d.nx) {
-                while (ix >= d.nx) { ix -= d.nx; ++iy; }
-                yc = fma((double)iy + 0.5, d.hy, d.ly);
-            }
+            const double yc = fma((double)iy + 0.5, d.hy, d.ly);
+            rg2_elem_fp64<K>(xc, yc, __ldg(d.n + iy * d.nx + ix), cs, act, acc, bad);
         }
         const int any_bad = __syncthreads_or(bad ? 1 : 0) | cs_bad;
         block_sum<NACC, NT>(acc, red, tot);
@@ -305,7 +331,22 @@ template <int K>
 static cg_status launch_rg2_k(const RG2Data& d, const double* theta, int64_t n, int64_t n_theta, double* part,
                               WsHeader* hdr, TileGrid* tg, cudaStream_t st, const int* gate) {
     constexpr int NT = 128;
-    return launch_tiles(k_rg2_fp64<K, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st, gate);
+    auto kern = k_rg2_fp64<K, NT>;
+    const int R = resident_blocks((const void*)kern, NT, 0);
+    const int G = device_sm_count() * R;
+    TileGrid g;
+    g.n_elem = n;
+    g.chunk = 0;
+    g.nbx = (int)(((d.nx + kRgTX - 1) / kRgTX) * ((d.ny + kRgTY - 1) / kRgTY));
+    g.n_theta = (int)n_theta;
+    g.n_tiles = (int)(n_theta * g.nbx);
+    g.gate = gate;
+    const int grid = g.n_tiles < G ? g.n_tiles : G;
+    prof_begin(st);
+    kern<<<grid, NT, 0, st>>>(d, theta, g, part, hdr);
+    prof_end(st);
+    *tg = g;
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
 }
 
 cg_status grad_points(const cg_problem* pb, const double* theta, int64_t n_theta, double* value, double* grad,
@@ -373,6 +414,7 @@ cg_status grad_points(const cg_problem* pb, const double* theta, int64_t n_theta
         RG2Data d;
         d.n = pb->data;
         d.nx = pb->n_bins[0];
+        d.ny = pb->n_bins[1];
         d.lx = pb->lo[0];
         d.ly = pb->lo[1];
         d.hx = (pb->hi[0] - pb->lo[0]) / (double)pb->n_bins[0];

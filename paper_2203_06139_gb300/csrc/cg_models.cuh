@@ -214,7 +214,7 @@ struct RG2Consts {
 
 struct RG2Data {
     const double* n;   // counts [ny][nx]
-    int64_t nx;
+    int64_t nx, ny;
     double lx, ly, hx, hy;
 };
 
@@ -237,13 +237,18 @@ __device__ __forceinline__ bool rg2_prologue(const double* __restrict__ th, RG2C
     return ok && isfinite(c.C);
 }
 
+// act: bit k set when Gaussian k can contribute in this tile (uniform per block)
 template <int K>
-__device__ __forceinline__ void rg2_elem_fp64(double x, double y, double n, const RG2Consts& c,
+__device__ __forceinline__ void rg2_elem_fp64(double x, double y, double n, const RG2Consts& c, unsigned act,
                                               double (&acc)[RG2Acc<K>::N], bool& bad) {
     double u[K], v[K], e[K];
     double mu = c.C;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
+        if (!(act & (1u << k))) {
+            u[k] = v[k] = e[k] = 0.0;
+            continue;
+        }
         const double dx = x - c.mx[k], dy = y - c.my[k];
         u[k] = fma(c.cs[k], dx, c.sn[k] * dy);
         v[k] = fma(c.cs[k], dy, -c.sn[k] * dx);
@@ -257,6 +262,7 @@ __device__ __forceinline__ void rg2_elem_fp64(double x, double y, double n, cons
     acc[0] += T;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
+        if (!(act & (1u << k))) continue;
         const double w = g * e[k];
         const double wu = w * u[k], wv = w * v[k];
         acc[1 + 6 * k] += w;
