@@ -46,7 +46,10 @@ def _load():
     global _lib
     if _lib is not None:
         return _lib
-    lib = ctypes.CDLL(build())
+    # CG_ORACLE_LIB: load a library built elsewhere (the mutation tests build
+    # copies of cg_oracle.c with planted mistakes and point this at them)
+    override = os.environ.get("CG_ORACLE_LIB")
+    lib = ctypes.CDLL(override if override else build())
     dp = ctypes.POINTER(ctypes.c_double)
     i64, c_int, c_d = ctypes.c_int64, ctypes.c_int, ctypes.c_double
     lib.orc_binned1d.argtypes = [c_int, c_int, c_int, c_int, i64, c_d, c_d, dp, dp, dp, dp, dp, dp]

@@ -1,0 +1,67 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of oracle/cg_oracle.c (a flipped sign
+in a local partial derivative, a dropped term, a wrong factor, a transposed
+operand), builds it with gcc and runs the pin suite against it in a
+subprocess; at least one pin must fail.  The real oracle is never modified.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+from tests.conftest import ROOT
+
+SRC = os.path.join(ROOT, "oracle", "cg_oracle.c")
+
+MUTATIONS = {
+    # reverse sweep: d(a - b)/db = -1 -> +1
+    "sub_partial_sign": ("return push(T, VAL(a) - VAL(b), a, 1.0, b, -1.0);",
+                         "return push(T, VAL(a) - VAL(b), a, 1.0, b, 1.0);"),
+    # d(a/b)/db = -q/b -> q/b
+    "div_partial_sign": ("return push(T, q, a, 1.0 / VAL(b), b, -q / VAL(b));",
+                         "return push(T, q, a, 1.0 / VAL(b), b, q / VAL(b));"),
+    # d exp(x)/dx = e -> 1
+    "exp_partial": ("double e = exp(VAL(a)); return push(T, e, a, e, -1, 0.0);",
+                    "double e = exp(VAL(a)); return push(T, e, a, 1.0, -1, 0.0);"),
+    # d erfc/dz sign
+    "erfc_partial_sign": ("-2.0 / sqrt(M_PI) * exp(-z * z)", "2.0 / sqrt(M_PI) * exp(-z * z)"),
+    # Gaussian width: 2 s^2 -> s^2
+    "gauss_factor_two": ("int32_t den = t_mulc(T, t_mul(T, s, s), 2.0);  /* 2 s^2 */",
+                         "int32_t den = t_mul(T, s, s);  /* 2 s^2 */"),
+    # chi-square weight 1/max(y, 1) -> 1
+    "chi2_weight": ("double w = 1.0 / fmax(y, 1.0);\n        int32_t r = t_rsubc(T, y, f);",
+                    "double w = 1.0;\n        int32_t r = t_rsubc(T, y, f);"),
+    # Baker-Cousins factor 2 dropped
+    "bc_factor": ("return t_mulc(T, inner, 2.0);", "return inner;"),
+    # mixture normalisation: Z_E = e^{-l lo} - e^{-l hi} -> only the first term
+    "mixture_ZE": ("int32_t ZE = t_sub(&T, t_exp(&T, t_mulc(&T, lam, -lo)), t_exp(&T, t_mulc(&T, lam, -hi)));",
+                   "int32_t ZE = t_exp(&T, t_mulc(&T, lam, -lo));"),
+    # rotation: v = -s dx + c dy -> s dx + c dy
+    "rotation_sign": ("int32_t v = t_add(&T, t_neg(&T, t_mul(&T, s, dx)), t_mul(&T, c, dy));",
+                      "int32_t v = t_add(&T, t_mul(&T, s, dx), t_mul(&T, c, dy));"),
+    # polynomial in t: (2x - lo - hi)/(hi - lo) -> (x - lo)/(hi - lo)
+    "poly_t_map": ("double u = (poly_mode == 1) ? (2.0 * x - lo - hi) / (hi - lo) : x;\n        int32_t f = rec_gauss_poly(&T, K, D, x, u);\n        int32_t t = rec_binned_term",
+                   "double u = (poly_mode == 1) ? (x - lo) / (hi - lo) : x;\n        int32_t f = rec_gauss_poly(&T, K, D, x, u);\n        int32_t t = rec_binned_term"),
+    # compensated sum loses its correction
+    "neumaier_dropped": ("static double nval(const nsum *acc) { return acc->s + acc->c; }",
+                         "static double nval(const nsum *acc) { return acc->s; }"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_mutation(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, "mutation anchor not found: " + name
+    msrc = tmp_path / "cg_oracle_mut.c"
+    msrc.write_text(src.replace(old, new))
+    lib = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(lib),
+                           str(msrc), "-lm"])
+    env = dict(os.environ, CG_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")], env=env, cwd=ROOT,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, "no pin failed for mutation %s:\n%s" % (name, r.stdout[-2000:])

@@ -348,3 +348,15 @@ def test_oracle_fit_reaches_lstsq_consistent_minimum():
     ndf = n - 5
     assert abs(res["F"] / ndf - 1) < 5 * math.sqrt(2 / ndf)
     assert abs(th[1] - 5.0) < 0.01
+
+
+def test_compensated_sum_of_identical_terms():
+    """10^6 identical events: the NLL is N times one event's term to a few
+    ulps (a plain running sum drifts by ~N eps / 2 relative)."""
+    N = 10 ** 6
+    th = np.array([0.3, 2.0, 0.3, 0.5])
+    one = oracle.unbinned_mix(np.array([2.345]), 0.0, 10.0, th)
+    r = oracle.unbinned_mix(np.full(N, 2.345), 0.0, 10.0, th)
+    eps = np.finfo(float).eps
+    assert abs(r.value - N * one.value) <= 4 * eps * abs(N * one.value)
+    np.testing.assert_allclose(r.grad, N * one.grad, rtol=4 * eps)
