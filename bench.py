@@ -532,6 +532,52 @@ def run_c4(args):
     print(json.dumps(line), flush=True)
 
 
+def run_fig3b(args):
+    """Gradient cost vs number of parameters (the comparison of Fig. 3b, whose
+    data is lost): for K = 1..4 Gaussian peaks + linear background on one
+    10^6-bin histogram, one reverse-mode gradient (fused launch), one
+    objective value, and a central-difference gradient (2P objective values,
+    batched in one launch)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2203_06139_gb300 import cg, synth
+    n = 10 ** 6
+    rows = []
+    for K in (1, 2, 3, 4):
+        p = synth.random_gauss_poly(K, 1, n, seed=300 + K)
+        P = 3 * K + 2
+        pb = cg.Problem.gauss_poly(torch.tensor(p["y"], device="cuda"), 0.0, 1.0, K, 1, cg.OBJ_CHI2,
+                                   precision=cg.PREC_DF64)
+        th = torch.tensor(p["theta"], device="cuda")
+        h = 1e-6 * np.maximum(np.abs(p["theta"]), 1e-3)
+        fd_pts = np.repeat(p["theta"][None, :], 2 * P, axis=0)
+        for k in range(P):
+            fd_pts[2 * k, k] += h[k]
+            fd_pts[2 * k + 1, k] -= h[k]
+        fd_t = torch.tensor(fd_pts, device="cuda")
+        one = th[None, :].contiguous()
+        v1 = torch.empty(1, dtype=torch.float64, device="cuda")
+        vfd = torch.empty(2 * P, dtype=torch.float64, device="cuda")
+        g1 = torch.empty((1, P), dtype=torch.float64, device="cuda")
+        t_ad = _timed(lambda: cg.batch_gradient(pb, one, v1, g1), args.steps, max(3, args.warmup))
+        t_val = _timed(lambda: cg.batch_objective(pb, one, v1), args.steps, max(3, args.warmup))
+        t_fd = _timed(lambda: cg.batch_objective(pb, fd_t, vfd), args.steps, max(3, args.warmup))
+        f = vfd.cpu().numpy()
+        g_fd = (f[0::2] - f[1::2]) / (2 * h)
+        g_ad = g1[0].cpu().numpy()
+        rows.append({"K": K, "P": P, "ms_gradient_ad": t_ad, "ms_value": t_val, "ms_gradient_fd": t_fd,
+                     "ad_over_value": t_ad / t_val, "fd_over_ad": t_fd / t_ad,
+                     "fd_vs_ad_max_rel": float(np.max(np.abs(g_fd - g_ad) / np.maximum(np.abs(g_ad), 1e-3)))})
+    line = {"metric": METRIC, "workload": "fig3b", "value": rows[-1]["fd_over_ad"], "unit": "FD/AD gradient time at K=4",
+            "higher_is_better": True,
+            "config": {"workload": "chi2, K Gaussians + linear, 10^6 bins, double-float kernels; FD = 2P values "
+                                   "in one batched launch, h = 1e-6 relative"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -542,7 +588,7 @@ def main():
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64-path comparison leg")
     ap.add_argument("--events", type=int, default=N_EVENTS)
     ap.add_argument("--points", type=int, default=N_POINTS)
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "fig3b"])
     ap.add_argument("--plain-hists", type=int, default=0, help="c4: histograms timed on the plain path (0 = all)")
     ap.add_argument("--train-hists", type=int, default=0, help="c5: training histograms (0 = 10^6)")
     ap.add_argument("--epochs", type=int, default=0, help="c5: training epochs (0 = 6)")
@@ -555,6 +601,8 @@ def main():
         run_c3(args)
     elif args.workload == "c4":
         run_c4(args)
+    elif args.workload == "fig3b":
+        run_fig3b(args)
     elif args.workload == "c5":
         from paper_2203_06139_gb300 import learned_start
         learned_start.bench(args)

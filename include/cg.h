@@ -155,7 +155,8 @@ cg_status cg_gradient(const cg_problem *pb, const double *theta, double *value, 
  * [n_hist]; grad: device [n_hist][P].
  *  - offsets == NULL: n_hist parameter points on the single problem tmpl
  *    (one thread per evaluation in Listing 1; here each point's gradient is
- *    itself a reduction over all bins or events).
+ *    itself a reduction over all bins or events).  grad may be NULL: values
+ *    only (value-only kernels for the 1-D model in CG_PREC_DF64).
  *  - offsets != NULL: histogram h is evaluated at theta[h]; binned 1-D
  *    models only.  Workspace: cg_batch_workspace_size(). */
 size_t cg_batch_workspace_size(const cg_batch *b);

@@ -264,3 +264,16 @@ def gemm_bf16(A, B, M, N, K, transA=0, transB=0, Cf=None, Cb=None, bias=None, au
     _check(lib().cg_gemm_bf16(_ptr(A), _ptr(B), M, N, K, lda, ldb, transA, transB, _ptr(Cf), _ptr(Cb), ldc,
                               _ptr(bias), _ptr(aux_in), _ptr(aux_out), epilogue, _ptr(err), _stream(stream)),
            "cg_gemm_bf16")
+
+
+def batch_objective(pb, thetas, values=None, stream=None):
+    """Objective values [H] at H parameter points (no gradient; value-only kernels where available)."""
+    thetas = _dev_f64(thetas, "thetas")
+    H = thetas.shape[0]
+    if values is None:
+        values = torch.empty(H, dtype=torch.float64, device=thetas.device)
+    b = point_batch(pb, H)
+    ws = pb.workspace(H)
+    _check(lib().cg_batch_gradient(ctypes.byref(b), _ptr(thetas), _ptr(values), None, _ptr(ws), ws.numel(),
+                                   _stream(stream)), "cg_batch_gradient (values)")
+    return values

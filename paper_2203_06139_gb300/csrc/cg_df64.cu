@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(NT, 3) k_mix_df64(MixData d, const double* __r
 // ===========================================================================
 // 1-D Gaussian peaks + polynomial
 // ===========================================================================
-template <int K, int OBJ, int NT>
+template <int K, int OBJ, int NT, bool VO>
 __global__ void __launch_bounds__(NT, 2) k_gp1_df64(GP1Data d, const double* __restrict__ theta, TileGrid tg,
                                                     double* __restrict__ part, WsHeader* __restrict__ hdr) {
     constexpr int NACC = GP1Acc<K>::N;
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(NT, 2) k_gp1_df64(GP1Data d, const double* __r
         for (int64_t i = e0 + threadIdx.x; i < e1; i += NT) {
             const double yv = __ldg(d.y + i);
             const df X = d.centres ? df_split(__ldg(d.centres + i)) : gp1_centre_df(cs, i);
-            if (!gp1_elem_df64<K, OBJ>(X, yv, cs, d.D, d.pm, acc, tab)) {
+            if (!gp1_elem_df64<K, OBJ, VO>(X, yv, cs, d.D, d.pm, acc, tab)) {
                 const double x = d.centres ? d.centres[i] : fma((double)i + 0.5, d.h, d.lo);
                 gp1_elem_fp64<K, OBJ>(x, yv, cs64, d, sum, bad);
             }
@@ -207,29 +207,248 @@ __global__ void __launch_bounds__(NT, 2) k_gp1_df64(GP1Data d, const double* __r
     }
 }
 
-template <int K>
-static cg_status launch_gp1_df64_k(const cg_problem* pb, const GP1Data& d, const double* theta, int64_t n_theta,
-                                   double* part, WsHeader* hdr, TileGrid* tg, cudaStream_t st, const int* gate) {
+template <int K, bool VO>
+static cg_status launch_gp1_df64_kv(const cg_problem* pb, const GP1Data& d, const double* theta, int64_t n_theta,
+                                    double* part, WsHeader* hdr, TileGrid* tg, cudaStream_t st, const int* gate) {
     constexpr int NT = 256;
     const int64_t n = pb->n_bins[0];
     switch (pb->objective) {
         case CG_OBJ_CHI2:
-            return launch_tiles(k_gp1_df64<K, CG_OBJ_CHI2, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st, gate);
+            return launch_tiles(k_gp1_df64<K, CG_OBJ_CHI2, NT, VO>, NT, d, theta, n, n_theta, part, hdr, tg, st, gate);
         case CG_OBJ_POISSON:
-            return launch_tiles(k_gp1_df64<K, CG_OBJ_POISSON, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st, gate);
-        case CG_OBJ_POISSON_BC:
-            return launch_tiles(k_gp1_df64<K, CG_OBJ_POISSON_BC, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st,
+            return launch_tiles(k_gp1_df64<K, CG_OBJ_POISSON, NT, VO>, NT, d, theta, n, n_theta, part, hdr, tg, st,
                                 gate);
+        case CG_OBJ_POISSON_BC:
+            return launch_tiles(k_gp1_df64<K, CG_OBJ_POISSON_BC, NT, VO>, NT, d, theta, n, n_theta, part, hdr, tg,
+                                st, gate);
         default: return CG_ERR_UNSUPPORTED;
     }
 }
 
+template <int K>
+static cg_status launch_gp1_df64_k(const cg_problem* pb, const GP1Data& d, const double* theta, int64_t n_theta,
+                                   double* part, WsHeader* hdr, TileGrid* tg, cudaStream_t st, const int* gate,
+                                   bool value_only) {
+    if (value_only) return launch_gp1_df64_kv<K, true>(pb, d, theta, n_theta, part, hdr, tg, st, gate);
+    return launch_gp1_df64_kv<K, false>(pb, d, theta, n_theta, part, hdr, tg, st, gate);
+}
+
+// ===========================================================================
+// 2-D rotated Gaussians + constant, Poisson (64 x 64-bin tiles, two passes)
+// ===========================================================================
+constexpr int kR2TX = 64, kR2TY = 64;
+constexpr double kR2Cull = 80.0;
+
+struct RG2Df {
+    df A[CG_MAX_PEAKS_2D], mx[CG_MAX_PEAKS_2D], my[CG_MAX_PEAKS_2D];
+    df cs[CG_MAX_PEAKS_2D], sn[CG_MAX_PEAKS_2D], al[CG_MAX_PEAKS_2D], be[CG_MAX_PEAKS_2D];
+    df C, lx, ly, hx, hy;
+};
+
+// u, v and e = exp(al u^2 + be v^2) of Gaussian k at centre (X, Y); the same
+// code serves both passes, so both see bitwise the same values.
+__device__ __forceinline__ df rg2_uve_df(const RG2Df& c, int k, df X, df Y, df& u, df& v, const DfTables& tab,
+                                         bool& fl) {
+    const df dx = df_sub(X, c.mx[k]), dy = df_sub(Y, c.my[k]);
+    u = df_add(df_mul(c.cs[k], dx), df_mul(c.sn[k], dy));
+    v = df_sub(df_mul(c.cs[k], dy), df_mul(c.sn[k], dx));
+    const df q = df_add(df_mul(c.al[k], df_sqr(u)), df_mul(c.be[k], df_sqr(v)));
+    return df_exp(q, tab, fl);
+}
+
+template <int K, int NT>
+__global__ void __launch_bounds__(NT, 2) k_rg2_df64(RG2Data d, const double* __restrict__ theta, TileGrid tg,
+                                                    double* __restrict__ part, WsHeader* __restrict__ hdr) {
+    constexpr int NACC = RG2Acc<K>::N;
+    __shared__ DfTables tab;
+    __shared__ RG2Consts c64;
+    __shared__ RG2Df cs;
+    __shared__ int cs_bad;
+    __shared__ unsigned act_s;
+    __shared__ float2 gsm[kR2TX * kR2TY];
+    __shared__ double red[6 * (NT / 32)];
+    __shared__ double tot[NACC];
+    if (gated_off(tg)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
+    df_tables_init(tab);
+    const int P = 6 * K + 1;
+    const int ntx = (int)((d.nx + kR2TX - 1) / kR2TX);
+    for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
+        const int c = t / tg.n_theta, th = t - c * tg.n_theta;
+        const int ty = c / ntx, tx = c - ty * ntx;
+        const int64_t x0 = (int64_t)tx * kR2TX, y0 = (int64_t)ty * kR2TY;
+        const int64_t x1 = min(d.nx, x0 + kR2TX), y1 = min(d.ny, y0 + kR2TY);
+        if (threadIdx.x == 0) {
+            const double* tht = theta + (size_t)th * P;
+            cs_bad = rg2_prologue<K>(tht, c64) ? 0 : 1;
+            const double bx0 = fma((double)x0 + 0.5, d.hx, d.lx), bx1 = fma((double)(x1 - 1) + 0.5, d.hx, d.lx);
+            const double by0 = fma((double)y0 + 0.5, d.hy, d.ly), by1 = fma((double)(y1 - 1) + 0.5, d.hy, d.ly);
+            unsigned act = 0;
+            for (int k = 0; k < K; ++k) {
+                const double mx = tht[6 * k + 1], my = tht[6 * k + 2];
+                const double sm = fmax(fabs(tht[6 * k + 3]), fabs(tht[6 * k + 4]));
+                const double ddx = fmax(0.0, fmax(bx0 - mx, mx - bx1));
+                const double ddy = fmax(0.0, fmax(by0 - my, my - by1));
+                if (!(0.5 * (ddx * ddx + ddy * ddy) / (sm * sm) > kR2Cull)) act |= 1u << k;
+                cs.A[k] = df_from_double(c64.A[k]);
+                cs.mx[k] = df_from_double(c64.mx[k]);
+                cs.my[k] = df_from_double(c64.my[k]);
+                cs.cs[k] = df_from_double(c64.cs[k]);
+                cs.sn[k] = df_from_double(c64.sn[k]);
+                cs.al[k] = df_from_double(c64.al[k]);
+                cs.be[k] = df_from_double(c64.be[k]);
+            }
+            cs.C = df_from_double(c64.C);
+            cs.lx = df_from_double(d.lx);
+            cs.ly = df_from_double(d.ly);
+            cs.hx = df_from_double(d.hx);
+            cs.hy = df_from_double(d.hy);
+            act_s = act;
+        }
+        __syncthreads();
+        const unsigned act = act_s;
+        const int w = (int)(x1 - x0);
+        const int nbin = w * (int)(y1 - y0);
+        bool bad = false;
+        // pass 1: model value, objective term and its adjoint g per bin
+        DfAcc aT, aG;
+        aT.s = aT.c = aG.s = aG.c = 0.0f;
+        double sT = 0.0, sG = 0.0;
+        int cnt = 0;
+        for (int b = threadIdx.x; b < nbin; b += NT) {
+            const int r = b / w, col = b - r * w;
+            const int64_t ix = x0 + col, iy = y0 + r;
+            const df X = df_add(cs.lx, df_mul(cs.hx, two_sum((float)ix, 0.5f)));
+            const df Y = df_add(cs.ly, df_mul(cs.hy, two_sum((float)iy, 0.5f)));
+            const double nd = __ldg(d.n + iy * d.nx + ix);
+            df mu = cs.C;
+            bool fl = false;
+#pragma unroll 1
+            for (int k = 0; k < K; ++k) {
+                if (!(act & (1u << k))) continue;
+                df u, v;
+                const df e = rg2_uve_df(cs, k, X, Y, u, v, tab, fl);
+                mu = df_add(mu, df_mul_nn(cs.A[k], e));
+            }
+            df T, g;
+            if (!(mu.h > 1e-30f) || (fl && mu.h < 1e-13f)) {
+                // FP64 for this bin's model value (all Gaussians that can contribute)
+                const double xc = fma((double)ix + 0.5, d.hx, d.lx), yc = fma((double)iy + 0.5, d.hy, d.ly);
+                double m = c64.C;
+                for (int k = 0; k < K; ++k) {
+                    if (!(act & (1u << k))) continue;
+                    const double dx = xc - c64.mx[k], dy = yc - c64.my[k];
+                    const double uu = fma(c64.cs[k], dx, c64.sn[k] * dy), vv = fma(c64.cs[k], dy, -c64.sn[k] * dx);
+                    m = fma(c64.A[k], exp(fma(c64.al[k], uu * uu, c64.be[k] * vv * vv)), m);
+                }
+                const double T64 = (nd > 0.0) ? m - nd * log(m) : m;
+                const double g64 = 1.0 - nd / m;
+                bad |= ((nd > 0.0) && !(m > 0.0)) || !isfinite(T64);
+                sT += T64;
+                sG += g64;
+                g = df_from_double(g64);
+            } else {
+                const df y = df_split(nd);
+                const df rm = df_rcp(mu);
+                T = (y.h > 0.0f) ? df_sub(mu, df_mul(y, df_log(mu, tab))) : mu;
+                g = df_sub(df_make(1.0f, 0.0f), df_mul(y, rm));
+                dfacc_add(aT, T);
+                dfacc_add(aG, g);
+            }
+            gsm[b] = make_float2(g.h, g.l);
+            if (++cnt == 32) {
+                dfacc_flush(aT, sT);
+                dfacc_flush(aG, sG);
+                cnt = 0;
+            }
+        }
+        dfacc_flush(aT, sT);
+        dfacc_flush(aG, sG);
+        const int any_bad = __syncthreads_or(bad ? 1 : 0) | cs_bad;
+        // pass 2: the six adjoint sums of each Gaussian that can contribute
+#pragma unroll 1
+        for (int k = 0; k < K; ++k) {
+            if (!(act & (1u << k))) {
+                if (threadIdx.x < 6) tot[1 + 6 * k + threadIdx.x] = 0.0;
+                continue;
+            }
+            DfAcc a6[6];
+            double s6[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                a6[q].s = a6[q].c = 0.0f;
+                s6[q] = 0.0;
+            }
+            cnt = 0;
+            for (int b = threadIdx.x; b < nbin; b += NT) {
+                const int r = b / w, col = b - r * w;
+                const int64_t ix = x0 + col, iy = y0 + r;
+                const df X = df_add(cs.lx, df_mul(cs.hx, two_sum((float)ix, 0.5f)));
+                const df Y = df_add(cs.ly, df_mul(cs.hy, two_sum((float)iy, 0.5f)));
+                df u, v;
+                bool fl = false;
+                const df e = rg2_uve_df(cs, k, X, Y, u, v, tab, fl);
+                const float2 gg = gsm[b];
+                const df wgt = df_mul_nn(df_make(gg.x, gg.y), e);
+                const df wu = df_mul_nn(wgt, u), wv = df_mul_nn(wgt, v);
+                dfacc_add(a6[0], wgt);
+                dfacc_add(a6[1], wu);
+                dfacc_add(a6[2], wv);
+                dfacc_add(a6[3], df_mul_nn(wu, u));
+                dfacc_add(a6[4], df_mul_nn(wv, v));
+                dfacc_add(a6[5], df_mul_nn(wu, v));
+                if (++cnt == 32) {
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) dfacc_flush(a6[q], s6[q]);
+                    cnt = 0;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 6; ++q) dfacc_flush(a6[q], s6[q]);
+            block_sum<6, NT>(s6, red, tot + 1 + 6 * k);
+        }
+        double s2[2] = {sT, sG};
+        __shared__ double tot2[2];
+        block_sum<2, NT>(s2, red, tot2);
+        if (threadIdx.x == 0) {
+            tot[0] = tot2[0];
+            tot[1 + 6 * K] = tot2[1];
+        }
+        __syncthreads();
+        write_partial<NACC>(part, tg, th, c, tot, any_bad);
+        __syncthreads();
+    }
+}
+
+template <int K>
+static cg_status launch_rg2_df64_k(const RG2Data& d, const double* theta, int64_t n, int64_t n_theta, double* part,
+                                   WsHeader* hdr, TileGrid* tg, cudaStream_t st, const int* gate) {
+    constexpr int NT = 256;
+    auto kern = k_rg2_df64<K, NT>;
+    const int R = resident_blocks((const void*)kern, NT, 0);
+    const int G = device_sm_count() * R;
+    TileGrid g;
+    g.n_elem = n;
+    g.chunk = 0;
+    g.nbx = (int)(((d.nx + kR2TX - 1) / kR2TX) * ((d.ny + kR2TY - 1) / kR2TY));
+    g.n_theta = (int)n_theta;
+    g.n_tiles = (int)(n_theta * g.nbx);
+    g.gate = gate;
+    const int grid = g.n_tiles < G ? g.n_tiles : G;
+    prof_begin(st);
+    kern<<<grid, NT, 0, st>>>(d, theta, g, part, hdr);
+    prof_end(st);
+    *tg = g;
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
+
 bool df64_supported(const cg_problem* pb) {
-    return pb->model == CG_MODEL_MIX_GAUSS_EXP || (pb->model == CG_MODEL_GAUSS_POLY && pb->n_bins[0] < (1 << 24));
+    return pb->model == CG_MODEL_MIX_GAUSS_EXP || (pb->model == CG_MODEL_GAUSS_POLY && pb->n_bins[0] < (1 << 24)) ||
+           (pb->model == CG_MODEL_ROTGAUSS2D && pb->n_bins[0] < (1 << 24) && pb->n_bins[1] < (1 << 24));
 }
 
 cg_status launch_df64(const cg_problem* pb, const double* theta, int64_t n_theta, double* part, WsHeader* hdr,
-                      TileGrid* tg, cudaStream_t st, const int* gate) {
+                      TileGrid* tg, cudaStream_t st, const int* gate, bool value_only) {
     if (pb->model == CG_MODEL_MIX_GAUSS_EXP) {
         MixData d;
         d.x = pb->data;
@@ -254,11 +473,33 @@ cg_status launch_df64(const cg_problem* pb, const double* theta, int64_t n_theta
         d.pm = pb->poly_mode;
         d.vec_ok = 0;
         switch (pb->n_peaks) {
-            case 0: return launch_gp1_df64_k<0>(pb, d, theta, n_theta, part, hdr, tg, st, gate);
-            case 1: return launch_gp1_df64_k<1>(pb, d, theta, n_theta, part, hdr, tg, st, gate);
-            case 2: return launch_gp1_df64_k<2>(pb, d, theta, n_theta, part, hdr, tg, st, gate);
-            case 3: return launch_gp1_df64_k<3>(pb, d, theta, n_theta, part, hdr, tg, st, gate);
-            case 4: return launch_gp1_df64_k<4>(pb, d, theta, n_theta, part, hdr, tg, st, gate);
+            case 0: return launch_gp1_df64_k<0>(pb, d, theta, n_theta, part, hdr, tg, st, gate, value_only);
+            case 1: return launch_gp1_df64_k<1>(pb, d, theta, n_theta, part, hdr, tg, st, gate, value_only);
+            case 2: return launch_gp1_df64_k<2>(pb, d, theta, n_theta, part, hdr, tg, st, gate, value_only);
+            case 3: return launch_gp1_df64_k<3>(pb, d, theta, n_theta, part, hdr, tg, st, gate, value_only);
+            case 4: return launch_gp1_df64_k<4>(pb, d, theta, n_theta, part, hdr, tg, st, gate, value_only);
+            default: return CG_ERR_INVALID_ARG;
+        }
+    }
+    if (pb->model == CG_MODEL_ROTGAUSS2D) {
+        RG2Data d;
+        d.n = pb->data;
+        d.nx = pb->n_bins[0];
+        d.ny = pb->n_bins[1];
+        d.lx = pb->lo[0];
+        d.ly = pb->lo[1];
+        d.hx = (pb->hi[0] - pb->lo[0]) / (double)pb->n_bins[0];
+        d.hy = (pb->hi[1] - pb->lo[1]) / (double)pb->n_bins[1];
+        const int64_t n = d.nx * d.ny;
+        switch (pb->n_peaks) {
+            case 1: return launch_rg2_df64_k<1>(d, theta, n, n_theta, part, hdr, tg, st, gate);
+            case 2: return launch_rg2_df64_k<2>(d, theta, n, n_theta, part, hdr, tg, st, gate);
+            case 3: return launch_rg2_df64_k<3>(d, theta, n, n_theta, part, hdr, tg, st, gate);
+            case 4: return launch_rg2_df64_k<4>(d, theta, n, n_theta, part, hdr, tg, st, gate);
+            case 5: return launch_rg2_df64_k<5>(d, theta, n, n_theta, part, hdr, tg, st, gate);
+            case 6: return launch_rg2_df64_k<6>(d, theta, n, n_theta, part, hdr, tg, st, gate);
+            case 7: return launch_rg2_df64_k<7>(d, theta, n, n_theta, part, hdr, tg, st, gate);
+            case 8: return launch_rg2_df64_k<8>(d, theta, n, n_theta, part, hdr, tg, st, gate);
             default: return CG_ERR_INVALID_ARG;
         }
     }

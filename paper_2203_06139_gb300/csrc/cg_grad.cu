@@ -380,7 +380,7 @@ cg_status grad_points(const cg_problem* pb, const double* theta, int64_t n_theta
         cudaMemsetAsync(part, 0, (size_t)n_theta * (nacc + 1) * sizeof(double), st);
         s = CG_OK;
     } else if (pb->precision == CG_PREC_DF64) {
-        s = launch_df64(pb, theta, n_theta, part, hdr, &tg, st, gate);
+        s = launch_df64(pb, theta, n_theta, part, hdr, &tg, st, gate, grad == nullptr);
     } else if (pb->model == CG_MODEL_GAUSS_POLY) {
         GP1Data d;
         d.y = pb->data;

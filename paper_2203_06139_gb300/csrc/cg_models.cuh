@@ -337,6 +337,6 @@ __device__ inline double epilogue(const EpiParams& ep, const double* __restrict_
 // double-float path (cg_df64.cu)
 bool df64_supported(const cg_problem* pb);
 cg_status launch_df64(const cg_problem* pb, const double* theta, int64_t n_theta, double* part, WsHeader* hdr,
-                      TileGrid* tg, cudaStream_t st, const int* gate);
+                      TileGrid* tg, cudaStream_t st, const int* gate, bool value_only);
 
 }  // namespace cg

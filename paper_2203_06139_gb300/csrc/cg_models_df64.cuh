@@ -36,7 +36,8 @@ __device__ __forceinline__ df gp1_centre_df(const GP1Df& c, int64_t i) {
 // One bin at centre X (df64) with count y.  Returns false when the element
 // must be recomputed in FP64 (every Gaussian flushed while the model value is
 // tiny, or a non-positive model value under a log).
-template <int K, int OBJ>
+// VO (value only): accumulate T and skip the adjoint part.
+template <int K, int OBJ, bool VO = false>
 __device__ __forceinline__ bool gp1_elem_df64(df X, double yd, const GP1Df& c, int D, int pm,
                                               DfAcc (&acc)[GP1Acc<K>::N], const DfTables& tab) {
     const df u = pm ? df_add(df_mul(X, c.au), c.bu) : X;
@@ -77,6 +78,7 @@ __device__ __forceinline__ bool gp1_elem_df64(df X, double yd, const GP1Df& c, i
         }
     }
     dfacc_add(acc[0], T);
+    if (VO) return true;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const df t = df_mul_nn(g, ek[k]);

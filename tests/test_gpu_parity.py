@@ -306,3 +306,36 @@ def test_c1_df64_full_size_all_points(dev):
     g = g.cpu().numpy()
     for i, ref in enumerate(refs):
         check(v[i], g[i], ref)
+
+
+@pytest.mark.parametrize("obj", [cg.OBJ_CHI2, cg.OBJ_POISSON_BC])
+def test_value_only_matches_gradient_value(dev, obj):
+    p = synth.random_gauss_poly(3, 1, 5001, seed=77)
+    pb = cg.Problem.gauss_poly(torch.tensor(p["y"], device=dev), 0.0, 1.0, 3, 1, obj, precision=cg.PREC_DF64)
+    th = torch.tensor(np.stack([p["theta"], p["truth"]]), device=dev)
+    v, _ = cg.batch_gradient(pb, th)
+    vo = cg.batch_objective(pb, th)
+    for i in range(2):
+        ref = oracle.binned1d(3, 1, 0, OBJ_MAP[obj], p["y"], 0.0, 1.0, th[i].cpu().numpy())
+        assert abs(float(vo[i]) - ref.value) <= 1e-10 * abs(ref.value)
+    torch.testing.assert_close(vo, v, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("K,nx,ny", [(1, 31, 17), (3, 130, 70), (8, 200, 129)])
+def test_rotgauss2d_df64_small(dev, K, nx, ny):
+    truth = synth.c3_truth(K)
+    counts = np.random.default_rng(K).poisson(synth.expected_counts_2d(truth, K, nx, ny)).astype(float)
+    th = truth * (1 + np.random.default_rng(K + 1).uniform(-0.05, 0.05, truth.size))
+    p2 = cg.Problem.rotgauss2d(torch.tensor(counts, device=dev), K, precision=cg.PREC_DF64)
+    v, g = cg.gradient(p2, torch.tensor(th, device=dev))
+    assert p2.status() == cg.OK
+    check(v, g, oracle.binned2d(K, counts, 0.0, 1.0, 0.0, 1.0, th))
+
+
+@pytest.mark.slow
+def test_c3_df64_full_size(dev):
+    h = synth.c3_histogram()
+    th = synth.c3_theta_point(h["truth"])[0]
+    p2 = cg.Problem.rotgauss2d(torch.tensor(h["counts"], device=dev), 8, precision=cg.PREC_DF64)
+    v, g = cg.gradient(p2, torch.tensor(th, device=dev))
+    check(v, g, oracle.binned2d(8, h["counts"], 0.0, 1.0, 0.0, 1.0, th))
