@@ -20,6 +20,7 @@
 namespace cg {
 
 constexpr int kFlush = 32;   // elements per compensated run before the FP64 flush
+constexpr bool kMixPairs = true;   // unbinned kernel: two events per loop iteration
 
 // ===========================================================================
 // Unbinned mixture
@@ -123,8 +124,28 @@ __global__ void __launch_bounds__(NT, 3) k_mix_df64(MixData d, const double* __r
         int cnt = 0;
         const int64_t e0 = (int64_t)c * tg.chunk;
         const int64_t e1 = min(tg.n_elem, e0 + tg.chunk);
-        double xn = (e0 + threadIdx.x < e1) ? __ldg(d.x + e0 + threadIdx.x) : 0.0;
-        for (int64_t i = e0 + threadIdx.x; i < e1; i += NT) {
+        int64_t i = e0 + threadIdx.x;
+        if (kMixPairs) {
+            // two independent events per iteration: their dependency chains interleave
+            for (; i + NT < e1; i += 2 * NT) {
+                const double xa = __ldg(d.x + i), xb = __ldg(d.x + i + NT);
+                mix_elem_df64<W>(xa, W ? __ldg(d.w + i) : 1.0, cr, cs64, tab, acc, P, sum, &bad);
+                mix_elem_df64<W>(xb, W ? __ldg(d.w + i + NT) : 1.0, cr, cs64, tab, acc, P, sum, &bad);
+                cnt += 2;
+                if (cnt >= kFlush) {
+                    if (!W) {
+                        dfacc_add(acc[0], dfprod_log(P, tab));
+                        P.m = df_make(1.0f, 0.0f);
+                        P.E = 0;
+                    }
+#pragma unroll
+                    for (int a = 0; a < NACC; ++a) dfacc_flush(acc[a], sum[a * NT]);
+                    cnt = 0;
+                }
+            }
+        }
+        double xn = (i < e1) ? __ldg(d.x + i) : 0.0;
+        for (; i < e1; i += NT) {
             const double xi = xn;
             if (i + NT < e1) xn = __ldg(d.x + i + NT);   // next event in flight during this one
             mix_elem_df64<W>(xi, W ? __ldg(d.w + i) : 1.0, cr, cs64, tab, acc, P, sum, &bad);
