@@ -336,7 +336,7 @@ int orc_gauss_poly_eval(int K, int D, int poly_mode, double lo, double hi, int64
 /* Gauss-Newton diagonal of a 1-D binned objective:
  *     GN_k = sum_i h_i (d f_i / d theta_k)^2,
  * with h_i = d^2 T_i / d f_i^2 of the bin term: 2 w_i (chi2), y_i / f_i^2
- * (poisson), 2 y_i / f_i^2 (poisson_bc).  Used only to scale the initial
+ * (poisson), 2 y_i / f_i^2 (poisson_bc); 0 for an empty bin of the latter two.  Used only to scale the initial
  * inverse Hessian of the BFGS fit. */
 int orc_binned1d_gn(int K, int D, int poly_mode, int obj, int64_t n, double lo, double hi,
                     const double *centres, const double *y, const double *theta, double *gn) {
@@ -362,9 +362,11 @@ int orc_binned1d_gn(int K, int D, int poly_mode, int obj, int64_t n, double lo, 
             if (nd->b >= 0) adj[nd->b] += adj[j] * nd->pb;
         }
         double fv = T.n[f].v, hi_;
+        /* an empty bin's term is T = f (times 2 for poisson_bc): linear in f,
+         * curvature exactly 0 even where f itself underflows to 0 */
         if (obj == OBJ_CHI2) hi_ = 2.0 / fmax(y[i], 1.0);
-        else if (obj == OBJ_POISSON) hi_ = y[i] / (fv * fv);
-        else hi_ = 2.0 * y[i] / (fv * fv);
+        else if (obj == OBJ_POISSON) hi_ = (y[i] > 0.0) ? y[i] / (fv * fv) : 0.0;
+        else hi_ = (y[i] > 0.0) ? 2.0 * y[i] / (fv * fv) : 0.0;
         for (int32_t k = 0; k < P; ++k) nadd(&acc[k], hi_ * adj[k] * adj[k]);
         T.len = mark;
     }

@@ -182,6 +182,34 @@ def test_gauss_newton_diagonal():
         np.testing.assert_allclose(gn, (hh[None, :] * J ** 2).sum(1), rtol=1e-12)
 
 
+def test_empty_bins_where_the_model_underflows():
+    """One narrow peak without background: far from it the model underflows
+    to exactly 0 in FP64 and the bins are empty.  An empty bin's Poisson term
+    is T = f (2 f for Baker-Cousins), so it adds dT/df = 1 (2) times the
+    Jacobian to the gradient and nothing to the Gauss-Newton diagonal; the
+    oracle matches that closed form rather than producing 0/0."""
+    n = 2000
+    th = np.array([800.0, 0.5, 0.01])
+    x = synth.uniform_centres(n, 0.0, 1.0)
+    y = np.random.default_rng(2).poisson(th[0] * np.exp(-(x - th[1]) ** 2 / (2 * th[2] ** 2))).astype(float)
+    A, mu, s = t = th * np.array([1.02, 1.0, 0.97])
+    e = np.exp(-(x - mu) ** 2 / (2 * s * s))
+    f = A * e
+    assert np.any(f == 0.0) and np.all(y[f == 0.0] == 0.0)
+    J = np.array([e, A * e * (x - mu) / s ** 2, A * e * (x - mu) ** 2 / s ** 3])
+    fs = np.where(f > 0.0, f, 1.0)
+    for obj, c in ((oracle.POISSON, 1.0), (oracle.POISSON_BC, 2.0)):
+        with np.errstate(divide="ignore", invalid="ignore"):   # discarded branch: fs**2 may underflow
+            gi = np.where(y > 0.0, c * (1.0 - y / fs), c)
+            hh = np.where(y > 0.0, c * y / fs ** 2, 0.0)
+        r = oracle.binned1d(1, -1, 0, obj, y, 0.0, 1.0, t)
+        gref = (gi[None, :] * J).sum(1)
+        assert np.all(np.isfinite(r.grad))
+        np.testing.assert_allclose(r.grad, gref, rtol=1e-9, atol=1e-12 * np.abs(J).sum())
+        gn = oracle.binned1d_gn(1, -1, 0, obj, y, 0.0, 1.0, t)
+        np.testing.assert_allclose(gn, (hh[None, :] * J ** 2).sum(1), rtol=1e-12)
+
+
 # --------------------------------------------------------------------------
 # unbinned mixture
 # --------------------------------------------------------------------------
