@@ -102,68 +102,144 @@ __device__ __forceinline__ void acc_bins(const Geom& G, const GP1Consts& cs, con
     }
 }
 
-// The same in double-float arithmetic (FP32 pipe), flushed into the FP64
-// accumulators every 32 bins; elements that need it fall back to FP64.
+// Gauss-Newton diagonal terms of one bin: h (df/dtheta_k)^2 with h = d2T/df2.
 template <int K, int OBJ>
+__device__ __forceinline__ void gn_elem_fp64(double x, double y, const GP1Consts& cs, const GP1Data& dd,
+                                             double (&acc)[GP1Acc<K>::N]) {
+    const double u = dd.pm ? fma(x, dd.au, dd.bu) : x;
+    double f = 0.0;
+#pragma unroll
+    for (int j = 3; j >= 0; --j)
+        if (j <= dd.D) f = fma(f, u, cs.poly[j]);
+    double dk[K], ek[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        dk[k] = x - cs.mu[k];
+        ek[k] = exp(cs.c[k] * dk[k] * dk[k]);
+        f = fma(cs.A[k], ek[k], f);
+    }
+    double h;   // an empty bin's Poisson term is linear in f: curvature 0
+    if (OBJ == CG_OBJ_CHI2) h = 2.0 / fmax(y, 1.0);
+    else if (OBJ == CG_OBJ_POISSON) h = (y > 0.0) ? y / (f * f) : 0.0;
+    else h = (y > 0.0) ? 2.0 * y / (f * f) : 0.0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const double he = h * ek[k] * ek[k];
+        const double d2 = dk[k] * dk[k];
+        acc[1 + 3 * k] += he;
+        acc[2 + 3 * k] = fma(he, d2, acc[2 + 3 * k]);
+        acc[3 + 3 * k] = fma(he * d2, d2, acc[3 + 3 * k]);
+    }
+    double up = 1.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (j <= dd.D) acc[1 + 3 * K + j] = fma(h, up * up, acc[1 + 3 * K + j]);
+        up *= u;
+    }
+}
+
+template <int K, int OBJ>
+__device__ __forceinline__ void gn_bins(const Geom& G, const GP1Consts& cs, const GP1Data& dd, int t0, int T,
+                                        double (&acc)[GP1Acc<K>::N]) {
+    for (int64_t i = t0; i < G.n; i += T)
+        gn_elem_fp64<K, OBJ>(fma((double)i + 0.5, G.hw, G.lo), __ldg(G.y + i), cs, dd, acc);
+}
+
+// The df64 bin centres are exact below this many bins; longer histograms are
+// evaluated in FP64 whatever the batch precision.
+constexpr int64_t kDfMaxBins = (int64_t)1 << 24;
+constexpr int kFitFlush = 32;
+
+// Fold a compensated accumulator into a per-thread df64 running sum (FP32
+// pipe only; the one conversion to FP64 happens after the last bin).
+__device__ __forceinline__ void dfacc_fold(DfAcc& A, df& run) {
+    run = df_add(run, df_make(A.s, A.c));
+    A.s = A.c = 0.0f;
+}
+
+// FP64 terms of one bin that the df64 path hands back (rare).  Kept out of
+// line so that the bin loop keeps no FP64 state: out[0..N) gradient
+// accumulators, out[N..2N) Gauss-Newton terms (GN only).
+template <int K, int OBJ, bool GN>
+static __device__ __noinline__ void gp1_fallback_fp64(double x, double y, const GP1Consts& cs, GP1Data dd,
+                                                      double* out, int* bad) {
+    constexpr int N = GP1Acc<K>::N;
+    double a[N], g[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) a[i] = g[i] = 0.0;
+    bool b = false;
+    gp1_elem_fp64<K, OBJ>(x, y, cs, dd, a, b);
+    if (GN) gn_elem_fp64<K, OBJ>(x, y, cs, dd, g);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        out[i] = a[i];
+        out[N + i] = g[i];
+    }
+    *bad = b ? 1 : 0;
+}
+
+// The same in double-float arithmetic (FP32 pipe): every kFitFlush bins the
+// compensated accumulators are folded into df64 running sums, which are added
+// to the FP64 accumulators once at the end; elements that need it are
+// evaluated in FP64 and folded into the same running sums.  GN: also the
+// Gauss-Newton diagonal terms, into gn[].
+// Requires G.n < kDfMaxBins (bin index and centre exact in FP32 / df64).
+template <int K, int OBJ, bool GN>
 __device__ __forceinline__ void acc_bins_df64(const Geom& G, const GP1Consts& cs, const GP1Df& cd,
                                               const GP1Data& dd, const DfTables& tab, int t0, int T,
-                                              double (&acc)[GP1Acc<K>::N], bool& bad) {
+                                              double (&acc)[GP1Acc<K>::N], double (&gn)[GP1Acc<K>::N], bool& bad) {
     constexpr int N = GP1Acc<K>::N;
-    DfAcc da[N];
+    constexpr int NG = GN ? N : 1;
+    DfAcc da[N], ga[NG];
+    df run[N], grun[NG];
 #pragma unroll
-    for (int a = 0; a < N; ++a) da[a].s = da[a].c = 0.0f;
+    for (int a = 0; a < N; ++a) {
+        da[a].s = da[a].c = 0.0f;
+        run[a] = df_make(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int a = 0; a < NG; ++a) {
+        ga[a].s = ga[a].c = 0.0f;
+        grun[a] = df_make(0.0f, 0.0f);
+    }
+    const int n = (int)G.n;
+    const float fT = (float)T;
+    float fi = (float)t0;   // == i exactly (i < 2^24)
     int cnt = 0;
-    for (int64_t i = t0; i < G.n; i += T) {
+    for (int i = t0; i < n; i += T, fi += fT) {
         const double y = __ldg(G.y + i);
-        if (!gp1_elem_df64<K, OBJ>(gp1_centre_df(cd, i), y, cd, dd.D, dd.pm, da, tab))
-            gp1_elem_fp64<K, OBJ>(fma((double)i + 0.5, G.hw, G.lo), y, cs, dd, acc, bad);
-        if (++cnt == 32) {
+        if (!gp1_elem_df64<K, OBJ, false, GN>(gp1_centre_df(cd, fi), y, cd, dd.D, dd.pm, da, tab, ga)) {
+            double t[2 * N];
+            int b = 0;
+            gp1_fallback_fp64<K, OBJ, GN>(fma((double)i + 0.5, G.hw, G.lo), y, cs, dd, t, &b);
+            bad |= (b != 0);
 #pragma unroll
-            for (int a = 0; a < N; ++a) dfacc_flush(da[a], acc[a]);
+            for (int a = 0; a < N; ++a) run[a] = df_add(run[a], df_from_double(t[a]));
+            if (GN) {
+#pragma unroll
+                for (int a = 1; a < NG; ++a) grun[a] = df_add(grun[a], df_from_double(t[N + a]));
+            }
+        }
+        if (++cnt == kFitFlush) {
+#pragma unroll
+            for (int a = 0; a < N; ++a) dfacc_fold(da[a], run[a]);
+            if (GN) {
+#pragma unroll
+                for (int a = 1; a < NG; ++a) dfacc_fold(ga[a], grun[a]);
+            }
             cnt = 0;
         }
     }
 #pragma unroll
-    for (int a = 0; a < N; ++a) dfacc_flush(da[a], acc[a]);
-}
-
-// Gauss-Newton diagonal terms of one bin: h (df/dtheta_k)^2 with h = d2T/df2.
-template <int K, int OBJ>
-__device__ __forceinline__ void gn_bins(const Geom& G, const GP1Consts& cs, const GP1Data& dd, int t0, int T,
-                                        double (&acc)[GP1Acc<K>::N]) {
-    for (int64_t i = t0; i < G.n; i += T) {
-        const double x = fma((double)i + 0.5, G.hw, G.lo);
-        const double y = __ldg(G.y + i);
-        const double u = dd.pm ? fma(x, dd.au, dd.bu) : x;
-        double f = 0.0;
+    for (int a = 0; a < N; ++a) {
+        dfacc_fold(da[a], run[a]);
+        acc[a] += df_to_double(run[a]);
+    }
+    if (GN) {
 #pragma unroll
-        for (int j = 3; j >= 0; --j)
-            if (j <= dd.D) f = fma(f, u, cs.poly[j]);
-        double dk[K], ek[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            dk[k] = x - cs.mu[k];
-            ek[k] = exp(cs.c[k] * dk[k] * dk[k]);
-            f = fma(cs.A[k], ek[k], f);
-        }
-        double h;
-        if (OBJ == CG_OBJ_CHI2) h = 2.0 / fmax(y, 1.0);
-        else if (OBJ == CG_OBJ_POISSON) h = y / (f * f);
-        else h = 2.0 * y / (f * f);
-        acc[0] += 0.0;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const double he = h * ek[k] * ek[k];
-            const double d2 = dk[k] * dk[k];
-            acc[1 + 3 * k] += he;
-            acc[2 + 3 * k] = fma(he, d2, acc[2 + 3 * k]);
-            acc[3 + 3 * k] = fma(he * d2, d2, acc[3 + 3 * k]);
-        }
-        double up = 1.0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (j <= dd.D) acc[1 + 3 * K + j] = fma(h, up * up, acc[1 + 3 * K + j]);
-            up *= u;
+        for (int a = 1; a < NG; ++a) {
+            dfacc_fold(ga[a], grun[a]);
+            gn[a] += df_to_double(grun[a]);
         }
     }
 }
@@ -369,7 +445,7 @@ __device__ __forceinline__ void unit_eval(FitSm& s, GP1Consts& cs, GP1Df& cd, co
 #pragma unroll
     for (int a = 0; a < N; ++a) acc[a] = 0.0;
     bool bad = false;
-    if (PREC == CG_PREC_DF64) acc_bins_df64<K, OBJ>(G, cs, cd, dd, tab, t0, T, acc, bad);
+    if (PREC == CG_PREC_DF64 && G.n < kDfMaxBins) acc_bins_df64<K, OBJ, false>(G, cs, cd, dd, tab, t0, T, acc, acc, bad);
     else acc_bins<K, OBJ>(G, cs, dd, t0, T, acc, bad);
     int any_bad;
     if (UNIT == UNIT_WARP) {
@@ -561,8 +637,9 @@ __global__ void __launch_bounds__(512) k_fit_persistent(FitArgs a) {
 
 // Init (GN + first evaluation) and plain evaluation: one CTA per histogram,
 // grid-stride over histograms.  mode 0: value/grad at a.theta; mode 1: init.
-template <int K, int OBJ, int PREC>
-__global__ void __launch_bounds__(256) k_fit_eval(FitArgs a, int mode) {
+template <int K, int OBJ, int PREC, int MODE>
+__global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
+    constexpr int mode = MODE;
     constexpr int N = GP1Acc<K>::N;
     __shared__ GP1Consts cs;
     __shared__ GP1Df cd;
@@ -593,20 +670,21 @@ __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a, int mode) {
             if (PREC == CG_PREC_DF64) gp1_split(cs, G.lo, G.hw, dd.au, dd.bu, K, cd);
         }
         __syncthreads();
-        double acc[N];
+        double acc[N], gacc[N];
 #pragma unroll
-        for (int i = 0; i < N; ++i) acc[i] = 0.0;
+        for (int i = 0; i < N; ++i) acc[i] = gacc[i] = 0.0;
         bool bad = false;
-        if (PREC == CG_PREC_DF64 && mode == 0) acc_bins_df64<K, OBJ>(G, cs, cd, dd, tab, threadIdx.x, blockDim.x, acc, bad);
-        else acc_bins<K, OBJ>(G, cs, dd, threadIdx.x, blockDim.x, acc, bad);
+        if (PREC == CG_PREC_DF64 && G.n < kDfMaxBins) {
+            // mode 1: gradient and Gauss-Newton terms in one sweep over the bins
+            if constexpr (MODE == 0) acc_bins_df64<K, OBJ, false>(G, cs, cd, dd, tab, threadIdx.x, blockDim.x, acc, gacc, bad);
+            else acc_bins_df64<K, OBJ, true>(G, cs, cd, dd, tab, threadIdx.x, blockDim.x, acc, gacc, bad);
+        } else {
+            acc_bins<K, OBJ>(G, cs, dd, threadIdx.x, blockDim.x, acc, bad);
+            if constexpr (MODE == 1) gn_bins<K, OBJ>(G, cs, dd, threadIdx.x, blockDim.x, gacc);
+        }
         const int any_bad = __syncthreads_or(bad) | cs_bad;
         reduce_cta<N>(acc, red, tot);
-        if (mode == 1) {
-#pragma unroll
-            for (int i = 0; i < N; ++i) acc[i] = 0.0;
-            gn_bins<K, OBJ>(G, cs, dd, threadIdx.x, blockDim.x, acc);
-            reduce_cta<N>(acc, red, gn);
-        }
+        if constexpr (MODE == 1) reduce_cta<N>(gacc, red, gn);
         if (threadIdx.x == 0) {
             EpiParams ep;
             ep.model = CG_MODEL_GAUSS_POLY;
@@ -766,8 +844,14 @@ template <int K, int OBJ>
 cg_status launch_eval_k(const FitArgs& a, int mode, int prec, cudaStream_t st) {
     const int G = device_sm_count() * 4;
     const int grid = (int)(a.H < G ? a.H : G);
-    if (prec == CG_PREC_DF64 && mode == 0) k_fit_eval<K, OBJ, CG_PREC_DF64><<<grid, 256, 0, st>>>(a, mode);
-    else k_fit_eval<K, OBJ, CG_PREC_FP64><<<grid, 256, 0, st>>>(a, mode);
+    const bool df = prec == CG_PREC_DF64;
+    if (mode == 0) {
+        if (df) k_fit_eval<K, OBJ, CG_PREC_DF64, 0><<<grid, 256, 0, st>>>(a);
+        else k_fit_eval<K, OBJ, CG_PREC_FP64, 0><<<grid, 256, 0, st>>>(a);
+    } else {
+        if (df) k_fit_eval<K, OBJ, CG_PREC_DF64, 1><<<grid, 256, 0, st>>>(a);
+        else k_fit_eval<K, OBJ, CG_PREC_FP64, 1><<<grid, 256, 0, st>>>(a);
+    }
     return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
 }
 

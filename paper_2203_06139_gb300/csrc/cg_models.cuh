@@ -104,12 +104,12 @@ __device__ __forceinline__ void gp1_elem_fp64(double x, double y, const GP1Const
     } else if (OBJ == CG_OBJ_POISSON) {
         const double rf = 1.0 / f;
         T = (y > 0.0) ? f - y * log(f) : f;
-        g = 1.0 - y * rf;
+        g = (y > 0.0) ? 1.0 - y * rf : 1.0;   // empty bin: T = f, even where f underflows to 0
         bad |= (y > 0.0) && !(f > 0.0);
     } else {  // Baker-Cousins
         const double rf = 1.0 / f;
         T = (y > 0.0) ? 2.0 * (f - y + y * log(y * rf)) : 2.0 * f;
-        g = 2.0 * (1.0 - y * rf);
+        g = (y > 0.0) ? 2.0 * (1.0 - y * rf) : 2.0;
         bad |= (y > 0.0) && !(f > 0.0);
     }
     bad |= !isfinite(T);
@@ -257,7 +257,7 @@ __device__ __forceinline__ void rg2_elem_fp64(double x, double y, double n, cons
     }
     const double rm = 1.0 / mu;
     const double T = (n > 0.0) ? mu - n * log(mu) : mu;
-    const double g = 1.0 - n * rm;
+    const double g = (n > 0.0) ? 1.0 - n * rm : 1.0;
     bad |= ((n > 0.0) && !(mu > 0.0)) || !isfinite(T);
     acc[0] += T;
 #pragma unroll

@@ -347,12 +347,13 @@ def bench(args):
     t_train = time.perf_counter() - t0
     ev = evaluate(net)
     line = {"metric": "gradient evals/s and bin-grads/s (frac of roofline); time-to-fit vs plain path",
-            "workload": "c5", "value": ev["production"]["ms"] / 1e3, "unit": "s time-to-fit (65,536 histograms)",
+            "workload": "c5", "value": ev["learned"]["ms"] / 1e3, "unit": "s time-to-fit (65,536 histograms)",
             "higher_is_better": False,
             "config": {"workload": "3 Gaussians + linear, 2048 bins, Baker-Cousins NLL, 65,536 histograms; MLP "
                                    "256-512-512-11 BF16 trained on %d method-generated fits" % int(x.shape[0])},
             "heuristic_start": ev["heuristic"], "learned_start": ev["learned"], "production": ev["production"],
-            "speedup_vs_heuristic": ev["heuristic"]["ms"] / ev["production"]["ms"],
+            "speedup_vs_heuristic": ev["heuristic"]["ms"] / ev["learned"]["ms"],
+            "speedup_vs_heuristic_with_refit": ev["heuristic"]["ms"] / ev["production"]["ms"],
             "same_minimum_frac": ev["same_minimum_frac"],
             "nll_learned_le_heuristic_frac": ev["nll_learned_le_heuristic_frac"],
             "training": {"seconds_data": t_data, "seconds_train": t_train, "steps": net.step,

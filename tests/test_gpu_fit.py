@@ -159,3 +159,108 @@ def test_batched_fit_df64_reaches_oracle_minimum(dev, obj, K, D, pm):
         y = d["y"][d["offsets"][h]:d["offsets"][h + 1]]
         ref = oracle_fit(y, K, D, pm, OBJ_MAP[obj], 0.0, 1.0, start[h], max_iter=400)
         assert abs(F[h] - ref["F"]) <= 1e-6 * abs(ref["F"]), (h, F[h], ref["F"])
+
+
+def _narrow_peak_batch(ns, seed=5):
+    """One narrow Gaussian and no background on [0, 1]: far from the peak the
+    model underflows the double-float exponential, so those bins take the
+    FP64 fallback of the df64 bin loop."""
+    rng = np.random.default_rng(seed)
+    ys, starts = [], []
+    for n in ns:
+        th = np.array([rng.uniform(200.0, 2000.0), rng.uniform(0.4, 0.6), rng.uniform(0.01, 0.03)])
+        ys.append(rng.poisson(synth.expected_counts_1d(1, -1, 0, 0.0, 1.0, n, th)).astype(float))
+        starts.append(th * rng.uniform(0.95, 1.05, 3))
+    offsets = np.concatenate([[0], np.cumsum([len(y) for y in ys])]).astype(np.int64)
+    H = len(ns)
+    return dict(y=np.concatenate(ys), offsets=offsets, lo=np.zeros(H), hi=np.ones(H), start=np.stack(starts),
+                H=H, K=1, D=-1, pm=0)
+
+
+def _init_case(name):
+    if name == "chi2_gauss_quadratic":
+        d = small_c4(H=16)
+        d.update(K=1, D=2, pm=1)
+        return d, cg.OBJ_CHI2
+    d = _narrow_peak_batch([100, 700, 3000, 12000, 40000])
+    return d, (cg.OBJ_POISSON if name == "poisson_narrow_peak" else cg.OBJ_POISSON_BC)
+
+
+@pytest.mark.parametrize("name", ["chi2_gauss_quadratic", "poisson_narrow_peak", "bc_narrow_peak"])
+def test_init_df64_matches_oracle_gn_and_gradient(dev, name):
+    """The df64 init sweep (gradient and Gauss-Newton terms in one pass over
+    the bins) against the oracle: value and gradient to 1e-10, the GN
+    diagonal the inverse Hessian starts from to 1e-10."""
+    d, obj = _init_case(name)
+    K, D, pm = d["K"], d["D"], d["pm"]
+    P = 3 * K + D + 1
+    b = HistBatch(d["y"], d["offsets"], d["lo"], d["hi"], K, D, obj, poly_mode=pm, precision=cg.PREC_DF64)
+    f = BatchFitter(b, TileMap(1024, 8192, 256, 2))
+    st = f.init(torch.tensor(d["start"], device=dev))
+    raw = st.d.cpu().numpy()
+    for h in range(d["H"]):
+        y = d["y"][d["offsets"][h]:d["offsets"][h + 1]]
+        ref = oracle.binned1d(K, D, pm, OBJ_MAP[obj], y, 0.0, 1.0, d["start"][h])
+        gn = oracle.binned1d_gn(K, D, pm, OBJ_MAP[obj], y, 0.0, 1.0, d["start"][h])
+        assert abs(raw[h, 180] - ref.value) <= 1e-10 * abs(ref.value), (h, raw[h, 180], ref.value)
+        assert max_rel_err(raw[h, 12:12 + P], ref.grad, ref.scale) <= 1e-10, h
+        np.testing.assert_allclose(1.0 / raw[h, 168:168 + P], gn, rtol=1e-10)
+    assert torch.all(st.status == cg.FIT_RUNNING)
+
+
+@pytest.mark.parametrize("obj", [cg.OBJ_POISSON, cg.OBJ_POISSON_BC])
+def test_batch_gradient_df64_fallback_bins(dev, obj):
+    """Per-histogram df64 gradients where most bins take the FP64 fallback."""
+    d = _narrow_peak_batch([64, 1000, 5000, 33000], seed=6)
+    b = HistBatch(d["y"], d["offsets"], d["lo"], d["hi"], 1, -1, obj, precision=cg.PREC_DF64)
+    th = np.concatenate([d["start"], d["start"] * 1.01])
+    b2 = HistBatch(np.concatenate([d["y"], d["y"]]), np.concatenate([d["offsets"][:-1], d["offsets"] + d["offsets"][-1]]),
+                   np.zeros(8), np.ones(8), 1, -1, obj, precision=cg.PREC_DF64)
+    for batch, thetas in ((b, d["start"]), (b2, th)):
+        v, g = batch.gradient(torch.tensor(thetas, device=dev))
+        v, g = v.cpu().numpy(), g.cpu().numpy()
+        for h in range(len(thetas)):
+            hh = h % d["H"]
+            y = d["y"][d["offsets"][hh]:d["offsets"][hh + 1]]
+            ref = oracle.binned1d(1, -1, 0, OBJ_MAP[obj], y, 0.0, 1.0, thetas[h])
+            assert max_rel_err(g[h], ref.grad, ref.scale) <= 1e-10, h
+            assert abs(v[h] - ref.value) <= 1e-10 * abs(ref.value), h
+
+
+@pytest.mark.slow
+def test_df64_batch_longest_histograms_use_fp64(dev):
+    """A histogram of 2^24 + 5 bins is past the range where the df64 bin
+    centres are exact; the df64 batch evaluates it in FP64 and still matches
+    the oracle (gradient and init), next to a short one that stays df64."""
+    th = np.array([[1500.0, 0.45, 0.02, 30.0, 3.0, -2.0], [800.0, 0.6, 0.05, 20.0, 1.0, 1.0]])
+    ns = [(1 << 24) + 5, 1000]
+    rng = np.random.default_rng(8)
+    ys = [rng.poisson(synth.expected_counts_1d(1, 2, 1, 0.0, 1.0, n, t)).astype(float) for n, t in zip(ns, th)]
+    offsets = np.array([0, ns[0], ns[0] + ns[1]], dtype=np.int64)
+    b = HistBatch(np.concatenate(ys), offsets, np.zeros(2), np.ones(2), 1, 2, cg.OBJ_CHI2, poly_mode=1,
+                  precision=cg.PREC_DF64)
+    start = th * 1.02
+    v, g = b.gradient(torch.tensor(start, device=dev))
+    st = BatchFitter(b, TileMap(1024, 8192, 256, 2)).init(torch.tensor(start, device=dev))
+    raw = st.d.cpu().numpy()
+    for h in range(2):
+        ref = oracle.binned1d(1, 2, 1, oracle.CHI2, ys[h], 0.0, 1.0, start[h])
+        gn = oracle.binned1d_gn(1, 2, 1, oracle.CHI2, ys[h], 0.0, 1.0, start[h])
+        assert max_rel_err(g[h].cpu().numpy(), ref.grad, ref.scale) <= 1e-10
+        assert abs(float(v[h]) - ref.value) <= 1e-10 * abs(ref.value)
+        np.testing.assert_allclose(1.0 / raw[h, 168:174], gn, rtol=1e-10)
+
+
+def test_batched_fit_df64_fallback_bins_reach_oracle_minimum(dev):
+    """Poisson fits of one narrow peak without background: most bins take
+    the FP64 fallback inside warp, CTA and cluster units alike."""
+    d = _narrow_peak_batch([100, 700, 3000, 12000, 40000], seed=7)
+    b = HistBatch(d["y"], d["offsets"], d["lo"], d["hi"], 1, -1, cg.OBJ_POISSON, precision=cg.PREC_DF64)
+    f = BatchFitter(b, TileMap(1024, 8192, 256, 4))
+    f.init(torch.tensor(d["start"], device=dev))
+    st = f.step(200, 1e-12)
+    F = st.f.cpu().numpy()
+    for h in range(d["H"]):
+        y = d["y"][d["offsets"][h]:d["offsets"][h + 1]]
+        ref = oracle_fit(y, 1, -1, 0, oracle.POISSON, 0.0, 1.0, d["start"][h], max_iter=400)
+        assert abs(F[h] - ref["F"]) <= 1e-6 * abs(ref["F"]), (h, F[h], ref["F"])
