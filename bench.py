@@ -366,16 +366,24 @@ def _traffic_if_current(rec, n_events, n_points):
     return rec["bytes"] if h.hexdigest()[:16] == rec["sources_sha256_16"] else None
 
 
-def df64_roofline(dur_s, n_units, rates, sm_max_mhz):
+# FP32-pipe operations of one bin at one parameter point in the double-float
+# 1-D kernel for one Gaussian + linear background under chi2, counted from its
+# arithmetic (csrc/cg_models_df64.cuh): bin centre 24, Horner 18, the peak
+# (difference, square, exponent product, exp 60, product, sum) 100, count
+# split 2, chi2 term (reciprocal 8, residual, two products, adjoint) 36, value
+# accumulation 8, peak adjoints 36, polynomial adjoints 20.
+DF64_GP1_OPS = 244
+
+
+def df64_roofline(dur_s, n_units, rates, sm_max_mhz, ops=DF64_MIX_OPS, kernel="k_mix_df64", unit="event-point"):
     """ALU roofline of the double-float kernel: FP32-pipe operations / time vs the
     FP32 unit rate at the maximum SM clock (152 SMs x 128 lanes x 2 flop)."""
     nsm = rates["n_sm"] if rates else 152
     peak = nsm * 128 * 2 * (sm_max_mhz or 2070.0) * 1e6 / 1e12
-    achieved = DF64_MIX_OPS * n_units * 2 / dur_s / 1e12
+    achieved = ops * n_units * 2 / dur_s / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "k_mix_df64",
-            "work_per_unit": "%d FP32-pipe operations per event-point (FMA-equivalent flops = 2 per op)"
-                             % DF64_MIX_OPS,
+            "traffic": None, "kernel": kernel,
+            "work_per_unit": "%d FP32-pipe operations per %s (FMA-equivalent flops = 2 per op)" % (ops, unit),
             "peak_basis": "FP32 unit: %d SMs x 128 lanes x 2 flop x %.0f MHz (unit counts and max clock)"
                           % (nsm, sm_max_mhz or 2070.0)}
 
@@ -416,7 +424,36 @@ def run_c1(args):
     v = torch.empty(100, dtype=torch.float64, device="cuda")
     g = torch.empty((100, 5), dtype=torch.float64, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    ms = _timed(lambda: cg.batch_gradient(pb, th, v, g), args.steps, max(3, args.warmup), flush)
+    ms_eager = _timed(lambda: cg.batch_gradient(pb, th, v, g), args.steps, max(3, args.warmup), flush)
+    # the step as a repeated evaluation runs it: the one cg_batch_gradient call
+    # (tile kernel + finalize) captured in a CUDA graph and replayed
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        cg.batch_gradient(pb, th, v, g)
+    ms = _timed(graph.replay, args.steps, max(3, args.warmup), flush)
+    # the tile kernel alone (events around its launch, inside cg_batch_gradient)
+    k0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    k1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stream = torch.cuda.current_stream()
+    for e in k0 + k1:
+        e.record(stream)
+    clocks = Clocks(0)
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.zero_()
+        cg.set_profile_events(k0[i], k1[i])
+        cg.batch_gradient(pb, th, v, g)
+        cg.set_profile_events(None, None)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    kern_s = sum(a.elapsed_time(b) for a, b in zip(k0, k1)) / 1e3 / args.steps
+    rates = unit_rates()
+    if prec == cg.PREC_DF64:
+        roof = df64_roofline(kern_s, 100 * 10000, rates, clk.get("sm_max_mhz"), ops=DF64_GP1_OPS,
+                             kernel="k_gp1_df64", unit="bin-point")
+    else:
+        roof = None
     th0 = torch.tensor(synth.c1_theta_points(1)[0], device="cuda")
     sf = SingleFitter(pb64)
     torch.cuda.synchronize()
@@ -434,11 +471,13 @@ def run_c1(args):
             "higher_is_better": True, "ms_per_step": ms, "grad_evals_per_s": 100 / (ms / 1e3),
             "dtype": "f64" if prec == cg.PREC_FP64 else "df64",
             "config": {"workload": "chi2, Gaussian + linear, 10,000 bins x 100 parameter points",
-                       "l2": "flushed before every timed step"},
+                       "l2": "flushed before every timed step",
+                       "step": "one cg_batch_gradient call replayed from a CUDA graph"},
+            "eager_ms_per_step": ms_eager,
             "full_fit": {"plain_path_s": t_single, "plain_iters": int(st.iters[0]), "plain_evals": int(st.n_eval[0]),
                          "plain_F": float(st.f[0]), "one_cluster_fit_ms": ms_fit,
                          "one_cluster_F": float(bf.states.f[0]), "status": int(bf.states.status[0])},
-            "gpu_launches": 2 * args.steps}
+            "gpu_launches": 2 * args.steps, "kernel_ms": kern_s * 1e3, "roofline": roof, "clocks": clk}
     print(json.dumps(line), flush=True)
 
 
@@ -483,7 +522,7 @@ def run_c4(args):
     prec = cg.PREC_DF64 if args.prec == "df64" else cg.PREC_FP64
     b = HistBatch(d["y"], d["offsets"], d["lo"], d["hi"], 1, 2, cg.OBJ_CHI2, poly_mode=1, precision=prec)
     th0 = torch.tensor(d["start"], device="cuda")
-    best, timings = autotune(b, th0, n_steps=3)
+    best, timings = autotune(b, th0, n_steps=50)   # the iteration count of the timed fit
     f = BatchFitter(b, best)
     f.capture(50, 1e-9, theta0=th0)   # init + 50 iterations in one graph
     def batched():

@@ -191,39 +191,46 @@ __global__ void __launch_bounds__(NT, 2) k_gp1_df64(GP1Data d, const double* __r
     const int P = 3 * K + d.D + 1;
     for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
         const int c = t / tg.n_theta, th = t - c * tg.n_theta;   // chunk-major: a chunk stays in L2 across points
-        if (threadIdx.x == 0) {
-            cs_bad = gp1_prologue<K>(theta + (size_t)th * P, d.D, cs64) ? 0 : 1;
-            gp1_split(cs64, d.lo, d.h, d.au, d.bu, K, cs);
+        if (threadIdx.x < 32) {
+            const bool ok = gp1_prologue_warp<K, true>(theta + (size_t)th * P, d.D, d.lo, d.h, d.au, d.bu, cs64, cs);
+            if (threadIdx.x == 0) cs_bad = ok ? 0 : 1;
         }
         __syncthreads();
+        // per-thread sums stay df64 (FP32 pipe) up to the per-warp conversion
         DfAcc acc[NACC];
-        double sum[NACC];
+        df run[NACC];
 #pragma unroll
         for (int a = 0; a < NACC; ++a) {
             acc[a].s = acc[a].c = 0.0f;
-            sum[a] = 0.0;
+            run[a] = df_make(0.0f, 0.0f);
         }
         bool bad = false;
         int cnt = 0;
-        const int64_t e0 = (int64_t)c * tg.chunk;
-        const int64_t e1 = min(tg.n_elem, e0 + tg.chunk);
-        for (int64_t i = e0 + threadIdx.x; i < e1; i += NT) {
+        const int e0 = (int)((int64_t)c * tg.chunk);   // n < 2^24 on this path
+        const int e1 = (int)min(tg.n_elem, (int64_t)e0 + tg.chunk);
+        float fi = (float)(e0 + (int)threadIdx.x);     // == i exactly
+        for (int i = e0 + threadIdx.x; i < e1; i += NT, fi += (float)NT) {
             const double yv = __ldg(d.y + i);
-            const df X = d.centres ? df_split(__ldg(d.centres + i)) : gp1_centre_df(cs, i);
+            const df X = d.centres ? df_split(__ldg(d.centres + i)) : gp1_centre_df(cs, fi);
             if (!gp1_elem_df64<K, OBJ, VO>(X, yv, cs, d.D, d.pm, acc, tab)) {
-                const double x = d.centres ? d.centres[i] : fma((double)i + 0.5, d.h, d.lo);
-                gp1_elem_fp64<K, OBJ>(x, yv, cs64, d, sum, bad);
+                double tv[NACC];
+                int b = 0;
+                gp1_elem_fp64_ool<K, OBJ>(d.centres ? d.centres[i] : fma((double)i + 0.5, d.h, d.lo), yv, cs64, d,
+                                          tv, &b);
+                bad |= (b != 0);
+#pragma unroll
+                for (int a = 0; a < NACC; ++a) run[a] = df_add(run[a], df_from_double(tv[a]));
             }
             if (++cnt == kFlush) {
 #pragma unroll
-                for (int a = 0; a < NACC; ++a) dfacc_flush(acc[a], sum[a]);
+                for (int a = 0; a < NACC; ++a) dfacc_fold(acc[a], run[a]);
                 cnt = 0;
             }
         }
 #pragma unroll
-        for (int a = 0; a < NACC; ++a) dfacc_flush(acc[a], sum[a]);
+        for (int a = 0; a < NACC; ++a) dfacc_fold(acc[a], run[a]);
         const int any_bad = __syncthreads_or(bad ? 1 : 0) | cs_bad;
-        block_sum<NACC, NT>(sum, red, tot);
+        block_sum_df<NACC, NT>(run, red, tot);
         write_partial<NACC>(part, tg, th, c, tot, any_bad);
     }
 }

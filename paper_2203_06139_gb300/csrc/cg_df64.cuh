@@ -154,17 +154,15 @@ struct DfTables {
     float2 invF[64];    // 1/F_j
 };
 
+#include "cg_df64_tables.inc"
+
+// Copy the tables (generated, exactly rounded float pairs) into shared memory.
 // Call from all threads of a block, followed by __syncthreads().
 __device__ __forceinline__ void df_tables_init(DfTables& t) {
     for (int j = threadIdx.x; j < 64; j += blockDim.x) {
-        const double e = exp2((double)j / 64.0);
-        const double F = 1.0 + (2.0 * j + 1.0) / 128.0;
-        const double lf = log(F);
-        const double iv = 1.0 / F;
-        float h;
-        h = __double2float_rn(e);  t.exp2j[j] = make_float2(h, __double2float_rn(e - (double)h));
-        h = __double2float_rn(lf); t.logF[j] = make_float2(h, __double2float_rn(lf - (double)h));
-        h = __double2float_rn(iv); t.invF[j] = make_float2(h, __double2float_rn(iv - (double)h));
+        t.exp2j[j] = g_df_exp2j[j];
+        t.logF[j] = g_df_logF[j];
+        t.invF[j] = g_df_invF[j];
     }
 }
 
@@ -293,6 +291,81 @@ __device__ __forceinline__ void dfacc_flush(DfAcc& A, double& sum) {
     sum += (double)A.s + (double)A.c;
     A.s = 0.0f;
     A.c = 0.0f;
+}
+
+// Fold a compensated accumulator into a per-thread df64 running sum (FP32 pipe).
+__device__ __forceinline__ void dfacc_fold(DfAcc& A, df& run) {
+    run = df_add(run, df_make(A.s, A.c));
+    A.s = A.c = 0.0f;
+}
+
+// Warp butterfly sum of df64 values on the FP32 pipe.  TwoSum is exact and
+// symmetric, so both lanes of every exchange form the same sum and all lanes
+// end with the same total.
+__device__ __forceinline__ df warp_sum_df(df v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = df_add(v, df_make(__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)));
+    return v;
+}
+
+// Warp sums of N df64 values per lane by a reduce-scatter butterfly (FP32
+// pipe).  With NP = N rounded up to a power of two (at most 32), each of the
+// first log2(NP) exchanges (lane distances 16, 8, ...) has every lane keep
+// half of its values and add its partner's copy of that half, so the number
+// of values moved halves at every step; the exchanges left are plain
+// butterflies on the single value that remains.  Each total passes through
+// five additions in a fixed order, as in a butterfly per value, at about a
+// third of the operations for 6-8 values.  Accumulator a ends in the lanes
+// whose top log2(NP) lane-id bits spell a; the first of them writes its FP64
+// conversion to dst[a * stride].
+template <int N>
+__device__ __forceinline__ void warp_sum_df_to(const df (&v)[N], double* dst, int stride) {
+    static_assert(N >= 1 && N <= 32, "at most one value per lane after the scatter");
+    constexpr int L = (N <= 1) ? 0 : (N <= 2) ? 1 : (N <= 4) ? 2 : (N <= 8) ? 3 : (N <= 16) ? 4 : 5;
+    constexpr int NP = 1 << L;
+    const int lane = threadIdx.x & 31;
+    df w[NP];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) w[a] = (a < N) ? v[a] : df_make(0.0f, 0.0f);
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        const int o = 16 >> l;
+        const int H = (NP >> l) / 2;   // values kept after this exchange
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+            const df send = up ? w[j] : w[j + H];
+            const df keep = up ? w[j + H] : w[j];
+            const df recv = df_make(__shfl_xor_sync(0xffffffffu, send.h, o), __shfl_xor_sync(0xffffffffu, send.l, o));
+            w[j] = df_add(keep, recv);
+        }
+    }
+#pragma unroll
+    for (int o = 16 >> L; o > 0; o >>= 1)
+        w[0] = df_add(w[0], df_make(__shfl_xor_sync(0xffffffffu, w[0].h, o), __shfl_xor_sync(0xffffffffu, w[0].l, o)));
+    const int a = lane >> (5 - L);
+    if ((lane & ((1 << (5 - L)) - 1)) == 0 && a < N) dst[a * stride] = df_to_double(w[0]);
+}
+
+// Block sum of NACC per-thread df64 values in a fixed order: warp
+// reduce-scatter sums in df64, one conversion to FP64 per warp and
+// accumulator, then thread a adds accumulator a over the warps in warp order.
+// red: shared, NACC * (NT/32) doubles; out: shared, NACC doubles, valid in
+// all threads on return.
+template <int NACC, int NT>
+__device__ __forceinline__ void block_sum_df(const df (&v)[NACC], double* red, double* out) {
+    static_assert(NACC <= NT, "one thread per accumulator in the last step");
+    constexpr int NW = NT / 32;
+    const int wid = threadIdx.x >> 5;
+    warp_sum_df_to<NACC>(v, red + wid, NW);
+    __syncthreads();
+    if (threadIdx.x < NACC) {
+        double s = 0.0;
+        for (int w = 0; w < NW; ++w) s += red[threadIdx.x * NW + w];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
 }
 
 }  // namespace cg

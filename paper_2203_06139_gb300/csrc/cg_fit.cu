@@ -109,8 +109,10 @@ __device__ __forceinline__ void gn_elem_fp64(double x, double y, const GP1Consts
     const double u = dd.pm ? fma(x, dd.au, dd.bu) : x;
     double f = 0.0;
 #pragma unroll
-    for (int j = 3; j >= 0; --j)
-        if (j <= dd.D) f = fma(f, u, cs.poly[j]);
+    for (int j = 3; j >= 0; --j) {
+        if (j == dd.D) f = cs.poly[j];
+        else if (j < dd.D) f = fma(f, u, cs.poly[j]);
+    }
     double dk[K], ek[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -134,7 +136,7 @@ __device__ __forceinline__ void gn_elem_fp64(double x, double y, const GP1Consts
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         if (j <= dd.D) acc[1 + 3 * K + j] = fma(h, up * up, acc[1 + 3 * K + j]);
-        up *= u;
+        if (j < dd.D) up *= u;
     }
 }
 
@@ -149,13 +151,6 @@ __device__ __forceinline__ void gn_bins(const Geom& G, const GP1Consts& cs, cons
 // evaluated in FP64 whatever the batch precision.
 constexpr int64_t kDfMaxBins = (int64_t)1 << 24;
 constexpr int kFitFlush = 32;
-
-// Fold a compensated accumulator into a per-thread df64 running sum (FP32
-// pipe only; the one conversion to FP64 happens after the last bin).
-__device__ __forceinline__ void dfacc_fold(DfAcc& A, df& run) {
-    run = df_add(run, df_make(A.s, A.c));
-    A.s = A.c = 0.0f;
-}
 
 // FP64 terms of one bin that the df64 path hands back (rare).  Kept out of
 // line so that the bin loop keeps no FP64 state: out[0..N) gradient
@@ -179,19 +174,19 @@ static __device__ __noinline__ void gp1_fallback_fp64(double x, double y, const 
 }
 
 // The same in double-float arithmetic (FP32 pipe): every kFitFlush bins the
-// compensated accumulators are folded into df64 running sums, which are added
-// to the FP64 accumulators once at the end; elements that need it are
-// evaluated in FP64 and folded into the same running sums.  GN: also the
-// Gauss-Newton diagonal terms, into gn[].
+// compensated accumulators are folded into the df64 running sums run[]
+// (zeroed here), which leave the thread as df64 and are converted to FP64
+// once per warp by the reductions; elements that need it are evaluated in
+// FP64 and folded into the same running sums.  GN: also the Gauss-Newton
+// diagonal terms, into grun[].
 // Requires G.n < kDfMaxBins (bin index and centre exact in FP32 / df64).
 template <int K, int OBJ, bool GN>
 __device__ __forceinline__ void acc_bins_df64(const Geom& G, const GP1Consts& cs, const GP1Df& cd,
                                               const GP1Data& dd, const DfTables& tab, int t0, int T,
-                                              double (&acc)[GP1Acc<K>::N], double (&gn)[GP1Acc<K>::N], bool& bad) {
+                                              df (&run)[GP1Acc<K>::N], df (&grun)[GP1Acc<K>::N], bool& bad) {
     constexpr int N = GP1Acc<K>::N;
     constexpr int NG = GN ? N : 1;
     DfAcc da[N], ga[NG];
-    df run[N], grun[NG];
 #pragma unroll
     for (int a = 0; a < N; ++a) {
         da[a].s = da[a].c = 0.0f;
@@ -231,42 +226,42 @@ __device__ __forceinline__ void acc_bins_df64(const Geom& G, const GP1Consts& cs
         }
     }
 #pragma unroll
-    for (int a = 0; a < N; ++a) {
-        dfacc_fold(da[a], run[a]);
-        acc[a] += df_to_double(run[a]);
-    }
+    for (int a = 0; a < N; ++a) dfacc_fold(da[a], run[a]);
     if (GN) {
 #pragma unroll
-        for (int a = 1; a < NG; ++a) {
-            dfacc_fold(ga[a], grun[a]);
-            gn[a] += df_to_double(grun[a]);
-        }
+        for (int a = 1; a < NG; ++a) dfacc_fold(ga[a], grun[a]);
     }
 }
 
 // ---------------------------------------------------------------------------
 // Reductions of the accumulators over one unit; result in tot[] (shared).
 // ---------------------------------------------------------------------------
+// Warp totals of N accumulators into dst[a * stride]: FP64 butterflies for
+// FP64 values; for df64 values the reduce-scatter sum on the FP32 pipe with
+// one conversion per accumulator.
 template <int N>
-__device__ __forceinline__ void reduce_warp(const double (&acc)[N], double* tot) {
+__device__ __forceinline__ void warp_totals(const double (&acc)[N], double* dst, int stride) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int a = 0; a < N; ++a) {
         const double v = warp_sum(acc[a]);
-        if (lane == 0) tot[a] = v;
+        if (lane == 0) dst[a * stride] = v;
     }
-    __syncwarp();
+}
+template <int N>
+__device__ __forceinline__ void warp_totals(const df (&acc)[N], double* dst, int stride) {
+    warp_sum_df_to<N>(acc, dst, stride);
 }
 
-// red: shared [N][kMaxWarpsPerCta]
-template <int N>
-__device__ __forceinline__ void reduce_cta(const double (&acc)[N], double* red, double* tot) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int a = 0; a < N; ++a) {
-        const double v = warp_sum(acc[a]);
-        if (lane == 0) red[a * kMaxWarpsPerCta + wid] = v;
-    }
+template <int N, typename T>
+__device__ __forceinline__ void reduce_warp(const T (&acc)[N], double* tot) {
+    warp_totals<N>(acc, tot, 1);
+    __syncwarp();
+}
+template <int N, typename T>
+__device__ __forceinline__ void reduce_cta(const T (&acc)[N], double* red, double* tot) {
+    const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    warp_totals<N>(acc, red + wid, kMaxWarpsPerCta);
     __syncthreads();
     if (threadIdx.x < N) {
         double s = 0.0;
@@ -275,13 +270,10 @@ __device__ __forceinline__ void reduce_cta(const double (&acc)[N], double* red, 
     }
     __syncthreads();
 }
-
-// CTA sums into `part`, then rank 0 adds the ranks' parts in rank order and
-// every rank copies the total.
-template <int N>
-__device__ __forceinline__ void reduce_cluster(const double (&acc)[N], double* red, double* part, double* tot) {
+template <int N, typename T>
+__device__ __forceinline__ void reduce_cluster(const T (&acc)[N], double* red, double* part, double* tot) {
     cgx::cluster_group cl = cgx::this_cluster();
-    reduce_cta<N>(acc, red, part);
+    reduce_cta<N, T>(acc, red, part);
     cl.sync();
     const unsigned nr = cl.num_blocks();
     if (cl.block_rank() == 0 && threadIdx.x < N) {
@@ -426,6 +418,31 @@ __device__ __forceinline__ void ctl_after_eval(FitSm& s, int lane, double tol) {
     __syncwarp();
 }
 
+// Sum one unit's accumulators into tot[] (shared) and OR its domain flags.
+__device__ __forceinline__ void set_flag(double& x, bool b) { x = b ? 1.0 : 0.0; }
+__device__ __forceinline__ void set_flag(df& x, bool b) { x = df_make(b ? 1.0f : 0.0f, 0.0f); }
+
+template <int UNIT, int N, typename T>
+__device__ __forceinline__ int unit_reduce(const T (&v)[N], bool bad, double* red, double* part, double* tot) {
+    if (UNIT == UNIT_WARP) {
+        const int any_bad = __any_sync(0xffffffffu, bad);
+        reduce_warp<N, T>(v, tot);
+        return any_bad;
+    }
+    if (UNIT == UNIT_CTA) {
+        const int any_bad = __syncthreads_or(bad);
+        reduce_cta<N, T>(v, red, tot);
+        return any_bad;
+    }
+    // the flag travels as one more accumulator through the cluster sum
+    T v2[N + 1];
+#pragma unroll
+    for (int a = 0; a < N; ++a) v2[a] = v[a];
+    set_flag(v2[N], bad);
+    reduce_cluster<N + 1, T>(v2, red, part, tot);
+    return tot[N] != 0.0;
+}
+
 // ---------------------------------------------------------------------------
 // One objective evaluation of histogram G at s.tt by a unit (all threads).
 // ---------------------------------------------------------------------------
@@ -436,32 +453,23 @@ __device__ __forceinline__ void unit_eval(FitSm& s, GP1Consts& cs, GP1Df& cd, co
     constexpr int N = GP1Acc<K>::N;
     const int lane = threadIdx.x & 31;
     const bool leader = (UNIT == UNIT_WARP) ? (lane == 0) : (threadIdx.x == 0);
-    if (leader) {
-        s.bad = gp1_prologue<K>(s.tt, D, cs) ? 0 : 1;
-        if (PREC == CG_PREC_DF64) gp1_split(cs, G.lo, G.hw, dd.au, dd.bu, K, cd);
+    if (UNIT == UNIT_WARP || threadIdx.x < 32) {   // the constants, one per lane of the control warp
+        const bool ok = gp1_prologue_warp<K, PREC == CG_PREC_DF64>(s.tt, D, G.lo, G.hw, dd.au, dd.bu, cs, cd);
+        if (lane == 0) s.bad = ok ? 0 : 1;
     }
     if (UNIT == UNIT_WARP) __syncwarp(); else __syncthreads();
-    double acc[N];
-#pragma unroll
-    for (int a = 0; a < N; ++a) acc[a] = 0.0;
     bool bad = false;
-    if (PREC == CG_PREC_DF64 && G.n < kDfMaxBins) acc_bins_df64<K, OBJ, false>(G, cs, cd, dd, tab, t0, T, acc, acc, bad);
-    else acc_bins<K, OBJ>(G, cs, dd, t0, T, acc, bad);
     int any_bad;
-    if (UNIT == UNIT_WARP) {
-        any_bad = __any_sync(0xffffffffu, bad);
-        reduce_warp<N>(acc, tot);
-    } else if (UNIT == UNIT_CTA) {
-        any_bad = __syncthreads_or(bad);
-        reduce_cta<N>(acc, red, tot);
+    if (PREC == CG_PREC_DF64 && G.n < kDfMaxBins) {
+        df v[N], unused[N];
+        acc_bins_df64<K, OBJ, false>(G, cs, cd, dd, tab, t0, T, v, unused, bad);
+        any_bad = unit_reduce<UNIT, N>(v, bad, red, part, tot);
     } else {
-        // the flag travels as one more accumulator through the cluster sum
-        double acc2[N + 1];
+        double acc[N];
 #pragma unroll
-        for (int a = 0; a < N; ++a) acc2[a] = acc[a];
-        acc2[N] = bad ? 1.0 : 0.0;
-        reduce_cluster<N + 1>(acc2, red, part, tot);
-        any_bad = tot[N] != 0.0;
+        for (int a = 0; a < N; ++a) acc[a] = 0.0;
+        acc_bins<K, OBJ>(G, cs, dd, t0, T, acc, bad);
+        any_bad = unit_reduce<UNIT, N>(acc, bad, red, part, tot);
     }
     if (leader) {
         EpiParams ep;
@@ -665,26 +673,30 @@ __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
         dd.D = a.D;
         dd.pm = a.pm;
         dd.vec_ok = 0;
-        if (threadIdx.x == 0) {
-            cs_bad = gp1_prologue<K>(th, a.D, cs) ? 0 : 1;
-            if (PREC == CG_PREC_DF64) gp1_split(cs, G.lo, G.hw, dd.au, dd.bu, K, cd);
+        if (threadIdx.x < 32) {
+            const bool ok = gp1_prologue_warp<K, PREC == CG_PREC_DF64>(th, a.D, G.lo, G.hw, dd.au, dd.bu, cs, cd);
+            if (threadIdx.x == 0) cs_bad = ok ? 0 : 1;
         }
         __syncthreads();
-        double acc[N], gacc[N];
-#pragma unroll
-        for (int i = 0; i < N; ++i) acc[i] = gacc[i] = 0.0;
         bool bad = false;
+        int any_bad;
         if (PREC == CG_PREC_DF64 && G.n < kDfMaxBins) {
             // mode 1: gradient and Gauss-Newton terms in one sweep over the bins
-            if constexpr (MODE == 0) acc_bins_df64<K, OBJ, false>(G, cs, cd, dd, tab, threadIdx.x, blockDim.x, acc, gacc, bad);
-            else acc_bins_df64<K, OBJ, true>(G, cs, cd, dd, tab, threadIdx.x, blockDim.x, acc, gacc, bad);
+            df v[N], gv[N];
+            acc_bins_df64<K, OBJ, MODE == 1>(G, cs, cd, dd, tab, threadIdx.x, blockDim.x, v, gv, bad);
+            any_bad = __syncthreads_or(bad) | cs_bad;
+            reduce_cta<N, df>(v, red, tot);
+            if constexpr (MODE == 1) reduce_cta<N, df>(gv, red, gn);
         } else {
+            double acc[N], gacc[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) acc[i] = gacc[i] = 0.0;
             acc_bins<K, OBJ>(G, cs, dd, threadIdx.x, blockDim.x, acc, bad);
             if constexpr (MODE == 1) gn_bins<K, OBJ>(G, cs, dd, threadIdx.x, blockDim.x, gacc);
+            any_bad = __syncthreads_or(bad) | cs_bad;
+            reduce_cta<N, double>(acc, red, tot);
+            if constexpr (MODE == 1) reduce_cta<N, double>(gacc, red, gn);
         }
-        const int any_bad = __syncthreads_or(bad) | cs_bad;
-        reduce_cta<N>(acc, red, tot);
-        if constexpr (MODE == 1) reduce_cta<N>(gacc, red, gn);
         if (threadIdx.x == 0) {
             EpiParams ep;
             ep.model = CG_MODEL_GAUSS_POLY;

@@ -85,8 +85,10 @@ __device__ __forceinline__ void gp1_elem_fp64(double x, double y, const GP1Const
     // forward: polynomial by Horner, then the peaks
     double f = 0.0;
 #pragma unroll
-    for (int j = 3; j >= 0; --j)
-        if (j <= d.D) f = fma(f, u, cs.poly[j]);
+    for (int j = 3; j >= 0; --j) {   // Horner from the leading coefficient
+        if (j == d.D) f = cs.poly[j];
+        else if (j < d.D) f = fma(f, u, cs.poly[j]);
+    }
     double dk[K > 0 ? K : 1], ek[K > 0 ? K : 1];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -127,7 +129,7 @@ __device__ __forceinline__ void gp1_elem_fp64(double x, double y, const GP1Const
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         if (j <= d.D) acc[1 + 3 * K + j] = fma(g, up, acc[1 + 3 * K + j]);
-        up *= u;
+        if (j < d.D) up *= u;
     }
 }
 

@@ -27,6 +27,69 @@ __device__ __forceinline__ void gp1_split(const GP1Consts& c64, double lo, doubl
     c.bu = df_from_double(bu);
 }
 
+// Per-point constants of the 1-D model computed by the 32 lanes of one warp,
+// one constant per lane (the FP64 division and the double splits run side by
+// side instead of in one thread): FP64 values into c64 and, with SPLIT, their
+// df64 splits into cd.  Returns, on every lane, whether the point is valid
+// (finite parameters, nonzero widths).  Call from a whole warp; the caller
+// synchronises before the constants are read.
+template <int K, bool SPLIT>
+__device__ __forceinline__ bool gp1_prologue_warp(const double* __restrict__ th, int D, double lo, double h,
+                                                  double au, double bu, GP1Consts& c64, GP1Df& cd) {
+    static_assert(3 * K + 8 <= 32, "one constant per lane");
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    double v = 0.0;
+    df* dst = nullptr;
+    if (lane < 3 * K) {
+        const int k = lane / 3, r = lane - 3 * k;
+        const double x = th[lane];
+        ok = isfinite(x);
+        if (r == 0) {
+            v = x;
+            c64.A[k] = v;
+            dst = &cd.A[k];
+        } else if (r == 1) {
+            v = x;
+            c64.mu[k] = v;
+            dst = &cd.mu[k];
+        } else {
+            v = -0.5 / (x * x);
+            ok = ok && x != 0.0;
+            c64.c[k] = v;
+            dst = &cd.c[k];
+        }
+    } else if (lane < 3 * K + 4) {
+        const int j = lane - 3 * K;
+        v = (j <= D) ? th[lane] : 0.0;
+        ok = isfinite(v);
+        c64.poly[j] = v;
+        dst = &cd.poly[j];
+    } else if (lane < 3 * K + 8) {
+        const int j = lane - 3 * K - 4;
+        v = (j == 0) ? lo : (j == 1) ? h : (j == 2) ? au : bu;
+        dst = (j == 0) ? &cd.lo : (j == 1) ? &cd.h : (j == 2) ? &cd.au : &cd.bu;
+    }
+    if (SPLIT && dst) *dst = df_from_double(v);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// One bin in FP64, out of line (the rare fallback of the df64 bin loops):
+// its accumulator terms into out[0..N), *bad set on a domain error.
+template <int K, int OBJ>
+static __device__ __noinline__ void gp1_elem_fp64_ool(double x, double y, const GP1Consts& cs, GP1Data dd,
+                                                      double* out, int* bad) {
+    constexpr int N = GP1Acc<K>::N;
+    double a[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) a[i] = 0.0;
+    bool b = false;
+    gp1_elem_fp64<K, OBJ>(x, y, cs, dd, a, b);
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = a[i];
+    *bad = b ? 1 : 0;
+}
+
 // Bin centre lo + (i + 0.5) h in df64 (i < 2^24).
 __device__ __forceinline__ df gp1_centre_df(const GP1Df& c, float fi) {
     const df t = two_sum(fi, 0.5f);
@@ -48,8 +111,10 @@ __device__ __forceinline__ bool gp1_elem_df64(df X, double yd, const GP1Df& c, i
     const df u = pm ? df_add(df_mul(X, c.au), c.bu) : X;
     df f = df_make(0.0f, 0.0f);
 #pragma unroll
-    for (int j = 3; j >= 0; --j)
-        if (j <= D) f = df_add(df_mul(f, u), c.poly[j]);
+    for (int j = 3; j >= 0; --j) {   // Horner from the leading coefficient
+        if (j == D) f = c.poly[j];
+        else if (j < D) f = df_add(df_mul(f, u), c.poly[j]);
+    }
     df dk[K > 0 ? K : 1], ek[K > 0 ? K : 1];
     bool fl = false;
 #pragma unroll
@@ -100,12 +165,15 @@ __device__ __forceinline__ bool gp1_elem_df64(df X, double yd, const GP1Df& c, i
             dfacc_add(gacc[2 + 3 * k], hd2);
             dfacc_add(gacc[3 + 3 * k], df_mul_nn(hd2, d2));
         }
-        const df u2 = df_sqr(u);
-        df up2 = df_make(1.0f, 0.0f);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (j <= D) dfacc_add(gacc[1 + 3 * K + j], df_mul_nn(hh, up2));
-            if (j < 3) up2 = df_mul(up2, u2);
+        if (D >= 0) dfacc_add(gacc[1 + 3 * K], hh);
+        if (D >= 1) {
+            const df u2 = df_sqr(u);
+            dfacc_add(gacc[2 + 3 * K], df_mul_nn(hh, u2));
+            if (D >= 2) {
+                const df u4 = df_sqr(u2);
+                dfacc_add(gacc[3 + 3 * K], df_mul_nn(hh, u4));
+                if (D >= 3) dfacc_add(gacc[4 + 3 * K], df_mul_nn(hh, df_mul(u4, u2)));
+            }
         }
     }
 #pragma unroll
@@ -116,11 +184,15 @@ __device__ __forceinline__ bool gp1_elem_df64(df X, double yd, const GP1Df& c, i
         dfacc_add(acc[2 + 3 * k], td);
         dfacc_add(acc[3 + 3 * k], df_mul_nn(td, dk[k]));
     }
-    df up = df_make(1.0f, 0.0f);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        if (j <= D) dfacc_add(acc[1 + 3 * K + j], df_mul_nn(g, up));
-        if (j < 3) up = df_mul(up, u);
+    // polynomial adjoints g u^j, powers only up to the degree
+    if (D >= 0) dfacc_add(acc[1 + 3 * K], g);
+    if (D >= 1) {
+        dfacc_add(acc[2 + 3 * K], df_mul_nn(g, u));
+        if (D >= 2) {
+            const df u2 = df_sqr(u);
+            dfacc_add(acc[3 + 3 * K], df_mul_nn(g, u2));
+            if (D >= 3) dfacc_add(acc[4 + 3 * K], df_mul_nn(g, df_mul(u2, u)));
+        }
     }
     return true;
 }

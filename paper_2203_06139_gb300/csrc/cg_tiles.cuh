@@ -96,10 +96,10 @@ inline cg_status launch_tiles(KernelT kern, int NT, const DataT& d, const double
 template <int NACC>
 __device__ __forceinline__ void write_partial(double* __restrict__ part, const TileGrid& tg, int th,
                                               int c, const double* tot, int bad) {
-    if (threadIdx.x == 0) {
+    // one value per thread: NACC sums and the domain flag
+    if (threadIdx.x <= NACC) {
         double* p = part + (size_t)th * (NACC + 1) * tg.nbx + c;
-        for (int a = 0; a < NACC; ++a) p[(size_t)a * tg.nbx] = tot[a];
-        p[(size_t)NACC * tg.nbx] = bad ? 1.0 : 0.0;
+        p[(size_t)threadIdx.x * tg.nbx] = (threadIdx.x < NACC) ? tot[threadIdx.x] : (bad ? 1.0 : 0.0);
     }
 }
 

@@ -232,8 +232,8 @@ class SingleFitter:
 # ----------------------------------------------------------------------------
 DEFAULT_CANDIDATES = [
     TileMap(w, c, t, k)
-    for (w, c, t, k) in [(512, 8192, 256, 4), (1024, 16384, 256, 4), (2048, 32768, 256, 4), (2048, 16384, 256, 8),
-                         (1024, 32768, 512, 2), (4096, 65536, 256, 1), (512, 4096, 128, 8), (2048, 1 << 30, 256, 1)]
+    for (w, c, t, k) in [(2048, 1 << 30, 256, 1), (512, 1 << 30, 256, 1), (2048, 32767, 256, 2), (2048, 16383, 256, 2),
+                         (2048, 32767, 256, 4), (1024, 16384, 256, 4), (4096, 65536, 256, 1), (512, 4096, 128, 8)]
 ]
 
 
@@ -248,11 +248,13 @@ def _cache_path():
 
 
 def autotune(batch, theta0, candidates=None, n_steps=5, tol=1e-9, use_cache=True):
-    """Time a few BFGS iterations of the whole batch under each candidate map
-    and return (best_map, timings).  Results are cached per (GPU, size
-    signature, model) in a JSON file."""
-    key = "%s|%s|K%dD%dP%d" % (torch.cuda.get_device_name(), _size_signature(batch.sizes), batch.K, batch.D,
-                               batch.P)
+    """Time n_steps BFGS iterations of the whole batch under each candidate map
+    and return (best_map, timings).  Time the iteration count the fit will
+    run: the largest histograms set the tail of a long fit, which a few
+    iterations do not show.  Results are cached per (GPU, size signature,
+    model, n_steps) in a JSON file."""
+    key = "%s|%s|K%dD%dP%d|S%d" % (torch.cuda.get_device_name(), _size_signature(batch.sizes), batch.K, batch.D,
+                                   batch.P, n_steps)
     path = _cache_path()
     cache = {}
     if use_cache and os.path.exists(path):

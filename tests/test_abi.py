@@ -63,3 +63,22 @@ def test_host_side_validation_without_gpu(lib):
     assert lib.cg_gradient(ctypes.byref(p), ctypes.c_void_p(256), ctypes.c_void_p(512), ctypes.c_void_p(768),
                            ctypes.c_void_p(1025), 1 << 30, None) == cg.ERR_WORKSPACE
     assert lib.cg_status_string(cg.ERR_DOMAIN).startswith(b"domain")
+
+
+def test_df64_tables_match_their_generator():
+    """The committed lookup tables of the double-float exp/log are exactly what
+    the generator writes (exactly rounded float pairs from 60-digit values)."""
+    pytest.importorskip("mpmath")
+    import importlib.util
+    path = os.path.join(ROOT, "paper_2203_06139_gb300", "csrc", "gen_df64_tables.py")
+    spec = importlib.util.spec_from_file_location("gen_df64_tables", path)
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    with open(gen.OUT) as f:
+        assert f.read() == gen.render()
+    t = gen.tables()
+    # spot values: 2^(1/64), log(F_0) = log(1 + 1/128), 1/F_63 = 1/(1 + 127/128)
+    import math
+    for (hi, lo), ref in ((t["exp2j"][1], 2 ** (1 / 64)), (t["logF"][0], math.log1p(1 / 128)),
+                          (t["invF"][63], 128 / 255)):
+        assert abs(float(hi) + float(lo) - ref) <= 2.0 ** -48 * abs(ref)   # what a float pair holds
