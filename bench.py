@@ -481,6 +481,43 @@ def run_c1(args):
     print(json.dumps(line), flush=True)
 
 
+def run_gemm(args):
+    """The BF16 tensor-core GEMM of the learned-start network at the shapes of
+    its inference pass (65,536 histograms) and at 8192^3, next to cuBLAS."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2203_06139_gb300 import cg
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("bf16_tflops", 1900.0)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    rows = []
+    for (M, N, K) in ((65536, 512, 256), (65536, 512, 512), (65536, 16, 512), (8192, 8192, 8192)):
+        A = torch.randn((M, K), generator=g, device="cuda").to(torch.bfloat16)
+        B = torch.randn((N, K), generator=g, device="cuda").to(torch.bfloat16)
+        C = torch.empty((M, N), dtype=torch.float32, device="cuda")
+        ms = _timed(lambda: cg.gemm_bf16(A, B, M, N, K, Cf=C), max(args.steps, 5), max(args.warmup, 3), flush)
+        ref = (A.float() @ B.float().t()) if M * N <= (1 << 27) else None
+        err = float(((C - ref).abs().max() / ref.abs().max()).item()) if ref is not None else None
+        ms_cublas = _timed(lambda: torch.matmul(A, B.t()), max(args.steps, 5), max(args.warmup, 3), flush)
+        tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+        rows.append({"M": M, "N": N, "K": K, "ms": ms, "tflops": tf, "frac_of_peak": tf / peak,
+                     "cublas_ms": ms_cublas, "cublas_tflops": 2.0 * M * N * K / (ms_cublas * 1e-3) / 1e12,
+                     "max_rel_err_vs_fp32": err})
+        del A, B, C
+    dom = rows[1]
+    line = {"metric": "BF16 GEMM TFLOP/s (tcgen05, FP32 accumulate)", "workload": "gemm",
+            "value": dom["tflops"], "unit": "TFLOP/s", "higher_is_better": True,
+            "config": {"workload": "learned-start network layers at 65,536 rows; 8192^3 for scale"},
+            "roofline": {"bound": "tensor", "achieved": dom["tflops"], "peak": peak, "unit": "TFLOP/s",
+                         "frac": dom["tflops"] / peak, "traffic": None, "kernel": "k_gemm_tc",
+                         "peak_basis": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)"},
+            "shapes": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_c3(args):
     """4096 x 4096 bins, 8 rotated Gaussians: autograd forward + backward."""
     import torch
@@ -627,7 +664,7 @@ def main():
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64-path comparison leg")
     ap.add_argument("--events", type=int, default=N_EVENTS)
     ap.add_argument("--points", type=int, default=N_POINTS)
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "fig3b"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "fig3b", "gemm"])
     ap.add_argument("--plain-hists", type=int, default=0, help="c4: histograms timed on the plain path (0 = all)")
     ap.add_argument("--train-hists", type=int, default=0, help="c5: training histograms (0 = 10^6)")
     ap.add_argument("--epochs", type=int, default=0, help="c5: training epochs (0 = 6)")
@@ -645,6 +682,8 @@ def main():
     elif args.workload == "c5":
         from paper_2203_06139_gb300 import learned_start
         learned_start.bench(args)
+    elif args.workload == "gemm":
+        run_gemm(args)
     else:
         run(args)
 

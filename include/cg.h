@@ -158,7 +158,8 @@ cg_status cg_gradient(const cg_problem *pb, const double *theta, double *value, 
  *    itself a reduction over all bins or events).  grad may be NULL: values
  *    only (value-only kernels for the 1-D model in CG_PREC_DF64).
  *  - offsets != NULL: histogram h is evaluated at theta[h]; binned 1-D
- *    models only.  Workspace: cg_batch_workspace_size(). */
+ *    models only; grad may be NULL: values only (no adjoint sweep).
+ *    Workspace: cg_batch_workspace_size(). */
 size_t cg_batch_workspace_size(const cg_batch *b);
 cg_status cg_batch_gradient(const cg_batch *b, const double *theta, double *value, double *grad,
                             void *ws, size_t ws_bytes, void *stream);
@@ -225,10 +226,13 @@ cg_status cg_rebin_normalize(const double *y, int64_t H, int n_bins, int factor,
 
 /* Plain heuristic starting point for K Gaussian peaks + linear background on
  * [lo, hi] (y: device [H][n_bins] FP64; theta0: device [H][3K+2]): on the
- * histogram rebinned by `factor`, 5-bin box smoothing, background line
- * through the minima of the first and last eighth, the K highest local
- * maxima of the residual at least 3 rebinned bins apart, width from the
- * half-maximum crossings; peaks sorted by position. */
+ * histogram rebinned by `factor` (sums in bin order), 5-bin box smoothing,
+ * background line through the minima (first index of each) of the first and
+ * last eighth, the K highest local maxima of the residual (first index on
+ * ties), each at least 3 rebinned bins from every earlier one, width from the
+ * half-maximum crossings; peaks sorted by position.  Products and sums are
+ * rounded separately (no fused multiply-add), so the result is reproducible
+ * bit for bit.  K <= 8, n_bins/factor in [8, 3072]. */
 cg_status cg_heuristic_start(const double *y, int64_t H, int n_bins, int factor, double lo, double hi, int n_peaks,
                              double *theta0, void *stream);
 

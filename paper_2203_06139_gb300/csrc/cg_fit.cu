@@ -178,9 +178,9 @@ static __device__ __noinline__ void gp1_fallback_fp64(double x, double y, const 
 // (zeroed here), which leave the thread as df64 and are converted to FP64
 // once per warp by the reductions; elements that need it are evaluated in
 // FP64 and folded into the same running sums.  GN: also the Gauss-Newton
-// diagonal terms, into grun[].
+// diagonal terms, into grun[].  VO: the value term only (run[0]).
 // Requires G.n < kDfMaxBins (bin index and centre exact in FP32 / df64).
-template <int K, int OBJ, bool GN>
+template <int K, int OBJ, bool GN, bool VO = false>
 __device__ __forceinline__ void acc_bins_df64(const Geom& G, const GP1Consts& cs, const GP1Df& cd,
                                               const GP1Data& dd, const DfTables& tab, int t0, int T,
                                               df (&run)[GP1Acc<K>::N], df (&grun)[GP1Acc<K>::N], bool& bad) {
@@ -203,7 +203,7 @@ __device__ __forceinline__ void acc_bins_df64(const Geom& G, const GP1Consts& cs
     int cnt = 0;
     for (int i = t0; i < n; i += T, fi += fT) {
         const double y = __ldg(G.y + i);
-        if (!gp1_elem_df64<K, OBJ, false, GN>(gp1_centre_df(cd, fi), y, cd, dd.D, dd.pm, da, tab, ga)) {
+        if (!gp1_elem_df64<K, OBJ, VO, GN>(gp1_centre_df(cd, fi), y, cd, dd.D, dd.pm, da, tab, ga)) {
             double t[2 * N];
             int b = 0;
             gp1_fallback_fp64<K, OBJ, GN>(fma((double)i + 0.5, G.hw, G.lo), y, cs, dd, t, &b);
@@ -644,7 +644,8 @@ __global__ void __launch_bounds__(512) k_fit_persistent(FitArgs a) {
 }
 
 // Init (GN + first evaluation) and plain evaluation: one CTA per histogram,
-// grid-stride over histograms.  mode 0: value/grad at a.theta; mode 1: init.
+// grid-stride over histograms.  mode 0: value/grad at a.theta; mode 1: init;
+// mode 2: value only.
 template <int K, int OBJ, int PREC, int MODE>
 __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
     constexpr int mode = MODE;
@@ -683,9 +684,14 @@ __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
         if (PREC == CG_PREC_DF64 && G.n < kDfMaxBins) {
             // mode 1: gradient and Gauss-Newton terms in one sweep over the bins
             df v[N], gv[N];
-            acc_bins_df64<K, OBJ, MODE == 1>(G, cs, cd, dd, tab, threadIdx.x, blockDim.x, v, gv, bad);
+            acc_bins_df64<K, OBJ, MODE == 1, MODE == 2>(G, cs, cd, dd, tab, threadIdx.x, blockDim.x, v, gv, bad);
             any_bad = __syncthreads_or(bad) | cs_bad;
-            reduce_cta<N, df>(v, red, tot);
+            if constexpr (MODE == 2) {
+                const df v0[1] = {v[0]};
+                reduce_cta<1, df>(v0, red, tot);
+            } else {
+                reduce_cta<N, df>(v, red, tot);
+            }
             if constexpr (MODE == 1) reduce_cta<N, df>(gv, red, gn);
         } else {
             double acc[N], gacc[N];
@@ -694,7 +700,12 @@ __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
             acc_bins<K, OBJ>(G, cs, dd, threadIdx.x, blockDim.x, acc, bad);
             if constexpr (MODE == 1) gn_bins<K, OBJ>(G, cs, dd, threadIdx.x, blockDim.x, gacc);
             any_bad = __syncthreads_or(bad) | cs_bad;
-            reduce_cta<N, double>(acc, red, tot);
+            if constexpr (MODE == 2) {
+                const double v0[1] = {acc[0]};
+                reduce_cta<1, double>(v0, red, tot);
+            } else {
+                reduce_cta<N, double>(acc, red, tot);
+            }
             if constexpr (MODE == 1) reduce_cta<N, double>(gacc, red, gn);
         }
         if (threadIdx.x == 0) {
@@ -705,12 +716,15 @@ __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
             ep.P = a.P;
             ep.lo = ep.hi = 0.0;
             double g[kMaxParams];
-            const double v = epilogue(ep, th, tot, g);
-            if (mode == 0) {
+            if (mode == 2) {
+                a.value[h] = any_bad ? __longlong_as_double(0x7ff8000000000000LL) : tot[0];
+            } else if (mode == 0) {
+                const double v = epilogue(ep, th, tot, g);
                 a.value[h] = v;
                 for (int k = 0; k < a.P; ++k) a.grad[h * a.P + k] = g[k];
                 if (any_bad) a.value[h] = __longlong_as_double(0x7ff8000000000000LL);
             } else {
+                const double v = epilogue(ep, th, tot, g);
                 cg_fit_state* st = a.st + h;
                 // GN diagonal from its accumulators
                 double gd[FP];
@@ -860,6 +874,9 @@ cg_status launch_eval_k(const FitArgs& a, int mode, int prec, cudaStream_t st) {
     if (mode == 0) {
         if (df) k_fit_eval<K, OBJ, CG_PREC_DF64, 0><<<grid, 256, 0, st>>>(a);
         else k_fit_eval<K, OBJ, CG_PREC_FP64, 0><<<grid, 256, 0, st>>>(a);
+    } else if (mode == 2) {
+        if (df) k_fit_eval<K, OBJ, CG_PREC_DF64, 2><<<grid, 256, 0, st>>>(a);
+        else k_fit_eval<K, OBJ, CG_PREC_FP64, 2><<<grid, 256, 0, st>>>(a);
     } else {
         if (df) k_fit_eval<K, OBJ, CG_PREC_DF64, 1><<<grid, 256, 0, st>>>(a);
         else k_fit_eval<K, OBJ, CG_PREC_FP64, 1><<<grid, 256, 0, st>>>(a);
@@ -971,14 +988,14 @@ cg_status cg_batch_gradient(const cg_batch* b, const double* theta, double* valu
     if (!b || b->n_hist < 1) return CG_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     if (!b->offsets) return grad_points(&b->tmpl, theta, b->n_hist, value, grad, ws, ws_bytes, st, nullptr);
-    if (!theta || !value || !grad || !b->lo || !b->hi || !b->tmpl.data) return CG_ERR_INVALID_ARG;
+    if (!theta || !value || !b->lo || !b->hi || !b->tmpl.data) return CG_ERR_INVALID_ARG;
     if (!fit_supported(&b->tmpl)) return CG_ERR_UNSUPPORTED;
     if (!ws || ((uintptr_t)ws & 255) || ws_bytes < 256) return CG_ERR_WORKSPACE;
     FitArgs a = base_args(b);
     a.theta = theta;
     a.value = value;
     a.grad = grad;
-    return launch_eval(&b->tmpl, a, 0, st);
+    return launch_eval(&b->tmpl, a, grad ? 0 : 2, st);   // grad == NULL: values only
 }
 
 size_t cg_fit_workspace_size(const cg_batch* b) {

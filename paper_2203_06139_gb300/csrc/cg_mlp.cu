@@ -12,6 +12,7 @@
 // Every wait on the mbarrier is bounded by a clock budget; on timeout the
 // kernel records an error, waits once more (bounded), frees its TMEM and
 // returns.
+#include <algorithm>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -268,97 +269,130 @@ extern "C" cg_status cg_gemm_bf16(const void* A, const void* B, int M, int N, in
 namespace cg {
 namespace {
 
-// x[h][j] = bf16(r_j / max_j r_j), r_j = sum of `factor` consecutive counts;
-// scale[h] = max_j r_j (1 when the histogram is empty).
+// One warp per histogram for the rebinning and the heuristic start; shared
+// memory per warp: the rebinned sums (rebin) or sums + smoothed sums
+// (heuristic).
+constexpr int kHistWarps = 4;
+
+// x[h][j] = bf16(r_j / max_j r_j), r_j = sum of `factor` consecutive counts
+// (added in order); scale[h] = max_j r_j (1 when the histogram is empty).
 __global__ void k_rebin(const double* __restrict__ y, int64_t H, int n_bins, int factor, __nv_bfloat16* x,
                         float* scale) {
-    extern __shared__ double sr[];
+    extern __shared__ double sr_all[];
     const int nr = n_bins / factor;
-    for (int64_t h = blockIdx.x; h < H; h += gridDim.x) {
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    double* sr = sr_all + (size_t)wid * nr;
+    for (int64_t h = (int64_t)blockIdx.x * nw + wid; h < H; h += (int64_t)gridDim.x * nw) {
         const double* yh = y + h * (int64_t)n_bins;
-        for (int j = threadIdx.x; j < nr; j += blockDim.x) {
-            double s = 0.0;
-            for (int i = 0; i < factor; ++i) s += yh[j * factor + i];
-            sr[j] = s;
+        double m = 0.0;
+        for (int j = lane; j < nr; j += 32) {
+            double t = 0.0;
+            for (int i = 0; i < factor; ++i) t += yh[j * factor + i];
+            sr[j] = t;
+            m = fmax(m, t);
         }
-        __syncthreads();
-        __shared__ double mx;
-        if (threadIdx.x == 0) {
-            double m = 0.0;
-            for (int j = 0; j < nr; ++j) m = fmax(m, sr[j]);
-            mx = m > 0.0 ? m : 1.0;
-            scale[h] = (float)mx;
-        }
-        __syncthreads();
-        for (int j = threadIdx.x; j < nr; j += blockDim.x) x[h * nr + j] = __float2bfloat16((float)(sr[j] / mx));
-        __syncthreads();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        const double mx = m > 0.0 ? m : 1.0;
+        const double inv = 1.0 / mx;
+        if (lane == 0) scale[h] = (float)mx;
+        __syncwarp();
+        for (int j = lane; j < nr; j += 32) x[h * nr + j] = __float2bfloat16((float)(sr[j] * inv));
+        __syncwarp();
     }
 }
 
+// First index of the minimum of v[j0 .. j1) over the warp (all lanes get it).
+__device__ __forceinline__ int warp_argmin_first(const double* v, int j0, int j1) {
+    const int lane = threadIdx.x & 31;
+    int bj = -1;
+    double bv = 0.0;
+    for (int j = j0 + lane; j < j1; j += 32)
+        if (bj < 0 || v[j] < bv) { bv = v[j]; bj = j; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        if (oj >= 0 && (bj < 0 || ov < bv || (ov == bv && oj < bj))) { bv = ov; bj = oj; }
+    }
+    return bj;
+}
+
 // Heuristic starting point for K Gaussian peaks on a linear background, from
-// the rebinned histogram: 5-bin box smoothing; background = line through the
-// minima of the first and last eighth; peaks = the K highest local maxima of
-// the smoothed residual, at least 3 rebinned bins apart; amplitude =
-// residual height; width from the half-maximum crossings.  Output per original bin:
+// the rebinned histogram (sums of `factor` counts, in order): 5-bin box
+// smoothing; background = line through the minima (first index of the
+// minimum) of the first and last eighth; peaks = the K highest local maxima
+// of the smoothed residual (first index on ties), each closer than 3 rebinned
+// bins to no earlier peak; amplitude = residual height; width from the
+// half-maximum crossings.  One warp per histogram.  Output per original bin:
 // theta = (A_1, mu_1, s_1, ..., A_K, mu_K, s_K, b0, b1), peaks sorted by mu.
 __global__ void k_heuristic(const double* __restrict__ y, int64_t H, int n_bins, int factor, double lo, double hi,
                             int K, double* theta) {
-    extern __shared__ double sm[];
+    extern __shared__ double sm_all[];
     const int nr = n_bins / factor;
-    double* r = sm;
-    double* s = sm + nr;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    double* r = sm_all + (size_t)wid * 2 * nr;
+    double* s = r + nr;
     const double wr = (hi - lo) / nr;        // rebinned bin width
-    for (int64_t h = blockIdx.x; h < H; h += gridDim.x) {
+    for (int64_t h = (int64_t)blockIdx.x * nw + wid; h < H; h += (int64_t)gridDim.x * nw) {
         const double* yh = y + h * (int64_t)n_bins;
-        for (int j = threadIdx.x; j < nr; j += blockDim.x) {
+        for (int j = lane; j < nr; j += 32) {
             double t = 0.0;
             for (int i = 0; i < factor; ++i) t += yh[j * factor + i];
             r[j] = t;
         }
-        __syncthreads();
-        for (int j = threadIdx.x; j < nr; j += blockDim.x) {
+        __syncwarp();
+        for (int j = lane; j < nr; j += 32) {
             double t = 0.0;
             int c = 0;
             for (int q = j - 2; q <= j + 2; ++q)
                 if (q >= 0 && q < nr) { t += r[q]; ++c; }
             s[j] = t / c;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int seg = nr / 8 > 1 ? nr / 8 : 1;
-            int jl = 0, jr = nr - 1;
-            for (int j = 0; j < seg; ++j) if (s[j] < s[jl]) jl = j;
-            for (int j = nr - seg; j < nr; ++j) if (s[j] < s[jr]) jr = j;
-            const double xl = (jl + 0.5), xr = (jr + 0.5);
-            const double slope = (jr != jl) ? (s[jr] - s[jl]) / (xr - xl) : 0.0;   // per rebinned bin
-            const double b_at0 = s[jl] - slope * xl;                               // at rebinned coordinate 0
-            // residual in r (reuse r[] for it)
-            for (int j = 0; j < nr; ++j) r[j] = s[j] - (b_at0 + slope * (j + 0.5));
-            double pk_mu[8], pk_A[8], pk_s[8], pk_ex[8];
-            int found = 0;
-            for (int k = 0; k < K && k < 8; ++k) {
-                int best = -1;
-                for (int j = 1; j < nr - 1; ++j) {
-                    if (!(r[j] >= r[j - 1] && r[j] >= r[j + 1])) continue;
-                    bool far = true;   // outside the masked window of every accepted peak
-                    for (int q = 0; q < found; ++q)
-                        if (fabs((j + 0.5) * wr + lo - pk_mu[q]) < pk_ex[q]) far = false;
-                    if (!far) continue;
-                    if (best < 0 || r[j] > r[best]) best = j;
-                }
-                if (best < 0 || !(r[best] > 0.0)) break;
-                const double half = 0.5 * r[best];
-                int a = best, b = best;
-                while (a > 0 && r[a] > half) --a;
-                while (b < nr - 1 && r[b] > half) ++b;
-                double fw = (double)(b - a);
-                if (fw < 1.0) fw = 1.0;
-                pk_mu[found] = lo + (best + 0.5) * wr;
-                pk_A[found] = r[best] / factor;
-                pk_s[found] = fw * wr / 2.3548200450309493;
-                pk_ex[found] = 3.0 * wr;   // later peaks at least 3 rebinned bins away
-                ++found;
+        __syncwarp();
+        const int seg = nr / 8 > 1 ? nr / 8 : 1;
+        const int jl = warp_argmin_first(s, 0, seg), jr = warp_argmin_first(s, nr - seg, nr);
+        const double xl = (jl + 0.5), xr = (jr + 0.5);
+        const double slope = (jr != jl) ? (s[jr] - s[jl]) / (xr - xl) : 0.0;   // per rebinned bin
+        // products and sums rounded separately (no contraction): the definition in the header
+        const double b_at0 = __dsub_rn(s[jl], __dmul_rn(slope, xl));          // at rebinned coordinate 0
+        __syncwarp();
+        for (int j = lane; j < nr; j += 32) r[j] = __dsub_rn(s[j], __dadd_rn(b_at0, __dmul_rn(slope, j + 0.5)));
+        __syncwarp();
+        int pk_j[8];
+        double pk_A[8], pk_s[8];
+        int found = 0;
+        for (int k = 0; k < K && k < 8; ++k) {
+            int bj = -1;
+            double bv = 0.0;
+            for (int j = 1 + lane; j < nr - 1; j += 32) {
+                if (!(r[j] >= r[j - 1] && r[j] >= r[j + 1])) continue;
+                bool far = true;
+                for (int q = 0; q < found; ++q)
+                    if (abs(j - pk_j[q]) < 3) far = false;
+                if (far && (bj < 0 || r[j] > bv)) { bv = r[j]; bj = j; }
             }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+                if (oj >= 0 && (bj < 0 || ov > bv || (ov == bv && oj < bj))) { bv = ov; bj = oj; }
+            }
+            if (bj < 0 || !(r[bj] > 0.0)) break;
+            const double half = 0.5 * r[bj];   // every lane walks the same short way
+            int a = bj, b = bj;
+            while (a > 0 && r[a] > half) --a;
+            while (b < nr - 1 && r[b] > half) ++b;
+            double fw = (double)(b - a);
+            if (fw < 1.0) fw = 1.0;
+            pk_j[found] = bj;
+            pk_A[found] = r[bj] / factor;
+            pk_s[found] = fw * wr / 2.3548200450309493;
+            ++found;
+        }
+        if (lane == 0) {
+            double pk_mu[8];
+            for (int k = 0; k < found; ++k) pk_mu[k] = __dadd_rn(lo, __dmul_rn(pk_j[k] + 0.5, wr));
             for (int k = found; k < K; ++k) {    // not enough peaks: small ones spread over the range
                 pk_mu[k] = lo + (hi - lo) * (k + 0.5) / K;
                 pk_A[k] = 1.0;
@@ -379,11 +413,10 @@ __global__ void k_heuristic(const double* __restrict__ y, int64_t H, int n_bins,
             }
             // background per original bin: b(x) = b0 + b1 x with x the bin centre
             const double per_bin = 1.0 / factor;
-            const double b1 = slope / wr * per_bin;
             th[3 * K] = (b_at0 - slope * lo / wr) * per_bin;
-            th[3 * K + 1] = b1;
+            th[3 * K + 1] = slope / wr * per_bin;
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
@@ -461,9 +494,13 @@ cg_status cg_rebin_normalize(const double* y, int64_t H, int n_bins, int factor,
                              void* stream) {
     if (!y || !x_bf16 || !scale || H < 1 || factor < 1 || n_bins < factor || n_bins % factor) return CG_ERR_INVALID_ARG;
     const int nr = n_bins / factor;
-    const int g = (int)(H < 4 * cg::device_sm_count() ? H : 4 * cg::device_sm_count());
-    cg::k_rebin<<<g, 256, nr * sizeof(double), (cudaStream_t)stream>>>(y, H, n_bins, factor, (__nv_bfloat16*)x_bf16,
-                                                                      scale);
+    const size_t per_warp = (size_t)nr * sizeof(double);
+    if (per_warp > 48 * 1024) return CG_ERR_INVALID_ARG;
+    const int nw = (int)std::min<size_t>(cg::kHistWarps, 48 * 1024 / per_warp);
+    const int64_t blocks = (H + nw - 1) / nw;
+    const int g = (int)std::min<int64_t>(blocks, 16 * (int64_t)cg::device_sm_count());
+    cg::k_rebin<<<g, 32 * nw, nw * per_warp, (cudaStream_t)stream>>>(y, H, n_bins, factor, (__nv_bfloat16*)x_bf16,
+                                                                     scale);
     return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
 }
 
@@ -473,9 +510,13 @@ cg_status cg_heuristic_start(const double* y, int64_t H, int n_bins, int factor,
         return CG_ERR_INVALID_ARG;
     const int nr = n_bins / factor;
     if (nr < 8) return CG_ERR_INVALID_ARG;
-    const int g = (int)(H < 8 * cg::device_sm_count() ? H : 8 * cg::device_sm_count());
-    cg::k_heuristic<<<g, 128, 2 * nr * sizeof(double), (cudaStream_t)stream>>>(y, H, n_bins, factor, lo, hi,
-                                                                              n_peaks, theta0);
+    const size_t per_warp = 2 * (size_t)nr * sizeof(double);
+    if (per_warp > 48 * 1024) return CG_ERR_INVALID_ARG;
+    const int nw = (int)std::min<size_t>(cg::kHistWarps, 48 * 1024 / per_warp);
+    const int64_t blocks = (H + nw - 1) / nw;
+    const int g = (int)std::min<int64_t>(blocks, 16 * (int64_t)cg::device_sm_count());
+    cg::k_heuristic<<<g, 32 * nw, nw * per_warp, (cudaStream_t)stream>>>(y, H, n_bins, factor, lo, hi, n_peaks,
+                                                                        theta0);
     return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
 }
 

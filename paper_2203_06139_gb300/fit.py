@@ -125,6 +125,17 @@ class HistBatch:
                                              cg._ptr(ws), ws.numel(), cg._stream()), "cg_batch_gradient")
         return values, grads
 
+    def objective(self, thetas, values=None):
+        """Value of every histogram at its own parameters (no adjoint sweep)."""
+        thetas = cg._dev_f64(thetas, "thetas")
+        if values is None:
+            values = torch.empty(self.H, dtype=torch.float64, device=self.y.device)
+        n = cg.lib().cg_batch_workspace_size(ctypes.byref(self.c))
+        ws = torch.empty(max(n, 256), dtype=torch.uint8, device=self.y.device)
+        cg._check(cg.lib().cg_batch_gradient(ctypes.byref(self.c), cg._ptr(thetas), cg._ptr(values), None,
+                                             cg._ptr(ws), ws.numel(), cg._stream()), "cg_batch_gradient")
+        return values
+
 
 class BatchFitter:
     """BFGS fits of every histogram of a HistBatch in one persistent launch."""

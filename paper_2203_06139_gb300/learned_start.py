@@ -200,8 +200,8 @@ def choose_start(y_flat, H, th_a, th_b):
     b = HistBatch(y_flat, offs, np.zeros(H), np.ones(H), K_PEAKS, 1, cg.OBJ_POISSON_BC, poly_mode=0,
                   precision=FIT_PRECISION)
     th_a, th_b = th_a.contiguous(), th_b.contiguous()
-    fa, _ = b.gradient(th_a)
-    fb, _ = b.gradient(th_b)
+    fa = b.objective(th_a)
+    fb = b.objective(th_b)
     out = torch.empty_like(th_a)
     cg._check(cg.lib().cg_select_start(_p(fa), _p(fb), _p(th_a), _p(th_b), H, th_a.shape[1], _p(out), None, _s()),
               "cg_select_start")
@@ -287,11 +287,23 @@ def evaluate(net, H=65536, chunk=0, device="cuda", n_steps=50, tol=1e-9):
 
     fh, t_h = timed(lambda: fit_batch(y, H, heuristic_start(y, H), n_steps, tol))
 
+    stage_ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+
     def proposal():
+        stage_ev[0].record()
         x, scale = rebin(y, H)
-        return choose_start(y, H, net.predict_start(x, scale), heuristic_start(y, H))
+        stage_ev[1].record()
+        th_net = net.predict_start(x, scale)
+        stage_ev[2].record()
+        th_heu = heuristic_start(y, H)
+        stage_ev[3].record()
+        th = choose_start(y, H, th_net, th_heu)
+        stage_ev[4].record()
+        return th
 
     th_l, t_prop = timed(proposal)
+    stages = dict(zip(("rebin", "network", "heuristic", "choose"),
+                      (stage_ev[i].elapsed_time(stage_ev[i + 1]) for i in range(4))))
     fl, t_fit = timed(lambda: fit_batch(y, H, th_l, n_steps, tol))
     t_l = t_prop + t_fit
     Fh, Fl = fh.states.f.cpu().numpy(), fl.states.f.cpu().numpy()
@@ -320,7 +332,8 @@ def evaluate(net, H=65536, chunk=0, device="cuda", n_steps=50, tol=1e-9):
     eh, el = fh.states.n_eval.cpu().numpy(), fl.states.n_eval.cpu().numpy()
     return dict(H=H, heuristic=dict(ms=t_h, mean_iters=float(ih.mean()), mean_evals=float(eh.mean()),
                                     converged=int((sh == 1).sum()), mean_nll=float(np.mean(Fh[np.isfinite(Fh)]))),
-                learned=dict(ms=t_l, proposal_ms=t_prop, fit_ms=t_fit, mean_iters=float(il.mean()),
+                learned=dict(ms=t_l, proposal_ms=t_prop, proposal_stages_ms=stages, fit_ms=t_fit,
+                             mean_iters=float(il.mean()),
                              mean_evals=float(el.mean()), converged=int((sl == 1).sum()),
                              mean_nll=float(np.mean(Fl[np.isfinite(Fl)]))),
                 production=dict(ms=t_l + t_r, refit=int(len(idx)), refit_ms=t_r,

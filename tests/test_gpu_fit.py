@@ -264,3 +264,21 @@ def test_batched_fit_df64_fallback_bins_reach_oracle_minimum(dev):
         y = d["y"][d["offsets"][h]:d["offsets"][h + 1]]
         ref = oracle_fit(y, 1, -1, 0, oracle.POISSON, 0.0, 1.0, d["start"][h], max_iter=400)
         assert abs(F[h] - ref["F"]) <= 1e-6 * abs(ref["F"]), (h, F[h], ref["F"])
+
+
+@pytest.mark.parametrize("prec", [cg.PREC_FP64, cg.PREC_DF64])
+def test_batch_objective_values_only(dev, prec):
+    """cg_batch_gradient with grad = NULL on a histogram batch: values only,
+    equal to the oracle (1e-10) and to the values of the full evaluation."""
+    d = synth.c5_batch(H=20, n_bins=2048, index=6)
+    th = d["truth"] * np.random.default_rng(3).uniform(0.95, 1.05, d["truth"].shape)
+    b = HistBatch(d["y"], d["offsets"], d["lo"], d["hi"], 3, 1, cg.OBJ_POISSON_BC, poly_mode=0, precision=prec)
+    tt = torch.tensor(th, device=dev)
+    v = b.objective(tt).cpu().numpy()
+    v_full, _ = b.gradient(tt)
+    v_full = v_full.cpu().numpy()
+    for h in range(d["H"]):
+        y = d["y"][d["offsets"][h]:d["offsets"][h + 1]]
+        ref = oracle.binned1d(3, 1, 0, oracle.POISSON_BC, y, 0.0, 1.0, th[h])
+        assert abs(v[h] - ref.value) <= 1e-10 * abs(ref.value), (h, v[h], ref.value)
+        assert abs(v[h] - v_full[h]) <= 1e-12 * abs(v_full[h])

@@ -91,6 +91,83 @@ def test_heuristic_start_finds_the_peaks(dev):
     assert np.all(th[:, 0:9:3] > 0) and np.all(th[:, 2:9:3] > 0)
 
 
+def _heuristic_reference(y, factor, lo, hi, K):
+    """The heuristic start of cg_heuristic_start for one histogram, in the
+    order of operations its definition fixes (sums in bin order, products and
+    sums rounded separately)."""
+    nr = len(y) // factor
+    r = np.zeros(nr)
+    for i in range(factor):
+        r = r + y[i::factor][:nr]
+    t = np.zeros(nr)
+    c = np.zeros(nr)
+    for d in range(-2, 3):
+        q = np.arange(nr) + d
+        ok = (q >= 0) & (q < nr)
+        t = np.where(ok, t + r[np.clip(q, 0, nr - 1)], t)
+        c = c + ok
+    s = t / c
+    seg = max(nr // 8, 1)
+    jl = int(np.argmin(s[:seg]))
+    jr = nr - seg + int(np.argmin(s[nr - seg:]))
+    xl, xr = jl + 0.5, jr + 0.5
+    slope = (s[jr] - s[jl]) / (xr - xl) if jr != jl else 0.0
+    b_at0 = s[jl] - slope * xl
+    res = s - (b_at0 + slope * (np.arange(nr) + 0.5))
+    wr = (hi - lo) / nr
+    pk = []
+    for _ in range(min(K, 8)):
+        best = -1
+        for j in range(1, nr - 1):
+            if not (res[j] >= res[j - 1] and res[j] >= res[j + 1]):
+                continue
+            if any(abs(j - q[0]) < 3 for q in pk):
+                continue
+            if best < 0 or res[j] > res[best]:
+                best = j
+        if best < 0 or not res[best] > 0.0:
+            break
+        half = 0.5 * res[best]
+        a = b = best
+        while a > 0 and res[a] > half:
+            a -= 1
+        while b < nr - 1 and res[b] > half:
+            b += 1
+        fw = max(float(b - a), 1.0)
+        pk.append((best, res[best] / factor, fw * wr / 2.3548200450309493))
+    mu = [lo + (j + 0.5) * wr for j, _, _ in pk]
+    A = [a for _, a, _ in pk]
+    sg = [w for _, _, w in pk]
+    for k in range(len(pk), K):
+        mu.append(lo + (hi - lo) * (k + 0.5) / K)
+        A.append(1.0)
+        sg.append(2.0 * wr)
+    order = sorted(range(K), key=lambda k: (mu[k], k))
+    th = []
+    for k in order:
+        th += [A[k], mu[k], sg[k]]
+    per_bin = 1.0 / factor
+    th += [(b_at0 - slope * lo / wr) * per_bin, slope / wr * per_bin]
+    return np.array(th)
+
+
+def test_heuristic_start_matches_its_definition(dev):
+    """Bit for bit against the reference written from the header's definition,
+    on c5-like histograms plus a flat, an empty and a one-peak histogram (the
+    missing peaks are filled in)."""
+    H = 300
+    d = synth.c5_batch(H=H, n_bins=2048, index=9)
+    y = d["y"].reshape(H, 2048).copy()
+    y[0] = 50.0
+    y[1] = 0.0
+    xc = (np.arange(2048) + 0.5) / 2048
+    y[2] = np.round(20.0 + 3000.0 * np.exp(-0.5 * ((xc - 0.3) / 0.02) ** 2))
+    th = ls.heuristic_start(torch.tensor(y.reshape(-1), device=dev), H).cpu().numpy()
+    for h in range(H):
+        ref = _heuristic_reference(y[h], 8, 0.0, 1.0, 3)
+        assert np.array_equal(th[h], ref), (h, th[h], ref)
+
+
 def _ref_mlp(net, x, target):
     """Plain PyTorch FP32 forward/backward with BF16 rounding at the kernels' points."""
     bf = lambda t: t.bfloat16().float()
