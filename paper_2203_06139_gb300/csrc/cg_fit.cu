@@ -287,42 +287,40 @@ __device__ __forceinline__ void reduce_cluster(const T (&acc)[N], double* red, d
 }
 
 // ---------------------------------------------------------------------------
-// Control part, executed by one warp on the unit's FitSm.
+// Control part, executed by one full warp on the unit's FitSm.  Lane i < P
+// owns parameter i (and row i of the inverse-Hessian approximation); dot
+// products are lane products summed by a warp butterfly, and the P x P
+// update is spread over all 32 lanes.  An FP64 warp instruction occupies the
+// FP64 pipe for the whole warp whatever the number of active lanes, so the
+// control issues as few FP64 instructions as it can, none of them serial
+// over the parameters.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void ctl_direction(FitSm& s, int lane) {
     const int P = s.P;
-    if (lane < P) {
+    const bool own = lane < P;
+    double dl = 0.0;
+    if (own) {
         double acc = 0.0;
         for (int j = 0; j < P; ++j) acc = fma(s.H[lane * FP + j], s.g[j], acc);
-        s.d[lane] = -acc;
+        dl = -acc;
     }
-    __syncwarp();
-    if (lane == 0) {
-        double gd = 0.0;
-        for (int j = 0; j < P; ++j) gd = fma(s.g[j], s.d[j], gd);
-        s.gd = gd;
-        s.go = (gd < 0.0) ? 1 : 0;
-    }
-    __syncwarp();
-    if (!s.go) {  // not a descent direction: restart from the initial diagonal
-        if (lane < P) {
+    double gd = warp_sum(own ? s.g[lane] * dl : 0.0);
+    if (!(gd < 0.0)) {  // not a descent direction: restart from the initial diagonal
+        if (own) {
             for (int j = 0; j < P; ++j) s.H[lane * FP + j] = (j == lane) ? s.h0[lane] : 0.0;
-            s.d[lane] = -s.h0[lane] * s.g[lane];
+            dl = -s.h0[lane] * s.g[lane];
         }
-        __syncwarp();
-        if (lane == 0) {
-            double gd = 0.0;
-            for (int j = 0; j < P; ++j) gd = fma(s.g[j], s.d[j], gd);
-            s.gd = gd;
-        }
-        __syncwarp();
+        gd = warp_sum(own ? s.g[lane] * dl : 0.0);
+    }
+    if (own) {
+        s.d[lane] = dl;
+        s.tt[lane] = s.th[lane] + dl;
     }
     if (lane == 0) {
+        s.gd = gd;
         s.alpha = 1.0;
         s.ntrial = 0;
     }
-    __syncwarp();
-    if (lane < P) s.tt[lane] = s.th[lane] + s.d[lane];
     __syncwarp();
 }
 
@@ -330,6 +328,7 @@ __device__ __forceinline__ void ctl_direction(FitSm& s, int lane) {
 // with a new tt, 2 stop (line search failed).
 __device__ __forceinline__ void ctl_after_eval(FitSm& s, int lane, double tol) {
     const int P = s.P;
+    const bool own = lane < P;
     if (lane == 0) {
         s.n_eval += 1;
         const double ft = s.bad ? __longlong_as_double(0x7ff0000000000000LL) : s.ft;
@@ -358,64 +357,71 @@ __device__ __forceinline__ void ctl_after_eval(FitSm& s, int lane, double tol) {
     }
     __syncwarp();
     if (s.go == 0) {
-        if (lane < P) s.tt[lane] = fma(s.alpha, s.d[lane], s.th[lane]);
+        if (own) s.tt[lane] = fma(s.alpha, s.d[lane], s.th[lane]);
         __syncwarp();
         return;
     }
     if (s.go == 2) return;
     // accepted: BFGS update with step sv and gradient change yv
-    if (lane < P) {
-        s.sv[lane] = s.tt[lane] - s.th[lane];
-        s.yv[lane] = s.gt[lane] - s.g[lane];
+    double sv = 0.0, yv = 0.0;
+    if (own) {
+        sv = s.tt[lane] - s.th[lane];
+        yv = s.gt[lane] - s.g[lane];
+        s.sv[lane] = sv;
+        s.yv[lane] = yv;
     }
     __syncwarp();
-    if (lane < P) {
-        double acc = 0.0;
-        for (int j = 0; j < P; ++j) acc = fma(s.H[lane * FP + j], s.yv[j], acc);
-        s.hy[lane] = acc;
+    double hy = 0.0;
+    if (own) {
+        for (int j = 0; j < P; ++j) hy = fma(s.H[lane * FP + j], s.yv[j], hy);
+        s.hy[lane] = hy;
     }
+    const double sy = warp_sum(sv * yv), yhy = warp_sum(yv * hy);
+    const double ss = warp_sum(sv * sv), yy = warp_sum(yv * yv);
+    const double rq = sqrt(lane == 0 ? ss : yy);   // both roots in one instruction sequence
+    const double rs = __shfl_sync(0xffffffffu, rq, 0), ry = __shfl_sync(0xffffffffu, rq, 1);
     __syncwarp();
-    if (lane == 0) {
-        double sy = 0.0, yhy = 0.0, ss = 0.0, yy = 0.0;
-        for (int j = 0; j < P; ++j) {
-            sy = fma(s.sv[j], s.yv[j], sy);
-            yhy = fma(s.yv[j], s.hy[j], yhy);
-            ss = fma(s.sv[j], s.sv[j], ss);
-            yy = fma(s.yv[j], s.yv[j], yy);
+    if (sy > 1e-12 * rs * ry) {   // the same decision in every lane
+        const double r = 1.0 / sy;
+        const double c = (1.0 + r * yhy) * r;
+        for (int e = lane; e < P * P; e += 32) {
+            const int i = e / P, j = e - i * P;
+            s.H[i * FP + j] += -r * (s.sv[i] * s.hy[j] + s.hy[i] * s.sv[j]) + c * s.sv[i] * s.sv[j];
         }
-        s.upd = (sy > 1e-12 * sqrt(ss) * sqrt(yy)) ? 1 : 0;
-        s.gd = sy;      // reuse: s.y
-        s.alpha = yhy;  // reuse: y.H.y
     }
     __syncwarp();
-    if (s.upd && lane < P) {
-        const double r = 1.0 / s.gd;
-        const double c = (1.0 + r * s.alpha) * r;
-        for (int j = 0; j < P; ++j)
-            s.H[lane * FP + j] += -r * (s.sv[lane] * s.hy[j] + s.hy[lane] * s.sv[j]) + c * s.sv[lane] * s.sv[j];
-    }
-    __syncwarp();
-    if (lane < P) {
+    if (own) {
         s.th[lane] = s.tt[lane];
         s.g[lane] = s.gt[lane];
     }
     __syncwarp();
     // EDM with the updated approximation
-    if (lane < P) {
-        double acc = 0.0;
-        for (int j = 0; j < P; ++j) acc = fma(s.H[lane * FP + j], s.g[j], acc);
-        s.hy[lane] = acc;
+    double hg = 0.0;
+    if (own) {
+        for (int j = 0; j < P; ++j) hg = fma(s.H[lane * FP + j], s.g[j], hg);
     }
-    __syncwarp();
+    const double e = warp_sum(own ? s.g[lane] * hg : 0.0);
     if (lane == 0) {
         s.f = s.ft;
         s.iter += 1;
-        double e = 0.0;
-        for (int j = 0; j < P; ++j) e = fma(s.g[j], s.hy[j], e);
         s.edm = 0.5 * e;
         if (s.edm < tol * fmax(1.0, fabs(s.f))) s.status = CG_FIT_CONVERGED;
     }
     __syncwarp();
+}
+
+// Gradient component k of the 1-D model from its summed accumulators S (the
+// chain rule of the epilogue in cg_models.cuh, one parameter per lane).
+template <int K>
+__device__ __forceinline__ double gp1_grad_component(int k, const double* th, const double* S) {
+    if (k < 3 * K) {
+        const int p = k / 3, role = k - 3 * p;
+        const double A = th[3 * p], sg = th[3 * p + 2];
+        if (role == 0) return S[1 + 3 * p];
+        if (role == 1) return A / (sg * sg) * S[2 + 3 * p];
+        return A / (sg * sg * sg) * S[3 + 3 * p];
+    }
+    return S[1 + k];
 }
 
 // Sum one unit's accumulators into tot[] (shared) and OR its domain flags.
@@ -452,7 +458,6 @@ __device__ __forceinline__ void unit_eval(FitSm& s, GP1Consts& cs, GP1Df& cd, co
                                           int T) {
     constexpr int N = GP1Acc<K>::N;
     const int lane = threadIdx.x & 31;
-    const bool leader = (UNIT == UNIT_WARP) ? (lane == 0) : (threadIdx.x == 0);
     if (UNIT == UNIT_WARP || threadIdx.x < 32) {   // the constants, one per lane of the control warp
         const bool ok = gp1_prologue_warp<K, PREC == CG_PREC_DF64>(s.tt, D, G.lo, G.hw, dd.au, dd.bu, cs, cd);
         if (lane == 0) s.bad = ok ? 0 : 1;
@@ -471,17 +476,12 @@ __device__ __forceinline__ void unit_eval(FitSm& s, GP1Consts& cs, GP1Df& cd, co
         acc_bins<K, OBJ>(G, cs, dd, t0, T, acc, bad);
         any_bad = unit_reduce<UNIT, N>(acc, bad, red, part, tot);
     }
-    if (leader) {
-        EpiParams ep;
-        ep.model = CG_MODEL_GAUSS_POLY;
-        ep.K = K;
-        ep.D = D;
-        ep.P = s.P;
-        ep.lo = ep.hi = 0.0;
-        double g[kMaxParams];
-        s.ft = epilogue(ep, s.tt, tot, g);
-        for (int k = 0; k < s.P; ++k) s.gt[k] = g[k];
-        s.bad |= any_bad ? 1 : 0;
+    if (UNIT == UNIT_WARP || threadIdx.x < 32) {   // value and gradient, one parameter per lane
+        if (lane < s.P) s.gt[lane] = gp1_grad_component<K>(lane, s.tt, tot);
+        if (lane == 0) {
+            s.ft = tot[0];
+            s.bad |= any_bad ? 1 : 0;
+        }
     }
     if (UNIT == UNIT_WARP) __syncwarp(); else __syncthreads();
 }
