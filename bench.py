@@ -518,6 +518,39 @@ def run_gemm(args):
     print(json.dumps(line), flush=True)
 
 
+def run_c5fit(args):
+    """The batched Baker-Cousins fits of the learned-start workload alone: H
+    three-peak histograms of 2048 bins from the heuristic start, 50 BFGS
+    iterations, one warp per histogram; `--steps` timed repetitions."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2203_06139_gb300 import learned_start as ls, synth
+    H = args.hists or 65536
+    y = synth.c5_batch_device(H, ls.N_BINS)
+    th = ls.heuristic_start(y, H)
+    ls.fit_batch(y, H, th, 50, 1e-9)   # warm-up
+    ts = []
+    for _ in range(max(args.steps, 1)):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        f = ls.fit_batch(y, H, th, 50, 1e-9)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ev = f.states.n_eval.cpu().numpy().astype(np.float64)
+    ms = float(np.median(ts))
+    line = {"metric": "bin-evaluations/s of the batched fit", "workload": "c5fit",
+            "value": ev.sum() * ls.N_BINS / (ms * 1e-3), "unit": "bin-evaluations/s", "higher_is_better": True,
+            "ms_per_step": ms, "ms_all": ts,
+            "config": {"workload": "%d histograms x 2048 bins, 3 Gaussians + linear, Baker-Cousins, heuristic "
+                                   "start, 50 iterations, df64" % H},
+            "mean_evals": float(ev.mean()), "max_evals": int(ev.max())}
+    print(json.dumps(line), flush=True)
+
+
 def run_c3(args):
     """4096 x 4096 bins, 8 rotated Gaussians: autograd forward + backward."""
     import torch
@@ -664,8 +697,9 @@ def main():
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64-path comparison leg")
     ap.add_argument("--events", type=int, default=N_EVENTS)
     ap.add_argument("--points", type=int, default=N_POINTS)
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "fig3b", "gemm"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "c5fit", "fig3b", "gemm"])
     ap.add_argument("--plain-hists", type=int, default=0, help="c4: histograms timed on the plain path (0 = all)")
+    ap.add_argument("--hists", type=int, default=0, help="c5fit: histograms in the batch (0 = 65,536)")
     ap.add_argument("--train-hists", type=int, default=0, help="c5: training histograms (0 = 10^6)")
     ap.add_argument("--epochs", type=int, default=0, help="c5: training epochs (0 = 6)")
     args = ap.parse_args()
@@ -684,6 +718,8 @@ def main():
         learned_start.bench(args)
     elif args.workload == "gemm":
         run_gemm(args)
+    elif args.workload == "c5fit":
+        run_c5fit(args)
     else:
         run(args)
 
