@@ -13,8 +13,10 @@
 // kernel records an error, waits once more (bounded), frees its TMEM and
 // returns.
 #include <algorithm>
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <math.h>
 #include <stdint.h>
 
@@ -227,6 +229,287 @@ __global__ void __launch_bounds__(kThreads) k_gemm_tc(GemmArgs g) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined GEMM for K-major A [M][lda] and B [N][ldb]: the tensor memory
+// accelerator (TMA) loads 128 x 64 and BN x 64 tiles with 128-byte swizzle
+// into a ring of kStages shared-memory stages (full / empty mbarriers per
+// stage); one thread issues tcgen05.mma (M = 128, N = BN, K = 16 per
+// instruction) into a 128 x BN FP32 accumulator in tensor memory; four
+// epilogue warps read it back with tcgen05.ld, stage 32 x 32 blocks through
+// shared memory and apply the epilogue with loads and stores coalesced along
+// the columns.  Warp 0 = TMA producer, warp 1 = TMEM owner and MMA issuer,
+// warps 2-5 = epilogue (warp w may read TMEM lanes 32 (w % 4) .. + 31).
+// Every mbarrier wait is bounded; a wait that gives up sets a shared abort
+// flag and bit 0 of *err, the other roles stop at their next wait, and the
+// CTA lets its issued loads and MMAs finish (bounded) before freeing TMEM.
+// ---------------------------------------------------------------------------
+constexpr int kStages = 3;
+constexpr int kPipeThreads = 192;
+constexpr int kBK = 64;                      // 64 bf16 = one 128-byte swizzle row
+constexpr int kEpiLd = 33;                   // staging row stride (floats), conflict-free
+
+template <int BN>
+struct PipeSmem {
+    static constexpr int A_BYTES = kTM * kBK * 2;
+    static constexpr int B_BYTES = BN * kBK * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;   // a multiple of 1024: every tile 1024-aligned
+    static constexpr int PIPE = kStages * STAGE;
+    static constexpr int EPI = 4 * 32 * kEpiLd * 4;   // epilogue staging, reuses the stage buffers
+    static constexpr int BUF = PIPE > EPI ? PIPE : EPI;
+    static constexpr int BARS = (2 * kStages + 1) * 8;
+    static constexpr int TOTAL = 1024 + BUF + BARS + 16;
+    static_assert(STAGE % 1024 == 0 && A_BYTES % 1024 == 0, "swizzle atoms need 1024-byte aligned tiles");
+};
+
+// Shared-memory descriptor of a K-major tile in the 128-byte swizzle layout
+// written by TMA: rows of 128 bytes, 8-row groups 1024 bytes apart (SBO);
+// the leading offset is not used by this layout; version 1; layout 2
+// (128-byte swizzle).  A K = 16 step inside the row advances the start
+// address by 32 bytes.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3fffu);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait that also gives up when another role has aborted.
+__device__ __forceinline__ bool pipe_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+    const long long t0 = clock64();
+    for (int it = 0;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 63) == 63 && (*abort_flag || clock64() - t0 > kWaitCycles)) return false;
+    }
+}
+
+__device__ __forceinline__ void pipe_fail(volatile int* abort_flag, int* err) {
+    *abort_flag = 1;
+    if (err) atomicOr(err, 1);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kPipeThreads) k_gemm_pipe(const __grid_constant__ CUtensorMap tmA,
+                                                            const __grid_constant__ CUtensorMap tmB, GemmArgs g) {
+    using L = PipeSmem<BN>;
+    constexpr int TCOLS = BN < 32 ? 32 : BN;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_addr(smem_raw);
+    uint8_t* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::BUF);   // full[S], empty[S], acc
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const uint32_t sbase = smem_addr(smem);
+    const uint32_t bar0 = smem_addr(bars);
+    auto full_bar = [&](int s) { return bar0 + 8u * (uint32_t)s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (uint32_t)(kStages + s); };
+    const uint32_t acc_bar = bar0 + 8u * (uint32_t)(2 * kStages);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * BN;
+    const int nk = (g.K + kBK - 1) / kBK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(full_bar(s)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(empty_bar(s)) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(acc_bar) : "memory");
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_addr(tmem_slot)), "r"(TCOLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    int issued = 0;   // producer: loads issued
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int kc = 0; kc < nk; ++kc) {
+                const int s = kc % kStages;
+                if (kc >= kStages && !pipe_wait(empty_bar(s), (uint32_t)((kc / kStages - 1) & 1), abort_flag)) {
+                    pipe_fail(abort_flag, g.err);
+                    break;
+                }
+                const uint32_t a_dst = sbase + (uint32_t)(s * L::STAGE), b_dst = a_dst + (uint32_t)L::A_BYTES;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                             :: "r"(full_bar(s)), "r"((uint32_t)L::STAGE) : "memory");
+                asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                             " [%0], [%1, {%2, %3}], [%4];"
+                             :: "r"(a_dst), "l"((uint64_t)&tmA), "r"(kc * kBK), "r"(m0), "r"(full_bar(s))
+                             : "memory");
+                asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                             " [%0], [%1, {%2, %3}], [%4];"
+                             :: "r"(b_dst), "l"((uint64_t)&tmB), "r"(kc * kBK), "r"(n0), "r"(full_bar(s))
+                             : "memory");
+                issued = kc + 1;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(kTM, BN);
+            for (int kc = 0; kc < nk; ++kc) {
+                const int s = kc % kStages;
+                if (!pipe_wait(full_bar(s), (uint32_t)((kc / kStages) & 1), abort_flag)) {
+                    pipe_fail(abort_flag, g.err);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = sbase + (uint32_t)(s * L::STAGE), b0 = a0 + (uint32_t)L::A_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < kBK / 16; ++kk) {
+                    const uint64_t ad = sdesc_sw128(a0 + 32u * (uint32_t)kk);
+                    const uint64_t bd = sdesc_sw128(b0 + 32u * (uint32_t)kk);
+                    const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                        :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(empty_bar(s)) : "memory");
+            }
+            // the accumulator barrier completes once every MMA issued above has
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(acc_bar) : "memory");
+        }
+    } else {
+        const int q = warp & 3;                         // TMEM lane quarter of this warp
+        float* stg = reinterpret_cast<float*>(smem) + (warp - 2) * 32 * kEpiLd;
+        const bool ok = pipe_wait(acc_bar, 0u, abort_flag) && !*abort_flag;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // the staging area was last written by TMA (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (!ok) {
+            if (lane == 0) pipe_fail(abort_flag, g.err);
+        } else {
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t v[32];
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+                      "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+                      "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 32; ++j) stg[lane * kEpiLd + j] = __uint_as_float(v[j]);
+                __syncwarp();
+                const int col = n0 + c0 + lane;
+                const bool col_ok = (c0 + lane < BN) && col < g.N;
+                float bv = 0.0f;
+                if (col_ok && (g.epi == EPI_BIAS_F32 || g.epi == EPI_BIAS_GELU)) bv = g.bias[col];
+                for (int r = 0; r < 32; ++r) {
+                    const int row = m0 + q * 32 + r;
+                    if (row >= g.M || !col_ok) continue;
+                    const float a = stg[r * kEpiLd + lane];
+                    const size_t o = (size_t)row * g.ldc + col;
+                    if (g.epi == EPI_F32) {
+                        g.Cf[o] = a;
+                    } else if (g.epi == EPI_BIAS_F32) {
+                        g.Cf[o] = a + bv;
+                    } else if (g.epi == EPI_BIAS_GELU) {
+                        const float z = a + bv;
+                        const float h = gelu(z);
+                        if (g.aux_out) g.aux_out[o] = z;
+                        if (g.Cb) g.Cb[o] = __float2bfloat16(h);
+                        if (g.Cf) g.Cf[o] = h;
+                    } else {
+                        const float dz = a * gelu_grad(g.aux_in[o]);
+                        if (g.Cb) g.Cb[o] = __float2bfloat16(dz);
+                        if (g.Cf) g.Cf[o] = dz;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+    }
+
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (*abort_flag) {
+        // let issued loads and MMAs finish before the shared memory and TMEM go away
+        if (warp == 0 && lane == 0) {
+            for (int kc = issued - kStages < 0 ? 0 : issued - kStages; kc < issued; ++kc) {
+                const long long t0 = clock64();
+                while (!mbar_try(full_bar(kc % kStages), (uint32_t)((kc / kStages) & 1)) &&
+                       clock64() - t0 < kWaitCycles) {
+                }
+            }
+        }
+        if (warp == 1 && lane == 0) {
+            const long long t0 = clock64();
+            while (!mbar_try(acc_bar, 0u) && clock64() - t0 < kWaitCycles) {
+            }
+        }
+        __syncthreads();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TCOLS) : "memory");
+    }
+}
+
+// cuTensorMapEncodeTiled from the driver, through the runtime's entry-point query.
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// 2-D tensor map of a K-major bf16 matrix [rows][ld] (K = inner), box 64 x box_rows,
+// 128-byte swizzle, out-of-range elements read as zero.
+bool make_tmap(CUtensorMap* m, const void* ptr, int K, int rows, int ld, int box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+cg_status launch_gemm_pipe(const GemmArgs& g, cudaStream_t st) {
+    CUtensorMap ta, tb;
+    if (!make_tmap(&ta, g.A, g.K, g.M, g.lda, kTM) || !make_tmap(&tb, g.B, g.K, g.N, g.ldb, BN))
+        return CG_ERR_UNSUPPORTED;
+    using L = PipeSmem<BN>;
+    if (cudaFuncSetAttribute(k_gemm_pipe<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::TOTAL) != cudaSuccess)
+        return CG_ERR_CUDA;
+    const dim3 grid((g.N + BN - 1) / BN, (g.M + kTM - 1) / kTM);
+    k_gemm_pipe<BN><<<grid, kPipeThreads, L::TOTAL, st>>>(ta, tb, g);
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
+
 template <int BN>
 cg_status launch_gemm_bn(const GemmArgs& g, cudaStream_t st) {
     dim3 grid((g.N + BN - 1) / BN, (g.M + kTM - 1) / kTM);
@@ -242,6 +525,18 @@ cg_status gemm_bf16(const GemmArgs& g, cudaStream_t st) {
     if ((g.epi == EPI_F32 || g.epi == EPI_BIAS_F32) && !g.Cf) return CG_ERR_INVALID_ARG;
     if ((g.epi == EPI_BIAS_F32 || g.epi == EPI_BIAS_GELU) && !g.bias) return CG_ERR_INVALID_ARG;
     if (g.epi == EPI_GELU_GRAD && !g.aux_in) return CG_ERR_INVALID_ARG;
+    // K-major operands with 16-byte aligned rows: the TMA pipeline
+    const bool pipe = !g.transA && !g.transB && g.lda % 8 == 0 && g.ldb % 8 == 0 && g.lda >= g.K && g.ldb >= g.K &&
+                      ((uintptr_t)g.A & 15) == 0 && ((uintptr_t)g.B & 15) == 0 && g.M < (1 << 30) &&
+                      g.N < (1 << 30) && g.M <= 65535 * kTM;
+    if (pipe) {
+        cg_status r;
+        if (g.N >= 128) r = launch_gemm_pipe<128>(g, st);
+        else if (g.N > 32) r = launch_gemm_pipe<64>(g, st);
+        else if (g.N > 16) r = launch_gemm_pipe<32>(g, st);
+        else r = launch_gemm_pipe<16>(g, st);
+        if (r != CG_ERR_UNSUPPORTED) return r;
+    }
     if (g.N <= 16) return launch_gemm_bn<16>(g, st);
     if (g.N <= 64) return launch_gemm_bn<64>(g, st);
     return launch_gemm_bn<128>(g, st);

@@ -21,8 +21,13 @@ def _bf(shape, seed, dev, scale=1.0):
 
 
 @pytest.mark.parametrize("M,N,K,tA,tB", [(200, 512, 256, 0, 0), (300, 16, 512, 0, 0), (128, 128, 64, 0, 0),
-                                         (257, 512, 320, 0, 1), (512, 256, 200, 1, 1), (96, 40, 130, 1, 0)])
+                                         (257, 72, 200, 0, 0), (1000, 24, 520, 0, 0), (4096, 512, 512, 0, 0),
+                                         (64, 300, 130, 0, 0), (257, 512, 320, 0, 1), (512, 256, 200, 1, 1),
+                                         (96, 40, 130, 1, 0)])
 def test_gemm_matches_fp32_reference(dev, M, N, K, tA, tB):
+    """K-major operands with rows of a multiple of 8 elements take the TMA
+    pipeline (tails in M, N and K included); transposed operands and
+    K = 130 take the register-staged kernel."""
     A = _bf((K, M) if tA else (M, K), 1, dev)
     B = _bf((K, N) if tB else (N, K), 2, dev)
     C = torch.full((M, N), float("nan"), dtype=torch.float32, device=dev)
