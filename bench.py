@@ -324,7 +324,7 @@ def run(args):
             "e2e": {"value": units / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": x_pin.numel() * 8 + th_pin.numel() * 8,
                     "d2h_bytes_per_step": v_pin.numel() * 8 + g_pin.numel() * 8},
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": (3 if prec == cg.PREC_DF64 else 2) * args.steps,   # (split,) tiles, finalize
             "kernel_ms": kern_s * 1e3,
             "roofline": roof,
             "clocks": clk,
@@ -339,18 +339,20 @@ def run(args):
 
 
 # FP32-pipe operations of one event at one parameter point in the double-float
-# kernel, counted from its arithmetic (csrc/cg_df64.cuh, cg_df64.cu): double
-# split 2, two df64 subtractions 22, square + product for the exponent 14,
-# rate product 7, two exp 120, sum of two products 21, fallback test 4,
-# reciprocal 8, running product for the log 9, five adjoint products 25, five
-# compensated accumulations 40, the log and flushes amortised over 32 events 3.
-DF64_MIX_OPS = 275
+# kernel, counted from its arithmetic (csrc/cg_df64.cuh, cg_df64.cu): two df64
+# subtractions 22, square + product for the exponent 14, rate product 7, two
+# exp 120, sum of two products 21, fallback test 4, reciprocal 8, running
+# product for the log 9, five adjoint products 25, five compensated
+# accumulations 40, the log and flushes amortised over 32 events 3.  (The
+# events are split into float pairs once per call, 2 operations per event,
+# outside this kernel.)
+DF64_MIX_OPS = 273
 
 # DRAM bytes per launch of k_mix_df64 on the default workload, from
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum ... -k regex:k_mix_df64`
-# (80,100,864 read + 3,641,088 written), valid for the kernel sources whose
+# (80,480,512 read + 3,583,232 written), valid for the kernel sources whose
 # hash is given; reported as null once those sources change.
-DF64_MIX_TRAFFIC = {"bytes": 80100864 + 3641088, "sources_sha256_16": "9198080f62d83644",
+DF64_MIX_TRAFFIC = {"bytes": 80480512 + 3583232, "sources_sha256_16": "267e6442e6c3e0f7",
                     "sources": ["csrc/cg_df64.cu", "csrc/cg_df64.cuh", "csrc/cg_models.cuh", "csrc/cg_tiles.cuh",
                                 "csrc/cg_internal.cuh"]}
 

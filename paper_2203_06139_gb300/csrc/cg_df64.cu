@@ -7,6 +7,7 @@
 // every sum that leaves a thread is FP64.  Elements whose df64 evaluation
 // could lose accuracy (an exponential flushed to zero while the model value
 // is itself tiny) are recomputed in FP64 in place.
+#include <algorithm>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -48,14 +49,28 @@ __device__ __noinline__ void mix_elem_fallback(double x, double w, const MixCons
     if (b) *bad = 1;
 }
 
+// Events (and weights) split into df64 (hi, lo) float pairs once per call,
+// so the tiles of every parameter point read them ready to use.
+__global__ void k_split_events(const double* __restrict__ x, const double* __restrict__ w, int64_t n,
+                               float2* __restrict__ xs, float2* __restrict__ wsp) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const df a = df_split(__ldg(x + i));
+        xs[i] = make_float2(a.h, a.l);
+        if (w) {
+            const df b = df_split(__ldg(w + i));
+            wsp[i] = make_float2(b.h, b.l);
+        }
+    }
+}
+
 // One event: forward p(x), adjoint accumulators.  Without weights the log
 // terms are gathered as a running product P (one df_log per flush); with
-// weights each log is taken and weighted.
+// weights each log is taken and weighted.  X, Wd: the event and its weight
+// as df64; i: its index, for the FP64 fallback, which reads the originals.
 template <bool W>
-__device__ __forceinline__ void mix_elem_df64(double x, double w, const MixDf& c, const MixConsts& c64,
-                                              const DfTables& tab, DfAcc (&acc)[MixAcc::N], DfProd& P,
-                                              double* sum, int* bad) {
-    const df X = df_split(x);
+__device__ __forceinline__ void mix_elem_df64(df X, df Wd, int64_t i, const MixData& dd, const MixDf& c,
+                                              const MixConsts& c64, const DfTables& tab, DfAcc (&acc)[MixAcc::N],
+                                              DfProd& P, double* sum, int* bad) {
     const df d = df_sub(X, c.mu);
     const df q = df_mul(c.c, df_sqr(d));
     const df xl = (c.lo.h == 0.0f && c.lo.l == 0.0f) ? X : df_sub(X, c.lo);   // uniform per tile
@@ -66,14 +81,13 @@ __device__ __forceinline__ void mix_elem_df64(double x, double w, const MixDf& c
     const df p = df_add(df_mul_nn(c.a, eG), df_mul_nn(c.b, eE));
     // a flushed component (< 1e-30 of its coefficient) is negligible unless p is tiny too
     if ((flG && p.h < 1e-13f * fabsf(c.a.h)) || (flE && p.h < 1e-13f * fabsf(c.b.h)) || !(p.h > 1e-30f)) {
-        mix_elem_fallback<W>(x, w, c64, sum, bad);
+        mix_elem_fallback<W>(dd.x[i], W ? dd.w[i] : 1.0, c64, sum, bad);
         return;
     }
     df r = df_rcp(p);
     if (W) {
-        const df wd = df_split(w);
-        r = df_mul(r, wd);
-        dfacc_add(acc[0], df_mul(df_log(p, tab), wd));
+        r = df_mul(r, Wd);
+        dfacc_add(acc[0], df_mul(df_log(p, tab), Wd));
     } else {
         dfprod_mul(P, p);
     }
@@ -125,12 +139,19 @@ __global__ void __launch_bounds__(NT, 3) k_mix_df64(MixData d, const double* __r
         const int64_t e0 = (int64_t)c * tg.chunk;
         const int64_t e1 = min(tg.n_elem, e0 + tg.chunk);
         int64_t i = e0 + threadIdx.x;
+        const df one = df_make(1.0f, 0.0f);
+        auto ev = [&](int64_t k) { const float2 v = __ldg(d.xs + k); return df_make(v.x, v.y); };
+        auto wt = [&](int64_t k) {
+            if (!W) return one;
+            const float2 v = __ldg(d.wsp + k);
+            return df_make(v.x, v.y);
+        };
         if (kMixPairs) {
             // two independent events per iteration: their dependency chains interleave
             for (; i + NT < e1; i += 2 * NT) {
-                const double xa = __ldg(d.x + i), xb = __ldg(d.x + i + NT);
-                mix_elem_df64<W>(xa, W ? __ldg(d.w + i) : 1.0, cr, cs64, tab, acc, P, sum, &bad);
-                mix_elem_df64<W>(xb, W ? __ldg(d.w + i + NT) : 1.0, cr, cs64, tab, acc, P, sum, &bad);
+                const df xa = ev(i), xb = ev(i + NT);
+                mix_elem_df64<W>(xa, wt(i), i, d, cr, cs64, tab, acc, P, sum, &bad);
+                mix_elem_df64<W>(xb, wt(i + NT), i + NT, d, cr, cs64, tab, acc, P, sum, &bad);
                 cnt += 2;
                 if (cnt >= kFlush) {
                     if (!W) {
@@ -144,11 +165,11 @@ __global__ void __launch_bounds__(NT, 3) k_mix_df64(MixData d, const double* __r
                 }
             }
         }
-        double xn = (i < e1) ? __ldg(d.x + i) : 0.0;
+        df xn = (i < e1) ? ev(i) : one;
         for (; i < e1; i += NT) {
-            const double xi = xn;
-            if (i + NT < e1) xn = __ldg(d.x + i + NT);   // next event in flight during this one
-            mix_elem_df64<W>(xi, W ? __ldg(d.w + i) : 1.0, cr, cs64, tab, acc, P, sum, &bad);
+            const df xi = xn;
+            if (i + NT < e1) xn = ev(i + NT);   // next event in flight during this one
+            mix_elem_df64<W>(xi, wt(i), i, d, cr, cs64, tab, acc, P, sum, &bad);
             if (++cnt == kFlush) {
                 if (!W) {
                     dfacc_add(acc[0], dfprod_log(P, tab));
@@ -475,8 +496,13 @@ bool df64_supported(const cg_problem* pb) {
            (pb->model == CG_MODEL_ROTGAUSS2D && pb->n_bins[0] < (1 << 24) && pb->n_bins[1] < (1 << 24));
 }
 
+size_t df64_split_bytes(const cg_problem* pb) {
+    if (pb->model != CG_MODEL_MIX_GAUSS_EXP || pb->precision != CG_PREC_DF64) return 0;
+    return align_up((size_t)pb->n_events * sizeof(float2) * (pb->weights ? 2 : 1), 256);
+}
+
 cg_status launch_df64(const cg_problem* pb, const double* theta, int64_t n_theta, double* part, WsHeader* hdr,
-                      TileGrid* tg, cudaStream_t st, const int* gate, bool value_only) {
+                      TileGrid* tg, cudaStream_t st, const int* gate, bool value_only, void* split) {
     if (pb->model == CG_MODEL_MIX_GAUSS_EXP) {
         MixData d;
         d.x = pb->data;
@@ -484,6 +510,15 @@ cg_status launch_df64(const cg_problem* pb, const double* theta, int64_t n_theta
         d.lo = pb->lo[0];
         d.hi = pb->hi[0];
         d.vec_ok = 0;
+        float2* xs = reinterpret_cast<float2*>(split);
+        float2* wsp = pb->weights ? xs + pb->n_events : nullptr;
+        d.xs = xs;
+        d.wsp = wsp;
+        {
+            const int64_t blocks = std::min<int64_t>((pb->n_events + 255) / 256, 8 * (int64_t)device_sm_count());
+            k_split_events<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(pb->data, pb->weights,
+                                                                                  pb->n_events, xs, wsp);
+        }
         constexpr int NT = 256;
         if (pb->weights)
             return launch_tiles(k_mix_df64<true, NT>, NT, d, theta, pb->n_events, n_theta, part, hdr, tg, st, gate);

@@ -311,7 +311,8 @@ static int num_params(const cg_problem* pb) {
 size_t grad_workspace_bytes(const cg_problem* pb, int64_t n_theta) {
     if (validate(pb) != CG_OK || n_theta < 1) return 0;
     const int nacc = acc_count(pb);
-    return sizeof(WsHeader) + align_up((size_t)n_theta * (nacc + 1) * max_nbx(n_theta) * sizeof(double), 256);
+    return sizeof(WsHeader) + align_up((size_t)n_theta * (nacc + 1) * max_nbx(n_theta) * sizeof(double), 256) +
+           df64_split_bytes(pb);
 }
 
 template <int K>
@@ -380,7 +381,10 @@ cg_status grad_points(const cg_problem* pb, const double* theta, int64_t n_theta
         cudaMemsetAsync(part, 0, (size_t)n_theta * (nacc + 1) * sizeof(double), st);
         s = CG_OK;
     } else if (pb->precision == CG_PREC_DF64) {
-        s = launch_df64(pb, theta, n_theta, part, hdr, &tg, st, gate, grad == nullptr);
+        const int nacc_ = acc_count(pb);
+        void* split = (char*)ws + sizeof(WsHeader) +
+                      align_up((size_t)n_theta * (nacc_ + 1) * max_nbx(n_theta) * sizeof(double), 256);
+        s = launch_df64(pb, theta, n_theta, part, hdr, &tg, st, gate, grad == nullptr, split);
     } else if (pb->model == CG_MODEL_GAUSS_POLY) {
         GP1Data d;
         d.y = pb->data;

@@ -153,6 +153,8 @@ struct MixData {
     const double* w;
     double lo, hi;
     int vec_ok;
+    const float2* xs;   // df64 kernels: events split once per call into (hi, lo) float pairs
+    const float2* wsp;  // weights split likewise (or nullptr)
 };
 
 __device__ __forceinline__ double std_normal_cdf(double z) { return 0.5 * erfc(-z * 0.70710678118654752440); }
@@ -338,7 +340,8 @@ __device__ inline double epilogue(const EpiParams& ep, const double* __restrict_
 
 // double-float path (cg_df64.cu)
 bool df64_supported(const cg_problem* pb);
+size_t df64_split_bytes(const cg_problem* pb);   // workspace for events split into float pairs
 cg_status launch_df64(const cg_problem* pb, const double* theta, int64_t n_theta, double* part, WsHeader* hdr,
-                      TileGrid* tg, cudaStream_t st, const int* gate, bool value_only);
+                      TileGrid* tg, cudaStream_t st, const int* gate, bool value_only, void* split);
 
 }  // namespace cg
