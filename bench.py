@@ -132,6 +132,32 @@ def fp64_roofline(dur_s, n_units, rates, sm_max_mhz):
                           % (nsm, sm_max_mhz or 2070.0)}
 
 
+# FP64 work of one bin at one parameter point of the 1-D chi2 model with one
+# Gaussian and a linear background (centre, Horner, difference, square,
+# exponent, residual, weight, adjoint products and sums).
+GP1_OPS = dict(basic=22, exp=1, log=0, rcp=1)
+
+
+def fp64_equivalent(dur_s, n_units, rates, sm_max_mhz, ops):
+    """The same per-element work counted in FP64 DFMA-slot equivalents (calls
+    weighted by the measured FP64 call rates) against the FP64 unit's peak:
+    the roofline an FP64 kernel would have.  frac > 1: the kernel finishes
+    faster than an FP64 kernel could on this GPU."""
+    nsm = rates["n_sm"] if rates else 152
+    peak_dfma = nsm * 2 * (sm_max_mhz or 2070.0) * 1e6
+    if rates:
+        c_exp = rates["dfma_per_s"] / rates["exp_per_s"]
+        c_log = rates["dfma_per_s"] / rates["log_per_s"]
+        c_rcp = rates["dfma_per_s"] / rates["rcp_per_s"]
+    else:
+        c_exp, c_log, c_rcp = 23.7, 36.6, 7.8
+    slots = ops["basic"] + ops["exp"] * c_exp + ops["log"] * c_log + ops["rcp"] * c_rcp
+    t_bound = slots * n_units / peak_dfma
+    return {"slots_per_unit": slots, "fp64_bound_ms": t_bound * 1e3, "kernel_ms": dur_s * 1e3,
+            "frac": t_bound / dur_s,
+            "note": "FP64 roofline time of the same work / kernel time (> 1: faster than the FP64 roofline)"}
+
+
 def cpu_oracle_rate(n_events, thetas, threads=None):
     """The CPU tape oracle over a bounded sample, parallel over parameter points."""
     import oracle
@@ -143,6 +169,34 @@ def cpu_oracle_rate(n_events, thetas, threads=None):
     oracle.many(oracle.unbinned_mix, thetas, threads=threads, x=x, lo=0.0, hi=10.0)
     dt = time.perf_counter() - t0
     return n_events * len(thetas) / dt, threads, dt
+
+
+def cpu_closed_rates(n_events, thetas):
+    """The hand-written closed-form CPU gradient (OpenMP, all host cores and
+    one core) and the central-difference gradient (8 value-only passes) over a
+    bounded sample: the plain CPU ways to the same gradient."""
+    import oracle
+    from paper_2203_06139_gb300 import synth
+    oracle.build()
+    x = synth.c2_events(n_events)
+    cores = os.cpu_count() or 1
+    out = {}
+    for name, threads, pts in (("all_cores", 0, thetas), ("one_core", 1, thetas[:2])):
+        t0 = time.perf_counter()
+        for th in pts:
+            oracle.closed_mix(x, 0.0, 10.0, th, threads=threads)
+        dt = time.perf_counter() - t0
+        out[name] = n_events * len(pts) / dt
+    t0 = time.perf_counter()
+    for th in thetas[:4]:
+        oracle.closed_mix_fd(x, 0.0, 10.0, th, threads=0)
+    dt = time.perf_counter() - t0
+    return {"kind": "closed_form", "value": out["all_cores"], "unit": UNIT, "cores": cores,
+            "one_core_value": out["one_core"],
+            "central_fd": {"value": n_events * 4 / dt, "unit": UNIT, "cores": cores,
+                           "note": "gradients from 8 value-only passes (h = 1e-6 max(|theta|, 1e-3))"},
+            "sample": "first %d events x %d parameter points (one core: 2 points; FD: 4 points)"
+                      % (n_events, len(thetas))}
 
 
 def run_reference(args):
@@ -310,7 +364,9 @@ def run(args):
         if prec == cg.PREC_DF64:
             roof["traffic"] = _traffic_if_current(DF64_MIX_TRAFFIC, N_EV, N_PT)
             roof["algorithmic_bytes"] = N_EV * 8
+            roof["fp64_equivalent"] = fp64_equivalent(kern_s, N_EV * N_PT, rates, clk.get("sm_max_mhz"), MIX_OPS)
         cpu_v, cores, cpu_dt = cpu_oracle_rate(1000000, synth.c2_theta_points(N_PT))
+        cpu_closed = cpu_closed_rates(2000000, synth.c2_theta_points(N_PT)[:10])
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -331,7 +387,8 @@ def run(args):
             "unit_rates": rates,
             "fp64_path": fp64_leg,
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "first 1e6 events x %d parameter points (%.1f s wall)" % (N_PT, cpu_dt)},
+                             "sample": "first 1e6 events x %d parameter points (%.1f s wall)" % (N_PT, cpu_dt),
+                             "closed_form": cpu_closed},
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -454,6 +511,7 @@ def run_c1(args):
     if prec == cg.PREC_DF64:
         roof = df64_roofline(kern_s, 100 * 10000, rates, clk.get("sm_max_mhz"), ops=DF64_GP1_OPS,
                              kernel="k_gp1_df64", unit="bin-point")
+        roof["fp64_equivalent"] = fp64_equivalent(kern_s, 100 * 10000, rates, clk.get("sm_max_mhz"), GP1_OPS)
     else:
         roof = None
     th0 = torch.tensor(synth.c1_theta_points(1)[0], device="cuda")

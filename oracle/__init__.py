@@ -11,6 +11,11 @@ The arithmetic lives in ``cg_oracle.c``: a scalar tape-based reverse-mode AD
 (Sec. 4, Fig. 3).  This module compiles it with gcc (``-ffp-contract=off``)
 and calls it through ctypes.  ctypes releases the GIL during the call, so
 ``many()`` evaluates independent parameter points on several host threads.
+
+``cg_closed.c`` holds hand-written closed-form gradients (and a central
+finite-difference gradient) of the mixture NLL and the 1-D chi2, parallel
+with OpenMP: the CPU baselines timed beside the GPU kernels, and a second,
+independent statement of the derivatives that the tape must reproduce.
 """
 import ctypes
 import os
@@ -27,19 +32,32 @@ _LIB_PATH = os.path.join(_HERE, "libcg_oracle.so")
 CHI2, POISSON, POISSON_BC = 0, 1, 2
 OK, INVALID, DOMAIN = 0, 1, 2
 
+_CLOSED_SRC = os.path.join(_HERE, "cg_closed.c")
+_CLOSED_LIB = os.path.join(_HERE, "libcg_closed.so")
+
 _lib = None
+_closed = None
+
+
+def _gcc(src, out, extra=()):
+    stale = not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src)
+    if stale:
+        tmp = "%s.%d.tmp" % (out, os.getpid())
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", *extra,
+                               "-shared", "-o", tmp, src, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 def build(force=False):
-    """Compile cg_oracle.c into libcg_oracle.so next to it (plain gcc, no FMA contraction)."""
-    stale = (not os.path.exists(_LIB_PATH)
-             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
-    if force or stale:
-        tmp = "%s.%d.tmp" % (_LIB_PATH, os.getpid())
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC",
-                               "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    """Compile cg_oracle.c into libcg_oracle.so next to it (plain gcc, no FMA
+    contraction), and the closed-form CPU gradients cg_closed.c (OpenMP)."""
+    if force:
+        for f in (_LIB_PATH, _CLOSED_LIB):
+            if os.path.exists(f):
+                os.utime(f, (0, 0))
+    _gcc(_CLOSED_SRC, _CLOSED_LIB, ("-fopenmp",))
+    return _gcc(_SRC, _LIB_PATH)
 
 
 def _load():
@@ -165,6 +183,55 @@ def listing1_gauss(x, p, sigma):
     rc = lib.orc_listing1_gauss(x, p, sigma, ctypes.byref(v), ctypes.byref(dx), ctypes.byref(dp))
     assert rc == OK
     return v.value, dx.value, dp.value
+
+
+def _load_closed():
+    global _closed
+    if _closed is not None:
+        return _closed
+    build()
+    lib = ctypes.CDLL(_CLOSED_LIB)
+    dp = ctypes.POINTER(ctypes.c_double)
+    i64, c_int, c_d = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    lib.clf_mix.argtypes = [i64, dp, c_d, c_d, dp, dp, dp, c_int]
+    lib.clf_mix_fd.argtypes = [i64, dp, c_d, c_d, dp, dp, c_int]
+    lib.clf_gauss_poly_chi2.argtypes = [c_int, c_int, c_int, i64, c_d, c_d, dp, dp, dp, dp, c_int]
+    for f in (lib.clf_mix, lib.clf_mix_fd, lib.clf_gauss_poly_chi2):
+        f.restype = c_int
+    _closed = lib
+    return lib
+
+
+def closed_mix(x, lo, hi, theta, grad=True, threads=0):
+    """Mixture NLL and its hand-written gradient (cg_closed.c, OpenMP; threads 0 = all)."""
+    lib = _load_closed()
+    x, theta = _f64(x), _f64(theta)
+    g = np.zeros(4) if grad else None
+    v = ctypes.c_double(0.0)
+    rc = lib.clf_mix(x.size, _p(x), lo, hi, _p(theta), ctypes.byref(v), _p(g), threads)
+    assert rc == 0
+    return v.value, g
+
+
+def closed_mix_fd(x, lo, hi, theta, threads=0):
+    """Central-difference gradient of the mixture NLL from 8 value-only evaluations."""
+    lib = _load_closed()
+    x, theta = _f64(x), _f64(theta)
+    g = np.zeros(4)
+    assert lib.clf_mix_fd(x.size, _p(x), lo, hi, _p(theta), _p(g), threads) == 0
+    return g
+
+
+def closed_gauss_poly_chi2(K, D, poly_mode, y, lo, hi, theta, grad=True, threads=0):
+    """chi2 of K Gaussians + degree-D polynomial and its hand-written gradient."""
+    lib = _load_closed()
+    y, theta = _f64(y), _f64(theta)
+    g = np.zeros(3 * K + D + 1) if grad else None
+    v = ctypes.c_double(0.0)
+    rc = lib.clf_gauss_poly_chi2(K, D, poly_mode, y.size, lo, hi, _p(y), _p(theta), ctypes.byref(v), _p(g),
+                                 threads)
+    assert rc == 0
+    return v.value, g
 
 
 def many(fn, thetas, threads=None, **kw):
