@@ -588,7 +588,7 @@ def run_c5fit(args):
     __graft_entry__.build()
     from paper_2203_06139_gb300 import learned_start as ls, synth
     H = args.hists or 65536
-    y = synth.c5_batch_device(H, ls.N_BINS)
+    y = synth.c5_batch_device(H, ls.N_BINS)["y"]
     th = ls.heuristic_start(y, H)
     ls.fit_batch(y, H, th, 50, 1e-9)   # warm-up
     ts = []
@@ -608,6 +608,63 @@ def run_c5fit(args):
             "config": {"workload": "%d histograms x 2048 bins, 3 Gaussians + linear, Baker-Cousins, heuristic "
                                    "start, 50 iterations, df64" % H},
             "mean_evals": float(ev.mean()), "max_evals": int(ev.max())}
+    print(json.dumps(line), flush=True)
+
+
+def run_expr(args):
+    """Expression programs (source-transformation AD, NVRTC-compiled): the c1
+    and c2 objectives written as expressions, timed next to the hand-written
+    FP64 and double-float kernels of the same objectives."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2203_06139_gb300 import cg, synth
+    from paper_2203_06139_gb300 import expr as E
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    out = {}
+    # c1: chi2 of a Gaussian + line, 10,000 bins x 100 points
+    x = lambda: 0.0 + (E.index() + 0.5) * (10.0 / 10000)
+    xc = x()
+    A, mu, s, c0, c1 = (E.param(k) for k in range(5))
+    f = A * E.exp(-(xc - mu) ** 2 / (2.0 * s ** 2)) + c0 + c1 * xc
+    y = E.inp(0)
+    t0 = time.perf_counter()
+    prog1 = E.compile((y - f) ** 2 / E.maximum(y, 1.0), 5, 1)
+    compile_s = time.perf_counter() - t0
+    h = synth.c1_histogram()
+    yt = torch.tensor(h["y"], device="cuda")
+    th = torch.tensor(synth.c1_theta_points(), device="cuda")
+    p64 = cg.Problem.gauss_poly(yt, 0.0, 10.0, 1, 1, cg.OBJ_CHI2)
+    pdf = cg.Problem.gauss_poly(yt, 0.0, 10.0, 1, 1, cg.OBJ_CHI2, precision=cg.PREC_DF64)
+    ms_gen = _timed(lambda: prog1.gradient([yt], th), args.steps, max(3, args.warmup), flush)
+    ms_64 = _timed(lambda: cg.batch_gradient(p64, th), args.steps, max(3, args.warmup), flush)
+    ms_df = _timed(lambda: cg.batch_gradient(pdf, th), args.steps, max(3, args.warmup), flush)
+    out["c1"] = {"generated_fp64_ms": ms_gen, "hand_fp64_ms": ms_64, "hand_df64_ms": ms_df,
+                 "compile_s": compile_s, "accumulators": prog1.num_acc}
+    # c2: unbinned mixture NLL with both normalisations, 1e7 events x 50 points
+    xe = E.inp(0)
+    fr, mu2, s2, lam = (E.param(k) for k in range(4))
+    phi = lambda z: 0.5 * E.erfc(-z / np.sqrt(2.0))
+    ZG = phi((10.0 - mu2) / s2) - phi((0.0 - mu2) / s2)
+    ZE = 1.0 - E.exp(-lam * 10.0)
+    G = E.exp(-(xe - mu2) ** 2 / (2.0 * s2 ** 2)) / (s2 * np.sqrt(2.0 * np.pi) * ZG)
+    Ex = lam * E.exp(-lam * xe) / ZE
+    prog2 = E.compile(-E.log(fr * G + (1.0 - fr) * Ex), 4, 1)
+    xt = torch.tensor(synth.c2_events(), device="cuda")
+    th2 = torch.tensor(synth.c2_theta_points(), device="cuda")
+    m64 = cg.Problem.mixture(xt, 0.0, 10.0)
+    mdf = cg.Problem.mixture(xt, 0.0, 10.0, precision=cg.PREC_DF64)
+    steps = max(2, min(args.steps, 3))
+    ms2_gen = _timed(lambda: prog2.gradient([xt], th2), steps, 2, flush)
+    ms2_64 = _timed(lambda: cg.batch_gradient(m64, th2), steps, 2, flush)
+    ms2_df = _timed(lambda: cg.batch_gradient(mdf, th2), steps, 2, flush)
+    out["c2"] = {"generated_fp64_ms": ms2_gen, "hand_fp64_ms": ms2_64, "hand_df64_ms": ms2_df,
+                 "accumulators": prog2.num_acc}
+    line = {"metric": "time per batched gradient, generated vs hand-written kernels", "workload": "expr",
+            "value": 1e7 * 50 / (ms2_gen * 1e-3), "unit": UNIT, "higher_is_better": True,
+            "config": {"workload": "c1 (1e4 bins x 100 points) and c2 (1e7 events x 50 points) objectives as "
+                                   "expression programs, FP64"}, "results": out}
     print(json.dumps(line), flush=True)
 
 
@@ -757,7 +814,7 @@ def main():
     ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64-path comparison leg")
     ap.add_argument("--events", type=int, default=N_EVENTS)
     ap.add_argument("--points", type=int, default=N_POINTS)
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "c5fit", "fig3b", "gemm"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "c5fit", "fig3b", "gemm", "expr"])
     ap.add_argument("--plain-hists", type=int, default=0, help="c4: histograms timed on the plain path (0 = all)")
     ap.add_argument("--hists", type=int, default=0, help="c5fit: histograms in the batch (0 = 65,536)")
     ap.add_argument("--train-hists", type=int, default=0, help="c5: training histograms (0 = 10^6)")
@@ -780,6 +837,8 @@ def main():
         run_gemm(args)
     elif args.workload == "c5fit":
         run_c5fit(args)
+    elif args.workload == "expr":
+        run_expr(args)
     else:
         run(args)
 

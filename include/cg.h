@@ -368,6 +368,84 @@ cg_status cg_fit_single_init(const cg_problem *pb, const double *theta0, cg_fit_
 cg_status cg_fit_single_step(const cg_problem *pb, cg_fit_state *state, int n_evals, double tol,
                              void *ws, size_t ws_bytes, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Expression programs: the per-element term of an objective written as an
+ * expression, differentiated by source transformation.  The paper's tool
+ * turns the source of a C++ function into the source of its reverse-mode
+ * derivative (Sec. 2-3, Listings 1-2); here the function is a small
+ * expression DAG and libcg writes the CUDA source of one fused kernel (the
+ * forward evaluation and the reverse sweep of every element, summed per
+ * tile in a fixed order) plus a finalize kernel (chunk-ordered sums and the
+ * reverse sweep of the parameter-only part), compiles it at run time with
+ * NVRTC for this GPU and launches it.  Objective = sum over the n elements
+ * of the root node; gradient with respect to the parameters.
+ *
+ * Nodes are given in topological order (operands a, b refer to earlier
+ * nodes); the last node is the per-element term.  Subexpressions of the
+ * parameters alone (normalisations, 1/(2 s^2)) are evaluated once per
+ * parameter point and their adjoints accumulated over the elements, then
+ * chained to the parameters once (the prologue / epilogue of the hand-written
+ * kernels).  FP64 throughout.
+ * ------------------------------------------------------------------------ */
+typedef enum {
+    CG_EX_CONST = 0,   /* the constant c */
+    CG_EX_PARAM = 1,   /* theta[i] */
+    CG_EX_INPUT = 2,   /* input array i at the element */
+    CG_EX_INDEX = 3,   /* the element index, as a double */
+    CG_EX_ADD = 4,     /* a + b */
+    CG_EX_SUB = 5,     /* a - b */
+    CG_EX_MUL = 6,     /* a * b */
+    CG_EX_DIV = 7,     /* a / b */
+    CG_EX_NEG = 8,     /* -a */
+    CG_EX_EXP = 9,     /* exp(a) */
+    CG_EX_LOG = 10,    /* log(a) */
+    CG_EX_SQRT = 11,   /* sqrt(a) */
+    CG_EX_ERFC = 12,   /* erfc(a) */
+    CG_EX_POWI = 13,   /* a^i, integer i in [-16, 16] */
+    CG_EX_MAX = 14     /* max(a, b); the derivative goes to a when a >= b */
+} cg_expr_op;
+
+typedef struct {
+    int32_t op;   /* cg_expr_op */
+    int32_t a, b; /* operand node indices (earlier nodes), -1 when unused */
+    int32_t i;    /* parameter or input index, or the exponent of POWI */
+    double c;     /* the constant of CONST */
+} cg_expr_node;
+
+typedef struct cg_expr_program cg_expr_program;
+
+#define CG_EXPR_MAX_NODES 4096
+#define CG_EXPR_MAX_INPUTS 4
+#define CG_EXPR_MAX_PARAMS 128
+
+/* Generate, compile (NVRTC, loaded at first use) and load the kernels of an
+ * expression program on the current device.  *out receives the program
+ * (free with cg_expr_free).  CG_ERR_INVALID_ARG for a malformed program
+ * (bad operand order or index, a root that does not depend on the
+ * elements), CG_ERR_UNSUPPORTED when NVRTC or the driver entry points are
+ * unavailable or the elements use more than 63 parameter-only subexpressions
+ * (per-thread accumulators), CG_ERR_CUDA when compilation or loading fails.  With
+ * CG_ERR_UNSUPPORTED (no NVRTC, driver or device) or CG_ERR_CUDA, *out still
+ * receives a program that holds the generated source and the compiler log
+ * but cannot run; free it with cg_expr_free. */
+cg_status cg_expr_compile(const cg_expr_node *nodes, int n_nodes, int n_params, int n_inputs,
+                          cg_expr_program **out);
+/* The generated CUDA source and the last compiler log (owned by the program). */
+const char *cg_expr_source(const cg_expr_program *prog);
+const char *cg_expr_log(const cg_expr_program *prog);
+/* Number of per-thread accumulators of the generated tile kernel (1 value +
+ * one per parameter-only node the elements use). */
+int cg_expr_num_acc(const cg_expr_program *prog);
+size_t cg_expr_workspace_size(const cg_expr_program *prog, int64_t n, int64_t n_theta);
+/* Objective and gradient at n_theta parameter points.  inputs: host array of
+ * n_inputs device pointers, each [n] FP64; theta: device [n_theta][n_params];
+ * value: device [n_theta]; grad: device [n_theta][n_params] or NULL (values
+ * only).  Asynchronous on stream; capturable in a CUDA graph. */
+cg_status cg_expr_gradient(const cg_expr_program *prog, const double *const *inputs, int64_t n,
+                           const double *theta, int64_t n_theta, double *value, double *grad, void *ws,
+                           size_t ws_bytes, void *stream);
+void cg_expr_free(cg_expr_program *prog);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,9 @@ def _load():
     lib.orc_unbinned_mix.argtypes = [i64, dp, dp, c_d, c_d, dp, dp, dp, dp]
     lib.orc_binned2d.argtypes = [c_int, i64, i64, c_d, c_d, c_d, c_d, dp, dp, dp, dp, dp]
     lib.orc_listing1_gauss.argtypes = [c_d, c_d, c_d, dp, dp, dp]
+    ip = ctypes.POINTER(ctypes.c_int32)
+    lib.orc_expr.argtypes = [c_int, ip, ip, ip, ip, dp, c_int, c_int, ctypes.POINTER(dp), i64, dp, dp, dp, dp]
+    lib.orc_expr.restype = c_int
     for f in (lib.orc_binned1d, lib.orc_binned1d_gn, lib.orc_gauss_poly_eval,
               lib.orc_unbinned_mix, lib.orc_binned2d, lib.orc_listing1_gauss):
         f.restype = c_int
@@ -232,6 +235,32 @@ def closed_gauss_poly_chi2(K, D, poly_mode, y, lo, hi, theta, grad=True, threads
                                  threads)
     assert rc == 0
     return v.value, g
+
+
+def expr(nodes, n_params, inputs, theta, n=None):
+    """Objective and gradient of an expression program (nodes: rows of
+    (op, a, b, i, c), topological order, last = per-element term; the
+    operations are listed at orc_expr in cg_oracle.c)."""
+    lib = _load()
+    nodes = list(nodes)
+    op = np.ascontiguousarray([r[0] for r in nodes], dtype=np.int32)
+    na = np.ascontiguousarray([r[1] for r in nodes], dtype=np.int32)
+    nb = np.ascontiguousarray([r[2] for r in nodes], dtype=np.int32)
+    ni = np.ascontiguousarray([r[3] for r in nodes], dtype=np.int32)
+    nc = np.ascontiguousarray([r[4] for r in nodes], dtype=np.float64)
+    ins = [_f64(x) for x in inputs]
+    if n is None:
+        n = ins[0].size if ins else 0
+    dp = ctypes.POINTER(ctypes.c_double)
+    arr = (dp * max(1, len(ins)))(*[_p(x) for x in ins])
+    ip = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    theta = _f64(theta)
+    g = np.zeros(max(n_params, 1))
+    s = np.zeros(max(n_params, 1))
+    v = ctypes.c_double(0.0)
+    rc = lib.orc_expr(len(nodes), ip(op), ip(na), ip(nb), ip(ni), _p(nc), n_params, len(ins), arr, n, _p(theta),
+                      ctypes.byref(v), _p(g), _p(s))
+    return Result(v.value, g[:n_params], s[:n_params], rc)
 
 
 def many(fn, thetas, threads=None, **kw):

@@ -147,6 +147,22 @@ static int32_t t_erfc(tape *T, int32_t a) {
     /* d erfc(z)/dz = -2/sqrt(pi) exp(-z^2) */
     return push(T, erfc(z), a, -2.0 / sqrt(M_PI) * exp(-z * z), -1, 0.0);
 }
+static int32_t t_sqrt(tape *T, int32_t a) {
+    double r = sqrt(VAL(a));
+    if (!(VAL(a) >= 0.0)) T->domain = 1;
+    return push(T, r, a, 0.5 / r, -1, 0.0);
+}
+/* a^k for an integer k: d/da = k a^(k-1) */
+static int32_t t_powi(tape *T, int32_t a, int k) {
+    double x = VAL(a);
+    if (k == 0) return t_const(T, 1.0);
+    return push(T, pow(x, (double)k), a, (double)k * pow(x, (double)(k - 1)), -1, 0.0);
+}
+/* max(a, b): the derivative goes to a when a >= b */
+static int32_t t_max(tape *T, int32_t a, int32_t b) {
+    if (VAL(a) >= VAL(b)) return push(T, VAL(a), a, 1.0, b, 0.0);
+    return push(T, VAL(b), a, 0.0, b, 1.0);
+}
 static int32_t t_sin(tape *T, int32_t a) { return push(T, sin(VAL(a)), a, cos(VAL(a)), -1, 0.0); }
 static int32_t t_cos(tape *T, int32_t a) { return push(T, cos(VAL(a)), a, -sin(VAL(a)), -1, 0.0); }
 
@@ -496,3 +512,67 @@ int orc_listing1_gauss(double x, double p, double sigma, double *value, double *
     tape_free(&T);
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* Expression programs.                                                */
+/* ------------------------------------------------------------------ */
+
+/* Objective sum_e T_e of an expression program and its gradient: the nodes
+ * (op[j], a[j], b[j], i[j], c[j]) in topological order, the last one the
+ * per-element term T_e.  Operations: 0 constant c, 1 parameter theta[i],
+ * 2 input i at the element, 3 the element index, 4 a+b, 5 a-b, 6 a*b,
+ * 7 a/b, 8 -a, 9 exp a, 10 log a, 11 sqrt a, 12 erfc a, 13 a^i, 14 max(a, b)
+ * (derivative to a when a >= b).  inputs: n_inputs arrays of n doubles.
+ * Every element records all its nodes on the tape afresh (parameters are
+ * the tape's leaves), is swept in reverse and popped: no hoisting of the
+ * parameter-only part, so nothing but the definitions above is involved. */
+int orc_expr(int n_nodes, const int32_t *op, const int32_t *na, const int32_t *nb, const int32_t *ni,
+             const double *nc, int n_params, int n_inputs, const double *const *inputs, int64_t n,
+             const double *theta, double *value, double *grad, double *scale) {
+    if (n_nodes < 1 || n_params < 0 || n < 0) return ORC_INVALID;
+    tape T;
+    accum A;
+    if (!tape_init(&T, 64 + 2 * n_nodes) || !accum_init(&A, n_params > 0 ? n_params : 1)) return ORC_INVALID;
+    for (int k = 0; k < n_params; ++k) t_var(&T, theta[k]);
+    A.P = n_params;
+    A.mark = T.len;
+    int32_t *t = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_nodes);
+    int rc = ORC_OK;
+    for (int64_t e = 0; e < n && rc == ORC_OK; ++e) {
+        for (int j = 0; j < n_nodes; ++j) {
+            const int32_t a = na[j] >= 0 ? t[na[j]] : -1, b = nb[j] >= 0 ? t[nb[j]] : -1;
+            switch (op[j]) {
+                case 0: t[j] = t_const(&T, nc[j]); break;
+                case 1:
+                    if (ni[j] < 0 || ni[j] >= n_params) { rc = ORC_INVALID; break; }
+                    t[j] = ni[j];
+                    break;
+                case 2:
+                    if (ni[j] < 0 || ni[j] >= n_inputs) { rc = ORC_INVALID; break; }
+                    t[j] = t_const(&T, inputs[ni[j]][e]);
+                    break;
+                case 3: t[j] = t_const(&T, (double)e); break;
+                case 4: t[j] = t_add(&T, a, b); break;
+                case 5: t[j] = t_sub(&T, a, b); break;
+                case 6: t[j] = t_mul(&T, a, b); break;
+                case 7: t[j] = t_div(&T, a, b); break;
+                case 8: t[j] = t_neg(&T, a); break;
+                case 9: t[j] = t_exp(&T, a); break;
+                case 10: t[j] = t_log(&T, a); break;
+                case 11: t[j] = t_sqrt(&T, a); break;
+                case 12: t[j] = t_erfc(&T, a); break;
+                case 13: t[j] = t_powi(&T, a, ni[j]); break;
+                case 14: t[j] = t_max(&T, a, b); break;
+                default: rc = ORC_INVALID;
+            }
+            if (rc != ORC_OK) break;
+        }
+        if (rc == ORC_OK) finish_term(&T, &A, t[n_nodes - 1]);
+    }
+    if (rc == ORC_OK) rc = finish(&T, &A, value, grad, scale);
+    free(t);
+    tape_free(&T);
+    accum_free(&A);
+    return rc;
+}
+

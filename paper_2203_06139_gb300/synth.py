@@ -264,7 +264,8 @@ def c5_batch_device(H, n_bins=2048, index=4, chunk=0, device="cuda"):
     """Workload-4 histograms drawn on the GPU (for the 10^6-histogram training
     set): truth from c5_truth (numpy PCG64), expected counts at the bin
     centres, Poisson counts from a torch generator seeded with the same base
-    seed.  Returns the counts as a device tensor [H * n_bins]."""
+    seed.  Returns the batch as a dict whose "y" holds the counts as a device
+    tensor [H * n_bins]."""
     import torch
     truth = c5_truth(H, index, chunk)
     t = torch.tensor(truth, device=device)
