@@ -796,11 +796,48 @@ def run_fig3b(args):
         rows.append({"K": K, "P": P, "ms_gradient_ad": t_ad, "ms_value": t_val, "ms_gradient_fd": t_fd,
                      "ad_over_value": t_ad / t_val, "fd_over_ad": t_fd / t_ad,
                      "fd_vs_ad_max_rel": float(np.max(np.abs(g_fd - g_ad) / np.maximum(np.abs(g_ad), 1e-3)))})
-    line = {"metric": METRIC, "workload": "fig3b", "value": rows[-1]["fd_over_ad"], "unit": "FD/AD gradient time at K=4",
-            "higher_is_better": True,
-            "config": {"workload": "chi2, K Gaussians + linear, 10^6 bins, double-float kernels; FD = 2P values "
-                                   "in one batched launch, h = 1e-6 relative"},
-            "rows": rows}
+    # the same comparison to K = 16 (P = 50) with expression programs (FP64,
+    # generated kernels): AD = the gradient program at one point, FD = the
+    # value-only program at 2P points in one launch
+    from paper_2203_06139_gb300 import expr as E
+    rows_expr = []
+    for K in (1, 2, 4, 8, 16):
+        p = synth.random_gauss_poly(K, 1, n, seed=400 + K)
+        P = 3 * K + 2
+        x = (E.index() + 0.5) * (1.0 / n)
+        f = E.param(3 * K) + E.param(3 * K + 1) * x
+        for k in range(K):
+            A, mu, sg = E.param(3 * k), E.param(3 * k + 1), E.param(3 * k + 2)
+            f = f + A * E.exp(-(x - mu) ** 2 / (2.0 * sg ** 2))
+        y = E.inp(0)
+        term = (y - f) ** 2 / E.maximum(y, 1.0)
+        g_prog = E.compile(term, P, 1)
+        v_prog = E.compile(term, P, 1, value_only=True)
+        yt = torch.tensor(p["y"], device="cuda")
+        h = 1e-6 * np.maximum(np.abs(p["theta"]), 1e-3)
+        fd_pts = np.repeat(p["theta"][None, :], 2 * P, axis=0)
+        for k in range(P):
+            fd_pts[2 * k, k] += h[k]
+            fd_pts[2 * k + 1, k] -= h[k]
+        fd_t = torch.tensor(fd_pts, device="cuda")
+        one = torch.tensor(p["theta"][None, :], device="cuda")
+        t_ad = _timed(lambda: g_prog.gradient([yt], one), args.steps, max(3, args.warmup))
+        t_val = _timed(lambda: v_prog.objective([yt], one), args.steps, max(3, args.warmup))
+        t_fd = _timed(lambda: v_prog.objective([yt], fd_t), args.steps, max(3, args.warmup))
+        _, g1 = g_prog.gradient([yt], one)
+        f = v_prog.objective([yt], fd_t).cpu().numpy()
+        g_fd = (f[0::2] - f[1::2]) / (2 * h)
+        g_ad = g1[0].cpu().numpy()
+        rows_expr.append({"K": K, "P": P, "ms_gradient_ad": t_ad, "ms_value": t_val, "ms_gradient_fd": t_fd,
+                          "ad_over_value": t_ad / t_val, "fd_over_ad": t_fd / t_ad,
+                          "accumulators": g_prog.num_acc,
+                          "fd_vs_ad_max_rel": float(np.max(np.abs(g_fd - g_ad) / np.maximum(np.abs(g_ad), 1e-3)))})
+    line = {"metric": METRIC, "workload": "fig3b", "value": rows_expr[-1]["fd_over_ad"],
+            "unit": "FD/AD gradient time at K=16 (P=50)", "higher_is_better": True,
+            "config": {"workload": "chi2, K Gaussians + linear, 10^6 bins; rows: double-float hand-written kernels "
+                                   "K=1..4; rows_expr: FP64 expression programs K=1..16; FD = 2P values in one "
+                                   "batched launch, h = 1e-6 relative"},
+            "rows": rows, "rows_expr": rows_expr}
     print(json.dumps(line), flush=True)
 
 

@@ -419,7 +419,9 @@ typedef struct cg_expr_program cg_expr_program;
 #define CG_EXPR_MAX_PARAMS 128
 
 /* Generate, compile (NVRTC, loaded at first use) and load the kernels of an
- * expression program on the current device.  *out receives the program
+ * expression program on the current device (flags: 0, or CG_EXPR_VALUE_ONLY
+ * for a program whose kernels evaluate the objective only; its
+ * cg_expr_gradient calls must pass grad = NULL).  *out receives the program
  * (free with cg_expr_free).  CG_ERR_INVALID_ARG for a malformed program
  * (bad operand order or index, a root that does not depend on the
  * elements), CG_ERR_UNSUPPORTED when NVRTC or the driver entry points are
@@ -428,7 +430,8 @@ typedef struct cg_expr_program cg_expr_program;
  * CG_ERR_UNSUPPORTED (no NVRTC, driver or device) or CG_ERR_CUDA, *out still
  * receives a program that holds the generated source and the compiler log
  * but cannot run; free it with cg_expr_free. */
-cg_status cg_expr_compile(const cg_expr_node *nodes, int n_nodes, int n_params, int n_inputs,
+#define CG_EXPR_VALUE_ONLY 1   /* flags: objective only (no reverse sweep is generated) */
+cg_status cg_expr_compile(const cg_expr_node *nodes, int n_nodes, int n_params, int n_inputs, int flags,
                           cg_expr_program **out);
 /* The generated CUDA source and the last compiler log (owned by the program). */
 const char *cg_expr_source(const cg_expr_program *prog);

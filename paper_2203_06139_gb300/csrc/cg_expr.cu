@@ -50,7 +50,7 @@ typedef nvrtcResult_t (*fn_nvrtcDestroyProgram)(nvrtcProgram_t*);
 
 struct cg_expr_program {
     std::string source, log;
-    int n_params = 0, n_inputs = 0, n_acc = 0, device = -1;
+    int n_params = 0, n_inputs = 0, n_acc = 0, device = -1, value_only = 0;
     CUmodule mod = nullptr;
     CUfunction f_tiles = nullptr, f_fin = nullptr;
 };
@@ -267,8 +267,8 @@ std::vector<std::pair<int, std::string>> partials(const cg_expr_node& x, int j, 
     return r;
 }
 
-std::string generate(const cg_expr_node* nd, int n, int P, int NI, const Plan& pl) {
-    const int NF = (int)pl.front.size(), NACC = 1 + NF;
+std::string generate(const cg_expr_node* nd, int n, int P, int NI, const Plan& pl, bool value_only) {
+    const int NF = (int)pl.front.size(), NACC = value_only ? 1 : 1 + NF;
     const int root = n - 1;
     // per-element divisions by values fixed per point (constants, parameter-only
     // nodes) become products with a reciprocal taken once per point
@@ -326,7 +326,7 @@ std::string generate(const cg_expr_node* nd, int n, int P, int NI, const Plan& p
         if (pl.cls[j] == K_INPUT_ONLY || pl.cls[j] == K_MIXED)
             s += "      const double " + v(j) + " = " + forward_expr(nd[j], true, recip_div(j)) + ";\n";
     s += "      acc[0] += " + v(root) + ";\n";
-    if (pl.cls[root] == K_MIXED) {
+    if (pl.cls[root] == K_MIXED && !value_only) {
         // adjoints of the mixed nodes and of the frontier, reverse order
         for (int j = 0; j < n; ++j)
             if (pl.cls[j] == K_MIXED || pl.front_slot[j] >= 0)
@@ -358,7 +358,12 @@ std::string generate(const cg_expr_node* nd, int n, int P, int NI, const Plan& p
     s += "  const int th = blockIdx.x * blockDim.x + threadIdx.x;\n  if (th >= n_theta) return;\n";
     s += "  double S[NACC];\n  for (int k = 0; k < NACC; ++k) {\n    double sum = 0.0;\n"
          "    for (int cc = 0; cc < nbx; ++cc) sum += part[((i64)th * NACC + k) * nbx + cc];\n    S[k] = sum;\n  }\n";
-    s += "  value[th] = S[0];\n  if (!grad) return;\n";
+    s += "  value[th] = S[0];\n";
+    if (value_only) {
+        s += "}\n";
+        return s;
+    }
+    s += "  if (!grad) return;\n";
     s += "  const double* tp = theta + (i64)th * NPAR;\n";
     for (int j = 0; j < n; ++j)
         if (pl.cls[j] == K_PARAM_ONLY || pl.cls[j] == K_CONST)
@@ -418,18 +423,20 @@ using namespace cg;
 
 extern "C" {
 
-cg_status cg_expr_compile(const cg_expr_node* nodes, int n_nodes, int n_params, int n_inputs,
+cg_status cg_expr_compile(const cg_expr_node* nodes, int n_nodes, int n_params, int n_inputs, int flags,
                           cg_expr_program** out) {
-    if (!out) return CG_ERR_INVALID_ARG;
+    if (!out || (flags & ~CG_EXPR_VALUE_ONLY)) return CG_ERR_INVALID_ARG;
     *out = nullptr;
+    const bool value_only = (flags & CG_EXPR_VALUE_ONLY) != 0;
     Plan pl;
     cg_status s = validate_and_plan(nodes, n_nodes, n_params, n_inputs, pl);
     if (s != CG_OK) return s;
     cg_expr_program* p = new cg_expr_program();
     p->n_params = n_params;
     p->n_inputs = n_inputs;
-    p->n_acc = 1 + (int)pl.front.size();
-    p->source = generate(nodes, n_nodes, n_params, n_inputs, pl);
+    p->value_only = value_only ? 1 : 0;
+    p->n_acc = value_only ? 1 : 1 + (int)pl.front.size();
+    p->source = generate(nodes, n_nodes, n_params, n_inputs, pl, value_only);
     const Nvrtc& nv = nvrtc();
     const Driver& dr = driver();
     if (!nv.ok || !dr.ok || cudaFree(nullptr) != cudaSuccess) {   // cudaFree(0): the runtime's context is current
@@ -484,6 +491,7 @@ cg_status cg_expr_gradient(const cg_expr_program* prog, const double* const* inp
                            int64_t n_theta, double* value, double* grad, void* ws, size_t ws_bytes, void* stream) {
     if (!prog || !prog->f_tiles || n < 1 || n_theta < 1 || n_theta > (1 << 24) || !theta || !value)
         return CG_ERR_INVALID_ARG;
+    if (grad && prog->value_only) return CG_ERR_INVALID_ARG;
     if (prog->n_inputs > 0 && !inputs) return CG_ERR_INVALID_ARG;
     for (int k = 0; k < prog->n_inputs; ++k)
         if (!inputs[k]) return CG_ERR_INVALID_ARG;

@@ -25,6 +25,7 @@ import torch
 from . import cg
 
 CONST, PARAM, INPUT, INDEX, ADD, SUB, MUL, DIV, NEG, EXP, LOG, SQRT, ERFC, POWI, MAX = range(15)
+VALUE_ONLY = 1   # compile flag: the objective only
 _UNARY = {NEG, EXP, LOG, SQRT, ERFC, POWI}
 _BINARY = {ADD, SUB, MUL, DIV, MAX}
 
@@ -118,7 +119,7 @@ def _lib():
     lib = cg.lib()
     if not _declared:
         vp, i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
-        lib.cg_expr_compile.argtypes = [ctypes.POINTER(_Node), c_int, c_int, c_int, ctypes.POINTER(vp)]
+        lib.cg_expr_compile.argtypes = [ctypes.POINTER(_Node), c_int, c_int, c_int, c_int, ctypes.POINTER(vp)]
         lib.cg_expr_compile.restype = c_int
         lib.cg_expr_source.argtypes = [vp]
         lib.cg_expr_source.restype = ctypes.c_char_p
@@ -140,14 +141,15 @@ class Program:
     """Compiled expression program: objective = sum over the elements of the
     root expression, gradient with respect to theta[0 .. n_params)."""
 
-    def __init__(self, root, n_params, n_inputs):
+    def __init__(self, root, n_params, n_inputs, value_only=False):
         lib = _lib()
         self.node_list = nodes(_wrap(root))
         arr = (_Node * len(self.node_list))(*[_Node(*r) for r in self.node_list])
         h = ctypes.c_void_p()
-        rc = lib.cg_expr_compile(arr, len(self.node_list), n_params, n_inputs, ctypes.byref(h))
+        rc = lib.cg_expr_compile(arr, len(self.node_list), n_params, n_inputs, VALUE_ONLY if value_only else 0,
+                                 ctypes.byref(h))
         self._h = h
-        self.n_params, self.n_inputs = n_params, n_inputs
+        self.n_params, self.n_inputs, self.value_only = n_params, n_inputs, value_only
         if rc != cg.OK:
             log = lib.cg_expr_log(h).decode() if h.value else ""
             raise cg.CgError(rc, "cg_expr_compile: %s" % (log or "invalid or unsupported program"))
@@ -184,6 +186,8 @@ class Program:
 
     def gradient(self, inputs, thetas, values=None, grads=None, stream=None):
         """Values [H] and gradients [H, P] at the H rows of thetas."""
+        if self.value_only:
+            raise cg.CgError(cg.ERR_INVALID_ARG, "a value-only program has no gradient")
         H = thetas.shape[0]
         if values is None:
             values = torch.empty(H, dtype=torch.float64, device=thetas.device)
@@ -208,18 +212,18 @@ class Program:
                 pass
 
 
-def compile(root, n_params, n_inputs):
-    return Program(root, n_params, n_inputs)
+def compile(root, n_params, n_inputs, value_only=False):
+    return Program(root, n_params, n_inputs, value_only)
 
 
-def generated_source(root, n_params, n_inputs):
+def generated_source(root, n_params, n_inputs, value_only=False):
     """The CUDA source libcg generates for an expression (also where it cannot
     compile or run it, e.g. on a machine without a GPU)."""
     lib = _lib()
     nl = nodes(_wrap(root))
     arr = (_Node * len(nl))(*[_Node(*r) for r in nl])
     h = ctypes.c_void_p()
-    rc = lib.cg_expr_compile(arr, len(nl), n_params, n_inputs, ctypes.byref(h))
+    rc = lib.cg_expr_compile(arr, len(nl), n_params, n_inputs, VALUE_ONLY if value_only else 0, ctypes.byref(h))
     if not h.value:
         raise cg.CgError(rc, "cg_expr_compile rejected the program")
     try:

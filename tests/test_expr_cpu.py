@@ -91,7 +91,7 @@ def _compile_rc(nl, n_params, n_inputs):
     lib = E._lib()
     arr = (E._Node * len(nl))(*[E._Node(*r) for r in nl])
     h = ctypes.c_void_p()
-    return lib.cg_expr_compile(arr, len(nl), n_params, n_inputs, ctypes.byref(h))
+    return lib.cg_expr_compile(arr, len(nl), n_params, n_inputs, 0, ctypes.byref(h))
 
 
 def test_compile_rejects_malformed_programs_on_the_host():
@@ -118,3 +118,11 @@ def test_generated_source_hoists_the_parameter_only_part():
     loop = src[src.index("for (i64 e = e0"):src.index("for (int k = 0; k < NACC; ++k) {\n      const double w")]
     assert loop.count(" / ") == 1 and loop.count(" * r") >= 3
     assert "#define NACC 9" in src
+
+
+def test_value_only_source_has_no_reverse_sweep():
+    full = E.generated_source(mixture_nll(0.0, 10.0), 4, 1)
+    vo = E.generated_source(mixture_nll(0.0, 10.0), 4, 1, value_only=True)
+    assert "#define NACC 1" in vo and " g" not in vo.split("cgx_finalize")[0].split("acc[0] +=")[1]
+    assert "grad[" in full and "grad[" not in vo
+

@@ -79,3 +79,27 @@ def test_single_element_and_many_points(dev):
 def test_malformed_program_raises(dev):
     with pytest.raises(cg.CgError):
         E.compile(E.param(0) * 2.0, 1, 0)   # no element dependence
+
+
+def test_generated_eight_peaks_matches_the_oracle(dev):
+    """A program with 26 parameters (8 Gaussians + line): the sweep of the
+    Fig. 3b comparison uses such programs."""
+    K, n = 8, 20000
+    p = synth.random_gauss_poly(K, 1, n, seed=77)
+    x = (E.index() + 0.5) * (1.0 / n)
+    f = E.param(3 * K) + E.param(3 * K + 1) * x
+    for k in range(K):
+        f = f + E.param(3 * k) * E.exp(-(x - E.param(3 * k + 1)) ** 2 / (2.0 * E.param(3 * k + 2) ** 2))
+    y = E.inp(0)
+    root = (y - f) ** 2 / E.maximum(y, 1.0)
+    prog = E.compile(root, 3 * K + 2, 1)
+    th = np.stack([p["theta"], p["truth"] * 1.02])
+    _check(prog, E.nodes(root), 3 * K + 2, [p["y"]], th, dev)
+    vo = E.compile(root, 3 * K + 2, 1, value_only=True)
+    v = vo.objective([torch.tensor(p["y"], device=dev)], torch.tensor(th, device=dev)).cpu().numpy()
+    for h in range(2):
+        r = oracle.expr(E.nodes(root), 3 * K + 2, [p["y"]], th[h])
+        assert abs(v[h] - r.value) <= 1e-10 * abs(r.value)
+    with pytest.raises(cg.CgError):
+        vo.gradient([torch.tensor(p["y"], device=dev)], torch.tensor(th, device=dev))
+
