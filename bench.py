@@ -704,7 +704,7 @@ def run_c4(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2203_06139_gb300 import cg, synth
-    from paper_2203_06139_gb300.fit import BatchFitter, HistBatch, SingleFitter, autotune
+    from paper_2203_06139_gb300.fit import BatchFitter, HistBatch, LMFitter, SingleFitter, autotune
     d = synth.c4_batch()
     prec = cg.PREC_DF64 if args.prec == "df64" else cg.PREC_FP64
     b = HistBatch(d["y"], d["offsets"], d["lo"], d["hi"], 1, 2, cg.OBJ_CHI2, poly_mode=1, precision=prec)
@@ -718,6 +718,19 @@ def run_c4(args):
     Fb = f.states.f.cpu().numpy()
     stb = f.states.status.cpu().numpy()
     itb = f.states.iters.cpu().numpy()
+    # second-order fits (Levenberg-Marquardt on the Gauss-Newton matrix, df64
+    # batch): init + n_lm evaluations in one graph
+    n_lm = 30
+    b_lm = b if prec == cg.PREC_DF64 else HistBatch(d["y"], d["offsets"], d["lo"], d["hi"], 1, 2, cg.OBJ_CHI2,
+                                                    poly_mode=1, precision=cg.PREC_DF64)
+    flm = LMFitter(b_lm)
+    flm.capture(th0, n_steps=n_lm, tol=1e-9)
+    ms_lm = _timed(lambda: flm.replay(), max(1, min(args.steps, 5)), 2)
+    Fl = flm.states.f.cpu().numpy()
+    stl = flm.states.status.cpu().numpy()
+    itl = flm.states.iters.cpu().numpy()
+    nel = flm.states.n_eval.cpu().numpy()
+    same_lm = np.abs(Fl - Fb) <= 1e-6 * np.abs(Fb)
     # plain path: every histogram on its own, full-GPU launches per trial point
     n_plain = args.plain_hists or d["H"]
     idx = np.arange(d["H"]) if n_plain >= d["H"] else np.random.default_rng(0).choice(d["H"], n_plain, replace=False)
@@ -745,6 +758,13 @@ def run_c4(args):
             "dtype": "f64" if prec == cg.PREC_FP64 else "df64",
             "batched": {"converged": int((stb == cg.FIT_CONVERGED).sum()), "mean_iters": float(itb.mean()),
                         "ms": ms},
+            "levenberg_marquardt": {"ms": ms_lm, "evaluations": n_lm + 1, "dtype": "df64 (GN matrix FP32)",
+                                    "converged": int((stl == cg.FIT_CONVERGED).sum()),
+                                    "mean_iters": float(itl.mean()), "mean_evals": float(nel.mean()),
+                                    "status_counts": np.bincount(stl, minlength=5).tolist(),
+                                    "same_minimum_as_bfgs_frac": float(same_lm.mean()),
+                                    "lower_F_when_different": {"lm": int(((Fl < Fb) & ~same_lm).sum()),
+                                                               "bfgs": int(((Fb < Fl) & ~same_lm).sum())}},
             "plain_path": {"seconds_measured": t_plain, "histograms_measured": int(len(idx)),
                            "seconds_for_all": t_plain_full},
             "speedup_vs_plain": t_plain_full / (ms / 1e3),

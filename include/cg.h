@@ -357,6 +357,40 @@ cg_status cg_fit_init(const cg_batch *b, const cg_tile_map *map, const double *t
 cg_status cg_fit_step(const cg_batch *b, const cg_tile_map *map, cg_fit_state *state, int n_steps,
                       double tol, void *ws, size_t ws_bytes, void *stream);
 
+/* Gauss-Newton matrix of a batched binned fit (df64 batches only, else
+ * CG_ERR_UNSUPPORTED): for every histogram h, value[h], grad[h][P] and
+ * gn[h][P][P] (row-major, symmetric) at theta[h][P], with P = 3 n_peaks +
+ * poly_degree + 1.  GN = sum over bins of T''(f) (df/dtheta)(df/dtheta)^T,
+ * the Hessian of the objective with the model's own curvature dropped (the
+ * second derivatives Sec. 4 says the minimiser still takes by finite
+ * differences, here from the same reverse sweep); T'' = 2/max(y,1)
+ * for chi2, y/f^2 for Poisson, 2 y/f^2 for Baker-Cousins.  The products are
+ * accumulated in FP32 (relative error about 1e-6 of sqrt(GN_aa GN_bb)); the
+ * value and gradient are the df64 ones.  value[h] is NaN where the model
+ * leaves its domain or the histogram has 2^24 bins or more.  ws: >= 256
+ * bytes, 256-byte aligned (unused; reserved). */
+cg_status cg_batch_gn(const cg_batch *b, const double *theta, double *value, double *grad, double *gn,
+                      void *ws, size_t ws_bytes, void *stream);
+
+/* Levenberg-Marquardt fits of every histogram of a df64 batch, a second-order
+ * alternative to cg_fit_step: each step is one cg_batch_gn-style launch at the
+ * trial points plus a control kernel (one warp per histogram).  A trial is
+ * accepted when F(trial) < F; then lambda /= 10 (floor 1e-12), otherwise
+ * lambda *= 10 (CG_FIT_LINESEARCH_FAILED past 1e16); the next trial is
+ * theta + delta with (GN + lambda diag(GN)) delta = -g solved by Cholesky
+ * (diagonal entries <= 0 count as 1; a scaled gradient step where the matrix
+ * is not positive definite).  CG_FIT_CONVERGED when EDM = g^T GN^-1 g / 2 <
+ * tol max(1, |F|), GN the undamped matrix at theta.  state[h].hinv holds GN
+ * (not an inverse), h0[0] lambda; iter counts accepted steps, n_eval
+ * evaluations.  init evaluates theta0 [n_hist][P] (device) and sets lambda =
+ * 1e-3.  Capturable in a CUDA graph.  ws: cg_fit_lm_workspace_size bytes,
+ * 256-byte aligned. */
+size_t cg_fit_lm_workspace_size(const cg_batch *b);
+cg_status cg_fit_lm_init(const cg_batch *b, const double *theta0, cg_fit_state *state, double tol, void *ws,
+                         size_t ws_bytes, void *stream);
+cg_status cg_fit_lm_step(const cg_batch *b, cg_fit_state *state, int n_steps, double tol, void *ws,
+                         size_t ws_bytes, void *stream);
+
 /* The same iteration for ONE histogram on the full GPU (the plain
  * per-histogram path): every trial point is one cg_gradient-style launch
  * pair (tile kernel + finalize) followed by a one-warp control kernel; no

@@ -72,6 +72,7 @@ def _load():
     i64, c_int, c_d = ctypes.c_int64, ctypes.c_int, ctypes.c_double
     lib.orc_binned1d.argtypes = [c_int, c_int, c_int, c_int, i64, c_d, c_d, dp, dp, dp, dp, dp, dp]
     lib.orc_binned1d_gn.argtypes = [c_int, c_int, c_int, c_int, i64, c_d, c_d, dp, dp, dp, dp]
+    lib.orc_binned1d_gnmat.argtypes = [c_int, c_int, c_int, c_int, i64, c_d, c_d, dp, dp, dp, dp]
     lib.orc_gauss_poly_eval.argtypes = [c_int, c_int, c_int, c_d, c_d, i64, dp, dp, dp]
     lib.orc_unbinned_mix.argtypes = [i64, dp, dp, c_d, c_d, dp, dp, dp, dp]
     lib.orc_binned2d.argtypes = [c_int, i64, i64, c_d, c_d, c_d, c_d, dp, dp, dp, dp, dp]
@@ -79,7 +80,7 @@ def _load():
     ip = ctypes.POINTER(ctypes.c_int32)
     lib.orc_expr.argtypes = [c_int, ip, ip, ip, ip, dp, c_int, c_int, ctypes.POINTER(dp), i64, dp, dp, dp, dp]
     lib.orc_expr.restype = c_int
-    for f in (lib.orc_binned1d, lib.orc_binned1d_gn, lib.orc_gauss_poly_eval,
+    for f in (lib.orc_binned1d, lib.orc_binned1d_gn, lib.orc_binned1d_gnmat, lib.orc_gauss_poly_eval,
               lib.orc_unbinned_mix, lib.orc_binned2d, lib.orc_listing1_gauss):
         f.restype = c_int
     _lib = lib
@@ -135,6 +136,19 @@ def binned1d_gn(K, D, poly_mode, obj, y, lo, hi, theta, centres=None):
     gn = np.zeros(3 * K + D + 1)
     rc = lib.orc_binned1d_gn(K, D, poly_mode, obj, y.size, lo, hi, _p(centres), _p(y), _p(theta),
                              _p(gn))
+    assert rc == OK
+    return gn
+
+
+def binned1d_gnmat(K, D, poly_mode, obj, y, lo, hi, theta, centres=None):
+    """Gauss-Newton matrix sum_i h_i (df_i/dtheta_a)(df_i/dtheta_b) [P, P]."""
+    lib = _load()
+    y = _f64(y)
+    theta = _f64(theta)
+    centres = _f64(centres)
+    P = 3 * K + D + 1
+    gn = np.zeros((P, P))
+    rc = lib.orc_binned1d_gnmat(K, D, poly_mode, obj, y.size, lo, hi, _p(centres), _p(y), _p(theta), _p(gn))
     assert rc == OK
     return gn
 

@@ -331,6 +331,51 @@ int orc_binned1d(int K, int D, int poly_mode, int obj, int64_t n, double lo, dou
     return rc;
 }
 
+/* Gauss-Newton matrix of a 1-D binned objective:
+ *     GN_ab = sum_i h_i (d f_i / d theta_a) (d f_i / d theta_b),
+ * h_i as for the diagonal below.  It is the Hessian of the objective with
+ * the terms in the model's own second derivatives dropped; the second-order
+ * fit step (Levenberg-Marquardt) solves with it.  gn: P x P, row-major. */
+int orc_binned1d_gnmat(int K, int D, int poly_mode, int obj, int64_t n, double lo, double hi,
+                       const double *centres, const double *y, const double *theta, double *gn) {
+    int32_t P = 3 * K + D + 1;
+    tape T;
+    if (!tape_init(&T, 256)) return ORC_INVALID;
+    for (int32_t k = 0; k < P; ++k) t_var(&T, theta[k]);
+    int32_t mark = T.len;
+    double *adj = (double *)malloc(sizeof(double) * 256);
+    int32_t cap = 256;
+    nsum *acc = (nsum *)calloc((size_t)P * (size_t)P, sizeof(nsum));
+    double h = (hi - lo) / (double)n;
+    for (int64_t i = 0; i < n; ++i) {
+        double x = centres ? centres[i] : lo + ((double)i + 0.5) * h;
+        double u = (poly_mode == 1) ? (2.0 * x - lo - hi) / (hi - lo) : x;
+        int32_t f = rec_gauss_poly(&T, K, D, x, u);
+        if (cap < T.len) { while (cap < T.len) cap *= 2; adj = (double *)realloc(adj, sizeof(double) * (size_t)cap); }
+        for (int32_t j = 0; j < T.len; ++j) adj[j] = 0.0;
+        adj[f] = 1.0;
+        for (int32_t j = T.len - 1; j >= P; --j) {
+            const node *nd = &T.n[j];
+            if (nd->a >= 0) adj[nd->a] += adj[j] * nd->pa;
+            if (nd->b >= 0) adj[nd->b] += adj[j] * nd->pb;
+        }
+        double fv = T.n[f].v, hi_;
+        if (obj == OBJ_CHI2) hi_ = 2.0 / fmax(y[i], 1.0);
+        else if (obj == OBJ_POISSON) hi_ = (y[i] > 0.0) ? y[i] / (fv * fv) : 0.0;
+        else hi_ = (y[i] > 0.0) ? 2.0 * y[i] / (fv * fv) : 0.0;
+        for (int32_t a = 0; a < P; ++a)
+            for (int32_t b = a; b < P; ++b) nadd(&acc[(size_t)a * P + b], hi_ * adj[a] * adj[b]);
+        T.len = mark;
+    }
+    /* symmetric by definition: the upper triangle, mirrored */
+    for (int32_t a = 0; a < P; ++a)
+        for (int32_t b = 0; b < P; ++b) gn[(size_t)a * P + b] = nval(&acc[a <= b ? (size_t)a * P + b : (size_t)b * P + a]);
+    free(acc);
+    free(adj);
+    tape_free(&T);
+    return ORC_OK;
+}
+
 /* Model value f(x) of the 1-D family at explicit points (no objective). */
 int orc_gauss_poly_eval(int K, int D, int poly_mode, double lo, double hi, int64_t n,
                         const double *x, const double *theta, double *f_out) {

@@ -18,6 +18,22 @@ search.  The steps, in order, for one iteration:
   4. convergence when EDM = g.H.g / 2 < tol * max(1, |F|).
 The initial H is diag(1 / GN_k) with GN_k the Gauss-Newton diagonal of the
 objective (GN_k <= 0 gives 1).
+
+`lm_fit` is the second-order alternative: the minimiser handed the
+Gauss-Newton matrix GN = sum_i h_i J_i J_i^T (the second derivatives Sec. 4
+leaves to finite differences, here from the same adjoints) and damped as in
+Levenberg-Marquardt (Levenberg 1944, Marquardt 1963).  One evaluation:
+
+  1. at the trial point, F, g and GN; the trial is accepted when F(trial) < F
+     (then lambda /= 10, at least 1e-12), otherwise lambda *= 10 and the fit
+     fails once lambda > 1e16;
+  2. after an acceptance, EDM = g^T GN^-1 g / 2 with the undamped matrix;
+     converged when EDM < tol * max(1, |F|);
+  3. the next trial is theta + delta, (GN + lambda diag(GN)) delta = -g
+     (diagonal entries <= 0 count as 1); where the damped matrix is not
+     positive definite, delta_k = -g_k / ((1 + lambda) diag_k).
+The start evaluates theta0 with lambda = 1e-3 and checks EDM before the
+first step.
 """
 import numpy as np
 
@@ -78,3 +94,55 @@ def bfgs_fit(fg, gn, theta0, max_iter=50, tol=1e-9, max_trials=20, c1=1e-4):
     if status == RUNNING:
         status = MAX_ITER
     return dict(theta=theta, F=F, g=g, iters=it, evals=evals, status=status, edm=edm)
+
+
+def _chol_solve(M, b):
+    """Solution of M x = b by Cholesky, or None where M is not positive definite."""
+    try:
+        L = np.linalg.cholesky(M)
+    except np.linalg.LinAlgError:
+        return None
+    return np.linalg.solve(L.T, np.linalg.solve(L, b))
+
+
+def _edm(g, G):
+    z = _chol_solve(G, g)
+    if z is None:
+        dg = np.diag(G)
+        z = g / np.where(dg > 0, dg, 1.0)
+    return 0.5 * g @ z
+
+
+def lm_fit(fgh, theta0, max_evals=60, tol=1e-9, lam0=1e-3):
+    """Minimise F with callback fgh(theta) -> (F, g, GN).  Returns
+    dict(theta, F, g, iters, evals, status, edm, lam)."""
+    theta = np.array(theta0, dtype=np.float64)
+    F, g, G = fgh(theta)
+    evals, it, lam = 1, 0, lam0
+    status = RUNNING if np.isfinite(F) else 4
+    edm = 0.0
+    if status == RUNNING:
+        edm = _edm(g, G)
+        if edm < tol * max(1.0, abs(F)):
+            status = CONVERGED
+    while status == RUNNING and evals < max_evals:
+        dg = np.diag(G)
+        dpos = np.where(dg > 0, dg, 1.0)
+        delta = _chol_solve(G + lam * np.diag(dpos), -g)
+        if delta is None:
+            delta = -g / ((1.0 + lam) * dpos)
+        tt = theta + delta
+        Ft, gt, Gt = fgh(tt)
+        evals += 1
+        if np.isfinite(Ft) and Ft < F:
+            theta, F, g, G = tt, Ft, gt, Gt
+            it += 1
+            lam = max(lam * 0.1, 1e-12)
+            edm = _edm(g, G)
+            if edm < tol * max(1.0, abs(F)):
+                status = CONVERGED
+        else:
+            lam *= 10.0
+            if lam > 1e16:
+                status = LINESEARCH_FAILED
+    return dict(theta=theta, F=F, g=g, iters=it, evals=evals, status=status, edm=edm, lam=lam)

@@ -92,6 +92,10 @@ def lib():
         "cg_fit_init": (ctypes.c_int, [B, ctypes.POINTER(_TileMap), _dp, _vp, _vp, _sz, _vp]),
         "cg_fit_step": (ctypes.c_int, [B, ctypes.POINTER(_TileMap), _vp, ctypes.c_int, ctypes.c_double, _vp, _sz,
                                        _vp]),
+        "cg_batch_gn": (ctypes.c_int, [B, _dp, _dp, _dp, _dp, _vp, _sz, _vp]),
+        "cg_fit_lm_workspace_size": (_sz, [B]),
+        "cg_fit_lm_init": (ctypes.c_int, [B, _dp, _vp, ctypes.c_double, _vp, _sz, _vp]),
+        "cg_fit_lm_step": (ctypes.c_int, [B, _vp, ctypes.c_int, ctypes.c_double, _vp, _sz, _vp]),
         "cg_fit_single_workspace_size": (_sz, [P]),
         "cg_fit_single_init": (ctypes.c_int, [P, _dp, _vp, _vp, _sz, _vp]),
         "cg_fit_single_step": (ctypes.c_int, [P, _vp, ctypes.c_int, ctypes.c_double, _vp, _sz, _vp]),

@@ -72,6 +72,7 @@ struct FitArgs {
     const double* theta;   // grad mode: [H][P]; init mode: theta0 [H][P]
     double* value;         // grad mode
     double* grad;          // grad mode
+    double* gn;            // mode 4: Gauss-Newton matrices [H][P][P]
     const int* queue[3];   // histogram ids per unit kind (cluster, cta, warp), sorted by size
     const int* n_items;    // device [3]: queue lengths (written by the plan)
     int* counters;         // 3 ints, zeroed before each persistent launch
@@ -173,17 +174,62 @@ static __device__ __noinline__ void gp1_fallback_fp64(double x, double y, const 
     *bad = b ? 1 : 0;
 }
 
+// Gauss-Newton matrix factors of one bin in FP64, for the bins the df64
+// element hands to the FP64 fallback: q = the raw factors r (as in the df64
+// element) divided by f for the Poisson forms, and hs with h r_a r_b =
+// hs q_a q_b (2w for chi2, y for Poisson, 2y for Baker-Cousins; 0 for an empty
+// Poisson bin).
+template <int K, int OBJ>
+static __device__ __noinline__ void gnm_fallback_fp64(double x, double y, const GP1Consts& cs, GP1Data dd,
+                                                      double* q, double* hs) {
+    constexpr int R = GP1Gnm<K>::R;
+    const double u = dd.pm ? fma(x, dd.au, dd.bu) : x;
+    double f = 0.0;
+    for (int j = 3; j >= 0; --j) {
+        if (j == dd.D) f = cs.poly[j];
+        else if (j < dd.D) f = fma(f, u, cs.poly[j]);
+    }
+    double dk[K], ek[K];
+    for (int k = 0; k < K; ++k) {
+        dk[k] = x - cs.mu[k];
+        ek[k] = exp(cs.c[k] * dk[k] * dk[k]);
+        f = fma(cs.A[k], ek[k], f);
+    }
+    double sc = 1.0;
+    if (OBJ == CG_OBJ_CHI2) {
+        *hs = 2.0 / fmax(y, 1.0);
+    } else {
+        *hs = (y > 0.0) ? (OBJ == CG_OBJ_POISSON ? y : 2.0 * y) : 0.0;
+        sc = (y > 0.0) ? 1.0 / f : 0.0;
+    }
+    for (int k = 0; k < K; ++k) {
+        const double e = ek[k] * sc;
+        q[3 * k] = e;
+        q[3 * k + 1] = e * dk[k];
+        q[3 * k + 2] = e * dk[k] * dk[k];
+    }
+    double up = sc;
+    for (int j = 0; j < 4; ++j) {
+        q[3 * K + j] = (j <= dd.D) ? up : 0.0;
+        up *= u;
+    }
+    (void)R;
+}
+
 // The same in double-float arithmetic (FP32 pipe): every kFitFlush bins the
 // compensated accumulators are folded into the df64 running sums run[]
 // (zeroed here), which leave the thread as df64 and are converted to FP64
 // once per warp by the reductions; elements that need it are evaluated in
 // FP64 and folded into the same running sums.  GN: also the Gauss-Newton
-// diagonal terms, into grun[].  VO: the value term only (run[0]).
+// diagonal terms, into grun[].  VO: the value term only (run[0]).  GNM: the
+// Gauss-Newton matrix terms in FP32 into gm (elements that fall back to FP64
+// take their terms in FP64 and add them rounded to FP32).
 // Requires G.n < kDfMaxBins (bin index and centre exact in FP32 / df64).
-template <int K, int OBJ, bool GN, bool VO = false>
+template <int K, int OBJ, bool GN, bool VO = false, bool GNM = false>
 __device__ __forceinline__ void acc_bins_df64(const Geom& G, const GP1Consts& cs, const GP1Df& cd,
                                               const GP1Data& dd, const DfTables& tab, int t0, int T,
-                                              df (&run)[GP1Acc<K>::N], df (&grun)[GP1Acc<K>::N], bool& bad) {
+                                              df (&run)[GP1Acc<K>::N], df (&grun)[GP1Acc<K>::N], bool& bad,
+                                              float* gm = nullptr) {
     constexpr int N = GP1Acc<K>::N;
     constexpr int NG = GN ? N : 1;
     DfAcc da[N], ga[NG];
@@ -203,7 +249,7 @@ __device__ __forceinline__ void acc_bins_df64(const Geom& G, const GP1Consts& cs
     int cnt = 0;
     for (int i = t0; i < n; i += T, fi += fT) {
         const double y = __ldg(G.y + i);
-        if (!gp1_elem_df64<K, OBJ, VO, GN>(gp1_centre_df(cd, fi), y, cd, dd.D, dd.pm, da, tab, ga)) {
+        if (!gp1_elem_df64<K, OBJ, VO, GN, GNM>(gp1_centre_df(cd, fi), y, cd, dd.D, dd.pm, da, tab, ga, gm)) {
             double t[2 * N];
             int b = 0;
             gp1_fallback_fp64<K, OBJ, GN>(fma((double)i + 0.5, G.hw, G.lo), y, cs, dd, t, &b);
@@ -213,6 +259,21 @@ __device__ __forceinline__ void acc_bins_df64(const Geom& G, const GP1Consts& cs
             if (GN) {
 #pragma unroll
                 for (int a = 1; a < NG; ++a) grun[a] = df_add(grun[a], df_from_double(t[N + a]));
+            }
+            if constexpr (GNM) {
+                constexpr int R = GP1Gnm<K>::R;
+                double q[R], hs;
+                gnm_fallback_fp64<K, OBJ>(fma((double)i + 0.5, G.hw, G.lo), y, cs, dd, q, &hs);
+                int p = 0;
+#pragma unroll
+                for (int a2 = 0; a2 < R; ++a2) {
+                    const double ha = hs * q[a2];
+#pragma unroll
+                    for (int b2 = a2; b2 < R; ++b2) {
+                        gm[p] += (float)(ha * q[b2]);
+                        ++p;
+                    }
+                }
             }
         }
         if (++cnt == kFitFlush) {
@@ -251,6 +312,21 @@ __device__ __forceinline__ void warp_totals(const double (&acc)[N], double* dst,
 template <int N>
 __device__ __forceinline__ void warp_totals(const df (&acc)[N], double* dst, int stride) {
     warp_sum_df_to<N>(acc, dst, stride);
+}
+
+// Warp totals of NV FP32 accumulators (chunks of 32 values through the df64
+// reduce-scatter; exact FP32 inputs), one FP64 value per accumulator.
+template <int NV>
+__device__ __forceinline__ void warp_totals_f(const float (&v)[NV], double* dst, int stride) {
+    constexpr int NC = (NV + 31) / 32;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        constexpr int W = 32;
+        df w[W];
+#pragma unroll
+        for (int i = 0; i < W; ++i) w[i] = df_make((c * W + i < NV) ? v[(c * W + i < NV) ? c * W + i : 0] : 0.0f, 0.0f);
+        warp_sum_df_to<W>(w, dst + (size_t)c * W * stride, stride);
+    }
 }
 
 template <int N, typename T>
@@ -645,11 +721,16 @@ __global__ void __launch_bounds__(512) k_fit_persistent(FitArgs a) {
 
 // Init (GN + first evaluation) and plain evaluation: one CTA per histogram,
 // grid-stride over histograms.  mode 0: value/grad at a.theta; mode 1: init;
-// mode 2: value only.
+// mode 2: value only; mode 4: value, gradient and the full Gauss-Newton
+// matrix (df64 only; with a.st set, rows of stride FP and only RUNNING fits).
 template <int K, int OBJ, int PREC, int MODE>
 __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
     constexpr int mode = MODE;
     constexpr int N = GP1Acc<K>::N;
+    constexpr int NV = GP1Gnm<K>::NV, R = GP1Gnm<K>::R;
+    // warp_totals_f writes whole chunks of 32 accumulators (the tail past NV is zero)
+    __shared__ double gmred[(MODE == 4 ? (NV + 31) / 32 * 32 : 1) * kMaxWarpsPerCta];
+    __shared__ double gmtot[MODE == 4 ? NV : 1];
     __shared__ GP1Consts cs;
     __shared__ GP1Df cd;
     __shared__ DfTables tab;
@@ -662,7 +743,8 @@ __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
     __shared__ double tot[N + 1];
     __shared__ double gn[N + 1];
     for (int64_t h = blockIdx.x; h < a.H; h += gridDim.x) {
-        const double* th = a.theta + h * a.P;
+        if (MODE == 4 && a.st && a.st[h].status != CG_FIT_RUNNING) continue;   // uniform per block
+        const double* th = a.theta + h * (MODE == 4 && a.st ? (int64_t)FP : (int64_t)a.P);
         const Geom G = geom_of(a, h);
         GP1Data dd;
         dd.y = G.y;
@@ -681,11 +763,31 @@ __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
         __syncthreads();
         bool bad = false;
         int any_bad;
+        if (MODE == 4 && !(PREC == CG_PREC_DF64 && G.n < kDfMaxBins)) {
+            // the Gauss-Newton matrix is taken on the df64 path only
+            if (threadIdx.x == 0) a.value[h] = __longlong_as_double(0x7ff8000000000000LL);
+            __syncthreads();
+            continue;
+        }
         if (PREC == CG_PREC_DF64 && G.n < kDfMaxBins) {
             // mode 1: gradient and Gauss-Newton terms in one sweep over the bins
             df v[N], gv[N];
-            acc_bins_df64<K, OBJ, MODE == 1, MODE == 2>(G, cs, cd, dd, tab, threadIdx.x, blockDim.x, v, gv, bad);
+            float gm[MODE == 4 ? NV : 1];
+#pragma unroll
+            for (int i = 0; i < (MODE == 4 ? NV : 1); ++i) gm[i] = 0.0f;
+            acc_bins_df64<K, OBJ, MODE == 1, MODE == 2, MODE == 4>(G, cs, cd, dd, tab, threadIdx.x, blockDim.x, v,
+                                                                  gv, bad, gm);
             any_bad = __syncthreads_or(bad) | cs_bad;
+            if constexpr (MODE == 4) {
+                warp_totals_f<NV>(gm, gmred + (threadIdx.x >> 5), kMaxWarpsPerCta);
+                __syncthreads();
+                for (int i = threadIdx.x; i < NV; i += blockDim.x) {
+                    double sum = 0.0;
+                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += gmred[i * kMaxWarpsPerCta + w];
+                    gmtot[i] = sum;
+                }
+                __syncthreads();
+            }
             if constexpr (MODE == 2) {
                 const df v0[1] = {v[0]};
                 reduce_cta<1, df>(v0, red, tot);
@@ -718,6 +820,30 @@ __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
             double g[kMaxParams];
             if (mode == 2) {
                 a.value[h] = any_bad ? __longlong_as_double(0x7ff8000000000000LL) : tot[0];
+            } else if (mode == 4) {
+                // value, gradient and GN = D (sum h r r^T) D with the per-point scales D
+                const double v = epilogue(ep, th, tot, g);
+                a.value[h] = any_bad ? __longlong_as_double(0x7ff8000000000000LL) : v;
+                const int P = a.P;
+                const int gs = a.st ? FP : P;
+                for (int k = 0; k < P; ++k) a.grad[h * gs + k] = g[k];
+                double dsc[FP];
+                for (int k = 0; k < P; ++k) {
+                    dsc[k] = 1.0;
+                    if (k < 3 * K) {
+                        const int pk = k / 3, role = k - 3 * pk;
+                        const double A = th[3 * pk], sg = th[3 * pk + 2];
+                        if (role == 1) dsc[k] = A / (sg * sg);
+                        if (role == 2) dsc[k] = A / (sg * sg * sg);
+                    }
+                }
+                const int gm_s = a.st ? FP : P;
+                for (int i = 0; i < P; ++i)
+                    for (int j = 0; j < P; ++j) {
+                        const int lo_ = i < j ? i : j, hi_ = i < j ? j : i;
+                        const double raw = gmtot[lo_ * R - lo_ * (lo_ - 1) / 2 + (hi_ - lo_)];
+                        a.gn[(h * gm_s + i) * gm_s + j] = dsc[i] * dsc[j] * raw;
+                    }
             } else if (mode == 0) {
                 const double v = epilogue(ep, th, tot, g);
                 a.value[h] = v;
@@ -755,6 +881,148 @@ __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
         }
         __syncthreads();
     }
+}
+
+// ---------------------------------------------------------------------------
+// Levenberg-Marquardt fits: the (value, gradient, Gauss-Newton matrix)
+// evaluation of k_fit_eval mode 4 at the trial points, then this control
+// kernel, one warp per histogram.  State reuse: hinv holds the Gauss-Newton
+// matrix GN at theta, h0[0] the damping lambda.  One step: accept the trial
+// when F(trial) < F (theta, F, g, GN move there, lambda / 10, iteration + 1,
+// EDM = g^T GN^-1 g / 2 with the undamped matrix; converged when EDM < tol
+// max(1, |F|)), otherwise lambda x 10 (CG_FIT_LINESEARCH_FAILED past 1e16);
+// then the next trial theta + delta, (GN + lambda diag(GN)) delta = -g by
+// Cholesky (diag(GN) entries <= 0 count as 1).
+// ---------------------------------------------------------------------------
+struct LmArgs {
+    cg_fit_state* st;
+    double* th_trial;        // [H][FP]
+    const double* f_trial;   // [H]
+    const double* g_trial;   // [H][FP]
+    const double* gn_trial;  // [H][FP][FP]
+    int64_t H;
+    double tol;
+    int first;               // 1: the trial holds the start point's evaluation
+};
+
+// Solve (M) x = b for symmetric positive definite M (P x P, row stride FP) by
+// Cholesky in place on a copy; false when M is not positive definite.
+__device__ bool chol_solve(const double* M, const double* b, int P, double* x) {
+    double L[FP * FP];
+    for (int i = 0; i < P; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double sum = M[i * FP + j];
+            for (int k = 0; k < j; ++k) sum -= L[i * FP + k] * L[j * FP + k];
+            if (i == j) {
+                if (!(sum > 0.0)) return false;
+                L[i * FP + i] = sqrt(sum);
+            } else {
+                L[i * FP + j] = sum / L[j * FP + j];
+            }
+        }
+    double y[FP];
+    for (int i = 0; i < P; ++i) {
+        double sum = b[i];
+        for (int k = 0; k < i; ++k) sum -= L[i * FP + k] * y[k];
+        y[i] = sum / L[i * FP + i];
+    }
+    for (int i = P - 1; i >= 0; --i) {
+        double sum = y[i];
+        for (int k = i + 1; k < P; ++k) sum -= L[k * FP + i] * x[k];
+        x[i] = sum / L[i * FP + i];
+    }
+    return true;
+}
+
+// The evaluation writes the leading P x P block of each FP x FP matrix only.
+__device__ void lm_copy_gn(double* dst, const double* src, int P) {
+    for (int i = 0; i < FP; ++i)
+        for (int j = 0; j < FP; ++j) dst[i * FP + j] = (i < P && j < P) ? src[i * FP + j] : 0.0;
+}
+
+__global__ void k_lm_reset(cg_fit_state* st, int64_t H, int P) {
+    const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= H) return;
+    st[h].status = CG_FIT_RUNNING;
+    st[h].n_params = P;
+}
+
+__global__ void k_lm_control(LmArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t h = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (h >= a.H || lane != 0) return;
+    cg_fit_state& s = a.st[h];
+    const int P = s.n_params;
+    const double* gt = a.g_trial + h * FP;
+    const double* Gt = a.gn_trial + h * FP * FP;
+    double* tt = a.th_trial + h * FP;
+    const double ft = a.f_trial[h];
+    if (a.first) {
+        for (int k = 0; k < FP; ++k) {
+            s.theta[k] = k < P ? tt[k] : 0.0;
+            s.grad[k] = k < P ? gt[k] : 0.0;
+            s.h0[k] = 0.0;
+        }
+        lm_copy_gn(s.hinv, Gt, P);
+        s.f = ft;
+        s.iter = 0;
+        s.n_eval = 1;
+        s.h0[0] = 1e-3;
+        s.status = isfinite(ft) ? CG_FIT_RUNNING : CG_FIT_DOMAIN;
+        s.edm = 0.0;
+        if (s.status == CG_FIT_RUNNING) {
+            double z[FP];
+            if (chol_solve(s.hinv, s.grad, P, z)) {
+                double e = 0.0;
+                for (int k = 0; k < P; ++k) e += s.grad[k] * z[k];
+                s.edm = 0.5 * e;
+            } else {
+                double e = 0.0;
+                for (int k = 0; k < P; ++k) e += s.grad[k] * s.grad[k] / (s.hinv[k * FP + k] > 0.0 ? s.hinv[k * FP + k] : 1.0);
+                s.edm = 0.5 * e;
+            }
+            if (s.edm < a.tol * fmax(1.0, fabs(s.f))) s.status = CG_FIT_CONVERGED;
+        }
+    } else {
+        if (s.status != CG_FIT_RUNNING) return;
+        s.n_eval += 1;
+        if (isfinite(ft) && ft < s.f) {
+            for (int k = 0; k < P; ++k) {
+                s.theta[k] = tt[k];
+                s.grad[k] = gt[k];
+            }
+            lm_copy_gn(s.hinv, Gt, P);
+            s.f = ft;
+            s.iter += 1;
+            s.h0[0] = fmax(s.h0[0] * 0.1, 1e-12);
+            double z[FP];
+            double e = 0.0;
+            if (chol_solve(s.hinv, s.grad, P, z)) {
+                for (int k = 0; k < P; ++k) e += s.grad[k] * z[k];
+            } else {
+                for (int k = 0; k < P; ++k) e += s.grad[k] * s.grad[k] / (s.hinv[k * FP + k] > 0.0 ? s.hinv[k * FP + k] : 1.0);
+            }
+            s.edm = 0.5 * e;
+            if (s.edm < a.tol * fmax(1.0, fabs(s.f))) s.status = CG_FIT_CONVERGED;
+        } else {
+            s.h0[0] *= 10.0;
+            if (s.h0[0] > 1e16) s.status = CG_FIT_LINESEARCH_FAILED;
+        }
+    }
+    if (s.status != CG_FIT_RUNNING) return;
+    // next trial point
+    double M[FP * FP], b[FP], d[FP];
+    const double lam = s.h0[0];
+    for (int i = 0; i < P; ++i) {
+        for (int j = 0; j < P; ++j) M[i * FP + j] = s.hinv[i * FP + j];
+        const double dg = s.hinv[i * FP + i] > 0.0 ? s.hinv[i * FP + i] : 1.0;
+        M[i * FP + i] += lam * dg;
+        b[i] = -s.grad[i];
+    }
+    if (!chol_solve(M, b, P, d)) {   // not positive definite: a scaled gradient step
+        for (int i = 0; i < P; ++i) d[i] = b[i] / ((1.0 + lam) * (s.hinv[i * FP + i] > 0.0 ? s.hinv[i * FP + i] : 1.0));
+    }
+    for (int k = 0; k < FP; ++k) tt[k] = k < P ? s.theta[k] + d[k] : 0.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -877,6 +1145,9 @@ cg_status launch_eval_k(const FitArgs& a, int mode, int prec, cudaStream_t st) {
     } else if (mode == 2) {
         if (df) k_fit_eval<K, OBJ, CG_PREC_DF64, 2><<<grid, 256, 0, st>>>(a);
         else k_fit_eval<K, OBJ, CG_PREC_FP64, 2><<<grid, 256, 0, st>>>(a);
+    } else if (mode == 4) {
+        if (!df) return CG_ERR_UNSUPPORTED;
+        k_fit_eval<K, OBJ, CG_PREC_DF64, 4><<<grid, 256, 0, st>>>(a);
     } else {
         if (df) k_fit_eval<K, OBJ, CG_PREC_DF64, 1><<<grid, 256, 0, st>>>(a);
         else k_fit_eval<K, OBJ, CG_PREC_FP64, 1><<<grid, 256, 0, st>>>(a);
@@ -996,6 +1267,111 @@ cg_status cg_batch_gradient(const cg_batch* b, const double* theta, double* valu
     a.value = value;
     a.grad = grad;
     return launch_eval(&b->tmpl, a, grad ? 0 : 2, st);   // grad == NULL: values only
+}
+
+// Levenberg-Marquardt workspace: trial parameters, values, gradients, GN matrices.
+struct LmWs {
+    size_t th, f, g, gn, total;
+};
+static LmWs lm_ws_layout(int64_t H) {
+    LmWs L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o += align_up(bytes, 256); return r; };
+    L.th = take(sizeof(double) * (size_t)H * FP);
+    L.f = take(sizeof(double) * (size_t)H);
+    L.g = take(sizeof(double) * (size_t)H * FP);
+    L.gn = take(sizeof(double) * (size_t)H * FP * FP);
+    L.total = o;
+    return L;
+}
+
+size_t cg_fit_lm_workspace_size(const cg_batch* b) {
+    if (!b || b->n_hist < 1 || !b->offsets || !fit_supported(&b->tmpl)) return 0;
+    return lm_ws_layout(b->n_hist).total;
+}
+
+cg_status cg_batch_gn(const cg_batch* b, const double* theta, double* value, double* grad, double* gn, void* ws,
+                      size_t ws_bytes, void* stream) {
+    if (!b || b->n_hist < 1 || !b->offsets || !theta || !value || !grad || !gn || !b->lo || !b->hi ||
+        !b->tmpl.data)
+        return CG_ERR_INVALID_ARG;
+    if (!fit_supported(&b->tmpl)) return CG_ERR_UNSUPPORTED;
+    if (b->tmpl.precision != CG_PREC_DF64) return CG_ERR_UNSUPPORTED;
+    if (!ws || ((uintptr_t)ws & 255) || ws_bytes < 256) return CG_ERR_WORKSPACE;
+    FitArgs a = base_args(b);
+    a.theta = theta;
+    a.value = value;
+    a.grad = grad;
+    a.gn = gn;
+    return launch_eval(&b->tmpl, a, 4, (cudaStream_t)stream);
+}
+
+static cg_status lm_launch_control(const cg_batch* b, cg_fit_state* state, double tol, char* base, int first,
+                                   cudaStream_t st) {
+    const LmWs L = lm_ws_layout(b->n_hist);
+    LmArgs la;
+    la.st = state;
+    la.th_trial = (double*)(base + L.th);
+    la.f_trial = (const double*)(base + L.f);
+    la.g_trial = (const double*)(base + L.g);
+    la.gn_trial = (const double*)(base + L.gn);
+    la.H = b->n_hist;
+    la.tol = tol;
+    la.first = first;
+    const int per_block = 4;
+    k_lm_control<<<(unsigned)((b->n_hist + per_block - 1) / per_block), 32 * per_block, 0, st>>>(la);
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
+
+static cg_status lm_eval(const cg_batch* b, cg_fit_state* state, char* base, cudaStream_t st) {
+    const LmWs L = lm_ws_layout(b->n_hist);
+    FitArgs a = base_args(b);
+    a.st = state;
+    a.theta = (const double*)(base + L.th);
+    a.value = (double*)(base + L.f);
+    a.grad = (double*)(base + L.g);
+    a.gn = (double*)(base + L.gn);
+    return launch_eval(&b->tmpl, a, 4, st);
+}
+
+cg_status cg_fit_lm_init(const cg_batch* b, const double* theta0, cg_fit_state* state, double tol, void* ws,
+                         size_t ws_bytes, void* stream) {
+    if (!b || b->n_hist < 1 || !b->offsets || !theta0 || !state || !(tol >= 0.0)) return CG_ERR_INVALID_ARG;
+    if (!fit_supported(&b->tmpl)) return CG_ERR_UNSUPPORTED;
+    if (b->tmpl.precision != CG_PREC_DF64) return CG_ERR_UNSUPPORTED;
+    const LmWs L = lm_ws_layout(b->n_hist);
+    if (!ws || ((uintptr_t)ws & 255) || ws_bytes < L.total) return CG_ERR_WORKSPACE;
+    char* base = (char*)ws;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the start points into the trial buffer (row stride FP), statuses RUNNING
+    const int P = 3 * b->tmpl.n_peaks + b->tmpl.poly_degree + 1;
+    if (cudaMemsetAsync(base + L.th, 0, sizeof(double) * (size_t)b->n_hist * FP, st) != cudaSuccess ||
+        cudaMemcpy2DAsync(base + L.th, sizeof(double) * FP, theta0, sizeof(double) * P, sizeof(double) * P,
+                          (size_t)b->n_hist, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return CG_ERR_CUDA;
+    k_lm_reset<<<(unsigned)((b->n_hist + 255) / 256), 256, 0, st>>>(state, b->n_hist, P);
+    if (cudaGetLastError() != cudaSuccess) return CG_ERR_CUDA;
+    cg_status s = lm_eval(b, state, base, st);
+    if (s != CG_OK) return s;
+    return lm_launch_control(b, state, tol, base, 1, st);
+}
+
+cg_status cg_fit_lm_step(const cg_batch* b, cg_fit_state* state, int n_steps, double tol, void* ws, size_t ws_bytes,
+                         void* stream) {
+    if (!b || b->n_hist < 1 || !b->offsets || !state || n_steps < 0 || !(tol >= 0.0)) return CG_ERR_INVALID_ARG;
+    if (!fit_supported(&b->tmpl)) return CG_ERR_UNSUPPORTED;
+    if (b->tmpl.precision != CG_PREC_DF64) return CG_ERR_UNSUPPORTED;
+    const LmWs L = lm_ws_layout(b->n_hist);
+    if (!ws || ((uintptr_t)ws & 255) || ws_bytes < L.total) return CG_ERR_WORKSPACE;
+    char* base = (char*)ws;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < n_steps; ++i) {
+        cg_status s = lm_eval(b, state, base, st);
+        if (s != CG_OK) return s;
+        s = lm_launch_control(b, state, tol, base, 0, st);
+        if (s != CG_OK) return s;
+    }
+    return CG_OK;
 }
 
 size_t cg_fit_workspace_size(const cg_batch* b) {

@@ -104,10 +104,22 @@ __device__ __forceinline__ df gp1_centre_df(const GP1Df& c, int64_t i) { return 
 // GN: also accumulate the Gauss-Newton diagonal terms h (df/dtheta)^2, with
 // h = d2T/df2, into gacc (same slots as the gradient accumulators; slot 0 is
 // unused) -- the terms the fitter's initial inverse Hessian is built from.
-template <int K, int OBJ, bool VO = false, bool GN = false>
+// GNM: also the Gauss-Newton matrix terms h r_a r_b (a <= b), in FP32, into
+// gm (packed upper triangle of the R = 3K + 4 raw Jacobian factors r =
+// (e_1, e_1 d_1, e_1 d_1^2, ..., u^0 .. u^3), entries past the degree zero):
+// d f/d theta_a = D_a r_a with the per-point scales D applied once after the
+// sums (1, A/s^2, A/s^3 per peak, 1 per polynomial term).  Empty bins of the
+// Poisson forms add nothing (h = 0).
+template <int K>
+struct GP1Gnm {
+    static constexpr int R = 3 * K + 4;
+    static constexpr int NV = R * (R + 1) / 2;
+};
+
+template <int K, int OBJ, bool VO = false, bool GN = false, bool GNM = false>
 __device__ __forceinline__ bool gp1_elem_df64(df X, double yd, const GP1Df& c, int D, int pm,
                                               DfAcc (&acc)[GP1Acc<K>::N], const DfTables& tab,
-                                              DfAcc* gacc = nullptr) {
+                                              DfAcc* gacc = nullptr, float* gm = nullptr) {
     const df u = pm ? df_add(df_mul(X, c.au), c.bu) : X;
     df f = df_make(0.0f, 0.0f);
 #pragma unroll
@@ -127,17 +139,19 @@ __device__ __forceinline__ bool gp1_elem_df64(df X, double yd, const GP1Df& c, i
     }
     const df y = df_split(yd);
     df T, g, hh;
+    float gsc = 1.0f;   // GNM: the factors r are taken as r / f for the Poisson forms
     if (OBJ == CG_OBJ_CHI2) {
         const df w = df_rcp(df_make(fmaxf(y.h, 1.0f), y.h >= 1.0f ? y.l : 0.0f));
         const df r = df_sub(y, f);
         const df wr = df_mul(w, r);
         T = df_mul(wr, r);
         g = df_make(-2.0f * wr.h, -2.0f * wr.l);
-        if (GN) hh = df_make(2.0f * w.h, 2.0f * w.l);
+        if (GN || GNM) hh = df_make(2.0f * w.h, 2.0f * w.l);
     } else {
         if (!(f.h > 1e-30f) || (fl && f.h < 1e-13f)) return false;
         const df rf = df_rcp(f);
         const df yr = df_mul(y, rf);
+        if (GNM) gsc = rf.h;
         if (OBJ == CG_OBJ_POISSON) {
             T = (y.h > 0.0f) ? df_sub(f, df_mul(y, df_log(f, tab))) : f;
             g = df_sub(df_make(1.0f, 0.0f), yr);
@@ -155,6 +169,36 @@ __device__ __forceinline__ bool gp1_elem_df64(df X, double yd, const GP1Df& c, i
     }
     dfacc_add(acc[0], T);
     if (VO) return true;
+    if (GNM) {
+        constexpr int R = GP1Gnm<K>::R;
+        float r[R];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float e = ek[k].h * gsc, ed = e * dk[k].h;
+            r[3 * k] = e;
+            r[3 * k + 1] = ed;
+            r[3 * k + 2] = ed * dk[k].h;
+        }
+        float up = gsc;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            r[3 * K + j] = (j <= D) ? up : 0.0f;
+            up *= u.h;
+        }
+        // h r_a r_b = 2w r_a r_b (chi2), y (r_a/f)(r_b/f) (Poisson), twice that (Baker-Cousins):
+        // no y/f^2 in FP32, whose range it can leave where a peak has no background under it
+        const float hf = (OBJ == CG_OBJ_CHI2) ? hh.h : (OBJ == CG_OBJ_POISSON ? y.h : 2.0f * y.h);
+        int q = 0;
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+            const float ha = hf * r[a];
+#pragma unroll
+            for (int b = a; b < R; ++b) {
+                gm[q] = fmaf(ha, r[b], gm[q]);
+                ++q;
+            }
+        }
+    }
     if (GN) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {

@@ -3,8 +3,8 @@
 that picks the warp / CTA / cluster mapping.
 
 Marshalling only: every evaluation, line search and BFGS update runs in the
-CUDA kernels of libcg (cg_fit_plan / cg_fit_init / cg_fit_step and the
-cg_fit_single_* calls).
+CUDA kernels of libcg (cg_fit_plan / cg_fit_init / cg_fit_step, the
+Levenberg-Marquardt cg_fit_lm_* calls and the cg_fit_single_* calls).
 """
 import ctypes
 import json
@@ -135,6 +135,81 @@ class HistBatch:
         cg._check(cg.lib().cg_batch_gradient(ctypes.byref(self.c), cg._ptr(thetas), cg._ptr(values), None,
                                              cg._ptr(ws), ws.numel(), cg._stream()), "cg_batch_gradient")
         return values
+
+
+    def gauss_newton(self, thetas, values=None, grads=None, gn=None):
+        """Value, gradient and Gauss-Newton matrix [H, P, P] of every histogram
+        (df64 batches)."""
+        thetas = cg._dev_f64(thetas, "thetas")
+        dev = self.y.device
+        if values is None:
+            values = torch.empty(self.H, dtype=torch.float64, device=dev)
+        if grads is None:
+            grads = torch.empty((self.H, self.P), dtype=torch.float64, device=dev)
+        if gn is None:
+            gn = torch.empty((self.H, self.P, self.P), dtype=torch.float64, device=dev)
+        ws = torch.empty(256, dtype=torch.uint8, device=dev)
+        cg._check(cg.lib().cg_batch_gn(ctypes.byref(self.c), cg._ptr(thetas), cg._ptr(values), cg._ptr(grads),
+                                       cg._ptr(gn), cg._ptr(ws), ws.numel(), cg._stream()), "cg_batch_gn")
+        return values, grads, gn
+
+
+class LMFitter:
+    """Levenberg-Marquardt fits of every histogram of a df64 HistBatch: each
+    step evaluates value, gradient and Gauss-Newton matrix at the trial points
+    and runs the damping / Cholesky control kernel (cg_fit_lm_init /
+    cg_fit_lm_step).  States as for BatchFitter; hinv holds the GN matrix."""
+
+    def __init__(self, batch):
+        self.b = batch
+        n = cg.lib().cg_fit_lm_workspace_size(ctypes.byref(batch.c))
+        if n == 0:
+            raise cg.CgError(cg.ERR_UNSUPPORTED, "batch not supported by the fitter")
+        self.ws = torch.empty(n, dtype=torch.uint8, device=batch.y.device)
+        self.states = None
+        self.graph = None
+
+    def _init_into(self, theta0, tol, stream=None):
+        cg._check(cg.lib().cg_fit_lm_init(ctypes.byref(self.b.c), cg._ptr(theta0), cg._ptr(self.states.raw),
+                                          float(tol), cg._ptr(self.ws), self.ws.numel(), cg._stream(stream)),
+                  "cg_fit_lm_init")
+
+    def init(self, theta0, tol=1e-9):
+        theta0 = cg._dev_f64(theta0, "theta0")
+        if self.states is None:
+            raw = torch.zeros((self.b.H, STATE_BYTES), dtype=torch.uint8, device=self.b.y.device)
+            self.states = States(raw, self.b.P)
+        self._init_into(theta0, tol)
+        return self.states
+
+    def _step_into(self, n_steps, tol, stream=None):
+        cg._check(cg.lib().cg_fit_lm_step(ctypes.byref(self.b.c), cg._ptr(self.states.raw), int(n_steps), float(tol),
+                                          cg._ptr(self.ws), self.ws.numel(), cg._stream(stream)), "cg_fit_lm_step")
+
+    def step(self, n_steps=30, tol=1e-9):
+        self._step_into(n_steps, tol)
+        return self.states
+
+    def capture(self, theta0, n_steps=30, tol=1e-9):
+        """Capture init + n_steps steps into a CUDA graph (theta0 is kept)."""
+        self._theta0 = cg._dev_f64(theta0, "theta0")
+        if self.states is None:
+            self.init(self._theta0, tol)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            g.capture_begin()
+            self._init_into(self._theta0, tol, s)
+            self._step_into(n_steps, tol, s)
+            g.capture_end()
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+        return self.states
 
 
 class BatchFitter:

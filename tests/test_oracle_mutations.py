@@ -44,6 +44,12 @@ MUTATIONS = {
     # polynomial in t: (2x - lo - hi)/(hi - lo) -> (x - lo)/(hi - lo)
     "poly_t_map": ("double u = (poly_mode == 1) ? (2.0 * x - lo - hi) / (hi - lo) : x;\n        int32_t f = rec_gauss_poly(&T, K, D, x, u);\n        int32_t t = rec_binned_term",
                    "double u = (poly_mode == 1) ? (x - lo) / (hi - lo) : x;\n        int32_t f = rec_gauss_poly(&T, K, D, x, u);\n        int32_t t = rec_binned_term"),
+    # Gauss-Newton matrix: J_a J_b -> J_a J_a (the diagonal's product everywhere)
+    "gnmat_transposed_factor": ("nadd(&acc[(size_t)a * P + b], hi_ * adj[a] * adj[b]);",
+                                "nadd(&acc[(size_t)a * P + b], hi_ * adj[a] * adj[a]);"),
+    # Gauss-Newton matrix: Poisson curvature y/f^2 -> y/f
+    "gnmat_poisson_curvature": ("else if (obj == OBJ_POISSON) hi_ = (y[i] > 0.0) ? y[i] / (fv * fv) : 0.0;\n        else hi_ = (y[i] > 0.0) ? 2.0 * y[i] / (fv * fv) : 0.0;\n        for (int32_t a",
+                                "else if (obj == OBJ_POISSON) hi_ = (y[i] > 0.0) ? y[i] / fv : 0.0;\n        else hi_ = (y[i] > 0.0) ? 2.0 * y[i] / (fv * fv) : 0.0;\n        for (int32_t a"),
     # compensated sum loses its correction
     "neumaier_dropped": ("static double nval(const nsum *acc) { return acc->s + acc->c; }",
                          "static double nval(const nsum *acc) { return acc->s; }"),

@@ -16,7 +16,7 @@ import pytest
 from scipy import integrate
 
 import oracle
-from oracle.fit import CONVERGED, bfgs_fit
+from oracle.fit import CONVERGED, bfgs_fit, lm_fit
 from paper_2203_06139_gb300 import synth
 from tests._metrics import max_rel_err
 
@@ -180,6 +180,65 @@ def test_gauss_newton_diagonal():
         hh = {oracle.CHI2: 2 / np.maximum(y, 1), oracle.POISSON: y / f ** 2,
               oracle.POISSON_BC: 2 * y / f ** 2}[obj]
         np.testing.assert_allclose(gn, (hh[None, :] * J ** 2).sum(1), rtol=1e-12)
+
+
+def _hand_jacobian(K, D, poly_mode, lo, hi, n, theta):
+    """f and df/dtheta [n, P] of the 1-D family from derivatives taken by hand."""
+    x = lo + (np.arange(n) + 0.5) * ((hi - lo) / n)
+    u = x if poly_mode == 0 else (2 * x - lo - hi) / (hi - lo)
+    P = 3 * K + D + 1
+    J = np.zeros((n, P))
+    f = np.zeros(n)
+    for k in range(K):
+        A, mu, s = theta[3 * k:3 * k + 3]
+        e = np.exp(-(x - mu) ** 2 / (2 * s * s))
+        f += A * e
+        J[:, 3 * k], J[:, 3 * k + 1], J[:, 3 * k + 2] = e, A * e * (x - mu) / s ** 2, A * e * (x - mu) ** 2 / s ** 3
+    for j in range(D + 1):
+        f += theta[3 * K + j] * u ** j
+        J[:, 3 * K + j] = u ** j
+    return f, J
+
+
+@pytest.mark.parametrize("K,D,pm", [(1, 2, 1), (2, 1, 0), (3, 1, 0), (1, -1, 0)])
+def test_gauss_newton_matrix_hand_jacobian(K, D, pm):
+    """GN_ab = sum_i h_i J_ia J_ib with J from the hand derivatives and h the
+    curvature of each bin term; symmetric, diagonal = the GN diagonal."""
+    p = synth.random_gauss_poly(K, D, 500, poly_mode=pm, seed=4 + K)
+    th, y = p["theta"], p["y"]
+    f, J = _hand_jacobian(K, D, pm, 0.0, 1.0, 500, th)
+    for obj in OBJS:
+        G = oracle.binned1d_gnmat(K, D, pm, obj, y, 0.0, 1.0, th)
+        fs = np.where(y > 0, f, 1.0)
+        hh = {oracle.CHI2: 2 / np.maximum(y, 1), oracle.POISSON: np.where(y > 0, y / fs ** 2, 0.0),
+              oracle.POISSON_BC: np.where(y > 0, 2 * y / fs ** 2, 0.0)}[obj]
+        ref = (J * hh[:, None]).T @ J
+        d = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
+        assert np.max(np.abs(G - ref) / d) <= 1e-12
+        assert np.array_equal(G, G.T)
+        np.testing.assert_allclose(np.diag(G), oracle.binned1d_gn(K, D, pm, obj, y, 0.0, 1.0, th), rtol=1e-13)
+
+
+@pytest.mark.parametrize("obj", OBJS)
+def test_gauss_newton_matrix_is_the_hessian_at_zero_residual(obj):
+    """Where y = f(theta) exactly (noise-free, non-integer counts) the dropped
+    term (dT/df) d2f/dtheta2 vanishes for all three objectives, so GN equals
+    the Hessian: central differences of the oracle's exact gradient."""
+    K, D, pm = 2, 1, 1
+    p = synth.random_gauss_poly(K, D, 800, poly_mode=pm, seed=9, noise=False)
+    th, y = p["truth"], p["y"]
+    G = oracle.binned1d_gnmat(K, D, pm, obj, y, 0.0, 1.0, th)
+    P = th.size
+    Hs = np.zeros((P, P))
+    for b in range(P):
+        h = 1e-5 * max(abs(th[b]), 1e-2)
+        tp, tm = th.copy(), th.copy()
+        tp[b] += h
+        tm[b] -= h
+        Hs[:, b] = (oracle.binned1d(K, D, pm, obj, y, 0.0, 1.0, tp).grad
+                    - oracle.binned1d(K, D, pm, obj, y, 0.0, 1.0, tm).grad) / (2 * h)
+    d = np.sqrt(np.outer(np.diag(G), np.diag(G)))
+    assert np.max(np.abs(G - Hs) / d) <= 1e-6
 
 
 def test_empty_bins_where_the_model_underflows():
@@ -376,6 +435,45 @@ def test_oracle_fit_reaches_lstsq_consistent_minimum():
     ndf = n - 5
     assert abs(res["F"] / ndf - 1) < 5 * math.sqrt(2 / ndf)
     assert abs(th[1] - 5.0) < 0.01
+
+
+def test_oracle_lm_solves_linear_least_squares():
+    """With no peak (K = 0) chi2 is linear least squares and GN its exact
+    Hessian: LM ends at numpy.linalg.lstsq's solution."""
+    n, D = 3000, 3
+    r = np.random.default_rng(2)
+    x = synth.uniform_centres(n, 0.0, 1.0)
+    u = 2 * x - 1
+    y = r.poisson(50 + 20 * u - 10 * u ** 2 + 5 * u ** 3).astype(float)
+    fgh = lambda t: (lambda q: (q.value, q.grad, oracle.binned1d_gnmat(0, D, 1, oracle.CHI2, y, 0.0, 1.0, t)))(
+        oracle.binned1d(0, D, 1, oracle.CHI2, y, 0.0, 1.0, t))
+    res = lm_fit(fgh, np.array([1.0, 0.0, 0.0, 0.0]), tol=1e-14)
+    assert res["status"] == CONVERGED
+    sw = np.sqrt(1 / np.maximum(y, 1))
+    X = np.stack([u ** j for j in range(D + 1)], 1)
+    coef = np.linalg.lstsq(X * sw[:, None], y * sw, rcond=None)[0]
+    chi2_min = np.sum(sw ** 2 * (y - X @ coef) ** 2)
+    # the stop rule bounds EDM (tol |F|), i.e. F - F_min, not the parameters directly
+    assert abs(res["F"] - chi2_min) <= 1e-12 * chi2_min
+    np.testing.assert_allclose(res["theta"], coef, rtol=1e-6, atol=1e-6 * np.abs(coef).max())
+
+
+@pytest.mark.parametrize("obj", OBJS)
+def test_oracle_lm_reaches_the_bfgs_minimum(obj):
+    """The second-order fit and the gradient-only fit end at the same minimum
+    (objective to 1e-9 relative), LM in fewer evaluations."""
+    p = synth.random_gauss_poly(1, 2, 2000, poly_mode=1, seed=12)
+    y = p["y"]
+    th0 = p["truth"] * np.array([1.1, 0.98, 1.15, 0.9, 1.1, 0.9])
+    fg = lambda t: (lambda q: (q.value, q.grad))(oracle.binned1d(1, 2, 1, obj, y, 0.0, 1.0, t))
+    gn = lambda t: oracle.binned1d_gn(1, 2, 1, obj, y, 0.0, 1.0, t)
+    fgh = lambda t: fg(t) + (oracle.binned1d_gnmat(1, 2, 1, obj, y, 0.0, 1.0, t),)
+    ref = bfgs_fit(fg, gn, th0, max_iter=400, tol=1e-14)
+    lm = lm_fit(fgh, th0, max_evals=200, tol=1e-14)
+    assert ref["status"] == CONVERGED and lm["status"] == CONVERGED
+    assert abs(lm["F"] - ref["F"]) <= 1e-9 * abs(ref["F"])
+    np.testing.assert_allclose(lm["theta"], ref["theta"], rtol=1e-5, atol=1e-6 * np.abs(ref["theta"]).max())
+    assert lm["evals"] < ref["evals"]
 
 
 def test_compensated_sum_of_identical_terms():
