@@ -331,8 +331,10 @@ size_t cg_fit_workspace_size(const cg_batch *b);
  * map->cta_max_bins bins go to the cluster queue (or the CTA queue when
  * cluster_size == 1), those with more than map->warp_max_bins to the CTA
  * queue, the rest to the warp queue; each queue is sorted by decreasing
- * size.  Uploaded into ws; this call synchronises `stream`.  Must precede
- * cg_fit_init / cg_fit_step on the same ws with the same map. */
+ * size.  Also stores every histogram by decreasing size, the order in which
+ * cg_fit_init's evaluation kernel takes them (one CTA per histogram from an
+ * atomic counter).  Uploaded into ws; this call synchronises `stream`.  Must
+ * precede cg_fit_init / cg_fit_step on the same ws with the same map. */
 cg_status cg_fit_plan(const cg_batch *b, const int64_t *host_offsets, const cg_tile_map *map,
                       void *ws, size_t ws_bytes, void *stream);
 
@@ -383,9 +385,21 @@ cg_status cg_batch_gn(const cg_batch *b, const double *theta, double *value, dou
  * tol max(1, |F|), GN the undamped matrix at theta.  state[h].hinv holds GN
  * (not an inverse), h0[0] lambda; iter counts accepted steps, n_eval
  * evaluations.  init evaluates theta0 [n_hist][P] (device) and sets lambda =
- * 1e-3.  Capturable in a CUDA graph.  ws: cg_fit_lm_workspace_size bytes,
- * 256-byte aligned. */
-size_t cg_fit_lm_workspace_size(const cg_batch *b);
+ * 1e-3.  Capturable in a CUDA graph.
+ * Evaluation: the plan cuts every histogram into tiles of at most 16384 bins
+ * (histograms by decreasing size); per step, CTAs take tiles from a counter
+ * and write one partial row per tile (df64 value and gradient sums, a domain
+ * flag, FP32 Gauss-Newton products), then one warp per histogram sums its
+ * rows in tile order and runs the control.  Results do not depend on which
+ * CTA took which tile.
+ * ws: cg_fit_lm_workspace_size bytes, 256-byte aligned, written by
+ * cg_fit_lm_plan (host offsets host_offsets[n_hist + 1]; synchronises
+ * `stream`) before init / step.  A workspace without a plan makes init and
+ * step do nothing (the kernels check the plan's header and tile count
+ * against ws_bytes).  Histograms of 2^24 bins or more end CG_FIT_DOMAIN. */
+size_t cg_fit_lm_workspace_size(const cg_batch *b, const int64_t *host_offsets);
+cg_status cg_fit_lm_plan(const cg_batch *b, const int64_t *host_offsets, void *ws, size_t ws_bytes,
+                         void *stream);
 cg_status cg_fit_lm_init(const cg_batch *b, const double *theta0, cg_fit_state *state, double tol, void *ws,
                          size_t ws_bytes, void *stream);
 cg_status cg_fit_lm_step(const cg_batch *b, cg_fit_state *state, int n_steps, double tol, void *ws,

@@ -93,7 +93,8 @@ def lib():
         "cg_fit_step": (ctypes.c_int, [B, ctypes.POINTER(_TileMap), _vp, ctypes.c_int, ctypes.c_double, _vp, _sz,
                                        _vp]),
         "cg_batch_gn": (ctypes.c_int, [B, _dp, _dp, _dp, _dp, _vp, _sz, _vp]),
-        "cg_fit_lm_workspace_size": (_sz, [B]),
+        "cg_fit_lm_workspace_size": (_sz, [B, ctypes.POINTER(ctypes.c_int64)]),
+        "cg_fit_lm_plan": (ctypes.c_int, [B, ctypes.POINTER(ctypes.c_int64), _vp, _sz, _vp]),
         "cg_fit_lm_init": (ctypes.c_int, [B, _dp, _vp, ctypes.c_double, _vp, _sz, _vp]),
         "cg_fit_lm_step": (ctypes.c_int, [B, _vp, ctypes.c_int, ctypes.c_double, _vp, _sz, _vp]),
         "cg_fit_single_workspace_size": (_sz, [P]),

@@ -76,6 +76,12 @@ struct FitArgs {
     const int* queue[3];   // histogram ids per unit kind (cluster, cta, warp), sorted by size
     const int* n_items;    // device [3]: queue lengths (written by the plan)
     int* counters;         // 3 ints, zeroed before each persistent launch
+    const int* order;      // k_fit_eval: histograms by decreasing size (NULL: index order, grid-stride)
+    int* ectr;             // k_fit_eval / k_lm_tiles: queue position, zero at launch
+    const void* lm_hdr;    // LM: plan header (tile count, magic)
+    const int2* tiles;     // LM: (histogram, chunk) per tile, histograms by decreasing size
+    const int2* hspan;     // LM: (first tile, tile count) per histogram
+    size_t ws_bytes;       // LM: workspace size (bounds the tile count read from the header)
     int64_t H;
     int P, D, pm, n_steps;
     double tol;
@@ -719,15 +725,39 @@ __global__ void __launch_bounds__(512) k_fit_persistent(FitArgs a) {
     }
 }
 
+// Gauss-Newton matrix out[i * ld + j] (i, j < P) from the packed sums raw of
+// h r_a r_b over the raw factors r: GN_ij = D_i D_j raw_ij, with the per-point
+// scales D = (1, A/s^2, A/s^3) per peak and 1 per polynomial term.
+template <int K>
+__device__ void gn_scaled(const double* th, int P, const double* raw, double* out, int ld) {
+    constexpr int R = GP1Gnm<K>::R;
+    double dsc[FP];
+    for (int k = 0; k < P; ++k) {
+        dsc[k] = 1.0;
+        if (k < 3 * K) {
+            const int pk = k / 3, role = k - 3 * pk;
+            const double A = th[3 * pk], sg = th[3 * pk + 2];
+            if (role == 1) dsc[k] = A / (sg * sg);
+            if (role == 2) dsc[k] = A / (sg * sg * sg);
+        }
+    }
+    for (int i = 0; i < P; ++i)
+        for (int j = 0; j < P; ++j) {
+            const int lo = i < j ? i : j, hi = i < j ? j : i;
+            out[i * ld + j] = dsc[i] * dsc[j] * raw[lo * R - lo * (lo - 1) / 2 + (hi - lo)];
+        }
+}
+
 // Init (GN + first evaluation) and plain evaluation: one CTA per histogram,
-// grid-stride over histograms.  mode 0: value/grad at a.theta; mode 1: init;
+// taken from a.order through the counter a.ectr (largest first) or, without
+// an order, grid-stride in index order.  mode 0: value/grad at a.theta; mode 1: init;
 // mode 2: value only; mode 4: value, gradient and the full Gauss-Newton
 // matrix (df64 only; with a.st set, rows of stride FP and only RUNNING fits).
 template <int K, int OBJ, int PREC, int MODE>
 __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
     constexpr int mode = MODE;
     constexpr int N = GP1Acc<K>::N;
-    constexpr int NV = GP1Gnm<K>::NV, R = GP1Gnm<K>::R;
+    constexpr int NV = GP1Gnm<K>::NV;
     // warp_totals_f writes whole chunks of 32 accumulators (the tail past NV is zero)
     __shared__ double gmred[(MODE == 4 ? (NV + 31) / 32 * 32 : 1) * kMaxWarpsPerCta];
     __shared__ double gmtot[MODE == 4 ? NV : 1];
@@ -742,7 +772,21 @@ __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
     __shared__ double red[(N + 1) * kMaxWarpsPerCta];
     __shared__ double tot[N + 1];
     __shared__ double gn[N + 1];
-    for (int64_t h = blockIdx.x; h < a.H; h += gridDim.x) {
+    __shared__ int q_sh;
+    for (int64_t it = blockIdx.x;; it += gridDim.x) {
+        int64_t h;
+        if (a.order) {   // dynamic queue, largest histograms first
+            if (threadIdx.x == 0) q_sh = atomicAdd(a.ectr, 1);
+            __syncthreads();
+            const int q = q_sh;
+            __syncthreads();
+            if (q >= a.H) break;
+            h = a.order[q];
+            if (h < 0 || h >= a.H) continue;   // an order not written by a plan: skip, never index past H
+        } else {
+            if (it >= a.H) break;
+            h = it;
+        }
         if (MODE == 4 && a.st && a.st[h].status != CG_FIT_RUNNING) continue;   // uniform per block
         const double* th = a.theta + h * (MODE == 4 && a.st ? (int64_t)FP : (int64_t)a.P);
         const Geom G = geom_of(a, h);
@@ -827,23 +871,8 @@ __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
                 const int P = a.P;
                 const int gs = a.st ? FP : P;
                 for (int k = 0; k < P; ++k) a.grad[h * gs + k] = g[k];
-                double dsc[FP];
-                for (int k = 0; k < P; ++k) {
-                    dsc[k] = 1.0;
-                    if (k < 3 * K) {
-                        const int pk = k / 3, role = k - 3 * pk;
-                        const double A = th[3 * pk], sg = th[3 * pk + 2];
-                        if (role == 1) dsc[k] = A / (sg * sg);
-                        if (role == 2) dsc[k] = A / (sg * sg * sg);
-                    }
-                }
                 const int gm_s = a.st ? FP : P;
-                for (int i = 0; i < P; ++i)
-                    for (int j = 0; j < P; ++j) {
-                        const int lo_ = i < j ? i : j, hi_ = i < j ? j : i;
-                        const double raw = gmtot[lo_ * R - lo_ * (lo_ - 1) / 2 + (hi_ - lo_)];
-                        a.gn[(h * gm_s + i) * gm_s + j] = dsc[i] * dsc[j] * raw;
-                    }
+                gn_scaled<K>(th, P, gmtot, a.gn + h * gm_s * gm_s, gm_s);
             } else if (mode == 0) {
                 const double v = epilogue(ep, th, tot, g);
                 a.value[h] = v;
@@ -884,29 +913,59 @@ __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Levenberg-Marquardt fits: the (value, gradient, Gauss-Newton matrix)
-// evaluation of k_fit_eval mode 4 at the trial points, then this control
-// kernel, one warp per histogram.  State reuse: hinv holds the Gauss-Newton
-// matrix GN at theta, h0[0] the damping lambda.  One step: accept the trial
-// when F(trial) < F (theta, F, g, GN move there, lambda / 10, iteration + 1,
-// EDM = g^T GN^-1 g / 2 with the undamped matrix; converged when EDM < tol
-// max(1, |F|)), otherwise lambda x 10 (CG_FIT_LINESEARCH_FAILED past 1e16);
-// then the next trial theta + delta, (GN + lambda diag(GN)) delta = -g by
-// Cholesky (diag(GN) entries <= 0 count as 1).
+// Levenberg-Marquardt fits.  The plan cuts every histogram into tiles of at
+// most kLmTile bins (histograms by decreasing size, a histogram's tiles
+// consecutive).  One step is two launches:
+//  k_lm_tiles: resident CTAs take tiles from a counter; for a tile of a
+//    RUNNING fit, the df64 value / gradient accumulators, a domain flag and
+//    the FP32 Gauss-Newton products of its bins at the trial point, summed
+//    over the CTA into one partial row;
+//  k_lm_finish: one warp per histogram sums its tiles' rows in tile order
+//    (deterministic, no atomics on values), applies the epilogue (value,
+//    gradient, GN with the per-point scales) and runs the control on lane 0.
+// Control: accept the trial when F(trial) < F (theta, F, g, GN move there,
+// lambda / 10 down to 1e-12, iteration + 1, EDM = g^T GN^-1 g / 2 with the
+// undamped matrix; converged when EDM < tol max(1, |F|)); otherwise
+// lambda x 10 (CG_FIT_LINESEARCH_FAILED past 1e16); then the next trial
+// theta + delta, (GN + lambda diag(GN)) delta = -g by Cholesky (diag(GN)
+// entries <= 0 count as 1; a scaled gradient step where the damped matrix is
+// not positive definite).  State reuse: hinv holds GN at theta, h0[0] lambda.
 // ---------------------------------------------------------------------------
-struct LmArgs {
-    cg_fit_state* st;
-    double* th_trial;        // [H][FP]
-    const double* f_trial;   // [H]
-    const double* g_trial;   // [H][FP]
-    const double* gn_trial;  // [H][FP][FP]
-    int64_t H;
-    double tol;
-    int first;               // 1: the trial holds the start point's evaluation
+constexpr int kLmTile = 16384;
+constexpr int kLmMagic = 0x4c4d5431;
+
+struct LmHdr {
+    int ectr;      // tile queue position (zeroed by the plan, init and every k_lm_finish)
+    int n_tiles;
+    int magic;     // kLmMagic once a plan has been written
+    int pad;
 };
 
-// Solve (M) x = b for symmetric positive definite M (P x P, row stride FP) by
-// Cholesky in place on a copy; false when M is not positive definite.
+template <int K>
+struct LmRow {
+    static constexpr int N = GP1Acc<K>::N, NV = GP1Gnm<K>::NV, NP = N + 1 + NV;
+};
+
+__host__ __device__ inline size_t lm_align(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Partial rows follow the tile list: the address depends on the tile count.
+__device__ inline double* lm_part(const FitArgs& a, int n_tiles) {
+    return (double*)((char*)a.tiles + lm_align(sizeof(int2) * (size_t)n_tiles));
+}
+
+// Tile count from the plan header, or -1 when no plan of this size is there.
+template <int K>
+__device__ inline int lm_tiles_checked(const FitArgs& a) {
+    const LmHdr* hd = (const LmHdr*)a.lm_hdr;
+    const int T = hd->n_tiles;
+    if (hd->magic != kLmMagic || T < 1) return -1;
+    const size_t end = (size_t)((const char*)lm_part(a, T) - (const char*)a.lm_hdr) +
+                       sizeof(double) * (size_t)T * LmRow<K>::NP;
+    return end <= a.ws_bytes ? T : -1;
+}
+
+// Solve M x = b for symmetric positive definite M (P x P, row stride FP) by
+// Cholesky; false when M is not positive definite.
 __device__ bool chol_solve(const double* M, const double* b, int P, double* x) {
     double L[FP * FP];
     for (int i = 0; i < P; ++i)
@@ -934,10 +993,71 @@ __device__ bool chol_solve(const double* M, const double* b, int P, double* x) {
     return true;
 }
 
-// The evaluation writes the leading P x P block of each FP x FP matrix only.
-__device__ void lm_copy_gn(double* dst, const double* src, int P) {
-    for (int i = 0; i < FP; ++i)
-        for (int j = 0; j < FP; ++j) dst[i * FP + j] = (i < P && j < P) ? src[i * FP + j] : 0.0;
+// EDM = g^T GN^-1 g / 2 (GN^-1 by Cholesky; its diagonal where GN is not
+// positive definite, entries <= 0 counting as 1).
+__device__ double lm_edm(const double* G, const double* g, int P) {
+    double z[FP];
+    double e = 0.0;
+    if (chol_solve(G, g, P, z)) {
+        for (int k = 0; k < P; ++k) e += g[k] * z[k];
+    } else {
+        for (int k = 0; k < P; ++k) e += g[k] * g[k] / (G[k * FP + k] > 0.0 ? G[k * FP + k] : 1.0);
+    }
+    return 0.5 * e;
+}
+
+// The control of one fit after the evaluation (ft, gt, Gt: P x P, row
+// stride FP) of its trial point tt; writes the next trial point into tt.
+__device__ void lm_control_one(cg_fit_state& s, double* tt, double ft, const double* gt, const double* Gt, int P,
+                               double tol, bool first) {
+    auto take = [&](void) {
+        for (int k = 0; k < FP; ++k) {
+            s.theta[k] = k < P ? tt[k] : 0.0;
+            s.grad[k] = k < P ? gt[k] : 0.0;
+        }
+        for (int i = 0; i < FP; ++i)
+            for (int j = 0; j < FP; ++j) s.hinv[i * FP + j] = (i < P && j < P) ? Gt[i * FP + j] : 0.0;
+        s.f = ft;
+        s.edm = lm_edm(s.hinv, s.grad, P);
+        if (s.edm < tol * fmax(1.0, fabs(s.f))) s.status = CG_FIT_CONVERGED;
+    };
+    if (first) {
+        for (int k = 0; k < FP; ++k) s.h0[k] = 0.0;
+        s.h0[0] = 1e-3;
+        s.iter = 0;
+        s.n_eval = 1;
+        s.n_params = P;
+        s.edm = 0.0;
+        if (!isfinite(ft)) {
+            s.status = CG_FIT_DOMAIN;
+            return;
+        }
+        s.status = CG_FIT_RUNNING;
+        take();
+    } else {
+        s.n_eval += 1;
+        if (isfinite(ft) && ft < s.f) {
+            s.iter += 1;
+            s.h0[0] = fmax(s.h0[0] * 0.1, 1e-12);
+            take();
+        } else {
+            s.h0[0] *= 10.0;
+            if (s.h0[0] > 1e16) s.status = CG_FIT_LINESEARCH_FAILED;
+        }
+    }
+    if (s.status != CG_FIT_RUNNING) return;
+    double M[FP * FP], b[FP], d[FP];
+    const double lam = s.h0[0];
+    for (int i = 0; i < P; ++i) {
+        for (int j = 0; j < P; ++j) M[i * FP + j] = s.hinv[i * FP + j];
+        const double dg = s.hinv[i * FP + i] > 0.0 ? s.hinv[i * FP + i] : 1.0;
+        M[i * FP + i] += lam * dg;
+        b[i] = -s.grad[i];
+    }
+    if (!chol_solve(M, b, P, d)) {
+        for (int i = 0; i < P; ++i) d[i] = b[i] / ((1.0 + lam) * (s.hinv[i * FP + i] > 0.0 ? s.hinv[i * FP + i] : 1.0));
+    }
+    for (int k = 0; k < FP; ++k) tt[k] = k < P ? s.theta[k] + d[k] : 0.0;
 }
 
 __global__ void k_lm_reset(cg_fit_state* st, int64_t H, int P) {
@@ -947,82 +1067,142 @@ __global__ void k_lm_reset(cg_fit_state* st, int64_t H, int P) {
     st[h].n_params = P;
 }
 
-__global__ void k_lm_control(LmArgs a) {
-    const int lane = threadIdx.x & 31;
-    const int64_t h = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (h >= a.H || lane != 0) return;
+template <int K, int OBJ>
+__global__ void __launch_bounds__(256) k_lm_tiles(FitArgs a) {
+    constexpr int N = LmRow<K>::N, NV = LmRow<K>::NV, NP = LmRow<K>::NP;
+    __shared__ double gmred[(NV + 31) / 32 * 32 * kMaxWarpsPerCta];
+    __shared__ double red[(N + 1) * kMaxWarpsPerCta];
+    __shared__ double tot[N + 1];
+    __shared__ GP1Consts cs;
+    __shared__ GP1Df cd;
+    __shared__ DfTables tab;
+    __shared__ int cs_bad, q_sh;
+    const int T = lm_tiles_checked<K>(a);
+    if (T < 0) return;   // no plan in this workspace: nothing is read or written
+    double* part = lm_part(a, T);
+    df_tables_init(tab);
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x == 0) q_sh = atomicAdd(a.ectr, 1);
+        __syncthreads();
+        const int q = q_sh;
+        __syncthreads();
+        if (q >= T) break;
+        const int2 tl = a.tiles[q];
+        const int64_t h = tl.x;
+        if (h < 0 || h >= a.H || a.st[h].status != CG_FIT_RUNNING) continue;   // uniform per block
+        double* out = part + (size_t)q * NP;
+        const Geom G = geom_of(a, h);
+        const int64_t b0 = (int64_t)tl.y * kLmTile;
+        if (G.n >= kDfMaxBins || tl.y < 0 || (b0 >= G.n && b0 > 0)) {
+            // the df64 bin loop needs exact float bin indices: no value for this fit
+            for (int v = threadIdx.x; v < NP; v += blockDim.x) out[v] = (v == N) ? 1.0 : 0.0;
+            continue;
+        }
+        const double* th = a.theta + h * FP;
+        GP1Data dd;
+        dd.y = G.y;
+        dd.centres = nullptr;
+        dd.lo = G.lo;
+        dd.h = G.hw;
+        dd.au = 2.0 / (a.hi[h] - a.lo[h]);
+        dd.bu = -(a.lo[h] + a.hi[h]) / (a.hi[h] - a.lo[h]);
+        dd.D = a.D;
+        dd.pm = a.pm;
+        dd.vec_ok = 0;
+        if (threadIdx.x < 32) {
+            const bool ok = gp1_prologue_warp<K, true>(th, a.D, G.lo, G.hw, dd.au, dd.bu, cs, cd);
+            if (threadIdx.x == 0) cs_bad = ok ? 0 : 1;
+        }
+        __syncthreads();
+        Geom Gt = G;
+        Gt.n = G.n < b0 + kLmTile ? G.n : b0 + kLmTile;
+        df v[N], gv[N];
+        float gm[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) gm[i] = 0.0f;
+        bool bad = false;
+        acc_bins_df64<K, OBJ, false, false, true>(Gt, cs, cd, dd, tab, (int)b0 + threadIdx.x, blockDim.x, v, gv,
+                                                  bad, gm);
+        const int any_bad = __syncthreads_or(bad) | cs_bad;
+        warp_totals_f<NV>(gm, gmred + (threadIdx.x >> 5), kMaxWarpsPerCta);
+        reduce_cta<N, df>(v, red, tot);   // its barriers also order the gmred writes
+        const int nw = blockDim.x >> 5;
+        for (int i = threadIdx.x; i < NV; i += blockDim.x) {
+            double sum = 0.0;
+            for (int w = 0; w < nw; ++w) sum += gmred[i * kMaxWarpsPerCta + w];
+            out[N + 1 + i] = sum;
+        }
+        for (int i = threadIdx.x; i < N; i += blockDim.x) out[i] = tot[i];
+        if (threadIdx.x == 0) out[N] = any_bad ? 1.0 : 0.0;
+        __syncthreads();
+    }
+}
+
+template <int K, int OBJ>
+__global__ void __launch_bounds__(128) k_lm_finish(FitArgs a, int first) {
+    constexpr int N = LmRow<K>::N, NP = LmRow<K>::NP;
+    __shared__ double sums[4][NP];
+    if (blockIdx.x == 0 && threadIdx.x == 0) ((LmHdr*)a.lm_hdr)->ectr = 0;   // for the next tile launch
+    const int T = lm_tiles_checked<K>(a);
+    if (T < 0) return;
+    const double* part = lm_part(a, T);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t h = (int64_t)blockIdx.x * 4 + w;
+    if (h >= a.H) return;
     cg_fit_state& s = a.st[h];
-    const int P = s.n_params;
-    const double* gt = a.g_trial + h * FP;
-    const double* Gt = a.gn_trial + h * FP * FP;
-    double* tt = a.th_trial + h * FP;
-    const double ft = a.f_trial[h];
-    if (a.first) {
-        for (int k = 0; k < FP; ++k) {
-            s.theta[k] = k < P ? tt[k] : 0.0;
-            s.grad[k] = k < P ? gt[k] : 0.0;
-            s.h0[k] = 0.0;
-        }
-        lm_copy_gn(s.hinv, Gt, P);
-        s.f = ft;
-        s.iter = 0;
-        s.n_eval = 1;
-        s.h0[0] = 1e-3;
-        s.status = isfinite(ft) ? CG_FIT_RUNNING : CG_FIT_DOMAIN;
-        s.edm = 0.0;
-        if (s.status == CG_FIT_RUNNING) {
-            double z[FP];
-            if (chol_solve(s.hinv, s.grad, P, z)) {
-                double e = 0.0;
-                for (int k = 0; k < P; ++k) e += s.grad[k] * z[k];
-                s.edm = 0.5 * e;
-            } else {
-                double e = 0.0;
-                for (int k = 0; k < P; ++k) e += s.grad[k] * s.grad[k] / (s.hinv[k * FP + k] > 0.0 ? s.hinv[k * FP + k] : 1.0);
-                s.edm = 0.5 * e;
-            }
-            if (s.edm < a.tol * fmax(1.0, fabs(s.f))) s.status = CG_FIT_CONVERGED;
-        }
-    } else {
-        if (s.status != CG_FIT_RUNNING) return;
-        s.n_eval += 1;
-        if (isfinite(ft) && ft < s.f) {
-            for (int k = 0; k < P; ++k) {
-                s.theta[k] = tt[k];
-                s.grad[k] = gt[k];
-            }
-            lm_copy_gn(s.hinv, Gt, P);
-            s.f = ft;
-            s.iter += 1;
-            s.h0[0] = fmax(s.h0[0] * 0.1, 1e-12);
-            double z[FP];
-            double e = 0.0;
-            if (chol_solve(s.hinv, s.grad, P, z)) {
-                for (int k = 0; k < P; ++k) e += s.grad[k] * z[k];
-            } else {
-                for (int k = 0; k < P; ++k) e += s.grad[k] * s.grad[k] / (s.hinv[k * FP + k] > 0.0 ? s.hinv[k * FP + k] : 1.0);
-            }
-            s.edm = 0.5 * e;
-            if (s.edm < a.tol * fmax(1.0, fabs(s.f))) s.status = CG_FIT_CONVERGED;
-        } else {
-            s.h0[0] *= 10.0;
-            if (s.h0[0] > 1e16) s.status = CG_FIT_LINESEARCH_FAILED;
-        }
-    }
     if (s.status != CG_FIT_RUNNING) return;
-    // next trial point
-    double M[FP * FP], b[FP], d[FP];
-    const double lam = s.h0[0];
-    for (int i = 0; i < P; ++i) {
-        for (int j = 0; j < P; ++j) M[i * FP + j] = s.hinv[i * FP + j];
-        const double dg = s.hinv[i * FP + i] > 0.0 ? s.hinv[i * FP + i] : 1.0;
-        M[i * FP + i] += lam * dg;
-        b[i] = -s.grad[i];
+    const int2 span = a.hspan[h];
+    if (span.x < 0 || span.y < 1 || span.x + span.y > T) return;
+    double* sm = sums[w];
+    for (int v = lane; v < NP; v += 32) {
+        double acc = 0.0;
+        for (int t = 0; t < span.y; ++t) acc += part[(size_t)(span.x + t) * NP + v];
+        sm[v] = acc;
     }
-    if (!chol_solve(M, b, P, d)) {   // not positive definite: a scaled gradient step
-        for (int i = 0; i < P; ++i) d[i] = b[i] / ((1.0 + lam) * (s.hinv[i * FP + i] > 0.0 ? s.hinv[i * FP + i] : 1.0));
+    __syncwarp();
+    if (lane != 0) return;
+    double* tt = (double*)a.theta + h * FP;
+    EpiParams ep;
+    ep.model = CG_MODEL_GAUSS_POLY;
+    ep.K = K;
+    ep.D = a.D;
+    ep.P = a.P;
+    ep.lo = ep.hi = 0.0;
+    double g[kMaxParams], G[FP * FP];
+    const double v = epilogue(ep, tt, sm, g);
+    const double ft = (sm[N] != 0.0) ? __longlong_as_double(0x7ff8000000000000LL) : v;
+    gn_scaled<K>(tt, a.P, sm + N + 1, G, FP);
+    lm_control_one(s, tt, ft, g, G, a.P, a.tol, first != 0);
+}
+
+template <typename F>
+static int lm_blocks_per_sm(F kern, int threads) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, 0) != cudaSuccess || n < 1) n = 1;
+    return n;
+}
+
+template <int K, int OBJ>
+static cg_status lm_launch_k(const FitArgs& a, int first, bool tiles, cudaStream_t st) {
+    if (tiles) {
+        static int occ = 0;
+        if (occ == 0) occ = lm_blocks_per_sm(k_lm_tiles<K, OBJ>, 256);
+        k_lm_tiles<K, OBJ><<<device_sm_count() * occ, 256, 0, st>>>(a);
+    } else {
+        k_lm_finish<K, OBJ><<<(unsigned)((a.H + 3) / 4), 128, 0, st>>>(a, first);
     }
-    for (int k = 0; k < FP; ++k) tt[k] = k < P ? s.theta[k] + d[k] : 0.0;
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
+
+static cg_status lm_launch(const cg_batch* b, const FitArgs& a, int first, bool tiles, cudaStream_t st) {
+    const int K = b->tmpl.n_peaks, O = b->tmpl.objective;
+#define CG_LM_CASE(KK, OO) if (K == KK && O == OO) return lm_launch_k<KK, OO>(a, first, tiles, st);
+    CG_LM_CASE(1, CG_OBJ_CHI2) CG_LM_CASE(1, CG_OBJ_POISSON) CG_LM_CASE(1, CG_OBJ_POISSON_BC)
+    CG_LM_CASE(2, CG_OBJ_CHI2) CG_LM_CASE(2, CG_OBJ_POISSON) CG_LM_CASE(2, CG_OBJ_POISSON_BC)
+    CG_LM_CASE(3, CG_OBJ_CHI2) CG_LM_CASE(3, CG_OBJ_POISSON) CG_LM_CASE(3, CG_OBJ_POISSON_BC)
+#undef CG_LM_CASE
+    return CG_ERR_UNSUPPORTED;
 }
 
 // ---------------------------------------------------------------------------
@@ -1095,7 +1275,7 @@ __global__ void k_single_setup(SingleWs* w, int64_t n, double lo, double hi) {
 // Host helpers
 // ---------------------------------------------------------------------------
 struct FitWsLayout {
-    size_t hdr, counters, qmeta, queues, total;
+    size_t hdr, counters, qmeta, queues, order, total;
 };
 
 FitWsLayout fit_ws_layout(int64_t H) {
@@ -1104,7 +1284,8 @@ FitWsLayout fit_ws_layout(int64_t H) {
     L.counters = 256;
     L.qmeta = 512;
     L.queues = 768;
-    L.total = L.queues + align_up((size_t)3 * H * sizeof(int), 256);
+    L.order = L.queues + align_up((size_t)3 * H * sizeof(int), 256);
+    L.total = L.order + align_up((size_t)H * sizeof(int), 256);
     return L;
 }
 
@@ -1134,11 +1315,29 @@ FitArgs base_args(const cg_batch* b) {
     return a;
 }
 
+// Resident CTAs of 256 threads per SM for a k_fit_eval instantiation (the
+// size of a grid that takes its histograms from a queue).
+template <typename F>
+static int eval_blocks_per_sm(F kern) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 256, 0) != cudaSuccess || n < 1) n = 1;
+    return n;
+}
+
 template <int K, int OBJ>
 cg_status launch_eval_k(const FitArgs& a, int mode, int prec, cudaStream_t st) {
-    const int G = device_sm_count() * 4;
-    const int grid = (int)(a.H < G ? a.H : G);
+    int G = device_sm_count() * 4;
     const bool df = prec == CG_PREC_DF64;
+    if (a.order && df) {   // one wave of resident CTAs pulling from the queue
+        static int occ[5] = {0, 0, 0, 0, 0};
+        if (mode >= 0 && mode < 5 && occ[mode] == 0) {
+            if (mode == 1) occ[1] = eval_blocks_per_sm(k_fit_eval<K, OBJ, CG_PREC_DF64, 1>);
+            else if (mode == 4) occ[4] = eval_blocks_per_sm(k_fit_eval<K, OBJ, CG_PREC_DF64, 4>);
+            else occ[mode] = 4;
+        }
+        G = device_sm_count() * ((mode >= 0 && mode < 5) ? occ[mode] : 4);
+    }
+    const int grid = (int)(a.H < G ? a.H : G);
     if (mode == 0) {
         if (df) k_fit_eval<K, OBJ, CG_PREC_DF64, 0><<<grid, 256, 0, st>>>(a);
         else k_fit_eval<K, OBJ, CG_PREC_FP64, 0><<<grid, 256, 0, st>>>(a);
@@ -1269,25 +1468,77 @@ cg_status cg_batch_gradient(const cg_batch* b, const double* theta, double* valu
     return launch_eval(&b->tmpl, a, grad ? 0 : 2, st);   // grad == NULL: values only
 }
 
-// Levenberg-Marquardt workspace: trial parameters, values, gradients, GN matrices.
+// Levenberg-Marquardt workspace: plan header, trial points [H][FP], tile
+// spans [H], then the tile list [T] and the partial rows [T][NP].
 struct LmWs {
-    size_t th, f, g, gn, total;
+    size_t hdr, th, hspan, tiles, total;
 };
-static LmWs lm_ws_layout(int64_t H) {
+static int lm_row_doubles(int K) { return (1 + 3 * K + 4) + 1 + (3 * K + 4) * (3 * K + 5) / 2; }
+static LmWs lm_ws_layout(int64_t H, int64_t T, int K) {
     LmWs L;
-    size_t o = 0;
-    auto take = [&](size_t bytes) { size_t r = o; o += align_up(bytes, 256); return r; };
-    L.th = take(sizeof(double) * (size_t)H * FP);
-    L.f = take(sizeof(double) * (size_t)H);
-    L.g = take(sizeof(double) * (size_t)H * FP);
-    L.gn = take(sizeof(double) * (size_t)H * FP * FP);
-    L.total = o;
+    L.hdr = 0;
+    L.th = 256;
+    L.hspan = L.th + lm_align(sizeof(double) * (size_t)H * FP);
+    L.tiles = L.hspan + lm_align(sizeof(int2) * (size_t)H);
+    L.total = L.tiles + lm_align(sizeof(int2) * (size_t)T) + sizeof(double) * (size_t)T * lm_row_doubles(K);
     return L;
 }
+// Tiles of a batch (-1 when an offset is decreasing or the count leaves int).
+static int64_t lm_tile_count(const int64_t* ho, int64_t H) {
+    int64_t T = 0;
+    for (int64_t h = 0; h < H; ++h) {
+        const int64_t n = ho[h + 1] - ho[h];
+        if (n < 0) return -1;
+        T += n > 0 ? (n + kLmTile - 1) / kLmTile : 1;
+    }
+    return T < INT32_MAX ? T : -1;
+}
+static bool lm_batch_ok(const cg_batch* b) {
+    return b && b->n_hist >= 1 && b->n_hist <= ((int64_t)1 << 30) && b->offsets && b->lo && b->hi &&
+           b->tmpl.data && fit_supported(&b->tmpl) && b->tmpl.precision == CG_PREC_DF64;
+}
 
-size_t cg_fit_lm_workspace_size(const cg_batch* b) {
-    if (!b || b->n_hist < 1 || !b->offsets || !fit_supported(&b->tmpl)) return 0;
-    return lm_ws_layout(b->n_hist).total;
+size_t cg_fit_lm_workspace_size(const cg_batch* b, const int64_t* host_offsets) {
+    if (!lm_batch_ok(b) || !host_offsets) return 0;
+    const int64_t T = lm_tile_count(host_offsets, b->n_hist);
+    if (T < 1) return 0;
+    return lm_ws_layout(b->n_hist, T, b->tmpl.n_peaks).total;
+}
+
+cg_status cg_fit_lm_plan(const cg_batch* b, const int64_t* host_offsets, void* ws, size_t ws_bytes, void* stream) {
+    if (!b || !host_offsets) return CG_ERR_INVALID_ARG;
+    if (!lm_batch_ok(b)) return fit_supported(&b->tmpl) ? CG_ERR_UNSUPPORTED : CG_ERR_INVALID_ARG;
+    const int64_t H = b->n_hist;
+    const int64_t T = lm_tile_count(host_offsets, H);
+    if (T < 1) return CG_ERR_INVALID_ARG;
+    const LmWs L = lm_ws_layout(H, T, b->tmpl.n_peaks);
+    if (!ws || ((uintptr_t)ws & 255) || ws_bytes < L.total) return CG_ERR_WORKSPACE;
+    std::vector<std::pair<int64_t, int>> by_size((size_t)H);
+    for (int64_t h = 0; h < H; ++h) by_size[(size_t)h] = {host_offsets[h + 1] - host_offsets[h], (int)h};
+    std::stable_sort(by_size.begin(), by_size.end(),
+                     [](const std::pair<int64_t, int>& x, const std::pair<int64_t, int>& y) { return x.first > y.first; });
+    std::vector<int2> tiles;
+    tiles.reserve((size_t)T);
+    std::vector<int2> span((size_t)H);
+    for (auto& e : by_size) {
+        const int nt = e.first > 0 ? (int)((e.first + kLmTile - 1) / kLmTile) : 1;
+        span[(size_t)e.second] = make_int2((int)tiles.size(), nt);
+        for (int j = 0; j < nt; ++j) tiles.push_back(make_int2(e.second, j));
+    }
+    LmHdr hd;
+    hd.ectr = 0;
+    hd.n_tiles = (int)T;
+    hd.magic = kLmMagic;
+    hd.pad = 0;
+    char* base = (char*)ws;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(base + L.tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(base + L.hspan, span.data(), span.size() * sizeof(int2), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(base + L.hdr, &hd, sizeof(hd), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return CG_ERR_CUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? CG_OK : CG_ERR_CUDA;
 }
 
 cg_status cg_batch_gn(const cg_batch* b, const double* theta, double* value, double* grad, double* gn, void* ws,
@@ -1306,69 +1557,62 @@ cg_status cg_batch_gn(const cg_batch* b, const double* theta, double* value, dou
     return launch_eval(&b->tmpl, a, 4, (cudaStream_t)stream);
 }
 
-static cg_status lm_launch_control(const cg_batch* b, cg_fit_state* state, double tol, char* base, int first,
-                                   cudaStream_t st) {
-    const LmWs L = lm_ws_layout(b->n_hist);
-    LmArgs la;
-    la.st = state;
-    la.th_trial = (double*)(base + L.th);
-    la.f_trial = (const double*)(base + L.f);
-    la.g_trial = (const double*)(base + L.g);
-    la.gn_trial = (const double*)(base + L.gn);
-    la.H = b->n_hist;
-    la.tol = tol;
-    la.first = first;
-    const int per_block = 4;
-    k_lm_control<<<(unsigned)((b->n_hist + per_block - 1) / per_block), 32 * per_block, 0, st>>>(la);
-    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
-}
-
-static cg_status lm_eval(const cg_batch* b, cg_fit_state* state, char* base, cudaStream_t st) {
-    const LmWs L = lm_ws_layout(b->n_hist);
+static FitArgs lm_args(const cg_batch* b, cg_fit_state* state, double tol, void* ws, size_t ws_bytes) {
+    const LmWs L = lm_ws_layout(b->n_hist, 0, b->tmpl.n_peaks);
+    char* base = (char*)ws;
     FitArgs a = base_args(b);
     a.st = state;
+    a.tol = tol;
     a.theta = (const double*)(base + L.th);
-    a.value = (double*)(base + L.f);
-    a.grad = (double*)(base + L.g);
-    a.gn = (double*)(base + L.gn);
-    return launch_eval(&b->tmpl, a, 4, st);
+    a.lm_hdr = base + L.hdr;
+    a.ectr = (int*)(base + L.hdr);   // LmHdr::ectr
+    a.hspan = (const int2*)(base + L.hspan);
+    a.tiles = (const int2*)(base + L.tiles);
+    a.ws_bytes = ws_bytes;
+    return a;
+}
+
+static cg_status lm_checks(const cg_batch* b, cg_fit_state* state, double tol, void* ws, size_t ws_bytes) {
+    if (!b || !state || !(tol >= 0.0)) return CG_ERR_INVALID_ARG;
+    if (!lm_batch_ok(b)) return fit_supported(&b->tmpl) ? CG_ERR_UNSUPPORTED : CG_ERR_INVALID_ARG;
+    // the tile part's size is known to the plan only; the kernels check it against ws_bytes
+    if (!ws || ((uintptr_t)ws & 255) || ws_bytes < lm_ws_layout(b->n_hist, 1, b->tmpl.n_peaks).total)
+        return CG_ERR_WORKSPACE;
+    return CG_OK;
 }
 
 cg_status cg_fit_lm_init(const cg_batch* b, const double* theta0, cg_fit_state* state, double tol, void* ws,
                          size_t ws_bytes, void* stream) {
-    if (!b || b->n_hist < 1 || !b->offsets || !theta0 || !state || !(tol >= 0.0)) return CG_ERR_INVALID_ARG;
-    if (!fit_supported(&b->tmpl)) return CG_ERR_UNSUPPORTED;
-    if (b->tmpl.precision != CG_PREC_DF64) return CG_ERR_UNSUPPORTED;
-    const LmWs L = lm_ws_layout(b->n_hist);
-    if (!ws || ((uintptr_t)ws & 255) || ws_bytes < L.total) return CG_ERR_WORKSPACE;
-    char* base = (char*)ws;
+    cg_status s = lm_checks(b, state, tol, ws, ws_bytes);
+    if (s != CG_OK) return s;
+    if (!theta0) return CG_ERR_INVALID_ARG;
+    const FitArgs a = lm_args(b, state, tol, ws, ws_bytes);
     cudaStream_t st = (cudaStream_t)stream;
-    // the start points into the trial buffer (row stride FP), statuses RUNNING
-    const int P = 3 * b->tmpl.n_peaks + b->tmpl.poly_degree + 1;
-    if (cudaMemsetAsync(base + L.th, 0, sizeof(double) * (size_t)b->n_hist * FP, st) != cudaSuccess ||
-        cudaMemcpy2DAsync(base + L.th, sizeof(double) * FP, theta0, sizeof(double) * P, sizeof(double) * P,
-                          (size_t)b->n_hist, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    const int P = a.P;
+    double* th = (double*)a.theta;
+    if (cudaMemsetAsync(th, 0, sizeof(double) * (size_t)b->n_hist * FP, st) != cudaSuccess ||
+        cudaMemcpy2DAsync(th, sizeof(double) * FP, theta0, sizeof(double) * P, sizeof(double) * P,
+                          (size_t)b->n_hist, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(a.ectr, 0, sizeof(int), st) != cudaSuccess)
         return CG_ERR_CUDA;
     k_lm_reset<<<(unsigned)((b->n_hist + 255) / 256), 256, 0, st>>>(state, b->n_hist, P);
     if (cudaGetLastError() != cudaSuccess) return CG_ERR_CUDA;
-    cg_status s = lm_eval(b, state, base, st);
+    s = lm_launch(b, a, 1, true, st);
     if (s != CG_OK) return s;
-    return lm_launch_control(b, state, tol, base, 1, st);
+    return lm_launch(b, a, 1, false, st);
 }
 
 cg_status cg_fit_lm_step(const cg_batch* b, cg_fit_state* state, int n_steps, double tol, void* ws, size_t ws_bytes,
                          void* stream) {
-    if (!b || b->n_hist < 1 || !b->offsets || !state || n_steps < 0 || !(tol >= 0.0)) return CG_ERR_INVALID_ARG;
-    if (!fit_supported(&b->tmpl)) return CG_ERR_UNSUPPORTED;
-    if (b->tmpl.precision != CG_PREC_DF64) return CG_ERR_UNSUPPORTED;
-    const LmWs L = lm_ws_layout(b->n_hist);
-    if (!ws || ((uintptr_t)ws & 255) || ws_bytes < L.total) return CG_ERR_WORKSPACE;
-    char* base = (char*)ws;
+    cg_status s = lm_checks(b, state, tol, ws, ws_bytes);
+    if (s != CG_OK) return s;
+    if (n_steps < 0) return CG_ERR_INVALID_ARG;
+    const FitArgs a = lm_args(b, state, tol, ws, ws_bytes);
     cudaStream_t st = (cudaStream_t)stream;
     for (int i = 0; i < n_steps; ++i) {
-        cg_status s = lm_eval(b, state, base, st);
+        s = lm_launch(b, a, 0, true, st);
         if (s != CG_OK) return s;
-        s = lm_launch_control(b, state, tol, base, 0, st);
+        s = lm_launch(b, a, 0, false, st);
         if (s != CG_OK) return s;
     }
     return CG_OK;
@@ -1409,7 +1653,11 @@ cg_status cg_fit_plan(const cg_batch* b, const int64_t* host_offsets, const cg_t
     meta.cluster_size = map->cluster_size;
     cudaStream_t st = (cudaStream_t)stream;
     char* base = (char*)ws;
+    std::vector<int> order((size_t)H);
+    for (int64_t h = 0; h < H; ++h) order[(size_t)h] = by_size[(size_t)h].second;
     if (cudaMemcpyAsync(base + L.queues, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(base + L.order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, st) !=
             cudaSuccess ||
         cudaMemcpyAsync(base + L.qmeta, &meta, sizeof(meta), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemsetAsync(base, 0, 512, st) != cudaSuccess)
@@ -1425,6 +1673,11 @@ cg_status cg_fit_init(const cg_batch* b, const cg_tile_map* map, const double* t
     FitArgs a = base_args(b);
     a.theta = theta0;
     a.st = state;
+    const FitWsLayout L = fit_ws_layout(b->n_hist);
+    char* base = (char*)ws;
+    a.order = (const int*)(base + L.order);
+    a.ectr = (int*)(base + L.counters) + 4;
+    if (cudaMemsetAsync(a.ectr, 0, sizeof(int), (cudaStream_t)stream) != cudaSuccess) return CG_ERR_CUDA;
     return launch_eval(&b->tmpl, a, 1, (cudaStream_t)stream);
 }
 

@@ -157,15 +157,20 @@ class HistBatch:
 class LMFitter:
     """Levenberg-Marquardt fits of every histogram of a df64 HistBatch: each
     step evaluates value, gradient and Gauss-Newton matrix at the trial points
-    and runs the damping / Cholesky control kernel (cg_fit_lm_init /
-    cg_fit_lm_step).  States as for BatchFitter; hinv holds the GN matrix."""
+    (tiles of at most 16384 bins) and runs the damping / Cholesky control
+    (cg_fit_lm_plan / cg_fit_lm_init / cg_fit_lm_step).  States as for
+    BatchFitter; hinv holds the GN matrix, h0[0] the damping."""
 
     def __init__(self, batch):
         self.b = batch
-        n = cg.lib().cg_fit_lm_workspace_size(ctypes.byref(batch.c))
+        offs = (ctypes.c_int64 * len(batch.offsets_host))(*batch.offsets_host.tolist())
+        n = cg.lib().cg_fit_lm_workspace_size(ctypes.byref(batch.c), offs)
         if n == 0:
-            raise cg.CgError(cg.ERR_UNSUPPORTED, "batch not supported by the fitter")
+            raise cg.CgError(cg.ERR_UNSUPPORTED, "batch not supported by the Levenberg-Marquardt fitter "
+                                                 "(df64 Gaussian + polynomial batches only)")
         self.ws = torch.empty(n, dtype=torch.uint8, device=batch.y.device)
+        cg._check(cg.lib().cg_fit_lm_plan(ctypes.byref(batch.c), offs, cg._ptr(self.ws), self.ws.numel(),
+                                          cg._stream()), "cg_fit_lm_plan")
         self.states = None
         self.graph = None
 

@@ -82,3 +82,30 @@ def test_df64_tables_match_their_generator():
     for (hi, lo), ref in ((t["exp2j"][1], 2 ** (1 / 64)), (t["logF"][0], math.log1p(1 / 128)),
                           (t["invF"][63], 128 / 255)):
         assert abs(float(hi) + float(lo) - ref) <= 2.0 ** -48 * abs(ref)   # what a float pair holds
+
+
+def test_lm_plan_sizes_and_refusals_without_gpu(lib):
+    """The Levenberg-Marquardt workspace: tiles of at most 16384 bins per
+    histogram (one for an empty one), rows of N + 1 + R(R+1)/2 doubles; FP64
+    batches, decreasing offsets and missing plans' inputs are refused on the
+    host."""
+    from paper_2203_06139_gb300 import cg
+    b = cg._Batch()
+    b.tmpl.model, b.tmpl.objective, b.tmpl.precision = cg.MODEL_GAUSS_POLY, cg.OBJ_CHI2, cg.PREC_DF64
+    b.tmpl.n_peaks, b.tmpl.poly_degree = 1, 2
+    b.tmpl.data = 256
+    b.n_hist, b.offsets, b.lo, b.hi = 3, 512, 768, 1024
+    offs = (ctypes.c_int64 * 4)(0, 16384, 16385, 16385)   # 1 + 1 + 1 (empty) tiles
+    offs2 = (ctypes.c_int64 * 4)(0, 40000, 40001, 40001)  # 3 + 1 + 1 tiles
+    n1 = lib.cg_fit_lm_workspace_size(ctypes.byref(b), offs)
+    n2 = lib.cg_fit_lm_workspace_size(ctypes.byref(b), offs2)
+    row = (1 + 3 + 4) + 1 + 7 * 8 // 2
+    assert n1 > 0 and n2 - n1 == 2 * row * 8
+    assert lib.cg_fit_lm_workspace_size(ctypes.byref(b), (ctypes.c_int64 * 4)(0, 5, 3, 9)) == 0
+    b64 = cg._Batch.from_buffer_copy(b)
+    b64.tmpl.precision = cg.PREC_FP64
+    assert lib.cg_fit_lm_workspace_size(ctypes.byref(b64), offs) == 0
+    assert lib.cg_fit_lm_plan(ctypes.byref(b64), offs, ctypes.c_void_p(4096), 1 << 20, None) == cg.ERR_UNSUPPORTED
+    assert lib.cg_fit_lm_plan(ctypes.byref(b), offs, ctypes.c_void_p(4096), 16, None) == cg.ERR_WORKSPACE
+    assert lib.cg_fit_lm_step(ctypes.byref(b), ctypes.c_void_p(4096), 1, 1e-9, ctypes.c_void_p(4097), 1 << 20,
+                              None) == cg.ERR_WORKSPACE

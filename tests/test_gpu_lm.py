@@ -15,7 +15,7 @@ import torch
 import oracle
 from oracle.fit import CONVERGED, bfgs_fit, lm_fit
 from paper_2203_06139_gb300 import cg, synth
-from paper_2203_06139_gb300.fit import _H0, HistBatch, LMFitter
+from paper_2203_06139_gb300.fit import _H, _H0, HistBatch, LMFitter
 from tests._metrics import max_rel_err
 
 pytestmark = pytest.mark.gpu
@@ -152,4 +152,39 @@ def test_lm_needs_a_df64_batch(dev):
     with pytest.raises(cg.CgError):
         b.gauss_newton(torch.tensor(d["start"], device=dev))
     with pytest.raises(cg.CgError):
-        LMFitter(b).init(torch.tensor(d["start"], device=dev))
+        LMFitter(b)
+
+
+def test_lm_tiles_span_histograms_with_a_ragged_tail(dev):
+    """Histograms of 3 full tiles + 17 bins, exactly one tile, one tile + 1
+    bin and 300 bins: the state after init holds the tiled evaluation at the
+    start point (value and gradient to 1e-10, GN within the FP32 bound), and
+    the fits reach the oracle's minima."""
+    ns = [3 * 16384 + 17, 16384, 16385, 300]
+    ps = [synth.random_gauss_poly(1, 1, n, poly_mode=1, seed=40 + i) for i, n in enumerate(ns)]
+    y = np.concatenate([p["y"] for p in ps])
+    offs = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+    start = np.stack([p["theta"] for p in ps])
+    H = len(ns)
+    b = HistBatch(y, offs, np.zeros(H), np.ones(H), 1, 1, cg.OBJ_POISSON, poly_mode=1, precision=cg.PREC_DF64)
+    f = LMFitter(b)
+    st = f.init(torch.tensor(start, device=dev), tol=1e-12)
+    F0, g0 = st.f.cpu().numpy(), st.grad.cpu().numpy()
+    G0 = st.d[:, _H:_H + 144].cpu().numpy().reshape(H, 12, 12)[:, :5, :5]
+    for h in range(H):
+        yy = y[offs[h]:offs[h + 1]]
+        r = oracle.binned1d(1, 1, 1, oracle.POISSON, yy, 0.0, 1.0, start[h])
+        assert abs(F0[h] - r.value) <= 1e-10 * abs(r.value)
+        assert max_rel_err(g0[h], r.grad, r.scale) <= 1e-10
+        ref = oracle.binned1d_gnmat(1, 1, 1, oracle.POISSON, yy, 0.0, 1.0, start[h])
+        dd = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
+        assert np.max(np.abs(G0[h] - ref) / dd) <= GN_TOL
+    st = f.step(80, 1e-12)
+    F, status = st.f.cpu().numpy(), st.status.cpu().numpy()
+    assert np.all(status == CONVERGED), status
+    for h in range(H):
+        yy = y[offs[h]:offs[h + 1]]
+        fg = lambda t: (lambda q: (q.value, q.grad))(oracle.binned1d(1, 1, 1, oracle.POISSON, yy, 0.0, 1.0, t))
+        gn = lambda t: oracle.binned1d_gn(1, 1, 1, oracle.POISSON, yy, 0.0, 1.0, t)
+        ref = bfgs_fit(fg, gn, start[h], max_iter=400, tol=1e-12)
+        assert abs(F[h] - ref["F"]) <= 1e-6 * abs(ref["F"]), (h, F[h], ref["F"])
