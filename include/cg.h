@@ -473,7 +473,7 @@ typedef struct cg_expr_program cg_expr_program;
  * (free with cg_expr_free).  CG_ERR_INVALID_ARG for a malformed program
  * (bad operand order or index, a root that does not depend on the
  * elements), CG_ERR_UNSUPPORTED when NVRTC or the driver entry points are
- * unavailable or the elements use more than 63 parameter-only subexpressions
+ * unavailable or the elements use more than 127 parameter-only subexpressions
  * (per-thread accumulators), CG_ERR_CUDA when compilation or loading fails.  With
  * CG_ERR_UNSUPPORTED (no NVRTC, driver or device) or CG_ERR_CUDA, *out still
  * receives a program that holds the generated source and the compiler log

@@ -117,7 +117,7 @@ const Driver& driver() {
 }
 
 enum Cls { K_CONST = 0, K_PARAM_ONLY = 1, K_INPUT_ONLY = 2, K_MIXED = 3 };
-constexpr int kMaxExprAcc = 64;
+constexpr int kMaxExprAcc = 128;   // past about 60 the accumulators spill to local memory
 
 struct Plan {
     std::vector<int> cls;         // per node

@@ -103,3 +103,19 @@ def test_generated_eight_peaks_matches_the_oracle(dev):
     with pytest.raises(cg.CgError):
         vo.gradient([torch.tensor(p["y"], device=dev)], torch.tensor(th, device=dev))
 
+
+
+def test_generated_thirty_two_peaks_matches_the_oracle(dev):
+    """98 parameters (32 Gaussians + line): 99 per-thread accumulators, past
+    the register file (they spill); the largest program of the Fig. 3b sweep."""
+    K, n = 32, 3000
+    p = synth.random_gauss_poly(K, 1, n, seed=432)
+    x = (E.index() + 0.5) * (1.0 / n)
+    f = E.param(3 * K) + E.param(3 * K + 1) * x
+    for k in range(K):
+        f = f + E.param(3 * k) * E.exp(-(x - E.param(3 * k + 1)) ** 2 / (2.0 * E.param(3 * k + 2) ** 2))
+    y = E.inp(0)
+    root = (y - f) ** 2 / E.maximum(y, 1.0)
+    prog = E.compile(root, 3 * K + 2, 1)
+    assert prog.num_acc > 64
+    _check(prog, E.nodes(root), 3 * K + 2, [p["y"]], np.stack([p["theta"], p["truth"]]), dev)
