@@ -964,100 +964,165 @@ __device__ inline int lm_tiles_checked(const FitArgs& a) {
     return end <= a.ws_bytes ? T : -1;
 }
 
-// Solve M x = b for symmetric positive definite M (P x P, row stride FP) by
-// Cholesky; false when M is not positive definite.
-__device__ bool chol_solve(const double* M, const double* b, int P, double* x) {
-    double L[FP * FP];
-    for (int i = 0; i < P; ++i)
-        for (int j = 0; j <= i; ++j) {
-            double sum = M[i * FP + j];
-            for (int k = 0; k < j; ++k) sum -= L[i * FP + k] * L[j * FP + k];
-            if (i == j) {
-                if (!(sum > 0.0)) return false;
-                L[i * FP + i] = sqrt(sum);
-            } else {
-                L[i * FP + j] = sum / L[j * FP + j];
-            }
+// Warp-parallel dense algebra for the control: lane i < P holds row i of a
+// P x P matrix (or component i of a vector) in registers; loops run over the
+// compile-time bound FP so that every register index is static.
+__device__ __forceinline__ double lane_bcast(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+// Cholesky factorisation in place: on success lane i holds row i of L
+// (m[0..i]).  The result is the same on every lane (false: not positive
+// definite).
+__device__ __forceinline__ bool chol_warp(double (&m)[FP], int P, int lane) {
+#pragma unroll
+    for (int j = 0; j < FP; ++j) {
+        if (j >= P) break;
+        const double ajj = lane_bcast(m[j], j);
+        if (!(ajj > 0.0)) return false;
+        const double ljj = sqrt(ajj);
+        if (lane == j) m[j] = ljj;
+        else if (lane > j) m[j] = m[j] / ljj;
+#pragma unroll
+        for (int k = j + 1; k < FP; ++k) {
+            if (k >= P) break;
+            const double lkj = lane_bcast(m[j], k);
+            if (lane >= k) m[k] = fma(-m[j], lkj, m[k]);
         }
-    double y[FP];
-    for (int i = 0; i < P; ++i) {
-        double sum = b[i];
-        for (int k = 0; k < i; ++k) sum -= L[i * FP + k] * y[k];
-        y[i] = sum / L[i * FP + i];
-    }
-    for (int i = P - 1; i >= 0; --i) {
-        double sum = y[i];
-        for (int k = i + 1; k < P; ++k) sum -= L[k * FP + i] * x[k];
-        x[i] = sum / L[i * FP + i];
     }
     return true;
 }
 
-// EDM = g^T GN^-1 g / 2 (GN^-1 by Cholesky; its diagonal where GN is not
-// positive definite, entries <= 0 counting as 1).
-__device__ double lm_edm(const double* G, const double* g, int P) {
-    double z[FP];
-    double e = 0.0;
-    if (chol_solve(G, g, P, z)) {
-        for (int k = 0; k < P; ++k) e += g[k] * z[k];
-    } else {
-        for (int k = 0; k < P; ++k) e += g[k] * g[k] / (G[k * FP + k] > 0.0 ? G[k * FP + k] : 1.0);
+// x = (L L^T)^-1 b with L from chol_warp; b and x one component per lane.
+__device__ __forceinline__ double chol_solve_warp(const double (&l)[FP], double b, int P, int lane) {
+    double r = b, y = 0.0;
+#pragma unroll
+    for (int j = 0; j < FP; ++j) {   // L y = b, column by column
+        if (j >= P) break;
+        const double yj = lane_bcast(r / l[j], j);
+        if (lane == j) y = yj;
+        if (lane > j) r = fma(-l[j], yj, r);
     }
-    return 0.5 * e;
+    double x = 0.0;
+#pragma unroll
+    for (int j = FP - 1; j >= 0; --j) {   // L^T x = y, row j from the lanes below it
+        if (j >= P) continue;
+        const double sj = warp_sum((lane > j && lane < P) ? l[j] * x : 0.0);
+        if (lane == j) x = (y - sj) / l[j];
+    }
+    return x;
 }
 
-// The control of one fit after the evaluation (ft, gt, Gt: P x P, row
-// stride FP) of its trial point tt; writes the next trial point into tt.
-__device__ void lm_control_one(cg_fit_state& s, double* tt, double ft, const double* gt, const double* Gt, int P,
-                               double tol, bool first) {
-    auto take = [&](void) {
-        for (int k = 0; k < FP; ++k) {
-            s.theta[k] = k < P ? tt[k] : 0.0;
-            s.grad[k] = k < P ? gt[k] : 0.0;
+// Row i of the Gauss-Newton matrix from the packed sums raw (per-point
+// scales D = 1, A/s^2, A/s^3 per peak, 1 per polynomial term); zero past P.
+template <int K>
+__device__ __forceinline__ void gn_row(const double* th, int P, const double* raw, int i, double (&row)[FP]) {
+    constexpr int R = GP1Gnm<K>::R;
+    auto dsc = [&](int k) -> double {
+        if (k < 3 * K) {
+            const int pk = k / 3, role = k - 3 * pk;
+            const double A = th[3 * pk], sg = th[3 * pk + 2];
+            return role == 0 ? 1.0 : (role == 1 ? A / (sg * sg) : A / (sg * sg * sg));
         }
-        for (int i = 0; i < FP; ++i)
-            for (int j = 0; j < FP; ++j) s.hinv[i * FP + j] = (i < P && j < P) ? Gt[i * FP + j] : 0.0;
-        s.f = ft;
-        s.edm = lm_edm(s.hinv, s.grad, P);
-        if (s.edm < tol * fmax(1.0, fabs(s.f))) s.status = CG_FIT_CONVERGED;
+        return 1.0;
     };
-    if (first) {
-        for (int k = 0; k < FP; ++k) s.h0[k] = 0.0;
-        s.h0[0] = 1e-3;
-        s.iter = 0;
-        s.n_eval = 1;
-        s.n_params = P;
-        s.edm = 0.0;
-        if (!isfinite(ft)) {
-            s.status = CG_FIT_DOMAIN;
-            return;
-        }
-        s.status = CG_FIT_RUNNING;
-        take();
-    } else {
-        s.n_eval += 1;
-        if (isfinite(ft) && ft < s.f) {
-            s.iter += 1;
-            s.h0[0] = fmax(s.h0[0] * 0.1, 1e-12);
-            take();
+    const double di = i < P ? dsc(i) : 0.0;
+#pragma unroll
+    for (int j = 0; j < FP; ++j) {
+        if (i < P && j < P) {
+            const int lo = i < j ? i : j, hi = i < j ? j : i;
+            row[j] = di * dsc(j) * raw[lo * R - lo * (lo - 1) / 2 + (hi - lo)];
         } else {
-            s.h0[0] *= 10.0;
-            if (s.h0[0] > 1e16) s.status = CG_FIT_LINESEARCH_FAILED;
+            row[j] = 0.0;
         }
     }
-    if (s.status != CG_FIT_RUNNING) return;
-    double M[FP * FP], b[FP], d[FP];
-    const double lam = s.h0[0];
-    for (int i = 0; i < P; ++i) {
-        for (int j = 0; j < P; ++j) M[i * FP + j] = s.hinv[i * FP + j];
-        const double dg = s.hinv[i * FP + i] > 0.0 ? s.hinv[i * FP + i] : 1.0;
-        M[i * FP + i] += lam * dg;
-        b[i] = -s.grad[i];
+}
+
+// The control of one fit, all 32 lanes of a warp, after the evaluation of
+// its trial point tt (value ft, uniform; gradient component g_l and GN row G
+// of this lane); writes the next trial point into tt.
+__device__ void lm_control_warp(cg_fit_state& s, double* tt, double ft, double g_l, const double (&G)[FP], int P,
+                                double tol, bool first, int lane) {
+    const bool own = lane < P;
+    double lam = first ? 1e-3 : s.h0[0];
+    const double f_old = first ? 0.0 : s.f;
+    int status = first ? CG_FIT_RUNNING : s.status;
+    const int iter = first ? 0 : s.iter;
+    const int n_eval = first ? 1 : s.n_eval + 1;
+    bool accept;
+    if (first) {
+        accept = isfinite(ft);
+        if (!accept) status = CG_FIT_DOMAIN;
+    } else {
+        accept = isfinite(ft) && ft < f_old;
+        if (accept) {
+            lam = fmax(lam * 0.1, 1e-12);
+        } else {
+            lam *= 10.0;
+            if (lam > 1e16) status = CG_FIT_LINESEARCH_FAILED;
+        }
     }
-    if (!chol_solve(M, b, P, d)) {
-        for (int i = 0; i < P; ++i) d[i] = b[i] / ((1.0 + lam) * (s.hinv[i * FP + i] > 0.0 ? s.hinv[i * FP + i] : 1.0));
+    // the Gauss-Newton matrix and gradient at theta (this lane's row / component);
+    // the start point is kept also when its value is not finite
+    const bool use_trial = accept || first;
+    double row[FP], gth, th_l;
+    const double tt_l = lane < FP ? tt[lane] : 0.0;
+    if (use_trial) {
+#pragma unroll
+        for (int j = 0; j < FP; ++j) row[j] = G[j];
+        gth = own ? g_l : 0.0;
+        th_l = own ? tt_l : 0.0;
+    } else {
+#pragma unroll
+        for (int j = 0; j < FP; ++j) row[j] = (own && j < P) ? s.hinv[lane * FP + j] : 0.0;
+        gth = own ? s.grad[lane] : 0.0;
+        th_l = own ? s.theta[lane] : 0.0;
     }
-    for (int k = 0; k < FP; ++k) tt[k] = k < P ? s.theta[k] + d[k] : 0.0;
+    double dg = 0.0;
+#pragma unroll
+    for (int j = 0; j < FP; ++j)
+        if (j == lane) dg = row[j];
+    const double dpos = dg > 0.0 ? dg : 1.0;
+    double edm = first ? 0.0 : s.edm;
+    if (accept) {
+        double m[FP];
+#pragma unroll
+        for (int j = 0; j < FP; ++j) m[j] = row[j];
+        double e;
+        if (chol_warp(m, P, lane)) {
+            const double z = chol_solve_warp(m, gth, P, lane);
+            e = warp_sum(own ? gth * z : 0.0);
+        } else {
+            e = warp_sum(own ? gth * gth / dpos : 0.0);
+        }
+        edm = 0.5 * e;
+        if (status == CG_FIT_RUNNING && edm < tol * fmax(1.0, fabs(ft))) status = CG_FIT_CONVERGED;
+    }
+    __syncwarp();   // every lane has read the old state
+    if (use_trial && lane < FP) {
+        s.theta[lane] = th_l;
+        s.grad[lane] = gth;
+#pragma unroll
+        for (int j = 0; j < FP; ++j) s.hinv[lane * FP + j] = row[j];
+        s.h0[lane] = 0.0;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        if (use_trial) s.f = ft;
+        s.h0[0] = lam;
+        s.edm = edm;
+        s.iter = iter + ((accept && !first) ? 1 : 0);
+        s.n_eval = n_eval;
+        s.n_params = P;
+        s.status = status;
+    }
+    if (status != CG_FIT_RUNNING) return;
+    // next trial: (GN + lambda diag(GN)) delta = -g, diagonal entries <= 0 counting as 1
+    double m[FP];
+#pragma unroll
+    for (int j = 0; j < FP; ++j) m[j] = row[j] + ((j == lane) ? lam * dpos : 0.0);
+    double d;
+    if (chol_warp(m, P, lane)) d = chol_solve_warp(m, -gth, P, lane);
+    else d = -gth / ((1.0 + lam) * dpos);
+    if (lane < FP) tt[lane] = own ? th_l + d : 0.0;
 }
 
 __global__ void k_lm_reset(cg_fit_state* st, int64_t H, int P) {
@@ -1143,6 +1208,8 @@ template <int K, int OBJ>
 __global__ void __launch_bounds__(128) k_lm_finish(FitArgs a, int first) {
     constexpr int N = LmRow<K>::N, NP = LmRow<K>::NP;
     __shared__ double sums[4][NP];
+    __shared__ double gsh[4][FP];
+    __shared__ double fsh[4];
     if (blockIdx.x == 0 && threadIdx.x == 0) ((LmHdr*)a.lm_hdr)->ectr = 0;   // for the next tile launch
     const int T = lm_tiles_checked<K>(a);
     if (T < 0) return;
@@ -1161,19 +1228,23 @@ __global__ void __launch_bounds__(128) k_lm_finish(FitArgs a, int first) {
         sm[v] = acc;
     }
     __syncwarp();
-    if (lane != 0) return;
     double* tt = (double*)a.theta + h * FP;
-    EpiParams ep;
-    ep.model = CG_MODEL_GAUSS_POLY;
-    ep.K = K;
-    ep.D = a.D;
-    ep.P = a.P;
-    ep.lo = ep.hi = 0.0;
-    double g[kMaxParams], G[FP * FP];
-    const double v = epilogue(ep, tt, sm, g);
-    const double ft = (sm[N] != 0.0) ? __longlong_as_double(0x7ff8000000000000LL) : v;
-    gn_scaled<K>(tt, a.P, sm + N + 1, G, FP);
-    lm_control_one(s, tt, ft, g, G, a.P, a.tol, first != 0);
+    if (lane == 0) {
+        EpiParams ep;
+        ep.model = CG_MODEL_GAUSS_POLY;
+        ep.K = K;
+        ep.D = a.D;
+        ep.P = a.P;
+        ep.lo = ep.hi = 0.0;
+        double g[kMaxParams];
+        const double v = epilogue(ep, tt, sm, g);
+        fsh[w] = (sm[N] != 0.0) ? __longlong_as_double(0x7ff8000000000000LL) : v;
+        for (int k = 0; k < a.P; ++k) gsh[w][k] = g[k];
+    }
+    __syncwarp();
+    double G[FP];
+    gn_row<K>(tt, a.P, sm + N + 1, lane, G);
+    lm_control_warp(s, tt, fsh[w], lane < a.P ? gsh[w][lane] : 0.0, G, a.P, a.tol, first != 0, lane);
 }
 
 template <typename F>

@@ -209,6 +209,11 @@ __global__ void __launch_bounds__(NT) k_rg2_fp64(RG2Data d, const double* __rest
 // ---------------------------------------------------------------------------
 // Finalize: fixed-order sum of the tile partials of one parameter point and
 // the epilogue (adjoints of the prologue constants chained back to theta).
+// Warp w sums accumulators w, w + NT/32, ...: lane l adds chunks l, l + 32,
+// ... in order, then a butterfly (the same sum on every lane).  Launched as a
+// programmatic dependent of the tile kernel: its blocks may be scheduled
+// while the tile kernel's last blocks run, and wait here until the tile
+// kernel has completed and its partials are visible.
 // ---------------------------------------------------------------------------
 template <int NT>
 __global__ void __launch_bounds__(NT) k_finalize(const double* __restrict__ part, int nacc, TileGrid tg,
@@ -216,24 +221,18 @@ __global__ void __launch_bounds__(NT) k_finalize(const double* __restrict__ part
                                                  double* __restrict__ value, double* __restrict__ grad,
                                                  WsHeader* __restrict__ hdr) {
     __shared__ double tot[kMaxAcc + 1];
-    __shared__ double red[NT / 32];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (gated_off(tg)) return;
     const int th = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int a = 0; a <= nacc; ++a) {
+    for (int a = wid; a <= nacc; a += NT / 32) {
         const double* p = part + ((size_t)th * (nacc + 1) + a) * tg.nbx;
         double s = 0.0;
-        for (int c = threadIdx.x; c < tg.nbx; c += NT) s += p[c];
+        for (int c = lane; c < tg.nbx; c += 32) s += p[c];
         s = warp_sum(s);
-        if (lane == 0) red[wid] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < NT / 32; ++w) t += red[w];
-            tot[a] = t;
-        }
-        __syncthreads();
+        if (lane == 0) tot[a] = s;
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
         const double* tht = theta + (size_t)th * ep.P;
         double g[kMaxParams];
@@ -436,7 +435,19 @@ cg_status grad_points(const cg_problem* pb, const double* theta, int64_t n_theta
         }
     }
     if (s != CG_OK) return s;
-    k_finalize<128><<<(unsigned)n_theta, 128, 0, st>>>(part, nacc, tg, ep, theta, value, grad, hdr);
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)n_theta);
+    cfg.blockDim = dim3(128);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_finalize<128>, (const double*)part, nacc, tg, ep, theta, value, grad, hdr) !=
+        cudaSuccess)
+        return CG_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
 }
 
