@@ -188,3 +188,32 @@ def test_lm_tiles_span_histograms_with_a_ragged_tail(dev):
         gn = lambda t: oracle.binned1d_gn(1, 1, 1, oracle.POISSON, yy, 0.0, 1.0, t)
         ref = bfgs_fit(fg, gn, start[h], max_iter=400, tol=1e-12)
         assert abs(F[h] - ref["F"]) <= 1e-6 * abs(ref["F"]), (h, F[h], ref["F"])
+
+
+def test_lm_edge_cases_in_one_batch(dev):
+    """An empty histogram (value 0, converged at the start), a 1-bin histogram
+    (rank-one matrix: the fit may not converge, but F never increases), a
+    start with a zero width (CG_FIT_DOMAIN, start kept) and an ordinary
+    histogram (the oracle's minimum) in one batch."""
+    p = synth.random_gauss_poly(1, 2, 700, poly_mode=1, seed=61)
+    ys = [np.zeros(0), np.array([37.0]), p["y"].copy(), p["y"]]
+    offs = np.concatenate([[0], np.cumsum([len(y) for y in ys])]).astype(np.int64)
+    start = np.stack([p["theta"]] * 4)
+    start[2, 2] = 0.0
+    H = 4
+    b = HistBatch(np.concatenate(ys), offs, np.zeros(H), np.ones(H), 1, 2, cg.OBJ_CHI2, poly_mode=1,
+                  precision=cg.PREC_DF64)
+    f = LMFitter(b)
+    st = f.init(torch.tensor(start, device=dev), tol=1e-12)
+    F0 = st.f.cpu().numpy().copy()
+    assert st.status[2].item() == 4 and np.array_equal(st.theta[2].cpu().numpy(), start[2])
+    st = f.step(60, 1e-12)
+    F, status = st.f.cpu().numpy(), st.status.cpu().numpy()
+    assert status[0] == CONVERGED and F[0] == 0.0
+    assert F[1] <= F0[1] and status[1] in (0, 1, 3)
+    assert status[2] == 4
+    assert status[3] == CONVERGED
+    fg = lambda t: (lambda q: (q.value, q.grad))(oracle.binned1d(1, 2, 1, oracle.CHI2, ys[3], 0.0, 1.0, t))
+    gn = lambda t: oracle.binned1d_gn(1, 2, 1, oracle.CHI2, ys[3], 0.0, 1.0, t)
+    ref = bfgs_fit(fg, gn, start[3], max_iter=400, tol=1e-12)
+    assert abs(F[3] - ref["F"]) <= 1e-6 * abs(ref["F"])
