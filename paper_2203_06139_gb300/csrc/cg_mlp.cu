@@ -469,6 +469,293 @@ __global__ void __launch_bounds__(kPipeThreads) k_gemm_pipe(const __grid_constan
     }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent TMA + tcgen05 GEMM for N >= 128 (K-major operands): one CTA per
+// SM walks output tiles t = blockIdx.x, + gridDim.x, ... (N-tiles fastest).
+// Warp 0 = TMA producer over a kPStages ring that runs across tiles; warp 1 =
+// TMEM owner and MMA issuer into two accumulators of BN columns each (tile i
+// uses accumulator i & 1); warps 2-5 = epilogue, which drains accumulator
+// i & 1 while the MMAs of tile i + 1 go into the other, storing each lane's
+// row segment straight from the tcgen05.ld registers.  Barriers: full /
+// empty per stage, acc_full (one tcgen05.commit per tile) and acc_empty
+// (one arrival per epilogue warp) per accumulator.  Every wait is bounded;
+// on a failed wait all roles stop, the producer waits (bounded) for its
+// issued loads and the MMA thread for a final commit before TMEM is freed.
+// ---------------------------------------------------------------------------
+constexpr int kPStages = 4;
+
+template <int BN>
+struct PersistSmem {
+    static constexpr int A_BYTES = kTM * kBK * 2;
+    static constexpr int B_BYTES = BN * kBK * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int PIPE = kPStages * STAGE;
+    static constexpr int NBARS = 2 * kPStages + 5;   // full, empty, acc_full[2], acc_empty[2], drain
+    static constexpr int TOTAL = 1024 + PIPE + NBARS * 8 + 16;
+    static_assert(STAGE % 1024 == 0 && A_BYTES % 1024 == 0, "swizzle atoms need 1024-byte aligned tiles");
+    static_assert(TOTAL <= 227 * 1024, "shared memory per CTA");
+};
+
+// One accumulator row segment (columns col0 .. col0 + 31 of row `row`, the
+// 32 values tcgen05.ld gave this lane) through the epilogue of g, straight
+// from registers: 16-byte stores when the segment is inside N and every
+// operand is 16-byte aligned with ldc a multiple of 8, else element by element.
+__device__ __forceinline__ void epi_segment(const GemmArgs& g, const uint32_t (&v)[32], int row, int col0, bool vec) {
+    if (row >= g.M) return;
+    const size_t o = (size_t)row * g.ldc + col0;
+    if (vec) {
+#pragma unroll
+        for (int j = 0; j < 32; j += 8) {
+            float a[8], z[8], r[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) a[e] = __uint_as_float(v[j + e]);
+            if (g.epi == EPI_F32) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) r[e] = a[e];
+            } else if (g.epi == EPI_BIAS_F32 || g.epi == EPI_BIAS_GELU) {
+                const float4 b0 = *reinterpret_cast<const float4*>(g.bias + col0 + j);
+                const float4 b1 = *reinterpret_cast<const float4*>(g.bias + col0 + j + 4);
+                const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    z[e] = a[e] + bb[e];
+                    r[e] = g.epi == EPI_BIAS_GELU ? gelu(z[e]) : z[e];
+                }
+                if (g.epi == EPI_BIAS_GELU && g.aux_out) {
+                    *reinterpret_cast<float4*>(g.aux_out + o + j) = make_float4(z[0], z[1], z[2], z[3]);
+                    *reinterpret_cast<float4*>(g.aux_out + o + j + 4) = make_float4(z[4], z[5], z[6], z[7]);
+                }
+            } else {
+                const float4 z0 = *reinterpret_cast<const float4*>(g.aux_in + o + j);
+                const float4 z1 = *reinterpret_cast<const float4*>(g.aux_in + o + j + 4);
+                const float zz[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+#pragma unroll
+                for (int e = 0; e < 8; ++e) r[e] = a[e] * gelu_grad(zz[e]);
+            }
+            if (g.Cf) {
+                *reinterpret_cast<float4*>(g.Cf + o + j) = make_float4(r[0], r[1], r[2], r[3]);
+                *reinterpret_cast<float4*>(g.Cf + o + j + 4) = make_float4(r[4], r[5], r[6], r[7]);
+            }
+            if (g.Cb && g.epi != EPI_F32 && g.epi != EPI_BIAS_F32) {
+                __nv_bfloat162 p[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) p[e] = __floats2bfloat162_rn(r[2 * e], r[2 * e + 1]);
+                *reinterpret_cast<uint4*>(g.Cb + o + j) = *reinterpret_cast<const uint4*>(p);
+            }
+        }
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const int col = col0 + j;
+        if (col >= g.N) continue;
+        const float a = __uint_as_float(v[j]);
+        const size_t oj = o + j;
+        if (g.epi == EPI_F32) {
+            g.Cf[oj] = a;
+        } else if (g.epi == EPI_BIAS_F32) {
+            g.Cf[oj] = a + g.bias[col];
+        } else if (g.epi == EPI_BIAS_GELU) {
+            const float z = a + g.bias[col];
+            const float h = gelu(z);
+            if (g.aux_out) g.aux_out[oj] = z;
+            if (g.Cb) g.Cb[oj] = __float2bfloat16(h);
+            if (g.Cf) g.Cf[oj] = h;
+        } else {
+            const float dz = a * gelu_grad(g.aux_in[oj]);
+            if (g.Cb) g.Cb[oj] = __float2bfloat16(dz);
+            if (g.Cf) g.Cf[oj] = dz;
+        }
+    }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kPipeThreads, 1) k_gemm_persist(const __grid_constant__ CUtensorMap tmA,
+                                                                  const __grid_constant__ CUtensorMap tmB,
+                                                                  GemmArgs g) {
+    using L = PersistSmem<BN>;
+    constexpr int TCOLS = 2 * BN;   // two accumulators
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_addr(smem_raw);
+    uint8_t* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::PIPE);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + L::NBARS);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const uint32_t sbase = smem_addr(smem);
+    const uint32_t bar0 = smem_addr(bars);
+    auto full_bar = [&](int st) { return bar0 + 8u * (uint32_t)st; };
+    auto empty_bar = [&](int st) { return bar0 + 8u * (uint32_t)(kPStages + st); };
+    auto accf_bar = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kPStages + b); };
+    auto acce_bar = [&](int b) { return bar0 + 8u * (uint32_t)(2 * kPStages + 2 + b); };
+    const uint32_t drain_bar = bar0 + 8u * (uint32_t)(2 * kPStages + 4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = (g.K + kBK - 1) / kBK;
+    const int ntn = (g.N + BN - 1) / BN;
+    const int n_tiles = ntn * ((g.M + kTM - 1) / kTM);
+
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < kPStages; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(full_bar(st)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(empty_bar(st)) : "memory");
+        }
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(accf_bar(b)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" :: "r"(acce_bar(b)) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(drain_bar) : "memory");
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_addr(tmem_slot)), "r"(TCOLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    int issued = 0;     // producer: chunks whose loads were issued
+    bool mma_any = false;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int c = 0;
+            for (int t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x) {
+                const int m0 = (t / ntn) * kTM, n0 = (t % ntn) * BN;
+                bool ok = true;
+                for (int kc = 0; kc < nk; ++kc, ++c) {
+                    const int st = c % kPStages;
+                    if (c >= kPStages && !pipe_wait(empty_bar(st), (uint32_t)((c / kPStages - 1) & 1), abort_flag)) {
+                        pipe_fail(abort_flag, g.err);
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t a_dst = sbase + (uint32_t)(st * L::STAGE), b_dst = a_dst + (uint32_t)L::A_BYTES;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                                 :: "r"(full_bar(st)), "r"((uint32_t)L::STAGE) : "memory");
+                    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                                 " [%0], [%1, {%2, %3}], [%4];"
+                                 :: "r"(a_dst), "l"((uint64_t)&tmA), "r"(kc * kBK), "r"(m0), "r"(full_bar(st))
+                                 : "memory");
+                    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                                 " [%0], [%1, {%2, %3}], [%4];"
+                                 :: "r"(b_dst), "l"((uint64_t)&tmB), "r"(kc * kBK), "r"(n0), "r"(full_bar(st))
+                                 : "memory");
+                    issued = c + 1;
+                }
+                if (!ok) break;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(kTM, BN);
+            int c = 0, i = 0;
+            for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++i) {
+                const int b = i & 1;
+                if (i >= 2 && !pipe_wait(acce_bar(b), (uint32_t)(((i >> 1) - 1) & 1), abort_flag)) {
+                    pipe_fail(abort_flag, g.err);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t dt = tmem + (uint32_t)(b * BN);
+                bool ok = true;
+                for (int kc = 0; kc < nk; ++kc, ++c) {
+                    const int st = c % kPStages;
+                    if (!pipe_wait(full_bar(st), (uint32_t)((c / kPStages) & 1), abort_flag)) {
+                        pipe_fail(abort_flag, g.err);
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = sbase + (uint32_t)(st * L::STAGE), b0 = a0 + (uint32_t)L::A_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                        const uint64_t ad = sdesc_sw128(a0 + 32u * (uint32_t)kk);
+                        const uint64_t bd = sdesc_sw128(b0 + 32u * (uint32_t)kk);
+                        const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                            :: "r"(dt), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+                    }
+                    mma_any = true;
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 :: "r"(empty_bar(st)) : "memory");
+                }
+                if (!ok) break;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(accf_bar(b)) : "memory");
+            }
+        }
+    } else {
+        const int q = warp & 3;                         // TMEM lane quarter of this warp
+        auto al16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+        const bool aligned = g.ldc % 8 == 0 && al16(g.Cf) && al16(g.Cb) && al16(g.aux_in) && al16(g.aux_out) &&
+                             al16(g.bias);
+        int i = 0;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++i) {
+            const int b = i & 1;
+            const bool ok = pipe_wait(accf_bar(b), (uint32_t)((i >> 1) & 1), abort_flag) && !*abort_flag;
+            if (!ok) {
+                if (lane == 0) pipe_fail(abort_flag, g.err);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int m0 = (t / ntn) * kTM, n0 = (t % ntn) * BN;
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t v[32];
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+                      "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+                      "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (c0 + 32 >= BN) {
+                    // the whole accumulator is in registers or stored: hand it back to the MMA warp
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(acce_bar(b)) : "memory");
+                }
+                const int col0 = n0 + c0;
+                if (col0 < g.N) epi_segment(g, v, m0 + q * 32 + lane, col0, aligned && col0 + 32 <= g.N);
+            }
+        }
+    }
+
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (*abort_flag) {
+        // let issued loads and MMAs finish before the shared memory and TMEM go away
+        if (warp == 0 && lane == 0) {
+            for (int c = issued - kPStages < 0 ? 0 : issued - kPStages; c < issued; ++c) {
+                const long long t0 = clock64();
+                while (!mbar_try(full_bar(c % kPStages), (uint32_t)((c / kPStages) & 1)) &&
+                       clock64() - t0 < kWaitCycles) {
+                }
+            }
+        }
+        if (warp == 1 && lane == 0 && mma_any) {
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(drain_bar) : "memory");
+            const long long t0 = clock64();
+            while (!mbar_try(drain_bar, 0u) && clock64() - t0 < kWaitCycles) {
+            }
+        }
+        __syncthreads();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TCOLS) : "memory");
+    }
+}
+
 // cuTensorMapEncodeTiled from the driver, through the runtime's entry-point query.
 PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
@@ -511,6 +798,22 @@ cg_status launch_gemm_pipe(const GemmArgs& g, cudaStream_t st) {
 }
 
 template <int BN>
+cg_status launch_gemm_persist(const GemmArgs& g, cudaStream_t st) {
+    CUtensorMap ta, tb;
+    if (!make_tmap(&ta, g.A, g.K, g.M, g.lda, kTM) || !make_tmap(&tb, g.B, g.K, g.N, g.ldb, BN))
+        return CG_ERR_UNSUPPORTED;
+    using L = PersistSmem<BN>;
+    if (cudaFuncSetAttribute(k_gemm_persist<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::TOTAL) !=
+        cudaSuccess)
+        return CG_ERR_CUDA;
+    const long long tiles = (long long)((g.N + BN - 1) / BN) * ((g.M + kTM - 1) / kTM);
+    const int sms = device_sm_count();
+    const int grid = (int)(tiles < sms ? tiles : sms);   // one CTA per SM (shared memory and TMEM)
+    k_gemm_persist<BN><<<grid, kPipeThreads, L::TOTAL, st>>>(ta, tb, g);
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
+
+template <int BN>
 cg_status launch_gemm_bn(const GemmArgs& g, cudaStream_t st) {
     dim3 grid((g.N + BN - 1) / BN, (g.M + kTM - 1) / kTM);
     k_gemm_tc<BN><<<grid, kThreads, 0, st>>>(g);
@@ -531,7 +834,8 @@ cg_status gemm_bf16(const GemmArgs& g, cudaStream_t st) {
                       g.N < (1 << 30) && g.M <= 65535 * kTM;
     if (pipe) {
         cg_status r;
-        if (g.N >= 128) r = launch_gemm_pipe<128>(g, st);
+        if (g.N >= 256) r = launch_gemm_persist<256>(g, st);
+        else if (g.N >= 128) r = launch_gemm_persist<128>(g, st);
         else if (g.N > 32) r = launch_gemm_pipe<64>(g, st);
         else if (g.N > 16) r = launch_gemm_pipe<32>(g, st);
         else r = launch_gemm_pipe<16>(g, st);

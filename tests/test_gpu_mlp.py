@@ -26,8 +26,8 @@ def _bf(shape, seed, dev, scale=1.0):
                                          (96, 40, 130, 1, 0)])
 def test_gemm_matches_fp32_reference(dev, M, N, K, tA, tB):
     """K-major operands with rows of a multiple of 8 elements take the TMA
-    pipeline (tails in M, N and K included); transposed operands and
-    K = 130 take the register-staged kernel."""
+    kernels (persistent for N >= 128; tails in M, N and K included);
+    transposed operands and K = 130 take the register-staged kernel."""
     A = _bf((K, M) if tA else (M, K), 1, dev)
     B = _bf((K, N) if tB else (N, K), 2, dev)
     C = torch.full((M, N), float("nan"), dtype=torch.float32, device=dev)
@@ -39,6 +39,39 @@ def test_gemm_matches_fp32_reference(dev, M, N, K, tA, tB):
     ref = (a.T if tA else a) @ (b if tB else b.T)
     assert int(err.item()) == 0
     torch.testing.assert_close(C.cpu(), ref, rtol=1e-4, atol=1e-4 * float(ref.abs().max()))
+
+
+@pytest.mark.parametrize("M,N,K", [(8192, 1024, 256), (20000, 512, 192), (40000, 200, 136), (300, 2048, 64)])
+def test_gemm_persistent_many_tiles_per_cta(dev, M, N, K):
+    """The persistent kernel (N >= 128) with more output tiles than SMs:
+    both TMEM accumulators of a CTA alternate, and the stage ring runs across
+    tiles; tails in M, N and K."""
+    A = _bf((M, K), 5, dev)
+    B = _bf((N, K), 6, dev)
+    C = torch.full((M, N), float("nan"), dtype=torch.float32, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    cg.gemm_bf16(A, B, M, N, K, Cf=C, err=err)
+    torch.cuda.synchronize()
+    ref = A.float().cpu() @ B.float().cpu().T
+    assert int(err.item()) == 0
+    torch.testing.assert_close(C.cpu(), ref, rtol=1e-4, atol=1e-4 * float(ref.abs().max()))
+
+
+def test_gemm_persistent_epilogues(dev):
+    M, N, K = 3000, 384, 256
+    A, B = _bf((M, K), 7, dev), _bf((N, K), 8, dev)
+    bias = torch.randn(N, device=dev)
+    z = torch.empty((M, N), device=dev)
+    h = torch.empty((M, N), dtype=torch.bfloat16, device=dev)
+    cg.gemm_bf16(A, B, M, N, K, Cb=h, bias=bias, aux_out=z, epilogue=cg.EPI_BIAS_GELU)
+    ref_z = A.float() @ B.float().T + bias
+    torch.testing.assert_close(z, ref_z, rtol=1e-4, atol=1e-3)
+    torch.testing.assert_close(h.float(), torch.nn.functional.gelu(ref_z).bfloat16().float(), rtol=1e-2, atol=1e-2)
+    dz = torch.empty((M, N), device=dev)
+    cg.gemm_bf16(A, B, M, N, K, Cf=dz, aux_in=z, epilogue=cg.EPI_GELU_GRAD)
+    zz = z.clone().requires_grad_(True)
+    torch.nn.functional.gelu(zz).backward(A.float() @ B.float().T)
+    torch.testing.assert_close(dz, zz.grad, rtol=1e-3, atol=1e-3)
 
 
 def test_gemm_epilogues(dev):
