@@ -490,8 +490,9 @@ struct PersistSmem {
     static constexpr int B_BYTES = BN * kBK * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
     static constexpr int PIPE = kPStages * STAGE;
+    static constexpr int XPOSE = 4 * 32 * 32 * 4;     // one 32 x 32 FP32 block per epilogue warp
     static constexpr int NBARS = 2 * kPStages + 5;   // full, empty, acc_full[2], acc_empty[2], drain
-    static constexpr int TOTAL = 1024 + PIPE + NBARS * 8 + 16;
+    static constexpr int TOTAL = 1024 + PIPE + XPOSE + NBARS * 8 + 16;
     static_assert(STAGE % 1024 == 0 && A_BYTES % 1024 == 0, "swizzle atoms need 1024-byte aligned tiles");
     static_assert(TOTAL <= 227 * 1024, "shared memory per CTA");
 };
@@ -569,6 +570,27 @@ __device__ __forceinline__ void epi_segment(const GemmArgs& g, const uint32_t (&
     }
 }
 
+// A 32 x 32 FP32 block (lane l holds row row0 + l, columns col0 .. col0 + 31,
+// bias already added) stored with whole 128-byte rows per 8 lanes: the rows
+// go through this warp's 4 KB buffer, float4 slot c of row r kept at
+// c ^ (r & 7) so that both the writes and the reads are free of bank
+// conflicts; then each store instruction writes 4 full rows.
+__device__ __forceinline__ void store_block_f32(float* C, int ldc, int M, int row0, int col0, const float (&a)[32],
+                                                float4* buf, int lane) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        buf[lane * 8 + (c ^ (lane & 7))] = make_float4(a[4 * c], a[4 * c + 1], a[4 * c + 2], a[4 * c + 3]);
+    __syncwarp();
+    const int c = lane & 7;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int r = 4 * k + (lane >> 3);
+        const float4 val = buf[r * 8 + (c ^ (r & 7))];
+        if (row0 + r < M) *reinterpret_cast<float4*>(C + (size_t)(row0 + r) * ldc + col0 + 4 * c) = val;
+    }
+    __syncwarp();
+}
+
 template <int BN>
 __global__ void __launch_bounds__(kPipeThreads, 1) k_gemm_persist(const __grid_constant__ CUtensorMap tmA,
                                                                   const __grid_constant__ CUtensorMap tmB,
@@ -578,7 +600,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_gemm_persist(const __grid_c
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_addr(smem_raw);
     uint8_t* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::PIPE);
+    float4* xpose_all = reinterpret_cast<float4*>(smem + L::PIPE);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::PIPE + L::XPOSE);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + L::NBARS);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const uint32_t sbase = smem_addr(smem);
@@ -724,7 +747,26 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_gemm_persist(const __grid_c
                     if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(acce_bar(b)) : "memory");
                 }
                 const int col0 = n0 + c0;
-                if (col0 < g.N) epi_segment(g, v, m0 + q * 32 + lane, col0, aligned && col0 + 32 <= g.N);
+                if (col0 >= g.N) continue;
+                const bool vec = aligned && col0 + 32 <= g.N;
+                if (vec && (g.epi == EPI_F32 || g.epi == EPI_BIAS_F32)) {
+                    float a[32];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) a[j] = __uint_as_float(v[j]);
+                    if (g.epi == EPI_BIAS_F32) {
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4) {
+                            const float4 bb = *reinterpret_cast<const float4*>(g.bias + col0 + j);
+                            a[j] += bb.x;
+                            a[j + 1] += bb.y;
+                            a[j + 2] += bb.z;
+                            a[j + 3] += bb.w;
+                        }
+                    }
+                    store_block_f32(g.Cf, g.ldc, g.M, m0 + q * 32, col0, a, xpose_all + (warp - 2) * 256, lane);
+                } else {
+                    epi_segment(g, v, m0 + q * 32 + lane, col0, vec);
+                }
             }
         }
     }
