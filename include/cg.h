@@ -213,7 +213,14 @@ cg_status cg_mixture_gradient_noalloc(const cg_problem *pb, const double *theta,
  * 0 Cf = acc; 1 Cf = acc + bias[n]; 2 z = acc + bias[n], aux_out = z,
  * Cb = bf16(gelu(z)) (and Cf = gelu(z) if given); 3 dz = acc * gelu'(aux_in),
  * Cb = bf16(dz) (and/or Cf = dz).  gelu(z) = z Phi(z).  err (device int, may
- * be NULL) gets bit 0 when a bounded wait on the tensor core gave up. */
+ * be NULL) gets bit 0 when a bounded wait on the tensor core gave up.
+ * Kernels: K-major operands (transA = transB = 0) with lda, ldb multiples of
+ * 8 and 16-byte aligned A, B go through TMA loads (128-byte swizzle) into an
+ * mbarrier ring feeding tcgen05.mma: for N >= 128 a persistent kernel (one
+ * CTA per SM, 128 x 256 or 128 x 128 tiles, two TMEM accumulators so that a
+ * tile's epilogue overlaps the next tile's MMAs), for smaller N one CTA per
+ * tile; other operands are staged through registers.  Results do not depend
+ * on the kernel chosen beyond FP32 rounding of the accumulation order. */
 cg_status cg_gemm_bf16(const void *A, const void *B, int M, int N, int K, int lda, int ldb, int transA,
                        int transB, float *Cf, void *Cb, int ldc, const float *bias, const float *aux_in,
                        float *aux_out, int epilogue, int *err, void *stream);
