@@ -1444,8 +1444,7 @@ cg_status launch_persistent_k(const FitArgs& a, const cg_tile_map* m, cudaStream
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) != cudaSuccess)
         return CG_ERR_CUDA;
     const int csz = CL ? m->cluster_size : 1;
-    cudaLaunchConfig_t cfg;
-    memset(&cfg, 0, sizeof(cfg));
+    cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(nt);
     cfg.dynamicSmemBytes = L.total;
     cfg.stream = st;

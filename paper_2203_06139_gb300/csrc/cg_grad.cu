@@ -435,8 +435,7 @@ cg_status grad_points(const cg_problem* pb, const double* theta, int64_t n_theta
         }
     }
     if (s != CG_OK) return s;
-    cudaLaunchConfig_t cfg;
-    memset(&cfg, 0, sizeof(cfg));
+    cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)n_theta);
     cfg.blockDim = dim3(128);
     cfg.stream = st;
