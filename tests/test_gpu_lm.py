@@ -52,6 +52,12 @@ def _case(name):
         d = synth.c5_batch(H=6, n_bins=2048)
         d["start"] = d["truth"] * np.random.default_rng(1).uniform(0.97, 1.03, d["truth"].shape)
         return d, cg.OBJ_POISSON_BC, 3, 1, 0
+    if name == "bc_K1_D3":
+        ps = [synth.random_gauss_poly(1, 3, n, poly_mode=1, seed=30 + i) for i, n in enumerate([500, 7000])]
+        y = np.concatenate([p["y"] for p in ps])
+        offs = np.concatenate([[0], np.cumsum([p["n"] for p in ps])]).astype(np.int64)
+        d = dict(y=y, offsets=offs, lo=np.zeros(2), hi=np.ones(2), start=np.stack([p["theta"] for p in ps]), H=2)
+        return d, cg.OBJ_POISSON_BC, 1, 3, 1
     if name == "poisson_K2_D0":
         ps = [synth.random_gauss_poly(2, 0, n, seed=20 + i) for i, n in enumerate([100, 1500, 9000])]
         y = np.concatenate([p["y"] for p in ps])
@@ -62,7 +68,7 @@ def _case(name):
     return d, (cg.OBJ_POISSON if name == "poisson_narrow_peak" else cg.OBJ_POISSON_BC), 1, -1, 0
 
 
-CASES = ["chi2_K1_D2", "bc_K3_D1", "poisson_K2_D0", "poisson_narrow_peak", "bc_narrow_peak"]
+CASES = ["chi2_K1_D2", "bc_K3_D1", "bc_K1_D3", "poisson_K2_D0", "poisson_narrow_peak", "bc_narrow_peak"]
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -88,7 +94,7 @@ def test_gauss_newton_matrix_matches_the_oracle(dev, name):
     assert np.array_equal(v, vb) or np.max(np.abs(v - vb) / np.abs(vb)) <= 1e-15
 
 
-@pytest.mark.parametrize("name", ["chi2_K1_D2", "bc_K3_D1", "poisson_narrow_peak"])
+@pytest.mark.parametrize("name", ["chi2_K1_D2", "bc_K3_D1", "bc_K1_D3", "poisson_narrow_peak"])
 def test_lm_fit_reaches_the_oracle_minimum(dev, name):
     """Every fit converges; its objective equals the oracle's BFGS minimum
     (and the oracle's LM minimum) to 1e-6 relative."""
