@@ -752,7 +752,7 @@ __device__ void gn_scaled(const double* th, int P, const double* raw, double* ou
 // taken from a.order through the counter a.ectr (largest first) or, without
 // an order, grid-stride in index order.  mode 0: value/grad at a.theta; mode 1: init;
 // mode 2: value only; mode 4: value, gradient and the full Gauss-Newton
-// matrix (df64 only; with a.st set, rows of stride FP and only RUNNING fits).
+// matrix [H][P][P] (df64 only).
 template <int K, int OBJ, int PREC, int MODE>
 __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
     constexpr int mode = MODE;
@@ -787,8 +787,7 @@ __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
             if (it >= a.H) break;
             h = it;
         }
-        if (MODE == 4 && a.st && a.st[h].status != CG_FIT_RUNNING) continue;   // uniform per block
-        const double* th = a.theta + h * (MODE == 4 && a.st ? (int64_t)FP : (int64_t)a.P);
+        const double* th = a.theta + h * (int64_t)a.P;
         const Geom G = geom_of(a, h);
         GP1Data dd;
         dd.y = G.y;
@@ -869,10 +868,8 @@ __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
                 const double v = epilogue(ep, th, tot, g);
                 a.value[h] = any_bad ? __longlong_as_double(0x7ff8000000000000LL) : v;
                 const int P = a.P;
-                const int gs = a.st ? FP : P;
-                for (int k = 0; k < P; ++k) a.grad[h * gs + k] = g[k];
-                const int gm_s = a.st ? FP : P;
-                gn_scaled<K>(th, P, gmtot, a.gn + h * gm_s * gm_s, gm_s);
+                for (int k = 0; k < P; ++k) a.grad[h * P + k] = g[k];
+                gn_scaled<K>(th, P, gmtot, a.gn + h * P * P, P);
             } else if (mode == 0) {
                 const double v = epilogue(ep, th, tot, g);
                 a.value[h] = v;
