@@ -391,7 +391,8 @@ cg_status cg_batch_gn(const cg_batch *b, const double *theta, double *value, dou
  * is not positive definite).  CG_FIT_CONVERGED when EDM = g^T GN^-1 g / 2 <
  * tol max(1, |F|), GN the undamped matrix at theta.  state[h].hinv holds GN
  * (not an inverse), h0[0] lambda; iter counts accepted steps, n_eval
- * evaluations.  init evaluates theta0 [n_hist][P] (device) and sets lambda =
+ * evaluations; a fit that has not converged after the last step keeps
+ * CG_FIT_RUNNING (more steps continue it).  init evaluates theta0 [n_hist][P] (device) and sets lambda =
  * 1e-3.  Capturable in a CUDA graph.
  * Evaluation: the plan cuts every histogram into tiles of at most 16384 bins
  * (histograms by decreasing size); per step, CTAs take tiles from a counter
