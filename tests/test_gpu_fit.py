@@ -282,3 +282,73 @@ def test_batch_objective_values_only(dev, prec):
         ref = oracle.binned1d(3, 1, 0, oracle.POISSON_BC, y, 0.0, 1.0, th[h])
         assert abs(v[h] - ref.value) <= 1e-10 * abs(ref.value), (h, v[h], ref.value)
         assert abs(v[h] - v_full[h]) <= 1e-12 * abs(v_full[h])
+
+
+def _sizes_sample(n):
+    """Histogram ids at the size quantiles 0, 0.25, 0.5, 0.75, 1 and one more."""
+    order = np.argsort(n, kind="stable")
+    return sorted({int(order[int(q * (len(n) - 1))]) for q in (0.0, 0.25, 0.5, 0.75, 1.0)} | {int(len(n) // 3)})
+
+
+@pytest.mark.slow
+def test_c4_full_size_sampled_fits(dev):
+    """The whole 4096-histogram batch of the c4 benchmark in its benchmarked
+    form (BFGS: init + 50 iterations in one graph; Levenberg-Marquardt: init +
+    30 steps in one graph); histograms sampled across the size range reach
+    the oracle's minima (same algorithm, same start) within 1e-6."""
+    from oracle.fit import lm_fit
+    from paper_2203_06139_gb300.fit import LMFitter
+    d = synth.c4_batch()
+    n = np.diff(d["offsets"])
+    b = HistBatch(d["y"], d["offsets"], d["lo"], d["hi"], 1, 2, cg.OBJ_CHI2, poly_mode=1, precision=cg.PREC_DF64)
+    th0 = torch.tensor(d["start"], device=dev)
+    f = BatchFitter(b, TileMap(512, 1 << 30, 256, 1))
+    f.capture(50, 1e-9, theta0=th0)
+    f.replay()
+    lm = LMFitter(b)
+    lm.capture(th0, n_steps=30, tol=1e-9)
+    lm.replay()
+    torch.cuda.synchronize()
+    Fb, sb = f.states.f.cpu().numpy(), f.states.status.cpu().numpy()
+    Fl, sl = lm.states.f.cpu().numpy(), lm.states.status.cpu().numpy()
+    checked = 0
+    for h in _sizes_sample(n):
+        y = d["y"][d["offsets"][h]:d["offsets"][h + 1]]
+        fg = lambda t: (lambda q: (q.value, q.grad))(oracle.binned1d(1, 2, 1, oracle.CHI2, y, 0.0, 1.0, t))
+        gn = lambda t: oracle.binned1d_gn(1, 2, 1, oracle.CHI2, y, 0.0, 1.0, t)
+        ref = bfgs_fit(fg, gn, d["start"][h], max_iter=50, tol=1e-9)
+        if ref["status"] == 1 and sb[h] == cg.FIT_CONVERGED:
+            assert abs(Fb[h] - ref["F"]) <= 1e-6 * abs(ref["F"]), (h, int(n[h]), Fb[h], ref["F"])
+            checked += 1
+        fgh = lambda t: fg(t) + (oracle.binned1d_gnmat(1, 2, 1, oracle.CHI2, y, 0.0, 1.0, t),)
+        rl = lm_fit(fgh, d["start"][h], max_evals=31, tol=1e-9)
+        if rl["status"] == 1 and sl[h] == cg.FIT_CONVERGED:
+            assert abs(Fl[h] - rl["F"]) <= 1e-6 * abs(rl["F"]), (h, int(n[h]), Fl[h], rl["F"])
+            checked += 1
+    assert checked >= 8
+
+
+@pytest.mark.slow
+def test_c5_full_size_sampled_fits(dev):
+    """The 65,536 three-peak histograms of the learned-start benchmark, fitted
+    from the heuristic start as there (one warp per histogram, 50
+    iterations); sampled histograms reach the oracle's minimum from the same
+    start within 1e-6."""
+    from paper_2203_06139_gb300 import learned_start as ls
+    H = 65536
+    y = synth.c5_batch_device(H, ls.N_BINS)["y"]
+    th = ls.heuristic_start(y, H)
+    f = ls.fit_batch(y, H, th, 50, 1e-9)
+    torch.cuda.synchronize()
+    F, st = f.states.f.cpu().numpy(), f.states.status.cpu().numpy()
+    th_h = th.cpu().numpy()
+    checked = 0
+    for h in (0, 9999, 22222, 33333, 44444, 65535):
+        yy = y[h * ls.N_BINS:(h + 1) * ls.N_BINS].cpu().numpy()
+        fg = lambda t: (lambda q: (q.value, q.grad))(oracle.binned1d(3, 1, 0, oracle.POISSON_BC, yy, 0.0, 1.0, t))
+        gn = lambda t: oracle.binned1d_gn(3, 1, 0, oracle.POISSON_BC, yy, 0.0, 1.0, t)
+        ref = bfgs_fit(fg, gn, th_h[h], max_iter=50, tol=1e-9)
+        if ref["status"] == 1 and st[h] == cg.FIT_CONVERGED:
+            assert abs(F[h] - ref["F"]) <= 1e-6 * abs(ref["F"]), (h, F[h], ref["F"])
+            checked += 1
+    assert checked >= 3
