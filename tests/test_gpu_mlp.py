@@ -57,6 +57,25 @@ def test_gemm_persistent_many_tiles_per_cta(dev, M, N, K):
     torch.testing.assert_close(C.cpu(), ref, rtol=1e-4, atol=1e-4 * float(ref.abs().max()))
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("M,N,K", [(65536, 512, 512), (8192, 8192, 8192)])
+def test_gemm_full_size_sampled_rows(dev, M, N, K):
+    """The benchmarked shapes: sampled rows of C (first, last and spread
+    between) against an FP32 reference of the same BF16 operands."""
+    g = torch.Generator(device=dev).manual_seed(9)
+    A = torch.randn((M, K), generator=g, device=dev).to(torch.bfloat16)
+    B = torch.randn((N, K), generator=g, device=dev).to(torch.bfloat16)
+    C = torch.full((M, N), float("nan"), dtype=torch.float32, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    cg.gemm_bf16(A, B, M, N, K, Cf=C, err=err)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    rows = torch.tensor(sorted({0, M - 1, 127, 128, M // 2, M // 3} | set(range(1000, M, M // 24))), device=dev)
+    ref = A[rows].float().cpu() @ B.float().cpu().T
+    torch.testing.assert_close(C[rows].cpu(), ref, rtol=1e-4, atol=1e-4 * float(ref.abs().max()))
+    assert not torch.isnan(C).any()
+
+
 def test_gemm_persistent_epilogues(dev):
     M, N, K = 3000, 384, 256
     A, B = _bf((M, K), 7, dev), _bf((N, K), 8, dev)
