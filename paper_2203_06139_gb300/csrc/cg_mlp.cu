@@ -4,14 +4,20 @@
 // accumulation on the 5th-generation tensor cores: one elected thread issues
 // tcgen05.mma (kind::f16, M = 128, N = BN) from shared-memory operands, the
 // accumulator lives in tensor memory (TMEM, allocated per CTA), completion is
-// signalled through an mbarrier, and the epilogue reads the accumulator with
-// tcgen05.ld (warp w of the 4-warp CTA owns TMEM lanes 32w .. 32w + 31, i.e.
-// rows 32w .. 32w + 31 of the tile).  Operands are staged K-major in the
-// canonical no-swizzle layout of 8 x 16-byte core matrices; the loader
-// transposes on the fly, so A and B may each be stored either way round.
-// Every wait on the mbarrier is bounded by a clock budget; on timeout the
-// kernel records an error, waits once more (bounded), frees its TMEM and
-// returns.
+// signalled through mbarriers, and the epilogue reads the accumulator with
+// tcgen05.ld (a warp owns the 32 TMEM lanes of its quarter, i.e. 32 rows of
+// the tile).  Three kernels:
+//  k_gemm_persist  K-major operands, N >= 128: persistent, TMA loads into a
+//                  4-stage ring, two TMEM accumulators (epilogue of one tile
+//                  overlaps the MMAs of the next);
+//  k_gemm_pipe     K-major operands, N < 128: the same TMA ring, one tile per
+//                  CTA;
+//  k_gemm_tc       anything else: operands staged through registers into the
+//                  canonical no-swizzle layout (8 x 16-byte core matrices),
+//                  transposed on the fly, so A and B may be stored either way.
+// Every wait on an mbarrier is bounded by a clock budget; on timeout the
+// kernel records an error, lets its issued copies and MMAs finish (bounded),
+// frees its TMEM and returns.
 #include <algorithm>
 #include <cuda.h>
 #include <cuda_bf16.h>
