@@ -2,8 +2,9 @@
 
 Each case plants one mistake in a copy of oracle/cg_oracle.c (a flipped sign
 in a local partial derivative, a dropped term, a wrong factor, a transposed
-operand), builds it with gcc and runs the pin suite against it in a
-subprocess; at least one pin must fail.  The real oracle is never modified.
+operand), builds it with gcc and runs the pin suites (the model pins and the
+expression-interpreter pins) against it in a subprocess; at least one pin
+must fail.  The real oracle is never modified.
 """
 import os
 import subprocess
@@ -50,6 +51,15 @@ MUTATIONS = {
     # Gauss-Newton matrix: Poisson curvature y/f^2 -> y/f
     "gnmat_poisson_curvature": ("else if (obj == OBJ_POISSON) hi_ = (y[i] > 0.0) ? y[i] / (fv * fv) : 0.0;\n        else hi_ = (y[i] > 0.0) ? 2.0 * y[i] / (fv * fv) : 0.0;\n        for (int32_t a",
                                 "else if (obj == OBJ_POISSON) hi_ = (y[i] > 0.0) ? y[i] / fv : 0.0;\n        else hi_ = (y[i] > 0.0) ? 2.0 * y[i] / (fv * fv) : 0.0;\n        for (int32_t a"),
+    # expression interpreter: d sqrt(a)/da = 1/(2 sqrt a) -> 1/sqrt a
+    "expr_sqrt_partial": ("return push(T, r, a, 0.5 / r, -1, 0.0);", "return push(T, r, a, 1.0 / r, -1, 0.0);"),
+    # expression interpreter: d a^k/da = k a^(k-1) -> k a^k
+    "expr_powi_partial": ("(double)k * pow(x, (double)(k - 1))", "(double)k * pow(x, (double)k)"),
+    # expression interpreter: max sends its adjoint to the smaller operand
+    "expr_max_branch": ("if (VAL(a) >= VAL(b)) return push(T, VAL(a), a, 1.0, b, 0.0);",
+                        "if (VAL(a) >= VAL(b)) return push(T, VAL(a), a, 0.0, b, 1.0);"),
+    # expression interpreter: the element index off by one
+    "expr_index": ("case 3: t[j] = t_const(&T, (double)e); break;", "case 3: t[j] = t_const(&T, (double)(e + 1)); break;"),
     # compensated sum loses its correction
     "neumaier_dropped": ("static double nval(const nsum *acc) { return acc->s + acc->c; }",
                          "static double nval(const nsum *acc) { return acc->s; }"),
@@ -68,6 +78,7 @@ def test_pins_catch_mutation(name, tmp_path):
                            str(msrc), "-lm"])
     env = dict(os.environ, CG_ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")], env=env, cwd=ROOT,
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_expr_cpu.py")], env=env, cwd=ROOT,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, "no pin failed for mutation %s:\n%s" % (name, r.stdout[-2000:])
