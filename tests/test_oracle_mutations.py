@@ -45,6 +45,9 @@ MUTATIONS = {
     # polynomial in t: (2x - lo - hi)/(hi - lo) -> (x - lo)/(hi - lo)
     "poly_t_map": ("double u = (poly_mode == 1) ? (2.0 * x - lo - hi) / (hi - lo) : x;\n        int32_t f = rec_gauss_poly(&T, K, D, x, u);\n        int32_t t = rec_binned_term",
                    "double u = (poly_mode == 1) ? (x - lo) / (hi - lo) : x;\n        int32_t f = rec_gauss_poly(&T, K, D, x, u);\n        int32_t t = rec_binned_term"),
+    # Gauss-Newton diagonal: h J_k^2 -> h J_k
+    "gn_diag_square": ("for (int32_t k = 0; k < P; ++k) nadd(&acc[k], hi_ * adj[k] * adj[k]);",
+                       "for (int32_t k = 0; k < P; ++k) nadd(&acc[k], hi_ * adj[k]);"),
     # Gauss-Newton matrix: J_a J_b -> J_a J_a (the diagonal's product everywhere)
     "gnmat_transposed_factor": ("nadd(&acc[(size_t)a * P + b], hi_ * adj[a] * adj[b]);",
                                 "nadd(&acc[(size_t)a * P + b], hi_ * adj[a] * adj[a]);"),
