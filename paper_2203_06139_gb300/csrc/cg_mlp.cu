@@ -597,6 +597,30 @@ __device__ __forceinline__ void store_block_f32(float* C, int ldc, int M, int ro
     __syncwarp();
 }
 
+// The same for a BF16 output (64 bytes per row): 16-byte slot c of row r kept
+// at c ^ ((r >> 1) & 3) of the row's 4 (conflict-free both ways); each store
+// instruction writes 8 rows of 64 bytes.
+__device__ __forceinline__ void store_block_bf16(__nv_bfloat16* C, int ldc, int M, int row0, int col0,
+                                                 const float (&a)[32], float4* buf, int lane) {
+    uint4* b16 = reinterpret_cast<uint4*>(buf);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        __nv_bfloat162 p[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) p[e] = __floats2bfloat162_rn(a[8 * c + 2 * e], a[8 * c + 2 * e + 1]);
+        b16[lane * 4 + (c ^ ((lane >> 1) & 3))] = *reinterpret_cast<const uint4*>(p);
+    }
+    __syncwarp();
+    const int c = lane & 3;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int r = 8 * k + (lane >> 2);
+        const uint4 val = b16[r * 4 + (c ^ ((r >> 1) & 3))];
+        if (row0 + r < M) *reinterpret_cast<uint4*>(C + (size_t)(row0 + r) * ldc + col0 + 8 * c) = val;
+    }
+    __syncwarp();
+}
+
 template <int BN>
 __global__ void __launch_bounds__(kPipeThreads, 1) k_gemm_persist(const __grid_constant__ CUtensorMap tmA,
                                                                   const __grid_constant__ CUtensorMap tmB,
@@ -755,11 +779,12 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_gemm_persist(const __grid_c
                 const int col0 = n0 + c0;
                 if (col0 >= g.N) continue;
                 const bool vec = aligned && col0 + 32 <= g.N;
-                if (vec && (g.epi == EPI_F32 || g.epi == EPI_BIAS_F32)) {
+                if (vec && g.epi != EPI_GELU_GRAD) {
+                    float4* xb = xpose_all + (warp - 2) * 256;
                     float a[32];
 #pragma unroll
                     for (int j = 0; j < 32; ++j) a[j] = __uint_as_float(v[j]);
-                    if (g.epi == EPI_BIAS_F32) {
+                    if (g.epi != EPI_F32) {   // + bias
 #pragma unroll
                         for (int j = 0; j < 32; j += 4) {
                             const float4 bb = *reinterpret_cast<const float4*>(g.bias + col0 + j);
@@ -769,7 +794,14 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_gemm_persist(const __grid_c
                             a[j + 3] += bb.w;
                         }
                     }
-                    store_block_f32(g.Cf, g.ldc, g.M, m0 + q * 32, col0, a, xpose_all + (warp - 2) * 256, lane);
+                    const int row0 = m0 + q * 32;
+                    if (g.epi == EPI_BIAS_GELU) {
+                        if (g.aux_out) store_block_f32(g.aux_out, g.ldc, g.M, row0, col0, a, xb, lane);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) a[j] = gelu(a[j]);
+                        if (g.Cb) store_block_bf16(g.Cb, g.ldc, g.M, row0, col0, a, xb, lane);
+                    }
+                    if (g.Cf) store_block_f32(g.Cf, g.ldc, g.M, row0, col0, a, xb, lane);
                 } else {
                     epi_segment(g, v, m0 + q * 32 + lane, col0, vec);
                 }
