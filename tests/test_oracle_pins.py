@@ -476,6 +476,26 @@ def test_oracle_lm_reaches_the_bfgs_minimum(obj):
     assert lm["evals"] < ref["evals"]
 
 
+def test_oracle_lm_steps_on_a_separable_quadratic():
+    """F = sum_i a_i (theta_i - t_i)^2 has GN = diag(2a) = its Hessian, so
+    the damped step is -(theta - t) / (1 + lambda): after accepted steps with
+    lambda_j = 1e-3 / 10^j, theta_k - t = (theta_0 - t) prod_j lambda_j /
+    (1 + lambda_j).  Three steps from the start, checked to rounding."""
+    a = np.array([3.0, 0.5, 20.0])
+    t = np.array([1.0, -2.0, 0.25])
+    th0 = np.array([4.0, 1.0, -1.0])
+    fgh = lambda th: (float(np.sum(a * (th - t) ** 2)), 2 * a * (th - t), np.diag(2 * a))
+    one = lm_fit(fgh, th0, max_evals=2, tol=0.0)
+    np.testing.assert_allclose(one["theta"] - t, (th0 - t) * (1e-3 / (1 + 1e-3)), rtol=1e-10)
+    res = lm_fit(fgh, th0, max_evals=4, tol=0.0)
+    factor = np.prod([l / (1 + l) for l in (1e-3, 1e-4, 1e-5)])
+    # theta - t is ~1e-12 here: compare theta itself, to a few units of its rounding
+    np.testing.assert_allclose(res["theta"], t + (th0 - t) * factor, rtol=0, atol=4e-16 * np.abs(t).max() * 4)
+    assert res["iters"] == 3 and res["evals"] == 4
+    assert res["lam"] == max(1e-3 * 0.1 * 0.1 * 0.1, 1e-12)
+    assert abs(res["edm"] - float(np.sum(a * (res["theta"] - t) ** 2))) <= 1e-12 * res["edm"]
+
+
 def test_compensated_sum_of_identical_terms():
     """10^6 identical events: the NLL is N times one event's term to a few
     ulps (a plain running sum drifts by ~N eps / 2 relative)."""
