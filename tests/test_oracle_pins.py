@@ -496,6 +496,18 @@ def test_oracle_lm_steps_on_a_separable_quadratic():
     assert abs(res["edm"] - float(np.sum(a * (res["theta"] - t) ** 2))) <= 1e-12 * res["edm"]
 
 
+def test_oracle_bfgs_first_step_is_newton_on_a_separable_quadratic():
+    """With H_0 = diag(1 / GN) and GN the exact (diagonal) Hessian, the first
+    direction is the Newton step, accepted at alpha = 1 (Armijo holds with
+    F = 0): one iteration, two evaluations, theta = t to rounding."""
+    a = np.array([3.0, 0.5, 20.0, 7.0])
+    t = np.array([1.0, -2.0, 0.25, 3.0])
+    fg = lambda th: (float(np.sum(a * (th - t) ** 2)), 2 * a * (th - t))
+    res = bfgs_fit(fg, lambda th: 2 * a, np.array([4.0, 1.0, -1.0, 0.0]), tol=1e-12)
+    assert res["status"] == CONVERGED and res["iters"] == 1 and res["evals"] == 2
+    np.testing.assert_allclose(res["theta"], t, rtol=0, atol=1e-15 * 4)
+
+
 def test_compensated_sum_of_identical_terms():
     """10^6 identical events: the NLL is N times one event's term to a few
     ulps (a plain running sum drifts by ~N eps / 2 relative)."""
