@@ -42,7 +42,7 @@ RUNNING, CONVERGED, MAX_ITER, LINESEARCH_FAILED = 0, 1, 2, 3
 
 def bfgs_fit(fg, gn, theta0, max_iter=50, tol=1e-9, max_trials=20, c1=1e-4):
     """Minimise F with value+gradient callback fg(theta)->(F, g) and Gauss-Newton
-    diagonal callback gn(theta)->GN.  Returns dict(theta, F, g, iters, evals, status, edm)."""
+    diagonal callback gn(theta)->GN.  Returns dict(theta, F, g, iters, evals, status, edm, H)."""
     theta = np.array(theta0, dtype=np.float64)
     F, g = fg(theta)
     evals = 1
@@ -93,7 +93,7 @@ def bfgs_fit(fg, gn, theta0, max_iter=50, tol=1e-9, max_trials=20, c1=1e-4):
             status = CONVERGED
     if status == RUNNING:
         status = MAX_ITER
-    return dict(theta=theta, F=F, g=g, iters=it, evals=evals, status=status, edm=edm)
+    return dict(theta=theta, F=F, g=g, iters=it, evals=evals, status=status, edm=edm, H=H)
 
 
 def _chol_solve(M, b):

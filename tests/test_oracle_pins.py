@@ -508,6 +508,23 @@ def test_oracle_bfgs_first_step_is_newton_on_a_separable_quadratic():
     np.testing.assert_allclose(res["theta"], t, rtol=0, atol=1e-15 * 4)
 
 
+def test_oracle_bfgs_update_satisfies_the_secant_condition():
+    """After one iteration on F = (theta - t)^T A (theta - t) with a full SPD
+    A, the updated inverse Hessian maps the gradient change to the step
+    (H y = s) and stays symmetric."""
+    r = np.random.default_rng(8)
+    Q = r.normal(size=(5, 5))
+    A = Q @ Q.T + 5 * np.eye(5)
+    t = r.normal(size=5)
+    fg = lambda th: (float((th - t) @ A @ (th - t)), 2 * A @ (th - t))
+    th0 = t + r.normal(size=5)
+    res = bfgs_fit(fg, lambda th: 2 * np.diag(A), th0, max_iter=1, tol=0.0)
+    s = res["theta"] - th0
+    y = res["g"] - fg(th0)[1]
+    np.testing.assert_allclose(res["H"] @ y, s, rtol=1e-10, atol=1e-12 * np.abs(s).max())
+    np.testing.assert_allclose(res["H"], res["H"].T, rtol=1e-12, atol=1e-15)
+
+
 def test_compensated_sum_of_identical_terms():
     """10^6 identical events: the NLL is N times one event's term to a few
     ulps (a plain running sum drifts by ~N eps / 2 relative)."""
