@@ -109,3 +109,34 @@ def test_lm_plan_sizes_and_refusals_without_gpu(lib):
     assert lib.cg_fit_lm_plan(ctypes.byref(b), offs, ctypes.c_void_p(4096), 16, None) == cg.ERR_WORKSPACE
     assert lib.cg_fit_lm_step(ctypes.byref(b), ctypes.c_void_p(4096), 1, 1e-9, ctypes.c_void_p(4097), 1 << 20,
                               None) == cg.ERR_WORKSPACE
+
+
+def test_fit_plan_refusals_without_gpu(lib):
+    """cg_fit_plan checks its map and the host offsets before touching the
+    device: CTA sizes outside 64..512 or not multiples of 32, cluster sizes
+    other than 1/2/4/8, warp_max_bins > cta_max_bins and decreasing offsets
+    are invalid arguments; FP64/df64 only; a too-small workspace is refused."""
+    from paper_2203_06139_gb300 import cg
+    b = cg._Batch()
+    b.tmpl.model, b.tmpl.objective, b.tmpl.precision = cg.MODEL_GAUSS_POLY, cg.OBJ_CHI2, cg.PREC_DF64
+    b.tmpl.n_peaks, b.tmpl.poly_degree = 1, 2
+    b.tmpl.data = 256
+    b.n_hist, b.offsets, b.lo, b.hi = 3, 512, 768, 1024
+    n = lib.cg_fit_workspace_size(ctypes.byref(b))
+    assert n > 0
+    offs = (ctypes.c_int64 * 4)(0, 100, 300, 600)
+    ws = ctypes.c_void_p(4096)
+    good = dict(warp_max_bins=128, cta_max_bins=4096, cta_threads=256, cluster_size=2)
+    for bad in (dict(cta_threads=48), dict(cta_threads=1024), dict(cta_threads=100), dict(cluster_size=3),
+                dict(warp_max_bins=5000)):
+        m = cg._TileMap()
+        for k, v in dict(good, **bad).items():
+            setattr(m, k, v)
+        assert lib.cg_fit_plan(ctypes.byref(b), offs, ctypes.byref(m), ws, n, None) == cg.ERR_INVALID_ARG, bad
+    m = cg._TileMap()
+    for k, v in good.items():
+        setattr(m, k, v)
+    assert lib.cg_fit_plan(ctypes.byref(b), (ctypes.c_int64 * 4)(0, 100, 50, 600), ctypes.byref(m), ws, n,
+                           None) == cg.ERR_INVALID_ARG
+    assert lib.cg_fit_plan(ctypes.byref(b), offs, ctypes.byref(m), ws, n - 1, None) == cg.ERR_WORKSPACE
+    assert lib.cg_fit_plan(ctypes.byref(b), offs, ctypes.byref(m), ctypes.c_void_p(4097), n, None) == cg.ERR_WORKSPACE
