@@ -331,6 +331,18 @@ def test_unbinned_asimov_gradient_vanishes():
     assert np.all(np.abs(r2.grad) > 1e-5 * r2.scale)
 
 
+def test_unbinned_gradient_at_truth_shrinks_like_one_over_sqrt_n():
+    """Events drawn from the model at its truth: the score has mean zero, so
+    the summed gradient grows like sqrt(N) while the sum of per-event |terms|
+    S_k grows like N.  |g_k| <= 5 S_k / sqrt(N) at N = 1e4, 1e5, 1e6 (a
+    normalisation or sampling mistake leaves |g_k| of order S_k)."""
+    truth = synth.C2_TRUTH
+    for n in (10 ** 4, 10 ** 5, 10 ** 6):
+        x = synth.c2_events(n)
+        r = oracle.unbinned_mix(x, 0.0, 10.0, truth)
+        assert np.all(np.abs(r.grad) <= 5.0 * r.scale / math.sqrt(n)), (n, r.grad, r.scale)
+
+
 def test_unbinned_central_fd():
     x = synth.c2_events(5000)
     th = np.array([0.28, 1.9, 0.33, 0.47])
