@@ -31,6 +31,42 @@ def combine(value, grad, group=None):
     return tot[0], tot[1:]
 
 
+def shard_batch(offsets, rank, world):
+    """Histograms [h0, h1) of `rank` for a batch with CSR bin offsets
+    (offsets[H] + 1 entries): contiguous ranges cut where the running bin count
+    first reaches r / world of the total, so every rank's bins are within one
+    histogram's size of total / world."""
+    import numpy as np
+    offsets = np.asarray(offsets, dtype=np.int64)
+    H = len(offsets) - 1
+    total = int(offsets[-1] - offsets[0])
+
+    def cut(r):
+        if r <= 0:
+            return 0
+        if r >= world:
+            return H
+        return int(np.searchsorted(offsets, offsets[0] + total * r / world, side="left"))
+
+    lo = cut(rank)
+    return lo, max(lo, cut(rank + 1))
+
+
+def gather_batch(values, grads, h0, H, group=None):
+    """Every rank's per-histogram results (values [h1 - h0], grads [h1 - h0, P]
+    of its histograms from h0) assembled into [H] and [H, P] on every rank:
+    one all-reduce of zero-padded arrays, exact (each entry is one rank's
+    number plus zeros)."""
+    P = grads.shape[1] if grads.dim() == 2 else 0
+    n = values.numel()
+    full = torch.zeros(H * (1 + P), dtype=torch.float64, device=values.device)
+    full[h0:h0 + n] = values.double()
+    if P:
+        full[H + h0 * P:H + (h0 + n) * P] = grads.double().reshape(-1)
+    dist.all_reduce(full, op=dist.ReduceOp.SUM, group=group)
+    return full[:H], full[H:].reshape(H, P)
+
+
 def max_over_ranks(seconds, group=None, device="cpu"):
     """The slowest rank's time (the job's time)."""
     t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)

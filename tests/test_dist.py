@@ -26,6 +26,20 @@ def test_shard_partitions_exactly():
             assert max(sizes) - min(sizes) <= 1
 
 
+def test_shard_batch_balances_bins():
+    rng = np.random.default_rng(4)
+    for H in (1, 2, 7, 4096):
+        n = np.rint(np.exp(rng.uniform(np.log(64), np.log(65536), H))).astype(np.int64)
+        offs = np.concatenate([[0], np.cumsum(n)])
+        for world in (1, 2, 3, 8):
+            rs = [cgdist.shard_batch(offs, r, world) for r in range(world)]
+            assert rs[0][0] == 0 and rs[-1][1] == H
+            for (a, b), (c, d) in zip(rs, rs[1:]):
+                assert b == c
+            bins = [int(offs[b] - offs[a]) for a, b in rs]
+            assert max(abs(x - offs[-1] / world) for x in bins) <= n.max()
+
+
 def _port():
     s = socket.socket()
     s.bind(("127.0.0.1", 0))
@@ -56,6 +70,39 @@ def _worker(rank, world, port, x, theta, out_dir, mode):
                 dist.destroy_process_group()
             except Exception:
                 pass
+
+
+def _batch_worker(rank, world, port, ys, offs, out_dir):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    import oracle
+    try:
+        h0, h1 = cgdist.shard_batch(offs, rank, world)
+        th = np.array([1000.0, 0.5, 0.05, 50.0, 2.0, -1.0])
+        rs = [oracle.binned1d(1, 2, 1, oracle.CHI2, ys[offs[h]:offs[h + 1]], 0.0, 1.0, th) for h in range(h0, h1)]
+        v = torch.tensor([r.value for r in rs], dtype=torch.float64)
+        g = torch.tensor(np.array([r.grad for r in rs]).reshape(-1, 6), dtype=torch.float64)
+        V, G = cgdist.gather_batch(v, g, h0, len(offs) - 1)
+        np.save(os.path.join(out_dir, "b%d.npy" % rank), np.concatenate([V.numpy(), G.numpy().reshape(-1)]))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_batch_equals_single_process(tmp_path):
+    """Histograms split by bins over two gloo ranks, each evaluating its own
+    (CPU oracle here), gathered: bit-identical to one process."""
+    import oracle
+    from paper_2203_06139_gb300 import synth
+    d = synth.c4_batch(H=9, max_bins=3000)
+    ys, offs = d["y"], d["offsets"]
+    mp.start_processes(_batch_worker, args=(2, _port(), ys, offs, str(tmp_path)), nprocs=2, start_method="spawn")
+    b0, b1 = np.load(tmp_path / "b0.npy"), np.load(tmp_path / "b1.npy")
+    assert np.array_equal(b0, b1)
+    th = np.array([1000.0, 0.5, 0.05, 50.0, 2.0, -1.0])
+    ref = [oracle.binned1d(1, 2, 1, oracle.CHI2, ys[offs[h]:offs[h + 1]], 0.0, 1.0, th) for h in range(9)]
+    assert np.array_equal(b0[:9], np.array([r.value for r in ref]))
+    assert np.array_equal(b0[9:].reshape(9, 6), np.array([r.grad for r in ref]))
 
 
 def test_two_ranks_sum_equals_single_process(tmp_path):
