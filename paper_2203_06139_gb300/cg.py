@@ -282,3 +282,9 @@ def batch_objective(pb, thetas, values=None, stream=None):
     _check(lib().cg_batch_gradient(ctypes.byref(b), _ptr(thetas), _ptr(values), None, _ptr(ws), ws.numel(),
                                    _stream(stream)), "cg_batch_gradient (values)")
     return values
+
+
+# The calls of include/cg.h under their C names (the fitting calls are in fit.py).
+cg_objective = objective
+cg_gradient = gradient
+cg_batch_gradient = batch_gradient

@@ -382,3 +382,19 @@ def autotune(batch, theta0, candidates=None, n_steps=5, tol=1e-9, use_cache=True
         except OSError:
             pass
     return best, timings
+
+
+# The fitting calls of include/cg.h under their C names.
+def cg_fit_step(fitter, n_steps=50, tol=1e-9):
+    """cg_fit_step on a BatchFitter's batch, plan and states."""
+    return fitter.step(n_steps, tol)
+
+
+def cg_fit_lm_step(fitter, n_steps=30, tol=1e-9):
+    """cg_fit_lm_step on an LMFitter's batch, plan and states."""
+    return fitter.step(n_steps, tol)
+
+
+def cg_batch_gn(batch, thetas):
+    """cg_batch_gn: value, gradient and Gauss-Newton matrix of every histogram."""
+    return batch.gauss_newton(thetas)

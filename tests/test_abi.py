@@ -140,3 +140,11 @@ def test_fit_plan_refusals_without_gpu(lib):
                            None) == cg.ERR_INVALID_ARG
     assert lib.cg_fit_plan(ctypes.byref(b), offs, ctypes.byref(m), ws, n - 1, None) == cg.ERR_WORKSPACE
     assert lib.cg_fit_plan(ctypes.byref(b), offs, ctypes.byref(m), ctypes.c_void_p(4097), n, None) == cg.ERR_WORKSPACE
+
+
+def test_python_binding_has_the_c_names():
+    from paper_2203_06139_gb300 import cg, fit
+    for n in ("cg_objective", "cg_gradient", "cg_batch_gradient"):
+        assert callable(getattr(cg, n))
+    for n in ("cg_fit_step", "cg_fit_lm_step", "cg_batch_gn"):
+        assert callable(getattr(fit, n))
