@@ -374,16 +374,18 @@ cg_status cg_fit_step(const cg_batch *b, const cg_tile_map *map, cg_fit_state *s
  * second derivatives Sec. 4 says the minimiser still takes by finite
  * differences, here from the same reverse sweep); T'' = 2/max(y,1)
  * for chi2, y/f^2 for Poisson, 2 y/f^2 for Baker-Cousins.  The products are
- * accumulated in FP32 (relative error about 1e-6 of sqrt(GN_aa GN_bb)); the
- * value and gradient are the df64 ones.  value[h] is NaN where the model
+ * accumulated in FP32: with m bins per thread an entry is within about
+ * (m + 8) 2^-24 sqrt(GN_aa GN_bb) (1e-5 at 20,000 bins); the value and
+ * gradient are the df64 ones.  value[h] is NaN where the model
  * leaves its domain or the histogram has 2^24 bins or more.  ws: >= 256
  * bytes, 256-byte aligned (unused; reserved). */
 cg_status cg_batch_gn(const cg_batch *b, const double *theta, double *value, double *grad, double *gn,
                       void *ws, size_t ws_bytes, void *stream);
 
 /* Levenberg-Marquardt fits of every histogram of a df64 batch, a second-order
- * alternative to cg_fit_step: each step is one cg_batch_gn-style launch at the
- * trial points plus a control kernel (one warp per histogram).  A trial is
+ * alternative to cg_fit_step: each step evaluates value, gradient and the
+ * Gauss-Newton matrix at the trial points (tiled, below) and runs the control,
+ * one warp per histogram.  A trial is
  * accepted when F(trial) < F; then lambda /= 10 (floor 1e-12), otherwise
  * lambda *= 10 (CG_FIT_LINESEARCH_FAILED past 1e16); the next trial is
  * theta + delta with (GN + lambda diag(GN)) delta = -g solved by Cholesky
@@ -392,8 +394,8 @@ cg_status cg_batch_gn(const cg_batch *b, const double *theta, double *value, dou
  * tol max(1, |F|), GN the undamped matrix at theta.  state[h].hinv holds GN
  * (not an inverse), h0[0] lambda; iter counts accepted steps, n_eval
  * evaluations; a fit that has not converged after the last step keeps
- * CG_FIT_RUNNING (more steps continue it).  init evaluates theta0 [n_hist][P] (device) and sets lambda =
- * 1e-3.  Capturable in a CUDA graph.
+ * CG_FIT_RUNNING (more steps continue it).  init evaluates theta0
+ * [n_hist][P] (device) and sets lambda = 1e-3.  Capturable in a CUDA graph.
  * Evaluation: the plan cuts every histogram into tiles of at most 16384 bins
  * (histograms by decreasing size); per step, CTAs take tiles from a counter
  * and write one partial row per tile (df64 value and gradient sums, a domain
