@@ -887,6 +887,7 @@ cg_status launch_gemm_persist(const GemmArgs& g, cudaStream_t st) {
         cudaSuccess)
         return CG_ERR_CUDA;
     const long long tiles = (long long)((g.N + BN - 1) / BN) * ((g.M + kTM - 1) / kTM);
+    if (tiles >= INT32_MAX) return CG_ERR_UNSUPPORTED;   // the kernel counts tiles in int
     const int sms = device_sm_count();
     const int grid = (int)(tiles < sms ? tiles : sms);   // one CTA per SM (shared memory and TMEM)
     k_gemm_persist<BN><<<grid, kPipeThreads, L::TOTAL, st>>>(ta, tb, g);
