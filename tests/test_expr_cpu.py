@@ -126,3 +126,27 @@ def test_value_only_source_has_no_reverse_sweep():
     assert "#define NACC 1" in vo and " g" not in vo.split("cgx_finalize")[0].split("acc[0] +=")[1]
     assert "grad[" in full and "grad[" not in vo
 
+
+
+def test_accumulator_limit_on_the_host():
+    """Up to 127 frontier adjoints (+ the value) per thread: the 32-peak
+    program (99 accumulators) and 126 frontier nodes (127) get their source;
+    128 frontier nodes are refused by the host-side validation (no handle,
+    no source)."""
+    import pytest
+    from paper_2203_06139_gb300 import cg
+    K, n = 32, 100
+    x = (E.index() + 0.5) * (1.0 / n)
+    f = E.param(3 * K) + E.param(3 * K + 1) * x
+    for k in range(K):
+        f = f + E.param(3 * k) * E.exp(-(x - E.param(3 * k + 1)) ** 2 / (2.0 * E.param(3 * k + 2) ** 2))
+    src = E.generated_source((E.inp(0) - f) ** 2, 3 * K + 2, 1)
+    assert "#define NACC 99" in src
+    def two_per_param(m):   # p_k and p_k^2 both multiply the element: 2m frontier nodes
+        e = E.const(0.0)
+        for k in range(m):
+            e = e + E.param(k) * E.inp(0) + (E.param(k) * E.param(k)) * E.index()
+        return e
+    assert "#define NACC 127" in E.generated_source(two_per_param(63), 63, 1)
+    with pytest.raises(cg.CgError):
+        E.generated_source(two_per_param(64), 64, 1)
