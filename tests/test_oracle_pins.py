@@ -537,6 +537,33 @@ def test_oracle_bfgs_update_satisfies_the_secant_condition():
     np.testing.assert_allclose(res["H"], res["H"].T, rtol=1e-12, atol=1e-15)
 
 
+def test_fig3a_fit_recovers_the_generating_gaussian():
+    """Fig. 3a's histogram (1000 bins on [-5, 5], 10^5 draws of a Gaussian of
+    mean 1 and width 3 within the range): the oracle's fits return the
+    generating shape.  Peak height per bin = 10^5 x 0.01 x phi(0) / 3 / P(range)
+    = 150.1; mu and s within 5 standard errors (s / sqrt(N) and s / sqrt(2N));
+    the Baker-Cousins (maximum-likelihood) height within 2 %, the chi2 one
+    within 4 % (the 1/max(y, 1) weights pull it low); chi2 / ndf sane."""
+    from scipy.special import ndtr
+    h = synth.fig3a_histogram()
+    y = h["y"]
+    mass = ndtr(4.0 / 3.0) - ndtr(-2.0)
+    A_true = 1e5 * 0.01 / (3.0 * math.sqrt(2 * math.pi)) / mass
+    n_eff = y.sum()
+    for obj, tolA in ((oracle.CHI2, 0.04), (oracle.POISSON_BC, 0.02)):
+        fg = lambda t: (lambda q: (q.value, q.grad))(oracle.binned1d(1, -1, 0, obj, y, -5.0, 5.0, t))
+        gn = lambda t: oracle.binned1d_gn(1, -1, 0, obj, y, -5.0, 5.0, t)
+        res = bfgs_fit(fg, gn, np.array([120.0, 0.5, 2.5]), max_iter=200, tol=1e-12)
+        assert res["status"] == CONVERGED
+        A, mu, sg = res["theta"]
+        assert abs(mu - 1.0) <= 5 * 3.0 / math.sqrt(n_eff)
+        assert abs(abs(sg) - 3.0) <= 5 * 3.0 / math.sqrt(2 * n_eff)
+        assert abs(A - A_true) <= tolA * A_true, (obj, A, A_true)
+        if obj == oracle.CHI2:
+            ndf = y.size - 3
+            assert abs(res["F"] / ndf - 1) < 5 * math.sqrt(2 / ndf)
+
+
 def test_compensated_sum_of_identical_terms():
     """10^6 identical events: the NLL is N times one event's term to a few
     ulps (a plain running sum drifts by ~N eps / 2 relative)."""
