@@ -85,3 +85,40 @@ def test_pins_catch_mutation(name, tmp_path):
                         os.path.join(ROOT, "tests", "test_expr_cpu.py")], env=env, cwd=ROOT,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, "no pin failed for mutation %s:\n%s" % (name, r.stdout[-2000:])
+
+
+# Planted mistakes in copies of the fit drivers (oracle/fit.py), each caught
+# by the drivers' closed-form pins.
+FIT_SRC = os.path.join(ROOT, "oracle", "fit.py")
+FIT_MUTATIONS = {
+    # BFGS inverse update with the outer products transposed
+    "bfgs_update_transposed": ("H = (I - r * np.outer(s, y)) @ H @ (I - r * np.outer(y, s)) + r * np.outer(s, s)",
+                               "H = (I - r * np.outer(y, s)) @ H @ (I - r * np.outer(s, y)) + r * np.outer(s, s)",
+                               "check_bfgs_secant"),
+    # initial inverse Hessian = GN instead of 1 / GN
+    "bfgs_h0_not_inverted": ("Hdiag = np.where(d0 > 0, 1.0 / np.where(d0 > 0, d0, 1.0), 1.0)",
+                             "Hdiag = np.where(d0 > 0, np.where(d0 > 0, d0, 1.0), 1.0)",
+                             "check_bfgs_first_step_is_newton"),
+    # damping relaxed by 2 instead of 10 after an accepted step
+    "lm_damping_factor": ("lam = max(lam * 0.1, 1e-12)", "lam = max(lam * 0.5, 1e-12)",
+                          "check_lm_steps_on_a_separable_quadratic"),
+    # step towards larger F
+    "lm_step_sign": ("delta = _chol_solve(G + lam * np.diag(dpos), -g)", "delta = _chol_solve(G + lam * np.diag(dpos), g)",
+                     "check_lm_steps_on_a_separable_quadratic"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(FIT_MUTATIONS))
+def test_fit_pins_catch_mutation(name):
+    import types
+    import oracle.fit as real
+    from tests import test_oracle_pins as pins
+    old, new, check = FIT_MUTATIONS[name]
+    src = open(FIT_SRC).read()
+    assert src.count(old) == 1, "mutation anchor not found: " + name
+    mod = types.ModuleType("fit_mutated")
+    exec(compile(src.replace(old, new), "fit_mutated", "exec"), mod.__dict__)
+    which = "lm_fit" if check.startswith("check_lm") else "bfgs_fit"
+    getattr(pins, check)(getattr(real, which))          # the real driver passes
+    with pytest.raises(AssertionError):
+        getattr(pins, check)(getattr(mod, which))       # the planted mistake does not

@@ -488,7 +488,7 @@ def test_oracle_lm_reaches_the_bfgs_minimum(obj):
     assert lm["evals"] < ref["evals"]
 
 
-def test_oracle_lm_steps_on_a_separable_quadratic():
+def check_lm_steps_on_a_separable_quadratic(lm_fit):
     """F = sum_i a_i (theta_i - t_i)^2 has GN = diag(2a) = its Hessian, so
     the damped step is -(theta - t) / (1 + lambda): after accepted steps with
     lambda_j = 1e-3 / 10^j, theta_k - t = (theta_0 - t) prod_j lambda_j /
@@ -508,7 +508,11 @@ def test_oracle_lm_steps_on_a_separable_quadratic():
     assert abs(res["edm"] - float(np.sum(a * (res["theta"] - t) ** 2))) <= 1e-12 * res["edm"]
 
 
-def test_oracle_bfgs_first_step_is_newton_on_a_separable_quadratic():
+def test_oracle_lm_steps_on_a_separable_quadratic():
+    check_lm_steps_on_a_separable_quadratic(lm_fit)
+
+
+def check_bfgs_first_step_is_newton(bfgs_fit):
     """With H_0 = diag(1 / GN) and GN the exact (diagonal) Hessian, the first
     direction is the Newton step, accepted at alpha = 1 (Armijo holds with
     F = 0): one iteration, two evaluations, theta = t to rounding."""
@@ -520,7 +524,11 @@ def test_oracle_bfgs_first_step_is_newton_on_a_separable_quadratic():
     np.testing.assert_allclose(res["theta"], t, rtol=0, atol=1e-15 * 4)
 
 
-def test_oracle_bfgs_update_satisfies_the_secant_condition():
+def test_oracle_bfgs_first_step_is_newton_on_a_separable_quadratic():
+    check_bfgs_first_step_is_newton(bfgs_fit)
+
+
+def check_bfgs_secant(bfgs_fit):
     """After one iteration on F = (theta - t)^T A (theta - t) with a full SPD
     A, the updated inverse Hessian maps the gradient change to the step
     (H y = s) and stays symmetric."""
@@ -535,6 +543,10 @@ def test_oracle_bfgs_update_satisfies_the_secant_condition():
     y = res["g"] - fg(th0)[1]
     np.testing.assert_allclose(res["H"] @ y, s, rtol=1e-10, atol=1e-12 * np.abs(s).max())
     np.testing.assert_allclose(res["H"], res["H"].T, rtol=1e-12, atol=1e-15)
+
+
+def test_oracle_bfgs_update_satisfies_the_secant_condition():
+    check_bfgs_secant(bfgs_fit)
 
 
 def test_fig3a_fit_recovers_the_generating_gaussian():
