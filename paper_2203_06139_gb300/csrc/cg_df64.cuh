@@ -18,8 +18,9 @@
 //    16(4), 1990: p = 2^E m, F = 1 + (2j+1)/128 nearest m, log p = E ln2 +
 //    log F + log1p((m - F)/F), log1p from its Taylor series;
 //  - reciprocal: one Newton step in df64 from a float estimate.
-// The tables (2^(j/64), log F, 1/F) are computed at block start in FP64 with
-// the CUDA math library and split into float pairs.
+// The tables (2^(j/64), log F, 1/F) are generated offline as float pairs
+// from 60-digit mpmath values (gen_df64_tables.py, cg_df64_tables.inc) and
+// copied into shared memory at block start by df_tables_init.
 //
 // Every float operation below is written with explicit round-to-nearest
 // intrinsics (or fmaf) so the compiler cannot contract or reorder the

@@ -1244,18 +1244,10 @@ __global__ void __launch_bounds__(128) k_lm_finish(FitArgs a, int first) {
     lm_control_warp(s, tt, fsh[w], lane < a.P ? gsh[w][lane] : 0.0, G, a.P, a.tol, first != 0, lane);
 }
 
-template <typename F>
-static int lm_blocks_per_sm(F kern, int threads) {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, 0) != cudaSuccess || n < 1) n = 1;
-    return n;
-}
-
 template <int K, int OBJ>
 static cg_status lm_launch_k(const FitArgs& a, int first, bool tiles, cudaStream_t st) {
     if (tiles) {
-        static int occ = 0;
-        if (occ == 0) occ = lm_blocks_per_sm(k_lm_tiles<K, OBJ>, 256);
+        const int occ = resident_blocks((const void*)k_lm_tiles<K, OBJ>, 256, 0);
         k_lm_tiles<K, OBJ><<<device_sm_count() * occ, 256, 0, st>>>(a);
     } else {
         k_lm_finish<K, OBJ><<<(unsigned)((a.H + 3) / 4), 128, 0, st>>>(a, first);
@@ -1383,27 +1375,16 @@ FitArgs base_args(const cg_batch* b) {
     return a;
 }
 
-// Resident CTAs of 256 threads per SM for a k_fit_eval instantiation (the
-// size of a grid that takes its histograms from a queue).
-template <typename F>
-static int eval_blocks_per_sm(F kern) {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 256, 0) != cudaSuccess || n < 1) n = 1;
-    return n;
-}
-
 template <int K, int OBJ>
 cg_status launch_eval_k(const FitArgs& a, int mode, int prec, cudaStream_t st) {
     int G = device_sm_count() * 4;
     const bool df = prec == CG_PREC_DF64;
     if (a.order && df) {   // one wave of resident CTAs pulling from the queue
-        static int occ[5] = {0, 0, 0, 0, 0};
-        if (mode >= 0 && mode < 5 && occ[mode] == 0) {
-            if (mode == 1) occ[1] = eval_blocks_per_sm(k_fit_eval<K, OBJ, CG_PREC_DF64, 1>);
-            else if (mode == 4) occ[4] = eval_blocks_per_sm(k_fit_eval<K, OBJ, CG_PREC_DF64, 4>);
-            else occ[mode] = 4;
-        }
-        G = device_sm_count() * ((mode >= 0 && mode < 5) ? occ[mode] : 4);
+        // resident CTAs of 256 threads per SM (per device, cached)
+        int occ = 4;
+        if (mode == 1) occ = resident_blocks((const void*)k_fit_eval<K, OBJ, CG_PREC_DF64, 1>, 256, 0);
+        else if (mode == 4) occ = resident_blocks((const void*)k_fit_eval<K, OBJ, CG_PREC_DF64, 4>, 256, 0);
+        G = device_sm_count() * occ;
     }
     const int grid = (int)(a.H < G ? a.H : G);
     if (mode == 0) {

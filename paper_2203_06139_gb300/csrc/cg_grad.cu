@@ -30,6 +30,7 @@
 
 #include "cg_internal.cuh"
 #include "cg_models.cuh"
+#include "cg_models_fp64.cuh"
 #include "cg_tiles.cuh"
 
 namespace cg {
@@ -48,73 +49,128 @@ int device_sm_count() {
 // Tile accumulation kernels
 // ---------------------------------------------------------------------------
 
-template <int K, int OBJ, int NT>
+// Write the partial sums of the np points of one tile: part[(th * (NACC + 1)
+// + a) * nbx + c] for th = th0 .. th0 + np - 1; entry NACC is the point's
+// domain flag (bit pt of badm).
+template <int NACC, int NT>
+__device__ __forceinline__ void write_partials(double* __restrict__ part, const TileGrid& tg, int th0, int np, int c,
+                                               const double* tot, int badm) {
+    for (int k = threadIdx.x; k < np * (NACC + 1); k += NT) {
+        const int pt = k / (NACC + 1), a = k - pt * (NACC + 1);
+        part[((size_t)(th0 + pt) * (NACC + 1) + a) * tg.nbx + c] =
+            (a < NACC) ? tot[pt * NACC + a] : (((badm >> pt) & 1) ? 1.0 : 0.0);
+    }
+}
+
+// True when x is infinite or NaN (integer test of the exponent field).
+__device__ __forceinline__ bool nonfinite(double x) { return (__double2hiint(x) & 0x7ff00000) == 0x7ff00000; }
+
+// 1-D Gaussian peaks + polynomial, FP64.  A tile is (PT consecutive
+// parameter points, one chunk of bins); every bin's point-independent part
+// is taken once and reused for the PT points.  In a ragged last group the
+// missing points repeat the group's first point and are not written.
+template <int K, int OBJ, int PT, int NT>
 __global__ void __launch_bounds__(NT) k_gp1_fp64(GP1Data d, const double* __restrict__ theta,
                                                  TileGrid tg, double* __restrict__ part,
                                                  WsHeader* __restrict__ hdr) {
-    constexpr int NACC = GP1Acc<K>::N;
-    __shared__ GP1Consts cs;
-    __shared__ int cs_bad;
-    __shared__ double red[NACC * (NT / 32)];
-    __shared__ double tot[NACC];
+    constexpr int N = GP1Acc<K>::N;
+    __shared__ Fp64Tab tab;
+    __shared__ GP1Consts cs[PT];
+    __shared__ GP1C2 cq[PT];
+    __shared__ int s_badm;
+    __shared__ double red[N * PT * (NT / 32)];
+    __shared__ double tot[N * PT];
     if (gated_off(tg)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
+    fp64_tab_load(tab);
     const int P = 3 * K + d.D + 1;
     for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
-        const int c = t / tg.n_theta, th = t - c * tg.n_theta;   // chunk-major: a chunk stays in L2 across points
-        if (threadIdx.x == 0) cs_bad = gp1_prologue<K>(theta + (size_t)th * P, d.D, cs) ? 0 : 1;
+        const int c = t / tg.n_theta, grp = t - c * tg.n_theta;   // chunk-major: a chunk stays in L2 across points
+        const int th0 = grp * PT;
+        const int np = min(PT, tg.n_pts - th0);
+        if (threadIdx.x == 0) s_badm = 0;
         __syncthreads();
-        double acc[NACC];
+        if (threadIdx.x < PT) {
+            const int pt = threadIdx.x;
+            const bool ok = gp1_prologue<K>(theta + (size_t)(th0 + (pt < np ? pt : 0)) * P, d.D, cs[pt]);
+            gp1_c2(cs[pt], K, cq[pt]);
+            if (!ok && pt < np) atomicOr(&s_badm, 1 << pt);
+        }
+        __syncthreads();
+        double acc[PT][N];
 #pragma unroll
-        for (int a = 0; a < NACC; ++a) acc[a] = 0.0;
-        bool bad = false;
+        for (int p = 0; p < PT; ++p)
+#pragma unroll
+            for (int a = 0; a < N; ++a) acc[p][a] = 0.0;
+        bool bad[PT];
+#pragma unroll
+        for (int p = 0; p < PT; ++p) bad[p] = false;
+        auto bin = [&](double x, double y) {
+            const GP1Bin b = gp1_bin<OBJ>(x, y, d, tab);
+#pragma unroll
+            for (int p = 0; p < PT; ++p) gp1_elem_f64<K, OBJ>(b, cs[p], cq[p], d.D, tab, acc[p], bad[p]);
+        };
         const int64_t e0 = (int64_t)c * tg.chunk;
         const int64_t e1 = min(tg.n_elem, e0 + tg.chunk);
         if (d.vec_ok) {
-            // two consecutive bins per thread with one 16-byte load of the counts
+            // two consecutive bins per thread with one 16-byte load of the counts (e0 is even)
             for (int64_t i = e0 + 2 * threadIdx.x; i < e1; i += 2 * NT) {
                 if (i + 1 < e1) {
                     const double2 y2 = __ldg(reinterpret_cast<const double2*>(d.y + i));
                     double2 x2;
                     if (d.centres) x2 = __ldg(reinterpret_cast<const double2*>(d.centres + i));
                     else { x2.x = fma((double)i + 0.5, d.h, d.lo); x2.y = fma((double)i + 1.5, d.h, d.lo); }
-                    gp1_elem_fp64<K, OBJ>(x2.x, y2.x, cs, d, acc, bad);
-                    gp1_elem_fp64<K, OBJ>(x2.y, y2.y, cs, d, acc, bad);
+                    bin(x2.x, y2.x);
+                    bin(x2.y, y2.y);
                 } else {
-                    const double x = d.centres ? d.centres[i] : fma((double)i + 0.5, d.h, d.lo);
-                    gp1_elem_fp64<K, OBJ>(x, d.y[i], cs, d, acc, bad);
+                    bin(d.centres ? d.centres[i] : fma((double)i + 0.5, d.h, d.lo), d.y[i]);
                 }
             }
         } else {
-            for (int64_t i = e0 + threadIdx.x; i < e1; i += NT) {
-                const double x = d.centres ? d.centres[i] : fma((double)i + 0.5, d.h, d.lo);
-                gp1_elem_fp64<K, OBJ>(x, d.y[i], cs, d, acc, bad);
-            }
+            for (int64_t i = e0 + threadIdx.x; i < e1; i += NT)
+                bin(d.centres ? d.centres[i] : fma((double)i + 0.5, d.h, d.lo), d.y[i]);
         }
-        const int any_bad = __syncthreads_or(bad ? 1 : 0) | cs_bad;
-        block_sum<NACC, NT>(acc, red, tot);
-        write_partial<NACC>(part, tg, th, c, tot, any_bad);
+        int bm = 0;
+#pragma unroll
+        for (int p = 0; p < PT; ++p) {
+            gp1_tile_scale<K, OBJ>(acc[p]);
+            if (bad[p] || nonfinite(acc[p][0])) bm |= 1 << p;
+        }
+        if (bm) atomicOr(&s_badm, bm);
+        __syncthreads();
+        const int badm = s_badm;
+        block_sum<N * PT, NT>(reinterpret_cast<const double(&)[N * PT]>(acc), red, tot);
+        write_partials<N, NT>(part, tg, th0, np, c, tot, badm);
     }
 }
 
+// Unbinned Gaussian + exponential mixture, FP64: one point per tile.
 template <bool W, int NT>
 __global__ void __launch_bounds__(NT) k_mix_fp64(MixData d, const double* __restrict__ theta,
                                                  TileGrid tg, double* __restrict__ part,
                                                  WsHeader* __restrict__ hdr) {
     constexpr int NACC = MixAcc::N;
+    __shared__ Fp64Tab tab;
     __shared__ MixConsts cs;
+    __shared__ MixC2 cq;
     __shared__ int cs_bad;
     __shared__ double red[NACC * (NT / 32)];
     __shared__ double tot[NACC];
     if (gated_off(tg)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
+    fp64_tab_load(tab);
     for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
         const int c = t / tg.n_theta, th = t - c * tg.n_theta;   // chunk-major: a chunk stays in L2 across points
-        if (threadIdx.x == 0) cs_bad = mix_prologue(theta + (size_t)th * 4, d.lo, d.hi, cs) ? 0 : 1;
+        if (threadIdx.x == 0) {
+            cs_bad = mix_prologue(theta + (size_t)th * 4, d.lo, d.hi, cs) ? 0 : 1;
+            mix_c2(cs, cq);
+        }
         __syncthreads();
         double acc[NACC];
 #pragma unroll
         for (int a = 0; a < NACC; ++a) acc[a] = 0.0;
+        LogProd lp;
+        logprod_init(lp);
         bool bad = false;
         const int64_t e0 = (int64_t)c * tg.chunk;
         const int64_t e1 = min(tg.n_elem, e0 + tg.chunk);
@@ -124,16 +180,17 @@ __global__ void __launch_bounds__(NT) k_mix_fp64(MixData d, const double* __rest
                     const double2 x2 = __ldg(reinterpret_cast<const double2*>(d.x + i));
                     double2 w2 = make_double2(1.0, 1.0);
                     if (W) w2 = __ldg(reinterpret_cast<const double2*>(d.w + i));
-                    mix_elem_fp64<W>(x2.x, w2.x, cs, acc, bad);
-                    mix_elem_fp64<W>(x2.y, w2.y, cs, acc, bad);
+                    mix_elem_f64<W>(x2.x, w2.x, cs, cq, tab, acc, lp, bad);
+                    mix_elem_f64<W>(x2.y, w2.y, cs, cq, tab, acc, lp, bad);
                 } else {
-                    mix_elem_fp64<W>(d.x[i], W ? d.w[i] : 1.0, cs, acc, bad);
+                    mix_elem_f64<W>(d.x[i], W ? d.w[i] : 1.0, cs, cq, tab, acc, lp, bad);
                 }
             }
         } else {
             for (int64_t i = e0 + threadIdx.x; i < e1; i += NT)
-                mix_elem_fp64<W>(d.x[i], W ? d.w[i] : 1.0, cs, acc, bad);
+                mix_elem_f64<W>(d.x[i], W ? d.w[i] : 1.0, cs, cq, tab, acc, lp, bad);
         }
+        if (!W) acc[0] += logprod_log(lp, tab);
         const int any_bad = __syncthreads_or(bad ? 1 : 0) | cs_bad;
         block_sum<NACC, NT>(acc, red, tot);
         write_partial<NACC>(part, tg, th, c, tot, any_bad);
@@ -154,13 +211,16 @@ __global__ void __launch_bounds__(NT) k_rg2_fp64(RG2Data d, const double* __rest
                                                  TileGrid tg, double* __restrict__ part,
                                                  WsHeader* __restrict__ hdr) {
     constexpr int NACC = RG2Acc<K>::N;
+    __shared__ Fp64Tab tab;
     __shared__ RG2Consts cs;
+    __shared__ RG2Q cq;
     __shared__ int cs_bad;
     __shared__ unsigned act_s;
     __shared__ double red[NACC * (NT / 32)];
     __shared__ double tot[NACC];
     if (gated_off(tg)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
+    fp64_tab_load(tab);
     const int P = 6 * K + 1;
     const int ntx = (int)((d.nx + kRgTX - 1) / kRgTX);
     for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
@@ -171,6 +231,7 @@ __global__ void __launch_bounds__(NT) k_rg2_fp64(RG2Data d, const double* __rest
         if (threadIdx.x == 0) {
             const double* tht = theta + (size_t)th * P;
             cs_bad = rg2_prologue<K>(tht, cs) ? 0 : 1;
+            rg2_q<K>(cs, cq);
             // box of bin centres of this tile
             const double bx0 = fma((double)x0 + 0.5, d.hx, d.lx), bx1 = fma((double)(x1 - 1) + 0.5, d.hx, d.lx);
             const double by0 = fma((double)y0 + 0.5, d.hy, d.ly), by1 = fma((double)(y1 - 1) + 0.5, d.hy, d.ly);
@@ -198,10 +259,14 @@ __global__ void __launch_bounds__(NT) k_rg2_fp64(RG2Data d, const double* __rest
             const int64_t ix = x0 + col, iy = y0 + r;
             const double xc = fma((double)ix + 0.5, d.hx, d.lx);
             const double yc = fma((double)iy + 0.5, d.hy, d.ly);
-            rg2_elem_fp64<K>(xc, yc, __ldg(d.n + iy * d.nx + ix), cs, act, acc, bad);
+            rg2_elem_f64<K>(xc, yc, __ldg(d.n + iy * d.nx + ix), cs, cq, act, tab, acc, bad);
         }
+        bad |= nonfinite(acc[0]);
         const int any_bad = __syncthreads_or(bad ? 1 : 0) | cs_bad;
         block_sum<NACC, NT>(acc, red, tot);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < K; ++k) rg2_rotate_moments(tot + 1 + 6 * k, cs.cs[k], cs.sn[k]);
+        __syncthreads();
         write_partial<NACC>(part, tg, th, c, tot, any_bad);
     }
 }
@@ -314,17 +379,27 @@ size_t grad_workspace_bytes(const cg_problem* pb, int64_t n_theta) {
            df64_split_bytes(pb);
 }
 
+// Points per tile of the 1-D FP64 kernel: 4 for models of at most one peak
+// (their per-thread sums stay in registers), else 1.
 template <int K>
 static cg_status launch_gp1_k(const cg_problem* pb, const GP1Data& d, const double* theta, int64_t n_theta,
                               double* part, WsHeader* hdr, TileGrid* tg, cudaStream_t st, const int* gate) {
-    constexpr int NT = 256;
+    constexpr int NT = 128;
     const int64_t n = pb->n_bins[0];
+    constexpr int PTM = (K <= 1) ? 4 : 1;
+    const bool multi = PTM > 1 && n_theta >= PTM;
+#define CG_GP1_LAUNCH(OO)                                                                                        \
+    return multi ? launch_tiles_balanced(k_gp1_fp64<K, OO, PTM, NT>, NT, PTM, d, theta, n, n_theta, part, hdr, tg, \
+                                         st, gate)                                                               \
+                 : launch_tiles_balanced(k_gp1_fp64<K, OO, 1, NT>, NT, 1, d, theta, n, n_theta, part, hdr, tg, st, \
+                                         gate);
     switch (pb->objective) {
-        case CG_OBJ_CHI2: return launch_tiles(k_gp1_fp64<K, CG_OBJ_CHI2, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st, gate);
-        case CG_OBJ_POISSON: return launch_tiles(k_gp1_fp64<K, CG_OBJ_POISSON, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st, gate);
-        case CG_OBJ_POISSON_BC: return launch_tiles(k_gp1_fp64<K, CG_OBJ_POISSON_BC, NT>, NT, d, theta, n, n_theta, part, hdr, tg, st, gate);
+        case CG_OBJ_CHI2: CG_GP1_LAUNCH(CG_OBJ_CHI2)
+        case CG_OBJ_POISSON: CG_GP1_LAUNCH(CG_OBJ_POISSON)
+        case CG_OBJ_POISSON_BC: CG_GP1_LAUNCH(CG_OBJ_POISSON_BC)
         default: return CG_ERR_UNSUPPORTED;
     }
+#undef CG_GP1_LAUNCH
 }
 
 template <int K>
@@ -411,8 +486,10 @@ cg_status grad_points(const cg_problem* pb, const double* theta, int64_t n_theta
         d.hi = pb->hi[0];
         d.vec_ok = (((uintptr_t)pb->data & 15) == 0) && (!pb->weights || (((uintptr_t)pb->weights & 15) == 0));
         constexpr int NT = 256;
-        if (pb->weights) s = launch_tiles(k_mix_fp64<true, NT>, NT, d, theta, n, n_theta, part, hdr, &tg, st, gate);
-        else s = launch_tiles(k_mix_fp64<false, NT>, NT, d, theta, n, n_theta, part, hdr, &tg, st, gate);
+        if (pb->weights)
+            s = launch_tiles_balanced(k_mix_fp64<true, NT>, NT, 1, d, theta, n, n_theta, part, hdr, &tg, st, gate);
+        else
+            s = launch_tiles_balanced(k_mix_fp64<false, NT>, NT, 1, d, theta, n, n_theta, part, hdr, &tg, st, gate);
     } else {
         RG2Data d;
         d.n = pb->data;

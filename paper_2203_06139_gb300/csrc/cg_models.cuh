@@ -19,11 +19,13 @@ constexpr int kMaxParams = CG_MAX_PARAMS;
 
 struct TileGrid {
     int64_t n_elem;   // elements per parameter point
-    int64_t chunk;    // elements per tile (multiple of 2 * threads)
+    int64_t chunk;    // elements per tile (even; a multiple of 2 * threads for the df64 kernels)
     int nbx;          // tiles per parameter point
-    int n_theta;
+    int n_theta;      // parameter points (groups of pt points for multi-point kernels)
     int n_tiles;      // n_theta * nbx
     const int* gate = nullptr;   // when set, every kernel of the launch returns at once while *gate == 0
+    int pt = 1;       // parameter points per tile
+    int n_pts = 0;    // multi-point kernels: the number of points (n_theta is then the number of groups)
 };
 
 __device__ __forceinline__ bool gated_off(const TileGrid& tg) {

@@ -1,0 +1,263 @@
+// cg_models_fp64.cuh -- FP64 forward + adjoint of the three model families on
+// the table-driven FP64 functions of cg_fp64.cuh (the FP64 path of
+// cg_batch_gradient / cg_gradient / cg_objective).
+//
+// Same reverse-mode structure and the same accumulators as the elements of
+// cg_models.cuh (whose epilogue they feed), with three changes that cut FP64
+// instructions and leave every value in FP64:
+//  - exponentials as exp2 of exponents whose per-point constants carry
+//    log2(e) (no extra instruction), reciprocals by frcp, logarithms by flog
+//    or, for a plain sum of logs, by a running product (logprod_*);
+//  - work that depends on the bin or event only (centre, weight 1/max(y,1),
+//    y log y, the sign of y) is done once per element for all the points of
+//    a multi-point tile (the elem functions take it precomputed);
+//  - constant factors of an objective (-2 of chi2's adjoint, 2 of
+//    Baker-Cousins) are applied to the per-thread sums once per tile
+//    (exact: powers of two), and non-finite terms are detected from those
+//    sums (a NaN or infinity in any term reaches the sum).
+#pragma once
+#include "cg_fp64.cuh"
+#include "cg_models.cuh"
+
+namespace cg {
+
+// ===========================================================================
+// 1-D binned: K Gaussian peaks + polynomial of degree D.
+// ===========================================================================
+
+// log2(e)-scaled exponent coefficients of the peaks: e_k = 2^(c2_k d_k^2).
+struct GP1C2 {
+    double c2[CG_MAX_PEAKS_1D];
+};
+
+__device__ __forceinline__ void gp1_c2(const GP1Consts& cs, int K, GP1C2& c) {
+    for (int k = 0; k < K; ++k) c.c2[k] = cs.c[k] * kLog2e;
+}
+
+// Point-independent part of one bin.
+struct GP1Bin {
+    double x, u, y;
+    double ny;    // -y (Poisson / Baker-Cousins); chi2: -2 / max(y, 1)
+    double ymy;   // Baker-Cousins: y log y - y (0 for y = 0)
+    bool ypos;    // y > 0 (Poisson / Baker-Cousins)
+};
+
+// max(y, 1) by an integer test of y's sign and exponent (y >= 1 exactly when
+// its high word is at least that of 1.0 and the sign is clear).
+__device__ __forceinline__ double max_y_1(double y) { return (__double2hiint(y) >= 0x3ff00000) ? y : 1.0; }
+
+template <int OBJ>
+__device__ __forceinline__ GP1Bin gp1_bin(double x, double y, const GP1Data& d, const Fp64Tab& tab) {
+    GP1Bin b;
+    b.x = x;
+    b.u = d.pm ? fma(x, d.au, d.bu) : x;
+    b.y = y;
+    b.ypos = __double_as_longlong(y) > 0;   // exact test of y > 0 (a NaN count reads as positive: its term is NaN)
+    b.ymy = 0.0;
+    if (OBJ == CG_OBJ_CHI2) {
+        b.ny = -2.0 * frcp_any(max_y_1(y));
+    } else {
+        b.ny = -y;
+        if (OBJ == CG_OBJ_POISSON_BC && b.ypos) b.ymy = fma(y, flog(y, tab), -y);
+    }
+    return b;
+}
+
+// One bin at one point.  Accumulators as gp1_elem_fp64 (value, per peak
+// g e, g e d, g e d^2, then g u^j), except the scale: chi2 accumulates
+// -2 T in acc[0] and the true adjoint g = -2 w r elsewhere (gp1_tile_scale
+// multiplies acc[0] by -1/2); Poisson accumulates T and g; Baker-Cousins
+// accumulates T/2 and g/2 (gp1_tile_scale doubles everything).
+template <int K, int OBJ>
+__device__ __forceinline__ void gp1_elem_f64(const GP1Bin& b, const GP1Consts& cs, const GP1C2& c2, int D,
+                                             const Fp64Tab& tab, double (&acc)[GP1Acc<K>::N], bool& bad) {
+    double f = 0.0;
+#pragma unroll
+    for (int j = 3; j >= 0; --j) {   // Horner from the leading coefficient
+        if (j == D) f = cs.poly[j];
+        else if (j < D) f = fma(f, b.u, cs.poly[j]);
+    }
+    double dk[K > 0 ? K : 1], ek[K > 0 ? K : 1];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        dk[k] = b.x - cs.mu[k];
+        ek[k] = fexp2((c2.c2[k] * dk[k]) * dk[k], tab);
+        f = fma(cs.A[k], ek[k], f);
+    }
+    double g;
+    if (OBJ == CG_OBJ_CHI2) {
+        const double r = b.y - f;
+        g = b.ny * r;                     // -2 w r
+        acc[0] = fma(g, r, acc[0]);       // -2 w r^2
+    } else {
+        double L, rf;
+        if (fp64_fast_range(f)) {
+            L = flog_fast(f, tab);
+            rf = frcp(f);
+        } else {
+            L = flog_slow(f);
+            rf = frcp_slow(f);
+            bad |= b.ypos && !(f > 0.0);
+        }
+        if (b.ypos) {
+            acc[0] += fma(b.ny, L, (OBJ == CG_OBJ_POISSON_BC) ? f + b.ymy : f);
+            g = fma(b.ny, rf, 1.0);
+        } else {                          // empty bin: T = f (2 f), even where f underflows to 0
+            acc[0] += f;
+            g = 1.0;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const double t = g * ek[k];
+        const double td = t * dk[k];
+        acc[1 + 3 * k] += t;
+        acc[2 + 3 * k] += td;
+        acc[3 + 3 * k] = fma(td, dk[k], acc[3 + 3 * k]);
+    }
+    double up = 1.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (j <= D) acc[1 + 3 * K + j] = fma(g, up, acc[1 + 3 * K + j]);
+        if (j < D) up *= b.u;
+    }
+}
+
+// The objective's constant factors on one thread's sums (see gp1_elem_f64).
+template <int K, int OBJ>
+__device__ __forceinline__ void gp1_tile_scale(double (&acc)[GP1Acc<K>::N]) {
+    if (OBJ == CG_OBJ_CHI2) {
+        acc[0] *= -0.5;
+    } else if (OBJ == CG_OBJ_POISSON_BC) {
+#pragma unroll
+        for (int a = 0; a < GP1Acc<K>::N; ++a) acc[a] *= 2.0;
+    }
+}
+
+// ===========================================================================
+// Unbinned mixture: p = a 2^(c2 d^2) + b 2^(nl2 (x - lo)),
+// c2 = -log2(e)/(2 s^2), nl2 = -lambda log2(e).  Accumulators as
+// mix_elem_fp64; without weights acc[0] is not touched per event: the log of
+// p goes into the running product lp (the caller adds logprod_log(lp)).
+// ===========================================================================
+struct MixC2 {
+    double c2, nl2;
+};
+
+__device__ __forceinline__ void mix_c2(const MixConsts& cs, MixC2& c) {
+    c.c2 = cs.c * kLog2e;
+    c.nl2 = -cs.lam * kLog2e;
+}
+
+template <bool W>
+__device__ __forceinline__ void mix_elem_f64(double x, double w, const MixConsts& cs, const MixC2& c2,
+                                             const Fp64Tab& tab, double (&acc)[MixAcc::N], LogProd& lp,
+                                             bool& bad) {
+    const double d = x - cs.mu;
+    const double eG = fexp2((c2.c2 * d) * d, tab);
+    const double xl = x - cs.lo;
+    const double eE = fexp2(c2.nl2 * xl, tab);
+    const double p = fma(cs.a, eG, cs.b * eE);
+    double r;
+    if (fp64_fast_range(p)) {
+        r = frcp(p);
+        if (W) acc[0] = fma(w, flog_fast(p, tab), acc[0]);
+        else logprod_mul(lp, p);
+    } else {                              // p <= 0, subnormal, huge or NaN: IEEE path
+        r = frcp_slow(p);
+        acc[0] += W ? w * flog_slow(p) : flog_slow(p);
+        bad |= !(p > 0.0);
+    }
+    if (W) r *= w;
+    const double U = eG * r, V = eE * r;
+    const double Ud = U * d;
+    acc[1] += U;
+    acc[2] += Ud;
+    acc[3] = fma(Ud, d, acc[3]);
+    acc[4] += V;
+    acc[5] = fma(V, xl, acc[5]);
+}
+
+// ===========================================================================
+// 2-D binned Poisson NLL of K rotated Gaussians + C.  The exponent is taken
+// as a quadratic form in (dx, dy) = (x - mu_x, y - mu_y):
+//   q log2(e) = qa dx^2 + 2 qb dx dy + qc dy^2,
+//   qa = (al c^2 + be s^2) log2 e, qb = (al - be) c s log2 e,
+//   qc = (al s^2 + be c^2) log2 e   (c, s = cos, sin phi),
+// and the adjoint sums are kept in (dx, dy): sum g e (1, dx, dy, dx^2, dy^2,
+// dx dy); rg2_rotate_moments turns them into the (u, v) sums of rg2_elem_fp64
+// (1, u, v, u^2, v^2, u v) once per tile, a rotation of the moments.
+// ===========================================================================
+struct RG2Q {
+    double qa[CG_MAX_PEAKS_2D], qb2[CG_MAX_PEAKS_2D], qc[CG_MAX_PEAKS_2D];   // qb2 = 2 qb
+};
+
+template <int K>
+__device__ __forceinline__ void rg2_q(const RG2Consts& c, RG2Q& q) {
+    for (int k = 0; k < K; ++k) {
+        const double cs = c.cs[k], sn = c.sn[k], al = c.al[k], be = c.be[k];
+        q.qa[k] = fma(al, cs * cs, be * sn * sn) * kLog2e;
+        q.qb2[k] = 2.0 * ((al - be) * cs * sn) * kLog2e;
+        q.qc[k] = fma(al, sn * sn, be * cs * cs) * kLog2e;
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void rg2_elem_f64(double x, double y, double n, const RG2Consts& c, const RG2Q& q,
+                                             unsigned act, const Fp64Tab& tab, double (&acc)[RG2Acc<K>::N],
+                                             bool& bad) {
+    double dx[K], dy[K], e[K];
+    double mu = c.C;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (!(act & (1u << k))) {
+            dx[k] = dy[k] = e[k] = 0.0;
+            continue;
+        }
+        dx[k] = x - c.mx[k];
+        dy[k] = y - c.my[k];
+        const double t = fma(q.qa[k], dx[k], q.qb2[k] * dy[k]);
+        e[k] = fexp2(fma(dx[k], t, (q.qc[k] * dy[k]) * dy[k]), tab);
+        mu = fma(c.A[k], e[k], mu);
+    }
+    const bool npos = __double_as_longlong(n) > 0;
+    double L, rm;
+    if (fp64_fast_range(mu)) {
+        L = flog_fast(mu, tab);
+        rm = frcp(mu);
+    } else {
+        L = flog_slow(mu);
+        rm = frcp_slow(mu);
+        bad |= npos && !(mu > 0.0);
+    }
+    const double g = npos ? fma(-n, rm, 1.0) : 1.0;
+    acc[0] += npos ? fma(-n, L, mu) : mu;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (!(act & (1u << k))) continue;
+        const double w = g * e[k];
+        const double wx = w * dx[k], wy = w * dy[k];
+        acc[1 + 6 * k] += w;
+        acc[2 + 6 * k] += wx;
+        acc[3 + 6 * k] += wy;
+        acc[4 + 6 * k] = fma(wx, dx[k], acc[4 + 6 * k]);
+        acc[5 + 6 * k] = fma(wy, dy[k], acc[5 + 6 * k]);
+        acc[6 + 6 * k] = fma(wx, dy[k], acc[6 + 6 * k]);
+    }
+    acc[1 + 6 * K] += g;
+}
+
+// (dx, dy) moments of one Gaussian -> (u, v) moments, in place: S[0..5] =
+// sum g e (1, dx, dy, dx^2, dy^2, dx dy) on entry, (1, u, v, u^2, v^2, u v) on exit,
+// u = c dx + s dy, v = -s dx + c dy.
+__device__ __forceinline__ void rg2_rotate_moments(double* S, double cs, double sn) {
+    const double Sx = S[1], Sy = S[2], Sxx = S[3], Syy = S[4], Sxy = S[5];
+    S[1] = fma(cs, Sx, sn * Sy);
+    S[2] = fma(cs, Sy, -sn * Sx);
+    const double cc = cs * cs, ss = sn * sn, c2s = 2.0 * cs * sn;
+    S[3] = fma(cc, Sxx, fma(c2s, Sxy, ss * Syy));
+    S[4] = fma(ss, Sxx, fma(-c2s, Sxy, cc * Syy));
+    S[5] = fma(cs * sn, Syy - Sxx, (cc - ss) * Sxy);
+}
+
+}  // namespace cg

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <mutex>
 #include <unordered_map>
 
@@ -16,16 +17,35 @@ namespace cg {
 
 static constexpr int kMaxTiles = 16384;
 
-// Resident blocks per SM of a kernel, cached per (kernel, threads).
+// Resident blocks per SM of a kernel on the current device, cached per
+// (device, kernel, threads, dynamic shared memory): the figure depends on the
+// device's limits, so a process driving several GPUs keeps one per device.
 inline int resident_blocks(const void* fn, int threads, size_t smem) {
+    struct Key {
+        int dev;
+        const void* fn;
+        int threads;
+        size_t smem;
+        bool operator==(const Key& o) const {
+            return dev == o.dev && fn == o.fn && threads == o.threads && smem == o.smem;
+        }
+    };
+    struct Hash {
+        size_t operator()(const Key& k) const {
+            return std::hash<const void*>()(k.fn) ^ ((size_t)k.dev << 1) ^ ((size_t)k.threads << 8) ^ (k.smem << 20);
+        }
+    };
     static std::mutex mu;
-    static std::unordered_map<const void*, int> cache;
+    static std::unordered_map<Key, int, Hash> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+    const Key key{dev, fn, threads, smem};
     std::lock_guard<std::mutex> lk(mu);
-    auto it = cache.find(fn);
+    auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     int r = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, fn, threads, smem) != cudaSuccess || r < 1) r = 1;
-    cache[fn] = r;
+    cache[key] = r;
     return r;
 }
 
@@ -85,6 +105,62 @@ inline cg_status launch_tiles(KernelT kern, int NT, const DataT& d, const double
     TileGrid tg = make_tiles(n_elem, n_theta, NT, G);
     tg.gate = gate;
     int grid = tg.n_tiles < G ? tg.n_tiles : G;
+    prof_begin(st);
+    kern<<<grid, NT, 0, st>>>(d, theta, tg, part, hdr);
+    prof_end(st);
+    *tg_out = tg;
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
+
+// Tile grid of the FP64 kernels, whose time is set by the FP64 unit of each
+// SM, not by occupancy: among chunk counts per point group nbx (chunks of
+// at least 2 elements per thread, even, within the workspace bound), the one
+// whose busiest SM gets the fewest element-points, i.e. the smallest
+// ceil(n_groups * nbx / n_sm) * chunk (ties: fewer tiles).  n_groups =
+// ceil(n_theta / pt) groups of pt points.
+inline TileGrid make_tiles_balanced(int64_t n_elem, int64_t n_theta, int pt, int NT, int n_sm) {
+    TileGrid tg;
+    tg.n_elem = n_elem;
+    const int64_t groups = (n_theta + pt - 1) / pt;
+    int64_t most = (n_elem + 2 * NT - 1) / (2 * NT);
+    const int64_t cap = (kMaxTiles + groups - 1) / groups;
+    if (most > cap) most = cap;
+    if (most > max_nbx(n_theta)) most = max_nbx(n_theta);
+    if (most < 1) most = 1;
+    const int64_t S = n_sm > 0 ? n_sm : 1;
+    int64_t best = 1, best_cost = -1;
+    for (int64_t nbx = 1; nbx <= most; ++nbx) {
+        int64_t chunk = (n_elem + nbx - 1) / nbx;
+        chunk += chunk & 1;
+        if ((n_elem + chunk - 1) / chunk != nbx) continue;
+        const int64_t cost = (groups * nbx + S - 1) / S * chunk;
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = nbx;
+        }
+    }
+    int64_t chunk = (n_elem + best - 1) / best;
+    chunk += chunk & 1;
+    if (chunk < 2) chunk = 2;
+    tg.chunk = chunk;
+    tg.nbx = (int)((n_elem + chunk - 1) / chunk);
+    tg.n_theta = (int)groups;
+    tg.n_tiles = (int)(groups * tg.nbx);
+    tg.pt = pt;
+    tg.n_pts = (int)n_theta;
+    return tg;
+}
+
+template <typename KernelT, typename DataT>
+inline cg_status launch_tiles_balanced(KernelT kern, int NT, int pt, const DataT& d, const double* theta,
+                                       int64_t n_elem, int64_t n_theta, double* part, WsHeader* hdr,
+                                       TileGrid* tg_out, cudaStream_t st, const int* gate = nullptr) {
+    const int nsm = device_sm_count();
+    const int R = resident_blocks((const void*)kern, NT, 0);
+    TileGrid tg = make_tiles_balanced(n_elem, n_theta, pt, NT, nsm);
+    tg.gate = gate;
+    const int G = nsm * R;
+    const int grid = tg.n_tiles < G ? tg.n_tiles : G;
     prof_begin(st);
     kern<<<grid, NT, 0, st>>>(d, theta, tg, part, hdr);
     prof_end(st);

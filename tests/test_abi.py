@@ -84,6 +84,32 @@ def test_df64_tables_match_their_generator():
         assert abs(float(hi) + float(lo) - ref) <= 2.0 ** -48 * abs(ref)   # what a float pair holds
 
 
+def test_fp64_tables_match_their_generator():
+    """The committed tables of the FP64 exp2 and log are exactly what the
+    generator writes: every entry the double nearest 2^(j/4096), log(F_j) or
+    1/F_j (F_j = 1 + (2j+1)/256), checked here against Python's own
+    correctly rounded arithmetic where it has it."""
+    pytest.importorskip("mpmath")
+    import importlib.util
+    import math
+    path = os.path.join(ROOT, "paper_2203_06139_gb300", "csrc", "gen_fp64_tables.py")
+    spec = importlib.util.spec_from_file_location("gen_fp64_tables", path)
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    with open(gen.OUT) as f:
+        assert f.read() == gen.render()
+    t = gen.table()
+    logF, invF = gen.log_tables()
+    assert len(t) == 4096 and len(logF) == len(invF) == 128
+    assert t[0] == 1.0 and t[2048] == math.sqrt(2.0)          # sqrt is correctly rounded
+    assert t[1024] == math.sqrt(math.sqrt(2.0)) or abs(t[1024] - 2 ** 0.25) <= 2 ** -52
+    for j in (0, 1, 77, 127):
+        F = 1.0 + (2 * j + 1) / 256.0                          # exact in binary
+        assert invF[j] == 1.0 / F                              # IEEE division is correctly rounded
+        assert abs(logF[j] - math.log(F)) <= 2 ** -52 * abs(math.log(F))
+    assert all(1.0 <= v < 2.0 for v in t) and all(t[i] < t[i + 1] for i in range(4095))
+
+
 def test_lm_plan_sizes_and_refusals_without_gpu(lib):
     """The Levenberg-Marquardt workspace: tiles of at most 16384 bins per
     histogram (one for an empty one), rows of N + 1 + R(R+1)/2 doubles; FP64

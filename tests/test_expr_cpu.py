@@ -130,9 +130,9 @@ def test_value_only_source_has_no_reverse_sweep():
 
 def test_accumulator_limit_on_the_host():
     """Up to 127 frontier adjoints (+ the value) per thread: the 32-peak
-    program (99 accumulators) and 126 frontier nodes (127) get their source;
-    128 frontier nodes are refused by the host-side validation (no handle,
-    no source)."""
+    program (99 accumulators), 126 and 127 frontier nodes (127 and 128
+    accumulators) get their source; 128 frontier nodes are refused by the
+    host-side validation (no handle, no source)."""
     import pytest
     from paper_2203_06139_gb300 import cg
     K, n = 32, 100
@@ -148,5 +148,10 @@ def test_accumulator_limit_on_the_host():
             e = e + E.param(k) * E.inp(0) + (E.param(k) * E.param(k)) * E.index()
         return e
     assert "#define NACC 127" in E.generated_source(two_per_param(63), 63, 1)
+    # the boundary itself: 127 frontier nodes (NACC 128) are accepted, 128 refused
+    odd = two_per_param(63) + E.param(63) * E.inp(0)
+    assert "#define NACC 128" in E.generated_source(odd, 64, 1)
+    with pytest.raises(cg.CgError):
+        E.generated_source(odd + E.param(64) * E.inp(0), 65, 1)
     with pytest.raises(cg.CgError):
         E.generated_source(two_per_param(64), 64, 1)
