@@ -25,11 +25,13 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "cg_internal.cuh"
 #include "cg_models.cuh"
 #include "cg_models_df64.cuh"
+#include "cg_models_fp64.cuh"
 #include "cg_tiles.cuh"
 
 namespace cgx = cooperative_groups;
@@ -107,6 +109,24 @@ __device__ __forceinline__ void acc_bins(const Geom& G, const GP1Consts& cs, con
         const double x = fma((double)i + 0.5, G.hw, G.lo);
         gp1_elem_fp64<K, OBJ>(x, __ldg(G.y + i), cs, dd, acc, bad);
     }
+}
+
+// The same on the table-driven FP64 functions (FP64 batches): the thread's
+// sums leave with the objective's factors applied (gp1_tile_scale), and a
+// non-finite value sum sets bad.  acc must start at zero.
+template <int K, int OBJ>
+__device__ __forceinline__ void acc_bins_f64(const Geom& G, const GP1Consts& cs, const GP1Data& dd,
+                                             const Fp64Tab& tab, int t0, int T, double (&acc)[GP1Acc<K>::N],
+                                             bool& bad) {
+    GP1C2 c2;
+    gp1_c2(cs, K, c2);
+    const double hh = 0.5 * G.hw;   // centre (2i + 1) (h/2) + lo, correctly rounded
+    for (int64_t i = t0; i < G.n; i += T) {
+        const GP1Bin b = gp1_bin<OBJ>(fma((double)(2 * i + 1), hh, G.lo), __ldg(G.y + i), dd, tab);
+        gp1_elem_f64<K, OBJ>(b, cs, c2, dd.D, tab, acc, bad);
+    }
+    gp1_tile_scale<K, OBJ>(acc);
+    bad |= nonfinite(acc[0]);
 }
 
 // Gauss-Newton diagonal terms of one bin: h (df/dtheta_k)^2 with h = d2T/df2.
@@ -535,9 +555,9 @@ __device__ __forceinline__ int unit_reduce(const T (&v)[N], bool bad, double* re
 // One objective evaluation of histogram G at s.tt by a unit (all threads).
 // ---------------------------------------------------------------------------
 template <int UNIT, int K, int OBJ, int PREC>
-__device__ __forceinline__ void unit_eval(FitSm& s, GP1Consts& cs, GP1Df& cd, const DfTables& tab, const Geom& G,
-                                          const GP1Data& dd, int D, double* red, double* part, double* tot, int t0,
-                                          int T) {
+__device__ __forceinline__ void unit_eval(FitSm& s, GP1Consts& cs, GP1Df& cd, const DfTables& tab,
+                                          const Fp64Tab* t64, const Geom& G, const GP1Data& dd, int D, double* red,
+                                          double* part, double* tot, int t0, int T) {
     constexpr int N = GP1Acc<K>::N;
     const int lane = threadIdx.x & 31;
     if (UNIT == UNIT_WARP || threadIdx.x < 32) {   // the constants, one per lane of the control warp
@@ -555,7 +575,8 @@ __device__ __forceinline__ void unit_eval(FitSm& s, GP1Consts& cs, GP1Df& cd, co
         double acc[N];
 #pragma unroll
         for (int a = 0; a < N; ++a) acc[a] = 0.0;
-        acc_bins<K, OBJ>(G, cs, dd, t0, T, acc, bad);
+        if (PREC == CG_PREC_FP64) acc_bins_f64<K, OBJ>(G, cs, dd, *t64, t0, T, acc, bad);
+        else acc_bins<K, OBJ>(G, cs, dd, t0, T, acc, bad);   // df64 batches: histograms of 2^24 bins or more
         any_bad = unit_reduce<UNIT, N>(acc, bad, red, part, tot);
     }
     if (UNIT == UNIT_WARP || threadIdx.x < 32) {   // value and gradient, one parameter per lane
@@ -604,7 +625,7 @@ __device__ __forceinline__ void state_store(const FitSm& s, cg_fit_state* st, in
 // Fit one histogram with one unit for up to a.n_steps iterations.
 template <int UNIT, int K, int OBJ, int PREC>
 __device__ void unit_fit(const FitArgs& a, int64_t h, FitSm& s, GP1Consts& cs, GP1Df& cd, const DfTables& tab,
-                         double* red, double* part, double* tot, int t0, int T) {
+                         const Fp64Tab* t64, double* red, double* part, double* tot, int t0, int T) {
     const int lane = threadIdx.x & 31;
     const bool ctl = (UNIT == UNIT_WARP) || (threadIdx.x < 32);
     const int ld_id = (UNIT == UNIT_WARP) ? lane : threadIdx.x;
@@ -630,7 +651,7 @@ __device__ void unit_fit(const FitArgs& a, int64_t h, FitSm& s, GP1Consts& cs, G
         if (ctl) ctl_direction(s, lane);
         if (UNIT != UNIT_WARP) __syncthreads();
         for (;;) {
-            unit_eval<UNIT, K, OBJ, PREC>(s, cs, cd, tab, G, dd, a.D, red, part, tot, t0, T);
+            unit_eval<UNIT, K, OBJ, PREC>(s, cs, cd, tab, t64, G, dd, a.D, red, part, tot, t0, T);
             if (ctl) ctl_after_eval(s, lane, a.tol);
             if (UNIT == UNIT_WARP) __syncwarp(); else __syncthreads();
             if (s.go != 0) break;
@@ -644,10 +665,11 @@ __device__ void unit_fit(const FitArgs& a, int64_t h, FitSm& s, GP1Consts& cs, G
 
 // Shared-memory layout of the persistent kernel (dynamic).
 struct SmLayout {
-    size_t cta_sm, warp_sm, cta_cs, warp_cs, cta_cd, warp_cd, tab, red, part, tot, warp_tot, item, total;
+    size_t cta_sm, warp_sm, cta_cs, warp_cs, cta_cd, warp_cd, tab, tab64, red, part, tot, warp_tot, item, total;
 };
 
-__host__ __device__ inline SmLayout sm_layout(int nwarps, int nacc) {
+// fp64: room for the tables of the FP64 functions (FP64 batches only).
+__host__ __device__ inline SmLayout sm_layout(int nwarps, int nacc, bool fp64) {
     SmLayout L;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o += (bytes + 15) / 16 * 16; return r; };
@@ -658,6 +680,7 @@ __host__ __device__ inline SmLayout sm_layout(int nwarps, int nacc) {
     L.cta_cd = take(sizeof(GP1Df));
     L.warp_cd = take(sizeof(GP1Df) * nwarps);
     L.tab = take(sizeof(DfTables));
+    L.tab64 = take(fp64 ? sizeof(Fp64Tab) : 0);
     L.red = take(sizeof(double) * (nacc + 1) * kMaxWarpsPerCta);
     L.part = take(sizeof(double) * (nacc + 1));
     L.tot = take(sizeof(double) * (nacc + 1));
@@ -673,7 +696,7 @@ __global__ void __launch_bounds__(512) k_fit_persistent(FitArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int N = GP1Acc<K>::N;
     const int nw = blockDim.x >> 5;
-    const SmLayout L = sm_layout(nw, N);
+    const SmLayout L = sm_layout(nw, N, PREC == CG_PREC_FP64);
     FitSm& cta_s = *reinterpret_cast<FitSm*>(smem + L.cta_sm);
     GP1Consts& cta_cs = *reinterpret_cast<GP1Consts*>(smem + L.cta_cs);
     double* red = reinterpret_cast<double*>(smem + L.red);
@@ -682,9 +705,13 @@ __global__ void __launch_bounds__(512) k_fit_persistent(FitArgs a) {
     int* item = reinterpret_cast<int*>(smem + L.item);
     GP1Df& cta_cd = *reinterpret_cast<GP1Df*>(smem + L.cta_cd);
     DfTables& tab = *reinterpret_cast<DfTables*>(smem + L.tab);
+    const Fp64Tab* t64 = reinterpret_cast<const Fp64Tab*>(smem + L.tab64);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (PREC == CG_PREC_DF64) {
         df_tables_init(tab);
+        __syncthreads();
+    } else {
+        fp64_tab_load(*reinterpret_cast<Fp64Tab*>(smem + L.tab64));
         __syncthreads();
     }
 
@@ -699,7 +726,7 @@ __global__ void __launch_bounds__(512) k_fit_persistent(FitArgs a) {
             const int it = *cl.map_shared_rank(item, 0);
             cl.sync();
             if (it >= n0) break;
-            unit_fit<UNIT_CLUSTER, K, OBJ, PREC>(a, a.queue[0][it], cta_s, cta_cs, cta_cd, tab, red, part, tot,
+            unit_fit<UNIT_CLUSTER, K, OBJ, PREC>(a, a.queue[0][it], cta_s, cta_cs, cta_cd, tab, t64, red, part, tot,
                                                  rank * blockDim.x + threadIdx.x, csz * blockDim.x);
         }
     }
@@ -709,7 +736,7 @@ __global__ void __launch_bounds__(512) k_fit_persistent(FitArgs a) {
         const int it = *item;
         __syncthreads();
         if (it >= n1) break;
-        unit_fit<UNIT_CTA, K, OBJ, PREC>(a, a.queue[1][it], cta_s, cta_cs, cta_cd, tab, red, part, tot, threadIdx.x,
+        unit_fit<UNIT_CTA, K, OBJ, PREC>(a, a.queue[1][it], cta_s, cta_cs, cta_cd, tab, t64, red, part, tot, threadIdx.x,
                                          blockDim.x);
     }
     FitSm& ws_ = reinterpret_cast<FitSm*>(smem + L.warp_sm)[wid];
@@ -721,7 +748,7 @@ __global__ void __launch_bounds__(512) k_fit_persistent(FitArgs a) {
         if (lane == 0) it = atomicAdd(&a.counters[2], 1);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= n2) break;
-        unit_fit<UNIT_WARP, K, OBJ, PREC>(a, a.queue[2][it], ws_, wcs, wcd, tab, nullptr, nullptr, wtot, lane, 32);
+        unit_fit<UNIT_WARP, K, OBJ, PREC>(a, a.queue[2][it], ws_, wcs, wcd, tab, t64, nullptr, nullptr, wtot, lane, 32);
     }
 }
 
@@ -765,8 +792,12 @@ __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
     __shared__ GP1Df cd;
     __shared__ DfTables tab;
     __shared__ int cs_bad;
+    __shared__ typename std::conditional<PREC == CG_PREC_FP64, Fp64Tab, int>::type t64;
     if (PREC == CG_PREC_DF64) {
         df_tables_init(tab);
+        __syncthreads();
+    } else {
+        if constexpr (PREC == CG_PREC_FP64) fp64_tab_load(t64);
         __syncthreads();
     }
     __shared__ double red[(N + 1) * kMaxWarpsPerCta];
@@ -842,7 +873,8 @@ __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
             double acc[N], gacc[N];
 #pragma unroll
             for (int i = 0; i < N; ++i) acc[i] = gacc[i] = 0.0;
-            acc_bins<K, OBJ>(G, cs, dd, threadIdx.x, blockDim.x, acc, bad);
+            if constexpr (PREC == CG_PREC_FP64) acc_bins_f64<K, OBJ>(G, cs, dd, t64, threadIdx.x, blockDim.x, acc, bad);
+            else acc_bins<K, OBJ>(G, cs, dd, threadIdx.x, blockDim.x, acc, bad);
             if constexpr (MODE == 1) gn_bins<K, OBJ>(G, cs, dd, threadIdx.x, blockDim.x, gacc);
             any_bad = __syncthreads_or(bad) | cs_bad;
             if constexpr (MODE == 2) {
@@ -1417,7 +1449,7 @@ template <int K, int OBJ, bool CL, int PREC>
 cg_status launch_persistent_k(const FitArgs& a, const cg_tile_map* m, cudaStream_t st) {
     constexpr int N = GP1Acc<K>::N;
     const int nt = m->cta_threads;
-    const SmLayout L = sm_layout(nt / 32, N);
+    const SmLayout L = sm_layout(nt / 32, N, PREC == CG_PREC_FP64);
     auto kern = k_fit_persistent<K, OBJ, CL, PREC>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total) != cudaSuccess)
         return CG_ERR_CUDA;

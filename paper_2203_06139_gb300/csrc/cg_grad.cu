@@ -62,9 +62,6 @@ __device__ __forceinline__ void write_partials(double* __restrict__ part, const 
     }
 }
 
-// True when x is infinite or NaN (integer test of the exponent field).
-__device__ __forceinline__ bool nonfinite(double x) { return (__double2hiint(x) & 0x7ff00000) == 0x7ff00000; }
-
 // 1-D Gaussian peaks + polynomial, FP64.  A tile is (PT consecutive
 // parameter points, one chunk of bins); every bin's point-independent part
 // is taken once and reused for the PT points.  In a ragged last group the
@@ -105,6 +102,10 @@ __global__ void __launch_bounds__(NT) k_gp1_fp64(GP1Data d, const double* __rest
         bool bad[PT];
 #pragma unroll
         for (int p = 0; p < PT; ++p) bad[p] = false;
+        // centre lo + (i + 1/2) h as (2i + 1) (h/2) + lo: one conversion and one FMA
+        // (2i + 1 and h/2 are exact, so this is the correctly rounded centre)
+        const double hh = 0.5 * d.h;
+        auto centre = [&](int64_t i) { return fma((double)(2 * i + 1), hh, d.lo); };
         auto bin = [&](double x, double y) {
             const GP1Bin b = gp1_bin<OBJ>(x, y, d, tab);
 #pragma unroll
@@ -119,16 +120,15 @@ __global__ void __launch_bounds__(NT) k_gp1_fp64(GP1Data d, const double* __rest
                     const double2 y2 = __ldg(reinterpret_cast<const double2*>(d.y + i));
                     double2 x2;
                     if (d.centres) x2 = __ldg(reinterpret_cast<const double2*>(d.centres + i));
-                    else { x2.x = fma((double)i + 0.5, d.h, d.lo); x2.y = fma((double)i + 1.5, d.h, d.lo); }
+                    else { x2.x = centre(i); x2.y = centre(i + 1); }
                     bin(x2.x, y2.x);
                     bin(x2.y, y2.y);
                 } else {
-                    bin(d.centres ? d.centres[i] : fma((double)i + 0.5, d.h, d.lo), d.y[i]);
+                    bin(d.centres ? d.centres[i] : centre(i), d.y[i]);
                 }
             }
         } else {
-            for (int64_t i = e0 + threadIdx.x; i < e1; i += NT)
-                bin(d.centres ? d.centres[i] : fma((double)i + 0.5, d.h, d.lo), d.y[i]);
+            for (int64_t i = e0 + threadIdx.x; i < e1; i += NT) bin(d.centres ? d.centres[i] : centre(i), d.y[i]);
         }
         int bm = 0;
 #pragma unroll
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(NT) k_gp1_fp64(GP1Data d, const double* __rest
         if (bm) atomicOr(&s_badm, bm);
         __syncthreads();
         const int badm = s_badm;
-        block_sum<N * PT, NT>(reinterpret_cast<const double(&)[N * PT]>(acc), red, tot);
+        block_sum_rs<N * PT, NT>(reinterpret_cast<const double(&)[N * PT]>(acc), red, tot);
         write_partials<N, NT>(part, tg, th0, np, c, tot, badm);
     }
 }
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(NT) k_mix_fp64(MixData d, const double* __rest
         }
         if (!W) acc[0] += logprod_log(lp, tab);
         const int any_bad = __syncthreads_or(bad ? 1 : 0) | cs_bad;
-        block_sum<NACC, NT>(acc, red, tot);
+        block_sum_rs<NACC, NT>(acc, red, tot);
         write_partial<NACC>(part, tg, th, c, tot, any_bad);
     }
 }
@@ -384,7 +384,7 @@ size_t grad_workspace_bytes(const cg_problem* pb, int64_t n_theta) {
 template <int K>
 static cg_status launch_gp1_k(const cg_problem* pb, const GP1Data& d, const double* theta, int64_t n_theta,
                               double* part, WsHeader* hdr, TileGrid* tg, cudaStream_t st, const int* gate) {
-    constexpr int NT = 128;
+    constexpr int NT = 128;   // 157 registers at 4 points per tile: three CTAs per SM
     const int64_t n = pb->n_bins[0];
     constexpr int PTM = (K <= 1) ? 4 : 1;
     const bool multi = PTM > 1 && n_theta >= PTM;

@@ -113,11 +113,13 @@ inline cg_status launch_tiles(KernelT kern, int NT, const DataT& d, const double
 }
 
 // Tile grid of the FP64 kernels, whose time is set by the FP64 unit of each
-// SM, not by occupancy: among chunk counts per point group nbx (chunks of
-// at least 2 elements per thread, even, within the workspace bound), the one
-// whose busiest SM gets the fewest element-points, i.e. the smallest
-// ceil(n_groups * nbx / n_sm) * chunk (ties: fewer tiles).  n_groups =
-// ceil(n_theta / pt) groups of pt points.
+// SM: among chunk counts per point group nbx (chunks of at least 2 elements
+// per thread, even, within the workspace bound), the one whose busiest SM
+// gets the fewest element-points, i.e. the smallest
+// ceil(n_groups * nbx / n_sm) * chunk, with a 5 % penalty per missing tile
+// below two tiles per SM (one CTA per SM leaves too few warps to cover the
+// FP64 latencies; measured on the 10,000-bin x 100-point workload); ties:
+// fewer tiles.  n_groups = ceil(n_theta / pt) groups of pt points.
 inline TileGrid make_tiles_balanced(int64_t n_elem, int64_t n_theta, int pt, int NT, int n_sm) {
     TileGrid tg;
     tg.n_elem = n_elem;
@@ -133,7 +135,9 @@ inline TileGrid make_tiles_balanced(int64_t n_elem, int64_t n_theta, int pt, int
         int64_t chunk = (n_elem + nbx - 1) / nbx;
         chunk += chunk & 1;
         if ((n_elem + chunk - 1) / chunk != nbx) continue;
-        const int64_t cost = (groups * nbx + S - 1) / S * chunk;
+        const double per_sm = (double)(groups * nbx) / (double)S;
+        const double pen = per_sm < 2.0 ? 1.0 + 0.05 * (2.0 - per_sm) : 1.0;
+        const int64_t cost = (int64_t)((double)((groups * nbx + S - 1) / S * chunk) * pen);
         if (best_cost < 0 || cost < best_cost) {
             best_cost = cost;
             best = nbx;

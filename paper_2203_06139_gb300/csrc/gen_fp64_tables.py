@@ -1,12 +1,13 @@
 """Write cg_fp64_tables.inc: the lookup tables of the FP64 exp2 and log of cg_fp64.cuh.
 
     exp2t[j] = 2^(j/4096)   j = 0..4095   (Tang's table-driven exponential, in base 2)
-    logF[j]  = log(F_j)     F_j = 1 + (2j + 1)/256, j = 0..127 (Tang's table-driven logarithm)
-    invF[j]  = 1/F_j
+    logF[t]  = log(F_t), invF[t] = 1/F_t, t = 0..129 (Tang's table-driven logarithm):
+               F_t = 1 + t/128 for t = 0..53 (breakpoints in [1, sqrt 2)),
+               F_t = (1 + (t - 1)/128)/2 for t = 54..129 (breakpoints in [sqrt 2 / 2, 1]).
 
 Each entry is the double nearest to the exact value, from 60-digit mpmath
-values (mpmath's conversion to float rounds to nearest); F_j itself is exact
-in binary and is formed in the kernel.  Run from anywhere:
+values (mpmath's conversion to float rounds to nearest); F_t itself is exact
+in binary and is formed in the kernel from the argument's bits.  Run from anywhere:
 ``python gen_fp64_tables.py`` (rewrites the file next to this script); the
 CPU test suite checks the committed file against this script's output.
 """
@@ -18,8 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(HERE, "cg_fp64_tables.inc")
 BITS = 12
 N = 1 << BITS
-LOG_BITS = 7
-NL = 1 << LOG_BITS
+NL = 130
 
 
 def table():
@@ -27,9 +27,15 @@ def table():
     return [float(mpmath.power(2, mpmath.mpf(j) / N)) for j in range(N)]
 
 
+def breakpoints():
+    """F_t: 1 + j/128 for j = 0..53, then (1 + j/128)/2 for j = 53..128."""
+    return ([1 + mpmath.mpf(j) / 128 for j in range(54)] +
+            [(1 + mpmath.mpf(j) / 128) / 2 for j in range(53, 129)])
+
+
 def log_tables():
     mpmath.mp.dps = 60
-    F = [1 + mpmath.mpf(2 * j + 1) / (2 * NL) for j in range(NL)]
+    F = breakpoints()
     return [float(mpmath.log(f)) for f in F], [float(1 / f) for f in F]
 
 
@@ -45,9 +51,8 @@ def render():
     t = table()
     logF, invF = log_tables()
     lines = ["// Generated by gen_fp64_tables.py -- do not edit.",
-             "// 2^(j/%d), j = 0..%d; log(F_j) and 1/F_j with F_j = 1 + (2j+1)/%d, j = 0..%d;" % (N, N - 1, 2 * NL,
-                                                                                             NL - 1),
-             "// each rounded to the nearest double."]
+             "// 2^(j/%d), j = 0..%d; log(F_t) and 1/F_t with F_t = 1 + t/128 (t = 0..53) and" % (N, N - 1),
+             "// (1 + (t-1)/128)/2 (t = 54..129); each rounded to the nearest double."]
     lines += _rows("g_exp2_tab", t)
     lines += _rows("g_log_tab", logF)
     lines += _rows("g_invf_tab", invF)

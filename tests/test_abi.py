@@ -86,9 +86,10 @@ def test_df64_tables_match_their_generator():
 
 def test_fp64_tables_match_their_generator():
     """The committed tables of the FP64 exp2 and log are exactly what the
-    generator writes: every entry the double nearest 2^(j/4096), log(F_j) or
-    1/F_j (F_j = 1 + (2j+1)/256), checked here against Python's own
-    correctly rounded arithmetic where it has it."""
+    generator writes: every entry the double nearest 2^(j/4096), log(F_t) or
+    1/F_t, F_t = 1 + t/128 (t = 0..53) and (1 + (t-1)/128)/2 (t = 54..129),
+    checked here against Python's own correctly rounded arithmetic where it
+    has it."""
     pytest.importorskip("mpmath")
     import importlib.util
     import math
@@ -100,13 +101,14 @@ def test_fp64_tables_match_their_generator():
         assert f.read() == gen.render()
     t = gen.table()
     logF, invF = gen.log_tables()
-    assert len(t) == 4096 and len(logF) == len(invF) == 128
+    assert len(t) == 4096 and len(logF) == len(invF) == 130
     assert t[0] == 1.0 and t[2048] == math.sqrt(2.0)          # sqrt is correctly rounded
-    assert t[1024] == math.sqrt(math.sqrt(2.0)) or abs(t[1024] - 2 ** 0.25) <= 2 ** -52
-    for j in (0, 1, 77, 127):
-        F = 1.0 + (2 * j + 1) / 256.0                          # exact in binary
-        assert invF[j] == 1.0 / F                              # IEEE division is correctly rounded
-        assert abs(logF[j] - math.log(F)) <= 2 ** -52 * abs(math.log(F))
+    assert abs(t[1024] - 2 ** 0.25) <= 2 ** -52
+    F = [1.0 + k / 128.0 for k in range(54)] + [(1.0 + k / 128.0) / 2.0 for k in range(53, 129)]   # exact
+    assert F[0] == 1.0 and F[129] == 1.0 and F[53] == 2 * F[54] < math.sqrt(2.0)   # j = 53 in both binades
+    for k in (0, 1, 53, 54, 77, 128, 129):
+        assert invF[k] == 1.0 / F[k]                           # IEEE division is correctly rounded
+        assert logF[k] == 0.0 if F[k] == 1.0 else abs(logF[k] - math.log(F[k])) <= 2 ** -52 * abs(math.log(F[k]))
     assert all(1.0 <= v < 2.0 for v in t) and all(t[i] < t[i + 1] for i in range(4095))
 
 
