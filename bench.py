@@ -1,23 +1,38 @@
 #!/usr/bin/env python
 """Throughput of exact fit-objective gradients on GB300.
 
-One step = one cg_batch_gradient call: the unbinned Gaussian + exponential
-mixture NLL and its exact gradient over 10^7 events at 50 parameter points
-(the fused forward + adjoint kernel and the fixed-order finalize).  The
-events (80 MB) are below L2 size, so L2 is flushed (a 256 MB write) before
-every timed step; only the step itself is inside the CUDA events.
+Headline (one step): one cg_batch_gradient call of the unbinned Gaussian +
+exponential mixture NLL and its exact gradient over 10^7 events at 50
+parameter points, on the FP64 path (the fused FP64 forward + adjoint tile
+kernel and the fixed-order finalize).  The events (80 MB) are below L2
+size, so L2 is flushed (a 256 MB write) before every timed step; only the
+step itself is inside the CUDA events.
 
-Reported: bin-grads/s (events x parameter points per second, the headline
-value), gradient evaluations/s, the end-to-end figure through the public
-API with host buffers, the roofline of the dominant kernel, and the CPU
-oracle timed on the host's cores.  `--impl reference` times the CPU oracle
-alone (the reference arm).  Under torchrun each rank evaluates its own 50
-parameter points on its own copy of the events (weak scaling; no
-collective on the data path).
+Reported on the same JSON line: bin-grads/s (events x parameter points per
+second), gradient evaluations/s, the end-to-end figure through the public
+API with host buffers, the roofline of the dominant kernel (FP64-pipe
+instructions counted from the kernel's code against the FP64 unit's peak,
+with the ncu FP64-pipe figure of the same kernel beside it), the
+double-float variant (FP32 pipe) with its error against FP64, the CPU
+oracle timed on the host's cores, and -- under "configs" -- the other
+workloads measured in the same run: c1 (10,000-bin chi2 at 100 points and
+one full fit), c3 (the 2-D autograd forward + backward), c4 (4096 uneven
+histograms, batched time-to-fit against the plain per-histogram FP64 path)
+and c5 (the learned start against the heuristic start and the plain path),
+each with its arithmetic type, roofline, CPU oracle baseline and oracle
+parity at sampled points.
+
+`--impl reference` times the CPU oracle alone (the reference arm).  Under
+torchrun each rank evaluates its own 50 parameter points on its own copy of
+the events (weak scaling; no collective on the data path) and the configs
+are not run.  Other workloads: --workload c1|c3|c4|c5 (one config alone),
+c5fit, fig3b, gemm, expr.
 """
 import argparse
 import ctypes
+import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -31,6 +46,7 @@ METRIC = "gradient evals/s and bin-grads/s (frac of roofline); time-to-fit vs pl
 UNIT = "bin-grads/s"
 N_EVENTS = 10 ** 7
 N_POINTS = 50
+PKG = os.path.join(ROOT, "paper_2203_06139_gb300")
 
 
 def workload_name(n_events, n_points):
@@ -43,6 +59,11 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def log(msg):
+    sys.stderr.write("[bench] %s\n" % msg)
+    sys.stderr.flush()
 
 
 class Clocks:
@@ -58,7 +79,7 @@ class Clocks:
 
     def start(self):
         try:
-            self.out = open(os.devnull if False else "/tmp/cg_clocks_%d.csv" % os.getpid(), "w")
+            self.out = open("/tmp/cg_clocks_%d.csv" % os.getpid(), "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
                                        "--format=csv,noheader,nounits", "-lms", "200"],
                                       stdout=self.out, stderr=subprocess.DEVNULL)
@@ -88,87 +109,192 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+# ----------------------------------------------------------------------------
+# Peaks
+# ----------------------------------------------------------------------------
+PROBE_SRC = os.path.join(ROOT, "bench_support", "unit_rates.cu")
+PROBE_LIB = os.path.join(ROOT, "bench_support", "libcg_probe.so")
+
+
+def build_probe():
+    """Compile the unit-rate probe (nvcc, sm_103a) next to its source."""
+    if os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(PROBE_SRC):
+        return PROBE_LIB
+    tmp = "%s.%d.tmp" % (PROBE_LIB, os.getpid())
+    nvcc = os.environ.get("NVCC") or ("/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc")
+                                      else "nvcc")
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
+                    "-shared", "-cudart", "shared", "-o", tmp, PROBE_SRC], check=True, capture_output=True)
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
+
+
 def unit_rates():
-    """FP64 FMA, exp, log, reciprocal and FP32 FMA rates measured on this GPU."""
+    """FP64 and FP32 FMA instruction rates measured on this GPU (per thread-level instruction)."""
     import torch
-    from paper_2203_06139_gb300 import _build
-    L = ctypes.CDLL(_build.build_probe())
+    L = ctypes.CDLL(build_probe())
     L.cgp_unit_rates.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     scratch = torch.empty(nsm * 4 * 256, dtype=torch.float64, device="cuda")
-    out = (ctypes.c_double * 6)()
+    out = (ctypes.c_double * 3)()
     rc = L.cgp_unit_rates(out, ctypes.c_void_p(scratch.data_ptr()))
     torch.cuda.synchronize()
     if rc != 0:
         return None
-    return dict(dfma_per_s=out[0], exp_per_s=out[1], log_per_s=out[2], rcp_per_s=out[3], ffma_per_s=out[4],
-                n_sm=int(out[5]))
+    return dict(dfma_per_s=out[0], ffma_per_s=out[1], n_sm=int(out[2]))
 
 
-# Algorithmic FP64 work of one event at one parameter point in the fused
-# unbinned kernel: basic add/mul/fma operations and library calls.
-MIX_OPS = dict(basic=17, exp=2, log=1, rcp=1)
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p))
+    except (OSError, ValueError):
+        return {}
 
 
-def fp64_roofline(dur_s, n_units, rates, sm_max_mhz):
-    """ALU roofline of the FP64 kernel: DFMA-slot-equivalent work / time vs the
-    FP64 unit rate at the maximum SM clock (152 SMs x 2 DFMA/clk x 2 flop)."""
+# ----------------------------------------------------------------------------
+# Rooflines.  The FP64 kernels are bound by the FP64 unit: 2 DFMA per clock
+# per SM on GB300 (the recipe's 1.25 TFLOP/s = 152 SMs x 2 x 2 flop x 2.07
+# GHz; the probe measures the same within 1 %).  Their work is the number of
+# FP64-pipe instructions per unit, counted from the kernel's code below; one
+# FP64-pipe instruction is counted as one FMA slot (2 flop), so achieved /
+# peak is the FP64 unit's busy fraction that the counted work alone needs,
+# and it cannot exceed 1.  The double-float kernels run on the FP32 pipe
+# (152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s).
+# ----------------------------------------------------------------------------
+
+# FP64-pipe instructions per unit of work, counted from the code
+# (cg_models_fp64.cuh, cg_fp64.cuh, cg_grad.cu, cg_fit.cu):
+#  - exp2: 3 for the reduction (two additions of 1.5 * 2^40, one
+#    subtraction), 3 for the polynomial, 1 for T (1 + p) = 7;
+#  - reciprocal: 3 FMAs after the hardware estimate; log: 13;
+#  - event-point of the mixture: x - mu, c2 d, (c2 d) d, exp2, x - lo,
+#    nl2 xl, exp2, b eE, fma, reciprocal, running product, U, V, U d, five
+#    accumulations = 1+1+1+7+1+1+7+1+1+3+1+1+1+1+5 = 33;
+#  - bin-point of the 1-D chi2 of one Gaussian + line, four points per
+#    tile: Horner 1, d 1, exponent 2, exp2 7, peak 1, residual / adjoint /
+#    value 3, peak adjoints 5, polynomial adjoints 2 = 22, plus the bin's
+#    own work shared by the four points (centre: conversion + FMA; weight:
+#    3 FMAs of the reciprocal and the factor -2) 6 / 4 = 1.5: 23.5;
+#  - bin-evaluation of the batched chi2 fit of one Gaussian + quadratic
+#    (one point per bin): centre 2, weight 4, Horner 2, peak 11, chi2 3,
+#    peak adjoints 5, polynomial adjoints 5 = 32;
+#  - bin-evaluation of the Baker-Cousins fit of three Gaussians + line: bin
+#    work 2 + log of y 13 + 1, Horner 1, peaks 3 x 11, log 13, reciprocal
+#    3, value 3, adjoint 1, peak adjoints 15, polynomial adjoints 2 = 87;
+#  - 2-D bin: centres 2 x 3, log 13, reciprocal 3, adjoint seed, value and
+#    constant 4 = 26; per (bin, Gaussian kept by the tile's culling):
+#    dx, dy 2, quadratic form 5, exp2 7, model 1, adjoints 3 + 6 = 24.
+FP64_INSTR = {"mix": 33, "gp1_c1": 23.5, "fit_c4": 32, "fit_c5": 87, "rg2_bin": 26, "rg2_gauss": 24}
+
+# FP32-pipe operations per unit of the double-float kernels (cg_df64.cuh,
+# cg_df64.cu, cg_models_df64.cuh): event-point of the mixture: two df64
+# subtractions 22, square + product for the exponent 14, rate product 7, two
+# exp 120, sum of two products 21, fallback test 4, reciprocal 8, running
+# product for the log 9, five adjoint products 25, five compensated
+# accumulations 40, the log and flushes amortised over 32 events 3 = 273;
+# bin-point of the 1-D chi2 (one Gaussian + line): bin centre 24, Horner 18,
+# the peak 100, count split 2, chi2 term 36, value accumulation 8, peak
+# adjoints 36, polynomial adjoints 20 = 244.
+DF64_OPS = {"mix": 273, "gp1_c1": 244}
+
+
+def fp64_peak_tflops(sm_max_mhz, n_sm=152):
+    return n_sm * 2 * 2 * (sm_max_mhz or 2070.0) * 1e6 / 1e12
+
+
+def fp32_peak_tflops(sm_max_mhz, n_sm=152):
+    return n_sm * 128 * 2 * (sm_max_mhz or 2070.0) * 1e6 / 1e12
+
+
+def roofline_fp64(kernel, instr_per_unit, n_units, dur_s, sm_max_mhz, rates=None, unit="unit"):
+    """ALU roofline of an FP64 kernel (see the comment above FP64_INSTR)."""
     nsm = rates["n_sm"] if rates else 152
-    peak_dfma = nsm * 2 * (sm_max_mhz or 2070.0) * 1e6
+    peak = fp64_peak_tflops(sm_max_mhz, nsm)
+    achieved = instr_per_unit * n_units * 2 / dur_s / 1e12
+    r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+         "traffic": None, "kernel": kernel,
+         "work_per_unit": "%g FP64-pipe instructions per %s (counted from the code; 2 flop per instruction slot)"
+                          % (instr_per_unit, unit),
+         "peak_basis": "FP64 unit: %d SMs x 2 DFMA/clk x 2 flop x %.0f MHz (unit counts and max clock)"
+                       % (nsm, sm_max_mhz or 2070.0)}
     if rates:
-        c_exp = rates["dfma_per_s"] / rates["exp_per_s"]
-        c_log = rates["dfma_per_s"] / rates["log_per_s"]
-        c_rcp = rates["dfma_per_s"] / rates["rcp_per_s"]
-    else:
-        c_exp, c_log, c_rcp = 23.7, 36.6, 7.8
-    slots = MIX_OPS["basic"] + MIX_OPS["exp"] * c_exp + MIX_OPS["log"] * c_log + MIX_OPS["rcp"] * c_rcp
-    achieved = slots * n_units * 2 / dur_s / 1e12
-    peak = peak_dfma * 2 / 1e12
+        r["probe_fp64_tflops"] = rates["dfma_per_s"] * 2 / 1e12
+    return r
+
+
+def roofline_df64(kernel, ops_per_unit, n_units, dur_s, sm_max_mhz, rates=None, unit="unit"):
+    """ALU roofline of a double-float kernel: FP32-pipe operations / time vs the FP32 unit."""
+    nsm = rates["n_sm"] if rates else 152
+    peak = fp32_peak_tflops(sm_max_mhz, nsm)
+    achieved = ops_per_unit * n_units * 2 / dur_s / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "k_mix_fp64",
-            "work_per_unit": "%.1f DFMA-slot equivalents per event-point (17 add/mul/fma + 2 exp x %.1f + "
-                             "1 log x %.1f + 1 rcp x %.1f)" % (slots, c_exp, c_log, c_rcp),
-            "peak_basis": "FP64 unit: %d SMs x 2 DFMA/clk x 2 flop x %.0f MHz (unit counts and max clock)"
+            "traffic": None, "kernel": kernel,
+            "work_per_unit": "%d FP32-pipe operations per %s of the double-float emulation (2 flop each); frac is "
+                             "the FP32-issue efficiency of the emulation, not a fraction of the method's FP64 work"
+                             % (ops_per_unit, unit),
+            "peak_basis": "FP32 unit: %d SMs x 128 lanes x 2 flop x %.0f MHz (unit counts and max clock)"
                           % (nsm, sm_max_mhz or 2070.0)}
 
 
-# FP64 work of one bin at one parameter point of the 1-D chi2 model with one
-# Gaussian and a linear background (centre, Horner, difference, square,
-# exponent, residual, weight, adjoint products and sums).
-GP1_OPS = dict(basic=22, exp=1, log=0, rcp=1)
+def sources_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(PKG, f), "rb").read())
+    return h.hexdigest()[:16]
 
 
-def fp64_equivalent(dur_s, n_units, rates, sm_max_mhz, ops):
-    """The same per-element work counted in FP64 DFMA-slot equivalents (calls
-    weighted by the measured FP64 call rates) against the FP64 unit's peak:
-    the roofline an FP64 kernel would have.  frac > 1: the kernel finishes
-    faster than an FP64 kernel could on this GPU."""
-    nsm = rates["n_sm"] if rates else 152
-    peak_dfma = nsm * 2 * (sm_max_mhz or 2070.0) * 1e6
-    if rates:
-        c_exp = rates["dfma_per_s"] / rates["exp_per_s"]
-        c_log = rates["dfma_per_s"] / rates["log_per_s"]
-        c_rcp = rates["dfma_per_s"] / rates["rcp_per_s"]
-    else:
-        c_exp, c_log, c_rcp = 23.7, 36.6, 7.8
-    slots = ops["basic"] + ops["exp"] * c_exp + ops["log"] * c_log + ops["rcp"] * c_rcp
-    t_bound = slots * n_units / peak_dfma
-    return {"slots_per_unit": slots, "fp64_bound_ms": t_bound * 1e3, "kernel_ms": dur_s * 1e3,
-            "frac": t_bound / dur_s,
-            "note": "FP64 roofline time of the same work / kernel time (> 1: faster than the FP64 roofline)"}
+# Figures of one ncu capture per kernel, valid for the kernel sources whose
+# hash is given (reported as null once those sources change): DRAM bytes per
+# launch of the benchmarked workload and the FP64-pipe busy fraction (the
+# capture's workload named).  The commands are in profiles/.
+FP64_SOURCES = ["csrc/cg_grad.cu", "csrc/cg_fp64.cuh", "csrc/cg_fp64_tables.inc", "csrc/cg_models_fp64.cuh",
+                "csrc/cg_models.cuh", "csrc/cg_tiles.cuh", "csrc/cg_internal.cuh"]
+NCU_RECORDS = {}
 
 
-def cpu_oracle_rate(n_events, thetas, threads=None):
-    """The CPU tape oracle over a bounded sample, parallel over parameter points."""
+def ncu_record(kernel, n_events=None, n_points=None):
+    rec = NCU_RECORDS.get(kernel)
+    if not rec:
+        return None
+    if rec.get("workload") and (n_events, n_points) != tuple(rec["workload"]):
+        return None
+    if sources_hash(rec["sources"]) != rec["sources_sha256_16"]:
+        return None
+    return rec
+
+
+# ----------------------------------------------------------------------------
+# Parity: e_k = |g_k - o_k| / max(|o_k|, 1e-6 S_k) against the oracle (the
+# error metric of the 1e-10 bar), the value compared plainly.
+# ----------------------------------------------------------------------------
+def parity(values, grads, refs):
+    import numpy as np
+    eg, ev = 0.0, 0.0
+    for v, g, r in zip(values, grads, refs):
+        den = np.maximum(np.abs(r.grad), 1e-6 * r.scale)
+        eg = max(eg, float(np.max(np.abs(np.asarray(g) - r.grad) / den)))
+        ev = max(ev, abs(float(v) - r.value) / max(abs(r.value), 1e-300))
+    return {"max_grad_rel_err": eg, "max_value_rel_err": ev, "points": len(refs), "bar": 1e-10,
+            "ok": bool(eg <= 1e-10 and ev <= 1e-10)}
+
+
+def _threads():
+    return os.cpu_count() or 1
+
+
+def cpu_oracle_mix(n_events, thetas, threads=None):
+    """The CPU tape oracle over a bounded sample, parallel over parameter
+    points: (event-points/s, threads, seconds, the oracle's results)."""
     import oracle
     from paper_2203_06139_gb300 import synth
     oracle.build()
     x = synth.c2_events(n_events)
-    threads = threads or os.cpu_count() or 1
+    threads = threads or _threads()
     t0 = time.perf_counter()
-    oracle.many(oracle.unbinned_mix, thetas, threads=threads, x=x, lo=0.0, hi=10.0)
+    refs = oracle.many(oracle.unbinned_mix, thetas, threads=threads, x=x, lo=0.0, hi=10.0)
     dt = time.perf_counter() - t0
-    return n_events * len(thetas) / dt, threads, dt
+    return n_events * len(thetas) / dt, threads, dt, refs
 
 
 def cpu_closed_rates(n_events, thetas):
@@ -179,7 +305,7 @@ def cpu_closed_rates(n_events, thetas):
     from paper_2203_06139_gb300 import synth
     oracle.build()
     x = synth.c2_events(n_events)
-    cores = os.cpu_count() or 1
+    cores = _threads()
     out = {}
     for name, threads, pts in (("all_cores", 0, thetas), ("one_core", 1, thetas[:2])):
         t0 = time.perf_counter()
@@ -199,46 +325,68 @@ def cpu_closed_rates(n_events, thetas):
                       % (n_events, len(thetas))}
 
 
-def run_reference(args):
-    rank, world, _ = dist_env()
-    if rank != 0:
-        return
-    from paper_2203_06139_gb300 import synth
-    thetas = synth.c2_theta_points(args.points)
-    n_sample = 400000
-    cores = os.cpu_count() or 1
-    times = []
-    for _ in range(args.warmup):
-        cpu_oracle_rate(n_sample, thetas, cores)
-    for _ in range(args.steps):
-        r, cores, dt = cpu_oracle_rate(n_sample, thetas, cores)
-        times.append(dt)
-    dt = sum(times) / len(times)
-    value = n_sample * args.points / dt
-    sample = "first %d of the %g events x all %d parameter points per step" % (n_sample, args.events, args.points)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(args.events, args.points), "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+def _timed(fn, steps, warmup, flush=None):
+    """Device time per call of fn (CUDA events on the current stream), L2 flushed before each."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return sum(ms) / len(ms)
 
 
-def run(args):
+def _graph_timed(fn, steps, warmup, flush=None):
+    """Device time per call of fn replayed from a CUDA graph (no host work
+    inside the timed region), L2 flushed before each replay."""
+    import torch
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(max(warmup, 1)):
+            fn()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        fn()
+    return _timed(graph.replay, steps, warmup, flush)
+
+
+def _kernel_ms(cg, fn, steps, flush=None):
+    """Average duration of the dominant kernel of fn (events recorded by libcg
+    around its launch, on the launching stream), L2 flushed before each."""
+    import torch
+    stream = torch.cuda.current_stream()
+    k0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    k1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for e in k0 + k1:
+        e.record(stream)
+    torch.cuda.synchronize()
+    for i in range(steps):
+        if flush is not None:
+            flush.zero_()
+        cg.set_profile_events(k0[i], k1[i])
+        fn()
+        cg.set_profile_events(None, None)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in zip(k0, k1)) / steps
+
+
+# ----------------------------------------------------------------------------
+# Headline: the unbinned mixture, 10^7 events x 50 points, FP64
+# ----------------------------------------------------------------------------
+def headline(args, dev, rank, world, local):
     import numpy as np
     import torch
-
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local if world > 1 else 0)
-    torch.cuda.set_device(dev)
-
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_2203_06139_gb300 import cg, synth
 
     N_EV, N_PT = args.events, args.points
@@ -246,8 +394,7 @@ def run(args):
     th_host = synth.c2_theta_points(N_PT * world)[rank * N_PT:(rank + 1) * N_PT].copy()
     x = torch.tensor(x_host, device=dev)
     th = torch.tensor(th_host, device=dev)
-    prec = cg.PREC_DF64 if args.prec == "df64" else cg.PREC_FP64
-    pb = cg.Problem.mixture(x, 0.0, 10.0, precision=prec)
+    pb = cg.Problem.mixture(x, 0.0, 10.0, precision=cg.PREC_FP64)
     values = torch.empty(N_PT, dtype=torch.float64, device=dev)
     grads = torch.empty((N_PT, 4), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -261,8 +408,6 @@ def run(args):
     torch.cuda.synchronize()
     if pb.status(N_PT) != cg.OK:
         raise SystemExit("device status not OK after warm-up")
-
-    rates = unit_rates() if rank == 0 else None
 
     # ---- timed region: K steps, L2 flushed before each, CUDA events per step ----
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -305,13 +450,17 @@ def run(args):
     g_pin = torch.empty((N_PT, 4), dtype=torch.float64).pin_memory()
     x_dev = torch.empty_like(x)
     th_dev = torch.empty_like(th)
-    pe = cg.Problem.mixture(x_dev, 0.0, 10.0, precision=prec)
-    for _ in range(2):
+    pe = cg.Problem.mixture(x_dev, 0.0, 10.0, precision=cg.PREC_FP64)
+
+    def e2e_step():
         x_dev.copy_(x_pin, non_blocking=True)
         th_dev.copy_(th_pin, non_blocking=True)
         cg.batch_gradient(pe, th_dev, values, grads)
         v_pin.copy_(values, non_blocking=True)
         g_pin.copy_(grads, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -319,11 +468,7 @@ def run(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        x_dev.copy_(x_pin, non_blocking=True)
-        th_dev.copy_(th_pin, non_blocking=True)
-        cg.batch_gradient(pe, th_dev, values, grads)
-        v_pin.copy_(values, non_blocking=True)
-        g_pin.copy_(grads, non_blocking=True)
+        e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_s = e0.elapsed_time(e1) / 1e3
@@ -332,192 +477,110 @@ def run(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s = float(t.item())
     assert np.allclose(v_pin.numpy(), values.cpu().numpy())
+    v64, g64 = values.clone(), grads.clone()
 
-    # ---- the same step on the FP64 path (comparison leg) ----
-    fp64_leg = None
-    if prec != cg.PREC_FP64 and not args.no_fp64_leg:
-        p64 = cg.Problem.mixture(x, 0.0, 10.0, precision=cg.PREC_FP64)
-        v64 = torch.empty_like(values)
-        g64 = torch.empty_like(grads)
-        for _ in range(3):
-            cg.batch_gradient(p64, th, v64, g64)
-        torch.cuda.synchronize()
-        f0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        f1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        for i in range(args.steps):
-            flush.zero_()
-            f0[i].record(stream)
-            cg.batch_gradient(p64, th, v64, g64)
-            f1[i].record(stream)
-        torch.cuda.synchronize()
-        ms64 = sum(a.elapsed_time(b) for a, b in zip(f0, f1)) / args.steps
-        cg.batch_gradient(pb, th, values, grads)
-        rel_g = float(((grads - g64).abs() / g64.abs()).max())
-        rel_v = float(((values - v64).abs() / v64.abs()).max())
-        fp64_leg = {"ms_per_step": ms64, "value": N_EV * N_PT / (ms64 / 1e3), "unit": UNIT,
-                    "speedup_of_headline": ms64 / (total_s / args.steps * 1e3),
-                    "headline_vs_fp64_max_rel_err": {"grad": rel_g, "value": rel_v}}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "dtype_note": "FP64 arithmetic throughout (table-driven FP64 exp2/log and a Newton reciprocal, each within "
+                      "2 ulp); FP64 accumulation",
+        "data": "synthetic (seeded numpy PCG64; see synth.py)",
+        "config": {"workload": workload_name(N_EV, N_PT), "events": N_EV, "points_per_gpu": N_PT,
+                   "l2": "flushed before every timed step (256 MB write)",
+                   "parallelism": "replicas over %d GPU(s), independent parameter points" % world},
+        "grad_evals_per_s": N_PT * args.steps * world / total_s,
+        "e2e": {"value": units / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": x_pin.numel() * 8 + th_pin.numel() * 8,
+                "d2h_bytes_per_step": v_pin.numel() * 8 + g_pin.numel() * 8},
+        "gpu_launches": 2 * args.steps,   # tile kernel + finalize per step
+        "kernel_ms": kern_s * 1e3,
+        "clocks": clk,
+    }
+    if rank != 0:
+        return line, None
+    rates = unit_rates()
+    roof = roofline_fp64("k_mix_fp64", FP64_INSTR["mix"], N_EV * N_PT, kern_s, clk.get("sm_max_mhz"), rates,
+                         "event-point")
+    rec = ncu_record("k_mix_fp64", N_EV, N_PT)
+    roof["algorithmic_bytes"] = N_EV * 8
+    roof["traffic"] = rec["dram_bytes"] if rec else None
+    roof["ncu_fp64_pipe_pct"] = rec["fp64_pipe_pct"] if rec else None
+    line["roofline"] = roof
+    line["unit_rates"] = rates
 
-    if rank == 0:
-        roof = fp64_roofline(kern_s, N_EV * N_PT, rates, clk.get("sm_max_mhz")) if prec == cg.PREC_FP64 \
-            else df64_roofline(kern_s, N_EV * N_PT, rates, clk.get("sm_max_mhz"))
-        if prec == cg.PREC_DF64:
-            roof["traffic"] = _traffic_if_current(DF64_MIX_TRAFFIC, N_EV, N_PT)
-            roof["algorithmic_bytes"] = N_EV * 8
-            roof["fp64_equivalent"] = fp64_equivalent(kern_s, N_EV * N_PT, rates, clk.get("sm_max_mhz"), MIX_OPS)
-        cpu_n = min(N_EV, 10000000)   # the whole workload at its default size (about 6 s on 16 Grace cores)
-        cpu_v, cores, cpu_dt = cpu_oracle_rate(cpu_n, synth.c2_theta_points(N_PT))
-        cpu_closed = cpu_closed_rates(2000000, synth.c2_theta_points(N_PT)[:10])
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == cg.PREC_FP64 else "df64",
-            "dtype_note": "f64 arithmetic" if prec == cg.PREC_FP64 else
-            "double-float (pairs of f32 on the FP32 pipe, f64-accurate) with f64 accumulation",
-            "data": "synthetic (seeded numpy PCG64; see synth.py)",
-            "config": {"workload": workload_name(N_EV, N_PT), "events": N_EV, "points_per_gpu": N_PT,
-                       "l2": "flushed before every timed step (256 MB write)", "parallelism":
-                       "replicas over %d GPU(s), independent parameter points" % world},
-            "grad_evals_per_s": N_PT * args.steps * world / total_s,
-            "e2e": {"value": units / e2e_s, "unit": UNIT,
-                    "h2d_bytes_per_step": x_pin.numel() * 8 + th_pin.numel() * 8,
-                    "d2h_bytes_per_step": v_pin.numel() * 8 + g_pin.numel() * 8},
-            "gpu_launches": (3 if prec == cg.PREC_DF64 else 2) * args.steps,   # (split,) tiles, finalize
-            "kernel_ms": kern_s * 1e3,
-            "roofline": roof,
-            "clocks": clk,
-            "unit_rates": rates,
-            "fp64_path": fp64_leg,
-            "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "first %d events x %d parameter points (%.1f s wall)" % (cpu_n, N_PT, cpu_dt),
-                             "closed_form": cpu_closed},
-        }
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
-
-
-# FP32-pipe operations of one event at one parameter point in the double-float
-# kernel, counted from its arithmetic (csrc/cg_df64.cuh, cg_df64.cu): two df64
-# subtractions 22, square + product for the exponent 14, rate product 7, two
-# exp 120, sum of two products 21, fallback test 4, reciprocal 8, running
-# product for the log 9, five adjoint products 25, five compensated
-# accumulations 40, the log and flushes amortised over 32 events 3.  (The
-# events are split into float pairs once per call, 2 operations per event,
-# outside this kernel.)
-DF64_MIX_OPS = 273
-
-# DRAM bytes per launch of k_mix_df64 on the default workload, from
-# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum ... -k regex:k_mix_df64`
-# (80,480,512 read + 3,583,232 written), valid for the kernel sources whose
-# hash is given; reported as null once those sources change.
-DF64_MIX_TRAFFIC = {"bytes": 80480512 + 3583232, "sources_sha256_16": "267e6442e6c3e0f7",
-                    "sources": ["csrc/cg_df64.cu", "csrc/cg_df64.cuh", "csrc/cg_models.cuh", "csrc/cg_tiles.cuh",
-                                "csrc/cg_internal.cuh"]}
-
-
-def _traffic_if_current(rec, n_events, n_points):
-    import hashlib
-    if n_events != N_EVENTS or n_points != N_POINTS:
-        return None
-    pkg = os.path.join(ROOT, "paper_2203_06139_gb300")
-    h = hashlib.sha256()
-    for f in rec["sources"]:
-        h.update(open(os.path.join(pkg, f), "rb").read())
-    return rec["bytes"] if h.hexdigest()[:16] == rec["sources_sha256_16"] else None
-
-
-# FP32-pipe operations of one bin at one parameter point in the double-float
-# 1-D kernel for one Gaussian + linear background under chi2, counted from its
-# arithmetic (csrc/cg_models_df64.cuh): bin centre 24, Horner 18, the peak
-# (difference, square, exponent product, exp 60, product, sum) 100, count
-# split 2, chi2 term (reciprocal 8, residual, two products, adjoint) 36, value
-# accumulation 8, peak adjoints 36, polynomial adjoints 20.
-DF64_GP1_OPS = 244
-
-
-def df64_roofline(dur_s, n_units, rates, sm_max_mhz, ops=DF64_MIX_OPS, kernel="k_mix_df64", unit="event-point"):
-    """ALU roofline of the double-float kernel: FP32-pipe operations / time vs the
-    FP32 unit rate at the maximum SM clock (152 SMs x 128 lanes x 2 flop)."""
-    nsm = rates["n_sm"] if rates else 152
-    peak = nsm * 128 * 2 * (sm_max_mhz or 2070.0) * 1e6 / 1e12
-    achieved = ops * n_units * 2 / dur_s / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": kernel,
-            "work_per_unit": "%d FP32-pipe operations per %s (FMA-equivalent flops = 2 per op)" % (ops, unit),
-            "peak_basis": "FP32 unit: %d SMs x 128 lanes x 2 flop x %.0f MHz (unit counts and max clock)"
-                          % (nsm, sm_max_mhz or 2070.0)}
-
-
-def _timed(fn, steps, warmup, flush=None):
-    """Device time per call of fn (CUDA events on the current stream), L2 flushed before each."""
-    import torch
-    for _ in range(warmup):
-        fn()
+    # ---- the double-float variant of the same step (FP32 pipe) ----
+    pd = cg.Problem.mixture(x, 0.0, 10.0, precision=cg.PREC_DF64)
+    vd = torch.empty_like(values)
+    gd = torch.empty_like(grads)
+    ms_df = _timed(lambda: cg.batch_gradient(pd, th, vd, gd), args.steps, 3, flush)
+    kd = _kernel_ms(cg, lambda: cg.batch_gradient(pd, th, vd, gd), args.steps, flush) / 1e3
+    cg.batch_gradient(pd, th, vd, gd)
     torch.cuda.synchronize()
-    ms = []
-    for _ in range(steps):
-        if flush is not None:
-            flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        fn()
-        b.record()
-        torch.cuda.synchronize()
-        ms.append(a.elapsed_time(b))
-    return sum(ms) / len(ms)
+    line["variants"] = {"df64": {
+        "dtype": "df64", "note": "double-float: pairs of FP32 values with error-free transformations on the FP32 "
+                                 "pipe (about 48 significand bits, the FP32 exponent range), FP64 accumulation",
+        "ms_per_step": ms_df, "value": N_EV * N_PT / (ms_df / 1e3), "unit": UNIT,
+        "speedup_over_fp64": (total_s / args.steps * 1e3) / ms_df,
+        "max_rel_err_vs_fp64": {"grad": float(((gd - g64).abs() / g64.abs()).max()),
+                                "value": float(((vd - v64).abs() / v64.abs()).max())},
+        "roofline": roofline_df64("k_mix_df64", DF64_OPS["mix"], N_EV * N_PT, kd, clk.get("sm_max_mhz"), rates,
+                                  "event-point")}}
+    # ---- the CPU oracle on the host cores, and parity of every point of the step ----
+    cpu_n = min(N_EV, 10 ** 7)
+    cpu_v, cores, cpu_dt, refs = cpu_oracle_mix(cpu_n, th_host)
+    line["cpu_baseline"] = {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": "first %d events x %d parameter points (%.1f s wall)" % (cpu_n, N_PT, cpu_dt),
+                            "closed_form": cpu_closed_rates(2000000, th_host[:10])}
+    if cpu_n == N_EV:
+        line["parity"] = parity(v64.cpu().numpy(), g64.cpu().numpy(), refs)
+        line["parity"]["what"] = "all %d points of the timed step over all %d events against the CPU tape oracle" % (
+            N_PT, N_EV)
+    return line, rates
 
 
-def run_c1(args):
-    """10,000-bin histogram: gradients at 100 points, and one full fit."""
+# ----------------------------------------------------------------------------
+# Configurations measured beside the headline
+# ----------------------------------------------------------------------------
+def config_c1(args, rates, sm_max_mhz):
+    """10,000-bin chi2 histogram (one Gaussian + line): gradients at 100
+    parameter points in one cg_batch_gradient call replayed from a CUDA graph,
+    and one full fit on the plain path and batched."""
     import numpy as np
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
+    import oracle
+    from oracle.fit import bfgs_fit
     from paper_2203_06139_gb300 import cg, synth
     from paper_2203_06139_gb300.fit import BatchFitter, HistBatch, SingleFitter, TileMap
+    oracle.build()
     h = synth.c1_histogram()
     y = torch.tensor(h["y"], device="cuda")
-    prec = cg.PREC_DF64 if args.prec == "df64" else cg.PREC_FP64
-    pb = cg.Problem.gauss_poly(y, 0.0, 10.0, 1, 1, cg.OBJ_CHI2, precision=prec)
-    pb64 = cg.Problem.gauss_poly(y, 0.0, 10.0, 1, 1, cg.OBJ_CHI2)
-    th = torch.tensor(synth.c1_theta_points(), device="cuda")
-    v = torch.empty(100, dtype=torch.float64, device="cuda")
-    g = torch.empty((100, 5), dtype=torch.float64, device="cuda")
+    th_np = synth.c1_theta_points()
+    th = torch.tensor(th_np, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    ms_eager = _timed(lambda: cg.batch_gradient(pb, th, v, g), args.steps, max(3, args.warmup), flush)
-    # the step as a repeated evaluation runs it: the one cg_batch_gradient call
-    # (tile kernel + finalize) captured in a CUDA graph and replayed
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        cg.batch_gradient(pb, th, v, g)
-    ms = _timed(graph.replay, args.steps, max(3, args.warmup), flush)
-    # the tile kernel alone (events around its launch, inside cg_batch_gradient)
-    k0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    k1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stream = torch.cuda.current_stream()
-    for e in k0 + k1:
-        e.record(stream)
-    clocks = Clocks(0)
-    torch.cuda.synchronize()
-    clocks.start()
-    for i in range(args.steps):
-        flush.zero_()
-        cg.set_profile_events(k0[i], k1[i])
-        cg.batch_gradient(pb, th, v, g)
-        cg.set_profile_events(None, None)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    kern_s = sum(a.elapsed_time(b) for a, b in zip(k0, k1)) / 1e3 / args.steps
-    rates = unit_rates()
-    if prec == cg.PREC_DF64:
-        roof = df64_roofline(kern_s, 100 * 10000, rates, clk.get("sm_max_mhz"), ops=DF64_GP1_OPS,
-                             kernel="k_gp1_df64", unit="bin-point")
-        roof["fp64_equivalent"] = fp64_equivalent(kern_s, 100 * 10000, rates, clk.get("sm_max_mhz"), GP1_OPS)
-    else:
-        roof = None
+    steps, warm = max(args.steps, 20), max(args.warmup, 5)
+    out = {}
+    for name, prec in (("fp64", cg.PREC_FP64), ("df64", cg.PREC_DF64)):
+        pb = cg.Problem.gauss_poly(y, 0.0, 10.0, 1, 1, cg.OBJ_CHI2, precision=prec)
+        v = torch.empty(100, dtype=torch.float64, device="cuda")
+        g = torch.empty((100, 5), dtype=torch.float64, device="cuda")
+        call = lambda: cg.batch_gradient(pb, th, v, g)
+        ms = _graph_timed(call, steps, warm, flush)
+        kern = _kernel_ms(cg, call, steps, flush) / 1e3
+        call()
+        torch.cuda.synchronize()
+        out[name] = dict(ms=ms, kern_s=kern, v=v.cpu().numpy(), g=g.cpu().numpy())
+    f64 = out["fp64"]
+    refs = oracle.many(oracle.binned1d, th_np, K=1, D=1, poly_mode=0, obj=oracle.CHI2, y=h["y"], lo=0.0, hi=10.0)
+    t0 = time.perf_counter()
+    oracle.many(oracle.binned1d, th_np, K=1, D=1, poly_mode=0, obj=oracle.CHI2, y=h["y"], lo=0.0, hi=10.0)
+    cpu_dt = time.perf_counter() - t0
+    # one full fit from the first parameter point: the plain per-histogram
+    # path (full-GPU launches per trial point) and one batched fit
     th0 = torch.tensor(synth.c1_theta_points(1)[0], device="cuda")
+    pb64 = cg.Problem.gauss_poly(y, 0.0, 10.0, 1, 1, cg.OBJ_CHI2)
     sf = SingleFitter(pb64)
+    sf.fit(th0, max_iter=50, tol=1e-9)   # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     st = sf.fit(th0, max_iter=50, tol=1e-9)
@@ -525,39 +588,550 @@ def run_c1(args):
     t_single = time.perf_counter() - t0
     b = HistBatch(y, [0, 10000], [0.0], [10.0], 1, 1, cg.OBJ_CHI2)
     bf = BatchFitter(b, TileMap(0, 0, 512, 8))
+
     def batched():
         bf.init(th0.view(1, 5))
         bf.step(50, 1e-9)
     ms_fit = _timed(batched, 3, 2)
-    line = {"metric": METRIC, "workload": "c1", "value": 100 * 10000 / (ms / 1e3), "unit": UNIT,
-            "higher_is_better": True, "ms_per_step": ms, "grad_evals_per_s": 100 / (ms / 1e3),
-            "dtype": "f64" if prec == cg.PREC_FP64 else "df64",
-            "config": {"workload": "chi2, Gaussian + linear, 10,000 bins x 100 parameter points",
-                       "l2": "flushed before every timed step",
-                       "step": "one cg_batch_gradient call replayed from a CUDA graph"},
-            "eager_ms_per_step": ms_eager,
-            "full_fit": {"plain_path_s": t_single, "plain_iters": int(st.iters[0]), "plain_evals": int(st.n_eval[0]),
-                         "plain_F": float(st.f[0]), "one_cluster_fit_ms": ms_fit,
-                         "one_cluster_F": float(bf.states.f[0]), "status": int(bf.states.status[0])},
-            "gpu_launches": 2 * args.steps, "kernel_ms": kern_s * 1e3, "roofline": roof, "clocks": clk}
+    fg = lambda t: (lambda r: (r.value, r.grad))(oracle.binned1d(1, 1, 0, oracle.CHI2, h["y"], 0.0, 10.0, t))
+    gn = lambda t: oracle.binned1d_gn(1, 1, 0, oracle.CHI2, h["y"], 0.0, 10.0, t)
+    t0 = time.perf_counter()
+    ref_fit = bfgs_fit(fg, gn, synth.c1_theta_points(1)[0], max_iter=50, tol=1e-9)
+    t_cpu_fit = time.perf_counter() - t0
+    F_plain, F_batch = float(st.f[0]), float(bf.states.f[0])
+    roof = roofline_fp64("k_gp1_fp64", FP64_INSTR["gp1_c1"], 100 * 10000, f64["kern_s"], sm_max_mhz, rates,
+                         "bin-point")
+    rec = ncu_record("k_gp1_fp64")
+    roof["ncu_fp64_pipe_pct"] = rec["fp64_pipe_pct"] if rec else None
+    roof["traffic"] = rec["dram_bytes"] if rec else None
+    roof["algorithmic_bytes"] = 10000 * 16
+    rel = lambda a, b_: float(np.max(np.abs(a - b_) / np.abs(b_)))
+    return {
+        "workload": "chi2, Gaussian + linear, 10,000 bins x 100 parameter points; one full fit", "dtype": "f64",
+        "value": 1e6 / (f64["ms"] / 1e3), "unit": UNIT, "grad_evals_per_s": 100 / (f64["ms"] / 1e3),
+        "ms_per_step": f64["ms"], "kernel_ms": f64["kern_s"] * 1e3,
+        "step": "one cg_batch_gradient call (tile kernel + finalize) replayed from a CUDA graph, L2 flushed",
+        "roofline": roof,
+        "parity": dict(parity(f64["v"], f64["g"], refs), what="all 100 points against the CPU tape oracle"),
+        "variants": {"df64": {"dtype": "df64", "ms_per_step": out["df64"]["ms"],
+                              "value": 1e6 / (out["df64"]["ms"] / 1e3),
+                              "max_rel_err_vs_fp64": {"grad": rel(out["df64"]["g"], f64["g"]),
+                                                      "value": rel(out["df64"]["v"], f64["v"])},
+                              "roofline": roofline_df64("k_gp1_df64", DF64_OPS["gp1_c1"], 1e6,
+                                                        out["df64"]["kern_s"], sm_max_mhz, rates, "bin-point")}},
+        "full_fit": {"plain_path_ms": t_single * 1e3, "plain_iters": int(st.iters[0]),
+                     "plain_evals": int(st.n_eval[0]), "plain_F": F_plain, "plain_status": int(st.status[0]),
+                     "batched_ms": ms_fit, "batched_F": F_batch, "batched_status": int(bf.states.status[0]),
+                     "oracle_F": float(ref_fit["F"]), "oracle_iters": int(ref_fit["iters"]),
+                     "same_minimum_as_oracle": bool(abs(F_batch - ref_fit["F"]) <= 1e-6 * abs(ref_fit["F"]) and
+                                                    abs(F_plain - ref_fit["F"]) <= 1e-6 * abs(ref_fit["F"])),
+                     "dtype": "f64"},
+        "cpu_baseline": {"value": 1e6 / cpu_dt, "unit": UNIT, "cores": _threads(), "kind": "oracle",
+                         "sample": "the whole workload: 10,000 bins x 100 points (%.2f s)" % cpu_dt,
+                         "fit_s": t_cpu_fit, "fit_note": "the oracle's BFGS fit from the same start, one core"},
+    }
+
+
+def _c3_active_pairs(truth_or_theta, K=8, nx=4096, ny=4096, tile=64, cull=80.0):
+    """(bin, Gaussian) pairs the 2-D kernels evaluate: per 64 x 64 tile, the
+    Gaussians whose exponent can be below 80 somewhere in the tile's box of
+    bin centres (the kernels' culling rule), times the tile's bins."""
+    import numpy as np
+    th = np.asarray(truth_or_theta, dtype=np.float64)
+    hx, hy = 1.0 / nx, 1.0 / ny
+    tx = np.arange(0, nx, tile)
+    ty = np.arange(0, ny, tile)
+    bx0 = (tx + 0.5) * hx
+    bx1 = (np.minimum(tx + tile, nx) - 0.5) * hx
+    by0 = (ty + 0.5) * hy
+    by1 = (np.minimum(ty + tile, ny) - 0.5) * hy
+    nbx = (np.minimum(tx + tile, nx) - tx)
+    nby = (np.minimum(ty + tile, ny) - ty)
+    pairs = 0
+    for k in range(K):
+        mx, my = th[6 * k + 1], th[6 * k + 2]
+        sm = max(abs(th[6 * k + 3]), abs(th[6 * k + 4]))
+        ddx = np.maximum(0.0, np.maximum(bx0 - mx, mx - bx1))
+        ddy = np.maximum(0.0, np.maximum(by0 - my, my - by1))
+        q = 0.5 * (ddx[None, :] ** 2 + ddy[:, None] ** 2) / (sm * sm)
+        pairs += int(((q <= cull) * (nby[:, None] * nbx[None, :])).sum())
+    return pairs
+
+
+def config_c3(args, rates, sm_max_mhz):
+    """4096 x 4096 bins, 8 rotated Gaussians + constant, Poisson NLL, 49
+    parameters: the torch.autograd.Function forward + backward."""
+    import numpy as np
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+    from paper_2203_06139_gb300 import cg, synth
+    from paper_2203_06139_gb300.autograd import fit_objective
+    oracle.build()
+    hh = synth.c3_histogram()
+    counts = torch.tensor(hh["counts"], device="cuda")
+    th_np = synth.c3_theta_point(hh["truth"])[0]
+    steps, warm = max(args.steps, 5), max(args.warmup, 3)
+    out = {}
+    for name, prec in (("fp64", cg.PREC_FP64), ("df64", cg.PREC_DF64)):
+        pb = cg.Problem.rotgauss2d(counts, 8, precision=prec)
+        th = torch.tensor(th_np, device="cuda", requires_grad=True)
+
+        def fwd_bwd():
+            th.grad = None
+            fit_objective(th, pb).backward()
+        ms = _timed(fwd_bwd, steps, warm)
+        kern = _kernel_ms(cg, fwd_bwd, steps) / 1e3
+        th.grad = None
+        val = fit_objective(th, pb)
+        val.backward()
+        torch.cuda.synchronize()
+        out[name] = dict(ms=ms, kern_s=kern, v=float(val.detach()), g=th.grad.detach().cpu().numpy())
+    n = 4096 * 4096
+    pairs = _c3_active_pairs(th_np)
+    instr = FP64_INSTR["rg2_bin"] * n + FP64_INSTR["rg2_gauss"] * pairs
+    roof = roofline_fp64("k_rg2_fp64", instr / n, n, out["fp64"]["kern_s"], sm_max_mhz, rates, "bin")
+    roof["work_note"] = ("%.1f Gaussians per bin survive the 64 x 64-bin tiles' culling (%d pairs): %g + %g x %.2f "
+                         "instructions per bin" % (pairs / n, pairs, FP64_INSTR["rg2_bin"], FP64_INSTR["rg2_gauss"],
+                                                   pairs / n))
+    roof["algorithmic_bytes"] = n * 8
+    # parity and the CPU oracle: bands of rows, each a sub-problem with the
+    # same bin centres (its range [r0/4096, r1/4096) in y)
+    c_np = hh["counts"]
+
+    def band(r0, r1, theta):
+        return oracle.binned2d(8, np.ascontiguousarray(c_np[r0:r1]), 0.0, 1.0, r0 / 4096.0, r1 / 4096.0, theta)
+    r0 = 2048
+    pbb = cg.Problem.rotgauss2d(counts[r0:r0 + 16].contiguous(), 8, lo=(0.0, r0 / 4096.0),
+                                hi=(1.0, (r0 + 16) / 4096.0))
+    vb, gb = cg.gradient(pbb, torch.tensor(th_np, device="cuda"))
+    torch.cuda.synchronize()
+    ref = band(r0, r0 + 16, th_np)
+    rows = 64
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=_threads()) as ex:
+        list(ex.map(lambda i: band(i * 4, i * 4 + 4, th_np), range(rows // 4)))
+    cpu_dt = time.perf_counter() - t0
+    rel = lambda a, b_: float(np.max(np.abs(a - b_) / np.maximum(np.abs(b_), 1e-300)))
+    return {
+        "workload": "Poisson NLL, 8 rotated 2-D Gaussians + constant, 4096 x 4096 bins, 49 params, "
+                    "torch.autograd.Function forward + backward", "dtype": "f64",
+        "value": n / (out["fp64"]["ms"] / 1e3), "unit": UNIT, "grad_evals_per_s": 1e3 / out["fp64"]["ms"],
+        "ms_per_step": out["fp64"]["ms"], "kernel_ms": out["fp64"]["kern_s"] * 1e3,
+        "l2": "counts (134 MB) larger than L2", "roofline": roof,
+        "parity": dict(parity([float(vb)], [gb.cpu().numpy()], [ref]),
+                       what="rows 2048-2063 (65,536 bins) as a sub-problem against the CPU tape oracle"),
+        "variants": {"df64": {"dtype": "df64", "ms_per_step": out["df64"]["ms"],
+                              "value": n / (out["df64"]["ms"] / 1e3),
+                              "max_rel_err_vs_fp64": {"grad": rel(out["df64"]["g"], out["fp64"]["g"]),
+                                                      "value": abs(out["df64"]["v"] - out["fp64"]["v"]) /
+                                                      abs(out["fp64"]["v"])}}},
+        "cpu_baseline": {"value": rows * 4096 / cpu_dt, "unit": UNIT, "cores": _threads(), "kind": "oracle",
+                         "sample": "rows 0-63 (262,144 bins) in bands of 4 rows on a thread pool (%.1f s)" % cpu_dt},
+    }
+
+
+def _bin_evals(states, sizes):
+    import numpy as np
+    return float((states.n_eval.cpu().numpy().astype(np.float64) * np.asarray(sizes, dtype=np.float64)).sum())
+
+
+def _fit_to_convergence(fitter, theta0, block=50, cap=500, tol=1e-9):
+    """Device time from the start to every fit CONVERGED or failed (or the
+    iteration cap): init, then blocks of iterations until no fit is RUNNING."""
+    import torch
+    from paper_2203_06139_gb300 import cg
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fitter.init(theta0)
+    it = 0
+    while it < cap:
+        fitter.step(block, tol)
+        it += block
+        if not bool((fitter.states.status == cg.FIT_RUNNING).any()):
+            break
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), it
+
+
+def _strata(sizes, n_strata, per_stratum, seed=0):
+    """Indices of a size-stratified sample: histograms sorted by size, cut into
+    n_strata equal-count strata, per_stratum drawn from each (seeded)."""
+    import numpy as np
+    order = np.argsort(sizes, kind="stable")
+    parts = np.array_split(order, n_strata)
+    r = np.random.default_rng(seed)
+    return [(p, np.sort(r.choice(p, min(per_stratum, len(p)), replace=False))) for p in parts]
+
+
+def stratified_estimate(rows):
+    """Total over a population from a stratified sample: rows of (N_s, the
+    sampled values of stratum s); the estimate sum_s N_s mean_s and its
+    standard error sqrt(sum_s N_s^2 var_s / n_s (1 - n_s / N_s)) (sample
+    variance; a stratum sampled once contributes no variance)."""
+    est, var = 0.0, 0.0
+    for Ns, t in rows:
+        ns = len(t)
+        est += Ns * float(t.mean())
+        if ns > 1:
+            var += Ns * Ns * float(t.var(ddof=1)) / ns * (1.0 - ns / Ns)
+    return est, math.sqrt(var)
+
+
+def _plain_fits(make_problem, theta0, strata, max_iter, tol=1e-9):
+    """The plain per-histogram path on a stratified sample: per stratum the
+    mean fit time, and the estimate for the whole batch with its standard
+    error (stratified_estimate)."""
+    import numpy as np
+    import torch
+    from paper_2203_06139_gb300 import cg
+    from paper_2203_06139_gb300.fit import SingleFitter
+    rows = []
+    F, status, iters = {}, {}, {}
+    for part, idx in strata:
+        ts = []
+        for h in idx:
+            pb = make_problem(int(h))
+            sf = SingleFitter(pb)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = sf.fit(theta0[int(h)], max_iter=max_iter, tol=tol)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+            F[int(h)], status[int(h)], iters[int(h)] = float(st.f[0]), int(st.status[0]), int(st.iters[0])
+        rows.append((len(part), np.array(ts)))
+    est, se = stratified_estimate(rows)
+    return {"seconds_for_all": est, "standard_error_s": se,
+            "strata": [{"histograms": N, "sampled": len(t), "mean_ms": float(t.mean()) * 1e3} for N, t in rows],
+            "histograms_measured": sum(len(i) for _, i in strata)}, F, status, iters
+
+
+def config_c4(args, rates, sm_max_mhz):
+    """4096 histograms of 64-65,536 bins (log-uniform): 50 BFGS iterations of
+    every fit in one graph-captured persistent launch (tile map from the
+    autotuner), and the time to all fits converged, against the plain
+    per-histogram FP64 path on a size-stratified sample."""
+    import numpy as np
+    import torch
+    import oracle
+    from oracle.fit import bfgs_fit
+    from paper_2203_06139_gb300 import cg, synth
+    from paper_2203_06139_gb300.fit import BatchFitter, HistBatch, autotune
+    oracle.build()
+    d = synth.c4_batch()
+    sizes = np.diff(d["offsets"])
+    th0 = torch.tensor(d["start"], device="cuda")
+    res = {}
+    for name, prec in (("fp64", cg.PREC_FP64), ("df64", cg.PREC_DF64)):
+        b = HistBatch(d["y"], d["offsets"], d["lo"], d["hi"], 1, 2, cg.OBJ_CHI2, poly_mode=1, precision=prec)
+        best, timings = autotune(b, th0, n_steps=50)
+        f = BatchFitter(b, best)
+        f.capture(50, 1e-9, theta0=th0)
+        ms = _timed(f.replay, 3, 2)
+        st = f.states
+        r = dict(map=best.as_dict(), ms=ms, F=st.f.cpu().numpy(), status=st.status.cpu().numpy(),
+                 iters=st.iters.cpu().numpy(), evals=st.n_eval.cpu().numpy(), bin_evals=_bin_evals(st, sizes),
+                 autotune=timings[:3])
+        fc = BatchFitter(b, best)
+        r["conv_ms"], r["conv_iters"] = _fit_to_convergence(fc, th0)
+        r["conv_status"] = fc.states.status.cpu().numpy()
+        r["conv_F"] = fc.states.f.cpu().numpy()
+        res[name] = r
+        del f, fc
+    f64 = res["fp64"]
+    yt = torch.tensor(d["y"], device="cuda")
+
+    def problem(h):
+        o0, o1 = int(d["offsets"][h]), int(d["offsets"][h + 1])
+        return cg.Problem.gauss_poly(yt[o0:o1], 0.0, 1.0, 1, 2, cg.OBJ_CHI2, poly_mode=1)
+    strata = _strata(sizes, 8, max(8, args.plain_per_stratum))
+    problem(0)
+    plain50, Fp, sp, ip = _plain_fits(problem, th0, strata, 50)
+    plain_conv, Fpc, spc, _ = _plain_fits(problem, th0, strata, 500)
+    idx = np.array(sorted(Fp))
+    Fb = f64["F"][idx]
+    Fpv = np.array([Fp[h] for h in idx])
+    same = np.abs(Fb - Fpv) <= 1e-6 * np.abs(Fpv)
+    # oracle fits of a few sampled histograms (<= 8192 bins: seconds each on one core)
+    small = [int(i) for _, ii in strata for i in ii if sizes[int(i)] <= 8192][::6][:6]
+    t_cpu, orc = 0.0, []
+    for h in small:
+        o0, o1 = int(d["offsets"][h]), int(d["offsets"][h + 1])
+        yh = d["y"][o0:o1]
+        fg = lambda t, yh=yh: (lambda q: (q.value, q.grad))(oracle.binned1d(1, 2, 1, oracle.CHI2, yh, 0.0, 1.0, t))
+        gn = lambda t, yh=yh: oracle.binned1d_gn(1, 2, 1, oracle.CHI2, yh, 0.0, 1.0, t)
+        t0 = time.perf_counter()
+        ref = bfgs_fit(fg, gn, d["start"][h], max_iter=50, tol=1e-9)
+        t_cpu += time.perf_counter() - t0
+        orc.append((h, ref, (o1 - o0) * ref["evals"]))
+    cpu_rate = sum(x[2] for x in orc) / t_cpu
+    par_same = [abs(f64["F"][h] - ref["F"]) <= 1e-6 * abs(ref["F"]) for h, ref, _ in orc
+                if f64["status"][h] == cg.FIT_CONVERGED and ref["status"] == 1]
+    roof = roofline_fp64("k_fit_persistent", FP64_INSTR["fit_c4"], f64["bin_evals"], f64["ms"] / 1e3, sm_max_mhz,
+                         rates, "bin-evaluation")
+    roof["note"] = "the whole graph (init + persistent launch) timed; bin-evaluations from the fit states"
+    counts = lambda s: np.bincount(s, minlength=5).tolist()
+    return {
+        "workload": "4096 histograms, 64-65536 bins (log-uniform), Gaussian + quadratic, chi2, 50 BFGS iterations "
+                    "in one graph-captured persistent launch", "dtype": "f64",
+        "value": f64["ms"] / 1e3, "unit": "s time-to-fit (50 iterations, 4096 histograms)", "higher_is_better": False,
+        "bins": int(d["offsets"][-1]), "tile_map": f64["map"], "autotune": f64["autotune"],
+        "batched": {"ms": f64["ms"], "converged": int((f64["status"] == cg.FIT_CONVERGED).sum()),
+                    "status_counts": counts(f64["status"]), "mean_iters": float(f64["iters"].mean()),
+                    "mean_evals": float(f64["evals"].mean()), "bin_evaluations": f64["bin_evals"]},
+        "batched_to_convergence": {"ms": f64["conv_ms"], "iterations_run": f64["conv_iters"],
+                                   "status_counts": counts(f64["conv_status"])},
+        "plain_path": dict(plain50, dtype="f64", max_iter=50,
+                           converged_frac=float(np.mean([sp[h] == cg.FIT_CONVERGED for h in idx]))),
+        "plain_path_to_convergence": dict(plain_conv, max_iter=500,
+                                          converged_frac=float(np.mean([spc[h] == cg.FIT_CONVERGED for h in idx]))),
+        "speedup_vs_plain": plain50["seconds_for_all"] / (f64["ms"] / 1e3),
+        "speedup_vs_plain_to_convergence": plain_conv["seconds_for_all"] / (f64["conv_ms"] / 1e3),
+        "same_minimum_frac_sampled": float(same.mean()),
+        "lower_F_when_different": {"batched": int(((Fb < Fpv) & ~same).sum()),
+                                   "plain": int(((Fpv < Fb) & ~same).sum())},
+        "roofline": roof,
+        "parity": {"what": "oracle BFGS fits of %d sampled histograms (<= 8192 bins): batched FP64 minimum within "
+                           "1e-6 of the oracle's where both converged" % len(orc),
+                   "checked": len(par_same), "same_minimum": int(sum(par_same)),
+                   "ok": bool(len(par_same) > 0 and all(par_same))},
+        "variants": {"df64": {"dtype": "df64", "ms": res["df64"]["ms"], "map": res["df64"]["map"],
+                              "converged": int((res["df64"]["status"] == cg.FIT_CONVERGED).sum()),
+                              "to_convergence_ms": res["df64"]["conv_ms"],
+                              "same_minimum_as_fp64_frac": float(np.mean(
+                                  np.abs(res["df64"]["F"] - f64["F"]) <= 1e-6 * np.abs(f64["F"])))}},
+        "cpu_baseline": {"value": cpu_rate, "unit": "bin-evaluations/s", "cores": 1, "kind": "oracle",
+                         "sample": "oracle BFGS fits of %d sampled histograms of <= 8192 bins (%.1f s)"
+                                   % (len(orc), t_cpu),
+                         "seconds_for_batch_at_this_rate": f64["bin_evals"] / cpu_rate},
+    }
+
+
+def config_c5(args, rates, sm_max_mhz):
+    """Learned start: the network (BF16 tensor-core kernels) trained on fits
+    of method-generated histograms, then 65,536 held-out histograms fitted
+    from the learned start (refit from the heuristic start where that fit did
+    not converge, the lower minimum kept) against the heuristic start and
+    against the plain per-histogram FP64 path."""
+    import numpy as np
+    import torch
+    import oracle
+    from oracle.fit import bfgs_fit
+    from paper_2203_06139_gb300 import cg, synth
+    from paper_2203_06139_gb300 import learned_start as ls
+    oracle.build()
+    n_train = args.train_hists or 10 ** 6
+    t0 = time.perf_counter()
+    x, scale, theta = ls.make_training_set(n_train)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = ls.MLP(seed=0)
+    t0 = time.perf_counter()
+    curve = ls.train(net, x, scale, theta, epochs=args.epochs or 6, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del x, scale, theta
+    H = args.hists or 65536
+    y = synth.c5_batch_device(H, ls.N_BINS, chunk=0)["y"]
+    hw = min(H, 1024)
+    yw = y[:hw * ls.N_BINS]
+    for prec in (cg.PREC_FP64, cg.PREC_DF64):   # warm-up of every kernel on the timed paths
+        ls.production_fit(net, yw, hw, 2, 1e-9, precision=prec)
+        ls.fit_batch(yw, hw, ls.heuristic_start(yw, hw), 2, 1e-9, precision=prec)
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    res = {}
+    for name, prec in (("fp64", cg.PREC_FP64), ("df64", cg.PREC_DF64)):
+        fh, t_h = timed(lambda: ls.fit_batch(y, H, ls.heuristic_start(y, H), 50, 1e-9, precision=prec))
+        pr, t_p = timed(lambda: ls.production_fit(net, y, H, 50, 1e-9, precision=prec))
+        Fh, Fp = fh.states.f.cpu().numpy(), pr["f"].cpu().numpy()
+        sh, sp = fh.states.status.cpu().numpy(), pr["status"].cpu().numpy()
+        sl = pr["learned"].states.status.cpu().numpy()
+        fin = np.isfinite(Fh) & np.isfinite(Fp)
+        same = np.abs(Fp - Fh) <= 1e-6 * np.abs(Fh)
+        res[name] = dict(
+            heuristic={"ms": t_h, "converged": int((sh == cg.FIT_CONVERGED).sum()),
+                       "mean_iters": float(fh.states.iters.double().mean()),
+                       "mean_evals": float(fh.states.n_eval.double().mean()),
+                       "mean_nll": float(Fh[fin].mean()),
+                       "bin_evaluations": float(fh.states.n_eval.double().sum()) * ls.N_BINS},
+            production={"ms": t_p, "converged": int((sp == cg.FIT_CONVERGED).sum()),
+                        "learned_fit_converged": int((sl == cg.FIT_CONVERGED).sum()),
+                        "refit_from_heuristic": int(len(pr["refit"])),
+                        "mean_iters_learned_fit": float(pr["learned"].states.iters.double().mean()),
+                        "mean_evals_total": float(pr["evals"].double().mean()),
+                        "mean_nll": float(Fp[fin].mean()),
+                        "bin_evaluations": float(pr["evals"].double().sum()) * ls.N_BINS},
+            same_minimum_frac=float(same.mean()),
+            lower_than_heuristic=int((Fp < Fh * (1 - 1e-6)).sum()),
+            higher_than_heuristic=int((Fp > Fh * (1 + 1e-6)).sum()),
+            speedup_vs_heuristic=t_h / t_p, Fp=Fp, theta=pr["theta"])
+    f64 = res["fp64"]
+    # the plain per-histogram FP64 path on a sample, from the same learned
+    # and heuristic starts as the batched paths
+    yh_all = y.view(H, ls.N_BINS)
+    r = np.random.default_rng(5)
+    samp = np.sort(r.choice(H, min(H, max(8, args.plain_per_stratum * 4)), replace=False))
+    th_heu = ls.heuristic_start(y, H)
+    xs, ss = ls.rebin(y, H)
+    th_net = net.predict_start(xs, ss)
+
+    def problem(h):
+        return cg.Problem.gauss_poly(yh_all[h].contiguous(), 0.0, 1.0, 3, 1, cg.OBJ_POISSON_BC)
+    plain_h, Fph, sph, _ = _plain_fits(problem, th_heu, [(np.arange(H), samp)], 50)
+    plain_l, Fpl, spl, _ = _plain_fits(problem, th_net, [(np.arange(H), samp)], 50)
+    # oracle fits of a few histograms from the production path's start points
+    t_cpu, checked, same_o = 0.0, 0, 0
+    y_np = yh_all[samp[:4]].cpu().numpy()
+    for j, h in enumerate(samp[:4]):
+        yh = y_np[j]
+        fg = lambda t, yh=yh: (lambda q: (q.value, q.grad))(oracle.binned1d(3, 1, 0, oracle.POISSON_BC, yh, 0.0, 1.0, t))
+        gn = lambda t, yh=yh: oracle.binned1d_gn(3, 1, 0, oracle.POISSON_BC, yh, 0.0, 1.0, t)
+        t0 = time.perf_counter()
+        ref = bfgs_fit(fg, gn, th_net[int(h)].cpu().numpy(), max_iter=50, tol=1e-9)
+        t_cpu += time.perf_counter() - t0
+        if ref["status"] == 1:
+            checked += 1
+            same_o += int(f64["Fp"][int(h)] <= ref["F"] * (1 + 1e-6))
+    roof = roofline_fp64("k_fit_persistent", FP64_INSTR["fit_c5"], f64["production"]["bin_evaluations"],
+                         f64["production"]["ms"] / 1e3, sm_max_mhz, rates, "bin-evaluation")
+    roof["note"] = "production path: rebin, network, decode, fit and refits timed as a whole"
+    strip = lambda d: {k: v for k, v in d.items() if k not in ("Fp", "theta")}
+    return {
+        "workload": "3 Gaussians + linear, 2048 bins, Baker-Cousins NLL, %d held-out histograms; MLP 256-512-512-11 "
+                    "BF16 (tcgen05) trained on %d method-generated fits" % (H, n_train), "dtype": "f64",
+        "value": f64["production"]["ms"] / 1e3, "unit": "s time-to-fit (learned start, %d histograms)" % H,
+        "higher_is_better": False,
+        "rule": "every histogram fitted from the network's start; where that fit does not converge in 50 iterations "
+                "it is fitted again from the heuristic start and the lower minimum is kept",
+        "fp64": strip(f64),
+        "plain_path": {"dtype": "f64", "from_heuristic_start": dict(plain_h, converged_frac=float(np.mean(
+            [sph[int(h)] == cg.FIT_CONVERGED for h in samp]))),
+                       "from_learned_start": dict(plain_l, converged_frac=float(np.mean(
+                           [spl[int(h)] == cg.FIT_CONVERGED for h in samp])))},
+        "speedup_vs_plain_heuristic": plain_h["seconds_for_all"] / (f64["production"]["ms"] / 1e3),
+        "roofline": roof,
+        "parity": {"what": "oracle BFGS fits of 4 sampled histograms from the network's start: production minimum "
+                           "at or below the oracle's (1e-6 relative) where the oracle converged",
+                   "checked": checked, "ok_count": same_o, "ok": bool(checked > 0 and same_o == checked)},
+        "variants": {"df64": strip(res["df64"])},
+        "training": {"histograms": n_train, "seconds_data": t_data, "seconds_train": t_train, "steps": net.step,
+                     "loss_first": curve[0][1] if curve else None, "loss_last": curve[-1][1] if curve else None,
+                     "targets": "converged double-float batched fits started at the truth"},
+        "cpu_baseline": {"value": 4 / t_cpu, "unit": "fits/s", "cores": 1, "kind": "oracle",
+                         "sample": "oracle BFGS fits of 4 histograms from the network's start (%.1f s)" % t_cpu},
+    }
+
+
+# ----------------------------------------------------------------------------
+# The reference arm: the CPU oracle on the host cores
+# ----------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2203_06139_gb300 import synth
+    thetas = synth.c2_theta_points(args.points)
+    n_sample = 400000
+    cores = _threads()
+    times = []
+    for _ in range(args.warmup):
+        cpu_oracle_mix(n_sample, thetas, cores)
+    for _ in range(args.steps):
+        _, cores, dt, _ = cpu_oracle_mix(n_sample, thetas, cores)
+        times.append(dt)
+    dt = sum(times) / len(times)
+    value = n_sample * args.points / dt
+    sample = "first %d of the %g events x all %d parameter points per step" % (n_sample, args.events, args.points)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.events, args.points), "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def _graph_timed(fn, steps, warmup, flush=None):
-    """Device time per call of fn replayed from a CUDA graph (no host work
-    inside the timed region), L2 flushed before each replay."""
+CONFIGS = {"c1": config_c1, "c3": config_c3, "c4": config_c4, "c5": config_c5}
+
+
+def _json_safe(o):
+    import numpy as np
+    if isinstance(o, dict):
+        return {str(k): _json_safe(v) for k, v in o.items()}
+    if isinstance(o, (list, tuple)):
+        return [_json_safe(v) for v in o]
+    if isinstance(o, (np.integer,)):
+        return int(o)
+    if isinstance(o, (np.floating,)):
+        return float(o)
+    if isinstance(o, np.ndarray):
+        return o.tolist()
+    if isinstance(o, float) and not math.isfinite(o):
+        return None
+    return o
+
+
+def run_configs(args, names, rates, sm_max_mhz):
+    out = {}
+    for name in names:
+        t0 = time.perf_counter()
+        log("config %s" % name)
+        try:
+            out[name] = CONFIGS[name](args, rates, sm_max_mhz)
+        except Exception as e:   # the line still reports the others, and this one's error
+            import traceback
+            traceback.print_exc()
+            out[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+        out[name]["wall_s"] = time.perf_counter() - t0
+    return out
+
+
+def run(args):
     import torch
-    s = torch.cuda.Stream()
-    s.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(s):
-        for _ in range(max(warmup, 1)):
-            fn()
-    torch.cuda.current_stream().wait_stream(s)
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        fn()
-    return _timed(graph.replay, steps, warmup, flush)
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    line, rates = headline(args, dev, rank, world, local)
+    if rank == 0:
+        names = [] if args.configs == "none" else [c for c in args.configs.split(",") if c]
+        if world == 1 and names:
+            line["configs"] = run_configs(args, names, rates, line["clocks"].get("sm_max_mhz"))
+        print(json.dumps(_json_safe(line)), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_one_config(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    rates = unit_rates()
+    clocks = Clocks(0)
+    clocks.start()
+    res = run_configs(args, [args.workload], rates, None)
+    clk = clocks.stop()
+    line = {"metric": METRIC, "workload": args.workload, "clocks": clk, "unit_rates": rates}
+    line.update(res[args.workload])
+    print(json.dumps(_json_safe(line)), flush=True)
 
 
 def run_gemm(args):
@@ -600,7 +1174,6 @@ def run_gemm(args):
             "shapes": rows}
     print(json.dumps(line), flush=True)
 
-
 def run_c5fit(args):
     """The batched Baker-Cousins fits of the learned-start workload alone: H
     three-peak histograms of 2048 bins from the heuristic start, 50 BFGS
@@ -632,7 +1205,6 @@ def run_c5fit(args):
                                    "start, 50 iterations, df64" % H},
             "mean_evals": float(ev.mean()), "max_evals": int(ev.max())}
     print(json.dumps(line), flush=True)
-
 
 def run_expr(args):
     """Expression programs (source-transformation AD, NVRTC-compiled): the c1
@@ -689,117 +1261,6 @@ def run_expr(args):
             "config": {"workload": "c1 (1e4 bins x 100 points) and c2 (1e7 events x 50 points) objectives as "
                                    "expression programs, FP64"}, "results": out}
     print(json.dumps(line), flush=True)
-
-
-def run_c3(args):
-    """4096 x 4096 bins, 8 rotated Gaussians: autograd forward + backward."""
-    import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_2203_06139_gb300 import cg, synth
-    from paper_2203_06139_gb300.autograd import fit_objective
-    hh = synth.c3_histogram()
-    prec = cg.PREC_DF64 if args.prec == "df64" else cg.PREC_FP64
-    try:
-        pb = cg.Problem.rotgauss2d(torch.tensor(hh["counts"], device="cuda"), 8, precision=prec)
-        pb.workspace(1)
-    except cg.CgError:
-        prec = cg.PREC_FP64
-        pb = cg.Problem.rotgauss2d(torch.tensor(hh["counts"], device="cuda"), 8, precision=prec)
-    th = torch.tensor(synth.c3_theta_point(hh["truth"])[0], device="cuda", requires_grad=True)
-    def fwd_bwd():
-        th.grad = None
-        fit_objective(th, pb).backward()
-    ms = _timed(fwd_bwd, args.steps, max(3, args.warmup))
-    n = 4096 * 4096
-    line = {"metric": METRIC, "workload": "c3", "value": n / (ms / 1e3), "unit": UNIT, "higher_is_better": True,
-            "ms_per_step": ms, "grad_evals_per_s": 1e3 / ms, "dtype": "f64" if prec == cg.PREC_FP64 else "df64",
-            "config": {"workload": "Poisson NLL, 8 rotated 2-D Gaussians + constant, 4096 x 4096 bins, 49 params, "
-                                   "autograd forward+backward", "l2": "inputs (134 MB) larger than L2"},
-            "gpu_launches": 2 * args.steps}
-    print(json.dumps(line), flush=True)
-
-
-def run_c4(args):
-    """4096 uneven histograms: time-to-fit, batched persistent launch vs the plain per-histogram path."""
-    import numpy as np
-    import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_2203_06139_gb300 import cg, synth
-    from paper_2203_06139_gb300.fit import BatchFitter, HistBatch, LMFitter, SingleFitter, autotune
-    d = synth.c4_batch()
-    prec = cg.PREC_DF64 if args.prec == "df64" else cg.PREC_FP64
-    b = HistBatch(d["y"], d["offsets"], d["lo"], d["hi"], 1, 2, cg.OBJ_CHI2, poly_mode=1, precision=prec)
-    th0 = torch.tensor(d["start"], device="cuda")
-    best, timings = autotune(b, th0, n_steps=50)   # the iteration count of the timed fit
-    f = BatchFitter(b, best)
-    f.capture(50, 1e-9, theta0=th0)   # init + 50 iterations in one graph
-    def batched():
-        f.replay()
-    ms = _timed(batched, max(1, min(args.steps, 5)), 2)
-    Fb = f.states.f.cpu().numpy()
-    stb = f.states.status.cpu().numpy()
-    itb = f.states.iters.cpu().numpy()
-    # second-order fits (Levenberg-Marquardt on the Gauss-Newton matrix, df64
-    # batch): init + n_lm evaluations in one graph
-    n_lm = 30
-    b_lm = b if prec == cg.PREC_DF64 else HistBatch(d["y"], d["offsets"], d["lo"], d["hi"], 1, 2, cg.OBJ_CHI2,
-                                                    poly_mode=1, precision=cg.PREC_DF64)
-    flm = LMFitter(b_lm)
-    flm.capture(th0, n_steps=n_lm, tol=1e-9)
-    ms_lm = _timed(lambda: flm.replay(), max(1, min(args.steps, 5)), 2)
-    Fl = flm.states.f.cpu().numpy()
-    stl = flm.states.status.cpu().numpy()
-    itl = flm.states.iters.cpu().numpy()
-    nel = flm.states.n_eval.cpu().numpy()
-    same_lm = np.abs(Fl - Fb) <= 1e-6 * np.abs(Fb)
-    # plain path: every histogram on its own, full-GPU launches per trial point
-    n_plain = args.plain_hists or d["H"]
-    idx = np.arange(d["H"]) if n_plain >= d["H"] else np.random.default_rng(0).choice(d["H"], n_plain, replace=False)
-    yt = b.y
-    Fp = np.zeros(len(idx))
-    sp = np.zeros(len(idx), dtype=np.int64)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for j, h in enumerate(idx):
-        o0, o1 = int(d["offsets"][h]), int(d["offsets"][h + 1])
-        pb = cg.Problem.gauss_poly(yt[o0:o1], 0.0, 1.0, 1, 2, cg.OBJ_CHI2, poly_mode=1)
-        st = SingleFitter(pb).fit(th0[h], max_iter=50, tol=1e-9)
-        Fp[j] = float(st.f[0])
-        sp[j] = int(st.status[0])
-    torch.cuda.synchronize()
-    t_plain = time.perf_counter() - t0
-    t_plain_full = t_plain * d["H"] / len(idx)
-    same = np.abs(Fb[idx] - Fp) <= 1e-6 * np.abs(Fp)
-    both = (stb[idx] == cg.FIT_CONVERGED) & (sp == cg.FIT_CONVERGED)
-    line = {"metric": METRIC, "workload": "c4", "value": ms / 1e3, "unit": "s time-to-fit (4096 histograms)",
-            "higher_is_better": False, "ms_per_step": ms,
-            "config": {"workload": "4096 histograms, 64-65536 bins (log-uniform), Gaussian + quadratic, chi2, "
-                                   "50 BFGS iterations in one graph-captured persistent launch",
-                       "tile_map": best.as_dict(), "bins": int(d["offsets"][-1])},
-            "dtype": "f64" if prec == cg.PREC_FP64 else "df64",
-            "batched": {"converged": int((stb == cg.FIT_CONVERGED).sum()), "mean_iters": float(itb.mean()),
-                        "ms": ms},
-            "levenberg_marquardt": {"ms": ms_lm, "evaluations": n_lm + 1, "dtype": "df64 (GN matrix FP32)",
-                                    "converged": int((stl == cg.FIT_CONVERGED).sum()),
-                                    "mean_iters": float(itl.mean()), "mean_evals": float(nel.mean()),
-                                    "status_counts": np.bincount(stl, minlength=5).tolist(),
-                                    "same_minimum_as_bfgs_frac": float(same_lm.mean()),
-                                    "lower_F_when_different": {"lm": int(((Fl < Fb) & ~same_lm).sum()),
-                                                               "bfgs": int(((Fb < Fl) & ~same_lm).sum())}},
-            "plain_path": {"seconds_measured": t_plain, "histograms_measured": int(len(idx)),
-                           "seconds_for_all": t_plain_full},
-            "speedup_vs_plain": t_plain_full / (ms / 1e3),
-            "status_counts": {"batched": np.bincount(stb, minlength=5).tolist(),
-                              "plain": np.bincount(sp, minlength=5).tolist()},
-            "same_minimum_frac": float(same.mean()),
-            "same_minimum_frac_both_converged": float(same[both].mean()) if both.any() else None,
-            "lower_F_when_different": {"batched": int(((Fb[idx] < Fp) & ~same).sum()),
-                                       "plain": int(((Fp < Fb[idx]) & ~same).sum())},
-            "autotune": timings[:4]}
-    print(json.dumps(line), flush=True)
-
 
 def run_fig3b(args):
     """Gradient cost vs number of parameters (the comparison of Fig. 3b, whose
@@ -883,44 +1344,38 @@ def run_fig3b(args):
             "rows": rows, "rows_expr": rows_expr}
     print(json.dumps(line), flush=True)
 
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cg", choices=["cg", "reference"])
-    ap.add_argument("--prec", default="df64", choices=["fp64", "df64"])
-    ap.add_argument("--no-fp64-leg", action="store_true", help="skip the FP64-path comparison leg")
     ap.add_argument("--events", type=int, default=N_EVENTS)
     ap.add_argument("--points", type=int, default=N_POINTS)
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "c5fit", "fig3b", "gemm", "expr"])
-    ap.add_argument("--plain-hists", type=int, default=0, help="c4: histograms timed on the plain path (0 = all)")
-    ap.add_argument("--hists", type=int, default=0, help="c5fit: histograms in the batch (0 = 65,536)")
+    ap.add_argument("--workload", default="c2",
+                    choices=["c2", "c1", "c3", "c4", "c5", "c5fit", "fig3b", "gemm", "expr"])
+    ap.add_argument("--configs", default="c1,c3,c4,c5",
+                    help="configs measured beside the headline (comma list, or none)")
+    ap.add_argument("--plain-per-stratum", type=int, default=24,
+                    help="c4: histograms per size stratum timed on the plain path (c5: x4 in one sample)")
+    ap.add_argument("--hists", type=int, default=0, help="c5 / c5fit: histograms fitted (0 = 65,536)")
     ap.add_argument("--train-hists", type=int, default=0, help="c5: training histograms (0 = 10^6)")
     ap.add_argument("--epochs", type=int, default=0, help="c5: training epochs (0 = 6)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "c1":
-        run_c1(args)
-    elif args.workload == "c3":
-        run_c3(args)
-    elif args.workload == "c4":
-        run_c4(args)
-    elif args.workload == "fig3b":
-        run_fig3b(args)
-    elif args.workload == "c5":
-        from paper_2203_06139_gb300 import learned_start
-        learned_start.bench(args)
+    elif args.workload == "c2":
+        run(args)
+    elif args.workload in CONFIGS:
+        run_one_config(args)
     elif args.workload == "gemm":
         run_gemm(args)
     elif args.workload == "c5fit":
         run_c5fit(args)
     elif args.workload == "expr":
         run_expr(args)
-    else:
-        run(args)
+    elif args.workload == "fig3b":
+        run_fig3b(args)
 
 
 if __name__ == "__main__":

@@ -15,8 +15,6 @@ ROOT = os.path.dirname(PKG)
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcg.so")
-PROBE_SRC = os.path.join(PKG, "probe", "unit_rates.cu")
-PROBE_LIB = os.path.join(PKG, "libcg_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-split-compile=0"]
 
@@ -45,23 +43,8 @@ def up_to_date():
     return all(os.path.getmtime(f) <= t for f in _deps() + [__file__])
 
 
-def build_probe(force=False):
-    """The unit-rate probe library used by bench.py for the ALU roofline."""
-    if not force and os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(PROBE_SRC):
-        return PROBE_LIB
-    tmp = "%s.%d.tmp" % (PROBE_LIB, os.getpid())
-    cmd = [_nvcc()] + ARCH + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-cudart", "shared",
-                               "-o", tmp, PROBE_SRC]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("nvcc failed on %s:\n%s\n%s" % (PROBE_SRC, r.stdout, r.stderr))
-    os.replace(tmp, PROBE_LIB)
-    return PROBE_LIB
-
-
 def build(force=False, verbose=False, extra_flags=()):
-    """Compile and link libcg.so (and the probe library) if anything changed; returns libcg's path."""
-    build_probe(force)
+    """Compile and link libcg.so if anything changed; returns its path."""
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)

@@ -20,7 +20,11 @@ def shard(n, rank, world):
 
 
 def combine(value, grad, group=None):
-    """All-gather every rank's (value, grad) and sum them in rank order."""
+    """All-gather every rank's (value, grad) and sum them in rank order.
+
+    One exchange of (1 + P) doubles per rank, on the device the tensors live
+    on (CUDA tensors under NCCL, CPU tensors under gloo); the rank-ordered
+    sum makes the result the same on every rank and on every run."""
     vec = torch.cat([value.reshape(1).double(), grad.reshape(-1).double()])
     world = dist.get_world_size(group)
     bufs = [torch.empty_like(vec) for _ in range(world)]
@@ -52,16 +56,19 @@ def shard_batch(offsets, rank, world):
     return lo, max(lo, cut(rank + 1))
 
 
-def gather_batch(values, grads, h0, H, group=None):
+def gather_batch(values, grads, h0, H, P, group=None):
     """Every rank's per-histogram results (values [h1 - h0], grads [h1 - h0, P]
-    of its histograms from h0) assembled into [H] and [H, P] on every rank:
-    one all-reduce of zero-padded arrays, exact (each entry is one rank's
-    number plus zeros)."""
-    P = grads.shape[1] if grads.dim() == 2 else 0
+    of its histograms from h0; a rank with no histograms passes empty
+    tensors) assembled into [H] and [H, P] on every rank: one all-reduce of
+    zero-padded arrays of H (1 + P) doubles, exact (each entry is one rank's
+    number plus zeros).  P is passed, not read from grads, so that every rank
+    reduces the same length whatever it holds."""
     n = values.numel()
+    if grads.numel() != n * P:
+        raise ValueError("grads must hold P = %d values per histogram" % P)
     full = torch.zeros(H * (1 + P), dtype=torch.float64, device=values.device)
     full[h0:h0 + n] = values.double()
-    if P:
+    if P and n:
         full[H + h0 * P:H + (h0 + n) * P] = grads.double().reshape(-1)
     dist.all_reduce(full, op=dist.ReduceOp.SUM, group=group)
     return full[:H], full[H:].reshape(H, P)
@@ -76,13 +83,13 @@ def max_over_ranks(seconds, group=None, device="cpu"):
 
 def sharded_mixture_gradient(x, lo, hi, theta, group=None, precision=None):
     """Unbinned-mixture NLL and gradient of all events x (device tensor, the full
-    sample on every rank or this rank's slice of it when `x` is already local),
-    with this rank evaluating its shard on its GPU."""
+    sample on every rank), with this rank evaluating its contiguous shard on
+    its GPU (FP64 unless another precision is asked for) and the (1 + 4)
+    partial sums exchanged on the device by combine()."""
     from . import cg
     rank, world = dist.get_rank(group), dist.get_world_size(group)
     a, b = shard(x.numel(), rank, world)
     pb = cg.Problem.mixture(x[a:b].contiguous(), lo, hi,
-                            precision=cg.PREC_DF64 if precision is None else precision)
+                            precision=cg.PREC_FP64 if precision is None else precision)
     v, g = cg.gradient(pb, theta)
-    vv, gg = combine(v.cpu(), g.cpu(), group)
-    return vv, gg
+    return combine(v, g, group)

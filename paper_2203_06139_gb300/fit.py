@@ -338,14 +338,22 @@ def _cache_path():
     return os.environ.get("CG_AUTOTUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "cg_autotune.json"))
 
 
+def _autotune_key(batch, n_steps):
+    c = batch.pb.c
+    return "%s|%s|K%dD%dP%d|obj%d|prec%d|pm%d|S%d" % (
+        torch.cuda.get_device_name(), _size_signature(batch.sizes), batch.K, batch.D, batch.P, c.objective,
+        c.precision, c.poly_mode, n_steps)
+
+
 def autotune(batch, theta0, candidates=None, n_steps=5, tol=1e-9, use_cache=True):
     """Time n_steps BFGS iterations of the whole batch under each candidate map
     and return (best_map, timings).  Time the iteration count the fit will
     run: the largest histograms set the tail of a long fit, which a few
     iterations do not show.  Results are cached per (GPU, size signature,
-    model, n_steps) in a JSON file."""
-    key = "%s|%s|K%dD%dP%d|S%d" % (torch.cuda.get_device_name(), _size_signature(batch.sizes), batch.K, batch.D,
-                                   batch.P, n_steps)
+    model, objective, precision, n_steps) in a JSON file: a chi2 and a
+    Poisson batch of the same shape, or an FP64 and a double-float batch,
+    differ in per-bin cost and keep separate entries."""
+    key = _autotune_key(batch, n_steps)
     path = _cache_path()
     cache = {}
     if use_cache and os.path.exists(path):

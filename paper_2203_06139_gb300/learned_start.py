@@ -8,15 +8,12 @@ backward, MSE loss, AdamW with FP32 master weights) and inference run in the
 kernels of libcg (cg_gemm_bf16 on the tensor cores, cg_rebin_normalize,
 cg_mse_loss, cg_colsum, cg_adamw, cg_decode_start).  Targets are the
 converged fits of the plain method (the BFGS fitter) on method-generated
-histograms.  A learned start is judged by the plain fit: where its fit does
-not converge, or ends above the heuristic-start fit, the heuristic result is
-kept.  The paper has no network; this is the learned-start extension of the
-batched fitter.
+histograms.  A learned start is judged by the plain fit (production_fit):
+where its fit does not converge, the histogram is fitted again from the
+plain heuristic start and the lower minimum is kept.  The paper has no
+network; this is the learned-start extension of the batched fitter.
 """
-import ctypes
-import json
 import math
-import time
 
 import numpy as np
 import torch
@@ -182,11 +179,11 @@ class MLP:
         return out
 
 
-def fit_batch(y_flat, H, theta0, n_steps=50, tol=1e-9):
+def fit_batch(y_flat, H, theta0, n_steps=50, tol=1e-9, precision=FIT_PRECISION):
     """Batched Baker-Cousins fits of H 2048-bin histograms from theta0; returns the fitter."""
     offs = np.arange(H + 1, dtype=np.int64) * N_BINS
     b = HistBatch(y_flat, offs, np.zeros(H), np.ones(H), K_PEAKS, 1, cg.OBJ_POISSON_BC, poly_mode=0,
-                  precision=FIT_PRECISION)
+                  precision=precision)
     f = BatchFitter(b, FIT_MAP)
     f.init(theta0.contiguous())
     f.step(n_steps, tol)
@@ -208,7 +205,7 @@ def choose_start(y_flat, H, th_a, th_b):
     return out
 
 
-def make_training_set(n_hist, chunk=65536, first_chunk=1, device="cuda", log=None):
+def make_training_set(n_hist, chunk=65536, first_chunk=1, device="cuda", log=None, precision=FIT_PRECISION):
     """Method-generated histograms and their converged plain fits (started at
     the truth): network inputs x (bf16), scales and fitted parameters."""
     xs, ss, ts = [], [], []
@@ -217,7 +214,7 @@ def make_training_set(n_hist, chunk=65536, first_chunk=1, device="cuda", log=Non
         H = min(chunk, n_hist - n_done)
         d = synth.c5_batch_device(H, N_BINS, chunk=c, device=device)
         x, scale = rebin(d["y"], H)
-        f = fit_batch(d["y"], H, torch.tensor(d["truth"], device=device))
+        f = fit_batch(d["y"], H, torch.tensor(d["truth"], device=device), precision=precision)
         ok = f.states.status == cg.FIT_CONVERGED
         xs.append(x[ok])
         ss.append(scale[ok])
@@ -230,145 +227,135 @@ def make_training_set(n_hist, chunk=65536, first_chunk=1, device="cuda", log=Non
     return torch.cat(xs), torch.cat(ss), torch.cat(ts)
 
 
-def train(net, x, scale, theta, epochs=3, batch=1024, lr=1e-3, seed=0, log=None, cosine=True):
-    """AdamW on the MSE of z-scored targets (cosine-decayed learning rate);
-    returns the loss curve (first step, then every 50 steps)."""
-    t = encode_targets(theta, scale)
-    net.t_mean = t.mean(0).float().contiguous()
-    w = torch.tensor(TARGET_WEIGHTS, dtype=torch.float32, device=x.device)
-    # dividing the scale by w weights the squared error of target j by w_j^2
-    net.t_std = (t.std(0).clamp_min(1e-6).float() / w).contiguous()
-    tz = ((t - net.t_mean.double()) / net.t_std.double()).float().contiguous()
-    N = x.shape[0]
-    g = torch.Generator(device=x.device)
-    g.manual_seed(seed)
-    curve = []
-    total = epochs * (N // batch)
-    for ep in range(epochs):
-        perm = torch.randperm(N, generator=g, device=x.device)
-        for i0 in range(0, N - batch + 1, batch):
-            frac = net.step / max(total, 1)
-            lr_now = lr * (0.5 * (1.0 + math.cos(math.pi * frac)) * 0.95 + 0.05) if cosine else lr
-            idx = perm[i0:i0 + batch]
-            xb = x.index_select(0, idx).contiguous()
-            tb = tz.index_select(0, idx).contiguous()
+class Trainer:
+    """AdamW on the MSE of z-scored targets with a cosine-decayed learning
+    rate, over shuffled minibatches of a fixed training set.
+
+    The whole training state -- FP32 master weights and biases, Adam
+    moments, the step count, the target normalisation, the epoch, the
+    position inside it and the shuffling generator's state at the epoch's
+    start -- goes into state_dict(); a Trainer built from it continues with
+    exactly the same minibatches and kernels, so the loss curve after a
+    resume is bitwise the one of an uninterrupted run."""
+
+    def __init__(self, net, x, scale, theta, epochs=3, batch=1024, lr=1e-3, seed=0, cosine=True, log_every=50):
+        self.net, self.x = net, x
+        self.log_every = log_every
+        self.epochs, self.batch, self.lr, self.cosine = epochs, batch, lr, cosine
+        t = encode_targets(theta, scale)
+        net.t_mean = t.mean(0).float().contiguous()
+        w = torch.tensor(TARGET_WEIGHTS, dtype=torch.float32, device=x.device)
+        # dividing the scale by w weights the squared error of target j by w_j^2
+        net.t_std = (t.std(0).clamp_min(1e-6).float() / w).contiguous()
+        self.tz = ((t - net.t_mean.double()) / net.t_std.double()).float().contiguous()
+        self.N = x.shape[0]
+        self.gen = torch.Generator(device=x.device)
+        self.gen.manual_seed(seed)
+        self.epoch, self.i0 = 0, 0
+        self._new_epoch()
+        self.curve = []
+
+    def _new_epoch(self):
+        self.gen_state = self.gen.get_state()   # the permutation of this epoch is drawn from here
+        self.perm = torch.randperm(self.N, generator=self.gen, device=self.x.device)
+
+    @property
+    def total_steps(self):
+        return self.epochs * (self.N // self.batch)
+
+    def done(self):
+        return self.epoch >= self.epochs
+
+    def run(self, n_steps=None, log=None):
+        """Train n_steps minibatches (None: to the end); returns the loss
+        curve so far, (step, loss) at the first step and every log_every steps."""
+        net = self.net
+        left = n_steps
+        while not self.done() and (left is None or left > 0):
+            if self.i0 + self.batch > self.N:
+                if log:
+                    log("epoch %d: loss %.4f" % (self.epoch, self.curve[-1][1] if self.curve else float("nan")))
+                self.epoch += 1
+                self.i0 = 0
+                if self.done():
+                    break
+                self._new_epoch()
+                continue
+            frac = net.step / max(self.total_steps, 1)
+            lr_now = self.lr * (0.5 * (1.0 + math.cos(math.pi * frac)) * 0.95 + 0.05) if self.cosine else self.lr
+            idx = self.perm[self.i0:self.i0 + self.batch]
+            xb = self.x.index_select(0, idx).contiguous()
+            tb = self.tz.index_select(0, idx).contiguous()
             net.forward(xb)
             net.loss_and_grad(tb)
             net.backward(xb)
             net.adamw(lr=lr_now)
-            if net.step == 1 or net.step % 50 == 0:
-                curve.append((net.step, float(net.loss)))
-        if log:
-            log("epoch %d: loss %.4f" % (ep, curve[-1][1] if curve else float("nan")))
-    return curve
+            self.i0 += self.batch
+            if net.step == 1 or net.step % self.log_every == 0:
+                self.curve.append((net.step, float(net.loss)))
+            if left is not None:
+                left -= 1
+        return self.curve
+
+    def state_dict(self):
+        net = self.net
+        return {"W": [w.clone() for w in net.W], "b": [b.clone() for b in net.b],
+                "m": [m.clone() for m in net.m], "v": [v.clone() for v in net.v], "step": net.step,
+                "t_mean": net.t_mean.clone(), "t_std": net.t_std.clone(), "epoch": self.epoch, "i0": self.i0,
+                "gen_state": self.gen_state.clone(), "curve": list(self.curve),
+                "config": {"epochs": self.epochs, "batch": self.batch, "lr": self.lr, "cosine": self.cosine}}
+
+    def load_state_dict(self, sd):
+        net = self.net
+        for dst, src in zip(net.W + net.b + net.m + net.v, sd["W"] + sd["b"] + sd["m"] + sd["v"]):
+            dst.copy_(src)
+        for w, wb in zip(net.W, net.Wb):
+            cg._check(cg.lib().cg_to_bf16(_p(w), w.numel(), _p(wb), _s()), "cg_to_bf16")
+        net.step = int(sd["step"])
+        net.t_mean = sd["t_mean"].clone()
+        net.t_std = sd["t_std"].clone()
+        c = sd["config"]
+        self.epochs, self.batch, self.lr, self.cosine = c["epochs"], c["batch"], c["lr"], c["cosine"]
+        self.epoch, self.i0 = int(sd["epoch"]), int(sd["i0"])
+        self.gen.set_state(sd["gen_state"].clone())
+        self._new_epoch()          # the same permutation as at the checkpoint's epoch start
+        self.curve = list(sd["curve"])
+
+    def save(self, path):
+        torch.save(self.state_dict(), path)
+
+    def load(self, path):
+        self.load_state_dict(torch.load(path, map_location=self.x.device, weights_only=False))
 
 
-def evaluate(net, H=65536, chunk=0, device="cuda", n_steps=50, tol=1e-9):
-    """Learned start vs heuristic start on held-out histograms (both fitted in
-    full to count agreement; the production path refits only the learned fits
-    that did not converge, from the heuristic start)."""
-    d = synth.c5_batch_device(H, N_BINS, chunk=chunk, device=device)
-    y = d["y"]
-    # warm-up of every kernel on the timed paths (first launches load code)
-    hw = min(H, 1024)
-    yw = y[:hw * N_BINS]
-    xw, sw = rebin(yw, hw)
-    fit_batch(yw, hw, choose_start(yw, hw, net.predict_start(xw, sw), heuristic_start(yw, hw)), 2, tol)
-    torch.cuda.synchronize()
-
-    def timed(fn):
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        r = fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return r, e0.elapsed_time(e1)
-
-    fh, t_h = timed(lambda: fit_batch(y, H, heuristic_start(y, H), n_steps, tol))
-
-    stage_ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-
-    def proposal():
-        stage_ev[0].record()
-        x, scale = rebin(y, H)
-        stage_ev[1].record()
-        th_net = net.predict_start(x, scale)
-        stage_ev[2].record()
-        th_heu = heuristic_start(y, H)
-        stage_ev[3].record()
-        th = choose_start(y, H, th_net, th_heu)
-        stage_ev[4].record()
-        return th
-
-    th_l, t_prop = timed(proposal)
-    stages = dict(zip(("rebin", "network", "heuristic", "choose"),
-                      (stage_ev[i].elapsed_time(stage_ev[i + 1]) for i in range(4))))
-    fl, t_fit = timed(lambda: fit_batch(y, H, th_l, n_steps, tol))
-    t_l = t_prop + t_fit
-    Fh, Fl = fh.states.f.cpu().numpy(), fl.states.f.cpu().numpy()
-    sh, sl = fh.states.status.cpu().numpy(), fl.states.status.cpu().numpy()
-    ih, il = fh.states.iters.cpu().numpy(), fl.states.iters.cpu().numpy()
-    flagged_prod = sl != cg.FIT_CONVERGED
-    idx = np.nonzero(flagged_prod)[0]
-
-    def refit():
-        if len(idx) == 0:
-            return None
-        ii = torch.tensor(idx, device=device)
-        ysub = y.view(H, N_BINS).index_select(0, ii).reshape(-1).contiguous()
-        return fit_batch(ysub, len(idx), heuristic_start(ysub, len(idx)), n_steps, tol)
-
-    fr, t_r = timed(refit)
-    Ffinal = Fl.copy()
-    if fr is not None:
-        Fr = fr.states.f.cpu().numpy()
-        better = Fr < Ffinal[idx]
-        Ffinal[idx[better]] = Fr[better]
-    # judged by the plain fit: learned fits above the heuristic fit are rejected
-    worse = Fl > Fh * (1 + 1e-6)
-    Fjudged = np.where((sl != cg.FIT_CONVERGED) | worse, np.minimum(Fh, Fl), Fl)
-    same = np.abs(Ffinal - Fh) <= 1e-6 * np.abs(Fh)
-    eh, el = fh.states.n_eval.cpu().numpy(), fl.states.n_eval.cpu().numpy()
-    return dict(H=H, heuristic=dict(ms=t_h, mean_iters=float(ih.mean()), mean_evals=float(eh.mean()),
-                                    converged=int((sh == 1).sum()), mean_nll=float(np.mean(Fh[np.isfinite(Fh)]))),
-                learned=dict(ms=t_l, proposal_ms=t_prop, proposal_stages_ms=stages, fit_ms=t_fit,
-                             mean_iters=float(il.mean()),
-                             mean_evals=float(el.mean()), converged=int((sl == 1).sum()),
-                             mean_nll=float(np.mean(Fl[np.isfinite(Fl)]))),
-                production=dict(ms=t_l + t_r, refit=int(len(idx)), refit_ms=t_r,
-                                mean_nll=float(np.mean(Ffinal[np.isfinite(Ffinal)]))),
-                rejected_by_plain_fit=int(((sl != cg.FIT_CONVERGED) | worse).sum()),
-                lower_than_heuristic=int((Fjudged < Fh * (1 - 1e-6)).sum()),
-                same_minimum_frac=float(same.mean()),
-                nll_learned_le_heuristic_frac=float((Ffinal <= Fh * (1 + 1e-6)).mean()))
+def train(net, x, scale, theta, epochs=3, batch=1024, lr=1e-3, seed=0, log=None, cosine=True):
+    """Train to the end (see Trainer); returns the loss curve."""
+    return Trainer(net, x, scale, theta, epochs=epochs, batch=batch, lr=lr, seed=seed, cosine=cosine).run(log=log)
 
 
-def bench(args):
-    """bench.py --workload c5: train on method-generated fits, then time fits
-    of 65,536 histograms from the learned vs the heuristic start."""
-    import __graft_entry__
-    __graft_entry__.build()
-    n_train = getattr(args, "train_hists", 0) or 10 ** 6
-    t0 = time.perf_counter()
-    x, scale, theta = make_training_set(n_train)
-    t_data = time.perf_counter() - t0
-    net = MLP(seed=0)
-    t0 = time.perf_counter()
-    curve = train(net, x, scale, theta, epochs=getattr(args, "epochs", 0) or 6, lr=2e-3)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    ev = evaluate(net)
-    line = {"metric": "gradient evals/s and bin-grads/s (frac of roofline); time-to-fit vs plain path",
-            "workload": "c5", "value": ev["learned"]["ms"] / 1e3, "unit": "s time-to-fit (65,536 histograms)",
-            "higher_is_better": False,
-            "config": {"workload": "3 Gaussians + linear, 2048 bins, Baker-Cousins NLL, 65,536 histograms; MLP "
-                                   "256-512-512-11 BF16 trained on %d method-generated fits" % int(x.shape[0])},
-            "heuristic_start": ev["heuristic"], "learned_start": ev["learned"], "production": ev["production"],
-            "speedup_vs_heuristic": ev["heuristic"]["ms"] / ev["learned"]["ms"],
-            "speedup_vs_heuristic_with_refit": ev["heuristic"]["ms"] / ev["production"]["ms"],
-            "same_minimum_frac": ev["same_minimum_frac"],
-            "nll_learned_le_heuristic_frac": ev["nll_learned_le_heuristic_frac"],
-            "training": {"seconds_data": t_data, "seconds_train": t_train, "steps": net.step,
-                         "loss_first": curve[0][1] if curve else None, "loss_last": curve[-1][1] if curve else None}}
-    print(json.dumps(line), flush=True)
+def production_fit(net, y, H, n_steps=50, tol=1e-9, precision=FIT_PRECISION):
+    """Fits of H histograms from the learned start, judged by the plain fit:
+    every histogram is fitted from the network's start; the histograms whose
+    fit did not converge within n_steps iterations are fitted again from the
+    plain peak-finding heuristic start, and the lower of the two minima is
+    kept.  Returns dict(theta [H, P], f [H], status [H], iters [H], evals
+    [H], refit (indices refitted, host), learned (the learned-start fitter))."""
+    x, scale = rebin(y, H)
+    th0 = net.predict_start(x, scale)
+    fl = fit_batch(y, H, th0, n_steps, tol, precision=precision)
+    st = fl.states
+    theta, f = st.theta.clone(), st.f.clone()
+    status, iters, evals = st.status.clone(), st.iters.clone(), st.n_eval.clone()
+    idx = torch.nonzero(status != cg.FIT_CONVERGED).flatten()
+    if idx.numel():
+        ysub = y.view(H, N_BINS).index_select(0, idx).reshape(-1).contiguous()
+        fr = fit_batch(ysub, idx.numel(), heuristic_start(ysub, idx.numel()), n_steps, tol, precision=precision)
+        rs = fr.states
+        better = rs.f < f[idx]
+        pick = idx[better]
+        theta[pick] = rs.theta[better]
+        f[pick] = rs.f[better]
+        status[pick] = rs.status[better]
+        iters[idx] += rs.iters
+        evals[idx] += rs.n_eval
+    return dict(theta=theta, f=f, status=status, iters=iters, evals=evals, refit=idx.cpu().numpy(), learned=fl)

@@ -176,3 +176,38 @@ def test_python_binding_has_the_c_names():
         assert callable(getattr(cg, n))
     for n in ("cg_fit_step", "cg_fit_lm_step", "cg_batch_gn"):
         assert callable(getattr(fit, n))
+
+
+def test_the_package_never_reaches_the_oracle():
+    """The product package imports neither the oracle nor the build entry
+    point on any path (the oracle is test infrastructure); checked on every
+    module's import statements and on a fresh interpreter's module table
+    after importing every module of the package."""
+    import ast
+    import subprocess
+    import sys
+    pkg = os.path.join(ROOT, "paper_2203_06139_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if not f.endswith(".py"):
+                continue
+            tree = ast.parse(open(os.path.join(dirpath, f)).read())
+            for node in ast.walk(tree):
+                names = []
+                if isinstance(node, ast.Import):
+                    names = [a.name for a in node.names]
+                elif isinstance(node, ast.ImportFrom):
+                    names = [node.module or ""]
+                for n in names:
+                    assert not n.startswith("oracle") and n != "__graft_entry__", (f, n)
+    code = ("import sys; sys.path.insert(0, %r)\n" % ROOT +
+            "import importlib, pkgutil, paper_2203_06139_gb300 as p\n"
+            "import os\n"
+            "for m in pkgutil.iter_modules(p.__path__):\n"
+            "    if os.path.exists(os.path.join(p.__path__[0], m.name + '.py')):\n"
+            "        importlib.import_module('paper_2203_06139_gb300.' + m.name)\n"
+            "bad = [k for k in sys.modules if k == 'oracle' or k.startswith('oracle.') or k == '__graft_entry__']\n"
+            "print(','.join(bad))\n")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == "", r.stdout

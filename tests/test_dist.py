@@ -82,8 +82,8 @@ def _batch_worker(rank, world, port, ys, offs, out_dir):
         th = np.array([1000.0, 0.5, 0.05, 50.0, 2.0, -1.0])
         rs = [oracle.binned1d(1, 2, 1, oracle.CHI2, ys[offs[h]:offs[h + 1]], 0.0, 1.0, th) for h in range(h0, h1)]
         v = torch.tensor([r.value for r in rs], dtype=torch.float64)
-        g = torch.tensor(np.array([r.grad for r in rs]).reshape(-1, 6), dtype=torch.float64)
-        V, G = cgdist.gather_batch(v, g, h0, len(offs) - 1)
+        g = torch.tensor(np.array([r.grad for r in rs], dtype=np.float64).reshape(-1, 6), dtype=torch.float64)
+        V, G = cgdist.gather_batch(v, g, h0, len(offs) - 1, 6)
         np.save(os.path.join(out_dir, "b%d.npy" % rank), np.concatenate([V.numpy(), G.numpy().reshape(-1)]))
     finally:
         dist.destroy_process_group()
@@ -126,3 +126,19 @@ def test_rank_leaving_makes_the_exchange_fail_not_hang(tmp_path):
     mp.start_processes(_worker, args=(2, _port(), x, th, str(tmp_path), "leave"), nprocs=2, start_method="spawn")
     assert (tmp_path / "err0.txt").exists(), "rank 0 should see the exchange fail"
     assert not (tmp_path / "r0.npy").exists()
+
+
+def test_a_rank_without_histograms_still_gathers(tmp_path):
+    """One histogram over two ranks: the second rank owns none, passes empty
+    results, and both ranks still assemble the same [H], [H, P] arrays."""
+    import oracle
+    from paper_2203_06139_gb300 import synth
+    d = synth.c4_batch(H=1, max_bins=3000)
+    ys, offs = d["y"], d["offsets"]
+    assert cgdist.shard_batch(offs, 1, 2) == (1, 1)
+    mp.start_processes(_batch_worker, args=(2, _port(), ys, offs, str(tmp_path)), nprocs=2, start_method="spawn")
+    b0, b1 = np.load(tmp_path / "b0.npy"), np.load(tmp_path / "b1.npy")
+    assert np.array_equal(b0, b1) and b0.size == 1 + 6
+    th = np.array([1000.0, 0.5, 0.05, 50.0, 2.0, -1.0])
+    ref = oracle.binned1d(1, 2, 1, oracle.CHI2, ys, 0.0, 1.0, th)
+    assert b0[0] == ref.value and np.array_equal(b0[1:], ref.grad)

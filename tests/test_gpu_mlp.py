@@ -1,5 +1,6 @@
 """BF16 tensor-core kernels of the learned-start network against CPU FP32
 references computed from the same BF16-rounded inputs."""
+import numpy as np
 import pytest
 import torch
 
@@ -265,11 +266,16 @@ def test_mlp_forward_backward_vs_reference(dev):
     net.backward(x)
     torch.cuda.synchronize()
     Yr, lr_, gr = _ref_mlp(net, x, t)
-    torch.testing.assert_close(Y, Yr, rtol=2e-2, atol=2e-2)
-    assert abs(float(loss) - float(lr_)) <= 1e-2 * float(lr_)
+    # the bars of the network's parity: outputs within 1e-3 and weight
+    # gradients within 1e-2 (normwise: largest deviation over the largest
+    # entry) of an FP32 reference with BF16 rounding at the kernel's points;
+    # what remains is FP32 summation order and the rare BF16 rounding that
+    # tips the other way
+    assert float((Y - Yr).abs().max()) <= 1e-3 * float(Yr.abs().max())
+    assert abs(float(loss) - float(lr_)) <= 1e-4 * float(lr_)
     for got, ref in zip(net.grads, gr):
         scale = float(ref.abs().max())
-        assert float((got - ref).abs().max()) <= 2e-2 * scale, (got.shape, float((got - ref).abs().max()), scale)
+        assert float((got - ref).abs().max()) <= 1e-2 * scale, (got.shape, float((got - ref).abs().max()), scale)
 
 
 def test_training_reduces_loss(dev):
@@ -282,15 +288,51 @@ def test_training_reduces_loss(dev):
     assert curve[-1][1] < 0.6 * curve[0][1], curve[:3] + curve[-3:]
 
 
+def test_training_checkpoint_resume_is_bitwise(dev, tmp_path):
+    """A training run checkpointed part-way (weights, Adam moments, step,
+    target normalisation, epoch position, shuffling generator) and resumed
+    by a fresh Trainer on a differently initialised network follows the
+    uninterrupted run's loss curve and ends at its weights, bit for bit."""
+    d = synth.c5_batch_device(8192, chunk=92, device=dev)
+    x, scale = ls.rebin(d["y"], 8192)
+    theta = torch.tensor(d["truth"], device=dev)
+    net = ls.MLP(seed=1)
+    tr = ls.Trainer(net, x, scale, theta, epochs=3, batch=256, lr=1e-3, log_every=1)
+    tr.run(40)                                  # 32 steps per epoch: the checkpoint falls inside epoch 1
+    ck = tmp_path / "train.pt"
+    tr.save(ck)
+    tr.run()
+    curve = list(tr.curve)
+    W_end = [w.clone() for w in net.W] + [b.clone() for b in net.b]
+    assert net.step == 96 and len(curve) == 96
+    net2 = ls.MLP(seed=7)
+    tr2 = ls.Trainer(net2, x, scale, theta, epochs=1, batch=128, lr=5e-3, seed=123, log_every=1)
+    tr2.load(ck)
+    tr2.run()
+    assert net2.step == 96
+    assert tr2.curve == curve                   # float losses compared exactly
+    for a, b in zip(W_end, net2.W + net2.b):
+        assert torch.equal(a, b)
+
+
 @pytest.mark.slow
 def test_learned_start_gains_over_the_heuristic(dev):
-    """Trained on 262,144 method-generated fits, the network's start (chosen per
-    histogram against the heuristic by the objective) ends held-out fits at a
-    lower mean NLL with no fewer converged fits than the heuristic start."""
+    """Trained on 262,144 method-generated fits, the production path (network
+    start, refit from the heuristic start where the fit did not converge,
+    lower minimum kept) ends held-out fits at no higher NLL than the
+    heuristic-start fits in nearly every histogram, converges at least as
+    many, and the network's starts need fewer iterations on average."""
     x, scale, theta = ls.make_training_set(262144)
     net = ls.MLP(seed=0)
     ls.train(net, x, scale, theta, epochs=6, lr=2e-3)
-    ev = ls.evaluate(net, H=4096, chunk=0)
-    assert ev["learned"]["mean_nll"] < ev["heuristic"]["mean_nll"], ev
-    assert ev["learned"]["converged"] >= ev["heuristic"]["converged"], ev
-    assert ev["nll_learned_le_heuristic_frac"] > 0.9, ev
+    H = 4096
+    y = synth.c5_batch_device(H, ls.N_BINS, chunk=0, device=dev)["y"]
+    fh = ls.fit_batch(y, H, ls.heuristic_start(y, H), 50, 1e-9)
+    pr = ls.production_fit(net, y, H, 50, 1e-9)
+    Fh, Fp = fh.states.f.cpu().numpy(), pr["f"].cpu().numpy()
+    conv_h = int((fh.states.status == cg.FIT_CONVERGED).sum())
+    conv_p = int((pr["status"] == cg.FIT_CONVERGED).sum())
+    assert conv_p >= conv_h
+    assert np.mean(Fp <= Fh * (1 + 1e-6)) > 0.95
+    il = pr["learned"].states.iters.double().mean().item()
+    assert il < fh.states.iters.double().mean().item()

@@ -60,6 +60,28 @@ def test_noalloc_matches_batch_gradient_twice(env):
         _close(v, g, v_ref, g_ref)
 
 
+def test_noalloc_leaves_free_device_memory_unchanged(env):
+    """After a first call (which takes the scratch array's device address),
+    further calls allocate nothing: the device's free memory, read through
+    cudaMemGetInfo, is the same before and after them."""
+    cg, f, dev = env
+    x = torch.tensor(synth.c2_events(200003), device=dev)
+    pb = cg.Problem.mixture(x, 0.0, 10.0)
+    th = torch.tensor(synth.c2_theta_points(5), device=dev)
+    v = torch.empty(5, dtype=torch.float64, device=dev)
+    g = torch.empty((5, 4), dtype=torch.float64, device=dev)
+    args = (ctypes.byref(pb.c), ctypes.c_void_p(th.data_ptr()), 5, ctypes.c_void_p(v.data_ptr()),
+            ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert f(*args) == cg.OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(4):
+        assert f(*args) == cg.OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
 def test_noalloc_weighted_and_limits(env):
     cg, f, dev = env
     x = torch.tensor(synth.c2_events(20001), device=dev)
