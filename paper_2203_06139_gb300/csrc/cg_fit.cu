@@ -121,10 +121,13 @@ __device__ __forceinline__ void acc_bins_f64(const Geom& G, const GP1Consts& cs,
     GP1C2 c2;
     gp1_c2(cs, K, c2);
     const double hh = 0.5 * G.hw;   // centre (2i + 1) (h/2) + lo, correctly rounded
-    for (int64_t i = t0; i < G.n; i += T) {
-        const GP1Bin b = gp1_bin<OBJ>(fma((double)(2 * i + 1), hh, G.lo), __ldg(G.y + i), dd, tab);
-        gp1_elem_f64<K, OBJ>(b, cs, c2, dd.D, tab, acc, bad);
-    }
+    gp1_dispatch(dd.D, dd.pm, [&](auto dd_, auto pm_) {
+        constexpr int DD = decltype(dd_)::value, PM = decltype(pm_)::value;
+        for (int64_t i = t0; i < G.n; i += T) {
+            const GP1Bin b = gp1_bin<OBJ, PM>(fma((double)(2 * i + 1), hh, G.lo), __ldg(G.y + i), dd, tab);
+            gp1_elem_f64<K, OBJ, DD>(b, cs, c2, tab, acc, bad);
+        }
+    });
     gp1_tile_scale<K, OBJ>(acc);
     bad |= nonfinite(acc[0]);
 }

@@ -106,30 +106,34 @@ __global__ void __launch_bounds__(NT) k_gp1_fp64(GP1Data d, const double* __rest
         // (2i + 1 and h/2 are exact, so this is the correctly rounded centre)
         const double hh = 0.5 * d.h;
         auto centre = [&](int64_t i) { return fma((double)(2 * i + 1), hh, d.lo); };
-        auto bin = [&](double x, double y) {
-            const GP1Bin b = gp1_bin<OBJ>(x, y, d, tab);
-#pragma unroll
-            for (int p = 0; p < PT; ++p) gp1_elem_f64<K, OBJ>(b, cs[p], cq[p], d.D, tab, acc[p], bad[p]);
-        };
         const int64_t e0 = (int64_t)c * tg.chunk;
         const int64_t e1 = min(tg.n_elem, e0 + tg.chunk);
-        if (d.vec_ok) {
-            // two consecutive bins per thread with one 16-byte load of the counts (e0 is even)
-            for (int64_t i = e0 + 2 * threadIdx.x; i < e1; i += 2 * NT) {
-                if (i + 1 < e1) {
-                    const double2 y2 = __ldg(reinterpret_cast<const double2*>(d.y + i));
-                    double2 x2;
-                    if (d.centres) x2 = __ldg(reinterpret_cast<const double2*>(d.centres + i));
-                    else { x2.x = centre(i); x2.y = centre(i + 1); }
-                    bin(x2.x, y2.x);
-                    bin(x2.y, y2.y);
-                } else {
-                    bin(d.centres ? d.centres[i] : centre(i), d.y[i]);
+        gp1_dispatch(d.D, d.pm, [&](auto dd_, auto pm_) {
+            constexpr int DD = decltype(dd_)::value, PM = decltype(pm_)::value;
+            auto bin = [&](double x, double y) {
+                const GP1Bin b = gp1_bin<OBJ, PM>(x, y, d, tab);
+#pragma unroll
+                for (int p = 0; p < PT; ++p) gp1_elem_f64<K, OBJ, DD>(b, cs[p], cq[p], tab, acc[p], bad[p]);
+            };
+            if (d.vec_ok) {
+                // two consecutive bins per thread with one 16-byte load of the counts (e0 is even)
+                for (int64_t i = e0 + 2 * threadIdx.x; i < e1; i += 2 * NT) {
+                    if (i + 1 < e1) {
+                        const double2 y2 = __ldg(reinterpret_cast<const double2*>(d.y + i));
+                        double2 x2;
+                        if (d.centres) x2 = __ldg(reinterpret_cast<const double2*>(d.centres + i));
+                        else { x2.x = centre(i); x2.y = centre(i + 1); }
+                        bin(x2.x, y2.x);
+                        bin(x2.y, y2.y);
+                    } else {
+                        bin(d.centres ? d.centres[i] : centre(i), d.y[i]);
+                    }
                 }
+            } else {
+                for (int64_t i = e0 + threadIdx.x; i < e1; i += NT)
+                    bin(d.centres ? d.centres[i] : centre(i), d.y[i]);
             }
-        } else {
-            for (int64_t i = e0 + threadIdx.x; i < e1; i += NT) bin(d.centres ? d.centres[i] : centre(i), d.y[i]);
-        }
+        });
         int bm = 0;
 #pragma unroll
         for (int p = 0; p < PT; ++p) {
@@ -190,7 +194,7 @@ __global__ void __launch_bounds__(NT) k_mix_fp64(MixData d, const double* __rest
             for (int64_t i = e0 + threadIdx.x; i < e1; i += NT)
                 mix_elem_f64<W>(d.x[i], W ? d.w[i] : 1.0, cs, cq, tab, acc, lp, bad);
         }
-        if (!W) acc[0] += logprod_log(lp, tab);
+        mix_tile_finish<W>(cs, tab, acc, lp);
         const int any_bad = __syncthreads_or(bad ? 1 : 0) | cs_bad;
         block_sum_rs<NACC, NT>(acc, red, tot);
         write_partial<NACC>(part, tg, th, c, tot, any_bad);
@@ -254,11 +258,13 @@ __global__ void __launch_bounds__(NT) k_rg2_fp64(RG2Data d, const double* __rest
         bool bad = false;
         const int w = (int)(x1 - x0);
         const int nbin = w * (int)(y1 - y0);
+        // centres lo + (i + 1/2) h as (2i + 1) (h/2) + lo (correctly rounded, one FMA each)
+        const double hhx = 0.5 * d.hx, hhy = 0.5 * d.hy;
         for (int b = threadIdx.x; b < nbin; b += NT) {
             const int r = b / w, col = b - r * w;
             const int64_t ix = x0 + col, iy = y0 + r;
-            const double xc = fma((double)ix + 0.5, d.hx, d.lx);
-            const double yc = fma((double)iy + 0.5, d.hy, d.ly);
+            const double xc = fma((double)(2 * ix + 1), hhx, d.lx);
+            const double yc = fma((double)(2 * iy + 1), hhy, d.ly);
             rg2_elem_f64<K>(xc, yc, __ldg(d.n + iy * d.nx + ix), cs, cq, act, tab, acc, bad);
         }
         bad |= nonfinite(acc[0]);

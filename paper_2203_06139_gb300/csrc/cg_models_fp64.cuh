@@ -16,6 +16,8 @@
 //    (exact: powers of two), and non-finite terms are detected from those
 //    sums (a NaN or infinity in any term reaches the sum).
 #pragma once
+#include <type_traits>
+
 #include "cg_fp64.cuh"
 #include "cg_models.cuh"
 
@@ -46,11 +48,13 @@ struct GP1Bin {
 // its high word is at least that of 1.0 and the sign is clear).
 __device__ __forceinline__ double max_y_1(double y) { return (__double2hiint(y) >= 0x3ff00000) ? y : 1.0; }
 
-template <int OBJ>
+// PM: the polynomial's variable, x (0) or t = au x + bu (1), fixed at compile
+// time so that neither is computed in vain.
+template <int OBJ, int PM>
 __device__ __forceinline__ GP1Bin gp1_bin(double x, double y, const GP1Data& d, const Fp64Tab& tab) {
     GP1Bin b;
     b.x = x;
-    b.u = d.pm ? fma(x, d.au, d.bu) : x;
+    b.u = PM ? fma(x, d.au, d.bu) : x;
     b.y = y;
     b.ypos = __double_as_longlong(y) > 0;   // exact test of y > 0 (a NaN count reads as positive: its term is NaN)
     b.ymy = 0.0;
@@ -67,9 +71,12 @@ __device__ __forceinline__ GP1Bin gp1_bin(double x, double y, const GP1Data& d, 
 // g e, g e d, g e d^2, then g u^j), except the scale: chi2 accumulates
 // -2 T in acc[0] and the true adjoint g = -2 w r elsewhere (gp1_tile_scale
 // multiplies acc[0] by -1/2); Poisson accumulates T and g; Baker-Cousins
-// accumulates T/2 and g/2 (gp1_tile_scale doubles everything).
-template <int K, int OBJ>
-__device__ __forceinline__ void gp1_elem_f64(const GP1Bin& b, const GP1Consts& cs, const GP1C2& c2, int D,
+// accumulates T/2 and g/2 (gp1_tile_scale doubles everything).  D: the
+// polynomial's degree (-1: none), fixed at compile time: with a run-time
+// degree the compiler evaluates every Horner step and adjoint term of the
+// largest degree and selects, several FP64 instructions per bin in vain.
+template <int K, int OBJ, int D>
+__device__ __forceinline__ void gp1_elem_f64(const GP1Bin& b, const GP1Consts& cs, const GP1C2& c2,
                                              const Fp64Tab& tab, double (&acc)[GP1Acc<K>::N], bool& bad) {
     double f = 0.0;
 #pragma unroll
@@ -115,12 +122,31 @@ __device__ __forceinline__ void gp1_elem_f64(const GP1Bin& b, const GP1Consts& c
         acc[2 + 3 * k] += td;
         acc[3 + 3 * k] = fma(td, dk[k], acc[3 + 3 * k]);
     }
-    double up = 1.0;
+    if (D >= 0) acc[1 + 3 * K] += g;
+    double up = b.u;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 1; j < 4; ++j) {
         if (j <= D) acc[1 + 3 * K + j] = fma(g, up, acc[1 + 3 * K + j]);
         if (j < D) up *= b.u;
     }
+}
+
+// Calls f(std::integral_constant<int, D>, std::integral_constant<int, PM>)
+// for the run-time degree d (-1..3) and polynomial mode pm: one switch per
+// tile or evaluation, outside the bin loops, so that every bin loop is
+// compiled for its degree.
+template <typename F>
+__device__ __forceinline__ void gp1_dispatch(int d, int pm, F&& f) {
+#define CG_GP1_D(DD)                                                                              \
+    case DD:                                                                                      \
+        if (pm) f(std::integral_constant<int, DD>{}, std::integral_constant<int, 1>{});           \
+        else f(std::integral_constant<int, DD>{}, std::integral_constant<int, 0>{});              \
+        break;
+    switch (d) {
+        CG_GP1_D(-1) CG_GP1_D(0) CG_GP1_D(1) CG_GP1_D(2) CG_GP1_D(3)
+        default: break;
+    }
+#undef CG_GP1_D
 }
 
 // The objective's constant factors on one thread's sums (see gp1_elem_f64).
@@ -135,18 +161,22 @@ __device__ __forceinline__ void gp1_tile_scale(double (&acc)[GP1Acc<K>::N]) {
 }
 
 // ===========================================================================
-// Unbinned mixture: p = a 2^(c2 d^2) + b 2^(nl2 (x - lo)),
-// c2 = -log2(e)/(2 s^2), nl2 = -lambda log2(e).  Accumulators as
-// mix_elem_fp64; without weights acc[0] is not touched per event: the log of
-// p goes into the running product lp (the caller adds logprod_log(lp)).
+// Unbinned mixture: p = a 2^(c2 d^2) + b 2^(nl2 x + nl2lo),
+// c2 = -log2(e)/(2 s^2), nl2 = -lambda log2(e), nl2lo = -nl2 lo (the
+// exponent -lambda (x - lo) log2(e) in one FMA).  Accumulators as
+// mix_elem_fp64, except that acc[5] accumulates V x and mix_tile_finish
+// turns it into sum V (x - lo) = sum V x - lo sum V once per thread; without
+// weights acc[0] is not touched per event: the log of p goes into the
+// running product lp (mix_tile_finish adds its logarithm).
 // ===========================================================================
 struct MixC2 {
-    double c2, nl2;
+    double c2, nl2, nl2lo;
 };
 
 __device__ __forceinline__ void mix_c2(const MixConsts& cs, MixC2& c) {
     c.c2 = cs.c * kLog2e;
     c.nl2 = -cs.lam * kLog2e;
+    c.nl2lo = -c.nl2 * cs.lo;
 }
 
 template <bool W>
@@ -155,8 +185,7 @@ __device__ __forceinline__ void mix_elem_f64(double x, double w, const MixConsts
                                              bool& bad) {
     const double d = x - cs.mu;
     const double eG = fexp2((c2.c2 * d) * d, tab);
-    const double xl = x - cs.lo;
-    const double eE = fexp2(c2.nl2 * xl, tab);
+    const double eE = fexp2(fma(c2.nl2, x, c2.nl2lo), tab);
     const double p = fma(cs.a, eG, cs.b * eE);
     double r;
     if (fp64_fast_range(p)) {
@@ -175,7 +204,16 @@ __device__ __forceinline__ void mix_elem_f64(double x, double w, const MixConsts
     acc[2] += Ud;
     acc[3] = fma(Ud, d, acc[3]);
     acc[4] += V;
-    acc[5] = fma(V, xl, acc[5]);
+    acc[5] = fma(V, x, acc[5]);
+}
+
+// End of a thread's events: sum V (x - lo) from sum V x and sum V, and the
+// log of the running product into the value (without weights).
+template <bool W>
+__device__ __forceinline__ void mix_tile_finish(const MixConsts& cs, const Fp64Tab& tab, double (&acc)[MixAcc::N],
+                                                const LogProd& lp) {
+    acc[5] = fma(-cs.lo, acc[4], acc[5]);
+    if (!W) acc[0] += logprod_log(lp, tab);
 }
 
 // ===========================================================================

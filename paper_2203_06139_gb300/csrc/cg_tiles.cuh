@@ -114,13 +114,14 @@ inline cg_status launch_tiles(KernelT kern, int NT, const DataT& d, const double
 
 // Tile grid of the FP64 kernels, whose time is set by the FP64 unit of each
 // SM: among chunk counts per point group nbx (chunks of at least 2 elements
-// per thread, even, within the workspace bound), the one whose busiest SM
-// gets the fewest element-points, i.e. the smallest
-// ceil(n_groups * nbx / n_sm) * chunk, with a 5 % penalty per missing tile
+// per thread, even, within the workspace bound), the one whose busiest CTA
+// of the persistent grid (grid = n_sm x resident CTAs, tiles dealt out
+// round-robin) gets the fewest element-points, i.e. the smallest
+// ceil(n_groups * nbx / grid) * chunk, with a 5 % penalty per missing tile
 // below two tiles per SM (one CTA per SM leaves too few warps to cover the
 // FP64 latencies; measured on the 10,000-bin x 100-point workload); ties:
 // fewer tiles.  n_groups = ceil(n_theta / pt) groups of pt points.
-inline TileGrid make_tiles_balanced(int64_t n_elem, int64_t n_theta, int pt, int NT, int n_sm) {
+inline TileGrid make_tiles_balanced(int64_t n_elem, int64_t n_theta, int pt, int NT, int n_sm, int resident) {
     TileGrid tg;
     tg.n_elem = n_elem;
     const int64_t groups = (n_theta + pt - 1) / pt;
@@ -130,6 +131,7 @@ inline TileGrid make_tiles_balanced(int64_t n_elem, int64_t n_theta, int pt, int
     if (most > max_nbx(n_theta)) most = max_nbx(n_theta);
     if (most < 1) most = 1;
     const int64_t S = n_sm > 0 ? n_sm : 1;
+    const int64_t G = S * (resident > 0 ? resident : 1);
     int64_t best = 1, best_cost = -1;
     for (int64_t nbx = 1; nbx <= most; ++nbx) {
         int64_t chunk = (n_elem + nbx - 1) / nbx;
@@ -137,7 +139,7 @@ inline TileGrid make_tiles_balanced(int64_t n_elem, int64_t n_theta, int pt, int
         if ((n_elem + chunk - 1) / chunk != nbx) continue;
         const double per_sm = (double)(groups * nbx) / (double)S;
         const double pen = per_sm < 2.0 ? 1.0 + 0.05 * (2.0 - per_sm) : 1.0;
-        const int64_t cost = (int64_t)((double)((groups * nbx + S - 1) / S * chunk) * pen);
+        const int64_t cost = (int64_t)((double)((groups * nbx + G - 1) / G * chunk) * pen);
         if (best_cost < 0 || cost < best_cost) {
             best_cost = cost;
             best = nbx;
@@ -161,7 +163,7 @@ inline cg_status launch_tiles_balanced(KernelT kern, int NT, int pt, const DataT
                                        TileGrid* tg_out, cudaStream_t st, const int* gate = nullptr) {
     const int nsm = device_sm_count();
     const int R = resident_blocks((const void*)kern, NT, 0);
-    TileGrid tg = make_tiles_balanced(n_elem, n_theta, pt, NT, nsm);
+    TileGrid tg = make_tiles_balanced(n_elem, n_theta, pt, NT, nsm, R);
     tg.gate = gate;
     const int G = nsm * R;
     const int grid = tg.n_tiles < G ? tg.n_tiles : G;

@@ -302,7 +302,7 @@ class Trainer:
         return {"W": [w.clone() for w in net.W], "b": [b.clone() for b in net.b],
                 "m": [m.clone() for m in net.m], "v": [v.clone() for v in net.v], "step": net.step,
                 "t_mean": net.t_mean.clone(), "t_std": net.t_std.clone(), "epoch": self.epoch, "i0": self.i0,
-                "gen_state": self.gen_state.clone(), "curve": list(self.curve),
+                "gen_state": self.gen_state.cpu().clone(), "curve": list(self.curve),
                 "config": {"epochs": self.epochs, "batch": self.batch, "lr": self.lr, "cosine": self.cosine}}
 
     def load_state_dict(self, sd):
@@ -317,7 +317,7 @@ class Trainer:
         c = sd["config"]
         self.epochs, self.batch, self.lr, self.cosine = c["epochs"], c["batch"], c["lr"], c["cosine"]
         self.epoch, self.i0 = int(sd["epoch"]), int(sd["i0"])
-        self.gen.set_state(sd["gen_state"].clone())
+        self.gen.set_state(sd["gen_state"].cpu().to(torch.uint8).clone())   # generator states are CPU byte tensors
         self._new_epoch()          # the same permutation as at the checkpoint's epoch start
         self.curve = list(sd["curve"])
 

@@ -12,7 +12,7 @@ import bench
 
 
 def test_fp64_roofline_arithmetic():
-    # 1e7 x 50 event-points of 33 FP64-pipe instructions in 31.5 ms
+    # 1e7 x 50 event-points of 33 FP64-pipe instructions in 31.5 ms (arithmetic only)
     r = bench.roofline_fp64("k", 33, 5e8, 31.5e-3, 2070.0)
     peak = 152 * 2 * 2 * 2070e6 / 1e12
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
@@ -38,11 +38,12 @@ def test_df64_roofline_arithmetic():
 def test_instruction_counts_add_up():
     # the per-unit FP64 counts are the sums spelled out next to them
     exp2, rcp, log = 7, 3, 13
-    assert bench.FP64_INSTR["mix"] == 1 + 1 + 1 + exp2 + 1 + 1 + exp2 + 1 + 1 + rcp + 1 + 1 + 1 + 1 + 5
+    assert bench.FP64_INSTR["mix"] == 1 + 1 + 1 + exp2 + 1 + exp2 + 1 + 1 + rcp + 1 + 1 + 1 + 1 + 5
     assert bench.FP64_INSTR["gp1_c1"] == 1 + 1 + 2 + exp2 + 1 + 3 + 5 + 2 + 6 / 4
     assert bench.FP64_INSTR["fit_c4"] == 2 + 4 + 2 + (1 + 2 + exp2 + 1) + 3 + 5 + 5
     assert bench.FP64_INSTR["fit_c5"] == 2 + log + 1 + 1 + 3 * (1 + 2 + exp2 + 1) + log + rcp + 3 + 1 + 15 + 2
     assert bench.FP64_INSTR["rg2_gauss"] == 2 + 5 + exp2 + 1 + 3 + 6
+    assert bench.FP64_INSTR["rg2_bin"] == 2 * 2 + log + rcp + 4
 
 
 def test_ncu_records_are_null_for_other_sizes_or_sources(monkeypatch):
