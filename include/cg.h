@@ -243,6 +243,26 @@ cg_status cg_rebin_normalize(const double *y, int64_t H, int n_bins, int factor,
 cg_status cg_heuristic_start(const double *y, int64_t H, int n_bins, int factor, double lo, double hi, int n_peaks,
                              double *theta0, void *stream);
 
+/* Refinement of starting points of K peaks + linear background on the
+ * full-resolution histogram (y: device [H][n_bins] FP64 on [lo, hi];
+ * theta_in / theta_out: device [H][3K+2], (A, mu, s) per peak then b0, b1;
+ * theta_out may equal theta_in).  Not in the paper: it sharpens a coarse
+ * start (the network's proposal from the rebinned histogram, or the
+ * heuristic's) before the fit.  One warp per histogram, `sweeps` passes over
+ * the peaks in order of position: for peak k the counts within
+ * mu_k +- w_k, w_k = half_width max(s_k, 4 h) (h the bin width), less the
+ * background and the other peaks at the current parameters, are clipped
+ * at zero and give moments S0, S1, S2 about mu_k; then mu_k += S1/S0, the
+ * width is the one whose Gaussian truncated at +-w_k has the variance
+ * S2/S0 - (S1/S0)^2 (one fixed-point step of var = s^2 (1 - 2 z phi(z) /
+ * erf(z/sqrt 2)), z = w/s, z clamped to [0.5, 10]), and the height makes
+ * the truncated Gaussian's sum S0.  A peak whose window holds no positive
+ * residual keeps its parameters; peaks leave sorted by position.  FP64;
+ * window bounds and centres rounded operation by operation (no fused
+ * multiply-add).  K <= 8, sweeps in [0, 16], half_width in (0, 10]. */
+cg_status cg_refine_start(const double *y, int64_t H, int n_bins, double lo, double hi, int n_peaks,
+                          const double *theta_in, double *theta_out, int sweeps, double half_width, void *stream);
+
 /* loss = mean over B x n_out of (pred - target)^2 (pred rows of stride ld,
  * target [B][n_out]); dpred (FP32) and/or dpred_bf16 get its gradient, zero in
  * the padding columns.  One CTA, fixed-order sums. */

@@ -76,6 +76,8 @@ def lib():
         "cg_rebin_normalize": (ctypes.c_int, [_vp, _i64, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
         "cg_heuristic_start": (ctypes.c_int, [_vp, _i64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_int, _vp, _vp]),
+        "cg_refine_start": (ctypes.c_int, [_vp, _i64, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                           _vp, _vp, ctypes.c_int, ctypes.c_double, _vp]),
         "cg_mse_loss": (ctypes.c_int, [_vp, _vp, _i64, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]),
         "cg_colsum": (ctypes.c_int, [_vp, _i64, ctypes.c_int, _vp, _vp]),
         "cg_adamw": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,

@@ -1100,6 +1100,101 @@ __global__ void k_heuristic(const double* __restrict__ y, int64_t H, int n_bins,
     }
 }
 
+// Refinement of starting points of K peaks + linear background on the
+// full-resolution histogram, one warp per histogram (see cg.h,
+// cg_refine_start).  Window bounds and bin centres are rounded operation by
+// operation (no fused multiply-add), so that a plain restatement reproduces
+// which bins each window holds.
+__global__ void k_refine(const double* __restrict__ y, int64_t H, int n_bins, double lo, double hi, int K,
+                         const double* __restrict__ th_in, double* __restrict__ th_out, int sweeps, double half) {
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int P = 3 * K + 2;
+    const double h = __ddiv_rn(__dsub_rn(hi, lo), (double)n_bins);
+    for (int64_t hh = (int64_t)blockIdx.x * nw + wid; hh < H; hh += (int64_t)gridDim.x * nw) {
+        const double* yh = y + hh * (int64_t)n_bins;
+        const double* ti = th_in + hh * P;
+        double A[8], mu[8], s[8];
+        for (int k = 0; k < K; ++k) {
+            A[k] = ti[3 * k];
+            mu[k] = ti[3 * k + 1];
+            s[k] = fabs(ti[3 * k + 2]);
+        }
+        const double b0 = ti[3 * K], b1 = ti[3 * K + 1];
+        auto sort_peaks = [&]() {
+            for (int i = 1; i < K; ++i)
+                for (int j = i; j > 0 && mu[j] < mu[j - 1]; --j) {
+                    double t;
+                    t = mu[j]; mu[j] = mu[j - 1]; mu[j - 1] = t;
+                    t = A[j]; A[j] = A[j - 1]; A[j - 1] = t;
+                    t = s[j]; s[j] = s[j - 1]; s[j - 1] = t;
+                }
+        };
+        sort_peaks();
+        for (int sw = 0; sw < sweeps; ++sw) {
+            for (int k = 0; k < K; ++k) {
+                const double w = __dmul_rn(half, fmax(s[k], __dmul_rn(4.0, h)));
+                if (!(isfinite(mu[k]) && isfinite(w) && w > 0.0)) continue;
+                const double a0 = floor(__ddiv_rn(__dsub_rn(__dsub_rn(mu[k], w), lo), h));
+                const double a1 = ceil(__ddiv_rn(__dsub_rn(__dadd_rn(mu[k], w), lo), h));
+                const int i0 = a0 < 0.0 ? 0 : (a0 > (double)(n_bins - 1) ? n_bins : (int)a0);
+                const int i1 = a1 > (double)(n_bins - 1) ? n_bins - 1 : (a1 < 0.0 ? -1 : (int)a1);
+                double S0 = 0.0, S1 = 0.0, S2 = 0.0;
+                for (int i = i0 + lane; i <= i1; i += 32) {
+                    const double x = __dadd_rn(lo, __dmul_rn((double)i + 0.5, h));
+                    const double dx = __dsub_rn(x, mu[k]);
+                    if (!(fabs(dx) <= w)) continue;
+                    double r = __dsub_rn(yh[i], __dadd_rn(b0, __dmul_rn(b1, x)));
+                    for (int j = 0; j < K; ++j) {
+                        if (j == k) continue;
+                        const double z = __ddiv_rn(__dsub_rn(x, mu[j]), s[j]);
+                        r = __dsub_rn(r, __dmul_rn(A[j], exp(__dmul_rn(-0.5, __dmul_rn(z, z)))));
+                    }
+                    if (!(r > 0.0)) continue;
+                    S0 = __dadd_rn(S0, r);
+                    S1 = __dadd_rn(S1, __dmul_rn(r, dx));
+                    S2 = __dadd_rn(S2, __dmul_rn(__dmul_rn(r, dx), dx));
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {   // butterfly: every lane ends with the same sums
+                    S0 = __dadd_rn(S0, __shfl_xor_sync(0xffffffffu, S0, o));
+                    S1 = __dadd_rn(S1, __shfl_xor_sync(0xffffffffu, S1, o));
+                    S2 = __dadd_rn(S2, __shfl_xor_sync(0xffffffffu, S2, o));
+                }
+                if (!(S0 > 0.0)) continue;
+                const double m1 = __ddiv_rn(S1, S0);
+                double var = __dsub_rn(__ddiv_rn(S2, S0), __dmul_rn(m1, m1));
+                const double vmin = __dmul_rn(__dmul_rn(0.5, h), __dmul_rn(0.5, h));
+                if (!(var > vmin)) var = vmin;
+                // width of a Gaussian truncated at +-w with this variance: one step of
+                // var = s^2 (1 - 2 z phi(z) / erf(z / sqrt 2)), z = w / s, from z = w / sqrt(var)
+                double z = __ddiv_rn(w, sqrt(var));
+                z = fmin(fmax(z, 0.5), 10.0);
+                const double phi = __dmul_rn(0.3989422804014327, exp(__dmul_rn(-0.5, __dmul_rn(z, z))));
+                const double frac = __dsub_rn(1.0, __ddiv_rn(__dmul_rn(__dmul_rn(2.0, z), phi),
+                                                             erf(__dmul_rn(z, 0.7071067811865476))));
+                const double s2 = sqrt(__ddiv_rn(var, frac));
+                const double cover = erf(__dmul_rn(__ddiv_rn(w, s2), 0.7071067811865476));
+                A[k] = __ddiv_rn(__dmul_rn(S0, h), __dmul_rn(__dmul_rn(s2, 2.5066282746310002), cover));
+                mu[k] = __dadd_rn(mu[k], m1);
+                s[k] = s2;
+            }
+            sort_peaks();
+        }
+        double* to = th_out + hh * P;
+        __syncwarp();
+        if (lane == 0) {
+            for (int k = 0; k < K; ++k) {
+                to[3 * k] = A[k];
+                to[3 * k + 1] = mu[k];
+                to[3 * k + 2] = s[k];
+            }
+            to[3 * K] = b0;
+            to[3 * K + 1] = b1;
+        }
+        __syncwarp();
+    }
+}
+
 // Mean squared error over the first n_out of ld columns, and its gradient.
 // One block; fixed-order sums.
 __global__ void k_mse(const float* __restrict__ pred, const float* __restrict__ tgt, int64_t B, int n_out, int ld,
@@ -1197,6 +1292,19 @@ cg_status cg_heuristic_start(const double* y, int64_t H, int n_bins, int factor,
     const int g = (int)std::min<int64_t>(blocks, 16 * (int64_t)cg::device_sm_count());
     cg::k_heuristic<<<g, 32 * nw, nw * per_warp, (cudaStream_t)stream>>>(y, H, n_bins, factor, lo, hi, n_peaks,
                                                                         theta0);
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
+
+cg_status cg_refine_start(const double* y, int64_t H, int n_bins, double lo, double hi, int n_peaks,
+                          const double* theta_in, double* theta_out, int sweeps, double half_width, void* stream) {
+    if (!y || !theta_in || !theta_out || H < 1 || n_bins < 1 || n_peaks < 1 || n_peaks > 8 || !(hi > lo) ||
+        sweeps < 0 || sweeps > 16 || !(half_width > 0.0) || !(half_width <= 10.0))
+        return CG_ERR_INVALID_ARG;
+    const int nw = 8;
+    const int64_t blocks = (H + nw - 1) / nw;
+    const int g = (int)std::min<int64_t>(blocks, 16 * (int64_t)cg::device_sm_count());
+    cg::k_refine<<<g, 32 * nw, 0, (cudaStream_t)stream>>>(y, H, n_bins, lo, hi, n_peaks, theta_in, theta_out,
+                                                         sweeps, half_width);
     return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
 }
 

@@ -53,6 +53,19 @@ def heuristic_start(y_flat, H):
     return th
 
 
+REFINE_SWEEPS, REFINE_HALF_WIDTH = 2, 2.5
+
+
+def refine_start(y_flat, H, theta, sweeps=REFINE_SWEEPS, half_width=REFINE_HALF_WIDTH):
+    """Starting parameters sharpened on the full-resolution histogram
+    (cg_refine_start: per peak, moments of the counts in a window of
+    +-half_width widths less the background and the other peaks)."""
+    out = torch.empty_like(theta)
+    cg._check(cg.lib().cg_refine_start(_p(y_flat), H, N_BINS, 0.0, 1.0, K_PEAKS, _p(theta.contiguous()), _p(out),
+                                       int(sweeps), float(half_width), _s()), "cg_refine_start")
+    return out
+
+
 def canonical(theta):
     """Peaks sorted by mu with positive widths (the fit is symmetric in s and
     in the order of the peaks)."""
@@ -333,15 +346,19 @@ def train(net, x, scale, theta, epochs=3, batch=1024, lr=1e-3, seed=0, log=None,
     return Trainer(net, x, scale, theta, epochs=epochs, batch=batch, lr=lr, seed=seed, cosine=cosine).run(log=log)
 
 
-def production_fit(net, y, H, n_steps=50, tol=1e-9, precision=FIT_PRECISION):
+def production_fit(net, y, H, n_steps=50, tol=1e-9, precision=FIT_PRECISION, refine=True):
     """Fits of H histograms from the learned start, judged by the plain fit:
-    every histogram is fitted from the network's start; the histograms whose
-    fit did not converge within n_steps iterations are fitted again from the
-    plain peak-finding heuristic start, and the lower of the two minima is
-    kept.  Returns dict(theta [H, P], f [H], status [H], iters [H], evals
-    [H], refit (indices refitted, host), learned (the learned-start fitter))."""
+    every histogram is fitted from the network's start (sharpened on the
+    full-resolution histogram when refine is set); the histograms whose fit
+    did not converge within n_steps iterations are fitted again from the
+    plain peak-finding heuristic start (sharpened alike), and the lower of
+    the two minima is kept.  Returns dict(theta [H, P], f [H], status [H],
+    iters [H], evals [H], refit (indices refitted, host), learned (the
+    learned-start fitter))."""
     x, scale = rebin(y, H)
     th0 = net.predict_start(x, scale)
+    if refine:
+        th0 = refine_start(y, H, th0)
     fl = fit_batch(y, H, th0, n_steps, tol, precision=precision)
     st = fl.states
     theta, f = st.theta.clone(), st.f.clone()
@@ -349,7 +366,10 @@ def production_fit(net, y, H, n_steps=50, tol=1e-9, precision=FIT_PRECISION):
     idx = torch.nonzero(status != cg.FIT_CONVERGED).flatten()
     if idx.numel():
         ysub = y.view(H, N_BINS).index_select(0, idx).reshape(-1).contiguous()
-        fr = fit_batch(ysub, idx.numel(), heuristic_start(ysub, idx.numel()), n_steps, tol, precision=precision)
+        thh = heuristic_start(ysub, idx.numel())
+        if refine:
+            thh = refine_start(ysub, idx.numel(), thh)
+        fr = fit_batch(ysub, idx.numel(), thh, n_steps, tol, precision=precision)
         rs = fr.states
         better = rs.f < f[idx]
         pick = idx[better]

@@ -288,6 +288,81 @@ def test_training_reduces_loss(dev):
     assert curve[-1][1] < 0.6 * curve[0][1], curve[:3] + curve[-3:]
 
 
+def _ref_refine(y, lo, hi, K, th, sweeps, half):
+    """The start refinement restated plainly (see cg.h, cg_refine_start)."""
+    import math
+    n = len(y)
+    h = (hi - lo) / n
+    A = [th[3 * k] for k in range(K)]
+    mu = [th[3 * k + 1] for k in range(K)]
+    s = [abs(th[3 * k + 2]) for k in range(K)]
+    b0, b1 = th[3 * K], th[3 * K + 1]
+
+    def sort():
+        order = sorted(range(K), key=lambda k: mu[k])
+        return [A[k] for k in order], [mu[k] for k in order], [s[k] for k in order]
+    A, mu, s = sort()
+    for _ in range(sweeps):
+        for k in range(K):
+            w = half * max(s[k], 4.0 * h)
+            if not (math.isfinite(mu[k]) and math.isfinite(w) and w > 0.0):
+                continue
+            a0 = math.floor(((mu[k] - w) - lo) / h)
+            a1 = math.ceil(((mu[k] + w) - lo) / h)
+            i0 = 0 if a0 < 0 else (n if a0 > n - 1 else int(a0))
+            i1 = n - 1 if a1 > n - 1 else (-1 if a1 < 0 else int(a1))
+            S0 = S1 = S2 = 0.0
+            for i in range(i0, i1 + 1):
+                x = lo + (i + 0.5) * h
+                dx = x - mu[k]
+                if not abs(dx) <= w:
+                    continue
+                r = y[i] - (b0 + b1 * x)
+                for j in range(K):
+                    if j != k:
+                        z = (x - mu[j]) / s[j]
+                        r = r - A[j] * math.exp(-0.5 * (z * z))
+                if not r > 0.0:
+                    continue
+                S0 += r
+                S1 += r * dx
+                S2 += (r * dx) * dx
+            if not S0 > 0.0:
+                continue
+            m1 = S1 / S0
+            var = max(S2 / S0 - m1 * m1, (0.5 * h) * (0.5 * h))
+            z = min(max(w / math.sqrt(var), 0.5), 10.0)
+            phi = 0.3989422804014327 * math.exp(-0.5 * (z * z))
+            frac = 1.0 - (2.0 * z * phi) / math.erf(z * 0.7071067811865476)
+            s2 = math.sqrt(var / frac)
+            cover = math.erf((w / s2) * 0.7071067811865476)
+            A[k] = (S0 * h) / ((s2 * 2.5066282746310002) * cover)
+            mu[k] = mu[k] + m1
+            s[k] = s2
+        A, mu, s = sort()
+    out = []
+    for k in range(K):
+        out += [A[k], mu[k], s[k]]
+    return np.array(out + [b0, b1])
+
+
+def test_refine_start_matches_its_definition(dev):
+    """cg_refine_start on the heuristic starts of 12 histograms against the
+    plain restatement above (sums in another order, exp and erf from
+    another library: agreement to 1e-9)."""
+    d = synth.c5_batch_device(12, chunk=93, device=dev)
+    th = ls.heuristic_start(d["y"], 12)
+    out = ls.refine_start(d["y"], 12, th)
+    torch.cuda.synchronize()
+    y = d["y"].view(12, ls.N_BINS).cpu().numpy()
+    th, out = th.cpu().numpy(), out.cpu().numpy()
+    for h in range(12):
+        ref = _ref_refine(y[h], 0.0, 1.0, 3, th[h], ls.REFINE_SWEEPS, ls.REFINE_HALF_WIDTH)
+        np.testing.assert_allclose(out[h], ref, rtol=1e-9, atol=1e-12)
+    # the start moves: peaks centred and sized on the full-resolution counts
+    assert np.any(np.abs(out[:, 1:9:3] - th[:, 1:9:3]) > 1e-6)
+
+
 def test_training_checkpoint_resume_is_bitwise(dev, tmp_path):
     """A training run checkpointed part-way (weights, Adam moments, step,
     target normalisation, epoch position, shuffling generator) and resumed
@@ -317,22 +392,26 @@ def test_training_checkpoint_resume_is_bitwise(dev, tmp_path):
 
 @pytest.mark.slow
 def test_learned_start_gains_over_the_heuristic(dev):
-    """Trained on 262,144 method-generated fits, the production path (network
-    start, refit from the heuristic start where the fit did not converge,
-    lower minimum kept) ends held-out fits at no higher NLL than the
-    heuristic-start fits in nearly every histogram, converges at least as
-    many, and the network's starts need fewer iterations on average."""
+    """What the trained network adds to the method (trained here on 262,144
+    method-generated fits, judged on 4096 held-out histograms): the
+    production path (network start refined on the full-resolution
+    histogram, refit from the refined heuristic start where that fit did not
+    converge, lower minimum kept) reaches the minimum of the fit started at
+    the generating truth in more histograms than the refined heuristic start
+    alone, converges at least as many, and ends lower more often than
+    higher."""
     x, scale, theta = ls.make_training_set(262144)
     net = ls.MLP(seed=0)
     ls.train(net, x, scale, theta, epochs=6, lr=2e-3)
     H = 4096
-    y = synth.c5_batch_device(H, ls.N_BINS, chunk=0, device=dev)["y"]
-    fh = ls.fit_batch(y, H, ls.heuristic_start(y, H), 50, 1e-9)
+    d = synth.c5_batch_device(H, ls.N_BINS, chunk=0, device=dev)
+    y = d["y"]
+    Ft = ls.fit_batch(y, H, torch.tensor(d["truth"], device=dev), 50, 1e-9).states.f.cpu().numpy()
+    fh = ls.fit_batch(y, H, ls.refine_start(y, H, ls.heuristic_start(y, H)), 50, 1e-9)
     pr = ls.production_fit(net, y, H, 50, 1e-9)
     Fh, Fp = fh.states.f.cpu().numpy(), pr["f"].cpu().numpy()
-    conv_h = int((fh.states.status == cg.FIT_CONVERGED).sum())
-    conv_p = int((pr["status"] == cg.FIT_CONVERGED).sum())
-    assert conv_p >= conv_h
-    assert np.mean(Fp <= Fh * (1 + 1e-6)) > 0.95
-    il = pr["learned"].states.iters.double().mean().item()
-    assert il < fh.states.iters.double().mean().item()
+    at_truth = lambda F: float(np.mean(np.abs(F - Ft) <= 1e-6 * np.abs(Ft)))
+    assert at_truth(Fp) > at_truth(Fh) + 0.03, (at_truth(Fp), at_truth(Fh))
+    assert int((pr["status"] == cg.FIT_CONVERGED).sum()) >= int((fh.states.status == cg.FIT_CONVERGED).sum())
+    lower, higher = int((Fp < Fh * (1 - 1e-6)).sum()), int((Fp > Fh * (1 + 1e-6)).sum())
+    assert lower > 2 * higher, (lower, higher)
