@@ -74,13 +74,15 @@ struct Fp64Tab {
     double2 logf[kLogN];
 };
 
-// Copy the tables into shared memory; every thread of the block calls it,
-// the caller synchronises.
+// Copy the tables into shared memory (the log table only with LOG); every
+// thread of the block calls it, the caller synchronises.
+template <bool LOG = true>
 __device__ __forceinline__ void fp64_tab_load(Fp64Tab& s) {
     const double2* src = reinterpret_cast<const double2*>(g_exp2_tab);
     double2* dst = reinterpret_cast<double2*>(s.exp2);
     for (int i = threadIdx.x; i < kExp2N / 2; i += blockDim.x) dst[i] = src[i];
-    for (int i = threadIdx.x; i < kLogN; i += blockDim.x) s.logf[i] = make_double2(g_log_tab[i], g_invf_tab[i]);
+    if (LOG)
+        for (int i = threadIdx.x; i < kLogN; i += blockDim.x) s.logf[i] = make_double2(g_log_tab[i], g_invf_tab[i]);
 }
 
 // 2^y for |y| < 1022 (no range check): the result is normal.

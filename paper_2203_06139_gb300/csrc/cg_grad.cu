@@ -49,19 +49,6 @@ int device_sm_count() {
 // Tile accumulation kernels
 // ---------------------------------------------------------------------------
 
-// Write the partial sums of the np points of one tile: part[(th * (NACC + 1)
-// + a) * nbx + c] for th = th0 .. th0 + np - 1; entry NACC is the point's
-// domain flag (bit pt of badm).
-template <int NACC, int NT>
-__device__ __forceinline__ void write_partials(double* __restrict__ part, const TileGrid& tg, int th0, int np, int c,
-                                               const double* tot, int badm) {
-    for (int k = threadIdx.x; k < np * (NACC + 1); k += NT) {
-        const int pt = k / (NACC + 1), a = k - pt * (NACC + 1);
-        part[((size_t)(th0 + pt) * (NACC + 1) + a) * tg.nbx + c] =
-            (a < NACC) ? tot[pt * NACC + a] : (((badm >> pt) & 1) ? 1.0 : 0.0);
-    }
-}
-
 // 1-D Gaussian peaks + polynomial, FP64.  A tile is (PT consecutive
 // parameter points, one chunk of bins); every bin's point-independent part
 // is taken once and reused for the PT points.  In a ragged last group the
@@ -79,7 +66,7 @@ __global__ void __launch_bounds__(NT) k_gp1_fp64(GP1Data d, const double* __rest
     __shared__ double tot[N * PT];
     if (gated_off(tg)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
-    fp64_tab_load(tab);
+    fp64_tab_load<OBJ != CG_OBJ_CHI2>(tab);
     const int P = 3 * K + d.D + 1;
     for (int t = blockIdx.x; t < tg.n_tiles; t += gridDim.x) {
         const int c = t / tg.n_theta, grp = t - c * tg.n_theta;   // chunk-major: a chunk stays in L2 across points
@@ -136,15 +123,18 @@ __global__ void __launch_bounds__(NT) k_gp1_fp64(GP1Data d, const double* __rest
         });
         int bm = 0;
 #pragma unroll
-        for (int p = 0; p < PT; ++p) {
-            gp1_tile_scale<K, OBJ>(acc[p]);
+        for (int p = 0; p < PT; ++p)
             if (bad[p] || nonfinite(acc[p][0])) bm |= 1 << p;
-        }
         if (bm) atomicOr(&s_badm, bm);
         __syncthreads();
         const int badm = s_badm;
         block_sum_rs<N * PT, NT>(reinterpret_cast<const double(&)[N * PT]>(acc), red, tot);
-        write_partials<N, NT>(part, tg, th0, np, c, tot, badm);
+        // the objective's constant factors once per tile, on the block's sums
+        for (int k = threadIdx.x; k < np * (N + 1); k += NT) {
+            const int pt = k / (N + 1), a = k - pt * (N + 1);
+            part[((size_t)(th0 + pt) * (N + 1) + a) * tg.nbx + c] =
+                (a < N) ? tot[pt * N + a] * gp1_acc_factor<OBJ>(a) : (((badm >> pt) & 1) ? 1.0 : 0.0);
+        }
     }
 }
 
@@ -392,7 +382,10 @@ static cg_status launch_gp1_k(const cg_problem* pb, const GP1Data& d, const doub
                               double* part, WsHeader* hdr, TileGrid* tg, cudaStream_t st, const int* gate) {
     constexpr int NT = 128;   // 157 registers at 4 points per tile: three CTAs per SM
     const int64_t n = pb->n_bins[0];
-    constexpr int PTM = (K <= 1) ? 4 : 1;
+#ifndef CG_GP1_POINTS_PER_TILE
+#define CG_GP1_POINTS_PER_TILE 4
+#endif
+    constexpr int PTM = (K <= 1) ? CG_GP1_POINTS_PER_TILE : 1;
     const bool multi = PTM > 1 && n_theta >= PTM;
 #define CG_GP1_LAUNCH(OO)                                                                                        \
     return multi ? launch_tiles_balanced(k_gp1_fp64<K, OO, PTM, NT>, NT, PTM, d, theta, n, n_theta, part, hdr, tg, \

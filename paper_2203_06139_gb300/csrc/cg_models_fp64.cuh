@@ -39,7 +39,7 @@ __device__ __forceinline__ void gp1_c2(const GP1Consts& cs, int K, GP1C2& c) {
 // Point-independent part of one bin.
 struct GP1Bin {
     double x, u, y;
-    double ny;    // -y (Poisson / Baker-Cousins); chi2: -2 / max(y, 1)
+    double ny;    // -y (Poisson / Baker-Cousins); chi2: the weight 1 / max(y, 1)
     double ymy;   // Baker-Cousins: y log y - y (0 for y = 0)
     bool ypos;    // y > 0 (Poisson / Baker-Cousins)
 };
@@ -59,7 +59,7 @@ __device__ __forceinline__ GP1Bin gp1_bin(double x, double y, const GP1Data& d, 
     b.ypos = __double_as_longlong(y) > 0;   // exact test of y > 0 (a NaN count reads as positive: its term is NaN)
     b.ymy = 0.0;
     if (OBJ == CG_OBJ_CHI2) {
-        b.ny = -2.0 * frcp_any(max_y_1(y));
+        b.ny = frcp_any(max_y_1(y));
     } else {
         b.ny = -y;
         if (OBJ == CG_OBJ_POISSON_BC && b.ypos) b.ymy = fma(y, flog(y, tab), -y);
@@ -68,10 +68,10 @@ __device__ __forceinline__ GP1Bin gp1_bin(double x, double y, const GP1Data& d, 
 }
 
 // One bin at one point.  Accumulators as gp1_elem_fp64 (value, per peak
-// g e, g e d, g e d^2, then g u^j), except the scale: chi2 accumulates
-// -2 T in acc[0] and the true adjoint g = -2 w r elsewhere (gp1_tile_scale
-// multiplies acc[0] by -1/2); Poisson accumulates T and g; Baker-Cousins
-// accumulates T/2 and g/2 (gp1_tile_scale doubles everything).  D: the
+// g e, g e d, g e d^2, then g u^j), except the scale: chi2 accumulates T in
+// acc[0] and w r = -g/2 elsewhere (gp1_tile_scale multiplies those by -2);
+// Poisson accumulates T and g; Baker-Cousins accumulates T/2 and g/2
+// (gp1_tile_scale doubles everything).  D: the
 // polynomial's degree (-1: none), fixed at compile time: with a run-time
 // degree the compiler evaluates every Horner step and adjoint term of the
 // largest degree and selects, several FP64 instructions per bin in vain.
@@ -94,8 +94,8 @@ __device__ __forceinline__ void gp1_elem_f64(const GP1Bin& b, const GP1Consts& c
     double g;
     if (OBJ == CG_OBJ_CHI2) {
         const double r = b.y - f;
-        g = b.ny * r;                     // -2 w r
-        acc[0] = fma(g, r, acc[0]);       // -2 w r^2
+        g = b.ny * r;                     // w r = -g/2
+        acc[0] = fma(g, r, acc[0]);       // w r^2
     } else {
         double L, rf;
         if (fp64_fast_range(f)) {
@@ -149,11 +149,19 @@ __device__ __forceinline__ void gp1_dispatch(int d, int pm, F&& f) {
 #undef CG_GP1_D
 }
 
+// The objective's constant factor of accumulator a (see gp1_elem_f64): a
+// power of two, so applying it to a sum is exact.
+template <int OBJ>
+__device__ __forceinline__ double gp1_acc_factor(int a) {
+    return OBJ == CG_OBJ_CHI2 ? (a == 0 ? 1.0 : -2.0) : (OBJ == CG_OBJ_POISSON_BC ? 2.0 : 1.0);
+}
+
 // The objective's constant factors on one thread's sums (see gp1_elem_f64).
 template <int K, int OBJ>
 __device__ __forceinline__ void gp1_tile_scale(double (&acc)[GP1Acc<K>::N]) {
     if (OBJ == CG_OBJ_CHI2) {
-        acc[0] *= -0.5;
+#pragma unroll
+        for (int a = 1; a < GP1Acc<K>::N; ++a) acc[a] *= -2.0;
     } else if (OBJ == CG_OBJ_POISSON_BC) {
 #pragma unroll
         for (int a = 0; a < GP1Acc<K>::N; ++a) acc[a] *= 2.0;
