@@ -26,7 +26,7 @@ parity at sampled points.
 torchrun each rank evaluates its own 50 parameter points on its own copy of
 the events (weak scaling; no collective on the data path) and the configs
 are not run.  Other workloads: --workload c1|c3|c4|c5 (one config alone),
-c5fit, fig3b, gemm, expr.
+c4fit, c5fit (the batched fits alone), fig3b, gemm, expr.
 """
 import argparse
 import ctypes
@@ -250,7 +250,15 @@ def sources_hash(files):
 # capture's workload named).  The commands are in profiles/.
 FP64_SOURCES = ["csrc/cg_grad.cu", "csrc/cg_fp64.cuh", "csrc/cg_fp64_tables.inc", "csrc/cg_models_fp64.cuh",
                 "csrc/cg_models.cuh", "csrc/cg_tiles.cuh", "csrc/cg_internal.cuh"]
-NCU_RECORDS = {}
+NCU_RECORDS = {
+    "k_mix_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "6506c10f2d049b90", "workload": [N_EVENTS, N_POINTS],
+                   "dram_bytes": 80288256 + 3860480, "fp64_pipe_pct": 86.85,
+                   "profile": "profiles/k_mix_fp64_unbinned_1e7x50.md"},
+    "k_gp1_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "6506c10f2d049b90", "dram_bytes": 218112, "fp64_pipe_pct": 75.48,
+                   "profile": "profiles/k_gp1_fp64_c1_10000bins_100points.md"},
+    "k_rg2_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "6506c10f2d049b90", "dram_bytes": 134412032 + 4738048,
+                   "fp64_pipe_pct": 83.98, "profile": "profiles/k_rg2_fp64_c3_4096x4096.md"},
+}
 
 
 def ncu_record(kernel, n_events=None, n_points=None):
@@ -695,6 +703,9 @@ def config_c3(args, rates, sm_max_mhz):
                          "instructions per bin" % (pairs / n, pairs, FP64_INSTR["rg2_bin"], FP64_INSTR["rg2_gauss"],
                                                    pairs / n))
     roof["algorithmic_bytes"] = n * 8
+    rec = ncu_record("k_rg2_fp64")
+    roof["traffic"] = rec["dram_bytes"] if rec else None
+    roof["ncu_fp64_pipe_pct"] = rec["fp64_pipe_pct"] if rec else None
     # parity and the CPU oracle on the whole histogram: the objective, its
     # gradient and the per-component scales S_k are sums over bins, so the
     # oracle runs on bands of 16 rows (each a sub-problem with the same bin
@@ -1226,6 +1237,35 @@ def run_c5fit(args):
             "mean_evals": float(ev.mean()), "max_evals": int(ev.max())}
     print(json.dumps(line), flush=True)
 
+def run_c4fit(args):
+    """The batched FP64 fits of the 4096 uneven histograms alone (init + 50
+    BFGS iterations, eager, one fixed tile map: warps up to 2048 bins, one
+    256-thread CTA above), `--steps` timed repetitions: the launch the
+    fitter's profile captures."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2203_06139_gb300 import cg, synth
+    from paper_2203_06139_gb300.fit import BatchFitter, HistBatch, TileMap
+    d = synth.c4_batch()
+    b = HistBatch(d["y"], d["offsets"], d["lo"], d["hi"], 1, 2, cg.OBJ_CHI2, poly_mode=1, precision=cg.PREC_FP64)
+    f = BatchFitter(b, TileMap(2048, 1 << 30, 256, 1))
+    th0 = torch.tensor(d["start"], device="cuda")
+
+    def fit():
+        f.init(th0)
+        f.step(50, 1e-9)
+    ms = _timed(fit, max(args.steps, 1), 2)
+    ev = float((f.states.n_eval.cpu().numpy().astype(np.float64) * np.diff(d["offsets"])).sum())
+    line = {"metric": "bin-evaluations/s of the batched fit", "workload": "c4fit", "value": ev / (ms * 1e-3),
+            "unit": "bin-evaluations/s", "higher_is_better": True, "ms_per_step": ms, "dtype": "f64",
+            "config": {"workload": "4096 histograms, 64-65536 bins, Gaussian + quadratic, chi2, init + 50 BFGS "
+                                   "iterations, FP64, map warp <= 2048 bins / CTA of 256 threads"},
+            "converged": int((f.states.status == cg.FIT_CONVERGED).sum())}
+    print(json.dumps(line), flush=True)
+
+
 def run_expr(args):
     """Expression programs (source-transformation AD, NVRTC-compiled): the c1
     and c2 objectives written as expressions, timed next to the hand-written
@@ -1373,7 +1413,7 @@ def main():
     ap.add_argument("--events", type=int, default=N_EVENTS)
     ap.add_argument("--points", type=int, default=N_POINTS)
     ap.add_argument("--workload", default="c2",
-                    choices=["c2", "c1", "c3", "c4", "c5", "c5fit", "fig3b", "gemm", "expr"])
+                    choices=["c2", "c1", "c3", "c4", "c5", "c4fit", "c5fit", "fig3b", "gemm", "expr"])
     ap.add_argument("--configs", default="c1,c3,c4,c5",
                     help="configs measured beside the headline (comma list, or none)")
     ap.add_argument("--plain-per-stratum", type=int, default=24,
@@ -1390,6 +1430,8 @@ def main():
         run_one_config(args)
     elif args.workload == "gemm":
         run_gemm(args)
+    elif args.workload == "c4fit":
+        run_c4fit(args)
     elif args.workload == "c5fit":
         run_c5fit(args)
     elif args.workload == "expr":
