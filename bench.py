@@ -866,10 +866,13 @@ def config_c4(args, rates, sm_max_mhz):
     Fb = f64["F"][idx]
     Fpv = np.array([Fp[h] for h in idx])
     same = np.abs(Fb - Fpv) <= 1e-6 * np.abs(Fpv)
-    # oracle fits of a few sampled histograms (<= 8192 bins: seconds each on one core)
-    small = [int(i) for _, ii in strata for i in ii if sizes[int(i)] <= 8192][::6][:6]
+    # oracle fits of sampled histograms (all strata, smallest first within a
+    # stratum), one core, until about 5 s of CPU time
+    small = [int(i) for _, ii in strata for i in ii][::3]
     t_cpu, orc = 0.0, []
     for h in small:
+        if t_cpu > 5.0:
+            break
         o0, o1 = int(d["offsets"][h]), int(d["offsets"][h + 1])
         yh = d["y"][o0:o1]
         fg = lambda t, yh=yh: (lambda q: (q.value, q.grad))(oracle.binned1d(1, 2, 1, oracle.CHI2, yh, 0.0, 1.0, t))
@@ -905,8 +908,8 @@ def config_c4(args, rates, sm_max_mhz):
         "lower_F_when_different": {"batched": int(((Fb < Fpv) & ~same).sum()),
                                    "plain": int(((Fpv < Fb) & ~same).sum())},
         "roofline": roof,
-        "parity": {"what": "oracle BFGS fits of %d sampled histograms (<= 8192 bins): batched FP64 minimum within "
-                           "1e-6 of the oracle's where both converged" % len(orc),
+        "parity": {"what": "oracle BFGS fits of %d sampled histograms: batched FP64 minimum within 1e-6 of the "
+                           "oracle's where both converged" % len(orc),
                    "checked": len(par_same), "same_minimum": int(sum(par_same)),
                    "ok": bool(len(par_same) > 0 and all(par_same))},
         "variants": {"df64": {"dtype": "df64", "ms": res["df64"]["ms"], "map": res["df64"]["map"],
@@ -915,7 +918,7 @@ def config_c4(args, rates, sm_max_mhz):
                               "same_minimum_as_fp64_frac": float(np.mean(
                                   np.abs(res["df64"]["F"] - f64["F"]) <= 1e-6 * np.abs(f64["F"])))}},
         "cpu_baseline": {"value": cpu_rate, "unit": "bin-evaluations/s", "cores": 1, "kind": "oracle",
-                         "sample": "oracle BFGS fits of %d sampled histograms of <= 8192 bins (%.1f s)"
+                         "sample": "oracle BFGS fits of %d histograms sampled across the size strata (%.1f s)"
                                    % (len(orc), t_cpu),
                          "seconds_for_batch_at_this_rate": f64["bin_evals"] / cpu_rate},
     }
@@ -1019,10 +1022,14 @@ def config_c5(args, rates, sm_max_mhz):
         return cg.Problem.gauss_poly(yh_all[h].contiguous(), 0.0, 1.0, 3, 1, cg.OBJ_POISSON_BC)
     plain_h, Fph, sph, _ = _plain_fits(problem, th_heu, [(np.arange(H), samp)], 50)
     plain_l, Fpl, spl, _ = _plain_fits(problem, th_net, [(np.arange(H), samp)], 50)
-    # oracle fits of a few histograms from the production path's start points
-    t_cpu, checked, same_o = 0.0, 0, 0
-    y_np = yh_all[samp[:4]].cpu().numpy()
-    for j, h in enumerate(samp[:4]):
+    # oracle fits of sampled histograms from the production path's start
+    # points, one core, until about 5 s of CPU time
+    t_cpu, checked, same_o, n_orc = 0.0, 0, 0, 0
+    y_np = yh_all[samp[:32]].cpu().numpy()
+    for j, h in enumerate(samp[:32]):
+        if t_cpu > 5.0:
+            break
+        n_orc += 1
         yh = y_np[j]
         fg = lambda t, yh=yh: (lambda q: (q.value, q.grad))(oracle.binned1d(3, 1, 0, oracle.POISSON_BC, yh, 0.0, 1.0, t))
         gn = lambda t, yh=yh: oracle.binned1d_gn(3, 1, 0, oracle.POISSON_BC, yh, 0.0, 1.0, t)
@@ -1053,15 +1060,16 @@ def config_c5(args, rates, sm_max_mhz):
                            [spl[int(h)] == cg.FIT_CONVERGED for h in samp])))},
         "speedup_vs_plain_heuristic": plain_h["seconds_for_all"] / (f64["production"]["ms"] / 1e3),
         "roofline": roof,
-        "parity": {"what": "oracle BFGS fits of 4 sampled histograms from the network's start: production minimum "
-                           "at or below the oracle's (1e-6 relative) where the oracle converged",
+        "parity": {"what": "oracle BFGS fits of %d sampled histograms from the network's start: production minimum "
+                           "at or below the oracle's (1e-6 relative) where the oracle converged" % n_orc,
                    "checked": checked, "ok_count": same_o, "ok": bool(checked > 0 and same_o == checked)},
         "variants": {"df64": strip(res["df64"])},
         "training": {"histograms": n_train, "seconds_data": t_data, "seconds_train": t_train, "steps": net.step,
                      "loss_first": curve[0][1] if curve else None, "loss_last": curve[-1][1] if curve else None,
                      "targets": "converged double-float batched fits started at the truth"},
-        "cpu_baseline": {"value": 4 / t_cpu, "unit": "fits/s", "cores": 1, "kind": "oracle",
-                         "sample": "oracle BFGS fits of 4 histograms from the network's start (%.1f s)" % t_cpu},
+        "cpu_baseline": {"value": n_orc / t_cpu, "unit": "fits/s", "cores": 1, "kind": "oracle",
+                         "sample": "oracle BFGS fits of %d histograms from the network's start (%.1f s)" % (n_orc, t_cpu),
+                         "seconds_for_all_at_this_rate": H * t_cpu / n_orc},
     }
 
 
