@@ -7,7 +7,7 @@
 Each value is stored as a pair of floats (hi, lo): hi = value rounded to
 float, lo = (value - hi) rounded to float, from 60-digit mpmath values, so the
 pair carries the value to about 2^-48 relative.  Run from anywhere:
-``python gen_df64_tables.py`` (rewrites the file next to this script); the
+``python gen_df64_tables.py`` (rewrites csrc/cg_df64_tables.inc beside this script); the
 CPU test suite checks the committed file against this script's output.
 """
 import os
@@ -16,7 +16,7 @@ import mpmath
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-OUT = os.path.join(HERE, "cg_df64_tables.inc")
+OUT = os.path.join(HERE, "csrc", "cg_df64_tables.inc")
 
 
 def _pair(v):

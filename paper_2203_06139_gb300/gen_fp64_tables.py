@@ -8,7 +8,7 @@
 Each entry is the double nearest to the exact value, from 60-digit mpmath
 values (mpmath's conversion to float rounds to nearest); F_t itself is exact
 in binary and is formed in the kernel from the argument's bits.  Run from anywhere:
-``python gen_fp64_tables.py`` (rewrites the file next to this script); the
+``python gen_fp64_tables.py`` (rewrites csrc/cg_fp64_tables.inc beside this script); the
 CPU test suite checks the committed file against this script's output.
 """
 import os
@@ -16,7 +16,7 @@ import os
 import mpmath
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-OUT = os.path.join(HERE, "cg_fp64_tables.inc")
+OUT = os.path.join(HERE, "csrc", "cg_fp64_tables.inc")
 BITS = 12
 N = 1 << BITS
 NL = 130

@@ -70,7 +70,7 @@ def test_df64_tables_match_their_generator():
     the generator writes (exactly rounded float pairs from 60-digit values)."""
     pytest.importorskip("mpmath")
     import importlib.util
-    path = os.path.join(ROOT, "paper_2203_06139_gb300", "csrc", "gen_df64_tables.py")
+    path = os.path.join(ROOT, "paper_2203_06139_gb300", "gen_df64_tables.py")
     spec = importlib.util.spec_from_file_location("gen_df64_tables", path)
     gen = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(gen)
@@ -93,7 +93,7 @@ def test_fp64_tables_match_their_generator():
     pytest.importorskip("mpmath")
     import importlib.util
     import math
-    path = os.path.join(ROOT, "paper_2203_06139_gb300", "csrc", "gen_fp64_tables.py")
+    path = os.path.join(ROOT, "paper_2203_06139_gb300", "gen_fp64_tables.py")
     spec = importlib.util.spec_from_file_location("gen_fp64_tables", path)
     gen = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(gen)
