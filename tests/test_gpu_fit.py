@@ -72,11 +72,16 @@ def test_batched_fit_reaches_oracle_minimum(dev, tmap):
     torch.cuda.synchronize()
     F = st.f.cpu().numpy()
     status = st.status.cpu().numpy()
-    assert np.all(status == cg.FIT_CONVERGED) or np.all(np.isin(status, [cg.FIT_CONVERGED, cg.FIT_LINESEARCH_FAILED]))
+    # at tol 1e-12 a fit may also end when the line search can no longer improve F
+    assert np.all(np.isin(status, [cg.FIT_CONVERGED, cg.FIT_LINESEARCH_FAILED]))
+    conv_gpu = conv_orc = 0
     for h in range(0, d["H"], 3):
         y = d["y"][d["offsets"][h]:d["offsets"][h + 1]]
         ref = oracle_fit(y, 1, 2, 1, oracle.CHI2, 0.0, 1.0, d["start"][h])
         assert abs(F[h] - ref["F"]) <= 1e-6 * abs(ref["F"]), (h, F[h], ref["F"], status[h])
+        conv_gpu += int(status[h] == cg.FIT_CONVERGED)
+        conv_orc += int(ref["status"] == 1)
+    assert conv_gpu >= conv_orc - 1, (conv_gpu, conv_orc)   # converges as often as the oracle
 
 
 def test_mappings_agree(dev):
@@ -312,20 +317,29 @@ def test_c4_full_size_sampled_fits(dev):
     Fb, sb = f.states.f.cpu().numpy(), f.states.status.cpu().numpy()
     Fl, sl = lm.states.f.cpu().numpy(), lm.states.status.cpu().numpy()
     checked = 0
+    conv = {"bfgs": [0, 0], "lm": [0, 0]}   # [GPU, oracle] converged counts over the sample
     for h in _sizes_sample(n):
         y = d["y"][d["offsets"][h]:d["offsets"][h + 1]]
         fg = lambda t: (lambda q: (q.value, q.grad))(oracle.binned1d(1, 2, 1, oracle.CHI2, y, 0.0, 1.0, t))
         gn = lambda t: oracle.binned1d_gn(1, 2, 1, oracle.CHI2, y, 0.0, 1.0, t)
         ref = bfgs_fit(fg, gn, d["start"][h], max_iter=50, tol=1e-9)
+        conv["bfgs"][0] += int(sb[h] == cg.FIT_CONVERGED)
+        conv["bfgs"][1] += int(ref["status"] == 1)
         if ref["status"] == 1 and sb[h] == cg.FIT_CONVERGED:
             assert abs(Fb[h] - ref["F"]) <= 1e-6 * abs(ref["F"]), (h, int(n[h]), Fb[h], ref["F"])
             checked += 1
         fgh = lambda t: fg(t) + (oracle.binned1d_gnmat(1, 2, 1, oracle.CHI2, y, 0.0, 1.0, t),)
         rl = lm_fit(fgh, d["start"][h], max_evals=31, tol=1e-9)
+        conv["lm"][0] += int(sl[h] == cg.FIT_CONVERGED)
+        conv["lm"][1] += int(rl["status"] == 1)
         if rl["status"] == 1 and sl[h] == cg.FIT_CONVERGED:
             assert abs(Fl[h] - rl["F"]) <= 1e-6 * abs(rl["F"]), (h, int(n[h]), Fl[h], rl["F"])
             checked += 1
     assert checked >= 8
+    # the GPU fits converge as often as the oracle's from the same starts (one
+    # borderline convergence decision at the iteration limit allowed)
+    for k, (g, o) in conv.items():
+        assert g >= o - 1, (k, g, o)
 
 
 @pytest.mark.slow
@@ -342,13 +356,16 @@ def test_c5_full_size_sampled_fits(dev):
     torch.cuda.synchronize()
     F, st = f.states.f.cpu().numpy(), f.states.status.cpu().numpy()
     th_h = th.cpu().numpy()
-    checked = 0
-    for h in (0, 9999, 22222, 33333, 44444, 65535):
+    checked = conv_gpu = conv_orc = 0
+    for h in (0, 9999, 22222, 33333, 44444, 65535, 12345, 54321):
         yy = y[h * ls.N_BINS:(h + 1) * ls.N_BINS].cpu().numpy()
         fg = lambda t: (lambda q: (q.value, q.grad))(oracle.binned1d(3, 1, 0, oracle.POISSON_BC, yy, 0.0, 1.0, t))
         gn = lambda t: oracle.binned1d_gn(3, 1, 0, oracle.POISSON_BC, yy, 0.0, 1.0, t)
         ref = bfgs_fit(fg, gn, th_h[h], max_iter=50, tol=1e-9)
+        conv_gpu += int(st[h] == cg.FIT_CONVERGED)
+        conv_orc += int(ref["status"] == 1)
         if ref["status"] == 1 and st[h] == cg.FIT_CONVERGED:
             assert abs(F[h] - ref["F"]) <= 1e-6 * abs(ref["F"]), (h, F[h], ref["F"])
             checked += 1
     assert checked >= 3
+    assert conv_gpu >= conv_orc - 1, (conv_gpu, conv_orc)   # converges as often as the oracle
