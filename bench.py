@@ -168,9 +168,10 @@ def measured_peaks():
 #  - exp2: 3 for the reduction (two additions of 1.5 * 2^40, one
 #    subtraction), 3 for the polynomial, 1 for T (1 + p) = 7;
 #  - reciprocal: 3 FMAs after the hardware estimate; log: 13;
-#  - event-point of the mixture: x - mu, c2 d, (c2 d) d, exp2, the
-#    exponential's exponent (one FMA), exp2, b eE, fma, reciprocal, running
-#    product, U, V, U d, five accumulations = 1+1+1+7+1+7+1+1+3+1+1+1+1+5 = 32;
+#  - event-point of the mixture (ratio form: p = b eE (1 + u), one exp2):
+#    d = x - mu, c2 d, the exponential's part of the exponent (one FMA), the
+#    exponent (one FMA), exp2, s = 1 + u, reciprocal, running product,
+#    r = u V, r d, five accumulations = 1+1+1+1+7+1+3+1+1+1+5 = 23;
 #  - bin-point of the 1-D chi2 of one Gaussian + line, four points per
 #    tile: Horner 1, d 1, exponent 2, exp2 7, peak 1, residual / adjoint /
 #    value 3, peak adjoints 5, polynomial adjoints 2 = 22, plus the bin's
@@ -185,7 +186,7 @@ def measured_peaks():
 #  - 2-D bin: centres 2 x 2, log 13, reciprocal 3, adjoint seed, value and
 #    constant 4 = 24; per (bin, Gaussian kept by the tile's culling):
 #    dx, dy 2, quadratic form 5, exp2 7, model 1, adjoints 3 + 6 = 24.
-FP64_INSTR = {"mix": 32, "gp1_c1": 23.25, "fit_c4": 30, "fit_c5": 87, "rg2_bin": 24, "rg2_gauss": 24}
+FP64_INSTR = {"mix": 23, "gp1_c1": 23.25, "fit_c4": 30, "fit_c5": 87, "rg2_bin": 24, "rg2_gauss": 24}
 
 # FP32-pipe operations per unit of the double-float kernels (cg_df64.cuh,
 # cg_df64.cu, cg_models_df64.cuh): event-point of the mixture: two df64

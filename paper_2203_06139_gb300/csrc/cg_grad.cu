@@ -138,15 +138,48 @@ __global__ void __launch_bounds__(NT) k_gp1_fp64(GP1Data d, const double* __rest
     }
 }
 
-// Unbinned Gaussian + exponential mixture, FP64: one point per tile.
+// The events [e0, e1) of one tile through one form of the mixture element
+// (RATIO: mix_elem_ratio, else mix_elem_f64); pairs of events per load when
+// the arrays are 16-byte aligned.
+template <bool W, int NT, bool RATIO>
+__device__ __forceinline__ void mix_events(const MixData& d, int64_t e0, int64_t e1, const MixConsts& cs,
+                                           const MixC2& cq, const MixR2& cr, const Fp64Tab& tab,
+                                           double (&acc)[MixAcc::N], LogProd& lp, bool& bad) {
+    auto elem = [&](double x, double w) {
+        if constexpr (RATIO) mix_elem_ratio<W>(x, w, cs, cr, tab, acc, lp, bad);
+        else mix_elem_f64<W>(x, w, cs, cq, tab, acc, lp, bad);
+    };
+    if (d.vec_ok) {
+        for (int64_t i = e0 + 2 * threadIdx.x; i < e1; i += 2 * NT) {
+            if (i + 1 < e1) {
+                const double2 x2 = __ldg(reinterpret_cast<const double2*>(d.x + i));
+                double2 w2 = make_double2(1.0, 1.0);
+                if (W) w2 = __ldg(reinterpret_cast<const double2*>(d.w + i));
+                elem(x2.x, w2.x);
+                elem(x2.y, w2.y);
+            } else {
+                elem(d.x[i], W ? d.w[i] : 1.0);
+            }
+        }
+    } else {
+        for (int64_t i = e0 + threadIdx.x; i < e1; i += NT) elem(d.x[i], W ? d.w[i] : 1.0);
+    }
+}
+
+// Unbinned Gaussian + exponential mixture, FP64: one point per tile.  A tile
+// whose point has both coefficients a, b > 0 (every point inside the
+// parameter space) takes the ratio form, one exponential per event; others
+// (a = 0 at f = 0, b <= 0 at f >= 1) take the two-exponential form.  The
+// choice is uniform over the tile and both give the same accumulators.
 template <bool W, int NT>
-__global__ void __launch_bounds__(NT) k_mix_fp64(MixData d, const double* __restrict__ theta,
+__global__ void __launch_bounds__(NT, 768 / NT) k_mix_fp64(MixData d, const double* __restrict__ theta,
                                                  TileGrid tg, double* __restrict__ part,
                                                  WsHeader* __restrict__ hdr) {
     constexpr int NACC = MixAcc::N;
     __shared__ Fp64Tab tab;
     __shared__ MixConsts cs;
     __shared__ MixC2 cq;
+    __shared__ MixR2 cr;
     __shared__ int cs_bad;
     __shared__ double red[NACC * (NT / 32)];
     __shared__ double tot[NACC];
@@ -158,8 +191,10 @@ __global__ void __launch_bounds__(NT) k_mix_fp64(MixData d, const double* __rest
         if (threadIdx.x == 0) {
             cs_bad = mix_prologue(theta + (size_t)th * 4, d.lo, d.hi, cs) ? 0 : 1;
             mix_c2(cs, cq);
+            mix_r2(cs, cr);
         }
         __syncthreads();
+        const bool ratio = cr.ok != 0;
         double acc[NACC];
 #pragma unroll
         for (int a = 0; a < NACC; ++a) acc[a] = 0.0;
@@ -168,25 +203,15 @@ __global__ void __launch_bounds__(NT) k_mix_fp64(MixData d, const double* __rest
         bool bad = false;
         const int64_t e0 = (int64_t)c * tg.chunk;
         const int64_t e1 = min(tg.n_elem, e0 + tg.chunk);
-        if (d.vec_ok) {
-            for (int64_t i = e0 + 2 * threadIdx.x; i < e1; i += 2 * NT) {
-                if (i + 1 < e1) {
-                    const double2 x2 = __ldg(reinterpret_cast<const double2*>(d.x + i));
-                    double2 w2 = make_double2(1.0, 1.0);
-                    if (W) w2 = __ldg(reinterpret_cast<const double2*>(d.w + i));
-                    mix_elem_f64<W>(x2.x, w2.x, cs, cq, tab, acc, lp, bad);
-                    mix_elem_f64<W>(x2.y, w2.y, cs, cq, tab, acc, lp, bad);
-                } else {
-                    mix_elem_f64<W>(d.x[i], W ? d.w[i] : 1.0, cs, cq, tab, acc, lp, bad);
-                }
-            }
-        } else {
-            for (int64_t i = e0 + threadIdx.x; i < e1; i += NT)
-                mix_elem_f64<W>(d.x[i], W ? d.w[i] : 1.0, cs, cq, tab, acc, lp, bad);
-        }
+        if (ratio) mix_events<W, NT, true>(d, e0, e1, cs, cq, cr, tab, acc, lp, bad);
+        else mix_events<W, NT, false>(d, e0, e1, cs, cq, cr, tab, acc, lp, bad);
         mix_tile_finish<W>(cs, tab, acc, lp);
         const int any_bad = __syncthreads_or(bad ? 1 : 0) | cs_bad;
         block_sum_rs<NACC, NT>(acc, red, tot);
+        if (ratio) {
+            if (threadIdx.x == 0) mix_ratio_sums(cs, cr, W ? tot[1] + tot[4] : (double)(e1 - e0), tot);
+            __syncthreads();
+        }
         write_partial<NACC>(part, tg, th, c, tot, any_bad);
     }
 }

@@ -224,6 +224,102 @@ __device__ __forceinline__ void mix_tile_finish(const MixConsts& cs, const Fp64T
     if (!W) acc[0] += logprod_log(lp, tab);
 }
 
+// ---------------------------------------------------------------------------
+// Ratio form of the same mixture, for a > 0 and b > 0: one exponential per
+// event instead of two.
+//   p = b eE (1 + u),  u = a eG / (b eE) = 2^t,
+//   t = c2 d^2 + lam log2(e) (x - lo) + log2(a / b).
+// With s = 1 + u, V = 1/s and r = u V (the Gaussian's share of p; the
+// exponential's is V = 1 - r):
+//   eG / p = r / a,  eE / p = V / b,  log p = log b - lam (x - lo) + log s.
+// A thread sums r (1, d, d^2), V (1, x) and the running product of s;
+// mix_ratio_sums turns a tile's block sums into the accumulators of
+// mix_elem_f64 (same meaning, same epilogue).  The sum of x - lo that the
+// value needs follows from r + V = 1 without an accumulator of its own:
+//   sum (x - lo) = sum V (x - lo) + sum r d + (mu - lo) sum r.
+// An event whose s leaves the fast range (u above 2^1021, or NaN) is taken
+// in the two-exponential form by mix_ratio_slow.
+// ---------------------------------------------------------------------------
+struct MixR2 {
+    double c2;    // -log2(e) / (2 s^2)
+    double ml2;   // lam log2(e)
+    double k0;    // log2(a / b) - lam log2(e) lo
+    double lb;    // log b
+    int ok;       // a > 0, b > 0, k0 and lb finite: the ratio form applies
+};
+
+__device__ inline void mix_r2(const MixConsts& cs, MixR2& c) {
+    c.c2 = cs.c * kLog2e;
+    c.ml2 = cs.lam * kLog2e;
+    const bool pos = cs.a > 0.0 && cs.b > 0.0;
+    c.k0 = pos ? fma(-c.ml2, cs.lo, log2(cs.a) - log2(cs.b)) : 0.0;
+    c.lb = pos ? log(cs.b) : 0.0;
+    c.ok = pos && isfinite(c.k0) && isfinite(c.lb) && isfinite(c.c2) && isfinite(c.ml2);
+}
+
+// One event in the two-exponential form, returning the ratio form's r, V
+// and log s (IEEE reciprocal and log; rare, out of line).
+static __device__ __noinline__ void mix_ratio_slow(double x, double d, const MixConsts& cs, const MixR2& c,
+                                                   const Fp64Tab& tab, double& r, double& V, double& ls,
+                                                   bool& bad) {
+    const double xl = x - cs.lo;
+    const double aG = cs.a * fexp2((c.c2 * d) * d, tab);
+    const double bE = cs.b * fexp2(-c.ml2 * xl, tab);
+    const double p = aG + bE;
+    bad |= !(p > 0.0);
+    const double ip = 1.0 / p;
+    r = aG * ip;
+    V = bE * ip;
+    ls = fma(cs.lam, xl, log(p) - c.lb);
+}
+
+template <bool W>
+__device__ __forceinline__ void mix_elem_ratio(double x, double w, const MixConsts& cs, const MixR2& c,
+                                               const Fp64Tab& tab, double (&acc)[MixAcc::N], LogProd& lp,
+                                               bool& bad) {
+    const double d = x - cs.mu;
+    const double u = fexp2(fma(c.c2 * d, d, fma(c.ml2, x, c.k0)), tab);
+    const double s = 1.0 + u;
+    double r, V;
+    if (fp64_fast_range(s)) {             // s in [1, 2^1021): every event but the most extreme
+        V = frcp(s);
+        if (W) {
+            acc[0] = fma(w, flog_fast(s, tab), acc[0]);
+            V *= w;
+        } else {
+            logprod_mul(lp, s);
+        }
+        r = u * V;
+    } else {
+        double ls;
+        mix_ratio_slow(x, d, cs, c, tab, r, V, ls, bad);
+        if (W) {
+            r *= w;
+            V *= w;
+        }
+        acc[0] += W ? w * ls : ls;
+    }
+    const double rd = r * d;
+    acc[1] += r;
+    acc[2] += rd;
+    acc[3] = fma(rd, d, acc[3]);
+    acc[4] += V;
+    acc[5] = fma(V, x, acc[5]);
+}
+
+// A tile's block sums of the ratio form (after mix_tile_finish: tot[5] is
+// sum V (x - lo)) into the accumulators of mix_elem_f64.  n_w: the tile's
+// event count, or its sum of weights.
+__device__ inline void mix_ratio_sums(const MixConsts& cs, const MixR2& c, double n_w, double* tot) {
+    const double sxl = tot[5] + fma(cs.mu - cs.lo, tot[1], tot[2]);   // sum w (x - lo)
+    tot[0] = fma(n_w, c.lb, fma(-cs.lam, sxl, tot[0]));
+    tot[1] /= cs.a;
+    tot[2] /= cs.a;
+    tot[3] /= cs.a;
+    tot[4] /= cs.b;
+    tot[5] /= cs.b;
+}
+
 // ===========================================================================
 // 2-D binned Poisson NLL of K rotated Gaussians + C.  The exponent is taken
 // as a quadratic form in (dx, dy) = (x - mu_x, y - mu_y):

@@ -179,6 +179,30 @@ def test_mixture_weighted_and_other_range(dev):
     check(v, g, oracle.unbinned_mix(x, 1.0, 7.5, th, weights=w))
 
 
+# Points that take each form of the FP64 mixture element: the ratio form
+# (a, b > 0), the two-exponential form (a = 0 at f = 0), a ratio form whose
+# Gaussian-to-exponential ratio exceeds 2^1021 for the events near a steep
+# exponential's far end (those take the per-event fallback), and a fraction
+# next to 1 (log2(a/b) near 23).
+MIX_FORM_POINTS = np.array([[0.3, 2.0, 0.3, 0.5],
+                            [0.0, 2.0, 0.3, 0.5],
+                            [0.3, 9.0, 0.5, 100.0],
+                            [0.9999999, 2.1, 0.28, 0.45],
+                            [0.999, 0.5, 0.05, 9.0]])
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_mixture_fp64_both_forms_in_one_launch(dev, weighted):
+    x = np.concatenate([synth.c2_events(40001), np.array([9.99, 9.999, 9.0, 0.0, 1e-12, 5.0])])
+    w = np.random.default_rng(11).uniform(0.2, 2.0, x.size) if weighted else None
+    wt = torch.tensor(w, device=dev) if weighted else None
+    pm = cg.Problem.mixture(torch.tensor(x, device=dev), 0.0, 10.0, weights=wt)
+    v, g = cg.batch_gradient(pm, torch.tensor(MIX_FORM_POINTS, device=dev))
+    assert pm.status(len(MIX_FORM_POINTS)) == cg.OK
+    for i, th in enumerate(MIX_FORM_POINTS):
+        check(v[i], g[i], oracle.unbinned_mix(x, 0.0, 10.0, th, weights=w))
+
+
 @pytest.mark.slow
 def test_c2_full_size_sampled_points(dev):
     """10^7 events x 50 points in the bench's launch; the oracle checks a sample of points."""
