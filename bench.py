@@ -181,12 +181,14 @@ def measured_peaks():
 #    (one point per bin): centre 2, weight 3, Horner 2, peak 11, chi2 3,
 #    peak adjoints 5, polynomial adjoints 4 = 30;
 #  - bin-evaluation of the Baker-Cousins fit of three Gaussians + line: bin
-#    work 2 + log of y 13 + 1, Horner 1, peaks 3 x 11, log 13, reciprocal
-#    3, value 3, adjoint 1, peak adjoints 15, polynomial adjoints 2 = 87;
+#    work 2, Horner 1, peaks 3 x 11, log 13, reciprocal 3, value 2, adjoint
+#    1, peak adjoints 15, polynomial adjoints 2 = 72 (the counts-only term
+#    y log y - y, a log and two more instructions per bin, is summed once
+#    per histogram at the fit's init, not at every evaluation);
 #  - 2-D bin: centres 2 x 2, log 13, reciprocal 3, adjoint seed, value and
 #    constant 4 = 24; per (bin, Gaussian kept by the tile's culling):
 #    dx, dy 2, quadratic form 5, exp2 7, model 1, adjoints 3 + 6 = 24.
-FP64_INSTR = {"mix": 23, "gp1_c1": 23.25, "fit_c4": 30, "fit_c5": 87, "rg2_bin": 24, "rg2_gauss": 24}
+FP64_INSTR = {"mix": 23, "gp1_c1": 23.25, "fit_c4": 30, "fit_c5": 72, "rg2_bin": 24, "rg2_gauss": 24}
 
 # FP32-pipe operations per unit of the double-float kernels (cg_df64.cuh,
 # cg_df64.cu, cg_models_df64.cuh): event-point of the mixture: two df64

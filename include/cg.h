@@ -332,6 +332,11 @@ typedef struct {
     double h0[CG_FIT_MAX_PARAMS];   /* initial diagonal: 1 / Gauss-Newton diagonal */
     double f;                       /* objective at theta */
     double edm;                     /* g^T H g / 2 */
+    double fdata;                   /* the part of f that depends on the counts alone (Baker-Cousins:
+                                       2 sum (y log y - y) over y > 0; chi2, Poisson: 0), written by
+                                       the FP64 init calls; cg_fit_step's FP64 evaluations skip that
+                                       part per bin and add this sum instead.  0 after a df64 or
+                                       Levenberg-Marquardt init, whose evaluations include it. */
     int32_t iter;                   /* accepted iterations */
     int32_t n_eval;                 /* objective+gradient evaluations */
     int32_t status;                 /* CG_FIT_* */

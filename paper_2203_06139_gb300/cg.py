@@ -46,8 +46,8 @@ class _TileMap(ctypes.Structure):
                 ("cta_threads", ctypes.c_int32), ("cluster_size", ctypes.c_int32)]
 
 
-# cg_fit_state as a flat record: 12 + 12 + 144 + 12 doubles, f, edm, 4 int32
-FIT_STATE_DOUBLES = FIT_MAX_PARAMS * 3 + FIT_MAX_PARAMS * FIT_MAX_PARAMS + 2
+# cg_fit_state as a flat record: 12 + 12 + 144 + 12 doubles, f, edm, fdata, 4 int32
+FIT_STATE_DOUBLES = FIT_MAX_PARAMS * 3 + FIT_MAX_PARAMS * FIT_MAX_PARAMS + 3
 FIT_STATE_BYTES = FIT_STATE_DOUBLES * 8 + 16
 
 _lib = None

@@ -55,6 +55,7 @@ struct FitSm {
     double th[FP], g[FP], d[FP], tt[FP], gt[FP], h0[FP], sv[FP], yv[FP], hy[FP];
     double H[FP * FP];
     double f, ft, gd, alpha, edm;
+    double fdata;   // the value's data-only part (cg_fit_state::fdata)
     int P, iter, n_eval, status, ntrial, go, upd, bad;
 };
 
@@ -113,8 +114,10 @@ __device__ __forceinline__ void acc_bins(const Geom& G, const GP1Consts& cs, con
 
 // The same on the table-driven FP64 functions (FP64 batches): the thread's
 // sums leave with the objective's factors applied (gp1_tile_scale), and a
-// non-finite value sum sets bad.  acc must start at zero.
-template <int K, int OBJ>
+// non-finite value sum sets bad.  acc must start at zero.  DATA = false
+// leaves out the part of the value that depends on the counts alone
+// (data_part_f64; the fit adds it from its state).
+template <int K, int OBJ, bool DATA = true>
 __device__ __forceinline__ void acc_bins_f64(const Geom& G, const GP1Consts& cs, const GP1Data& dd,
                                              const Fp64Tab& tab, int t0, int T, double (&acc)[GP1Acc<K>::N],
                                              bool& bad) {
@@ -124,12 +127,26 @@ __device__ __forceinline__ void acc_bins_f64(const Geom& G, const GP1Consts& cs,
     gp1_dispatch(dd.D, dd.pm, [&](auto dd_, auto pm_) {
         constexpr int DD = decltype(dd_)::value, PM = decltype(pm_)::value;
         for (int64_t i = t0; i < G.n; i += T) {
-            const GP1Bin b = gp1_bin<OBJ, PM>(fma((double)(2 * i + 1), hh, G.lo), __ldg(G.y + i), dd, tab);
-            gp1_elem_f64<K, OBJ, DD>(b, cs, c2, tab, acc, bad);
+            const GP1Bin b = gp1_bin<OBJ, PM, DATA>(fma((double)(2 * i + 1), hh, G.lo), __ldg(G.y + i), dd, tab);
+            gp1_elem_f64<K, OBJ, DD, DATA>(b, cs, c2, tab, acc, bad);
         }
     });
     gp1_tile_scale<K, OBJ>(acc);
     bad |= nonfinite(acc[0]);
+}
+
+// This thread's share of the value's part that depends on the counts alone:
+// Baker-Cousins 2 sum (y log y - y) over y > 0 (the terms gp1_bin leaves out
+// with DATA = false, in the same arithmetic); 0 for chi2 and Poisson.
+template <int OBJ>
+__device__ __forceinline__ double data_part_f64(const Geom& G, const Fp64Tab& tab, int t0, int T) {
+    double s = 0.0;
+    if (OBJ == CG_OBJ_POISSON_BC)
+        for (int64_t i = t0; i < G.n; i += T) {
+            const double y = __ldg(G.y + i);
+            if (__double_as_longlong(y) > 0) s += fma(y, flog(y, tab), -y);
+        }
+    return 2.0 * s;
 }
 
 // Gauss-Newton diagonal terms of one bin: h (df/dtheta_k)^2 with h = d2T/df2.
@@ -578,14 +595,15 @@ __device__ __forceinline__ void unit_eval(FitSm& s, GP1Consts& cs, GP1Df& cd, co
         double acc[N];
 #pragma unroll
         for (int a = 0; a < N; ++a) acc[a] = 0.0;
-        if (PREC == CG_PREC_FP64) acc_bins_f64<K, OBJ>(G, cs, dd, *t64, t0, T, acc, bad);
+        // FP64: the counts-only part of the value comes from the state (s.fdata)
+        if (PREC == CG_PREC_FP64) acc_bins_f64<K, OBJ, false>(G, cs, dd, *t64, t0, T, acc, bad);
         else acc_bins<K, OBJ>(G, cs, dd, t0, T, acc, bad);   // df64 batches: histograms of 2^24 bins or more
         any_bad = unit_reduce<UNIT, N>(acc, bad, red, part, tot);
     }
     if (UNIT == UNIT_WARP || threadIdx.x < 32) {   // value and gradient, one parameter per lane
         if (lane < s.P) s.gt[lane] = gp1_grad_component<K>(lane, s.tt, tot);
         if (lane == 0) {
-            s.ft = tot[0];
+            s.ft = tot[0] + s.fdata;
             s.bad |= any_bad ? 1 : 0;
         }
     }
@@ -603,6 +621,7 @@ __device__ __forceinline__ void state_load(FitSm& s, const cg_fit_state* st, int
     if (lane_or_tid == 0) {
         s.f = st->f;
         s.edm = st->edm;
+        s.fdata = st->fdata;
         s.iter = st->iter;
         s.n_eval = st->n_eval;
         s.status = st->status;
@@ -806,6 +825,7 @@ __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
     __shared__ double red[(N + 1) * kMaxWarpsPerCta];
     __shared__ double tot[N + 1];
     __shared__ double gn[N + 1];
+    __shared__ double fdt[1];   // init, FP64: the value's counts-only part
     __shared__ int q_sh;
     for (int64_t it = blockIdx.x;; it += gridDim.x) {
         int64_t h;
@@ -876,8 +896,17 @@ __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
             double acc[N], gacc[N];
 #pragma unroll
             for (int i = 0; i < N; ++i) acc[i] = gacc[i] = 0.0;
-            if constexpr (PREC == CG_PREC_FP64) acc_bins_f64<K, OBJ>(G, cs, dd, t64, threadIdx.x, blockDim.x, acc, bad);
-            else acc_bins<K, OBJ>(G, cs, dd, threadIdx.x, blockDim.x, acc, bad);
+            if constexpr (PREC == CG_PREC_FP64) {
+                if constexpr (MODE == 1) {   // init: the counts-only part once, into the fit state
+                    acc_bins_f64<K, OBJ, false>(G, cs, dd, t64, threadIdx.x, blockDim.x, acc, bad);
+                    const double fd[1] = {data_part_f64<OBJ>(G, t64, threadIdx.x, blockDim.x)};
+                    reduce_cta<1, double>(fd, red, fdt);
+                } else {
+                    acc_bins_f64<K, OBJ>(G, cs, dd, t64, threadIdx.x, blockDim.x, acc, bad);
+                }
+            } else {
+                acc_bins<K, OBJ>(G, cs, dd, threadIdx.x, blockDim.x, acc, bad);
+            }
             if constexpr (MODE == 1) gn_bins<K, OBJ>(G, cs, dd, threadIdx.x, blockDim.x, gacc);
             any_bad = __syncthreads_or(bad) | cs_bad;
             if constexpr (MODE == 2) {
@@ -932,7 +961,9 @@ __global__ void __launch_bounds__(256) k_fit_eval(FitArgs a) {
                     for (int j = 0; j < FP; ++j) st->hinv[k * FP + j] = (j == k) ? h0 : 0.0;
                     if (in) edm = fma(g[k] * h0, g[k], edm);
                 }
-                st->f = v;
+                const double fdata = (PREC == CG_PREC_FP64) ? fdt[0] : 0.0;
+                st->f = v + fdata;
+                st->fdata = fdata;
                 st->edm = 0.5 * edm;
                 st->iter = 0;
                 st->n_eval = 1;
@@ -1162,6 +1193,7 @@ __global__ void k_lm_reset(cg_fit_state* st, int64_t H, int P) {
     if (h >= H) return;
     st[h].status = CG_FIT_RUNNING;
     st[h].n_params = P;
+    st[h].fdata = 0.0;   // the Levenberg-Marquardt evaluations include the counts-only part
 }
 
 template <int K, int OBJ>

@@ -49,8 +49,10 @@ struct GP1Bin {
 __device__ __forceinline__ double max_y_1(double y) { return (__double2hiint(y) >= 0x3ff00000) ? y : 1.0; }
 
 // PM: the polynomial's variable, x (0) or t = au x + bu (1), fixed at compile
-// time so that neither is computed in vain.
-template <int OBJ, int PM>
+// time so that neither is computed in vain.  DATA = false leaves out the
+// Baker-Cousins term y log y - y, which depends on the count alone (callers
+// that evaluate one histogram many times add its sum once instead).
+template <int OBJ, int PM, bool DATA = true>
 __device__ __forceinline__ GP1Bin gp1_bin(double x, double y, const GP1Data& d, const Fp64Tab& tab) {
     GP1Bin b;
     b.x = x;
@@ -62,7 +64,7 @@ __device__ __forceinline__ GP1Bin gp1_bin(double x, double y, const GP1Data& d, 
         b.ny = frcp_any(max_y_1(y));
     } else {
         b.ny = -y;
-        if (OBJ == CG_OBJ_POISSON_BC && b.ypos) b.ymy = fma(y, flog(y, tab), -y);
+        if (OBJ == CG_OBJ_POISSON_BC && DATA && b.ypos) b.ymy = fma(y, flog(y, tab), -y);
     }
     return b;
 }
@@ -75,7 +77,8 @@ __device__ __forceinline__ GP1Bin gp1_bin(double x, double y, const GP1Data& d, 
 // polynomial's degree (-1: none), fixed at compile time: with a run-time
 // degree the compiler evaluates every Horner step and adjoint term of the
 // largest degree and selects, several FP64 instructions per bin in vain.
-template <int K, int OBJ, int D>
+// DATA as gp1_bin (false: the bin's y log y - y is not added).
+template <int K, int OBJ, int D, bool DATA = true>
 __device__ __forceinline__ void gp1_elem_f64(const GP1Bin& b, const GP1Consts& cs, const GP1C2& c2,
                                              const Fp64Tab& tab, double (&acc)[GP1Acc<K>::N], bool& bad) {
     double f = 0.0;
@@ -107,7 +110,7 @@ __device__ __forceinline__ void gp1_elem_f64(const GP1Bin& b, const GP1Consts& c
             bad |= b.ypos && !(f > 0.0);
         }
         if (b.ypos) {
-            acc[0] += fma(b.ny, L, (OBJ == CG_OBJ_POISSON_BC) ? f + b.ymy : f);
+            acc[0] += fma(b.ny, L, (OBJ == CG_OBJ_POISSON_BC && DATA) ? f + b.ymy : f);
             g = fma(b.ny, rf, 1.0);
         } else {                          // empty bin: T = f (2 f), even where f underflows to 0
             acc[0] += f;

@@ -16,10 +16,10 @@ import torch
 
 from . import cg
 
-STATE_DOUBLES = cg.FIT_MAX_PARAMS * 3 + cg.FIT_MAX_PARAMS * cg.FIT_MAX_PARAMS + 2
-STATE_BYTES = STATE_DOUBLES * 8 + 16
+STATE_DOUBLES = cg.FIT_STATE_DOUBLES
+STATE_BYTES = cg.FIT_STATE_BYTES
 _TH, _GR, _H, _H0 = 0, 12, 24, 168
-_F, _EDM = 180, 181
+_F, _EDM, _FDATA = 180, 181, 182
 
 
 class States:
@@ -48,6 +48,10 @@ class States:
     @property
     def edm(self):
         return self.d[:, _EDM]
+
+    @property
+    def fdata(self):
+        return self.d[:, _FDATA]
 
     @property
     def iters(self):

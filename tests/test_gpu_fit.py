@@ -126,6 +126,40 @@ def test_batched_fit_poisson_three_peaks(dev, obj):
         assert abs(F[h] - ref["F"]) <= 1e-6 * abs(ref["F"]), (h, F[h], ref["F"])
 
 
+@pytest.mark.parametrize("prec,tmap", [(cg.PREC_FP64, TileMap(4096, 1 << 30, 256, 1)),    # warps
+                                       (cg.PREC_FP64, TileMap(512, 1 << 30, 256, 1)),     # CTAs
+                                       (cg.PREC_FP64, TileMap(512, 1024, 128, 2)),        # clusters of 2
+                                       (cg.PREC_DF64, TileMap(512, 1 << 30, 256, 1))])
+def test_fit_state_value_includes_the_counts_only_part(dev, prec, tmap):
+    """The FP64 fit sums the Baker-Cousins value's counts-only part,
+    2 sum (y log y - y) over y > 0, once at init (the state's fdata) and adds
+    it to the evaluations that leave it out: the state's f is the full
+    objective at the state's theta after init and after steps (oracle, 1e-10).
+    The df64 path includes the term per bin and keeps fdata = 0."""
+    d = synth.c5_batch(H=12, n_bins=2048, index=6)
+    start = d["truth"] * np.random.default_rng(2).uniform(0.95, 1.05, d["truth"].shape)
+    b = HistBatch(d["y"], d["offsets"], d["lo"], d["hi"], 3, 1, cg.OBJ_POISSON_BC, poly_mode=0, precision=prec)
+    f = BatchFitter(b, tmap)
+    f.init(torch.tensor(start, device=dev))
+    fd = f.states.fdata.cpu().numpy()
+    F0 = f.states.f.cpu().numpy()
+    for h in range(d["H"]):
+        y = d["y"][d["offsets"][h]:d["offsets"][h + 1]]
+        yp = y[y > 0]
+        fd_ref = 2.0 * float(np.sum(yp * np.log(yp) - yp)) if prec == cg.PREC_FP64 else 0.0
+        assert abs(fd[h] - fd_ref) <= 1e-12 * abs(fd_ref), (h, fd[h], fd_ref)
+        ref = oracle.binned1d(3, 1, 0, oracle.POISSON_BC, y, 0.0, 1.0, start[h])
+        assert abs(F0[h] - ref.value) <= 1e-10 * abs(ref.value), (h, F0[h], ref.value)
+    f.step(6, 1e-12)
+    F = f.states.f.cpu().numpy()
+    th = f.states.theta.cpu().numpy()
+    assert np.all(f.states.iters.cpu().numpy() > 0)
+    for h in range(d["H"]):
+        y = d["y"][d["offsets"][h]:d["offsets"][h + 1]]
+        ref = oracle.binned1d(3, 1, 0, oracle.POISSON_BC, y, 0.0, 1.0, th[h])
+        assert abs(F[h] - ref.value) <= 1e-10 * abs(ref.value), (h, F[h], ref.value)
+
+
 def test_single_path_full_c1_fit(dev):
     """The plain per-histogram path on 10,000 bins, to the oracle's minimum."""
     h = synth.c1_histogram()
