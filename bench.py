@@ -254,8 +254,8 @@ def sources_hash(files):
 FP64_SOURCES = ["csrc/cg_grad.cu", "csrc/cg_fp64.cuh", "csrc/cg_fp64_tables.inc", "csrc/cg_models_fp64.cuh",
                 "csrc/cg_models.cuh", "csrc/cg_tiles.cuh", "csrc/cg_internal.cuh"]
 NCU_RECORDS = {
-    "k_mix_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "6506c10f2d049b90", "workload": [N_EVENTS, N_POINTS],
-                   "dram_bytes": 80288256 + 3860480, "fp64_pipe_pct": 86.85,
+    "k_mix_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "3504c97de2b978c2", "workload": [N_EVENTS, N_POINTS],
+                   "dram_bytes": 81056512 + 3583232, "fp64_pipe_pct": 87.00,
                    "profile": "profiles/k_mix_fp64_unbinned_1e7x50.md"},
     "k_gp1_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "6506c10f2d049b90", "dram_bytes": 218112, "fp64_pipe_pct": 75.48,
                    "profile": "profiles/k_gp1_fp64_c1_10000bins_100points.md"},
@@ -1219,22 +1219,24 @@ def run_gemm(args):
 def run_c5fit(args):
     """The batched Baker-Cousins fits of the learned-start workload alone: H
     three-peak histograms of 2048 bins from the heuristic start, 50 BFGS
-    iterations, one warp per histogram; `--steps` timed repetitions."""
+    iterations, one warp per histogram, in `--precision`; `--steps` timed
+    repetitions."""
     import numpy as np
     import torch
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2203_06139_gb300 import learned_start as ls, synth
+    from paper_2203_06139_gb300 import cg, learned_start as ls, synth
     H = args.hists or 65536
+    prec = cg.PREC_FP64 if args.precision == "fp64" else cg.PREC_DF64
     y = synth.c5_batch_device(H, ls.N_BINS)["y"]
     th = ls.heuristic_start(y, H)
-    ls.fit_batch(y, H, th, 50, 1e-9)   # warm-up
+    ls.fit_batch(y, H, th, 50, 1e-9, precision=prec)   # warm-up
     ts = []
     for _ in range(max(args.steps, 1)):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        f = ls.fit_batch(y, H, th, 50, 1e-9)
+        f = ls.fit_batch(y, H, th, 50, 1e-9, precision=prec)
         e1.record()
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
@@ -1244,7 +1246,7 @@ def run_c5fit(args):
             "value": ev.sum() * ls.N_BINS / (ms * 1e-3), "unit": "bin-evaluations/s", "higher_is_better": True,
             "ms_per_step": ms, "ms_all": ts,
             "config": {"workload": "%d histograms x 2048 bins, 3 Gaussians + linear, Baker-Cousins, heuristic "
-                                   "start, 50 iterations, df64" % H},
+                                   "start, 50 iterations, %s" % (H, args.precision)},
             "mean_evals": float(ev.mean()), "max_evals": int(ev.max())}
     print(json.dumps(line), flush=True)
 
@@ -1432,6 +1434,8 @@ def main():
     ap.add_argument("--hists", type=int, default=0, help="c5 / c5fit: histograms fitted (0 = 65,536)")
     ap.add_argument("--train-hists", type=int, default=0, help="c5: training histograms (0 = 10^6)")
     ap.add_argument("--epochs", type=int, default=0, help="c5: training epochs (0 = 6)")
+    ap.add_argument("--precision", default="df64", choices=["fp64", "df64"],
+                    help="c5fit: arithmetic of the objective evaluations")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
