@@ -185,10 +185,12 @@ def measured_peaks():
 #    1, peak adjoints 15, polynomial adjoints 2 = 72 (the counts-only term
 #    y log y - y, a log and two more instructions per bin, is summed once
 #    per histogram at the fit's init, not at every evaluation);
-#  - 2-D bin: centres 2 x 2, log 13, reciprocal 3, adjoint seed, value and
-#    constant 4 = 24; per (bin, Gaussian kept by the tile's culling):
-#    dx, dy 2, quadratic form 5, exp2 7, model 1, adjoints 3 + 6 = 24.
-FP64_INSTR = {"mix": 23, "gp1_c1": 23.25, "fit_c4": 30, "fit_c5": 72, "rg2_bin": 24, "rg2_gauss": 24}
+#  - 2-D bin (a thread walks one column of its tile: x and the column's
+#    per-Gaussian x terms once per tile): y centre 2, log 13, reciprocal 3,
+#    adjoint seed, value and constant 4 = 22; per (bin, Gaussian kept by
+#    the tile's culling): dy 1, the exponent -(u'^2 + v'^2) 4 (u', v', v'^2
+#    and one FMA), exp2 7, model 1, adjoints 2 + 3 = 18.
+FP64_INSTR = {"mix": 23, "gp1_c1": 23.25, "fit_c4": 30, "fit_c5": 72, "rg2_bin": 22, "rg2_gauss": 18}
 
 # FP32-pipe operations per unit of the double-float kernels (cg_df64.cuh,
 # cg_df64.cu, cg_models_df64.cuh): event-point of the mixture: two df64
@@ -645,27 +647,39 @@ def config_c1(args, rates, sm_max_mhz):
 
 def _c3_active_pairs(truth_or_theta, K=8, nx=4096, ny=4096, tile=64, cull=80.0):
     """(bin, Gaussian) pairs the 2-D kernels evaluate: per 64 x 64 tile, the
-    Gaussians whose exponent can be below 80 somewhere in the tile's box of
-    bin centres (the kernels' culling rule), times the tile's bins."""
+    Gaussians whose exponent reaches above -80 somewhere in the tile's box of
+    bin centres (the exact maximum of the concave quadratic exponent over the
+    box: 0 with the centre inside, else the largest of the four edge maxima;
+    the kernels' culling rule), times the tile's bins."""
     import numpy as np
     th = np.asarray(truth_or_theta, dtype=np.float64)
+    log2e = 1.0 / math.log(2.0)
     hx, hy = 1.0 / nx, 1.0 / ny
     tx = np.arange(0, nx, tile)
     ty = np.arange(0, ny, tile)
-    bx0 = (tx + 0.5) * hx
-    bx1 = (np.minimum(tx + tile, nx) - 0.5) * hx
-    by0 = (ty + 0.5) * hy
-    by1 = (np.minimum(ty + tile, ny) - 0.5) * hy
-    nbx = (np.minimum(tx + tile, nx) - tx)
-    nby = (np.minimum(ty + tile, ny) - ty)
+    bx0 = ((tx + 0.5) * hx)[None, :]
+    bx1 = ((np.minimum(tx + tile, nx) - 0.5) * hx)[None, :]
+    by0 = ((ty + 0.5) * hy)[:, None]
+    by1 = ((np.minimum(ty + tile, ny) - 0.5) * hy)[:, None]
+    nb = (np.minimum(ty + tile, ny) - ty)[:, None] * (np.minimum(tx + tile, nx) - tx)[None, :]
     pairs = 0
     for k in range(K):
-        mx, my = th[6 * k + 1], th[6 * k + 2]
-        sm = max(abs(th[6 * k + 3]), abs(th[6 * k + 4]))
-        ddx = np.maximum(0.0, np.maximum(bx0 - mx, mx - bx1))
-        ddy = np.maximum(0.0, np.maximum(by0 - my, my - by1))
-        q = 0.5 * (ddx[None, :] ** 2 + ddy[:, None] ** 2) / (sm * sm)
-        pairs += int(((q <= cull) * (nby[:, None] * nbx[None, :])).sum())
+        mx, my, sx, sy, phi = th[6 * k + 1:6 * k + 6]
+        al, be = -0.5 / (sx * sx), -0.5 / (sy * sy)
+        c, s = math.cos(phi), math.sin(phi)
+        qa = (al * c * c + be * s * s) * log2e
+        qb2 = 2.0 * (al - be) * c * s * log2e
+        qc = (al * s * s + be * c * c) * log2e
+        X0, X1, Y0, Y1 = bx0 - mx, bx1 - mx, by0 - my, by1 - my
+
+        def E(dx, dy):
+            return dx * (qa * dx + qb2 * dy) + qc * dy * dy
+        ry, rx = -0.5 * qb2 / qc, -0.5 * qb2 / qa
+        m = np.maximum.reduce([E(X0, np.clip(ry * X0, Y0, Y1)), E(X1, np.clip(ry * X1, Y0, Y1)),
+                               E(np.clip(rx * Y0, X0, X1), Y0), E(np.clip(rx * Y1, X0, X1), Y1)])
+        inside = (X0 <= 0) & (X1 >= 0) & (Y0 <= 0) & (Y1 >= 0)
+        m = np.where(inside, 0.0, m)
+        pairs += int((~(m < -cull * log2e) * nb).sum())
     return pairs
 
 

@@ -217,26 +217,73 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_mix_fp64(MixData d, const doub
 }
 
 // 2-D tiles of kRgTX x kRgTY bins.  Per tile, a Gaussian whose exponent
-// -q = (u^2/sx^2 + v^2/sy^2)/2 exceeds kRgCull everywhere in the tile's box of
-// bin centres is skipped: q >= r^2 / (2 max(sx, sy)^2) with r the distance
-// from its centre to the box, and exp(-80) A is below 1e-33 of any model
-// value (the constant is >= 0 and the counts are fitted by A, C > 0), far
-// under FP64 resolution.
+// -q = -(u^2/sx^2 + v^2/sy^2)/2 stays below -kRgCull everywhere in the tile's
+// box of bin centres is skipped (the exact maximum of the exponent over the
+// box, rg2_box_max_exponent).  The dropped term is below e^-80 A = 1.8e-35 A
+// at every bin of the tile, under the FP64 resolution of the model value
+// wherever that value exceeds 1.8e-19 A (a constant C > 0 or another
+// Gaussian within reach).
 constexpr int kRgTX = 64, kRgTY = 64;
 constexpr double kRgCull = 80.0;
 
+// The rows of one tile for the NA Gaussians kept by its culling: thread ->
+// one column (consecutive threads, consecutive bins of a row), rows r0,
+// r0 + NT / kRgTX, ...; the block's sums of the (dx, dy) moments over the
+// kept Gaussians land in totc[0 .. 2 + 6 NA).
+template <int NA, int NT>
+__device__ __forceinline__ void rg2_tile_rows(const RG2Data& d, int64_t x0, int64_t y0, int w, int h, double C,
+                                              const RG2Act& a, const Fp64Tab& tab, double* red, double* totc,
+                                              bool& bad) {
+    constexpr int NM = 2 + 6 * NA;
+    double m[NM];
+#pragma unroll
+    for (int i = 0; i < NM; ++i) m[i] = 0.0;
+    const int col_i = threadIdx.x % kRgTX, r0 = threadIdx.x / kRgTX;
+    if (col_i < w) {
+        // centres lo + (i + 1/2) h as (2i + 1) (h/2) + lo (correctly rounded, one FMA each)
+        const double hhy = 0.5 * d.hy;
+        const int64_t ix = x0 + col_i;
+        RG2Col<NA> col;
+        rg2_col<NA>(fma((double)(2 * ix + 1), 0.5 * d.hx, d.lx), a, col);
+        double cacc[2 + 3 * NA];
+#pragma unroll
+        for (int i = 0; i < 2 + 3 * NA; ++i) cacc[i] = 0.0;
+        for (int r = r0; r < h; r += NT / kRgTX) {
+            const int64_t iy = y0 + r;
+            rg2_elem_col<NA>(fma((double)(2 * iy + 1), hhy, d.ly), __ldg(d.n + iy * d.nx + ix), C, a, col, tab,
+                             cacc, bad);
+        }
+        rg2_col_moments<NA>(col, cacc, m);
+    }
+    bad |= nonfinite(m[0]);
+    block_sum_rs<NM, NT>(m, red, totc);
+}
+
+// rg2_tile_rows compiled for each count 0 .. NA of kept Gaussians; n selects
+// one (uniform over the block).
+template <int NA, int NT>
+__device__ __forceinline__ void rg2_rows_upto(int n, const RG2Data& d, int64_t x0, int64_t y0, int w, int h,
+                                              double C, const RG2Act& a, const Fp64Tab& tab, double* red,
+                                              double* totc, bool& bad) {
+    if (n == NA) rg2_tile_rows<NA, NT>(d, x0, y0, w, h, C, a, tab, red, totc, bad);
+    else if constexpr (NA > 0) rg2_rows_upto<NA - 1, NT>(n, d, x0, y0, w, h, C, a, tab, red, totc, bad);
+}
+
 template <int K, int NT>
-__global__ void __launch_bounds__(NT) k_rg2_fp64(RG2Data d, const double* __restrict__ theta,
+__global__ void __launch_bounds__(NT, 3) k_rg2_fp64(RG2Data d, const double* __restrict__ theta,
                                                  TileGrid tg, double* __restrict__ part,
                                                  WsHeader* __restrict__ hdr) {
     constexpr int NACC = RG2Acc<K>::N;
+    static_assert(NT % kRgTX == 0, "whole columns per block");
     __shared__ Fp64Tab tab;
     __shared__ RG2Consts cs;
     __shared__ RG2Q cq;
+    __shared__ RG2Act ka;
     __shared__ int cs_bad;
     __shared__ unsigned act_s;
     __shared__ double red[NACC * (NT / 32)];
-    __shared__ double tot[NACC];
+    __shared__ double totc[NACC];   // block sums over the kept Gaussians
+    __shared__ double tot[NACC];    // the same in accumulator order
     if (gated_off(tg)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) hdr->status = 0;
     fp64_tab_load(tab);
@@ -247,46 +294,54 @@ __global__ void __launch_bounds__(NT) k_rg2_fp64(RG2Data d, const double* __rest
         const int ty = c / ntx, tx = c - ty * ntx;
         const int64_t x0 = (int64_t)tx * kRgTX, y0 = (int64_t)ty * kRgTY;
         const int64_t x1 = min(d.nx, x0 + kRgTX), y1 = min(d.ny, y0 + kRgTY);
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {   // one Gaussian per lane: constants, culling, the kept set
+            const int k = threadIdx.x;
             const double* tht = theta + (size_t)th * P;
-            cs_bad = rg2_prologue<K>(tht, cs) ? 0 : 1;
-            rg2_q<K>(cs, cq);
-            // box of bin centres of this tile
-            const double bx0 = fma((double)x0 + 0.5, d.hx, d.lx), bx1 = fma((double)(x1 - 1) + 0.5, d.hx, d.lx);
-            const double by0 = fma((double)y0 + 0.5, d.hy, d.ly), by1 = fma((double)(y1 - 1) + 0.5, d.hy, d.ly);
-            unsigned act = 0;
-            for (int k = 0; k < K; ++k) {
-                const double mx = tht[6 * k + 1], my = tht[6 * k + 2];
-                const double sm = fmax(fabs(tht[6 * k + 3]), fabs(tht[6 * k + 4]));
-                const double ddx = fmax(0.0, fmax(bx0 - mx, mx - bx1));
-                const double ddy = fmax(0.0, fmax(by0 - my, my - by1));
-                const double qmin = 0.5 * (ddx * ddx + ddy * ddy) / (sm * sm);
-                if (!(qmin > kRgCull)) act |= 1u << k;   // NaN keeps the Gaussian
+            bool ok = true, keep = false;
+            if (k < K) {
+                ok = rg2_prologue_one(tht + 6 * k, k, cs);
+                rg2_q_one(cs, k, cq);
+                // the box of bin centres of this tile, as offsets from the Gaussian's centre
+                const double bx0 = fma((double)x0 + 0.5, d.hx, d.lx), bx1 = fma((double)(x1 - 1) + 0.5, d.hx, d.lx);
+                const double by0 = fma((double)y0 + 0.5, d.hy, d.ly), by1 = fma((double)(y1 - 1) + 0.5, d.hy, d.ly);
+                const double mx = cs.mx[k], my = cs.my[k];
+                const double emax = rg2_box_max_exponent(cq, k, bx0 - mx, bx1 - mx, by0 - my, by1 - my);
+                keep = !(emax < -kRgCull * kLog2e);   // NaN keeps the Gaussian
             }
-            act_s = act;
+            const unsigned act = __ballot_sync(0xffffffffu, keep);
+            const bool all_ok = __all_sync(0xffffffffu, ok);
+            if (keep) rg2_act_one(cs, k, __popc(act & ((1u << k) - 1u)), ka);
+            if (k == 0) {
+                cs.C = tht[6 * K];
+                cs_bad = (all_ok && isfinite(cs.C)) ? 0 : 1;
+                act_s = act;
+                ka.n = __popc(act);
+            }
         }
         __syncthreads();
         const unsigned act = act_s;
-        double acc[NACC];
-#pragma unroll
-        for (int a = 0; a < NACC; ++a) acc[a] = 0.0;
+        const int nact = ka.n;
         bool bad = false;
-        const int w = (int)(x1 - x0);
-        const int nbin = w * (int)(y1 - y0);
-        // centres lo + (i + 1/2) h as (2i + 1) (h/2) + lo (correctly rounded, one FMA each)
-        const double hhx = 0.5 * d.hx, hhy = 0.5 * d.hy;
-        for (int b = threadIdx.x; b < nbin; b += NT) {
-            const int r = b / w, col = b - r * w;
-            const int64_t ix = x0 + col, iy = y0 + r;
-            const double xc = fma((double)(2 * ix + 1), hhx, d.lx);
-            const double yc = fma((double)(2 * iy + 1), hhy, d.ly);
-            rg2_elem_f64<K>(xc, yc, __ldg(d.n + iy * d.nx + ix), cs, cq, act, tab, acc, bad);
-        }
-        bad |= nonfinite(acc[0]);
+        rg2_rows_upto<K, NT>(nact, d, x0, y0, (int)(x1 - x0), (int)(y1 - y0), cs.C, ka, tab, red, totc, bad);
         const int any_bad = __syncthreads_or(bad ? 1 : 0) | cs_bad;
-        block_sum<NACC, NT>(acc, red, tot);
-        if (threadIdx.x == 0)
-            for (int k = 0; k < K; ++k) rg2_rotate_moments(tot + 1 + 6 * k, cs.cs[k], cs.sn[k]);
+        // the kept Gaussians' moments rotated to (u, v) and put in accumulator order (0 for the culled)
+        if (threadIdx.x < nact) {
+            const int k = ka.k[threadIdx.x];
+            rg2_rotate_moments(totc + 1 + 6 * threadIdx.x, cs.cs[k], cs.sn[k]);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < NACC; i += NT) {
+            double v;
+            if (i == 0) {
+                v = totc[0];
+            } else if (i == NACC - 1) {
+                v = totc[1 + 6 * nact];
+            } else {
+                const int k = (i - 1) / 6, comp = i - 1 - 6 * k;
+                v = ((act >> k) & 1u) ? totc[1 + 6 * __popc(act & ((1u << k) - 1u)) + comp] : 0.0;
+            }
+            tot[i] = v;
+        }
         __syncthreads();
         write_partial<NACC>(part, tg, th, c, tot, any_bad);
     }

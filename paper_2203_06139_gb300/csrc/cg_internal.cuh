@@ -92,24 +92,41 @@ __device__ __forceinline__ double warp_reduce_scatter(const double (&v)[NA]) {
     return s;
 }
 
-// Block sum of NA <= 32 per-thread values by warp reduce-scatters, then the
-// per-warp totals of each accumulator added in warp order by one thread per
-// accumulator.  red: NA * (NT/32) doubles of shared scratch; the totals land
-// in tot[0 .. NA) (shared), valid for every thread after the call.
+// Block sum of NA <= 64 per-thread values by warp reduce-scatters (of the
+// first 32 values and of the rest), then the per-warp totals of each
+// accumulator added in warp order by one thread per accumulator.  red:
+// NA * (NT/32) doubles of shared scratch; the totals land in tot[0 .. NA)
+// (shared), valid for every thread after the call.
 template <int NA, int NT>
 __device__ __forceinline__ void block_sum_rs(const double (&acc)[NA], double* red, double* tot) {
+    static_assert(NA >= 1 && NA <= 64, "at most 64 values per thread");
     constexpr int NW = NT / 32;
-    constexpr int SH = WarpRS<NA>::SH;
+    constexpr int N1 = NA < 32 ? NA : 32, N2 = NA - N1;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const double s = warp_reduce_scatter<NA>(acc);
-    const int a = lane >> SH;
-    if ((lane & ((1 << SH) - 1)) == 0 && a < NA) red[a * NW + wid] = s;
+    {
+        double v[N1];
+#pragma unroll
+        for (int i = 0; i < N1; ++i) v[i] = acc[i];
+        constexpr int SH = WarpRS<N1>::SH;
+        const double s = warp_reduce_scatter<N1>(v);
+        const int a = lane >> SH;
+        if ((lane & ((1 << SH) - 1)) == 0 && a < N1) red[a * NW + wid] = s;
+    }
+    if constexpr (N2 > 0) {
+        double v[N2 > 0 ? N2 : 1];
+#pragma unroll
+        for (int i = 0; i < N2; ++i) v[i] = acc[N1 + i];
+        constexpr int SH = WarpRS<N2>::SH;
+        const double s = warp_reduce_scatter<N2>(v);
+        const int a = lane >> SH;
+        if ((lane & ((1 << SH) - 1)) == 0 && a < N2) red[(N1 + a) * NW + wid] = s;
+    }
     __syncthreads();
-    if (threadIdx.x < NA) {
+    for (int a = threadIdx.x; a < NA; a += NT) {
         double t = 0.0;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) t += red[threadIdx.x * NW + w];
-        tot[threadIdx.x] = t;
+        for (int w = 0; w < NW; ++w) t += red[a * NW + w];
+        tot[a] = t;
     }
     __syncthreads();
 }

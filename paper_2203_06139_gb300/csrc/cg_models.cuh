@@ -224,21 +224,25 @@ struct RG2Data {
     double lx, ly, hx, hy;
 };
 
+// Constants of Gaussian k from its six parameters t; false when one is not
+// finite or a width is 0.
+__device__ __forceinline__ bool rg2_prologue_one(const double* __restrict__ t, int k, RG2Consts& c) {
+    c.A[k] = t[0];
+    c.mx[k] = t[1];
+    c.my[k] = t[2];
+    c.al[k] = -0.5 / (t[3] * t[3]);
+    c.be[k] = -0.5 / (t[4] * t[4]);
+    sincos(t[5], &c.sn[k], &c.cs[k]);
+    bool ok = t[3] != 0.0 && t[4] != 0.0;
+    for (int j = 0; j < 6; ++j) ok = ok && isfinite(t[j]);
+    return ok;
+}
+
 template <int K>
 __device__ __forceinline__ bool rg2_prologue(const double* __restrict__ th, RG2Consts& c) {
     bool ok = true;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const double* t = th + 6 * k;
-        c.A[k] = t[0];
-        c.mx[k] = t[1];
-        c.my[k] = t[2];
-        c.al[k] = -0.5 / (t[3] * t[3]);
-        c.be[k] = -0.5 / (t[4] * t[4]);
-        sincos(t[5], &c.sn[k], &c.cs[k]);
-        for (int j = 0; j < 6; ++j) ok = ok && isfinite(t[j]);
-        ok = ok && t[3] != 0.0 && t[4] != 0.0;
-    }
+    for (int k = 0; k < K; ++k) ok = rg2_prologue_one(th + 6 * k, k, c) && ok;
     c.C = th[6 * K];
     return ok && isfinite(c.C);
 }

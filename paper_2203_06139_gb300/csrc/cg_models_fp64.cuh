@@ -334,36 +334,107 @@ __device__ inline void mix_ratio_sums(const MixConsts& cs, const MixR2& c, doubl
 // (1, u, v, u^2, v^2, u v) once per tile, a rotation of the moments.
 // ===========================================================================
 struct RG2Q {
-    double qa[CG_MAX_PEAKS_2D], qb2[CG_MAX_PEAKS_2D], qc[CG_MAX_PEAKS_2D];   // qb2 = 2 qb
+    double qa[CG_MAX_PEAKS_2D], qb2[CG_MAX_PEAKS_2D], qc[CG_MAX_PEAKS_2D];   // qb2 = 2 qb (tile culling)
 };
 
-template <int K>
-__device__ __forceinline__ void rg2_q(const RG2Consts& c, RG2Q& q) {
-    for (int k = 0; k < K; ++k) {
-        const double cs = c.cs[k], sn = c.sn[k], al = c.al[k], be = c.be[k];
-        q.qa[k] = fma(al, cs * cs, be * sn * sn) * kLog2e;
-        q.qb2[k] = 2.0 * ((al - be) * cs * sn) * kLog2e;
-        q.qc[k] = fma(al, sn * sn, be * cs * cs) * kLog2e;
+// The Gaussians that survive a tile's culling, packed in slots 0 .. n-1 (see
+// rg2_act_one and the column form below).
+struct RG2Act {
+    double A[CG_MAX_PEAKS_2D], mx[CG_MAX_PEAKS_2D], my[CG_MAX_PEAKS_2D];
+    double sa[CG_MAX_PEAKS_2D], ca[CG_MAX_PEAKS_2D], sb[CG_MAX_PEAKS_2D], cb[CG_MAX_PEAKS_2D];
+    int k[CG_MAX_PEAKS_2D];   // the Gaussian's index in the parameter vector
+    int n;                    // how many survive
+};
+
+__device__ __forceinline__ void rg2_q_one(const RG2Consts& c, int k, RG2Q& q) {
+    const double cs = c.cs[k], sn = c.sn[k], al = c.al[k], be = c.be[k];
+    q.qa[k] = fma(al, cs * cs, be * sn * sn) * kLog2e;
+    q.qb2[k] = 2.0 * ((al - be) * cs * sn) * kLog2e;
+    q.qc[k] = fma(al, sn * sn, be * cs * cs) * kLog2e;
+}
+
+// Gaussian k into slot j of the tile's kept set: the exponent evaluated per
+// bin as -(u'^2 + v'^2), u' = ra u, v' = rb v, ra = sqrt(-al log2 e),
+// rb = sqrt(-be log2 e):  u' = sa dy + ca dx, v' = cb dy - sb dx
+// (sa = ra s, ca = ra c, sb = rb s, cb = rb c).
+__device__ __forceinline__ void rg2_act_one(const RG2Consts& c, int k, int j, RG2Act& a) {
+    const double ra = sqrt(-c.al[k] * kLog2e), rb = sqrt(-c.be[k] * kLog2e);
+    a.A[j] = c.A[k];
+    a.mx[j] = c.mx[k];
+    a.my[j] = c.my[k];
+    a.sa[j] = ra * c.sn[k];
+    a.ca[j] = ra * c.cs[k];
+    a.sb[j] = rb * c.sn[k];
+    a.cb[j] = rb * c.cs[k];
+    a.k[j] = k;
+}
+
+// Largest exponent (log2 units) of Gaussian k over the box [X0, X1] x [Y0, Y1]
+// of offsets (dx, dy) from its centre: the exponent qa dx^2 + qb2 dx dy +
+// qc dy^2 is a concave quadratic, so its maximum over the box is 0 when the
+// centre lies inside, else on one of the four edges, where it is a concave
+// parabola maximised at its vertex clamped to the edge.  NaN for degenerate
+// coefficients (the caller keeps the Gaussian then).
+__device__ __forceinline__ double rg2_box_max_exponent(const RG2Q& q, int k, double X0, double X1, double Y0,
+                                                       double Y1) {
+    if (X0 <= 0.0 && 0.0 <= X1 && Y0 <= 0.0 && 0.0 <= Y1) return 0.0;
+    const double qa = q.qa[k], qb2 = q.qb2[k], qc = q.qc[k];
+    const auto E = [&](double dx, double dy) { return fma(dx, fma(qa, dx, qb2 * dy), (qc * dy) * dy); };
+    const auto clamp = [](double v, double lo, double hi) { return fmin(fmax(v, lo), hi); };
+    const double ry = -0.5 * qb2 / qc, rx = -0.5 * qb2 / qa;   // vertices: dy* = ry dx, dx* = rx dy
+    double m = E(X0, clamp(ry * X0, Y0, Y1));
+    m = fmax(m, E(X1, clamp(ry * X1, Y0, Y1)));
+    m = fmax(m, E(clamp(rx * Y0, X0, X1), Y0));
+    m = fmax(m, E(clamp(rx * Y1, X0, X1), Y1));
+    return (qa < 0.0 && qc < 0.0) ? m : __longlong_as_double(0x7ff8000000000000LL);
+}
+
+// ---------------------------------------------------------------------------
+// Column form of the element, for a thread that walks one column of bins
+// (x fixed), over the NA Gaussians that survive the tile's culling, packed
+// in RG2Act (NA fixed at compile time: a culled Gaussian costs nothing,
+// where a run-time skip inside an unrolled loop leaves its instructions
+// issued with every lane predicated off).  The exponent is taken in the
+// Gaussian's own axes, scaled,
+//   q log2(e) = -(u'^2 + v'^2),  u' = sa dy + ua,  v' = cb dy - vb,
+// with the column's parts ua = ca dx, vb = sb dx once per tile: a sum of two
+// squares, so its rounding error stays near eps |q| however elongated the
+// Gaussian (expanding the quadratic form in dx, dy instead cancels terms
+// larger than q by the squared aspect ratio).  The adjoint moments are kept
+// in (dx, dy) and, since dx is fixed, those with dx follow from sums over dy
+// alone:  sum w dx = dx sum w,  sum w dx^2 = dx^2 sum w,  sum w dx dy = dx sum w dy.
+// A thread sums [ T | (w, w dy, w dy^2) per kept Gaussian | g ], w = g e_j;
+// rg2_col_moments turns its sums into [ T | (S, Sx, Sy, Sxx, Syy, Sxy) per
+// kept Gaussian | sum g ], the layout of rg2_elem_fp64's accumulators over
+// the kept Gaussians.
+// ---------------------------------------------------------------------------
+template <int NA>
+struct RG2Col {
+    double dx[NA > 0 ? NA : 1], ua[NA > 0 ? NA : 1], vb[NA > 0 ? NA : 1];
+};
+
+template <int NA>
+__device__ __forceinline__ void rg2_col(double x, const RG2Act& a, RG2Col<NA>& col) {
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        const double dx = x - a.mx[j];
+        col.dx[j] = dx;
+        col.ua[j] = a.ca[j] * dx;
+        col.vb[j] = a.sb[j] * dx;
     }
 }
 
-template <int K>
-__device__ __forceinline__ void rg2_elem_f64(double x, double y, double n, const RG2Consts& c, const RG2Q& q,
-                                             unsigned act, const Fp64Tab& tab, double (&acc)[RG2Acc<K>::N],
-                                             bool& bad) {
-    double dx[K], dy[K], e[K];
-    double mu = c.C;
+template <int NA>
+__device__ __forceinline__ void rg2_elem_col(double y, double n, double C, const RG2Act& a, const RG2Col<NA>& col,
+                                             const Fp64Tab& tab, double (&acc)[2 + 3 * NA], bool& bad) {
+    double dy[NA > 0 ? NA : 1], e[NA > 0 ? NA : 1];
+    double mu = C;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        if (!(act & (1u << k))) {
-            dx[k] = dy[k] = e[k] = 0.0;
-            continue;
-        }
-        dx[k] = x - c.mx[k];
-        dy[k] = y - c.my[k];
-        const double t = fma(q.qa[k], dx[k], q.qb2[k] * dy[k]);
-        e[k] = fexp2(fma(dx[k], t, (q.qc[k] * dy[k]) * dy[k]), tab);
-        mu = fma(c.A[k], e[k], mu);
+    for (int j = 0; j < NA; ++j) {
+        dy[j] = y - a.my[j];
+        const double up = fma(a.sa[j], dy[j], col.ua[j]), vp = fma(a.cb[j], dy[j], -col.vb[j]);
+        e[j] = fexp2(fma(-up, up, -(vp * vp)), tab);
+        mu = fma(a.A[j], e[j], mu);
     }
     const bool npos = __double_as_longlong(n) > 0;
     double L, rm;
@@ -378,18 +449,33 @@ __device__ __forceinline__ void rg2_elem_f64(double x, double y, double n, const
     const double g = npos ? fma(-n, rm, 1.0) : 1.0;
     acc[0] += npos ? fma(-n, L, mu) : mu;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        if (!(act & (1u << k))) continue;
-        const double w = g * e[k];
-        const double wx = w * dx[k], wy = w * dy[k];
-        acc[1 + 6 * k] += w;
-        acc[2 + 6 * k] += wx;
-        acc[3 + 6 * k] += wy;
-        acc[4 + 6 * k] = fma(wx, dx[k], acc[4 + 6 * k]);
-        acc[5 + 6 * k] = fma(wy, dy[k], acc[5 + 6 * k]);
-        acc[6 + 6 * k] = fma(wx, dy[k], acc[6 + 6 * k]);
+    for (int j = 0; j < NA; ++j) {
+        const double w = g * e[j];
+        const double wy = w * dy[j];
+        acc[1 + 3 * j] += w;
+        acc[2 + 3 * j] += wy;
+        acc[3 + 3 * j] = fma(wy, dy[j], acc[3 + 3 * j]);
     }
-    acc[1 + 6 * K] += g;
+    acc[1 + 3 * NA] += g;
+}
+
+// One thread's column-form sums into (dx, dy) moments (layout above).
+template <int NA>
+__device__ __forceinline__ void rg2_col_moments(const RG2Col<NA>& col, const double (&c)[2 + 3 * NA],
+                                                double (&m)[2 + 6 * NA]) {
+    m[0] = c[0];
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        const double dx = col.dx[j], S = c[1 + 3 * j], Sy = c[2 + 3 * j];
+        const double Sx = dx * S;
+        m[1 + 6 * j] = S;
+        m[2 + 6 * j] = Sx;
+        m[3 + 6 * j] = Sy;
+        m[4 + 6 * j] = dx * Sx;
+        m[5 + 6 * j] = c[3 + 3 * j];
+        m[6 + 6 * j] = dx * Sy;
+    }
+    m[1 + 6 * NA] = c[1 + 3 * NA];
 }
 
 // (dx, dy) moments of one Gaussian -> (u, v) moments, in place: S[0..5] =

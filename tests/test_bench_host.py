@@ -42,8 +42,8 @@ def test_instruction_counts_add_up():
     assert bench.FP64_INSTR["gp1_c1"] == 1 + 1 + 2 + exp2 + 1 + 3 + 5 + 2 + 5 / 4
     assert bench.FP64_INSTR["fit_c4"] == 2 + 3 + 2 + (1 + 2 + exp2 + 1) + 3 + 5 + 4
     assert bench.FP64_INSTR["fit_c5"] == 2 + 1 + 3 * (1 + 2 + exp2 + 1) + log + rcp + 2 + 1 + 15 + 2
-    assert bench.FP64_INSTR["rg2_gauss"] == 2 + 5 + exp2 + 1 + 3 + 6
-    assert bench.FP64_INSTR["rg2_bin"] == 2 * 2 + log + rcp + 4
+    assert bench.FP64_INSTR["rg2_gauss"] == 1 + 4 + exp2 + 1 + 2 + 3   # column form
+    assert bench.FP64_INSTR["rg2_bin"] == 2 + log + rcp + 4
 
 
 def test_ncu_records_are_null_for_other_sizes_or_sources(monkeypatch):
@@ -99,3 +99,11 @@ def test_culled_pair_count_of_the_2d_kernels():
     narrow = np.array([100.0, 0.5, 0.5, 0.001, 0.001, 0.0, 5.0])
     # r^2 / (2 s^2) <= 80: r <= 0.0126, inside the 2 x 2 tiles of 64 / 1024 around the centre
     assert bench._c3_active_pairs(narrow, K=1, nx=1024, ny=1024) == 4 * 64 * 64
+    # elongated along y: the exponent reaches -80 within 0.0126 of the centre in x but
+    # everywhere in y (0.5^2 / (2 0.05^2) = 50), so 2 x 16 tiles of 1024^2; rotated by
+    # 90 degrees, 16 x 2; the isotropic bound max(sx, sy) would keep far more
+    long_y = np.array([100.0, 0.5, 0.5, 0.001, 0.05, 0.0, 5.0])
+    assert bench._c3_active_pairs(long_y, K=1, nx=1024, ny=1024) == 2 * 16 * 64 * 64
+    long_x = long_y.copy()
+    long_x[5] = np.pi / 2
+    assert bench._c3_active_pairs(long_x, K=1, nx=1024, ny=1024) == 2 * 16 * 64 * 64

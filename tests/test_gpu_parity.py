@@ -231,6 +231,23 @@ def test_rotgauss2d_small(dev, K, nx, ny):
     check(v, g, oracle.binned2d(K, counts, 0.0, 1.0, 0.0, 1.0, th))
 
 
+def test_rotgauss2d_elongated_culling(dev):
+    """Narrow, elongated Gaussians at 30 and 120 degrees across many 64 x 64
+    tiles of a ragged 333 x 301 grid (and one centred outside the grid): the
+    tiles' culling by the exact maximum of the exponent over each box keeps
+    the result at the oracle's, which has no culling."""
+    th = np.array([300.0, 0.4, 0.55, 0.004, 0.08, np.pi / 6,
+                   200.0, 0.7, 0.3, 0.06, 0.003, 2 * np.pi / 3,
+                   150.0, 1.05, 0.5, 0.01, 0.02, 0.3,
+                   2.0])
+    K, nx, ny = 3, 333, 301
+    counts = np.random.default_rng(21).poisson(synth.expected_counts_2d(th, K, nx, ny)).astype(float)
+    p2 = cg.Problem.rotgauss2d(torch.tensor(counts, device=dev), K)
+    for t in (th, th * (1 + np.random.default_rng(22).uniform(-0.03, 0.03, th.size))):
+        v, g = cg.gradient(p2, torch.tensor(t, device=dev))
+        check(v, g, oracle.binned2d(K, counts, 0.0, 1.0, 0.0, 1.0, t))
+
+
 @pytest.mark.slow
 def test_c3_full_size(dev):
     """4096 x 4096 bins, 8 rotated Gaussians + constant, one parameter point."""
