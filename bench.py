@@ -168,10 +168,11 @@ def measured_peaks():
 #  - exp2: 3 for the reduction (two additions of 1.5 * 2^40, one
 #    subtraction), 3 for the polynomial, 1 for T (1 + p) = 7;
 #  - reciprocal: 3 FMAs after the hardware estimate; log: 13;
-#  - event-point of the mixture (ratio form: p = b eE (1 + u), one exp2):
-#    d = x - mu, c2 d, the exponential's part of the exponent (one FMA), the
-#    exponent (one FMA), exp2, s = 1 + u, reciprocal, running product,
-#    r = u V, r d, five accumulations = 1+1+1+1+7+1+3+1+1+1+5 = 23;
+#  - event-point of the mixture (lean ratio form: p = b eE (1 + u), one
+#    exp2, the exponential's sums from V = 1 - r per tile): d = x - mu, c2 d,
+#    the exponential's part of the exponent (one FMA), the exponent (one
+#    FMA), exp2, s = 1 + u, reciprocal, running product, r = u V, r d, three
+#    accumulations = 1+1+1+1+7+1+3+1+1+1+3 = 21;
 #  - bin-point of the 1-D chi2 of one Gaussian + line, four points per
 #    tile: Horner 1, d 1, exponent 2, exp2 7, peak 1, residual / adjoint /
 #    value 3, peak adjoints 5, polynomial adjoints 2 = 22, plus the bin's
@@ -190,7 +191,7 @@ def measured_peaks():
 #    adjoint seed, value and constant 4 = 22; per (bin, Gaussian kept by
 #    the tile's culling): dy 1, the exponent -(u'^2 + v'^2) 4 (u', v', v'^2
 #    and one FMA), exp2 7, model 1, adjoints 2 + 3 = 18.
-FP64_INSTR = {"mix": 23, "gp1_c1": 23.25, "fit_c4": 30, "fit_c5": 72, "rg2_bin": 22, "rg2_gauss": 18}
+FP64_INSTR = {"mix": 21, "gp1_c1": 23.25, "fit_c4": 30, "fit_c5": 72, "rg2_bin": 22, "rg2_gauss": 18}
 
 # FP32-pipe operations per unit of the double-float kernels (cg_df64.cuh,
 # cg_df64.cu, cg_models_df64.cuh): event-point of the mixture: two df64
@@ -261,8 +262,8 @@ NCU_RECORDS = {
                    "profile": "profiles/k_mix_fp64_unbinned_1e7x50.md"},
     "k_gp1_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "6506c10f2d049b90", "dram_bytes": 218112, "fp64_pipe_pct": 75.48,
                    "profile": "profiles/k_gp1_fp64_c1_10000bins_100points.md"},
-    "k_rg2_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "6506c10f2d049b90", "dram_bytes": 134412032 + 4738048,
-                   "fp64_pipe_pct": 83.98, "profile": "profiles/k_rg2_fp64_c3_4096x4096.md"},
+    "k_rg2_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "323da5da32f35734", "dram_bytes": 134654208 + 4540160,
+                   "fp64_pipe_pct": 86.74, "profile": "profiles/k_rg2_fp64_c3_4096x4096.md"},
 }
 
 
@@ -506,7 +507,7 @@ def headline(args, dev, rank, world, local):
         "e2e": {"value": units / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": x_pin.numel() * 8 + th_pin.numel() * 8,
                 "d2h_bytes_per_step": v_pin.numel() * 8 + g_pin.numel() * 8},
-        "gpu_launches": 2 * args.steps,   # tile kernel + finalize per step
+        "gpu_launches": 3 * args.steps,   # chunk sums + tile kernel + finalize per step
         "kernel_ms": kern_s * 1e3,
         "clocks": clk,
     }

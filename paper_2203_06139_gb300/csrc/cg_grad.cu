@@ -139,14 +139,15 @@ __global__ void __launch_bounds__(NT) k_gp1_fp64(GP1Data d, const double* __rest
 }
 
 // The events [e0, e1) of one tile through one form of the mixture element
-// (RATIO: mix_elem_ratio, else mix_elem_f64); pairs of events per load when
-// the arrays are 16-byte aligned.
-template <bool W, int NT, bool RATIO>
+// (FORM 0: mix_elem_f64, 1: mix_elem_ratio, 2: mix_elem_lean); pairs of
+// events per load when the arrays are 16-byte aligned.
+template <bool W, int NT, int FORM>
 __device__ __forceinline__ void mix_events(const MixData& d, int64_t e0, int64_t e1, const MixConsts& cs,
                                            const MixC2& cq, const MixR2& cr, const Fp64Tab& tab,
                                            double (&acc)[MixAcc::N], LogProd& lp, bool& bad) {
     auto elem = [&](double x, double w) {
-        if constexpr (RATIO) mix_elem_ratio<W>(x, w, cs, cr, tab, acc, lp, bad);
+        if constexpr (FORM == 2) mix_elem_lean<W>(x, w, cs, cr, tab, acc, lp, bad);
+        else if constexpr (FORM == 1) mix_elem_ratio<W>(x, w, cs, cr, tab, acc, lp, bad);
         else mix_elem_f64<W>(x, w, cs, cq, tab, acc, lp, bad);
     };
     if (d.vec_ok) {
@@ -166,21 +167,73 @@ __device__ __forceinline__ void mix_events(const MixData& d, int64_t e0, int64_t
     }
 }
 
+// One tile's block sums in one form (see mix_events), the thread sums
+// finished by mix_tile_finish; returns the tile's domain flag.
+template <bool W, int NT, int FORM>
+__device__ __forceinline__ int mix_tile_sums(const MixData& d, int64_t e0, int64_t e1, const MixConsts& cs,
+                                             const MixC2& cq, const MixR2& cr, const Fp64Tab& tab, double* red,
+                                             double* tot) {
+    double acc[MixAcc::N];
+#pragma unroll
+    for (int a = 0; a < MixAcc::N; ++a) acc[a] = 0.0;
+    LogProd lp;
+    logprod_init(lp);
+    bool bad = false;
+    mix_events<W, NT, FORM>(d, e0, e1, cs, cq, cr, tab, acc, lp, bad);
+    mix_tile_finish<W>(cs, tab, acc, lp);
+    const int any_bad = __syncthreads_or(bad ? 1 : 0);
+    block_sum_rs<MixAcc::N, NT>(acc, red, tot);
+    return any_bad;
+}
+
+// Per chunk of the mixture's tile grid: sum (x - lo), and with weights sum w
+// and sum w (x - lo) (MixData::csum), one block per chunk in a fixed order.
+template <bool W, int NT>
+__global__ void __launch_bounds__(NT) k_mix_chunk_sums(MixData d, TileGrid tg, double* __restrict__ csum) {
+    __shared__ double red[3 * (NT / 32)];
+    __shared__ double tot[3];
+    if (gated_off(tg)) return;
+    for (int c = blockIdx.x; c < tg.nbx; c += gridDim.x) {
+        const int64_t e0 = (int64_t)c * tg.chunk, e1 = min(tg.n_elem, e0 + tg.chunk);
+        double a[3] = {0.0, 0.0, 0.0};
+        for (int64_t i = e0 + threadIdx.x; i < e1; i += NT) {
+            const double xl = d.x[i] - d.lo;
+            a[0] += xl;
+            if (W) {
+                const double w = d.w[i];
+                a[1] += w;
+                a[2] = fma(w, xl, a[2]);
+            }
+        }
+        block_sum_rs<3, NT>(a, red, tot);
+        if (threadIdx.x == 0) {
+            csum[c] = tot[0];
+            if (W) {
+                csum[tg.nbx + c] = tot[1];
+                csum[2 * tg.nbx + c] = tot[2];
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Unbinned Gaussian + exponential mixture, FP64: one point per tile.  A tile
 // whose point has both coefficients a, b > 0 (every point inside the
-// parameter space) takes the ratio form, one exponential per event; others
-// (a = 0 at f = 0, b <= 0 at f >= 1) take the two-exponential form.  The
-// choice is uniform over the tile and both give the same accumulators.
+// parameter space) takes the lean ratio form, one exponential and the
+// Gaussian's three sums per event; where the exponential's sums taken as
+// differences would cancel (mix_lean_sums), the tile is summed again in the
+// full ratio form.  Other points (a = 0 at f = 0, b <= 0 at f >= 1) take the
+// two-exponential form.  All three give the same accumulators.
 template <bool W, int NT>
 __global__ void __launch_bounds__(NT, 768 / NT) k_mix_fp64(MixData d, const double* __restrict__ theta,
-                                                 TileGrid tg, double* __restrict__ part,
-                                                 WsHeader* __restrict__ hdr) {
+                                                          TileGrid tg, double* __restrict__ part,
+                                                          WsHeader* __restrict__ hdr) {
     constexpr int NACC = MixAcc::N;
     __shared__ Fp64Tab tab;
     __shared__ MixConsts cs;
     __shared__ MixC2 cq;
     __shared__ MixR2 cr;
-    __shared__ int cs_bad;
+    __shared__ int cs_bad, lean_ok;
     __shared__ double red[NACC * (NT / 32)];
     __shared__ double tot[NACC];
     if (gated_off(tg)) return;
@@ -195,25 +248,44 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_mix_fp64(MixData d, const doub
         }
         __syncthreads();
         const bool ratio = cr.ok != 0;
-        double acc[NACC];
-#pragma unroll
-        for (int a = 0; a < NACC; ++a) acc[a] = 0.0;
-        LogProd lp;
-        logprod_init(lp);
-        bool bad = false;
         const int64_t e0 = (int64_t)c * tg.chunk;
         const int64_t e1 = min(tg.n_elem, e0 + tg.chunk);
-        if (ratio) mix_events<W, NT, true>(d, e0, e1, cs, cq, cr, tab, acc, lp, bad);
-        else mix_events<W, NT, false>(d, e0, e1, cs, cq, cr, tab, acc, lp, bad);
-        mix_tile_finish<W>(cs, tab, acc, lp);
-        const int any_bad = __syncthreads_or(bad ? 1 : 0) | cs_bad;
-        block_sum_rs<NACC, NT>(acc, red, tot);
+        int any_bad;
         if (ratio) {
-            if (threadIdx.x == 0) mix_ratio_sums(cs, cr, W ? tot[1] + tot[4] : (double)(e1 - e0), tot);
+            const double n_w = W ? d.csum[tg.nbx + c] : (double)(e1 - e0);
+            const double sxl = W ? d.csum[2 * tg.nbx + c] : d.csum[c];
+            any_bad = mix_tile_sums<W, NT, 2>(d, e0, e1, cs, cq, cr, tab, red, tot);
+            if (threadIdx.x == 0) lean_ok = mix_lean_sums(cs, cr, n_w, sxl, tot) ? 1 : 0;
             __syncthreads();
+            if (!lean_ok) {
+                any_bad = mix_tile_sums<W, NT, 1>(d, e0, e1, cs, cq, cr, tab, red, tot);
+                if (threadIdx.x == 0) mix_ratio_sums(cs, cr, n_w, sxl, tot);
+                __syncthreads();
+            }
+        } else {
+            any_bad = mix_tile_sums<W, NT, 0>(d, e0, e1, cs, cq, cr, tab, red, tot);
         }
-        write_partial<NACC>(part, tg, th, c, tot, any_bad);
+        write_partial<NACC>(part, tg, th, c, tot, any_bad | cs_bad);
     }
+}
+
+// The mixture's FP64 launch: the tile grid, the chunk sums, the tile kernel.
+template <bool W, int NT>
+static cg_status launch_mix_fp64(MixData d, double* csum, const double* theta, int64_t n, int64_t n_theta,
+                                 double* part, WsHeader* hdr, TileGrid* tg_out, cudaStream_t st, const int* gate) {
+    const int nsm = device_sm_count();
+    const int R = resident_blocks((const void*)k_mix_fp64<W, NT>, NT, 0);
+    TileGrid tg = make_tiles_balanced(n, n_theta, 1, NT, nsm, R);
+    tg.gate = gate;
+    k_mix_chunk_sums<W, NT><<<tg.nbx, NT, 0, st>>>(d, tg, csum);
+    d.csum = csum;
+    const int G = nsm * R;
+    const int grid = tg.n_tiles < G ? tg.n_tiles : G;
+    prof_begin(st);
+    k_mix_fp64<W, NT><<<grid, NT, 0, st>>>(d, theta, tg, part, hdr);
+    prof_end(st);
+    *tg_out = tg;
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
 }
 
 // 2-D tiles of kRgTX x kRgTY bins.  Per tile, a Gaussian whose exponent
@@ -451,8 +523,12 @@ static int num_params(const cg_problem* pb) {
 size_t grad_workspace_bytes(const cg_problem* pb, int64_t n_theta) {
     if (validate(pb) != CG_OK || n_theta < 1) return 0;
     const int nacc = acc_count(pb);
+    // then the df64 kernels' split events, or the FP64 mixture's three sums per chunk
+    const size_t mix_csum = (pb->model == CG_MODEL_MIX_GAUSS_EXP && pb->precision == CG_PREC_FP64)
+                                ? align_up((size_t)3 * max_nbx(n_theta) * sizeof(double), 256)
+                                : 0;
     return sizeof(WsHeader) + align_up((size_t)n_theta * (nacc + 1) * max_nbx(n_theta) * sizeof(double), 256) +
-           df64_split_bytes(pb);
+           df64_split_bytes(pb) + mix_csum;
 }
 
 // Points per tile of the 1-D FP64 kernel: 4 for models of at most one peak
@@ -565,10 +641,10 @@ cg_status grad_points(const cg_problem* pb, const double* theta, int64_t n_theta
         d.hi = pb->hi[0];
         d.vec_ok = (((uintptr_t)pb->data & 15) == 0) && (!pb->weights || (((uintptr_t)pb->weights & 15) == 0));
         constexpr int NT = 256;
-        if (pb->weights)
-            s = launch_tiles_balanced(k_mix_fp64<true, NT>, NT, 1, d, theta, n, n_theta, part, hdr, &tg, st, gate);
-        else
-            s = launch_tiles_balanced(k_mix_fp64<false, NT>, NT, 1, d, theta, n, n_theta, part, hdr, &tg, st, gate);
+        double* csum = (double*)((char*)ws + sizeof(WsHeader) +
+                                 align_up((size_t)n_theta * (nacc + 1) * max_nbx(n_theta) * sizeof(double), 256));
+        s = pb->weights ? launch_mix_fp64<true, NT>(d, csum, theta, n, n_theta, part, hdr, &tg, st, gate)
+                        : launch_mix_fp64<false, NT>(d, csum, theta, n, n_theta, part, hdr, &tg, st, gate);
     } else {
         RG2Data d;
         d.n = pb->data;

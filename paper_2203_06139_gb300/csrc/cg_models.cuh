@@ -157,6 +157,9 @@ struct MixData {
     int vec_ok;
     const float2* xs;   // df64 kernels: events split once per call into (hi, lo) float pairs
     const float2* wsp;  // weights split likewise (or nullptr)
+    // FP64 kernel: per chunk of the tile grid, sum (x - lo) in [0, nbx), and with
+    // weights sum w in [nbx, 2 nbx) and sum w (x - lo) in [2 nbx, 3 nbx)
+    const double* csum = nullptr;
 };
 
 __device__ __forceinline__ double std_normal_cdf(double z) { return 0.5 * erfc(-z * 0.70710678118654752440); }

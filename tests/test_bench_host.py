@@ -38,7 +38,7 @@ def test_df64_roofline_arithmetic():
 def test_instruction_counts_add_up():
     # the per-unit FP64 counts are the sums spelled out next to them
     exp2, rcp, log = 7, 3, 13
-    assert bench.FP64_INSTR["mix"] == 1 + 1 + 1 + 1 + exp2 + 1 + rcp + 1 + 1 + 1 + 5   # ratio form
+    assert bench.FP64_INSTR["mix"] == 1 + 1 + 1 + 1 + exp2 + 1 + rcp + 1 + 1 + 1 + 3   # lean ratio form
     assert bench.FP64_INSTR["gp1_c1"] == 1 + 1 + 2 + exp2 + 1 + 3 + 5 + 2 + 5 / 4
     assert bench.FP64_INSTR["fit_c4"] == 2 + 3 + 2 + (1 + 2 + exp2 + 1) + 3 + 5 + 4
     assert bench.FP64_INSTR["fit_c5"] == 2 + 1 + 3 * (1 + 2 + exp2 + 1) + log + rcp + 2 + 1 + 15 + 2

@@ -179,11 +179,14 @@ def test_mixture_weighted_and_other_range(dev):
     check(v, g, oracle.unbinned_mix(x, 1.0, 7.5, th, weights=w))
 
 
-# Points that take each form of the FP64 mixture element: the ratio form
-# (a, b > 0), the two-exponential form (a = 0 at f = 0), a ratio form whose
+# Points that take each form of the FP64 mixture element: the lean ratio
+# form (a, b > 0, the exponential's share well above 1/16), the
+# two-exponential form (a = 0 at f = 0), a ratio form whose
 # Gaussian-to-exponential ratio exceeds 2^1021 for the events near a steep
-# exponential's far end (those take the per-event fallback), and a fraction
-# next to 1 (log2(a/b) near 23).
+# exponential's far end (those take the per-event fallback), and fractions
+# next to 1 (log2(a/b) near 23: the exponential's share is so small that its
+# sums taken as differences would cancel, and the tiles are summed again in
+# the full ratio form).
 MIX_FORM_POINTS = np.array([[0.3, 2.0, 0.3, 0.5],
                             [0.0, 2.0, 0.3, 0.5],
                             [0.3, 9.0, 0.5, 100.0],
