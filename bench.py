@@ -257,13 +257,13 @@ def sources_hash(files):
 FP64_SOURCES = ["csrc/cg_grad.cu", "csrc/cg_fp64.cuh", "csrc/cg_fp64_tables.inc", "csrc/cg_models_fp64.cuh",
                 "csrc/cg_models.cuh", "csrc/cg_tiles.cuh", "csrc/cg_internal.cuh"]
 NCU_RECORDS = {
-    "k_mix_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "3504c97de2b978c2", "workload": [N_EVENTS, N_POINTS],
-                   "dram_bytes": 81056512 + 3583232, "fp64_pipe_pct": 87.00,
+    "k_mix_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "2c09d4d6b868fb9d", "workload": [N_EVENTS, N_POINTS],
+                   "dram_bytes": 80640512 + 3814144, "fp64_pipe_pct": 86.76,
                    "profile": "profiles/k_mix_fp64_unbinned_1e7x50.md"},
-    "k_gp1_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "6506c10f2d049b90", "dram_bytes": 218112, "fp64_pipe_pct": 75.48,
+    "k_gp1_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "2c09d4d6b868fb9d", "dram_bytes": 218368, "fp64_pipe_pct": 75.63,
                    "profile": "profiles/k_gp1_fp64_c1_10000bins_100points.md"},
-    "k_rg2_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "323da5da32f35734", "dram_bytes": 134654208 + 4540160,
-                   "fp64_pipe_pct": 86.74, "profile": "profiles/k_rg2_fp64_c3_4096x4096.md"},
+    "k_rg2_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "2c09d4d6b868fb9d", "dram_bytes": 134490880 + 4027648,
+                   "fp64_pipe_pct": 86.79, "profile": "profiles/k_rg2_fp64_c3_4096x4096.md"},
 }
 
 

@@ -196,14 +196,34 @@ __global__ void __launch_bounds__(NT) k_mix_chunk_sums(MixData d, TileGrid tg, d
     for (int c = blockIdx.x; c < tg.nbx; c += gridDim.x) {
         const int64_t e0 = (int64_t)c * tg.chunk, e1 = min(tg.n_elem, e0 + tg.chunk);
         double a[3] = {0.0, 0.0, 0.0};
-        for (int64_t i = e0 + threadIdx.x; i < e1; i += NT) {
-            const double xl = d.x[i] - d.lo;
+        auto add = [&](double x, double w) {
+            const double xl = x - d.lo;
             a[0] += xl;
             if (W) {
-                const double w = d.w[i];
                 a[1] += w;
                 a[2] = fma(w, xl, a[2]);
             }
+        };
+        if (d.vec_ok) {   // 8 events per thread and step, four 16-byte loads in flight (chunk starts are even)
+            for (int64_t i = e0 + 8 * threadIdx.x; i < e1; i += 8 * NT) {
+                if (i + 7 < e1) {
+                    double2 x2[4], w2[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        x2[q] = __ldg(reinterpret_cast<const double2*>(d.x + i) + q);
+                        w2[q] = W ? __ldg(reinterpret_cast<const double2*>(d.w + i) + q) : make_double2(1.0, 1.0);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        add(x2[q].x, w2[q].x);
+                        add(x2[q].y, w2[q].y);
+                    }
+                } else {
+                    for (int64_t j = i; j < e1; ++j) add(d.x[j], W ? d.w[j] : 1.0);
+                }
+            }
+        } else {
+            for (int64_t i = e0 + threadIdx.x; i < e1; i += NT) add(d.x[i], W ? d.w[i] : 1.0);
         }
         block_sum_rs<3, NT>(a, red, tot);
         if (threadIdx.x == 0) {
@@ -277,7 +297,7 @@ static cg_status launch_mix_fp64(MixData d, double* csum, const double* theta, i
     const int R = resident_blocks((const void*)k_mix_fp64<W, NT>, NT, 0);
     TileGrid tg = make_tiles_balanced(n, n_theta, 1, NT, nsm, R);
     tg.gate = gate;
-    k_mix_chunk_sums<W, NT><<<tg.nbx, NT, 0, st>>>(d, tg, csum);
+    k_mix_chunk_sums<W, 512><<<tg.nbx, 512, 0, st>>>(d, tg, csum);
     d.csum = csum;
     const int G = nsm * R;
     const int grid = tg.n_tiles < G ? tg.n_tiles : G;
