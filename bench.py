@@ -768,13 +768,14 @@ def _bin_evals(states, sizes):
 
 def _fit_to_convergence(fitter, theta0, block=50, cap=500, tol=1e-9):
     """Device time from the start to every fit CONVERGED or failed (or the
-    iteration cap): init, then blocks of iterations until no fit is RUNNING."""
+    iteration cap): init, then blocks of iterations until no fit is RUNNING.
+    theta0 may be a function that computes the starts (timed with the fits)."""
     import torch
     from paper_2203_06139_gb300 import cg
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    fitter.init(theta0)
+    fitter.init(theta0().contiguous() if callable(theta0) else theta0)
     it = 0
     while it < cap:
         fitter.step(block, tol)
@@ -954,6 +955,7 @@ def config_c5(args, rates, sm_max_mhz):
     from oracle.fit import bfgs_fit
     from paper_2203_06139_gb300 import cg, synth
     from paper_2203_06139_gb300 import learned_start as ls
+    from paper_2203_06139_gb300.fit import BatchFitter, HistBatch
     oracle.build()
     n_train = args.train_hists or 10 ** 6
     t0 = time.perf_counter()
@@ -1027,6 +1029,23 @@ def config_c5(args, rates, sm_max_mhz):
                                   "higher": int((Fp > Fr * (1 + 1e-6)).sum())},
             speedup_vs_heuristic=t_h / t_p, speedup_vs_heuristic_refined=t_r / t_p, Fp=Fp, theta=pr["theta"])
     f64 = res["fp64"]
+    # batched FP64 fits to convergence (blocks of 50 iterations until no fit
+    # is RUNNING, at most 500) from the refined heuristic and the refined
+    # learned start, the starts (rebin, network, heuristic, refinement)
+    # computed inside the timed region
+    offs_c = np.arange(H + 1, dtype=np.int64) * ls.N_BINS
+    conv = {}
+    starts = (("from_refined_heuristic_start", lambda: ls.refine_start(y, H, ls.heuristic_start(y, H))),
+              ("from_refined_learned_start", lambda: ls.refine_start(y, H, net.predict_start(*ls.rebin(y, H)))))
+    for name, start in starts:
+        fc = BatchFitter(HistBatch(y, offs_c, np.zeros(H), np.ones(H), 3, 1, cg.OBJ_POISSON_BC, poly_mode=0,
+                                   precision=cg.PREC_FP64), ls.FIT_MAP)
+        ms_c, it_c = _fit_to_convergence(fc, start)
+        stc = fc.states.status.cpu().numpy()
+        Fc = fc.states.f.cpu().numpy()
+        conv[name] = {"ms": ms_c, "iterations_run": it_c, "status_counts": np.bincount(stc, minlength=5).tolist(),
+                      "converged": int((stc == cg.FIT_CONVERGED).sum()),
+                      "at_truth_minimum_frac": float(np.mean(np.abs(Fc - Ft) <= 1e-6 * np.abs(Ft)))}
     # the plain per-histogram FP64 path on a sample, from the same (refined)
     # learned and heuristic starts as the batched paths
     yh_all = y.view(H, ls.N_BINS)
@@ -1077,6 +1096,8 @@ def config_c5(args, rates, sm_max_mhz):
                        "from_refined_learned_start": dict(plain_l, converged_frac=float(np.mean(
                            [spl[int(h)] == cg.FIT_CONVERGED for h in samp])))},
         "speedup_vs_plain_heuristic": plain_h["seconds_for_all"] / (f64["production"]["ms"] / 1e3),
+        "batched_to_convergence": dict(conv, speedup_learned_over_heuristic=(
+            conv["from_refined_heuristic_start"]["ms"] / conv["from_refined_learned_start"]["ms"])),
         "roofline": roof,
         "parity": {"what": "oracle BFGS fits of %d sampled histograms from the network's start: production minimum "
                            "at or below the oracle's (1e-6 relative) where the oracle converged" % n_orc,
@@ -1216,10 +1237,27 @@ def run_gemm(args):
         err = float(((C - ref).abs().max() / ref.abs().max()).item()) if ref is not None else None
         ms_cublas = _graph_timed(lambda: torch.matmul(A, B.t()), max(args.steps, 5), max(args.warmup, 3), flush)
         tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
-        rows.append({"M": M, "N": N, "K": K, "ms": ms, "tflops": tf, "frac_of_peak": tf / peak,
-                     "ms_eager_call": ms_call,
-                     "cublas_ms": ms_cublas, "cublas_tflops": 2.0 * M * N * K / (ms_cublas * 1e-3) / 1e12,
-                     "max_rel_err_vs_fp32": err})
+        row = {"M": M, "N": N, "K": K, "ms": ms, "tflops": tf, "frac_of_peak": tf / peak,
+               "ms_eager_call": ms_call,
+               "cublas_ms": ms_cublas, "cublas_tflops": 2.0 * M * N * K / (ms_cublas * 1e-3) / 1e12,
+               "cublas_output": "bf16 (torch.matmul of bf16 operands)", "output": "fp32",
+               "max_rel_err_vs_fp32": err}
+        if M == 65536 and N == 512:
+            # the network's inference layer: bias + GELU in the epilogue, BF16
+            # out (the bytes cuBLAS writes), no pre-activations kept
+            bias = torch.randn(N, generator=g, device="cuda") * 0.1
+            Cb = torch.empty((M, N), dtype=torch.bfloat16, device="cuda")
+            lay = lambda: cg.gemm_bf16(A, B, M, N, K, Cb=Cb, bias=bias, epilogue=cg.EPI_BIAS_GELU)
+            ms_l = _graph_timed(lay, max(args.steps, 5), max(args.warmup, 3), flush)
+            lay()
+            z = ref + bias
+            gelu = z * 0.5 * (1.0 + torch.erf(z / math.sqrt(2.0)))
+            row["bias_gelu_bf16_out"] = {
+                "ms": ms_l, "tflops": 2.0 * M * N * K / (ms_l * 1e-3) / 1e12,
+                "hbm_gbs": (M * K * 2 + N * K * 2 + M * N * 2) / (ms_l * 1e-3) / 1e9,
+                "max_abs_err_vs_fp32_over_max": float(((Cb.float() - gelu).abs().max() / gelu.abs().max()).item())}
+            del Cb, bias, z, gelu
+        rows.append(row)
         del A, B, C
     dom = rows[1]
     line = {"metric": "BF16 GEMM TFLOP/s (tcgen05, FP32 accumulate)", "workload": "gemm",

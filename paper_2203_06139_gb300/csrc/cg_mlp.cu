@@ -480,15 +480,20 @@ __global__ void __launch_bounds__(kPipeThreads) k_gemm_pipe(const __grid_constan
 // SM walks output tiles t = blockIdx.x, + gridDim.x, ... (N-tiles fastest).
 // Warp 0 = TMA producer over a kPStages ring that runs across tiles; warp 1 =
 // TMEM owner and MMA issuer into two accumulators of BN columns each (tile i
-// uses accumulator i & 1); warps 2-5 = epilogue, which drains accumulator
-// i & 1 while the MMAs of tile i + 1 go into the other, storing each lane's
-// row segment straight from the tcgen05.ld registers.  Barriers: full /
-// empty per stage, acc_full (one tcgen05.commit per tile) and acc_empty
-// (one arrival per epilogue warp) per accumulator.  Every wait is bounded;
+// uses accumulator i & 1); warps 2-9 = epilogue, which drains accumulator
+// i & 1 while the MMAs of tile i + 1 go into the other.  A warp reads the
+// TMEM lanes of its quarter (warp % 4), so two warps share each quarter and
+// take half of the tile's columns each: with bias + GELU in the epilogue
+// (an erf per element) four warps per SM were the bottleneck of the
+// network's layers.  Barriers: full / empty per stage, acc_full (one
+// tcgen05.commit per tile) and acc_empty (one arrival per epilogue warp)
+// per accumulator.  Every wait is bounded;
 // on a failed wait all roles stop, the producer waits (bounded) for its
 // issued loads and the MMA thread for a final commit before TMEM is freed.
 // ---------------------------------------------------------------------------
 constexpr int kPStages = 4;
+constexpr int kEpiWarps = 8;                                 // two per TMEM lane quarter
+constexpr int kPersistThreads = 32 * (2 + kEpiWarps);        // producer, MMA, epilogue
 
 template <int BN>
 struct PersistSmem {
@@ -496,11 +501,12 @@ struct PersistSmem {
     static constexpr int B_BYTES = BN * kBK * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
     static constexpr int PIPE = kPStages * STAGE;
-    static constexpr int XPOSE = 4 * 32 * 32 * 4;     // one 32 x 32 FP32 block per epilogue warp
+    static constexpr int XPOSE = kEpiWarps * 32 * 32 * 4;   // one 32 x 32 FP32 block per epilogue warp
     static constexpr int NBARS = 2 * kPStages + 5;   // full, empty, acc_full[2], acc_empty[2], drain
     static constexpr int TOTAL = 1024 + PIPE + XPOSE + NBARS * 8 + 16;
     static_assert(STAGE % 1024 == 0 && A_BYTES % 1024 == 0, "swizzle atoms need 1024-byte aligned tiles");
     static_assert(TOTAL <= 227 * 1024, "shared memory per CTA");
+    static_assert(BN % 64 == 0, "two epilogue warps per lane quarter take BN / 2 columns each, in steps of 32");
 };
 
 // One accumulator row segment (columns col0 .. col0 + 31 of row `row`, the
@@ -622,7 +628,7 @@ __device__ __forceinline__ void store_block_bf16(__nv_bfloat16* C, int ldc, int 
 }
 
 template <int BN>
-__global__ void __launch_bounds__(kPipeThreads, 1) k_gemm_persist(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(kPersistThreads, 1) k_gemm_persist(const __grid_constant__ CUtensorMap tmA,
                                                                   const __grid_constant__ CUtensorMap tmB,
                                                                   GemmArgs g) {
     using L = PersistSmem<BN>;
@@ -653,7 +659,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_gemm_persist(const __grid_c
         }
         for (int b = 0; b < 2; ++b) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(accf_bar(b)) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" :: "r"(acce_bar(b)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(acce_bar(b)), "r"(kEpiWarps) : "memory");
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(drain_bar) : "memory");
         *abort_flag = 0;
@@ -743,6 +749,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_gemm_persist(const __grid_c
         }
     } else {
         const int q = warp & 3;                         // TMEM lane quarter of this warp
+        const int cb = ((warp - 2) >> 2) * (BN / 2), ce = cb + BN / 2;   // its half of the columns
         auto al16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
         const bool aligned = g.ldc % 8 == 0 && al16(g.Cf) && al16(g.Cb) && al16(g.aux_in) && al16(g.aux_out) &&
                              al16(g.bias);
@@ -756,7 +763,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_gemm_persist(const __grid_c
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int m0 = (t / ntn) * kTM, n0 = (t % ntn) * BN;
-            for (int c0 = 0; c0 < BN; c0 += 32) {
+            for (int c0 = cb; c0 < ce; c0 += 32) {
                 uint32_t v[32];
                 const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c0);
                 asm volatile(
@@ -770,8 +777,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_gemm_persist(const __grid_c
                       "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
                     : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (c0 + 32 >= BN) {
-                    // the whole accumulator is in registers or stored: hand it back to the MMA warp
+                if (c0 + 32 >= ce) {
+                    // this warp's part of the accumulator is in registers or stored: hand it back
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncwarp();
                     if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(acce_bar(b)) : "memory");
@@ -890,7 +897,7 @@ cg_status launch_gemm_persist(const GemmArgs& g, cudaStream_t st) {
     if (tiles >= INT32_MAX) return CG_ERR_UNSUPPORTED;   // the kernel counts tiles in int
     const int sms = device_sm_count();
     const int grid = (int)(tiles < sms ? tiles : sms);   // one CTA per SM (shared memory and TMEM)
-    k_gemm_persist<BN><<<grid, kPipeThreads, L::TOTAL, st>>>(ta, tb, g);
+    k_gemm_persist<BN><<<grid, kPersistThreads, L::TOTAL, st>>>(ta, tb, g);
     return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
 }
 
