@@ -166,7 +166,9 @@ def measured_peaks():
 # FP64-pipe instructions per unit of work, counted from the code
 # (cg_models_fp64.cuh, cg_fp64.cuh, cg_grad.cu, cg_fit.cu):
 #  - exp2: 3 for the reduction (two additions of 1.5 * 2^40, one
-#    subtraction), 3 for the polynomial, 1 for T (1 + p) = 7;
+#    subtraction), 3 for the polynomial, 1 for T (1 + p) = 7; of an exact
+#    product a b (fexp2_prod, the peaks of the 1-D models): the same 7 with
+#    the product folded into the reduction's first and third instruction;
 #  - reciprocal: 3 FMAs after the hardware estimate; log: 13;
 #  - event-point of the mixture (lean ratio form: p = b eE (1 + u), one
 #    exp2, the exponential's sums from V = 1 - r per tile): d = x - mu, c2 d,
@@ -174,16 +176,16 @@ def measured_peaks():
 #    FMA), exp2, s = 1 + u, reciprocal, running product, r = u V, r d, three
 #    accumulations = 1+1+1+1+7+1+3+1+1+1+3 = 21;
 #  - bin-point of the 1-D chi2 of one Gaussian + line, four points per
-#    tile: Horner 1, d 1, exponent 2, exp2 7, peak 1, residual / adjoint /
-#    value 3, peak adjoints 5, polynomial adjoints 2 = 22, plus the bin's
-#    own work shared by the four points (centre: conversion + FMA; weight:
-#    3 FMAs of the reciprocal) 5 / 4 = 1.25: 23.25;
+#    tile: Horner 1, d 1, c2 d 1, exp2 of c2 d times d 7, peak 1, residual /
+#    adjoint / value 3, peak adjoints 5, polynomial adjoints 2 = 21, plus
+#    the bin's own work shared by the four points (centre: conversion + FMA;
+#    weight: 3 FMAs of the reciprocal) 5 / 4 = 1.25: 22.25;
 #  - bin-evaluation of the batched chi2 fit of one Gaussian + quadratic
-#    (one point per bin): centre 2, weight 3, Horner 2, peak 11, chi2 3,
-#    peak adjoints 5, polynomial adjoints 4 = 30;
+#    (one point per bin): centre 2, weight 3, Horner 2, peak 10, chi2 3,
+#    peak adjoints 5, polynomial adjoints 4 = 29;
 #  - bin-evaluation of the Baker-Cousins fit of three Gaussians + line: bin
-#    work 2, Horner 1, peaks 3 x 11, log 13, reciprocal 3, value 2, adjoint
-#    1, peak adjoints 15, polynomial adjoints 2 = 72 (the counts-only term
+#    work 2, Horner 1, peaks 3 x 10, log 13, reciprocal 3, value 2, adjoint
+#    1, peak adjoints 15, polynomial adjoints 2 = 69 (the counts-only term
 #    y log y - y, a log and two more instructions per bin, is summed once
 #    per histogram at the fit's init, not at every evaluation);
 #  - 2-D bin (a thread walks one column of its tile: x and the column's
@@ -191,7 +193,7 @@ def measured_peaks():
 #    adjoint seed, value and constant 4 = 22; per (bin, Gaussian kept by
 #    the tile's culling): dy 1, the exponent -(u'^2 + v'^2) 4 (u', v', v'^2
 #    and one FMA), exp2 7, model 1, adjoints 2 + 3 = 18.
-FP64_INSTR = {"mix": 21, "gp1_c1": 23.25, "fit_c4": 30, "fit_c5": 72, "rg2_bin": 22, "rg2_gauss": 18}
+FP64_INSTR = {"mix": 21, "gp1_c1": 22.25, "fit_c4": 29, "fit_c5": 69, "rg2_bin": 22, "rg2_gauss": 18}
 
 # FP32-pipe operations per unit of the double-float kernels (cg_df64.cuh,
 # cg_df64.cu, cg_models_df64.cuh): event-point of the mixture: two df64
@@ -257,12 +259,12 @@ def sources_hash(files):
 FP64_SOURCES = ["csrc/cg_grad.cu", "csrc/cg_fp64.cuh", "csrc/cg_fp64_tables.inc", "csrc/cg_models_fp64.cuh",
                 "csrc/cg_models.cuh", "csrc/cg_tiles.cuh", "csrc/cg_internal.cuh"]
 NCU_RECORDS = {
-    "k_mix_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "2c09d4d6b868fb9d", "workload": [N_EVENTS, N_POINTS],
-                   "dram_bytes": 80640512 + 3814144, "fp64_pipe_pct": 86.76,
+    "k_mix_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "c03f981ffdfb4073", "workload": [N_EVENTS, N_POINTS],
+                   "dram_bytes": 80714240 + 3789312, "fp64_pipe_pct": 86.75,
                    "profile": "profiles/k_mix_fp64_unbinned_1e7x50.md"},
-    "k_gp1_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "2c09d4d6b868fb9d", "dram_bytes": 218368, "fp64_pipe_pct": 75.63,
-                   "profile": "profiles/k_gp1_fp64_c1_10000bins_100points.md"},
-    "k_rg2_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "2c09d4d6b868fb9d", "dram_bytes": 134490880 + 4027648,
+    "k_gp1_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "c03f981ffdfb4073", "dram_bytes": 227840 + 0,
+                   "fp64_pipe_pct": 74.72, "profile": "profiles/k_gp1_fp64_c1_10000bins_100points.md"},
+    "k_rg2_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "c03f981ffdfb4073", "dram_bytes": 134618624 + 4046336,
                    "fp64_pipe_pct": 86.79, "profile": "profiles/k_rg2_fp64_c3_4096x4096.md"},
 }
 

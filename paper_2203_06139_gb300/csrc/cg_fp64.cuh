@@ -20,7 +20,9 @@
 //  the factor 2^(n >> 12) is an integer add to the exponent field.  Error:
 //  table 0.5 ulp + final rounding 0.5 ulp + polynomial below 0.1 ulp.
 //  Callers fold log2(e) into their per-point constants, so e^q is computed
-//  as exp2 of q log2(e) with no extra instruction.
+//  as exp2 of q log2(e) with no extra instruction.  For an exponent that is
+//  a product a b (a peak's c2 d x d) the product is folded into the
+//  reduction (fexp2_prod): one instruction fewer and no rounding of a b.
 //
 //  reciprocal: the hardware estimate rcp.approx.ftz.f64 refined by one
 //  third-order Newton-Raphson step, r = r0 (1 + e + e^2) with e = 1 - p r0
@@ -119,6 +121,39 @@ __device__ __forceinline__ double fexp2(double y, const Fp64Tab& tab) {
         return exp2_slow(y, tab);
     }
     return exp2_core(y, tab);
+}
+
+// 2^(a b) of the exact product a b: the product enters the reduction itself,
+// ks = fma(a, b, S) rounds a b to the 1/4096 grid and r = fma(a, b, -kd) is
+// the exact remainder, so the product is never rounded on its own (no
+// |a b| 2^-53 error from it) and takes no instruction of its own: 7 FP64
+// instructions against 8 for fexp2(a * b).  Far tails first, by integer
+// tests alone: the high word of |x| read as a fixed-point number with 20
+// fraction bits is 1023 + e + m for |x| = 2^e (1 + m), a lower bound of
+// 1023 + log2 |x| (m <= log2(1 + m) on [0, 1]), so the two high words add up
+// to at most 2046 + log2 |a b|; from 2046 + log2(1076) on, 2^(a b) is 0 for
+// a finite negative product (the far side of a narrow peak, most bins of a
+// wide histogram) without any FP64 instruction.  Overflow, infinities and
+// NaN, and 1022 <= |kd| below that bound, go to fexp2 of the rounded
+// product.
+__device__ __forceinline__ double fexp2_prod(double a, double b, const Fp64Tab& tab) {
+    const int ha = __double2hiint(a), hb = __double2hiint(b);
+    if ((unsigned)(ha & 0x7fffffff) + (unsigned)(hb & 0x7fffffff) >= 2155947190U) {   // |a b| >= 1076, or inf / NaN
+        const bool finite = (ha & 0x7ff00000) != 0x7ff00000 && (hb & 0x7ff00000) != 0x7ff00000;
+        if (finite && (ha ^ hb) < 0) return 0.0;                          // a b <= -1076
+        return fexp2(a * b, tab);
+    }
+    const double S = 1649267441664.0;          // 1.5 * 2^40: ulp 2^-12
+    const double ks = fma(a, b, S);            // S + n / 4096, n = round(4096 a b)
+    const double kd = ks - S;                  // n / 4096 (exact)
+    if ((__double2hiint(kd) & 0x7fffffff) >= 0x408ff000) return fexp2(a * b, tab);
+    const double r = fma(a, b, -kd);           // a b - n / 4096, |r| <= 2^-13 (one rounding below 2^-66)
+    const int n = __double2loint(ks);
+    const double t = tab.exp2[n & (kExp2N - 1)];
+    const double b1 = 0.6931471805599453, b2 = 0.24022650695910072, b3 = 0.05550410866482158;
+    const double p = r * fma(r, fma(r, b3, b2), b1);
+    const double v = fma(t, p, t);
+    return __hiloint2double(__double2hiint(v) + (n >> kExp2Bits) * (1 << 20), __double2loint(v));
 }
 
 // e^q = 2^(q log2 e); the kernels fold log2(e) into their constants instead.

@@ -91,7 +91,7 @@ __device__ __forceinline__ void gp1_elem_f64(const GP1Bin& b, const GP1Consts& c
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         dk[k] = b.x - cs.mu[k];
-        ek[k] = fexp2((c2.c2[k] * dk[k]) * dk[k], tab);
+        ek[k] = fexp2_prod(c2.c2[k] * dk[k], dk[k], tab);
         f = fma(cs.A[k], ek[k], f);
     }
     double g;

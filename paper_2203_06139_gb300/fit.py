@@ -349,6 +349,20 @@ def _autotune_key(batch, n_steps):
         c.precision, c.poly_mode, n_steps)
 
 
+def pick_map(timings, tie=0.02):
+    """The map to use from (ms, map dict) pairs: among the maps within
+    `tie` of the fastest (timing noise), the one with the smallest clusters,
+    then the largest CTAs.  Smaller clusters synchronise less per
+    evaluation, which sets the pace once only a few long fits are left: on
+    the 4096-histogram workload a map with clusters of 8 x 128 threads tied
+    with clusters of 2 x 256 over 50 iterations (50.9 against 51.1 ms) but
+    took 2.0 s instead of 0.14 s to bring every fit to convergence."""
+    fastest = min(t for t, _ in timings)
+    near = [(m["cluster_size"], -m["cta_threads"], t, i) for i, (t, m) in enumerate(timings)
+            if t <= fastest * (1.0 + tie)]
+    return timings[min(near)[3]][1]
+
+
 def autotune(batch, theta0, candidates=None, n_steps=5, tol=1e-9, use_cache=True):
     """Time n_steps BFGS iterations of the whole batch under each candidate map
     and return (best_map, timings).  Time the iteration count the fit will
@@ -385,7 +399,7 @@ def autotune(batch, theta0, candidates=None, n_steps=5, tol=1e-9, use_cache=True
         torch.cuda.synchronize()
         timings.append((e0.elapsed_time(e1), m.as_dict()))
     timings.sort(key=lambda t: t[0])
-    best = TileMap(**timings[0][1])
+    best = TileMap(**pick_map(timings))
     if use_cache:
         cache[key] = {"map": best.as_dict(), "timings": timings, "when": time.time()}
         try:

@@ -38,7 +38,26 @@ __global__ void k_logprod(const double* __restrict__ p, int groups, double* __re
     out[g] = logprod_log(s, tab);
 }
 
+// 2^(a b) through the product folded into the reduction, and CUDA's exp2 of
+// the rounded product beside it.
+__global__ void k_exp2_prod(const double* __restrict__ a, const double* __restrict__ b, int n,
+                            double* __restrict__ out) {
+    __shared__ Fp64Tab tab;
+    fp64_tab_load(tab);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[2 * (size_t)i] = fexp2_prod(a[i], b[i], tab);
+    out[2 * (size_t)i + 1] = exp2(a[i] * b[i]);
+}
+
 }  // namespace
+
+extern "C" int fp64_exp2_prod(const double* a, const double* b, int n, double* out) {
+    k_exp2_prod<<<(n + 255) / 256, 256>>>(a, b, n, out);
+    if (cudaGetLastError() != cudaSuccess) return 1;
+    return cudaDeviceSynchronize() == cudaSuccess ? 0 : 2;
+}
 
 extern "C" int fp64_check(const double* y, const double* p, int n, double* out) {
     k_check<<<(n + 255) / 256, 256>>>(y, p, n, out);

@@ -6,7 +6,9 @@ special values (overflow, underflow, subnormal results, NaN); the
 reciprocal within 1 ulp of the correctly rounded quotient; log (table
 driven, Tang 1990) within 3 ulp of CUDA's log (the two are within 1.9 and
 1 ulp of the exact value), next to 1 as well; the running-product sum of
-logs within its error bound of an exact sum of correctly rounded logs.
+logs within its error bound of an exact sum of correctly rounded logs;
+exp2 of an exact product (the product folded into the reduction) within 1
+ulp of the correctly rounded 2^(a b), with no error from rounding a b.
 """
 import ctypes
 import math
@@ -31,6 +33,7 @@ def helper(tmp_path_factory):
     L = ctypes.CDLL(so)
     L.fp64_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
     L.fp64_logprod.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    L.fp64_exp2_prod.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
     return L, torch
 
 
@@ -108,3 +111,54 @@ def test_running_product_sum_of_logs(helper):
     # 64 products at 2^-53 each, the logs' own ulps, the final rounding
     bound = 64 * 2.0 ** -53 + np.abs(lg).sum(1) * 2.0 ** -52 + 2 * np.spacing(np.abs(ref))
     assert np.all(np.abs(got - ref) <= bound)
+
+
+def _exp2_prod(helper, a, b):
+    L, torch = helper
+    ad, bd = torch.tensor(a, device="cuda"), torch.tensor(b, device="cuda")
+    out = torch.empty(2 * len(a), dtype=torch.float64, device="cuda")
+    assert L.fp64_exp2_prod(ctypes.c_void_p(ad.data_ptr()), ctypes.c_void_p(bd.data_ptr()), len(a),
+                            ctypes.c_void_p(out.data_ptr())) == 0
+    return out.cpu().numpy().reshape(-1, 2)
+
+
+def test_exp2_of_an_exact_product(helper):
+    """2^(a b) from the exact product: against 2^(a b) to 40 digits (the
+    product exact in rationals), within 1 ulp, over exponents of -1000 to
+    1000 and the narrow-peak form a = c2 d, b = d; CUDA's exp2 of the
+    rounded product is off by up to |a b| 2^-53 ln 2 relative in comparison."""
+    import decimal
+    from fractions import Fraction
+    rng = np.random.default_rng(11)
+    n = 3000
+    d = rng.uniform(-3.0, 3.0, n)
+    c2 = -rng.uniform(0.5, 110.0, n)
+    a = np.concatenate([c2 * d, rng.uniform(-40.0, 40.0, n)])
+    b = np.concatenate([d, rng.uniform(-25.0, 25.0, n)])
+    o = _exp2_prod(helper, a, b)
+    ctx = decimal.Context(prec=40)
+    ln2 = ctx.ln(decimal.Decimal(2))
+    ref = np.empty(len(a))
+    for i in range(len(a)):
+        q = Fraction(float(a[i])) * Fraction(float(b[i]))
+        y = ctx.divide(decimal.Decimal(q.numerator), decimal.Decimal(q.denominator))
+        ref[i] = float(ctx.exp(ctx.multiply(y, ln2)))
+    ok = np.abs(a * b) < 1000
+    assert ok.sum() > 5000
+    assert _ulps(o[ok, 0], ref[ok]).max() <= 1
+    # the rounded product costs CUDA's exp2 more than that for large exponents
+    assert _ulps(o[ok, 1], ref[ok]).max() > 1
+
+
+def test_exp2_of_a_product_outside_the_fast_range(helper):
+    """|a b| >= 1022, infinities and NaN: the same values as exp2 of the
+    rounded product (overflow to infinity, subnormal results, zero), also
+    through the integer early exit for |a| |b| >= 2^11."""
+    a = np.array([1024.0, 2.0, -1075.0, -1.0, 1e300, -1e300, np.inf, np.nan, 0.0, 1022.0, -1021.9999, 3.0,
+                  -3000.0, 50.0, 2000.0, -1.5, -np.inf, 1e-310, -2048.0, 1023.9, -1100.0, -33.0, 4.9e-324])
+    b = np.array([1.0, 511.25, 1.0, 1074.5, 1e10, 1e10, 1.0, 1.0, np.inf, 1.0, 1.0, -340.7,
+                  1.0, -50.0, 2.0, 1400.0, 2.0, 1e300, 1.0, -1.0, 1.0, 33.0, 1.7e308])
+    o = _exp2_prod(helper, a, b)
+    for k in range(len(a)):
+        x, e = o[k, 0], o[k, 1]
+        assert (np.isnan(x) and np.isnan(e)) or x == e or _ulps(np.array([x]), np.array([e]))[0] <= 1, (a[k], b[k], x, e)
