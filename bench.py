@@ -259,12 +259,12 @@ def sources_hash(files):
 FP64_SOURCES = ["csrc/cg_grad.cu", "csrc/cg_fp64.cuh", "csrc/cg_fp64_tables.inc", "csrc/cg_models_fp64.cuh",
                 "csrc/cg_models.cuh", "csrc/cg_tiles.cuh", "csrc/cg_internal.cuh"]
 NCU_RECORDS = {
-    "k_mix_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "c03f981ffdfb4073", "workload": [N_EVENTS, N_POINTS],
+    "k_mix_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "f386c73b18e26683", "workload": [N_EVENTS, N_POINTS],
                    "dram_bytes": 80714240 + 3789312, "fp64_pipe_pct": 86.75,
                    "profile": "profiles/k_mix_fp64_unbinned_1e7x50.md"},
-    "k_gp1_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "c03f981ffdfb4073", "dram_bytes": 227840 + 0,
+    "k_gp1_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "f386c73b18e26683", "dram_bytes": 227840 + 0,
                    "fp64_pipe_pct": 74.72, "profile": "profiles/k_gp1_fp64_c1_10000bins_100points.md"},
-    "k_rg2_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "c03f981ffdfb4073", "dram_bytes": 134618624 + 4046336,
+    "k_rg2_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "f386c73b18e26683", "dram_bytes": 134618624 + 4046336,
                    "fp64_pipe_pct": 86.79, "profile": "profiles/k_rg2_fp64_c3_4096x4096.md"},
 }
 
