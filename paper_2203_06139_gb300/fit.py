@@ -342,11 +342,16 @@ def _cache_path():
     return os.environ.get("CG_AUTOTUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "cg_autotune.json"))
 
 
+# Version of the selection rule (pick_map) in the cache key: entries chosen
+# by an earlier rule are not reused.
+_PICK_RULE = "pick2"
+
+
 def _autotune_key(batch, n_steps):
     c = batch.pb.c
-    return "%s|%s|K%dD%dP%d|obj%d|prec%d|pm%d|S%d" % (
+    return "%s|%s|K%dD%dP%d|obj%d|prec%d|pm%d|S%d|%s" % (
         torch.cuda.get_device_name(), _size_signature(batch.sizes), batch.K, batch.D, batch.P, c.objective,
-        c.precision, c.poly_mode, n_steps)
+        c.precision, c.poly_mode, n_steps, _PICK_RULE)
 
 
 def pick_map(timings, tie=0.02):
