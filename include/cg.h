@@ -225,6 +225,14 @@ cg_status cg_gemm_bf16(const void *A, const void *B, int M, int N, int K, int ld
                        int transB, float *Cf, void *Cb, int ldc, const float *bias, const float *aux_in,
                        float *aux_out, int epilogue, int *err, void *stream);
 
+/* Failure detection (not in the paper): every wait of the kernels above on
+ * another role or on the tensor core is bounded (about 1 s) and, when it
+ * gives up, sets bit 0 of `err` and lets the kernel end with nothing in
+ * flight.  This call runs that wait on a barrier that nothing completes, so
+ * that a test can see the limit work: after about 1 s bit 0 of *err (device
+ * int) is set; the context stays usable.  CG_ERR_INVALID_ARG for a NULL err. */
+cg_status cg_check_wait_timeout(int *err, void *stream);
+
 /* Rebinning for the network input: x[h][j] = bf16(r_j / max_j r_j) with
  * r_j the sum of `factor` consecutive counts of histogram h (y: device
  * [H][n_bins] FP64, x: device [H][n_bins/factor] bf16); scale[h] = max_j r_j. */

@@ -89,6 +89,7 @@ def lib():
         "cg_gemm_bf16": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp,
                                         _vp, ctypes.c_int, _vp, _vp]),
+        "cg_check_wait_timeout": (ctypes.c_int, [_vp, _vp]),
         "cg_fit_workspace_size": (_sz, [B]),
         "cg_fit_plan": (ctypes.c_int, [B, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_TileMap), _vp, _sz, _vp]),
         "cg_fit_init": (ctypes.c_int, [B, ctypes.POINTER(_TileMap), _dp, _vp, _vp, _sz, _vp]),
@@ -273,6 +274,15 @@ def gemm_bf16(A, B, M, N, K, transA=0, transB=0, Cf=None, Cb=None, bias=None, au
            "cg_gemm_bf16")
 
 
+def check_wait_timeout(err, stream=None):
+    """Run the kernels' bounded wait on a barrier that nothing completes
+    (cg_check_wait_timeout): bit 0 of err (int32 CUDA tensor) is set once the
+    wait gives up, after about a second."""
+    if err.dtype != torch.int32 or not err.is_cuda:
+        raise CgError(ERR_INVALID_ARG, "err must be an int32 CUDA tensor")
+    _check(lib().cg_check_wait_timeout(_ptr(err), _stream(stream)), "cg_check_wait_timeout")
+
+
 def batch_objective(pb, thetas, values=None, stream=None):
     """Objective values [H] at H parameter points (no gradient; value-only kernels where available)."""
     thetas = _dev_f64(thetas, "thetas")
@@ -290,3 +300,4 @@ def batch_objective(pb, thetas, values=None, stream=None):
 cg_objective = objective
 cg_gradient = gradient
 cg_batch_gradient = batch_gradient
+cg_check_wait_timeout = check_wait_timeout

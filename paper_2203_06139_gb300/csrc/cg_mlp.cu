@@ -934,9 +934,31 @@ cg_status gemm_bf16(const GemmArgs& g, cudaStream_t st) {
     return launch_gemm_bn<128>(g, st);
 }
 
+// Failure detection: the bounded wait of the GEMM pipelines (pipe_wait,
+// pipe_fail) on an mbarrier that nothing ever completes.  The wait gives up
+// after kWaitCycles, sets bit 0 of err and the kernel returns: nothing is in
+// flight, so the context stays usable.
+__global__ void k_wait_check(int* err) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = smem_addr(&bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b) : "memory");
+    abort_flag = 0;
+    // phase 0 completes on one arrival, which never comes
+    if (!pipe_wait(b, 0u, &abort_flag)) pipe_fail(&abort_flag, err);
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" :: "r"(b) : "memory");
+}
+
 }  // namespace cg
 
 using namespace cg;
+
+extern "C" cg_status cg_check_wait_timeout(int* err, void* stream) {
+    if (!err) return CG_ERR_INVALID_ARG;
+    k_wait_check<<<1, 32, 0, (cudaStream_t)stream>>>(err);
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
+}
 
 extern "C" cg_status cg_gemm_bf16(const void* A, const void* B, int M, int N, int K, int lda, int ldb, int transA,
                                   int transB, float* Cf, void* Cb, int ldc, const float* bias, const float* aux_in,

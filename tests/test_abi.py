@@ -63,6 +63,8 @@ def test_host_side_validation_without_gpu(lib):
     assert lib.cg_gradient(ctypes.byref(p), ctypes.c_void_p(256), ctypes.c_void_p(512), ctypes.c_void_p(768),
                            ctypes.c_void_p(1025), 1 << 30, None) == cg.ERR_WORKSPACE
     assert lib.cg_status_string(cg.ERR_DOMAIN).startswith(b"domain")
+    # the bounded-wait check refuses a missing status word before any launch
+    assert lib.cg_check_wait_timeout(None, None) == cg.ERR_INVALID_ARG
 
 
 def test_df64_tables_match_their_generator():
