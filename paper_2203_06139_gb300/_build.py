@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-split-compile=0"]
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + BUILD, "-split-compile=0"]
 
 
 def _nvcc():
@@ -43,11 +43,27 @@ def up_to_date():
     return all(os.path.getmtime(f) <= t for f in _deps() + [__file__])
 
 
+def write_fp64_text():
+    """_build/cg_fp64_text.inc: the text of csrc/cg_fp64.cuh as a C string,
+    handed by cg_expr.cu to NVRTC so that generated kernels use the same FP64
+    functions as the hand-written ones."""
+    text = open(os.path.join(CSRC, "cg_fp64.cuh")).read()
+    delim = "CGFP64TEXT"
+    assert (")" + delim) not in text
+    out = ("// Generated by _build.py from csrc/cg_fp64.cuh: do not edit.\n"
+           "static const char kCgFp64Text[] = R\"%s(%s)%s\";\n" % (delim, text, delim))
+    path = os.path.join(BUILD, "cg_fp64_text.inc")
+    if not os.path.exists(path) or open(path).read() != out:
+        with open(path, "w") as f:
+            f.write(out)
+
+
 def build(force=False, verbose=False, extra_flags=()):
     """Compile and link libcg.so if anything changed; returns its path."""
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    write_fp64_text()
     nvcc = _nvcc()
 
     def compile_one(src):

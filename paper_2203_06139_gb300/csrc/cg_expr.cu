@@ -13,7 +13,12 @@
 //                 and the reverse sweep of the parameter-only part seeded
 //                 with those sums (the epilogue),
 // compiles it with NVRTC (loaded with dlopen at first use) for the current
-// device's architecture and loads it through the driver entry points.
+// device's architecture and loads it through the driver entry points.  The
+// per-element exponentials, logarithms and divisions of cgx_tiles use the
+// table-driven FP64 functions of cg_fp64.cuh (its text handed to NVRTC as an
+// in-memory header; the tables are libcg's own, copied into shared memory
+// from pointers passed at launch); the per-point prologue and the finalize
+// keep CUDA's functions.
 //
 // Node classes: constant (no parameter, no element input), parameter-only
 // (evaluated once per point: the prologue), input-only (per element, no
@@ -36,6 +41,8 @@
 #include <string>
 #include <vector>
 
+#include "cg_fp64.cuh"
+#include "cg_fp64_text.inc"   // kCgFp64Text: the text of cg_fp64.cuh (written by _build.py)
 #include "cg_internal.cuh"
 
 // NVRTC entry points (resolved with dlsym; no link-time dependency)
@@ -51,6 +58,9 @@ typedef nvrtcResult_t (*fn_nvrtcDestroyProgram)(nvrtcProgram_t*);
 struct cg_expr_program {
     std::string source, log;
     int n_params = 0, n_inputs = 0, n_acc = 0, device = -1, value_only = 0;
+    const double* t_exp2 = nullptr;   // libcg's FP64 tables on the program's device
+    const double* t_log = nullptr;
+    const double* t_invf = nullptr;
     CUmodule mod = nullptr;
     CUfunction f_tiles = nullptr, f_fin = nullptr;
 };
@@ -199,6 +209,14 @@ std::string g(int j) { return "g" + std::to_string(j); }
 
 std::string rv(int j) { return "r" + std::to_string(j); }
 
+// The element's functions in cgx_tiles (fast = true): the table-driven FP64
+// functions on the block's tables `tab`; CUDA's elsewhere.
+std::string f_exp(const std::string& a, bool fast) { return fast ? "cg::fexp(" + a + ", tab)" : "exp(" + a + ")"; }
+std::string f_log(const std::string& a, bool fast) { return fast ? "cg::flog(" + a + ", tab)" : "log(" + a + ")"; }
+std::string f_div(const std::string& a, const std::string& b, bool fast) {
+    return fast ? a + " * cg::frcp_any(" + b + ")" : a + " / " + b;
+}
+
 // Value of node j from the values of its operands.  recip: the divisor of a
 // DIV is fixed per point and its reciprocal rv(b) is available.
 std::string forward_expr(const cg_expr_node& x, bool in_tiles, bool recip = false) {
@@ -212,10 +230,10 @@ std::string forward_expr(const cg_expr_node& x, bool in_tiles, bool recip = fals
         case CG_EX_ADD: return a + " + " + b;
         case CG_EX_SUB: return a + " - " + b;
         case CG_EX_MUL: return a + " * " + b;
-        case CG_EX_DIV: return a + " / " + b;
+        case CG_EX_DIV: return f_div(a, b, in_tiles);
         case CG_EX_NEG: return "-" + a;
-        case CG_EX_EXP: return "exp(" + a + ")";
-        case CG_EX_LOG: return "log(" + a + ")";
+        case CG_EX_EXP: return f_exp(a, in_tiles);
+        case CG_EX_LOG: return f_log(a, in_tiles);
         case CG_EX_SQRT: return "sqrt(" + a + ")";
         case CG_EX_ERFC: return "erfc(" + a + ")";
         case CG_EX_POWI: {
@@ -223,15 +241,17 @@ std::string forward_expr(const cg_expr_node& x, bool in_tiles, bool recip = fals
             std::string t = a;
             const int m = x.i < 0 ? -x.i : x.i;
             for (int k = 1; k < m; ++k) t += " * " + a;
-            return x.i < 0 ? "1.0 / (" + t + ")" : "(" + t + ")";
+            return x.i < 0 ? f_div("1.0", "(" + t + ")", in_tiles) : "(" + t + ")";
         }
         case CG_EX_MAX: return "(" + a + " >= " + b + " ? " + a + " : " + b + ")";
     }
     return "0.0";
 }
 
-// Adjoint contributions of node j (adjoint gj) to its operands: (operand, partial).
-std::vector<std::pair<int, std::string>> partials(const cg_expr_node& x, int j, bool recip = false) {
+// Adjoint contributions of node j (adjoint gj) to its operands: (operand,
+// partial); fast as for forward_expr's in_tiles.
+std::vector<std::pair<int, std::string>> partials(const cg_expr_node& x, int j, bool recip = false,
+                                                  bool fast = false) {
     const std::string a = x.a >= 0 ? v(x.a) : "", b = x.b >= 0 ? v(x.b) : "", vj = v(j);
     std::vector<std::pair<int, std::string>> r;
     if (x.op == CG_EX_DIV && recip) return {{x.a, rv(x.b)}, {x.b, "-" + vj + " * " + rv(x.b)}};
@@ -239,12 +259,12 @@ std::vector<std::pair<int, std::string>> partials(const cg_expr_node& x, int j, 
         case CG_EX_ADD: r = {{x.a, "1.0"}, {x.b, "1.0"}}; break;
         case CG_EX_SUB: r = {{x.a, "1.0"}, {x.b, "-1.0"}}; break;
         case CG_EX_MUL: r = {{x.a, b}, {x.b, a}}; break;
-        case CG_EX_DIV: r = {{x.a, "1.0 / " + b}, {x.b, "-" + vj + " / " + b}}; break;
+        case CG_EX_DIV: r = {{x.a, f_div("1.0", b, fast)}, {x.b, f_div("-" + vj, b, fast)}}; break;
         case CG_EX_NEG: r = {{x.a, "-1.0"}}; break;
         case CG_EX_EXP: r = {{x.a, vj}}; break;
-        case CG_EX_LOG: r = {{x.a, "1.0 / " + a}}; break;
-        case CG_EX_SQRT: r = {{x.a, "0.5 / " + vj}}; break;
-        case CG_EX_ERFC: r = {{x.a, "(-1.1283791670955125739 * exp(-" + a + " * " + a + "))"}}; break;
+        case CG_EX_LOG: r = {{x.a, f_div("1.0", a, fast)}}; break;
+        case CG_EX_SQRT: r = {{x.a, f_div("0.5", vj, fast)}}; break;
+        case CG_EX_ERFC: r = {{x.a, "(-1.1283791670955125739 * " + f_exp("-" + a + " * " + a, fast) + ")"}}; break;
         case CG_EX_POWI: {
             if (x.i == 0) break;
             // d a^i / da = i a^(i-1)
@@ -254,7 +274,7 @@ std::vector<std::pair<int, std::string>> partials(const cg_expr_node& x, int j, 
             else if (m < 0) {
                 std::string d = a;
                 for (int k = 1; k < -m; ++k) d += " * " + a;
-                t += " / (" + d + ")";
+                t = f_div(t, "(" + d + ")", fast);
             }
             r = {{x.a, "(" + t + ")"}};
             break;
@@ -286,11 +306,13 @@ std::string generate(const cg_expr_node* nd, int n, int P, int NI, const Plan& p
     const int NR = (int)recip_po.size();
     std::string s;
     s += "// Generated by libcg (cg_expr_compile): the per-element term and its reverse-mode adjoint.\n";
+    s += "#include \"cg_fp64.cuh\"\n";
     s += "typedef long long i64;\n";
     s += "#define NACC " + std::to_string(NACC) + "\n";
     s += "#define NPAR " + std::to_string(P) + "\n";
     s += "struct Args { const double* in0; const double* in1; const double* in2; const double* in3; i64 n;\n"
-         "  const double* theta; int n_theta; i64 chunk; int nbx; int n_tiles; double* part; };\n";
+         "  const double* theta; int n_theta; i64 chunk; int nbx; int n_tiles; double* part;\n"
+         "  const double* t_exp2; const double* t_log; const double* t_invf; };\n";
     s += "__device__ __forceinline__ double warp_sum(double x) {\n"
          "  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);\n  return x;\n}\n";
     // ---------------- tile kernel ----------------
@@ -298,6 +320,12 @@ std::string generate(const cg_expr_node* nd, int n, int P, int NI, const Plan& p
     s += "  __shared__ double fr_s[" + std::to_string(NF + NR > 0 ? NF + NR : 1) + "];\n";
     s += "  __shared__ double red[NACC * 8];\n";
     s += "  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;\n";
+    s += "  __shared__ cg::Fp64Tab tab;   // libcg's FP64 tables, copied once per block\n"
+         "  for (int i = threadIdx.x; i < cg::kExp2N / 2; i += blockDim.x)\n"
+         "    reinterpret_cast<double2*>(tab.exp2)[i] = __ldg(reinterpret_cast<const double2*>(a.t_exp2) + i);\n"
+         "  for (int i = threadIdx.x; i < cg::kLogN; i += blockDim.x)\n"
+         "    tab.logf[i] = make_double2(__ldg(a.t_log + i), __ldg(a.t_invf + i));\n"
+         "  __syncthreads();\n";
     s += "  for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {\n";
     s += "    const int c = t / a.n_theta, th = t - c * a.n_theta;   // chunk-major tiles\n";
     s += "    const double* tp = a.theta + (i64)th * NPAR;\n";
@@ -333,7 +361,7 @@ std::string generate(const cg_expr_node* nd, int n, int P, int NI, const Plan& p
                 s += "      double " + g(j) + " = " + (j == root ? "1.0" : "0.0") + ";\n";
         for (int j = root; j >= 0; --j) {
             if (pl.cls[j] != K_MIXED) continue;
-            for (auto& pr : partials(nd[j], j, recip_div(j))) {
+            for (auto& pr : partials(nd[j], j, recip_div(j), true)) {
                 const int o = pr.first;
                 if (o < 0) continue;
                 if (pl.cls[o] == K_MIXED || pl.front_slot[o] >= 0)
@@ -444,8 +472,22 @@ cg_status cg_expr_compile(const cg_expr_node* nodes, int n_nodes, int n_params, 
         return CG_ERR_UNSUPPORTED;
     }
     cudaGetDevice(&p->device);
+    if (cudaGetSymbolAddress((void**)&p->t_exp2, g_exp2_tab) != cudaSuccess ||
+        cudaGetSymbolAddress((void**)&p->t_log, g_log_tab) != cudaSuccess ||
+        cudaGetSymbolAddress((void**)&p->t_invf, g_invf_tab) != cudaSuccess) {
+        delete p;
+        return CG_ERR_CUDA;
+    }
+    // cg_fp64.cuh as an in-memory header; its table file and the C headers it
+    // names are stand-ins (the kernels read libcg's tables through pointers)
+    static const char kTablesStub[] =
+        "static __device__ __align__(16) const double g_exp2_tab[2] = {0.0, 0.0};\n"
+        "static __device__ const double g_log_tab[1] = {0.0};\n"
+        "static __device__ const double g_invf_tab[1] = {0.0};\n";
+    const char* hdr_src[] = {kCgFp64Text, kTablesStub, "", ""};
+    const char* hdr_name[] = {"cg_fp64.cuh", "cg_fp64_tables.inc", "math.h", "stdint.h"};
     nvrtcProgram_t prog = nullptr;
-    if (nv.create(&prog, p->source.c_str(), "cg_expr.cu", 0, nullptr, nullptr) != 0) {
+    if (nv.create(&prog, p->source.c_str(), "cg_expr.cu", 4, hdr_src, hdr_name) != 0) {
         delete p;
         return CG_ERR_CUDA;
     }
@@ -510,6 +552,9 @@ cg_status cg_expr_gradient(const cg_expr_program* prog, const double* const* inp
         int nbx;
         int n_tiles;
         double* part;
+        const double* t_exp2;
+        const double* t_log;
+        const double* t_invf;
     } args;
     memset(&args, 0, sizeof(args));
     for (int k = 0; k < prog->n_inputs; ++k) args.in[k] = inputs[k];
@@ -520,6 +565,9 @@ cg_status cg_expr_gradient(const cg_expr_program* prog, const double* const* inp
     args.nbx = g.nbx;
     args.n_tiles = g.n_tiles;
     args.part = (double*)ws;
+    args.t_exp2 = prog->t_exp2;
+    args.t_log = prog->t_log;
+    args.t_invf = prog->t_invf;
     void* p1[] = {&args};
     CUstream st = (CUstream)stream;
     prof_begin((cudaStream_t)stream);

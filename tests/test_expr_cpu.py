@@ -109,14 +109,19 @@ def test_compile_rejects_malformed_programs_on_the_host():
 def test_generated_source_hoists_the_parameter_only_part():
     """The CUDA source written for the mixture: deterministic; the divisions
     by per-point values (2 s^2, the Gaussian's normalisation, Z_E) are products
-    with reciprocals taken once per point, so the element loop divides only
-    where the adjoint of the log needs 1/p."""
+    with reciprocals taken once per point, so the element loop takes a
+    reciprocal only where the adjoint of the log needs 1/p, and its
+    exponentials, logarithm and reciprocal are the table-driven FP64
+    functions of cg_fp64.cuh (CUDA's stay in the per-point prologue)."""
     src = E.generated_source(mixture_nll(0.0, 10.0), 4, 1)
     assert src == E.generated_source(mixture_nll(0.0, 10.0), 4, 1)
     assert "extern \"C\" __global__ void __launch_bounds__(256) cgx_tiles" in src
     assert "cgx_finalize" in src
+    assert '#include "cg_fp64.cuh"' in src and "__shared__ cg::Fp64Tab tab;" in src
     loop = src[src.index("for (i64 e = e0"):src.index("for (int k = 0; k < NACC; ++k) {\n      const double w")]
-    assert loop.count(" / ") == 1 and loop.count(" * r") >= 3
+    assert loop.count(" / ") == 0 and loop.count("cg::frcp_any(") == 1 and loop.count(" * r") >= 3
+    assert loop.count("cg::fexp(") == 2 and loop.count("cg::flog(") == 1
+    assert "exp(" not in loop.replace("cg::fexp(", "") and "log(" not in loop.replace("cg::flog(", "")
     assert "#define NACC 9" in src
 
 
