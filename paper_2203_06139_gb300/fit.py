@@ -362,6 +362,8 @@ def pick_map(timings, tie=0.02):
     the 4096-histogram workload a map with clusters of 8 x 128 threads tied
     with clusters of 2 x 256 over 50 iterations (50.9 against 51.1 ms) but
     took 2.0 s instead of 0.14 s to bring every fit to convergence."""
+    if not timings:
+        raise cg.CgError(cg.ERR_UNSUPPORTED, "no tile map could be planned for this batch")
     fastest = min(t for t, _ in timings)
     near = [(m["cluster_size"], -m["cta_threads"], t, i) for i, (t, m) in enumerate(timings)
             if t <= fastest * (1.0 + tie)]
