@@ -192,8 +192,14 @@ def measured_peaks():
 #    per-Gaussian x terms once per tile): y centre 2, log 13, reciprocal 3,
 #    adjoint seed, value and constant 4 = 22; per (bin, Gaussian kept by
 #    the tile's culling): dy 1, the exponent -(u'^2 + v'^2) 4 (u', v', v'^2
-#    and one FMA), exp2 7, model 1, adjoints 2 + 3 = 18.
-FP64_INSTR = {"mix": 21, "gp1_c1": 22.25, "fit_c4": 29, "fit_c5": 69, "rg2_bin": 22, "rg2_gauss": 18}
+#    and one FMA), exp2 7, model 1, adjoints 2 + 3 = 18 in the direct form;
+#    in tiles of at most 5 kept Gaussians the row recurrence: dy 1, e R 1,
+#    R + R (q - 1) 1, model 1, adjoints 5 = 9 per pair, plus per thread's
+#    run (32 rows of a 64-row tile) and Gaussian the exponent at both ends
+#    10, two exp2 14 and the ratio's exponent 2 = 26.
+FP64_INSTR = {"mix": 21, "gp1_c1": 22.25, "fit_c4": 29, "fit_c5": 69, "rg2_bin": 22, "rg2_gauss": 18,
+              "rg2_gauss_rec": 9, "rg2_run_rec": 26}
+RG2_REC_MAX_KEPT, RG2_ROWS_PER_RUN = 5, 32   # kRgRecMaxKept; kRgTY / (threads per column)
 
 # FP32-pipe operations per unit of the double-float kernels (cg_df64.cuh,
 # cg_df64.cu, cg_models_df64.cuh): event-point of the mixture: two df64
@@ -259,13 +265,13 @@ def sources_hash(files):
 FP64_SOURCES = ["csrc/cg_grad.cu", "csrc/cg_fp64.cuh", "csrc/cg_fp64_tables.inc", "csrc/cg_models_fp64.cuh",
                 "csrc/cg_models.cuh", "csrc/cg_tiles.cuh", "csrc/cg_internal.cuh"]
 NCU_RECORDS = {
-    "k_mix_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "f386c73b18e26683", "workload": [N_EVENTS, N_POINTS],
-                   "dram_bytes": 80714240 + 3789312, "fp64_pipe_pct": 86.75,
+    "k_mix_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "eb7105f17522517a", "workload": [N_EVENTS, N_POINTS],
+                   "dram_bytes": 81323008 + 3812096, "fp64_pipe_pct": 86.77,
                    "profile": "profiles/k_mix_fp64_unbinned_1e7x50.md"},
-    "k_gp1_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "f386c73b18e26683", "dram_bytes": 227840 + 0,
-                   "fp64_pipe_pct": 74.72, "profile": "profiles/k_gp1_fp64_c1_10000bins_100points.md"},
-    "k_rg2_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "f386c73b18e26683", "dram_bytes": 134618624 + 4046336,
-                   "fp64_pipe_pct": 86.79, "profile": "profiles/k_rg2_fp64_c3_4096x4096.md"},
+    "k_gp1_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "eb7105f17522517a", "dram_bytes": 228352 + 0,
+                   "fp64_pipe_pct": 74.61, "profile": "profiles/k_gp1_fp64_c1_10000bins_100points.md"},
+    "k_rg2_fp64": {"sources": FP64_SOURCES, "sources_sha256_16": "eb7105f17522517a", "dram_bytes": 139594752 + 5907200,
+                   "fp64_pipe_pct": 85.80, "profile": "profiles/k_rg2_fp64_c3_4096x4096.md"},
 }
 
 
@@ -648,7 +654,7 @@ def config_c1(args, rates, sm_max_mhz):
     }
 
 
-def _c3_active_pairs(truth_or_theta, K=8, nx=4096, ny=4096, tile=64, cull=80.0):
+def _c3_active_pairs(truth_or_theta, K=8, nx=4096, ny=4096, tile=64, cull=80.0, by_kept=False):
     """(bin, Gaussian) pairs the 2-D kernels evaluate: per 64 x 64 tile, the
     Gaussians whose exponent reaches above -80 somewhere in the tile's box of
     bin centres (the exact maximum of the concave quadratic exponent over the
@@ -666,6 +672,7 @@ def _c3_active_pairs(truth_or_theta, K=8, nx=4096, ny=4096, tile=64, cull=80.0):
     by1 = ((np.minimum(ty + tile, ny) - 0.5) * hy)[:, None]
     nb = (np.minimum(ty + tile, ny) - ty)[:, None] * (np.minimum(tx + tile, nx) - tx)[None, :]
     pairs = 0
+    kept = np.zeros(nb.shape, dtype=np.int64)
     for k in range(K):
         mx, my, sx, sy, phi = th[6 * k + 1:6 * k + 6]
         al, be = -0.5 / (sx * sx), -0.5 / (sy * sy)
@@ -683,6 +690,9 @@ def _c3_active_pairs(truth_or_theta, K=8, nx=4096, ny=4096, tile=64, cull=80.0):
         inside = (X0 <= 0) & (X1 >= 0) & (Y0 <= 0) & (Y1 >= 0)
         m = np.where(inside, 0.0, m)
         pairs += int((~(m < -cull * log2e) * nb).sum())
+        kept += ~(m < -cull * log2e)
+    if by_kept:   # pairs in tiles of each kept count 0 .. K
+        return [int((nb * kept * (kept == c)).sum()) for c in range(K + 1)]
     return pairs
 
 
@@ -716,12 +726,17 @@ def config_c3(args, rates, sm_max_mhz):
         torch.cuda.synchronize()
         out[name] = dict(ms=ms, kern_s=kern, v=float(val.detach()), g=th.grad.detach().cpu().numpy())
     n = 4096 * 4096
-    pairs = _c3_active_pairs(th_np)
-    instr = FP64_INSTR["rg2_bin"] * n + FP64_INSTR["rg2_gauss"] * pairs
-    roof = roofline_fp64("k_rg2_fp64", instr / n, n, out["fp64"]["kern_s"], sm_max_mhz, rates, "bin")
-    roof["work_note"] = ("%.1f Gaussians per bin survive the 64 x 64-bin tiles' culling (%d pairs): %g + %g x %.2f "
-                         "instructions per bin" % (pairs / n, pairs, FP64_INSTR["rg2_bin"], FP64_INSTR["rg2_gauss"],
-                                                   pairs / n))
+    by_kept = _c3_active_pairs(th_np, by_kept=True)
+    pairs = sum(by_kept)
+    p_rec = sum(by_kept[1:RG2_REC_MAX_KEPT + 1])   # the recurrence's tiles (64 rows: every run takes it)
+    g_rec = FP64_INSTR["rg2_gauss_rec"] + FP64_INSTR["rg2_run_rec"] / RG2_ROWS_PER_RUN
+    instr = FP64_INSTR["rg2_bin"] * n + FP64_INSTR["rg2_gauss"] * (pairs - p_rec) + g_rec * p_rec
+    roof = roofline_fp64("k_rg2_fp64", round(instr / n, 3), n, out["fp64"]["kern_s"], sm_max_mhz, rates, "bin")
+    roof["work_note"] = ("%.2f Gaussians per bin survive the 64 x 64-bin tiles' culling (%d pairs), %.0f %% of them in "
+                         "tiles of at most %d kept Gaussians (the row recurrence, %g per pair): %g + %g x %.2f + %g x "
+                         "%.2f instructions per bin" % (pairs / n, pairs, 100.0 * p_rec / pairs, RG2_REC_MAX_KEPT,
+                                                        g_rec, FP64_INSTR["rg2_bin"], FP64_INSTR["rg2_gauss"],
+                                                        (pairs - p_rec) / n, g_rec, p_rec / n))
     roof["algorithmic_bytes"] = n * 8
     rec = ncu_record("k_rg2_fp64")
     roof["traffic"] = rec["dram_bytes"] if rec else None

@@ -317,6 +317,7 @@ static cg_status launch_mix_fp64(MixData d, double* csum, const double* theta, i
 // Gaussian within reach).
 constexpr int kRgTX = 64, kRgTY = 64;
 constexpr double kRgCull = 80.0;
+constexpr int kRgRecMaxKept = 5;   // more kept Gaussians per tile: the direct form (register pressure)
 
 // The rows of one tile for the NA Gaussians kept by its culling: thread ->
 // one column (consecutive threads, consecutive bins of a row), rows r0,
@@ -327,24 +328,75 @@ __device__ __forceinline__ void rg2_tile_rows(const RG2Data& d, int64_t x0, int6
                                               const RG2Act& a, const Fp64Tab& tab, double* red, double* totc,
                                               bool& bad) {
     constexpr int NM = 2 + 6 * NA;
+    constexpr int S = NT / kRgTX;   // rows between a thread's bins
+    constexpr int KA = NA > 0 ? NA : 1;
     double m[NM];
 #pragma unroll
     for (int i = 0; i < NM; ++i) m[i] = 0.0;
     const int col_i = threadIdx.x % kRgTX, r0 = threadIdx.x / kRgTX;
-    if (col_i < w) {
-        // centres lo + (i + 1/2) h as (2i + 1) (h/2) + lo (correctly rounded, one FMA each)
-        const double hhy = 0.5 * d.hy;
-        const int64_t ix = x0 + col_i;
-        RG2Col<NA> col;
-        rg2_col<NA>(fma((double)(2 * ix + 1), 0.5 * d.hx, d.lx), a, col);
-        double cacc[2 + 3 * NA];
+    const bool mine = col_i < w;
+    // centres lo + (i + 1/2) h as (2i + 1) (h/2) + lo (correctly rounded, one FMA each)
+    const double hhy = 0.5 * d.hy;
+    const int64_t ix = x0 + col_i;
+    const int nr = r0 < h ? (h - 1 - r0) / S + 1 : 0;   // this thread's rows
+    const double xc = fma((double)(2 * ix + 1), 0.5 * d.hx, d.lx);
+    double cacc[2 + 3 * NA];
 #pragma unroll
-        for (int i = 0; i < 2 + 3 * NA; ++i) cacc[i] = 0.0;
-        for (int r = r0; r < h; r += NT / kRgTX) {
-            const int64_t iy = y0 + r;
-            rg2_elem_col<NA>(fma((double)(2 * iy + 1), hhy, d.ly), __ldg(d.n + iy * d.nx + ix), C, a, col, tab,
-                             cacc, bad);
+    for (int i = 0; i < 2 + 3 * NA; ++i) cacc[i] = 0.0;
+    // the row recurrence (rg2_act_rec) where every kept Gaussian allows it at
+    // both ends of every thread's run, else the direct form for the whole tile
+    // (the column's constants are taken where they are used, so that the
+    // recurrence loop holds only E, R and the sums); compiled for up to
+    // kRgRecMaxKept kept Gaussians (more: the direct form, register pressure)
+    bool rec = false;
+    if constexpr (NA > 0 && NA <= kRgRecMaxKept) {
+        double E[KA], R[KA];
+        bool fail = h < 3 * S;   // h is the block's: short tiles take the direct form
+        if (mine && !fail) {
+            RG2Col<NA> col;
+            rg2_col<NA>(xc, a, col);
+            const double yf = fma((double)(2 * (y0 + r0) + 1), hhy, d.ly);
+            const double yl = fma((double)(2 * (y0 + r0 + (int64_t)(nr - 1) * S) + 1), hhy, d.ly);
+#pragma unroll
+            for (int j = 0; j < NA; ++j) {
+                double up, vp, ul, vl;
+                const double e0 = rg2_col_exponent<NA>(a, col, j, yf - a.my[j], up, vp);
+                const double el = rg2_col_exponent<NA>(a, col, j, yl - a.my[j], ul, vl);
+                const double lr = -fma(up, a.a2[j], fma(vp, a.b2[j], a.kk[j]));
+                fail |= !(e0 > -1000.0 && el > -1000.0 && fabs(lr) < 1000.0 && fabs(a.qm[j]) < kRgRecQMax);
+                E[j] = exp2_core(e0, tab);   // table index masked: in bounds for any argument
+                R[j] = exp2_core(lr, tab);
+            }
         }
+        rec = __syncthreads_or(fail ? 1 : 0) == 0;
+        if (rec && mine) {
+            int64_t iy = y0 + r0;
+            for (int r = 0; r < nr; ++r, iy += S) {
+                const double y = fma((double)(2 * iy + 1), hhy, d.ly);
+                double dy[KA], e[KA];
+#pragma unroll
+                for (int j = 0; j < NA; ++j) {
+                    dy[j] = y - a.my[j];
+                    e[j] = E[j];
+                    E[j] *= R[j];
+                    R[j] = fma(R[j], a.qm[j], R[j]);
+                }
+                rg2_elem_col_de<NA>(__ldg(d.n + iy * d.nx + ix), C, a, dy, e, tab, cacc, bad);
+            }
+        }
+    }
+    if (mine) {
+        if (!rec) {
+            RG2Col<NA> col;
+            rg2_col<NA>(xc, a, col);
+            for (int r = r0; r < h; r += S) {
+                const int64_t iy = y0 + r;
+                rg2_elem_col<NA>(fma((double)(2 * iy + 1), hhy, d.ly), __ldg(d.n + iy * d.nx + ix), C, a, col,
+                                 tab, cacc, bad);
+            }
+        }
+        RG2Col<NA> col;
+        rg2_col<NA>(xc, a, col);
         rg2_col_moments<NA>(col, cacc, m);
     }
     bad |= nonfinite(m[0]);
@@ -402,7 +454,11 @@ __global__ void __launch_bounds__(NT, 3) k_rg2_fp64(RG2Data d, const double* __r
             }
             const unsigned act = __ballot_sync(0xffffffffu, keep);
             const bool all_ok = __all_sync(0xffffffffu, ok);
-            if (keep) rg2_act_one(cs, k, __popc(act & ((1u << k) - 1u)), ka);
+            if (keep) {
+                const int slot = __popc(act & ((1u << k) - 1u));
+                rg2_act_one(cs, k, slot, ka);
+                rg2_act_rec(slot, (double)(NT / kRgTX) * d.hy, ka);
+            }
             if (k == 0) {
                 cs.C = tht[6 * K];
                 cs_bad = (all_ok && isfinite(cs.C)) ? 0 : 1;

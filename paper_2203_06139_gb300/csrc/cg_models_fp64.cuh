@@ -386,6 +386,9 @@ struct RG2Q {
 struct RG2Act {
     double A[CG_MAX_PEAKS_2D], mx[CG_MAX_PEAKS_2D], my[CG_MAX_PEAKS_2D];
     double sa[CG_MAX_PEAKS_2D], ca[CG_MAX_PEAKS_2D], sb[CG_MAX_PEAKS_2D], cb[CG_MAX_PEAKS_2D];
+    // the row recurrence (rg2_act_rec): 2 sa H, 2 cb H, (sa^2 + cb^2) H^2, and
+    // q - 1 (NaN where |q - 1| is too large for the series: no recurrence)
+    double a2[CG_MAX_PEAKS_2D], b2[CG_MAX_PEAKS_2D], kk[CG_MAX_PEAKS_2D], qm[CG_MAX_PEAKS_2D];
     int k[CG_MAX_PEAKS_2D];   // the Gaussian's index in the parameter vector
     int n;                    // how many survive
 };
@@ -411,6 +414,48 @@ __device__ __forceinline__ void rg2_act_one(const RG2Consts& c, int k, int j, RG
     a.sb[j] = rb * c.sn[k];
     a.cb[j] = rb * c.cs[k];
     a.k[j] = k;
+}
+
+// ---------------------------------------------------------------------------
+// Row recurrence of the factors down a column.  With x fixed the exponent
+// e(dy) = -(u'^2 + v'^2) is a concave parabola in dy, so for the rows
+// dy_j = dy_0 + j H of one thread,
+//   e_{j+1} = e_j R_j,  R_j = 2^(-(u'_j 2 sa H + v'_j 2 cb H + (sa^2 + cb^2) H^2)),
+//   R_{j+1} = R_j q,    q = 2^(-2 (sa^2 + cb^2) H^2)
+// (e_j here the factor 2^e(dy_j)).  After two exponentials at the start of
+// a run each further factor costs a product and an FMA, R + R (q - 1), in
+// place of u', v', v'^2, an FMA and exp2 (11 FP64 instructions).  q - 1 is
+// taken from its Taylor series to degree 8 (|2 (sa^2 + cb^2) H^2| < 2^-6:
+// below 1e-20 absolute), not through the table, so no rounding is shared by
+// all runs of a Gaussian beyond that of (sa^2 + cb^2) H^2 itself (its effect
+// after j steps, j^2/2 |q - 1| 2^-52, stays near 1e-15 on 32 steps); R_0
+// comes from its own exponential per run.  The kernel takes the recurrence
+// only where every kept Gaussian's exponent at both ends of every thread's
+// run is above -1000 (so every factor and ratio is normal), else the direct
+// form for the whole tile.
+// ---------------------------------------------------------------------------
+constexpr double kRgRecQMax = 0.015625;   // |2 (sa^2 + cb^2) H^2| below 2^-6
+
+__device__ __forceinline__ void rg2_act_rec(int j, double H, RG2Act& a) {
+    const double sa = a.sa[j], cb = a.cb[j];
+    a.a2[j] = (2.0 * H) * sa;
+    a.b2[j] = (2.0 * H) * cb;
+    const double kk = fma(sa, sa, cb * cb) * (H * H);
+    a.kk[j] = kk;
+    const double lq = -2.0 * kk;
+    double qm = __longlong_as_double(0x7ff8000000000000LL);
+    if (fabs(lq) < kRgRecQMax) {   // q - 1 = e^z - 1, z = lq ln 2, Horner to degree 8
+        const double z = lq * 0.6931471805599453;
+        double t = 1.0 + z * (1.0 / 8.0);
+        t = fma(z * (1.0 / 7.0), t, 1.0);
+        t = fma(z * (1.0 / 6.0), t, 1.0);
+        t = fma(z * (1.0 / 5.0), t, 1.0);
+        t = fma(z * (1.0 / 4.0), t, 1.0);
+        t = fma(z * (1.0 / 3.0), t, 1.0);
+        t = fma(z * 0.5, t, 1.0);
+        qm = z * t;
+    }
+    a.qm[j] = qm;
 }
 
 // Largest exponent (log2 units) of Gaussian k over the box [X0, X1] x [Y0, Y1]
@@ -468,18 +513,16 @@ __device__ __forceinline__ void rg2_col(double x, const RG2Act& a, RG2Col<NA>& c
     }
 }
 
+// One bin from the kept Gaussians' dy_j and factors e_j (the direct form
+// rg2_elem_col takes them per bin; the row recurrence from the run).
 template <int NA>
-__device__ __forceinline__ void rg2_elem_col(double y, double n, double C, const RG2Act& a, const RG2Col<NA>& col,
-                                             const Fp64Tab& tab, double (&acc)[2 + 3 * NA], bool& bad) {
-    double dy[NA > 0 ? NA : 1], e[NA > 0 ? NA : 1];
+__device__ __forceinline__ void rg2_elem_col_de(double n, double C, const RG2Act& a,
+                                                const double (&dy)[NA > 0 ? NA : 1],
+                                                const double (&e)[NA > 0 ? NA : 1], const Fp64Tab& tab,
+                                                double (&acc)[2 + 3 * NA], bool& bad) {
     double mu = C;
 #pragma unroll
-    for (int j = 0; j < NA; ++j) {
-        dy[j] = y - a.my[j];
-        const double up = fma(a.sa[j], dy[j], col.ua[j]), vp = fma(a.cb[j], dy[j], -col.vb[j]);
-        e[j] = fexp2(fma(-up, up, -(vp * vp)), tab);
-        mu = fma(a.A[j], e[j], mu);
-    }
+    for (int j = 0; j < NA; ++j) mu = fma(a.A[j], e[j], mu);
     const bool npos = __double_as_longlong(n) > 0;
     double L, rm;
     if (fp64_fast_range(mu)) {
@@ -501,6 +544,28 @@ __device__ __forceinline__ void rg2_elem_col(double y, double n, double C, const
         acc[3 + 3 * j] = fma(wy, dy[j], acc[3 + 3 * j]);
     }
     acc[1 + 3 * NA] += g;
+}
+
+template <int NA>
+__device__ __forceinline__ void rg2_elem_col(double y, double n, double C, const RG2Act& a, const RG2Col<NA>& col,
+                                             const Fp64Tab& tab, double (&acc)[2 + 3 * NA], bool& bad) {
+    double dy[NA > 0 ? NA : 1], e[NA > 0 ? NA : 1];
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        dy[j] = y - a.my[j];
+        const double up = fma(a.sa[j], dy[j], col.ua[j]), vp = fma(a.cb[j], dy[j], -col.vb[j]);
+        e[j] = fexp2(fma(-up, up, -(vp * vp)), tab);
+    }
+    rg2_elem_col_de<NA>(n, C, a, dy, e, tab, acc, bad);
+}
+
+// The exponent of slot j at offset dy of a column (rg2_elem_col's form).
+template <int NA>
+__device__ __forceinline__ double rg2_col_exponent(const RG2Act& a, const RG2Col<NA>& col, int j, double dy,
+                                                   double& up, double& vp) {
+    up = fma(a.sa[j], dy, col.ua[j]);
+    vp = fma(a.cb[j], dy, -col.vb[j]);
+    return fma(-up, up, -(vp * vp));
 }
 
 // One thread's column-form sums into (dx, dy) moments (layout above).

@@ -45,6 +45,10 @@ def test_instruction_counts_add_up():
     assert bench.FP64_INSTR["fit_c5"] == 2 + 1 + 3 * (1 + 1 + exp2 + 1) + log + rcp + 2 + 1 + 15 + 2
     assert bench.FP64_INSTR["rg2_gauss"] == 1 + 4 + exp2 + 1 + 2 + 3   # column form
     assert bench.FP64_INSTR["rg2_bin"] == 2 + log + rcp + 4
+    # row recurrence: dy, e R, R + R (q - 1), model, adjoints; per run the exponent at
+    # both ends (dy, u', v', v'^2, FMA each), two exp2, the ratio's exponent (two FMAs)
+    assert bench.FP64_INSTR["rg2_gauss_rec"] == 1 + 1 + 1 + 1 + 2 + 3
+    assert bench.FP64_INSTR["rg2_run_rec"] == 2 * 5 + 2 * exp2 + 2
 
 
 def test_ncu_records_are_null_for_other_sizes_or_sources(monkeypatch):
@@ -100,6 +104,8 @@ def test_culled_pair_count_of_the_2d_kernels():
     narrow = np.array([100.0, 0.5, 0.5, 0.001, 0.001, 0.0, 5.0])
     # r^2 / (2 s^2) <= 80: r <= 0.0126, inside the 2 x 2 tiles of 64 / 1024 around the centre
     assert bench._c3_active_pairs(narrow, K=1, nx=1024, ny=1024) == 4 * 64 * 64
+    # split by the tiles' kept counts (the recurrence takes tiles of at most 5): same total
+    assert bench._c3_active_pairs(narrow, K=1, nx=1024, ny=1024, by_kept=True) == [0, 4 * 64 * 64]
     # elongated along y: the exponent reaches -80 within 0.0126 of the centre in x but
     # everywhere in y (0.5^2 / (2 0.05^2) = 50), so 2 x 16 tiles of 1024^2; rotated by
     # 90 degrees, 16 x 2; the isotropic bound max(sx, sy) would keep far more
